@@ -1,0 +1,518 @@
+#!/usr/bin/env python
+"""Throughput of the particle-filter resampling step on GB300 (one JSON line on stdout).
+
+Workload (the paper's synthetic weight sets, Section 4.1): N = 2^20 particles, x ~ N(0,1),
+log-weight -(x - y)^2/2 with y = 2; Metropolis B from Eq. (B) with eps = 1/100 and
+beta = E(w)/w_max (B = 16); rejection bound log w_max = 0. One step = every resampler
+(multinomial, stratified, systematic, Metropolis, rejection) in binary32 and binary64, each
+followed by Permute (the paper's timing convention: until an ancestry vector satisfying the
+in-place predicate is delivered, Section 4.4), plus the offspring conversions (Codes 11,
+12, prefix sum and adjacent difference) of the systematic output. The metric is ancestors
+delivered per second over the step.
+
+Inputs: a pool of weight vectors per dtype, larger than L2 in total, resident in HBM; step k
+uses the next five vectors of each pool, so no input is re-read from L2 across steps.
+
+  python bench.py [--steps K] [--warmup W] [--gpus N] [--impl ours|reference]
+
+Under torchrun with N > 1 ranks, each rank runs an independent replica on its own GPU
+(resampling one filter does not shard); the value is the total over ranks divided by the
+slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import workload  # noqa: E402
+
+METRIC = "G ancestors/s per resampler at N=2^20 (FP32 vs FP64, % HBM roof); batched filters/s"
+UNIT = "G ancestors/s"
+SCHEME_NAMES = ["multinomial", "stratified", "systematic", "metropolis", "rejection"]
+SEED = 20130115
+L2_BYTES = 129 * 2**20
+
+
+def parse_args():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=30)
+    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--log2n", type=int, default=20)
+    p.add_argument("--y", type=float, default=2.0)
+    p.add_argument("--pool", type=int, default=40, help="weight vectors per dtype")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    return p.parse_args()
+
+
+def workload_params(args):
+    import oracle  # only for B; same formula as the library's rs_metropolis_B
+    N = 1 << args.log2n
+    B = oracle.metropolis_B(0.01, workload.beta_estimate(args.y))
+    return N, B
+
+
+# ---------------------------------------------------------------------------------------
+# distributed helpers (replicas; only timing is reduced)
+# ---------------------------------------------------------------------------------------
+def dist_info():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def dist_init(world, backend):
+    import torch.distributed as dist
+    if world > 1 and not dist.is_initialized():
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        os.environ.setdefault("MASTER_PORT", "29531")
+        dist.init_process_group(backend=backend)
+    return dist
+
+
+def reduce_max(value: float, world: int, device) -> float:
+    """Maximum of a per-rank scalar over all ranks (timing only, not the data path)."""
+    if world <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+# ---------------------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.path = None
+        self.proc = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(prefix="clocks_", suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        if not self.path or not os.path.exists(self.path):
+            return out
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        os.unlink(self.path)
+        if sm:
+            out.update(sm_mhz=statistics.median(sm), sm_max_mhz=max(smax),
+                       reasons=sorted(reasons), samples=len(sm))
+        return out
+
+
+# ---------------------------------------------------------------------------------------
+# algorithmic bytes / operations per kernel launch (roofline numerators)
+# ---------------------------------------------------------------------------------------
+def kernel_roofline_units(label: str, N: int, B: int):
+    """(bound, algorithmic amount per launch, unit) for a traced kernel label."""
+    S = 8 if label.endswith("_f64") else 4
+    V = 8 if (label.endswith("_f64") or label.endswith("_f32c")) else 4
+    if label.startswith("max_") or label.startswith("tile_sum_"):
+        return "hbm", S * N, "B"
+    if label.startswith("emit_systematic_") or label.startswith("emit_stratified_"):
+        return "hbm", S * N + 8 * N, "B"           # read logw, write a and the claims d
+    if label.startswith("emit_W_"):
+        return "hbm", S * N + V * N, "B"           # read logw, write W
+    if label.startswith("search_"):
+        return "hbm", V * N + 8 * N, "B"           # read W once, write a, claim d
+    if label.startswith("metropolis_"):
+        return "alu", B * N, "Philox"              # one Philox4x32-10 draw per step
+    if label.startswith("rejection_"):
+        return "alu", None, "Philox"
+    if label == "permute":
+        return "hbm", 16 * N, "B"                  # read a, d[i], d[a_i]; write c
+    if label == "fill":
+        return "hbm", 4 * N, "B"
+    if label == "offspring":
+        return "hbm", 12 * N, "B"
+    if label.startswith("iscan_"):
+        return "hbm", 8 * N, "B"
+    if label == "cumoff_to_ancestors":
+        return "hbm", 12 * N, "B"
+    return "hbm", None, "B"
+
+
+# ---------------------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------------------
+def run_ours(args):
+    import torch
+    import paper_1301_4019_gb300 as rs
+
+    world, rank, local = dist_info()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist_init(world, "nccl")
+    N, B = workload_params(args)
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) \
+        if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+    peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
+
+    R = max(5, args.pool - args.pool % 5)
+    dtypes = [("f32", np.float32, torch.float32), ("f64", np.float64, torch.float64)]
+    pools = {}
+    for name, npdt, _ in dtypes:
+        pools[name] = [torch.from_numpy(workload.synthetic_logw(N, args.y, seed=SEED + 1000 * r,
+                                                                dtype=npdt)).to(dev)
+                       for r in range(R)]
+    pool_bytes = sum(t.numel() * t.element_size() for p in pools.values() for t in p)
+    outs = {name: [torch.empty(N, dtype=torch.int32, device=dev) for _ in range(5)]
+            for name, _, _ in dtypes}
+    conv = {name: [torch.empty(N, dtype=torch.int32, device=dev) for _ in range(4)]
+            for name, _, _ in dtypes}
+    h = rs.Handle(N)
+
+    def step(k):
+        for name, _, _ in dtypes:
+            for s in range(5):
+                lw = pools[name][(5 * k + s) % R]
+                rs.rs_resample(h, s, lw, B=B, seed=SEED, step=k, out=outs[name][s],
+                               permute=True, log_wmax=0.0)
+        for name, _, _ in dtypes:
+            o, O, o2, a2 = conv[name]
+            rs.rs_offspring(h, outs[name][rs.SYSTEMATIC], o)
+            rs.rs_cumulative_offspring(h, o, O)
+            rs.rs_adjacent_difference(h, O, o2)
+            rs.rs_cumulative_offspring_to_ancestors(h, O, a2)
+
+    ancestors_per_step = 2 * 5 * N
+    stream = torch.cuda.current_stream()
+
+    # --- warm-up (direct launches), status check --------------------------------------
+    for k in range(args.warmup):
+        step(k)
+    st = rs.rs_last_error(h)
+    if st != rs.RS_OK:
+        raise SystemExit(f"device status after warm-up: {rs.rs_strerror(st)}")
+
+    # --- capture one CUDA graph per distinct pool position -----------------------------
+    period = R // 5
+    graphs = []
+    cap_stream = torch.cuda.Stream()
+    cap_stream.wait_stream(stream)
+    with torch.cuda.stream(cap_stream):
+        for p in range(period):
+            g = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(g, stream=cap_stream):
+                step(p)
+            graphs.append(g)
+    stream.wait_stream(cap_stream)
+    for g in graphs:
+        g.replay()
+    torch.cuda.synchronize()
+
+    # --- timed region: K graph replays back to back ------------------------------------
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    barrier(world)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    wall0 = time.perf_counter()
+    e0.record()
+    for k in range(args.steps):
+        graphs[k % period].replay()
+    e1.record()
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    barrier(world)
+    ms_total = e0.elapsed_time(e1)
+    st = rs.rs_last_error(h)
+    if st != rs.RS_OK:
+        raise SystemExit(f"device status after timed region: {rs.rs_strerror(st)}")
+
+    # --- traced steps: per-kernel durations on the launching stream ---------------------
+    n_ev = 256
+    ev_sets = []
+    for k in range(args.steps):
+        evs = [torch.cuda.Event(enable_timing=True) for _ in range(n_ev)]
+        for e in evs:
+            e.record()
+        ev_sets.append(evs)
+    torch.cuda.synchronize()
+    labels_per_step = None
+    durations = {}
+    t_traced0 = torch.cuda.Event(enable_timing=True)
+    t_traced1 = torch.cuda.Event(enable_timing=True)
+    t_traced0.record()
+    for k in range(args.steps):
+        rs.rs_trace(h, ev_sets[k])
+        step(k)
+        labels = rs.rs_trace_labels(h)
+        rs.rs_trace(h, [])
+        if labels_per_step is None:
+            labels_per_step = labels
+    t_traced1.record()
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms_traced_total = t_traced0.elapsed_time(t_traced1)
+    # kernel order inside a step is the same for every step
+    call_of = []
+    call_idx = 0
+    for lab in labels_per_step:
+        call_of.append(call_idx)
+        if lab == "end":
+            call_idx += 1
+    for k in range(args.steps):
+        evs = ev_sets[k]
+        for i, lab in enumerate(labels_per_step[:-1]):
+            if lab == "end":
+                continue
+            durations.setdefault((call_of[i], lab), []).append(evs[i].elapsed_time(evs[i + 1]))
+    gpu_launches_per_step = sum(1 for lab in labels_per_step if lab != "end")
+
+    # per kernel label totals
+    by_label = {}
+    for (_, lab), ds in durations.items():
+        by_label.setdefault(lab, []).extend(ds)
+    total_kernel_ms = sum(sum(v) for v in by_label.values())
+    dom_label = max(by_label, key=lambda lab: sum(by_label[lab]))
+    dom_ms = statistics.mean(by_label[dom_label])
+    launches_per_step_dom = len(by_label[dom_label]) / args.steps
+    bound, amount, unit = kernel_roofline_units(dom_label, N, B)
+    if dom_label.startswith("rejection_"):
+        # expected attempts per call: N + sum_i (1 - w_i/w_max) / p, p = mean(w)/w_max
+        w = np.exp(pools["f64"][0].double().cpu().numpy())
+        amount = int(N + np.sum(1.0 - w) / w.mean())
+    if bound == "hbm" and amount is not None:
+        achieved = amount / (dom_ms * 1e-3) / 1e9
+        roof = {"bound": "hbm", "kernel": dom_label, "achieved": round(achieved, 1),
+                "peak": hbm_peak, "unit": "GB/s", "frac": round(achieved / hbm_peak, 4),
+                "peak_source": peak_src, "traffic": None,
+                "algorithmic_bytes_per_launch": amount}
+    else:
+        philox_peak = 520.0  # G Philox4x32-10 draws/s, measured isolated-loop rate
+        achieved = (amount or 0) / (dom_ms * 1e-3) / 1e9
+        roof = {"bound": "alu", "kernel": dom_label, "achieved": round(achieved, 1),
+                "peak": philox_peak, "unit": "G Philox/s",
+                "frac": round(achieved / philox_peak, 4), "peak_source": "derived",
+                "traffic": None}
+    roof["share_of_step"] = round(sum(by_label[dom_label]) / total_kernel_ms, 4)
+    roof["avg_launch_ms"] = round(dom_ms, 5)
+
+    # per resampler breakdown: sum of the kernels of each resample call
+    per_call = {}
+    for (ci, lab), ds in durations.items():
+        per_call.setdefault(ci, {})[lab] = statistics.mean(ds)
+    per_scheme = {}
+    ci = 0
+    for name, _, _ in dtypes:
+        for s in range(5):
+            t_ms = sum(per_call.get(ci, {}).values())
+            per_scheme[f"{SCHEME_NAMES[s]}_{name}"] = {
+                "ms": round(t_ms, 5), "G_ancestors_per_s": round(N / (t_ms * 1e-3) / 1e9, 3)}
+            ci += 1
+
+    ms_per_step = ms_total / args.steps
+    ms_per_step = reduce_max(ms_per_step, world, dev)
+    value = world * ancestors_per_step / (ms_per_step * 1e-3) / 1e9
+
+    # --- end-to-end through the public API with pinned host buffers ---------------------
+    host_in = {name: [torch.from_numpy(workload.synthetic_logw(
+        N, args.y, seed=SEED + 7 + s, dtype=npdt)).pin_memory() for s in range(5)]
+        for name, npdt, _ in dtypes}
+    host_out = {name: [torch.empty(N, dtype=torch.int32).pin_memory() for _ in range(5)]
+                for name, _, _ in dtypes}
+    dev_in = {name: [torch.empty(N, dtype=tdt, device=dev) for _ in range(5)]
+              for name, _, tdt in dtypes}
+
+    def e2e_step(k):
+        for name, _, _ in dtypes:
+            for s in range(5):
+                dev_in[name][s].copy_(host_in[name][s], non_blocking=True)
+                rs.rs_resample(h, s, dev_in[name][s], B=B, seed=SEED, step=k,
+                               out=outs[name][s], permute=True, log_wmax=0.0)
+                host_out[name][s].copy_(outs[name][s], non_blocking=True)
+
+    for k in range(max(1, args.warmup)):
+        e2e_step(k)
+    torch.cuda.synchronize()
+    barrier(world)
+    f0 = torch.cuda.Event(enable_timing=True)
+    f1 = torch.cuda.Event(enable_timing=True)
+    f0.record()
+    for k in range(args.steps):
+        e2e_step(k)
+    f1.record()
+    torch.cuda.synchronize()
+    ms_e2e = reduce_max(f0.elapsed_time(f1) / args.steps, world, dev)
+    barrier(world)
+    st = rs.rs_last_error(h)
+    if st != rs.RS_OK:
+        raise SystemExit(f"device status after e2e: {rs.rs_strerror(st)}")
+    h2d = sum(t.numel() * t.element_size() for p in host_in.values() for t in p)
+    d2h = sum(t.numel() * t.element_size() for p in host_out.values() for t in p)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(N, B, args.y, budget_s=20.0)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_per_step, 5),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": f"N=2^{args.log2n} single filter, y={args.y}, B={B}, "
+                                   "5 resamplers x {f32, f64} + Permute + offspring conversions",
+                       "N": N, "y": args.y, "metropolis_B": B, "log_wmax": 0.0,
+                       "f32_prefix_sum": "plain binary32",
+                       "parallelism": f"replicas x{world}",
+                       "l2": f"inputs rotate through a {pool_bytes / 2**20:.0f} MiB pool "
+                             f"(> L2 {L2_BYTES // 2**20} MiB); no flush",
+                       "timing": "CUDA-graph replay of K steps, CUDA events"},
+            "e2e": {"value": round(world * ancestors_per_step / (ms_e2e * 1e-3) / 1e9, 3),
+                    "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                    "ms_per_step": round(ms_e2e, 5)},
+            "roofline": roof,
+            "per_scheme": per_scheme,
+            "gpu_launches": gpu_launches_per_step * args.steps,
+            "gpu_launches_per_step": gpu_launches_per_step,
+            "traced_ms_per_step": round(ms_traced_total / args.steps, 5),
+            "wall_s_timed_region": round(wall, 4),
+            "clocks": {"sm_mhz": clk["sm_mhz"], "sm_max_mhz": clk["sm_max_mhz"],
+                       "reasons": clk["reasons"], "samples": clk["samples"]},
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line))
+    h.close()
+
+
+# ---------------------------------------------------------------------------------------
+# the oracle on the host cores: CPU baseline and reference arm
+# ---------------------------------------------------------------------------------------
+def oracle_step(lw_by_dtype, B, seed, step):
+    import oracle
+    n = 0
+    for lw in lw_by_dtype:
+        for s in range(5):
+            st, a = oracle.resample(s, lw, B=B, seed=seed, step=step, log_wmax=0.0,
+                                    permuted=True)
+            assert st == oracle.OK
+            n += len(a)
+    return n
+
+
+def cpu_baseline(N, B, y, budget_s=20.0):
+    """The oracle as it stands, single-threaded, on a bounded sample of the workload."""
+    import oracle
+    oracle.build()
+    lws = [workload.synthetic_logw(N, y, seed=SEED + 99, dtype=np.float32),
+           workload.synthetic_logw(N, y, seed=SEED + 99, dtype=np.float64)]
+    done, t0, reps = 0, time.perf_counter(), 0
+    while True:
+        done += oracle_step(lws, B, SEED, reps)
+        reps += 1
+        if time.perf_counter() - t0 > budget_s / 2 or reps >= 3:
+            break
+    el = time.perf_counter() - t0
+    return {"value": round(done / el / 1e9, 6), "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{reps} pass(es) of the full step workload at N=2^{int(math.log2(N))} "
+                      f"(5 resamplers x 2 dtypes + Permute), single thread, {el:.1f} s"}
+
+
+def run_reference(args):
+    world, rank, _ = dist_info()
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    N, B = workload_params(args)
+    n_sample = min(N, 1 << 18)
+    lws = [workload.synthetic_logw(n_sample, args.y, seed=SEED + 5, dtype=np.float32),
+           workload.synthetic_logw(n_sample, args.y, seed=SEED + 5, dtype=np.float64)]
+    for k in range(args.warmup):
+        oracle_step(lws, B, SEED, k)
+    t0 = time.perf_counter()
+    done = 0
+    for k in range(args.steps):
+        done += oracle_step(lws, B, SEED, k)
+    el = time.perf_counter() - t0
+    value = done / el / 1e9
+    sample = (f"each step: 5 resamplers x 2 dtypes + Permute on a 2^{int(math.log2(n_sample))}-"
+              f"particle sample of the workload (y={args.y}, B={B}), single thread")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": round(value, 6), "unit": UNIT,
+        "n_gpus": 0, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(el / args.steps * 1e3, 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+        "config": {"workload": f"N=2^{args.log2n} single filter, y={args.y}, B={B}, "
+                               "5 resamplers x {f32, f64} + Permute + offspring conversions",
+                   "sample_N": n_sample},
+        "cpu_baseline": {"value": round(value, 6), "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": round(value, 6), "unit": UNIT, "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

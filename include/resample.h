@@ -1,0 +1,171 @@
+/*
+ * resample.h -- C ABI of the GB300 (sm_103a) particle-filter resampling library.
+ *
+ * The operations follow Murray, Lee & Jacob, "Parallel resampling in the particle filter":
+ * the resampling step Ancestors(w) -> a of the SMC loop (Section 1.1, Code 1), done by the
+ * multinomial (Appendix B.1, Code 5), stratified (Appendix B.2, Code 7), systematic
+ * (Appendix B.3, Code 8), Metropolis (Section 2.1, Code 2) and rejection (Section 2.2,
+ * Code 3) resamplers; the ancestor permutation that makes in-place propagation safe
+ * (Section 2.3, Eq. predicate; Appendix C, Code 10); and the ancestors <-> offspring
+ * conversions (Appendix D, Codes 11 and 12, and the primitives of Code 4).
+ *
+ * Conventions for every call:
+ *  - Indices are 0-based: particles are 0..N-1. 1 <= N <= 2^31 - 1.
+ *  - Log-weights are given, not weights (Appendix E). A log-weight may be -inf (a zero
+ *    weight) but not NaN or +inf. All schemes are invariant to adding a constant to every
+ *    log-weight.
+ *  - Pointers named *_dev are device pointers on the handle's device; they are owned by the
+ *    caller, must not overlap one another unless stated, and must stay valid until the
+ *    stream has executed the call. 16-byte alignment of logw gives the fastest loads; any
+ *    alignment of the element type is accepted.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = the legacy default stream). Calls are
+ *    asynchronous on that stream, make no host synchronisation and allocate no memory, so
+ *    they can be captured in a CUDA graph.
+ *  - Return value: RS_OK, or a negative status for errors found on the host before any
+ *    launch (nothing is launched then). Errors that only the device can see (NaN or +inf
+ *    log-weights, all weights zero, a violated rejection bound, the rejection trial cap)
+ *    are recorded in the handle and returned by rs_last_error; outputs of such a call are
+ *    valid indices but otherwise unspecified.
+ *  - Random numbers: draw n of particle (or stratum) i is Philox4x32-10 (Salmon et al.,
+ *    SC'11) with key = seed and counter = (i, n, step mod 2^32, filter * 8 + scheme), so any
+ *    result is reproducible from (seed, step) on any machine.
+ */
+#ifndef RS_RESAMPLE_H
+#define RS_RESAMPLE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------------------- */
+#define RS_OK 0
+#define RS_ERR_ARG (-1)            /* invalid argument (host check) or out-of-range index   */
+#define RS_ERR_NONFINITE (-2)      /* a log-weight is NaN or +inf                           */
+#define RS_ERR_ZERO_WEIGHT (-3)    /* every log-weight is -inf (scan-based schemes)          */
+#define RS_ERR_BOUND_VIOLATED (-4) /* rejection: a log-weight exceeds log_wmax (biased)      */
+#define RS_ERR_REJECTION_CAP (-5)  /* rejection: a particle hit max_trials; it keeps a^i = i */
+#define RS_ERR_TIMEOUT (-6)        /* a bounded device wait gave up                          */
+#define RS_ERR_CUDA (-7)           /* a CUDA runtime call failed                             */
+#define RS_ERR_CAPACITY (-8)       /* N exceeds the handle's max_n                           */
+
+/* ---- enumerations ------------------------------------------------------------------- */
+typedef enum {
+    RS_MULTINOMIAL = 0, /* Appendix B.1, Code 5  */
+    RS_STRATIFIED = 1,  /* Appendix B.2, Code 7  */
+    RS_SYSTEMATIC = 2,  /* Appendix B.3, Code 8  */
+    RS_METROPOLIS = 3,  /* Section 2.1, Code 2   */
+    RS_REJECTION = 4    /* Section 2.2, Code 3   */
+} rs_scheme;
+
+typedef enum { RS_F32 = 0, RS_F64 = 1 } rs_dtype; /* element type of the log-weights */
+
+/* Arithmetic of the prefix sum of the multinomial, stratified and systematic schemes for
+ * RS_F32 log-weights (Section 4.2 and Appendix B.1 discuss its instability in single
+ * precision). RS_F64 always sums in binary64. */
+typedef enum {
+    RS_PREC_PLAIN = 0,      /* binary32 sums: the paper's single-precision setting          */
+    RS_PREC_COMPENSATED = 1 /* two-float (about 48-bit) sums, binary64 tile totals          */
+} rs_precision;
+
+/* Optional per-call settings; pass NULL for the defaults shown. */
+typedef struct {
+    int32_t prec;       /* rs_precision, default RS_PREC_PLAIN                              */
+    double log_wmax;    /* rejection: a-priori bound log w_max on every log-weight, finite;
+                           default 0                                                       */
+    int64_t max_trials; /* rejection: attempts per particle before RS_ERR_REJECTION_CAP;
+                           default 1 << 20                                                 */
+    uint32_t filter;    /* filter id in the random-number counter (< 2^29), default 0; a
+                           single call with filter f reproduces filter f of a batched call  */
+} rs_opts;
+
+/* A handle owns the device scratch of the calls that need it (claim vector d, unpermuted
+ * ancestors, cumulative weights of the multinomial scheme, per-tile partial sums, the
+ * device status word): about 20 bytes per particle of max_n, allocated once here. */
+typedef struct rs_handle rs_handle;
+
+/* Creates a handle for problems of up to max_n particles on `device` (made current).
+ * Returns RS_OK, RS_ERR_ARG or RS_ERR_CUDA (allocation failure). */
+int rs_create(rs_handle** h, int64_t max_n, int device);
+
+/* Frees the handle's device memory. Safe on NULL. */
+int rs_destroy(rs_handle* h);
+
+/* Ancestors(w) -> a (Code 1, line "resample"). Reads N log-weights of type `dtype` from
+ * logw_dev and writes N ancestor indices to ancestors_dev (int32, values 0..N-1).
+ *  scheme  : rs_scheme.
+ *  B       : Metropolis steps per particle (Code 2), >= 0; ignored by other schemes. See
+ *            rs_metropolis_B for the choice of Eq. (B).
+ *  seed    : Philox key; step: SMC time index (counter word 2).
+ *  permute : 0 = the scheme's natural order (stratified and systematic give a
+ *            non-decreasing a); 1 = the result is permuted by Permute (Code 10) so that
+ *            o^i > 0 implies a^i = i (Eq. predicate), ready for in-place propagation.
+ *  opts    : NULL or settings above.
+ * ancestors_dev must not overlap logw_dev. */
+int rs_resample(rs_handle* h, int scheme, int dtype, const void* logw_dev, int64_t N,
+                int32_t B, uint64_t seed, uint64_t step, int32_t* ancestors_dev, int permute,
+                const rs_opts* opts, void* stream);
+
+/* Cumulative weights (Code 4 Inclusive-Prefix-Sum of the max-shifted weights, Appendix E):
+ * W_dev[i] = sum_{j<=i} exp(logw[j] - max logw) in `dtype` (compensated sums are rounded to
+ * binary32 on output), and *log_total_dev (one binary64 on the device) =
+ * max logw + log(sum_j exp(logw[j] - max logw)), the log of the sum of weights. */
+int rs_cumulative_weights(rs_handle* h, int dtype, int prec, const void* logw_dev, int64_t N,
+                          void* W_dev, double* log_total_dev, void* stream);
+
+/* Ancestors-to-Offspring (Code 12): o_dev[j] = #{i : a[i] = j}. Entries of a outside
+ * 0..N-1 are skipped and reported as RS_ERR_ARG through rs_last_error. */
+int rs_offspring(rs_handle* h, const int32_t* a_dev, int64_t N, int32_t* o_dev, void* stream);
+
+/* Offspring -> cumulative offspring: O = Inclusive-Prefix-Sum(o) on int32 (Appendix D). */
+int rs_cumulative_offspring(rs_handle* h, const int32_t* o_dev, int64_t N, int32_t* O_dev,
+                            void* stream);
+
+/* Cumulative offspring -> offspring: Adjacent-Difference of Code 4 (Appendix D). */
+int rs_adjacent_difference(rs_handle* h, const int32_t* O_dev, int64_t N, int32_t* o_dev,
+                           void* stream);
+
+/* Cumulative-Offspring-to-Ancestors (Code 11): particle i fills a[O[i-1] .. O[i]-1].
+ * O must be non-decreasing with O[N-1] = N (checked on the device: RS_ERR_ARG). */
+int rs_cumulative_offspring_to_ancestors(rs_handle* h, const int32_t* O_dev, int64_t N,
+                                         int32_t* a_dev, void* stream);
+
+/* Prepermute (Code 10): d_dev[j] = min{i : a[i] = j}, or N when j has no offspring. */
+int rs_prepermute(rs_handle* h, const int32_t* a_dev, int64_t N, int32_t* d_dev, void* stream);
+
+/* Permute (Code 10): c = a permuted so that o^i > 0 implies c^i = i (Eq. predicate). The
+ * result is the deterministic one of Code 10 (the lowest claimant keeps its slot).
+ * c_dev must not overlap a_dev. */
+int rs_permute(rs_handle* h, const int32_t* a_dev, int64_t N, int32_t* c_dev, void* stream);
+
+/* B* = log(eps) / log(1 - beta) of Eq. (B) (Section 2.1), rounded up: the number of
+ * Metropolis steps that bounds the total-variation distance of every chain by eps, for a
+ * lower bound beta on min_i(mean(w)/w^i) (Eq. beta), e.g. E(w)/w_max (Eq. beta2).
+ * Host-only; writes *B. RS_ERR_ARG unless 0 < eps < 1 and 0 < beta <= 1. */
+int rs_metropolis_B(double eps, double beta, int32_t* B);
+
+/* Synchronises `stream`, returns the first (highest-priority) device-side status recorded
+ * since the previous rs_last_error on this handle, and clears it. */
+int rs_last_error(rs_handle* h, void* stream);
+
+/* Per-kernel timing (an instrumentation aid; the paper times whole calls, Section 4.4).
+ * rs_trace(h, events, n) hands the handle n cudaEvent_t (as void*, created by the caller
+ * with timing enabled); until the next rs_trace call, every call on h records the next
+ * unused event on its stream before each kernel it launches and once after its last
+ * kernel. rs_trace(h, NULL, 0) stops tracing. Events are not recorded while the stream is
+ * being captured into a CUDA graph (do not trace during capture). rs_trace_count returns
+ * how many events were recorded; rs_trace_label(h, i) names the kernel that follows event
+ * i ("end" after the last kernel of a call), or NULL for i out of range. */
+int rs_trace(rs_handle* h, void* const* events, int n);
+int rs_trace_count(const rs_handle* h);
+const char* rs_trace_label(const rs_handle* h, int i);
+
+/* Human-readable text of a status code (static storage). */
+const char* rs_strerror(int status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RS_RESAMPLE_H */

@@ -1,0 +1,295 @@
+"""Python binding of the GB300 resampling library (``include/resample.h``).
+
+Argument marshalling only: every call passes device pointers of torch tensors, sizes and
+the current CUDA stream to the C ABI, and every step of the computation runs in the
+library's own CUDA kernels. There is no CPU fallback: if the shared library cannot be built
+or loaded, every call raises.
+
+The names mirror the C ABI. Operations follow Murray, Lee & Jacob, "Parallel resampling in
+the particle filter" (see the header for the section of each call).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import threading
+
+import torch
+
+from . import _build
+
+# status codes (include/resample.h)
+RS_OK = 0
+RS_ERR_ARG = -1
+RS_ERR_NONFINITE = -2
+RS_ERR_ZERO_WEIGHT = -3
+RS_ERR_BOUND_VIOLATED = -4
+RS_ERR_REJECTION_CAP = -5
+RS_ERR_TIMEOUT = -6
+RS_ERR_CUDA = -7
+RS_ERR_CAPACITY = -8
+
+MULTINOMIAL, STRATIFIED, SYSTEMATIC, METROPOLIS, REJECTION = range(5)
+SCHEMES = {"multinomial": MULTINOMIAL, "stratified": STRATIFIED, "systematic": SYSTEMATIC,
+           "metropolis": METROPOLIS, "rejection": REJECTION}
+F32, F64 = 0, 1
+PREC_PLAIN, PREC_COMPENSATED = 0, 1
+
+EXPORTED = [
+    "rs_create", "rs_destroy", "rs_resample", "rs_cumulative_weights", "rs_offspring",
+    "rs_cumulative_offspring", "rs_adjacent_difference", "rs_cumulative_offspring_to_ancestors",
+    "rs_prepermute", "rs_permute", "rs_metropolis_B", "rs_last_error", "rs_strerror",
+    "rs_trace", "rs_trace_count", "rs_trace_label",
+]
+
+_lock = threading.Lock()
+_lib = None
+
+
+class RsError(RuntimeError):
+    def __init__(self, status: int, what: str = ""):
+        self.status = status
+        super().__init__(f"{what}: {rs_strerror(status)} ({status})" if what else
+                         f"{rs_strerror(status)} ({status})")
+
+
+class _Opts(C.Structure):
+    _fields_ = [("prec", C.c_int32), ("log_wmax", C.c_double), ("max_trials", C.c_int64),
+                ("filter", C.c_uint32)]
+
+
+def library_path() -> str:
+    return _build.LIB_PATH
+
+
+def load(build: bool = True):
+    """Build (if stale) and load the shared library; raises if either fails."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.build() if build else _build.LIB_PATH
+            lib = C.CDLL(path)
+            _declare(lib)
+            _lib = lib
+    return _lib
+
+
+def _declare(lib):
+    P, I64, I32, U64, I = C.c_void_p, C.c_int64, C.c_int32, C.c_uint64, C.c_int
+    sig = {
+        "rs_create": (I, [C.POINTER(P), I64, I]),
+        "rs_destroy": (I, [P]),
+        "rs_resample": (I, [P, I, I, P, I64, I32, U64, U64, P, I, C.POINTER(_Opts), P]),
+        "rs_cumulative_weights": (I, [P, I, I, P, I64, P, P, P]),
+        "rs_offspring": (I, [P, P, I64, P, P]),
+        "rs_cumulative_offspring": (I, [P, P, I64, P, P]),
+        "rs_adjacent_difference": (I, [P, P, I64, P, P]),
+        "rs_cumulative_offspring_to_ancestors": (I, [P, P, I64, P, P]),
+        "rs_prepermute": (I, [P, P, I64, P, P]),
+        "rs_permute": (I, [P, P, I64, P, P]),
+        "rs_metropolis_B": (I, [C.c_double, C.c_double, C.POINTER(I32)]),
+        "rs_last_error": (I, [P, P]),
+        "rs_strerror": (C.c_char_p, [I]),
+        "rs_trace": (I, [P, C.POINTER(C.c_void_p), I]),
+        "rs_trace_count": (I, [P]),
+        "rs_trace_label": (C.c_char_p, [P, I]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+
+
+def _check(status: int, what: str):
+    if status != RS_OK:
+        raise RsError(status, what)
+
+
+def _stream(stream) -> C.c_void_p:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return C.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+
+
+def _dev(t: torch.Tensor, dtype, name: str):
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if dtype is not None and t.dtype not in (dtype if isinstance(dtype, tuple) else (dtype,)):
+        raise TypeError(f"{name} has dtype {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    return C.c_void_p(t.data_ptr())
+
+
+def _dtype_code(t: torch.Tensor) -> int:
+    if t.dtype == torch.float32:
+        return F32
+    if t.dtype == torch.float64:
+        return F64
+    raise TypeError("log-weights must be float32 or float64")
+
+
+class Handle:
+    """Owns the device scratch of one problem size (rs_create / rs_destroy)."""
+
+    def __init__(self, max_n: int, device: int | None = None):
+        lib = load()
+        if device is None:
+            device = torch.cuda.current_device()
+        self.device = device
+        self.max_n = int(max_n)
+        self._h = C.c_void_p()
+        _check(lib.rs_create(C.byref(self._h), self.max_n, device), "rs_create")
+
+    @property
+    def ptr(self):
+        if not self._h:
+            raise RuntimeError("handle is closed")
+        return self._h
+
+    def close(self):
+        if self._h:
+            load().rs_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def rs_resample(h: Handle, scheme: int, logw: torch.Tensor, B: int = 0, seed: int = 0,
+                step: int = 0, out: torch.Tensor | None = None, permute: bool = False,
+                prec: int = PREC_PLAIN, log_wmax: float = 0.0, max_trials: int = 1 << 20,
+                filter: int = 0, stream=None) -> torch.Tensor:
+    """Ancestors(w) -> a for one of the five schemes (optionally permuted, Code 10)."""
+    N = logw.numel()
+    if out is None:
+        out = torch.empty(N, dtype=torch.int32, device=logw.device)
+    opts = _Opts(prec, float(log_wmax), int(max_trials), int(filter))
+    _check(load().rs_resample(h.ptr, int(scheme), _dtype_code(logw),
+                              _dev(logw, (torch.float32, torch.float64), "logw"), N, int(B),
+                              int(seed) & 0xFFFFFFFFFFFFFFFF, int(step) & 0xFFFFFFFFFFFFFFFF,
+                              _dev(out, torch.int32, "out"), 1 if permute else 0,
+                              C.byref(opts), _stream(stream)), "rs_resample")
+    return out
+
+
+def rs_cumulative_weights(h: Handle, logw: torch.Tensor, prec: int = PREC_PLAIN,
+                          W: torch.Tensor | None = None, log_total: torch.Tensor | None = None,
+                          stream=None):
+    """Cumulative max-shifted weights and the log of their sum. Returns (W, log_total)."""
+    N = logw.numel()
+    if W is None:
+        W = torch.empty_like(logw)
+    if log_total is None:
+        log_total = torch.empty(1, dtype=torch.float64, device=logw.device)
+    _check(load().rs_cumulative_weights(h.ptr, _dtype_code(logw), int(prec),
+                                        _dev(logw, None, "logw"), N, _dev(W, logw.dtype, "W"),
+                                        _dev(log_total, torch.float64, "log_total"),
+                                        _stream(stream)), "rs_cumulative_weights")
+    return W, log_total
+
+
+def rs_offspring(h: Handle, a: torch.Tensor, o: torch.Tensor | None = None, stream=None):
+    """Ancestors-to-Offspring (Code 12)."""
+    N = a.numel()
+    if o is None:
+        o = torch.empty(N, dtype=torch.int32, device=a.device)
+    _check(load().rs_offspring(h.ptr, _dev(a, torch.int32, "a"), N, _dev(o, torch.int32, "o"),
+                               _stream(stream)), "rs_offspring")
+    return o
+
+
+def rs_cumulative_offspring(h: Handle, o: torch.Tensor, O: torch.Tensor | None = None,
+                            stream=None):
+    """O = Inclusive-Prefix-Sum(o)."""
+    N = o.numel()
+    if O is None:
+        O = torch.empty(N, dtype=torch.int32, device=o.device)
+    _check(load().rs_cumulative_offspring(h.ptr, _dev(o, torch.int32, "o"), N,
+                                          _dev(O, torch.int32, "O"), _stream(stream)),
+           "rs_cumulative_offspring")
+    return O
+
+
+def rs_adjacent_difference(h: Handle, O: torch.Tensor, o: torch.Tensor | None = None,
+                           stream=None):
+    """o = Adjacent-Difference(O)."""
+    N = O.numel()
+    if o is None:
+        o = torch.empty(N, dtype=torch.int32, device=O.device)
+    _check(load().rs_adjacent_difference(h.ptr, _dev(O, torch.int32, "O"), N,
+                                         _dev(o, torch.int32, "o"), _stream(stream)),
+           "rs_adjacent_difference")
+    return o
+
+
+def rs_cumulative_offspring_to_ancestors(h: Handle, O: torch.Tensor,
+                                         a: torch.Tensor | None = None, stream=None):
+    """Cumulative-Offspring-to-Ancestors (Code 11)."""
+    N = O.numel()
+    if a is None:
+        a = torch.empty(N, dtype=torch.int32, device=O.device)
+    _check(load().rs_cumulative_offspring_to_ancestors(h.ptr, _dev(O, torch.int32, "O"), N,
+                                                       _dev(a, torch.int32, "a"),
+                                                       _stream(stream)),
+           "rs_cumulative_offspring_to_ancestors")
+    return a
+
+
+def rs_prepermute(h: Handle, a: torch.Tensor, d: torch.Tensor | None = None, stream=None):
+    """Prepermute (Code 10): lowest claimant of each slot, or N."""
+    N = a.numel()
+    if d is None:
+        d = torch.empty(N, dtype=torch.int32, device=a.device)
+    _check(load().rs_prepermute(h.ptr, _dev(a, torch.int32, "a"), N, _dev(d, torch.int32, "d"),
+                                _stream(stream)), "rs_prepermute")
+    return d
+
+
+def rs_permute(h: Handle, a: torch.Tensor, c: torch.Tensor | None = None, stream=None):
+    """Permute (Code 10): c with o_i > 0 => c_i = i."""
+    N = a.numel()
+    if c is None:
+        c = torch.empty(N, dtype=torch.int32, device=a.device)
+    _check(load().rs_permute(h.ptr, _dev(a, torch.int32, "a"), N, _dev(c, torch.int32, "c"),
+                             _stream(stream)), "rs_permute")
+    return c
+
+
+def rs_metropolis_B(eps: float, beta: float) -> int:
+    """B* of Eq. (B), rounded up."""
+    B = C.c_int32()
+    _check(load().rs_metropolis_B(float(eps), float(beta), C.byref(B)), "rs_metropolis_B")
+    return B.value
+
+
+def rs_last_error(h: Handle, stream=None) -> int:
+    """Synchronise the stream and return (and clear) the device-side status."""
+    return load().rs_last_error(h.ptr, _stream(stream))
+
+
+def rs_trace(h: Handle, events) -> None:
+    """Record the given torch.cuda.Event objects (already recorded once, so that they exist)
+    around every kernel of the following calls; rs_trace(h, []) stops tracing."""
+    arr = (C.c_void_p * max(1, len(events)))(*[C.c_void_p(e.cuda_event) for e in events])
+    _check(load().rs_trace(h.ptr, arr if events else None, len(events)), "rs_trace")
+
+
+def rs_trace_labels(h: Handle) -> list:
+    """Labels of the events recorded since rs_trace (kernel names, 'end' after each call)."""
+    lib = load()
+    n = lib.rs_trace_count(h.ptr)
+    return [lib.rs_trace_label(h.ptr, i).decode() for i in range(n)]
+
+
+def rs_strerror(status: int) -> str:
+    lib = _lib if _lib is not None else load()
+    return lib.rs_strerror(int(status)).decode()

@@ -1,0 +1,320 @@
+// api.cu -- the C ABI declared in include/resample.h: handle lifetime, host-side argument
+// checks and dispatch to the kernels. No call allocates or synchronises except rs_create,
+// rs_destroy and rs_last_error.
+#include <climits>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <new>
+
+#include "common.cuh"
+#include "internal.h"
+
+struct rs_handle {
+  int device;
+  rsk::Scratch s;
+  rsk::Trace trace;
+};
+
+namespace {
+
+constexpr int64_t kMaxN = 2147483647LL;
+
+inline cudaStream_t as_stream(void* p) { return static_cast<cudaStream_t>(p); }
+
+int set_device(const rs_handle* h) {
+  int cur = -1;
+  if (cudaGetDevice(&cur) != cudaSuccess) return RS_ERR_CUDA;
+  if (cur != h->device && cudaSetDevice(h->device) != cudaSuccess) return RS_ERR_CUDA;
+  return RS_OK;
+}
+
+int check_n(const rs_handle* h, int64_t N) {
+  if (N < 1 || N > kMaxN) return RS_ERR_ARG;
+  if (h && N > h->s.max_n) return RS_ERR_CAPACITY;
+  return RS_OK;
+}
+
+int cuda_status(cudaError_t e) { return e == cudaSuccess ? RS_OK : RS_ERR_CUDA; }
+
+void end_mark(rs_handle* h, cudaStream_t st) { rsk::trace_mark(h->s.trace, "end", st); }
+
+void clear_trace(rs_handle* h) {
+  delete[] h->trace.ev;
+  delete[] h->trace.lbl;
+  h->trace = rsk::Trace{nullptr, nullptr, 0, 0};
+  h->s.trace = nullptr;
+}
+
+void free_scratch(rsk::Scratch& s) {
+  cudaFree(s.d);
+  cudaFree(s.a_tmp);
+  cudaFree(s.W);
+  cudaFree(s.rec);
+  cudaFree(s.blockmax);
+  cudaFree(s.irec);
+  cudaFree(s.glob);
+  cudaFree(s.err);
+  std::memset(&s, 0, sizeof(s));
+}
+
+}  // namespace
+
+extern "C" {
+
+int rs_create(rs_handle** out, int64_t max_n, int device) {
+  if (!out || max_n < 1 || max_n > kMaxN) return RS_ERR_ARG;
+  *out = nullptr;
+  if (cudaSetDevice(device) != cudaSuccess) return RS_ERR_CUDA;
+  rs_handle* h = new (std::nothrow) rs_handle();
+  if (!h) return RS_ERR_CUDA;
+  h->device = device;
+  rsk::Scratch& s = h->s;
+  std::memset(&s, 0, sizeof(s));
+  s.max_n = max_n;
+  s.max_tiles = (max_n + rsk::kTile - 1) / rsk::kTile;
+  s.max_blocks = 152 * 8;
+  bool ok = true;
+  ok &= cudaMalloc(&s.d, sizeof(int32_t) * max_n) == cudaSuccess;
+  ok &= cudaMalloc(&s.a_tmp, sizeof(int32_t) * max_n) == cudaSuccess;
+  ok &= cudaMalloc(&s.W, 8 * static_cast<size_t>(max_n)) == cudaSuccess;
+  ok &= cudaMalloc(&s.rec, sizeof(double2) * 2 * (s.max_tiles + 2)) == cudaSuccess;
+  ok &= cudaMalloc(&s.blockmax, sizeof(double) * s.max_blocks) == cudaSuccess;
+  ok &= cudaMalloc(&s.irec, sizeof(long long) * 2 * (s.max_tiles + 2)) == cudaSuccess;
+  ok &= cudaMalloc(&s.glob, sizeof(rsk::ScanGlob)) == cudaSuccess;
+  ok &= cudaMalloc(&s.err, sizeof(int)) == cudaSuccess;
+  if (ok) {
+    ok &= cudaMemset(s.glob, 0, sizeof(rsk::ScanGlob)) == cudaSuccess;
+    const int none = rsk::kNoError;
+    ok &= cudaMemcpy(s.err, &none, sizeof(int), cudaMemcpyHostToDevice) == cudaSuccess;
+    ok &= cudaDeviceSynchronize() == cudaSuccess;
+  }
+  if (!ok) {
+    free_scratch(s);
+    delete h;
+    return RS_ERR_CUDA;
+  }
+  *out = h;
+  return RS_OK;
+}
+
+int rs_destroy(rs_handle* h) {
+  if (!h) return RS_OK;
+  const int st = set_device(h);
+  clear_trace(h);
+  free_scratch(h->s);
+  delete h;
+  return st;
+}
+
+int rs_trace(rs_handle* h, void* const* events, int n) {
+  if (!h || n < 0 || (n > 0 && !events)) return RS_ERR_ARG;
+  clear_trace(h);
+  if (n == 0) return RS_OK;
+  h->trace.ev = new (std::nothrow) cudaEvent_t[n];
+  h->trace.lbl = new (std::nothrow) const char*[n];
+  if (!h->trace.ev || !h->trace.lbl) {
+    clear_trace(h);
+    return RS_ERR_ARG;
+  }
+  for (int i = 0; i < n; ++i) {
+    h->trace.ev[i] = static_cast<cudaEvent_t>(events[i]);
+    h->trace.lbl[i] = nullptr;
+  }
+  h->trace.n = n;
+  h->trace.pos = 0;
+  h->s.trace = &h->trace;
+  return RS_OK;
+}
+
+int rs_trace_count(const rs_handle* h) { return h ? h->trace.pos : 0; }
+
+const char* rs_trace_label(const rs_handle* h, int i) {
+  if (!h || i < 0 || i >= h->trace.pos) return nullptr;
+  return h->trace.lbl[i];
+}
+
+int rs_resample(rs_handle* h, int scheme, int dtype, const void* logw_dev, int64_t N,
+                int32_t B, uint64_t seed, uint64_t step, int32_t* ancestors_dev, int permute,
+                const rs_opts* opts, void* stream) {
+  if (!h || !logw_dev || !ancestors_dev) return RS_ERR_ARG;
+  int st = check_n(h, N);
+  if (st != RS_OK) return st;
+  if (scheme < RS_MULTINOMIAL || scheme > RS_REJECTION) return RS_ERR_ARG;
+  if (dtype != RS_F32 && dtype != RS_F64) return RS_ERR_ARG;
+  if (permute != 0 && permute != 1) return RS_ERR_ARG;
+  rs_opts o;
+  o.prec = RS_PREC_PLAIN;
+  o.log_wmax = 0.0;
+  o.max_trials = 1 << 20;
+  o.filter = 0;
+  if (opts) o = *opts;
+  if (o.prec != RS_PREC_PLAIN && o.prec != RS_PREC_COMPENSATED) return RS_ERR_ARG;
+  if (!std::isfinite(o.log_wmax)) return RS_ERR_ARG;
+  if (o.max_trials < 1 || o.max_trials > 0xFFFFFFFFLL) return RS_ERR_ARG;
+  if (o.filter >= (1u << 29)) return RS_ERR_ARG;
+  if (scheme == RS_METROPOLIS && B < 0) return RS_ERR_ARG;
+  if ((st = set_device(h)) != RS_OK) return st;
+  const cudaStream_t s = as_stream(stream);
+  const bool f64 = dtype == RS_F64;
+  int32_t* a_out = permute ? h->s.a_tmp : ancestors_dev;
+  int32_t* d = permute ? h->s.d : nullptr;
+  cudaError_t e = cudaSuccess;
+  switch (scheme) {
+    case RS_MULTINOMIAL:
+    case RS_STRATIFIED:
+    case RS_SYSTEMATIC: {
+      const rsk::Acc acc = f64 ? rsk::Acc::F64
+                               : (o.prec == RS_PREC_COMPENSATED ? rsk::Acc::F32C : rsk::Acc::F32);
+      e = rsk::launch_scan_resample(h->s, scheme, acc, logw_dev, N, seed, step, o.filter, a_out,
+                                    d, s);
+      break;
+    }
+    case RS_METROPOLIS:
+      if (d) {
+        rsk::trace_mark(h->s.trace, "fill", s);
+        e = rsk::launch_fill(d, N, static_cast<int32_t>(N), s);
+      }
+      if (e == cudaSuccess)
+        e = rsk::launch_metropolis(h->s, f64, logw_dev, N, B, seed, step, o.filter, a_out, d, s);
+      break;
+    case RS_REJECTION:
+      if (d) {
+        rsk::trace_mark(h->s.trace, "fill", s);
+        e = rsk::launch_fill(d, N, static_cast<int32_t>(N), s);
+      }
+      if (e == cudaSuccess)
+        e = rsk::launch_rejection(h->s, f64, logw_dev, N, o.log_wmax, o.max_trials, seed, step,
+                                  o.filter, a_out, d, s);
+      break;
+  }
+  if (e == cudaSuccess && permute) e = rsk::launch_permute(h->s, a_out, d, N, ancestors_dev, s);
+  end_mark(h, s);
+  return cuda_status(e);
+}
+
+int rs_cumulative_weights(rs_handle* h, int dtype, int prec, const void* logw_dev, int64_t N,
+                          void* W_dev, double* log_total_dev, void* stream) {
+  if (!h || !logw_dev || !W_dev) return RS_ERR_ARG;
+  int st = check_n(h, N);
+  if (st != RS_OK) return st;
+  if (dtype != RS_F32 && dtype != RS_F64) return RS_ERR_ARG;
+  if (prec != RS_PREC_PLAIN && prec != RS_PREC_COMPENSATED) return RS_ERR_ARG;
+  if ((st = set_device(h)) != RS_OK) return st;
+  const rsk::Acc acc = dtype == RS_F64 ? rsk::Acc::F64
+                                       : (prec == RS_PREC_COMPENSATED ? rsk::Acc::F32C : rsk::Acc::F32);
+  const cudaError_t e =
+      rsk::launch_cumulative_weights(h->s, acc, logw_dev, N, W_dev, log_total_dev, as_stream(stream));
+  end_mark(h, as_stream(stream));
+  return cuda_status(e);
+}
+
+int rs_offspring(rs_handle* h, const int32_t* a_dev, int64_t N, int32_t* o_dev, void* stream) {
+  if (!h || !a_dev || !o_dev) return RS_ERR_ARG;
+  int st = check_n(nullptr, N);
+  if (st != RS_OK) return st;
+  if ((st = set_device(h)) != RS_OK) return st;
+  const cudaError_t e = rsk::launch_offspring(h->s, a_dev, N, o_dev, as_stream(stream));
+  end_mark(h, as_stream(stream));
+  return cuda_status(e);
+}
+
+int rs_cumulative_offspring(rs_handle* h, const int32_t* o_dev, int64_t N, int32_t* O_dev,
+                            void* stream) {
+  if (!h || !o_dev || !O_dev) return RS_ERR_ARG;
+  int st = check_n(h, N);
+  if (st != RS_OK) return st;
+  if ((st = set_device(h)) != RS_OK) return st;
+  const cudaError_t e = rsk::launch_inclusive_scan_i32(h->s, o_dev, N, O_dev, as_stream(stream));
+  end_mark(h, as_stream(stream));
+  return cuda_status(e);
+}
+
+int rs_adjacent_difference(rs_handle* h, const int32_t* O_dev, int64_t N, int32_t* o_dev,
+                           void* stream) {
+  if (!h || !O_dev || !o_dev) return RS_ERR_ARG;
+  int st = check_n(nullptr, N);
+  if (st != RS_OK) return st;
+  if ((st = set_device(h)) != RS_OK) return st;
+  rsk::trace_mark(h->s.trace, "adjacent_difference", as_stream(stream));
+  const cudaError_t e = rsk::launch_adjacent_difference(O_dev, N, o_dev, as_stream(stream));
+  end_mark(h, as_stream(stream));
+  return cuda_status(e);
+}
+
+int rs_cumulative_offspring_to_ancestors(rs_handle* h, const int32_t* O_dev, int64_t N,
+                                         int32_t* a_dev, void* stream) {
+  if (!h || !O_dev || !a_dev) return RS_ERR_ARG;
+  int st = check_n(nullptr, N);
+  if (st != RS_OK) return st;
+  if ((st = set_device(h)) != RS_OK) return st;
+  const cudaError_t e = rsk::launch_cumoff_to_ancestors(h->s, O_dev, N, a_dev, as_stream(stream));
+  end_mark(h, as_stream(stream));
+  return cuda_status(e);
+}
+
+int rs_prepermute(rs_handle* h, const int32_t* a_dev, int64_t N, int32_t* d_dev, void* stream) {
+  if (!h || !a_dev || !d_dev) return RS_ERR_ARG;
+  int st = check_n(nullptr, N);
+  if (st != RS_OK) return st;
+  if ((st = set_device(h)) != RS_OK) return st;
+  const cudaError_t e = rsk::launch_prepermute(h->s, a_dev, N, d_dev, true, as_stream(stream));
+  end_mark(h, as_stream(stream));
+  return cuda_status(e);
+}
+
+int rs_permute(rs_handle* h, const int32_t* a_dev, int64_t N, int32_t* c_dev, void* stream) {
+  if (!h || !a_dev || !c_dev || a_dev == c_dev) return RS_ERR_ARG;
+  int st = check_n(h, N);
+  if (st != RS_OK) return st;
+  if ((st = set_device(h)) != RS_OK) return st;
+  const cudaStream_t s = as_stream(stream);
+  cudaError_t e = rsk::launch_prepermute(h->s, a_dev, N, h->s.d, true, s);
+  if (e == cudaSuccess) e = rsk::launch_permute(h->s, a_dev, h->s.d, N, c_dev, s);
+  end_mark(h, s);
+  return cuda_status(e);
+}
+
+int rs_metropolis_B(double eps, double beta, int32_t* B) {
+  if (!B || !(eps > 0.0 && eps < 1.0) || !(beta > 0.0 && beta <= 1.0)) return RS_ERR_ARG;
+  if (beta >= 1.0) {
+    *B = 1;
+    return RS_OK;
+  }
+  const double b = std::ceil(std::log(eps) / std::log1p(-beta));
+  if (!(b <= 2147483647.0)) return RS_ERR_ARG;
+  *B = b < 1.0 ? 1 : static_cast<int32_t>(b);
+  return RS_OK;
+}
+
+int rs_last_error(rs_handle* h, void* stream) {
+  if (!h) return RS_ERR_ARG;
+  int st = set_device(h);
+  if (st != RS_OK) return st;
+  const cudaStream_t s = as_stream(stream);
+  int v = rsk::kNoError;
+  const int none = rsk::kNoError;
+  if (cudaStreamSynchronize(s) != cudaSuccess) return RS_ERR_CUDA;
+  if (cudaMemcpy(&v, h->s.err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return RS_ERR_CUDA;
+  if (cudaMemcpy(h->s.err, &none, sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess)
+    return RS_ERR_CUDA;
+  return v == rsk::kNoError ? RS_OK : -v;
+}
+
+const char* rs_strerror(int status) {
+  switch (status) {
+    case RS_OK: return "ok";
+    case RS_ERR_ARG: return "invalid argument or out-of-range index";
+    case RS_ERR_NONFINITE: return "a log-weight is NaN or +inf";
+    case RS_ERR_ZERO_WEIGHT: return "every weight is zero";
+    case RS_ERR_BOUND_VIOLATED: return "rejection: a log-weight exceeds log_wmax";
+    case RS_ERR_REJECTION_CAP: return "rejection: a particle reached max_trials";
+    case RS_ERR_TIMEOUT: return "a bounded device wait gave up";
+    case RS_ERR_CUDA: return "CUDA runtime error";
+    case RS_ERR_CAPACITY: return "N exceeds the handle's max_n";
+    default: return "unknown status";
+  }
+}
+
+}  // extern "C"

@@ -1,0 +1,253 @@
+// aux.cu -- ancestry permutation (Appendix C, Code 10) and the auxiliary conversions of
+// Appendix D (Codes 11 and 12, Inclusive-Prefix-Sum and Adjacent-Difference of Code 4) on
+// sm_103a. Integer work only: every result is exact.
+#include "common.cuh"
+#include "internal.h"
+
+namespace rsk {
+namespace {
+
+__global__ void __launch_bounds__(kBlock) fill_kernel(int32_t* __restrict__ p, int64_t N, int32_t v) {
+  const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+  for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < N; i += stride)
+    p[i] = v;
+}
+
+// Prepermute: d[a_i] = min(d[a_i], i) (d initialised to the sentinel N beforehand).
+__global__ void __launch_bounds__(kBlock)
+prepermute_kernel(const int32_t* __restrict__ a, int64_t N, int32_t* __restrict__ d, int* err) {
+  const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  const int32_t ai = a[i];
+  if (ai < 0 || ai >= N) {
+    flag_error(err, RS_ERR_ARG);
+    return;
+  }
+  atomicMin(d + ai, static_cast<int32_t>(i));
+}
+
+// Permute (second procedure of Code 10) fused with its gather c^i = a^{d^i}:
+//  - a claimed slot i (d_i < N) keeps its own particle: c_i = a[d_i] = i;
+//  - a particle whose claim failed (d[a_i] != i) walks x = i, d[x], d[d[x]], ... to the
+//    first unclaimed slot x and writes c_x = a_i there.
+// The walks start at indices absent from d and d is injective on claimed slots, so the
+// walks are disjoint and end at distinct unclaimed slots (the termination argument of
+// Appendix C): they only read d, and every slot of c is written exactly once, in any order.
+__global__ void __launch_bounds__(kBlock)
+permute_kernel(const int32_t* __restrict__ a, const int32_t* __restrict__ d, int64_t N,
+               int32_t* __restrict__ c, int* err) {
+  const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  const int32_t sentinel = static_cast<int32_t>(N);
+  const int32_t ai = a[i];
+  if (ai < 0 || ai >= N) {
+    flag_error(err, RS_ERR_ARG);
+    return;
+  }
+  if (d[i] != sentinel) c[i] = static_cast<int32_t>(i);
+  if (d[ai] != static_cast<int32_t>(i)) {
+    int64_t x = i;
+    int64_t steps = 0;
+    for (;;) {
+      const int32_t dx = d[x];
+      if (dx == sentinel) break;
+      if (dx < 0 || dx > sentinel || ++steps > N) {  // only a corrupted d can get here
+        flag_error(err, RS_ERR_ARG);
+        return;
+      }
+      x = dx;
+    }
+    c[x] = ai;
+  }
+}
+
+// Ancestors-to-Offspring (Code 12).
+__global__ void __launch_bounds__(kBlock)
+offspring_kernel(const int32_t* __restrict__ a, int64_t N, int32_t* __restrict__ o, int* err) {
+  const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  const int32_t ai = a[i];
+  if (ai < 0 || ai >= N) {
+    flag_error(err, RS_ERR_ARG);
+    return;
+  }
+  atomicAdd(o + ai, 1);
+}
+
+// Adjacent-Difference: o_i = O_i - O_{i-1} (o_0 = O_0).
+__global__ void __launch_bounds__(kBlock)
+adjacent_difference_kernel(const int32_t* __restrict__ O, int64_t N, int32_t* __restrict__ o) {
+  const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  o[i] = i == 0 ? O[0] : O[i] - O[i - 1];
+}
+
+// Cumulative-Offspring-to-Ancestors (Code 11): particle i fills a[O_{i-1} .. O_i - 1].
+__global__ void __launch_bounds__(kBlock)
+cumoff_to_ancestors_kernel(const int32_t* __restrict__ O, int64_t N, int32_t* __restrict__ a,
+                           int* err) {
+  const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  const int64_t start = i == 0 ? 0 : O[i - 1];
+  const int64_t end = O[i];
+  if (start < 0 || end < start || end > N || (i == N - 1 && end != N)) {
+    flag_error(err, RS_ERR_ARG);
+    return;
+  }
+  for (int64_t j = start; j < end; ++j) a[j] = static_cast<int32_t>(i);
+}
+
+// Integer inclusive prefix sum, reduce-then-scan over tiles of 4096 (exact in int64):
+// pass 1 writes tile totals and the last CTA scans them; pass 2 scans each tile again and
+// adds its prefix.
+__device__ __forceinline__ long long block_tile_scan(const int32_t* __restrict__ in, int64_t N,
+                                                     int64_t base, long long (&v)[16],
+                                                     long long* sh) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  // thread t owns the 16 consecutive elements base + 16 t .. base + 16 t + 15
+  long long run = 0;
+  const int64_t idx = base + 16 * threadIdx.x;
+#pragma unroll
+  for (int q = 0; q < 16; ++q) {
+    const long long x = (idx + q < N) ? in[idx + q] : 0;
+    run += x;
+    v[q] = run;
+  }
+  long long incl = run;
+#pragma unroll
+  for (int dd = 1; dd < 32; dd <<= 1) {
+    const long long y = __shfl_up_sync(0xffffffffu, incl, dd);
+    if (lane >= dd) incl += y;
+  }
+  if (lane == 31) sh[warp] = incl;
+  __syncthreads();
+  long long pw = 0;
+  for (int k = 0; k < warp; ++k) pw += sh[k];
+  const long long excl = pw + incl - run;
+#pragma unroll
+  for (int q = 0; q < 16; ++q) v[q] += excl;
+  long long total = 0;
+  for (int k = 0; k < kWarps; ++k) total += sh[k];
+  return total;
+}
+
+__global__ void __launch_bounds__(kBlock)
+iscan_sum_kernel(const int32_t* __restrict__ in, int64_t N, long long* tot, long long* pre,
+                 unsigned int* ticket) {
+  __shared__ long long sh[kWarps];
+  __shared__ bool am_last;
+  long long v[16];
+  const long long total = block_tile_scan(in, N, static_cast<int64_t>(blockIdx.x) * kTile, v, sh);
+  if (threadIdx.x == 0) {
+    tot[blockIdx.x] = total;
+    __threadfence();
+    am_last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!am_last) return;
+  __threadfence();
+  // exclusive scan of the tile totals: a contiguous chunk per thread, then a block scan
+  const int T = static_cast<int>(gridDim.x);
+  const int chunk = (T + kBlock - 1) / kBlock;
+  const int t0 = min(T, static_cast<int>(threadIdx.x) * chunk), t1 = min(T, t0 + chunk);
+  long long local = 0;
+  for (int t = t0; t < t1; ++t) local += __ldcg(tot + t);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  long long incl = local;
+#pragma unroll
+  for (int dd = 1; dd < 32; dd <<= 1) {
+    const long long y = __shfl_up_sync(0xffffffffu, incl, dd);
+    if (lane >= dd) incl += y;
+  }
+  __syncthreads();
+  if (lane == 31) sh[warp] = incl;
+  __syncthreads();
+  long long p = incl - local;
+  for (int k = 0; k < warp; ++k) p += sh[k];
+  for (int t = t0; t < t1; ++t) {
+    pre[t] = p;
+    p += __ldcg(tot + t);
+  }
+  if (threadIdx.x == 0) *ticket = 0u;
+}
+
+__global__ void __launch_bounds__(kBlock)
+iscan_emit_kernel(const int32_t* __restrict__ in, int64_t N, const long long* pre,
+                  int32_t* __restrict__ out) {
+  __shared__ long long sh[kWarps];
+  long long v[16];
+  const int64_t base = static_cast<int64_t>(blockIdx.x) * kTile;
+  block_tile_scan(in, N, base, v, sh);
+  const long long p = pre[blockIdx.x];
+  const int64_t idx = base + 16 * threadIdx.x;
+#pragma unroll
+  for (int q = 0; q < 16; ++q)
+    if (idx + q < N) out[idx + q] = static_cast<int32_t>(v[q] + p);
+}
+
+inline int grid_for(int64_t N) { return static_cast<int>((N + kBlock - 1) / kBlock); }
+
+}  // namespace
+
+cudaError_t launch_fill(int32_t* p, int64_t N, int32_t v, cudaStream_t st) {
+  int64_t g = (N + kBlock - 1) / kBlock;
+  if (g > 152 * 16) g = 152 * 16;
+  fill_kernel<<<static_cast<int>(g), kBlock, 0, st>>>(p, N, v);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_prepermute(const Scratch& s, const int32_t* a, int64_t N, int32_t* d,
+                              bool init, cudaStream_t st) {
+  if (init) {
+    trace_mark(s.trace, "fill", st);
+    const cudaError_t e = launch_fill(d, N, static_cast<int32_t>(N), st);
+    if (e != cudaSuccess) return e;
+  }
+  trace_mark(s.trace, "prepermute", st);
+  prepermute_kernel<<<grid_for(N), kBlock, 0, st>>>(a, N, d, s.err);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_permute(const Scratch& s, const int32_t* a, const int32_t* d, int64_t N,
+                           int32_t* c, cudaStream_t st) {
+  trace_mark(s.trace, "permute", st);
+  permute_kernel<<<grid_for(N), kBlock, 0, st>>>(a, d, N, c, s.err);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_offspring(const Scratch& s, const int32_t* a, int64_t N, int32_t* o,
+                             cudaStream_t st) {
+  trace_mark(s.trace, "fill", st);
+  cudaError_t e = launch_fill(o, N, 0, st);
+  if (e != cudaSuccess) return e;
+  trace_mark(s.trace, "offspring", st);
+  offspring_kernel<<<grid_for(N), kBlock, 0, st>>>(a, N, o, s.err);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_inclusive_scan_i32(const Scratch& s, const int32_t* o, int64_t N,
+                                      int32_t* O, cudaStream_t st) {
+  const int tiles = static_cast<int>((N + kTile - 1) / kTile);
+  long long* tot = s.irec;
+  long long* pre = s.irec + (s.max_tiles + 2);
+  trace_mark(s.trace, "iscan_sum", st);
+  iscan_sum_kernel<<<tiles, kBlock, 0, st>>>(o, N, tot, pre, &s.glob->ticket_iscan);
+  trace_mark(s.trace, "iscan_emit", st);
+  iscan_emit_kernel<<<tiles, kBlock, 0, st>>>(o, N, pre, O);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_adjacent_difference(const int32_t* O, int64_t N, int32_t* o,
+                                       cudaStream_t st) {
+  adjacent_difference_kernel<<<grid_for(N), kBlock, 0, st>>>(O, N, o);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cumoff_to_ancestors(const Scratch& s, const int32_t* O, int64_t N,
+                                       int32_t* a, cudaStream_t st) {
+  trace_mark(s.trace, "cumoff_to_ancestors", st);
+  cumoff_to_ancestors_kernel<<<grid_for(N), kBlock, 0, st>>>(O, N, a, s.err);
+  return cudaGetLastError();
+}
+
+}  // namespace rsk

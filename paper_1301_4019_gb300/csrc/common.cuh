@@ -1,0 +1,158 @@
+// common.cuh -- device building blocks shared by the resampling kernels (sm_103a):
+// counter-based Philox draws, exact uniforms, the uniform index map, the pinned
+// exponential, the device status word and the value types of the prefix sums.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/resample.h"
+
+namespace rsk {
+
+constexpr int kBlock = 256;          // threads per CTA of the streaming kernels
+constexpr int kTile = 4096;          // particles per CTA tile of the scan kernels
+constexpr int kWarps = kBlock / 32;  // 8 warps
+constexpr int kRows = kTile / (kWarps * 128);  // 4 rows of 128 particles per warp
+
+// ---------------------------------------------------------------------------------------
+// Device status word: holds -status of the highest-priority error seen (lowest value),
+// or INT_MAX when none. RS_ERR_ARG (1) > NONFINITE (2) > ZERO_WEIGHT (3) > BOUND (4) >
+// REJECTION_CAP (5) > TIMEOUT (6).
+// ---------------------------------------------------------------------------------------
+constexpr int kNoError = 0x7fffffff;
+__device__ __forceinline__ void flag_error(int* err, int status) { atomicMin(err, -status); }
+
+// ---------------------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror & Shaw, SC'11): 10 rounds of two 32x32->64 products
+// on counter words 0 and 2, xor-mixed with the other words and the round key; the key is
+// bumped by the golden-ratio and sqrt(3)-1 Weyl constants between rounds.
+// ---------------------------------------------------------------------------------------
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int round = 0; round < 10; ++round) {
+    const uint64_t p0 = static_cast<uint64_t>(0xD2511F53u) * c.x;
+    const uint64_t p1 = static_cast<uint64_t>(0xCD9E8D57u) * c.z;
+    c = make_uint4(static_cast<uint32_t>(p1 >> 32) ^ c.y ^ k0, static_cast<uint32_t>(p1),
+                   static_cast<uint32_t>(p0 >> 32) ^ c.w ^ k1, static_cast<uint32_t>(p0));
+    k0 += 0x9E3779B9u;
+    k1 += 0xBB67AE85u;
+  }
+  return c;
+}
+
+// The draw keying of the library: key = seed; counter = (index, n, step, filter*8+scheme).
+struct Keys {
+  uint32_t k0, k1;  // seed low / high word
+  uint32_t step;    // SMC step mod 2^32
+  uint32_t tag;     // filter * 8 + scheme
+};
+__host__ __device__ inline Keys make_keys(uint64_t seed, uint64_t step, uint32_t filter,
+                                          uint32_t scheme) {
+  Keys k;
+  k.k0 = static_cast<uint32_t>(seed);
+  k.k1 = static_cast<uint32_t>(seed >> 32);
+  k.step = static_cast<uint32_t>(step);
+  k.tag = (filter << 3) | (scheme & 7u);
+  return k;
+}
+__device__ __forceinline__ uint4 draw(const Keys& k, uint32_t index, uint32_t n) {
+  return philox4x32_10(make_uint4(index, n, k.step, k.tag), k.k0, k.k1);
+}
+
+// U[0,1) with 24 (binary32) or 53 (binary64) random bits; both conversions are exact.
+__device__ __forceinline__ float u01_f32(uint4 x) {
+  return __fmul_rn(__uint2float_rn(x.x >> 8), 0x1p-24f);
+}
+__device__ __forceinline__ double u01_f64(uint4 x) {
+  const uint64_t m = (static_cast<uint64_t>(x.x) << 21) | static_cast<uint64_t>(x.y >> 11);
+  return __dmul_rn(__ull2double_rn(m), 0x1p-53);
+}
+template <typename T> __device__ __forceinline__ T u01(uint4 x);
+template <> __device__ __forceinline__ float u01<float>(uint4 x) { return u01_f32(x); }
+template <> __device__ __forceinline__ double u01<double>(uint4 x) { return u01_f64(x); }
+
+// Uniform index on {0..N-1}: the high 64 bits of V * N, V = words 2,3 as a 64-bit integer.
+__device__ __forceinline__ int64_t uniform_index(uint4 x, int64_t N) {
+  const uint64_t v = (static_cast<uint64_t>(x.z) << 32) | x.w;
+  return static_cast<int64_t>(__umul64hi(v, static_cast<uint64_t>(N)));
+}
+
+// ---------------------------------------------------------------------------------------
+// Pinned exponential for x <= 0, identical bit for bit on host and device: Cody & Waite
+// argument reduction (x = k ln2 + r with ln2 split in head and tail), Taylor polynomial of
+// e^r with coefficients 1/n! (degree 7 in binary32, 13 in binary64) in Horner form with
+// fused multiply-adds, exact scaling by 2^k. Every operation is an explicitly rounded
+// IEEE operation, so no compiler contraction can change a result. Below -86.5 (binary32)
+// or -707 (binary64) the result is 0, so that every non-zero result is a normal number.
+// ---------------------------------------------------------------------------------------
+__device__ __forceinline__ float exp_pinned(float x) {
+  if (x != x) return x;
+  if (x < -86.5f) return 0.0f;
+  const float k = rintf(__fmul_rn(x, 0x1.715476p+0f));
+  float r = __fmaf_rn(-k, 0x1.62e430p-1f, x);
+  r = __fmaf_rn(-k, -0x1.05c610p-29f, r);
+  float p = 0x1.a01a02p-13f;            // 1/7!
+  p = __fmaf_rn(p, r, 0x1.6c16c2p-10f);  // 1/6!
+  p = __fmaf_rn(p, r, 0x1.111112p-7f);   // 1/5!
+  p = __fmaf_rn(p, r, 0x1.555556p-5f);   // 1/4!
+  p = __fmaf_rn(p, r, 0x1.555556p-3f);   // 1/3!
+  p = __fmaf_rn(p, r, 0x1p-1f);          // 1/2!
+  p = __fmaf_rn(p, r, 1.0f);             // 1/1!
+  p = __fmaf_rn(p, r, 1.0f);             // 1/0!
+  const int ki = static_cast<int>(k);
+  const float scale = __uint_as_float(static_cast<uint32_t>(ki + 127) << 23);
+  return __fmul_rn(p, scale);
+}
+
+__device__ __forceinline__ double exp_pinned(double x) {
+  if (x != x) return x;
+  if (x < -707.0) return 0.0;
+  const double k = rint(__dmul_rn(x, 0x1.71547652b82fep+0));
+  double r = __fma_rn(-k, 0x1.62e42fefa39efp-1, x);
+  r = __fma_rn(-k, 0x1.abc9e3b39803fp-56, r);
+  double p = 0x1.6124613a86d09p-33;       // 1/13!
+  p = __fma_rn(p, r, 0x1.1eed8eff8d898p-29);  // 1/12!
+  p = __fma_rn(p, r, 0x1.ae64567f544e4p-26);  // 1/11!
+  p = __fma_rn(p, r, 0x1.27e4fb7789f5cp-22);  // 1/10!
+  p = __fma_rn(p, r, 0x1.71de3a556c734p-19);  // 1/9!
+  p = __fma_rn(p, r, 0x1.a01a01a01a01ap-16);  // 1/8!
+  p = __fma_rn(p, r, 0x1.a01a01a01a01ap-13);  // 1/7!
+  p = __fma_rn(p, r, 0x1.6c16c16c16c17p-10);  // 1/6!
+  p = __fma_rn(p, r, 0x1.1111111111111p-7);   // 1/5!
+  p = __fma_rn(p, r, 0x1.5555555555555p-5);   // 1/4!
+  p = __fma_rn(p, r, 0x1.5555555555555p-3);   // 1/3!
+  p = __fma_rn(p, r, 0x1p-1);                 // 1/2!
+  p = __fma_rn(p, r, 1.0);                    // 1/1!
+  p = __fma_rn(p, r, 1.0);                    // 1/0!
+  const long long ki = static_cast<long long>(k);
+  const double scale = __longlong_as_double((ki + 1023LL) << 52);
+  return __dmul_rn(p, scale);
+}
+
+// ---------------------------------------------------------------------------------------
+// Log-weight classification.
+// ---------------------------------------------------------------------------------------
+template <typename T> __device__ __forceinline__ bool nonfinite_logw(T v) {
+  return v != v || v == static_cast<T>(INFINITY);
+}
+template <typename T> __device__ __forceinline__ T neg_inf() { return -static_cast<T>(INFINITY); }
+
+// Order-preserving maps of floats to unsigned integers (for atomicMax of a maximum).
+__device__ __forceinline__ uint32_t ordered_key(float f) {
+  const uint32_t b = __float_as_uint(f);
+  return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+}
+__device__ __forceinline__ float from_ordered_key(uint32_t k) {
+  return __uint_as_float((k & 0x80000000u) ? (k & 0x7fffffffu) : ~k);
+}
+__device__ __forceinline__ unsigned long long ordered_key(double f) {
+  const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(f));
+  return (b & 0x8000000000000000ull) ? ~b : (b | 0x8000000000000000ull);
+}
+__device__ __forceinline__ double from_ordered_key(unsigned long long k) {
+  return __longlong_as_double(static_cast<long long>(
+      (k & 0x8000000000000000ull) ? (k & 0x7fffffffffffffffull) : ~k));
+}
+
+}  // namespace rsk

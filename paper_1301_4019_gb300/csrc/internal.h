@@ -1,0 +1,85 @@
+// internal.h -- launchers shared between the translation units of the library (host side).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace rsk {
+
+// Device-side state of the scan-based schemes (one per handle).
+struct ScanGlob {
+  double M;                  // max log-weight of the current call
+  double S_d;                // total of the max-shifted weights (binary64 view)
+  unsigned int ticket_max;   // last-CTA counters (self-resetting)
+  unsigned int ticket_tile;
+  unsigned int ticket_iscan;
+  unsigned int pad;
+  double2 S_raw;             // total, in the accumulator type of the call
+  double2 scale_raw;         // N / total, in the accumulator type of the call
+};
+
+// Optional per-kernel timing: while enabled, an event is recorded on the call's stream
+// before every kernel launch and after the last kernel of every call, with a label.
+struct Trace {
+  cudaEvent_t* ev;
+  const char** lbl;
+  int n;
+  int pos;
+};
+inline void trace_mark(Trace* t, const char* label, cudaStream_t st) {
+  if (t && t->pos < t->n) {
+    cudaEventRecord(t->ev[t->pos], st);
+    t->lbl[t->pos] = label;
+    ++t->pos;
+  }
+}
+
+struct Scratch {
+  Trace* trace;      // nullptr unless tracing is enabled
+  int32_t* d;        // claim vector (Prepermute), max_n
+  int32_t* a_tmp;    // unpermuted ancestors, max_n
+  void* W;           // cumulative weights of the multinomial scheme, 8 * max_n bytes
+  double2* rec;      // per-tile records: sums then prefixes (two blocks of max_tiles + 2)
+  double* blockmax;  // per-CTA maxima of the max pass
+  long long* irec;   // per-tile records of the integer scan (2 * (max_tiles + 2))
+  ScanGlob* glob;
+  int* err;          // device status word
+  int64_t max_n;
+  int64_t max_tiles;
+  int max_blocks;    // grid of the max pass
+};
+
+enum class Acc { F32, F32C, F64 };
+
+// scan.cu
+cudaError_t launch_scan_resample(const Scratch& s, int scheme, Acc acc, const void* logw,
+                                 int64_t N, uint64_t seed, uint64_t step, uint32_t filter,
+                                 int32_t* a_out, int32_t* d_or_null, cudaStream_t st);
+cudaError_t launch_cumulative_weights(const Scratch& s, Acc acc, const void* logw, int64_t N,
+                                      void* W_out, double* log_total, cudaStream_t st);
+
+// mcmc.cu
+cudaError_t launch_metropolis(const Scratch& s, bool f64, const void* logw, int64_t N,
+                              int32_t B, uint64_t seed, uint64_t step, uint32_t filter,
+                              int32_t* a_out, int32_t* d_or_null, cudaStream_t st);
+cudaError_t launch_rejection(const Scratch& s, bool f64, const void* logw, int64_t N,
+                             double log_wmax, int64_t max_trials, uint64_t seed,
+                             uint64_t step, uint32_t filter, int32_t* a_out,
+                             int32_t* d_or_null, cudaStream_t st);
+
+// aux.cu
+cudaError_t launch_fill(int32_t* p, int64_t N, int32_t v, cudaStream_t st);
+cudaError_t launch_prepermute(const Scratch& s, const int32_t* a, int64_t N, int32_t* d,
+                              bool init, cudaStream_t st);
+cudaError_t launch_permute(const Scratch& s, const int32_t* a, const int32_t* d, int64_t N,
+                           int32_t* c, cudaStream_t st);
+cudaError_t launch_offspring(const Scratch& s, const int32_t* a, int64_t N, int32_t* o,
+                             cudaStream_t st);
+cudaError_t launch_inclusive_scan_i32(const Scratch& s, const int32_t* o, int64_t N,
+                                      int32_t* O, cudaStream_t st);
+cudaError_t launch_adjacent_difference(const int32_t* O, int64_t N, int32_t* o,
+                                       cudaStream_t st);
+cudaError_t launch_cumoff_to_ancestors(const Scratch& s, const int32_t* O, int64_t N,
+                                       int32_t* a, cudaStream_t st);
+
+}  // namespace rsk

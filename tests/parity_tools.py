@@ -1,0 +1,102 @@
+"""Comparison rules of the GPU parity tests (test infrastructure; uses the oracle only).
+
+Metropolis, rejection, Permute and the integer conversions must match the oracle bit for
+bit. The multinomial, stratified and systematic resamplers add the weights in a different
+order than the oracle's sequential sum, so an output may differ only where the draw lies
+within the rounding bound of a cumulative-weight boundary. The bound used here:
+
+  kernel:  |W_i - W*_i| <= KERNEL_C * eps_acc * W^N     (W* = exact prefix of the same
+           weights; KERNEL_C covers the <= 30 roundings on any path of the tile scan, the
+           tile-prefix rounding and the final add; eps_acc = 2^-24 binary32, 2^-44 two-float,
+           2^-53 binary64)
+  oracle:  |W^o_i - W*_i| <= i * eps_dtype * W*_i        (sequential sum, Higham's bound)
+
+and r = N W / W^N inherits N times these relative bounds (plus a few roundings of the
+product). Mismatching positions are counted and returned so the tests can report them.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+import oracle
+
+KERNEL_C = 40.0
+EPS = {"f32": 2.0 ** -24, "f32c": 2.0 ** -44, "f64": 2.0 ** -53}
+EPS_DTYPE = {"f32": 2.0 ** -24, "f32c": 2.0 ** -24, "f64": 2.0 ** -53}
+
+
+def truth_prefix(lw: np.ndarray):
+    """Exact (double-double) prefix of the oracle's max-shifted weights: (Wstar, S)."""
+    st, w, _ = oracle.weights(lw)
+    assert st == oracle.OK
+    hi, lo = oracle.dd_prefix(w.astype(np.float64))
+    return hi + lo, hi[-1] + lo[-1]
+
+
+def _dist_to_int(x):
+    return np.abs(x - np.round(x))
+
+
+def offspring_from_ancestors(a: np.ndarray, N: int) -> np.ndarray:
+    return np.bincount(a, minlength=N).astype(np.int64)
+
+
+def cumulative_mismatches(kind: str, scheme: int, lw: np.ndarray, O_kernel: np.ndarray,
+                          O_oracle: np.ndarray, seed: int, step: int = 0, filter_: int = 0,
+                          oracle_is_sequential: bool = True):
+    """Positions where the cumulative offspring differ, and whether every one of them is
+    within the rounding bound of a boundary. Returns (n_mismatch, n_unexplained)."""
+    N = len(lw)
+    diff = np.nonzero(O_kernel != O_oracle)[0]
+    if len(diff) == 0:
+        return 0, 0
+    Wstar, S = truth_prefix(lw)
+    r = N * (Wstar / S)
+    tol_k = N * (KERNEL_C + 4) * EPS[kind]
+    idx = np.arange(N, dtype=np.float64)
+    tol_o = (N * (idx + 4) * EPS_DTYPE[kind]) if oracle_is_sequential else 0.0
+    tol = tol_k + tol_o + N * 8 * 2.0 ** -53
+    f32 = lw.dtype == np.float32
+    u01 = oracle.u01_f32 if f32 else oracle.u01_f64
+    if scheme == oracle.SYSTEMATIC:
+        u = u01(oracle.draw(seed, 0, 0, step, filter_, oracle.SYSTEMATIC))
+        near = _dist_to_int(r + u) <= tol
+    else:
+        near = _dist_to_int(r) <= tol
+        k = np.clip(np.floor(r).astype(np.int64), 0, N - 1)
+        for dk in (-1, 0, 1):
+            kk = np.clip(k + dk, 0, N - 1)
+            uk = np.array([u01(oracle.draw(seed, int(x), 0, step, filter_, oracle.STRATIFIED))
+                           for x in kk[diff]])
+            near_d = np.zeros(N, bool)
+            near_d[diff] = _dist_to_int(r[diff] + uk) <= (tol[diff] if np.ndim(tol) else tol)
+            near |= near_d
+    # the particle's own count changes with its own O and the previous one's
+    bad = [i for i in diff if not (near[i] or (i > 0 and near[i - 1]))]
+    return len(diff), len(bad)
+
+
+def multinomial_mismatches(kind: str, lw: np.ndarray, a_kernel: np.ndarray,
+                           a_oracle: np.ndarray, seed: int, step: int = 0, filter_: int = 0,
+                           oracle_is_sequential: bool = True):
+    """Output positions where the multinomial ancestors differ; each must have its draw
+    u_i = U_i W^N within the bound of a cumulative weight between the two answers."""
+    N = len(lw)
+    diff = np.nonzero(a_kernel != a_oracle)[0]
+    if len(diff) == 0:
+        return 0, 0
+    Wstar, S = truth_prefix(lw)
+    f32 = lw.dtype == np.float32
+    u01 = oracle.u01_f32 if f32 else oracle.u01_f64
+    bad = 0
+    for i in diff:
+        U = u01(oracle.draw(seed, int(i), 0, step, filter_, oracle.MULTINOMIAL))
+        u = U * S
+        lo, hi = sorted((int(a_kernel[i]), int(a_oracle[i])))
+        tol = (KERNEL_C + 4) * EPS[kind] * S + 4 * 2.0 ** -53 * S
+        if oracle_is_sequential:
+            tol += (hi + 4) * EPS_DTYPE[kind] * S
+        js = np.arange(max(lo - 1, 0), hi + 1)
+        if not np.any(np.abs(Wstar[js] - u) <= tol):
+            bad += 1
+    return len(diff), bad

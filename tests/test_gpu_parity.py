@@ -1,0 +1,335 @@
+"""GPU parity: the CUDA library (called through the C ABI) against the CPU oracle on the same
+seeded inputs. Bit-exact for Metropolis, rejection, Permute and the integer conversions;
+the scan-based resamplers may differ only at draws within the rounding bound of a
+cumulative-weight boundary (counted, see parity_tools)."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import workload
+from parity_tools import cumulative_mismatches, multinomial_mismatches, truth_prefix
+
+pytestmark = pytest.mark.gpu
+
+SIZES = [1, 2, 3, 5, 127, 1000, 4096, 4097, 12289, 65539]
+DEV = "cuda:0"
+
+
+@pytest.fixture(scope="module")
+def h(rs):
+    handle = rs.Handle(1 << 21)
+    yield handle
+    handle.close()
+
+
+def _lw(N, y, dtype, seed=3):
+    return workload.synthetic_logw(N, y, seed=seed + N, dtype=dtype)
+
+
+def _run(rs, h, scheme, lw, **kw):
+    t = torch.from_numpy(lw).to(DEV)
+    a = rs.rs_resample(h, scheme, t, **kw)
+    st = rs.rs_last_error(h)
+    return st, a.cpu().numpy()
+
+
+# ---------------------------------------------------------------------------------------
+# Metropolis and rejection: bit-exact
+# ---------------------------------------------------------------------------------------
+@pytest.mark.parametrize("dtype", [np.float32, np.float64])
+@pytest.mark.parametrize("N", SIZES)
+def test_metropolis_bit_exact(rs, h, dtype, N):
+    for y, B in [(0.0, 4), (2.0, 16), (4.0, 64), (2.0, 0), (1.0, 7)]:
+        lw = _lw(N, y, dtype)
+        st, a = _run(rs, h, rs.METROPOLIS, lw, B=B, seed=11, step=3)
+        assert st == rs.RS_OK
+        ost, want = oracle.metropolis(lw, B, seed=11, step=3)
+        assert np.array_equal(a, want), (y, B, np.sum(a != want))
+        st, c = _run(rs, h, rs.METROPOLIS, lw, B=B, seed=11, step=3, permute=True)
+        assert st == rs.RS_OK
+        assert np.array_equal(c, oracle.permute(want))
+
+
+@pytest.mark.parametrize("dtype", [np.float32, np.float64])
+@pytest.mark.parametrize("N", SIZES)
+def test_rejection_bit_exact(rs, h, dtype, N):
+    for y in [0.0, 2.0, 4.0]:
+        lw = _lw(N, y, dtype)
+        st, a = _run(rs, h, rs.REJECTION, lw, seed=5, step=1, log_wmax=0.0)
+        ost, want = oracle.rejection(lw, 0.0, seed=5, step=1)
+        assert st == rs.RS_OK and ost == oracle.OK
+        assert np.array_equal(a, want), (y, np.sum(a != want))
+        st, c = _run(rs, h, rs.REJECTION, lw, seed=5, step=1, log_wmax=0.0, permute=True)
+        assert st == rs.RS_OK
+        assert np.array_equal(c, oracle.permute(want))
+
+
+def test_rejection_and_metropolis_statuses(rs, h):
+    lw = np.array([-5.0, -6.0, -7.0, -8.0])
+    st, a = _run(rs, h, rs.REJECTION, lw, seed=1, max_trials=1)
+    ost, want = oracle.rejection(lw, 0.0, seed=1, max_trials=1)
+    assert st == rs.RS_ERR_REJECTION_CAP and ost == oracle.ERR_REJECTION_CAP
+    assert np.array_equal(a, want)
+    lw = np.array([0.5, -1.0, -2.0])
+    st, a = _run(rs, h, rs.REJECTION, lw, seed=1)
+    ost, want = oracle.rejection(lw, 0.0, seed=1)
+    assert st == rs.RS_ERR_BOUND_VIOLATED and ost == oracle.ERR_BOUND_VIOLATED
+    assert np.array_equal(a, want)
+    for scheme in range(5):
+        st, a = _run(rs, h, scheme, np.array([0.0, np.nan, -1.0]), B=4, seed=1)
+        assert st == rs.RS_ERR_NONFINITE, scheme
+        assert a.min() >= 0 and a.max() < 3
+        st, a = _run(rs, h, scheme, np.array([0.0, np.inf, -1.0], np.float32), B=4, seed=1)
+        assert st == rs.RS_ERR_NONFINITE, scheme
+    for scheme in (rs.MULTINOMIAL, rs.STRATIFIED, rs.SYSTEMATIC):
+        st, a = _run(rs, h, scheme, np.full(10, -np.inf), seed=1)
+        assert st == rs.RS_ERR_ZERO_WEIGHT
+        assert np.array_equal(np.sort(a), np.arange(10))
+    assert rs.rs_last_error(h) == rs.RS_OK  # cleared
+
+
+def test_scale_invariance_bit_exact(rs, h):
+    """Adding an exactly representable constant to every log-weight leaves the ancestors of
+    the collective-free schemes unchanged (Appendix E)."""
+    rng = np.random.default_rng(1)
+    lw = -np.round(rng.exponential(2.0, 3000) * 1024) / 1024
+    for c in [16.0, -64.0]:
+        _, a0 = _run(rs, h, rs.METROPOLIS, lw, B=16, seed=3)
+        _, a1 = _run(rs, h, rs.METROPOLIS, lw + c, B=16, seed=3)
+        assert np.array_equal(a0, a1)
+        _, r0 = _run(rs, h, rs.REJECTION, lw, seed=3, log_wmax=0.0)
+        _, r1 = _run(rs, h, rs.REJECTION, lw + c, seed=3, log_wmax=c)
+        assert np.array_equal(r0, r1)
+
+
+# ---------------------------------------------------------------------------------------
+# Scan-based resamplers: equal except near boundaries (counted)
+# ---------------------------------------------------------------------------------------
+KINDS = [("f32", np.float32, 0), ("f32c", np.float32, 1), ("f64", np.float64, 0)]
+
+
+def _check_valid_ancestry(a, lw, sorted_expected):
+    N = len(lw)
+    assert a.min() >= 0 and a.max() < N
+    if sorted_expected:
+        assert np.all(np.diff(a) >= 0)
+    w_zero = lw == -np.inf
+    assert not np.any(w_zero[a]), "a zero-weight particle was selected"
+
+
+@pytest.mark.parametrize("kind,dtype,prec", KINDS)
+@pytest.mark.parametrize("scheme", ["systematic", "stratified"])
+@pytest.mark.parametrize("N", SIZES)
+def test_systematic_stratified_parity(rs, h, kind, dtype, prec, scheme, N):
+    sch = rs.SYSTEMATIC if scheme == "systematic" else rs.STRATIFIED
+    f = oracle.systematic if scheme == "systematic" else oracle.stratified
+    total_mis = 0
+    for y in [0.0, 2.0, 4.0]:
+        lw = _lw(N, y, dtype)
+        if N > 10:
+            lw[N // 3] = -np.inf
+            lw[-2:] = -np.inf  # trailing zero weights
+        st, a = _run(rs, h, sch, lw, seed=21, step=2, prec=prec)
+        assert st == rs.RS_OK
+        _check_valid_ancestry(a, lw, sorted_expected=True)
+        O_k = np.cumsum(np.bincount(a, minlength=N))
+        for oprec in sorted({0, prec}):
+            ost, O_o, _ = f(lw, 21, step=2, prec=oprec)
+            assert ost == oracle.OK
+            n, bad = cumulative_mismatches(kind, sch, lw, O_k, O_o, seed=21, step=2,
+                                           oracle_is_sequential=(oprec == 0))
+            assert bad == 0, (y, oprec, n, bad)
+            total_mis += n
+        # Permute on the kernel's own ancestry is exact
+        st, c = _run(rs, h, sch, lw, seed=21, step=2, prec=prec, permute=True)
+        assert st == rs.RS_OK
+        assert np.array_equal(c, oracle.permute(a))
+    if kind == "f64" or N <= 5:
+        assert total_mis <= 2
+
+
+@pytest.mark.parametrize("kind,dtype,prec", KINDS)
+@pytest.mark.parametrize("N", SIZES)
+def test_multinomial_parity(rs, h, kind, dtype, prec, N):
+    total_mis = 0
+    for y in [0.0, 2.0, 4.0]:
+        lw = _lw(N, y, dtype)
+        if N > 10:
+            lw[N // 2] = -np.inf
+            lw[-1] = -np.inf
+        st, a = _run(rs, h, rs.MULTINOMIAL, lw, seed=8, step=4, prec=prec)
+        assert st == rs.RS_OK
+        _check_valid_ancestry(a, lw, sorted_expected=False)
+        for oprec in sorted({0, prec}):
+            ost, want = oracle.multinomial(lw, 8, step=4, prec=oprec)
+            n, bad = multinomial_mismatches(kind, lw, a, want, seed=8, step=4,
+                                            oracle_is_sequential=(oprec == 0))
+            assert bad == 0, (y, oprec, n, bad)
+            total_mis += n
+        st, c = _run(rs, h, rs.MULTINOMIAL, lw, seed=8, step=4, prec=prec, permute=True)
+        assert st == rs.RS_OK
+        assert np.array_equal(c, oracle.permute(a))
+    if kind == "f64":
+        assert total_mis <= 2
+
+
+@pytest.mark.parametrize("kind,dtype,prec", KINDS)
+def test_scan_schemes_deterministic_and_misaligned(rs, h, kind, dtype, prec):
+    """Two runs give identical results; a log-weight pointer that is not 16-byte aligned
+    (a view starting at element 1) gives the same result as an aligned copy."""
+    N = 20001
+    lw = _lw(N + 1, 2.0, dtype)
+    base = torch.from_numpy(lw).to(DEV)
+    view = base[1:]
+    aligned = view.clone()
+    assert view.data_ptr() % 16 != 0
+    for scheme in (rs.MULTINOMIAL, rs.STRATIFIED, rs.SYSTEMATIC):
+        a1 = rs.rs_resample(h, scheme, aligned, seed=4, prec=prec).cpu()
+        a2 = rs.rs_resample(h, scheme, aligned, seed=4, prec=prec).cpu()
+        a3 = rs.rs_resample(h, scheme, view, seed=4, prec=prec).cpu()
+        assert rs.rs_last_error(h) == rs.RS_OK
+        assert torch.equal(a1, a2) and torch.equal(a1, a3)
+
+
+def test_degenerate_inputs(rs, h):
+    for dtype in (np.float32, np.float64):
+        for scheme in range(5):
+            # N = 1
+            st, a = _run(rs, h, scheme, np.array([-3.0], dtype), B=5, seed=1, log_wmax=0.0)
+            assert st == rs.RS_OK and a.tolist() == [0]
+            # all equal weights
+            lw = np.zeros(777, dtype)
+            st, a = _run(rs, h, scheme, lw, B=5, seed=2, log_wmax=0.0)
+            assert st == rs.RS_OK
+            if scheme in (rs.STRATIFIED, rs.SYSTEMATIC):
+                assert np.array_equal(a, np.arange(777))
+            # one particle carries all the weight
+            lw = np.full(999, -np.inf, dtype)
+            lw[123] = -5.0
+            st, a = _run(rs, h, scheme, lw, B=5, seed=3, log_wmax=0.0, max_trials=1 << 16)
+            if scheme == rs.REJECTION:
+                assert st == rs.RS_ERR_REJECTION_CAP or np.all(a == 123)
+            elif scheme == rs.METROPOLIS:
+                assert st == rs.RS_OK
+            else:
+                assert st == rs.RS_OK and np.all(a == 123)
+
+
+# ---------------------------------------------------------------------------------------
+# Permute and conversions: bit-exact
+# ---------------------------------------------------------------------------------------
+def _adversarial(N, rng):
+    yield np.zeros(N, np.int32)
+    yield np.arange(N, dtype=np.int32)
+    yield np.arange(N - 1, -1, -1, dtype=np.int32)
+    yield np.concatenate([[0], np.arange(N - 1)]).astype(np.int32)
+    yield rng.integers(0, N, N).astype(np.int32)
+    yield np.sort(rng.integers(0, N, N)).astype(np.int32)
+    yield rng.integers(0, max(1, N // 16), N).astype(np.int32)
+
+
+@pytest.mark.parametrize("N", [1, 2, 3, 100, 4096, 4097, 70001])
+def test_permute_prepermute_exact(rs, h, N):
+    rng = np.random.default_rng(N)
+    for a in _adversarial(N, rng):
+        t = torch.from_numpy(a).to(DEV)
+        d = rs.rs_prepermute(h, t).cpu().numpy()
+        c = rs.rs_permute(h, t).cpu().numpy()
+        assert rs.rs_last_error(h) == rs.RS_OK
+        assert np.array_equal(d, oracle.prepermute(a))
+        assert np.array_equal(c, oracle.permute(a))
+
+
+@pytest.mark.parametrize("N", [1, 2, 3, 100, 4096, 4097, 70001])
+def test_conversions_exact(rs, h, N):
+    rng = np.random.default_rng(7 + N)
+    for a in _adversarial(N, rng):
+        t = torch.from_numpy(a).to(DEV)
+        o = rs.rs_offspring(h, t)
+        O = rs.rs_cumulative_offspring(h, o)
+        o2 = rs.rs_adjacent_difference(h, O)
+        a2 = rs.rs_cumulative_offspring_to_ancestors(h, O)
+        assert rs.rs_last_error(h) == rs.RS_OK
+        want_o = oracle.ancestors_to_offspring(a)
+        assert np.array_equal(o.cpu().numpy(), want_o)
+        assert np.array_equal(O.cpu().numpy(), oracle.inclusive_prefix_sum_i32(want_o))
+        assert np.array_equal(o2.cpu().numpy(), want_o)
+        assert np.array_equal(a2.cpu().numpy(),
+                              oracle.cumulative_offspring_to_ancestors(
+                                  oracle.inclusive_prefix_sum_i32(want_o)))
+
+
+def test_conversion_errors_flagged(rs, h):
+    t = torch.tensor([0, 5, 1], dtype=torch.int32, device=DEV)
+    rs.rs_offspring(h, t)
+    assert rs.rs_last_error(h) == rs.RS_ERR_ARG
+    O = torch.tensor([1, 1, 2], dtype=torch.int32, device=DEV)  # O[N-1] != N
+    rs.rs_cumulative_offspring_to_ancestors(h, O)
+    assert rs.rs_last_error(h) == rs.RS_ERR_ARG
+
+
+# ---------------------------------------------------------------------------------------
+# Cumulative weights (float outputs): 1e-12 relative in binary64, 1e-5 in binary32
+# ---------------------------------------------------------------------------------------
+@pytest.mark.parametrize("kind,dtype,prec,tol", [("f32", np.float32, 0, 1e-5),
+                                                 ("f32c", np.float32, 1, 1e-6),
+                                                 ("f64", np.float64, 0, 1e-12)])
+@pytest.mark.parametrize("N", [1, 3, 4096, 4097, 100003])
+def test_cumulative_weights(rs, h, kind, dtype, prec, tol, N):
+    lw = _lw(N, 3.0, dtype)
+    if N > 10:
+        lw[5] = -np.inf
+    t = torch.from_numpy(lw).to(DEV)
+    W, lt = rs.rs_cumulative_weights(h, t, prec=prec)
+    assert rs.rs_last_error(h) == rs.RS_OK
+    W = W.cpu().numpy().astype(np.float64)
+    Wstar, S = truth_prefix(lw)
+    nz = Wstar > 0
+    rel = np.abs(W[nz] - Wstar[nz]) / Wstar[nz]
+    assert rel.max() <= tol, rel.max()
+    assert np.all(np.diff(W) >= 0)
+    m = float(np.max(lw))
+    assert abs(lt.item() - (m + np.log(S))) <= (1e-12 if dtype == np.float64 else 1e-6) * max(1.0, abs(m + np.log(S)))
+
+
+# ---------------------------------------------------------------------------------------
+# Full-size workloads (the benchmark's N = 2^20 in both dtypes)
+# ---------------------------------------------------------------------------------------
+@pytest.mark.parametrize("dtype", [np.float32, np.float64])
+def test_full_size_collective_free_bit_exact(rs, dtype):
+    N = 1 << 20
+    with rs.Handle(N) as hh:
+        lw = workload.synthetic_logw(N, 2.0, seed=20130116, dtype=dtype)
+        st, a = _run(rs, hh, rs.METROPOLIS, lw, B=16, seed=99)
+        assert st == rs.RS_OK
+        assert np.array_equal(a, oracle.metropolis(lw, 16, seed=99)[1])
+        st, a = _run(rs, hh, rs.REJECTION, lw, seed=99, log_wmax=0.0)
+        assert st == rs.RS_OK
+        assert np.array_equal(a, oracle.rejection(lw, 0.0, seed=99)[1])
+
+
+@pytest.mark.parametrize("kind,dtype,prec", KINDS)
+def test_full_size_scan_schemes(rs, kind, dtype, prec):
+    N = 1 << 20
+    with rs.Handle(N) as hh:
+        lw = workload.synthetic_logw(N, 2.0, seed=20130116, dtype=dtype)
+        for sch, f in ((rs.SYSTEMATIC, oracle.systematic), (rs.STRATIFIED, oracle.stratified)):
+            st, a = _run(rs, hh, sch, lw, seed=5, prec=prec)
+            assert st == rs.RS_OK
+            _check_valid_ancestry(a, lw, True)
+            O_k = np.cumsum(np.bincount(a, minlength=N))
+            _, O_t, _ = f(lw, 5, prec=1)
+            n, bad = cumulative_mismatches(kind, sch, lw, O_k, O_t, seed=5,
+                                           oracle_is_sequential=False)
+            assert bad == 0, (sch, n, bad)
+            st, c = _run(rs, hh, sch, lw, seed=5, prec=prec, permute=True)
+            o = np.bincount(a, minlength=N)
+            assert np.all(c[o > 0] == np.nonzero(o > 0)[0])
+            assert np.array_equal(np.sort(c), a)
+        st, a = _run(rs, hh, rs.MULTINOMIAL, lw, seed=5, prec=prec)
+        assert st == rs.RS_OK
+        _check_valid_ancestry(a, lw, False)
+        _, want = oracle.multinomial(lw, 5, prec=1)
+        n, bad = multinomial_mismatches(kind, lw, a, want, seed=5, oracle_is_sequential=False)
+        assert bad == 0
