@@ -340,7 +340,8 @@ def run_ours(args):
                 "peak_source": peak_src, "traffic": None,
                 "algorithmic_bytes_per_launch": amount}
     else:
-        philox_peak = 520.0  # G Philox4x32-10 draws/s, measured isolated-loop rate
+        # G Philox4x32-10 draws/s: 152 SMs x 2070 MHz x 32 IMAD.WIDE/clk/SM / 20 per draw
+        philox_peak = 152 * 2.070 * 32 / 20
         achieved = (amount or 0) / (dom_ms * 1e-3) / 1e9
         roof = {"bound": "alu", "kernel": dom_label, "achieved": round(achieved, 1),
                 "peak": philox_peak, "unit": "G Philox/s",
