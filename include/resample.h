@@ -161,6 +161,31 @@ int rs_trace(rs_handle* h, void* const* events, int n);
 int rs_trace_count(const rs_handle* h);
 const char* rs_trace_label(const rs_handle* h, int i);
 
+/* ---- systematic resampling without any allocation ------------------------------------
+ * The paper has no counterpart to this call: it exists for callers that cannot allocate
+ * device memory -- code running under another framework's memory pool or allocator hooks,
+ * plugins whose host forbids cudaMalloc after start-up, real-time loops that must never wait
+ * on the allocator. It computes exactly what rs_resample(RS_SYSTEMATIC, permute = 0) computes
+ * (same kernels, same results) without a handle: its scratch (about 43 KB) is a static
+ * device array of the library, which every GPU that loads the library keeps until the
+ * process exits. The caller passes only inputs and outputs:
+ *   dtype, logw_dev, N : as for rs_resample; 1 <= N <= RS_NOALLOC_MAX_N, larger N returns
+ *                        RS_ERR_CAPACITY before anything is launched.
+ *   seed, step         : as for rs_resample (filter 0).
+ *   ancestors_dev      : N int32 outputs, non-decreasing.
+ *   status_dev         : NULL, or one device int32 that receives RS_OK or the device-side
+ *                        status (the codes of rs_last_error) when the stream reaches the end
+ *                        of the call.
+ * The first call on each device looks up the device address of the static array
+ * (cudaGetSymbolAddress) with that device current: make that first call before any stream
+ * capture. All calls on a device share the one array and overwrite it: calls that overlap
+ * on the GPU (several streams or host threads at once) race and must be serialised by the
+ * caller. The call allocates and frees nothing. */
+#define RS_NOALLOC_MAX_N (1 << 22)
+int rs_systematic_noalloc(int dtype, const void* logw_dev, int64_t N, uint64_t seed,
+                          uint64_t step, int32_t* ancestors_dev, int32_t* status_dev,
+                          void* stream);
+
 /* Human-readable text of a status code (static storage). */
 const char* rs_strerror(int status);
 

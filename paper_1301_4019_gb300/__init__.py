@@ -38,8 +38,9 @@ EXPORTED = [
     "rs_create", "rs_destroy", "rs_resample", "rs_cumulative_weights", "rs_offspring",
     "rs_cumulative_offspring", "rs_adjacent_difference", "rs_cumulative_offspring_to_ancestors",
     "rs_prepermute", "rs_permute", "rs_metropolis_B", "rs_last_error", "rs_strerror",
-    "rs_trace", "rs_trace_count", "rs_trace_label",
+    "rs_trace", "rs_trace_count", "rs_trace_label", "rs_systematic_noalloc",
 ]
+NOALLOC_MAX_N = 1 << 22
 
 _lock = threading.Lock()
 _lib = None
@@ -92,6 +93,7 @@ def _declare(lib):
         "rs_trace": (I, [P, C.POINTER(C.c_void_p), I]),
         "rs_trace_count": (I, [P]),
         "rs_trace_label": (C.c_char_p, [P, I]),
+        "rs_systematic_noalloc": (I, [I, P, I64, U64, U64, P, P, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -288,6 +290,24 @@ def rs_trace_labels(h: Handle) -> list:
     lib = load()
     n = lib.rs_trace_count(h.ptr)
     return [lib.rs_trace_label(h.ptr, i).decode() for i in range(n)]
+
+
+def rs_systematic_noalloc(logw: torch.Tensor, seed: int = 0, step: int = 0,
+                          out: torch.Tensor | None = None, status: torch.Tensor | None = None,
+                          stream=None) -> torch.Tensor:
+    """Systematic resampling for callers that cannot allocate device memory: no handle, the
+    scratch is a static device array of the library (N <= NOALLOC_MAX_N). Calls that overlap
+    on the GPU race on that array. ``out`` and ``status`` (one int32) are caller buffers."""
+    N = logw.numel()
+    if out is None:
+        out = torch.empty(N, dtype=torch.int32, device=logw.device)
+    st_ptr = _dev(status, torch.int32, "status") if status is not None else None
+    _check(load().rs_systematic_noalloc(_dtype_code(logw), _dev(logw, None, "logw"), N,
+                                        int(seed) & 0xFFFFFFFFFFFFFFFF,
+                                        int(step) & 0xFFFFFFFFFFFFFFFF,
+                                        _dev(out, torch.int32, "out"), st_ptr, _stream(stream)),
+           "rs_systematic_noalloc")
+    return out
 
 
 def rs_strerror(status: int) -> str:
