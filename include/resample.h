@@ -61,12 +61,24 @@ typedef enum {
 
 typedef enum { RS_F32 = 0, RS_F64 = 1 } rs_dtype; /* element type of the log-weights */
 
-/* Arithmetic of the prefix sum of the multinomial, stratified and systematic schemes for
- * RS_F32 log-weights (Section 4.2 and Appendix B.1 discuss its instability in single
- * precision). RS_F64 always sums in binary64. */
+/* Arithmetic of the weights and prefix sums of the multinomial, stratified and systematic
+ * schemes (Section 4.2 and Appendix B.1 discuss the instability of single precision):
+ *   RS_F32 + RS_PREC_PLAIN        binary32 weights and sums (the paper's setting).
+ *   RS_F32 + RS_PREC_COMPENSATED  binary32 weights, two-float sums (about 48 significand
+ *                                 bits), binary64 tile totals.
+ *   RS_F64 + RS_PREC_PLAIN or     double-float: weights exp(lw - max) and sums kept as pairs
+ *            RS_PREC_COMPENSATED  of binary32 (about 48 bits, relative error of every
+ *                                 cumulative weight below 2^-40), binary64 tile totals,
+ *                                 computed on the binary32 pipes (GB300 runs binary64 at
+ *                                 1/57 of the binary32 rate). Draws keep all 53 bits.
+ *   RS_F64 + RS_PREC_BINARY64     IEEE binary64 weights (pinned exp) and sums on the FP64
+ *                                 pipe (slow on GB300).
+ * The Metropolis and rejection schemes ignore this setting: their decisions are always exactly
+ * those of the element type. */
 typedef enum {
-    RS_PREC_PLAIN = 0,      /* binary32 sums: the paper's single-precision setting          */
-    RS_PREC_COMPENSATED = 1 /* two-float (about 48-bit) sums, binary64 tile totals          */
+    RS_PREC_PLAIN = 0,
+    RS_PREC_COMPENSATED = 1,
+    RS_PREC_BINARY64 = 2
 } rs_precision;
 
 /* Optional per-call settings; pass NULL for the defaults shown. */

@@ -32,7 +32,7 @@ MULTINOMIAL, STRATIFIED, SYSTEMATIC, METROPOLIS, REJECTION = range(5)
 SCHEMES = {"multinomial": MULTINOMIAL, "stratified": STRATIFIED, "systematic": SYSTEMATIC,
            "metropolis": METROPOLIS, "rejection": REJECTION}
 F32, F64 = 0, 1
-PREC_PLAIN, PREC_COMPENSATED = 0, 1
+PREC_PLAIN, PREC_COMPENSATED, PREC_BINARY64 = 0, 1, 2
 
 EXPORTED = [
     "rs_create", "rs_destroy", "rs_resample", "rs_cumulative_weights", "rs_offspring",

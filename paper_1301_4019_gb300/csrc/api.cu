@@ -37,6 +37,12 @@ int check_n(const rs_handle* h, int64_t N) {
 
 int cuda_status(cudaError_t e) { return e == cudaSuccess ? RS_OK : RS_ERR_CUDA; }
 
+// Accumulation of the scan-based schemes for a (dtype, precision) pair (checked before).
+rsk::Acc accumulation(int dtype, int prec) {
+  if (dtype == RS_F64) return prec == RS_PREC_BINARY64 ? rsk::Acc::F64N : rsk::Acc::F64;
+  return prec == RS_PREC_COMPENSATED ? rsk::Acc::F32C : rsk::Acc::F32;
+}
+
 void end_mark(rs_handle* h, cudaStream_t st) { rsk::trace_mark(h->s.trace, "end", st); }
 
 void clear_trace(rs_handle* h) {
@@ -149,7 +155,9 @@ int rs_resample(rs_handle* h, int scheme, int dtype, const void* logw_dev, int64
   o.max_trials = 1 << 20;
   o.filter = 0;
   if (opts) o = *opts;
-  if (o.prec != RS_PREC_PLAIN && o.prec != RS_PREC_COMPENSATED) return RS_ERR_ARG;
+  if (o.prec != RS_PREC_PLAIN && o.prec != RS_PREC_COMPENSATED && o.prec != RS_PREC_BINARY64)
+    return RS_ERR_ARG;
+  if (o.prec == RS_PREC_BINARY64 && dtype != RS_F64) return RS_ERR_ARG;
   if (!std::isfinite(o.log_wmax)) return RS_ERR_ARG;
   if (o.max_trials < 1 || o.max_trials > 0xFFFFFFFFLL) return RS_ERR_ARG;
   if (o.filter >= (1u << 29)) return RS_ERR_ARG;
@@ -164,8 +172,7 @@ int rs_resample(rs_handle* h, int scheme, int dtype, const void* logw_dev, int64
     case RS_MULTINOMIAL:
     case RS_STRATIFIED:
     case RS_SYSTEMATIC: {
-      const rsk::Acc acc = f64 ? rsk::Acc::F64
-                               : (o.prec == RS_PREC_COMPENSATED ? rsk::Acc::F32C : rsk::Acc::F32);
+      const rsk::Acc acc = accumulation(dtype, o.prec);
       e = rsk::launch_scan_resample(h->s, scheme, acc, logw_dev, N, seed, step, o.filter, a_out,
                                     d, s);
       break;
@@ -199,10 +206,11 @@ int rs_cumulative_weights(rs_handle* h, int dtype, int prec, const void* logw_de
   int st = check_n(h, N);
   if (st != RS_OK) return st;
   if (dtype != RS_F32 && dtype != RS_F64) return RS_ERR_ARG;
-  if (prec != RS_PREC_PLAIN && prec != RS_PREC_COMPENSATED) return RS_ERR_ARG;
+  if (prec != RS_PREC_PLAIN && prec != RS_PREC_COMPENSATED && prec != RS_PREC_BINARY64)
+    return RS_ERR_ARG;
+  if (prec == RS_PREC_BINARY64 && dtype != RS_F64) return RS_ERR_ARG;
   if ((st = set_device(h)) != RS_OK) return st;
-  const rsk::Acc acc = dtype == RS_F64 ? rsk::Acc::F64
-                                       : (prec == RS_PREC_COMPENSATED ? rsk::Acc::F32C : rsk::Acc::F32);
+  const rsk::Acc acc = accumulation(dtype, prec);
   const cudaError_t e =
       rsk::launch_cumulative_weights(h->s, acc, logw_dev, N, W_dev, log_total_dev, as_stream(stream));
   end_mark(h, as_stream(stream));

@@ -49,7 +49,9 @@ struct Scratch {
   int max_blocks;    // grid of the max pass
 };
 
-enum class Acc { F32, F32C, F64 };
+// Accumulation of the scan-based schemes: binary32, two-float over binary32 inputs,
+// double-float over binary64 inputs (binary32 pipes), native binary64 (FP64 pipe).
+enum class Acc { F32, F32C, F64, F64N };
 
 // scan.cu
 cudaError_t launch_scan_resample(const Scratch& s, int scheme, Acc acc, const void* logw,

@@ -21,18 +21,84 @@
 // clamped into [P_t, P_{t+1}] with P monotone. Cumulative weights are therefore
 // non-decreasing, the cumulative offspring too, and Code 11 writes every position of the
 // ancestry vector exactly once.
+//
+// Accumulators (input type T, accumulator V): binary32 (float, float), two-float
+// (float, float2), double-float for binary64 inputs on the binary32 pipes (double, float2:
+// weights by exp_df, GB300 runs binary64 at 1/57 rate), native binary64 (double, double).
 #include <cfloat>
 #include <climits>
 
 #include "common.cuh"
+#include "dfexp.cuh"
 #include "internal.h"
 #include "values.cuh"
 
 namespace rsk {
 namespace {
 
-__device__ __forceinline__ float sub_rn(float a, float b) { return __fsub_rn(a, b); }
-__device__ __forceinline__ double sub_rn(double a, double b) { return __dsub_rn(a, b); }
+// ---------------------------------------------------------------------------------------
+// Weights and uniforms per (input type, accumulator type)
+// ---------------------------------------------------------------------------------------
+struct WeightCtx {
+  double Md;          // maximum log-weight
+  float Mf;           // as binary32 (binary32 inputs: exact)
+  float2 M2;          // as two-float (double-float path)
+  const float2* tab;  // 2^(j/64) table in shared memory (double-float path)
+};
+
+template <typename T, typename V> struct Path;
+template <> struct Path<float, float> {
+  using U = float;
+  static constexpr int id = 0;
+  static constexpr bool kTable = false;
+  __device__ static float weight(float x, const WeightCtx& c) {
+    return (x == neg_inf<float>()) ? 0.0f : exp_pinned(__fsub_rn(x, c.Mf));
+  }
+  __device__ static U draw_u(uint4 x) { return u01_f32(x); }
+};
+template <> struct Path<float, float2> {
+  using U = float;
+  static constexpr int id = 1;
+  static constexpr bool kTable = false;
+  __device__ static float2 weight(float x, const WeightCtx& c) {
+    return make_float2((x == neg_inf<float>()) ? 0.0f : exp_pinned(__fsub_rn(x, c.Mf)), 0.0f);
+  }
+  __device__ static U draw_u(uint4 x) { return u01_f32(x); }
+};
+template <> struct Path<double, float2> {
+  using U = float2;
+  static constexpr int id = 2;
+  static constexpr bool kTable = true;
+  __device__ static float2 weight(double x, const WeightCtx& c) {
+    if (x == neg_inf<double>()) return make_float2(0.0f, 0.0f);
+    return exp_df(add22_accurate(split_f64(x), neg2(c.M2)), c.tab);
+  }
+  __device__ static U draw_u(uint4 x) { return u01_f2(x); }
+};
+template <> struct Path<double, double> {
+  using U = double;
+  static constexpr int id = 3;
+  static constexpr bool kTable = false;
+  __device__ static double weight(double x, const WeightCtx& c) {
+    return (x == neg_inf<double>()) ? 0.0 : exp_pinned(__dsub_rn(x, c.Md));
+  }
+  __device__ static U draw_u(uint4 x) { return u01_f64(x); }
+};
+
+// Builds the weight context (and stages the exp table in shared memory when needed).
+template <typename T, typename V>
+__device__ __forceinline__ WeightCtx make_ctx(double Md, float2* sh_tab) {
+  WeightCtx c;
+  c.Md = Md;
+  c.Mf = static_cast<float>(Md);
+  c.M2 = split_f64(Md);
+  c.tab = sh_tab;
+  if constexpr (Path<T, V>::kTable) {
+    if (threadIdx.x < 64) sh_tab[threadIdx.x] = kExp2Frac64[threadIdx.x];
+    __syncthreads();
+  }
+  return c;
+}
 
 // Reads the 4 consecutive log-weights idx..idx+3 (positions >= N read as -inf).
 template <typename T>
@@ -62,22 +128,22 @@ __device__ __forceinline__ int tile_offset(int warp, int r, int lane, int q) {
 // the tile up to and including the element (r, q) of this thread, as computed by a fixed
 // tree: sequential inside a lane, Hillis-Steele across the 32 lanes of a row, a running
 // carry across the 4 rows of a warp, and a sequential prefix over the 8 warps. Elements at
-// positions >= N have weight 0.
+// positions >= N have weight 0. All four rows are loaded before any arithmetic.
 template <typename T, typename V>
 __device__ __forceinline__ void tile_raw_values(const T* __restrict__ lw, int64_t N, int64_t base,
-                                                T M, bool vec, V (&val)[kRows][4], V* sh_tot) {
+                                                const WeightCtx& wc, bool vec,
+                                                V (&val)[kRows][4], V* sh_tot) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  T x[kRows][4];
+#pragma unroll
+  for (int r = 0; r < kRows; ++r) load4(lw, base + tile_offset(warp, r, lane, 0), N, vec, x[r]);
   V carry = vzero(V());
 #pragma unroll
   for (int r = 0; r < kRows; ++r) {
-    const int64_t idx = base + tile_offset(warp, r, lane, 0);
-    T x[4];
-    load4(lw, idx, N, vec, x);
     V loc[4];
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-      const T w = (x[q] == neg_inf<T>()) ? T(0) : exp_pinned(sub_rn(x[q], M));
-      const V wv = vfrom_w(w, V());
+      const V wv = vfrom_w(Path<T, V>::weight(x[r][q], wc), V());
       loc[q] = (q == 0) ? wv : vadd(loc[q - 1], wv);
     }
     V incl = loc[3];
@@ -168,37 +234,62 @@ template <> __device__ __forceinline__ float2 load_v_cg<float2>(const double2* p
 }
 
 // ---------------------------------------------------------------------------------------
-// Pass 1: maximum log-weight.
+// Pass 1: maximum log-weight, compared through order-preserving integer keys (exact, and
+// no binary64 arithmetic). NaN is skipped (and flagged, as is +inf).
 // ---------------------------------------------------------------------------------------
+__device__ __forceinline__ long long max_key(float v) {
+  const int b = __float_as_int(v);
+  return static_cast<long long>(b >= 0 ? b : (b ^ 0x7fffffff));
+}
+__device__ __forceinline__ long long max_key(double v) {
+  const long long b = __double_as_longlong(v);
+  return b >= 0 ? b : (b ^ 0x7fffffffffffffffLL);
+}
+__device__ __forceinline__ double key_to_double(long long k, float) {
+  const int b = static_cast<int>(k);
+  return static_cast<double>(__int_as_float(b >= 0 ? b : (b ^ 0x7fffffff)));
+}
+__device__ __forceinline__ double key_to_double(long long k, double) {
+  return __longlong_as_double(k >= 0 ? k : (k ^ 0x7fffffffffffffffLL));
+}
+
 template <typename T>
 __global__ void __launch_bounds__(kBlock)
 max_kernel(const T* __restrict__ lw, int64_t N, ScanGlob* g, double* blockmax, int* err,
            int32_t* d_init) {
-  __shared__ double sh[kWarps];
+  __shared__ long long sh[kWarps];
   __shared__ bool am_last;
-  double m = -INFINITY;  // -inf
+  const long long kMin = max_key(neg_inf<T>());
+  long long m = kMin;
   bool bad = false;
-  const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
-  for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < N; i += stride) {
-    const T v = lw[i];
-    bad |= nonfinite_logw(v);
-    const double vd = static_cast<double>(v);
-    m = vd > m ? vd : m;
-    if (d_init) d_init[i] = static_cast<int32_t>(N);
+  const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x * 4;
+  const bool vec = (reinterpret_cast<uintptr_t>(lw) & 15u) == 0;
+  for (int64_t i0 = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) * 4; i0 < N;
+       i0 += stride) {
+    T x[4];
+    load4(lw, i0, N, vec && i0 + 4 <= N, x);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const bool nan = x[q] != x[q];
+      bad |= nan || x[q] == static_cast<T>(INFINITY);
+      const long long k = max_key(x[q]);
+      if (!nan && k > m) m = k;
+      if (d_init && i0 + q < N) d_init[i0 + q] = static_cast<int32_t>(N);
+    }
   }
   if (bad) flag_error(err, RS_ERR_NONFINITE);
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
-    const double y = __shfl_xor_sync(0xffffffffu, m, o);
+    const long long y = __shfl_xor_sync(0xffffffffu, m, o);
     m = y > m ? y : m;
   }
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   if (lane == 0) sh[warp] = m;
   __syncthreads();
   if (threadIdx.x == 0) {
-    double bm = sh[0];
+    long long bm = sh[0];
     for (int k = 1; k < kWarps; ++k) bm = sh[k] > bm ? sh[k] : bm;
-    blockmax[blockIdx.x] = bm;
+    blockmax[blockIdx.x] = key_to_double(bm, T());
     __threadfence();
     const unsigned t = atomicAdd(&g->ticket_max, 1u);
     am_last = (t == gridDim.x - 1);
@@ -206,24 +297,25 @@ max_kernel(const T* __restrict__ lw, int64_t N, ScanGlob* g, double* blockmax, i
   __syncthreads();
   if (!am_last) return;
   __threadfence();
-  double mm = -INFINITY;
+  long long mm = max_key(-static_cast<double>(INFINITY));  // binary64 keys from here on
   for (int b = threadIdx.x; b < static_cast<int>(gridDim.x); b += blockDim.x) {
-    const double y = __ldcg(blockmax + b);
+    const long long y = max_key(__ldcg(blockmax + b));
     mm = y > mm ? y : mm;
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
-    const double y = __shfl_xor_sync(0xffffffffu, mm, o);
+    const long long y = __shfl_xor_sync(0xffffffffu, mm, o);
     mm = y > mm ? y : mm;
   }
   __syncthreads();
   if (lane == 0) sh[warp] = mm;
   __syncthreads();
   if (threadIdx.x == 0) {
-    double bm = sh[0];
+    long long bm = sh[0];
     for (int k = 1; k < kWarps; ++k) bm = sh[k] > bm ? sh[k] : bm;
-    g->M = bm;
-    if (bm == -INFINITY) flag_error(err, RS_ERR_ZERO_WEIGHT);
+    const double M = key_to_double(bm, 0.0);
+    g->M = M;
+    if (M == -INFINITY) flag_error(err, RS_ERR_ZERO_WEIGHT);
     g->ticket_max = 0u;
   }
 }
@@ -304,6 +396,7 @@ tile_sum_kernel(const T* __restrict__ lw, int64_t N, ScanGlob* g, double2* s_rec
                 double2* P_rec, int* err, double* log_total_out) {
   __shared__ V sh_tot[kWarps];
   __shared__ V sh_max[kWarps];
+  __shared__ float2 sh_tab[64];
   __shared__ bool am_last;
   const double Md = g->M;
   const bool zero = !(Md > -DBL_MAX);
@@ -311,9 +404,10 @@ tile_sum_kernel(const T* __restrict__ lw, int64_t N, ScanGlob* g, double2* s_rec
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   V m = vzero(V());
   if (!zero) {
+    const WeightCtx wc = make_ctx<T, V>(Md, sh_tab);
     const bool vec = ((reinterpret_cast<uintptr_t>(lw) & 15u) == 0) && (base + kTile <= N);
     V val[kRows][4];
-    tile_raw_values<T, V>(lw, N, base, static_cast<T>(Md), vec, val, sh_tot);
+    tile_raw_values<T, V>(lw, N, base, wc, vec, val, sh_tot);
 #pragma unroll
     for (int r = 0; r < kRows; ++r)
 #pragma unroll
@@ -342,15 +436,16 @@ tile_sum_kernel(const T* __restrict__ lw, int64_t N, ScanGlob* g, double2* s_rec
 
 // Cumulative offspring of a cumulative weight W (Codes 7 and 8 with r = W * N / W^N).
 template <typename T, typename V, bool STRAT>
-__device__ __forceinline__ int32_t cum_offspring(V W, V S, V scale, T u_sys, const Keys& keys,
-                                                 int64_t N) {
+__device__ __forceinline__ int32_t cum_offspring(V W, V S, V scale,
+                                                 typename Path<T, V>::U u_sys,
+                                                 const Keys& keys, int64_t N) {
   if (veq(W, S)) return static_cast<int32_t>(N);
   const V r = vscale(W, scale);
   int64_t o;
   if constexpr (STRAT) {
     int64_t k = floor_to_i64(r);
     k = k < N - 1 ? k : N - 1;
-    const T uk = u01<T>(draw(keys, static_cast<uint32_t>(k), 0u));
+    const auto uk = Path<T, V>::draw_u(draw(keys, static_cast<uint32_t>(k), 0u));
     o = floor_to_i64(vplus_u(r, uk));
     o = o < k + 1 ? o : k + 1;
   } else {
@@ -373,6 +468,7 @@ emit_cumoff_kernel(const T* __restrict__ lw, int64_t N, const ScanGlob* g, const
                    int32_t* __restrict__ d) {
   __shared__ V sh_tot[kWarps];
   __shared__ V sh_max[kWarps];
+  __shared__ float2 sh_tab[64];
   const int64_t base = static_cast<int64_t>(blockIdx.x) * kTile;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const double Md = g->M;
@@ -390,11 +486,13 @@ emit_cumoff_kernel(const T* __restrict__ lw, int64_t N, const ScanGlob* g, const
       }
     return;
   }
+  const WeightCtx wc = make_ctx<T, V>(Md, sh_tab);
   const V scale = load_v<V>(&g->scale_raw);
-  const T u_sys = STRAT ? T(0) : u01<T>(draw(keys, 0u, 0u));
+  using U = typename Path<T, V>::U;
+  const U u_sys = Path<T, V>::draw_u(draw(keys, 0u, 0u));
   const bool vec = ((reinterpret_cast<uintptr_t>(lw) & 15u) == 0) && (base + kTile <= N);
   V val[kRows][4];
-  tile_raw_values<T, V>(lw, N, base, static_cast<T>(Md), vec, val, sh_tot);
+  tile_raw_values<T, V>(lw, N, base, wc, vec, val, sh_tot);
   V prevmax;
   tile_running_max<V>(val, base, N, sh_max, prevmax);
   const int t = blockIdx.x;
@@ -451,6 +549,9 @@ template <> __device__ __forceinline__ float convert_out<float, float>(float v) 
 template <> __device__ __forceinline__ double convert_out<double, double>(double v) { return v; }
 template <> __device__ __forceinline__ float2 convert_out<float2, float2>(float2 v) { return v; }
 template <> __device__ __forceinline__ float convert_out<float2, float>(float2 v) { return v.x; }
+template <> __device__ __forceinline__ double convert_out<float2, double>(float2 v) {
+  return vto_double(v);
+}
 
 template <typename T, typename V, typename OUT>
 __global__ void __launch_bounds__(kBlock)
@@ -458,6 +559,7 @@ emit_W_kernel(const T* __restrict__ lw, int64_t N, const ScanGlob* g, const doub
               OUT* __restrict__ Wout) {
   __shared__ V sh_tot[kWarps];
   __shared__ V sh_max[kWarps];
+  __shared__ float2 sh_tab[64];
   const int64_t base = static_cast<int64_t>(blockIdx.x) * kTile;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const double Md = g->M;
@@ -469,9 +571,10 @@ emit_W_kernel(const T* __restrict__ lw, int64_t N, const ScanGlob* g, const doub
       }
     return;
   }
+  const WeightCtx wc = make_ctx<T, V>(Md, sh_tab);
   const bool vec = ((reinterpret_cast<uintptr_t>(lw) & 15u) == 0) && (base + kTile <= N);
   V val[kRows][4];
-  tile_raw_values<T, V>(lw, N, base, static_cast<T>(Md), vec, val, sh_tot);
+  tile_raw_values<T, V>(lw, N, base, wc, vec, val, sh_tot);
   V prevmax;
   tile_running_max<V>(val, base, N, sh_max, prevmax);
   const int t = blockIdx.x;
@@ -502,7 +605,7 @@ search_kernel(const V* __restrict__ W, int64_t N, const ScanGlob* g, Keys keys,
     return;
   }
   const V S = W[N - 1];
-  const T U = u01<T>(draw(keys, static_cast<uint32_t>(i), 0u));
+  const auto U = Path<T, V>::draw_u(draw(keys, static_cast<uint32_t>(i), 0u));
   const V u = vtimes_u(S, U);
   int64_t lo = 0, hi = N;
   while (lo < hi) {
@@ -519,16 +622,14 @@ int max_grid(int64_t N, int max_blocks) {
   return static_cast<int>(want < max_blocks ? want : max_blocks);
 }
 
-template <typename V> struct AccName;
-template <> struct AccName<float> { static constexpr int i = 0; };
-template <> struct AccName<float2> { static constexpr int i = 1; };
-template <> struct AccName<double> { static constexpr int i = 2; };
-const char* const kLblMax[3] = {"max_f32", "max_f32c", "max_f64"};
-const char* const kLblTile[3] = {"tile_sum_f32", "tile_sum_f32c", "tile_sum_f64"};
-const char* const kLblSys[3] = {"emit_systematic_f32", "emit_systematic_f32c", "emit_systematic_f64"};
-const char* const kLblStr[3] = {"emit_stratified_f32", "emit_stratified_f32c", "emit_stratified_f64"};
-const char* const kLblW[3] = {"emit_W_f32", "emit_W_f32c", "emit_W_f64"};
-const char* const kLblSearch[3] = {"search_f32", "search_f32c", "search_f64"};
+const char* const kLblMax[4] = {"max_f32", "max_f32c", "max_f64", "max_f64n"};
+const char* const kLblTile[4] = {"tile_sum_f32", "tile_sum_f32c", "tile_sum_f64", "tile_sum_f64n"};
+const char* const kLblSys[4] = {"emit_systematic_f32", "emit_systematic_f32c",
+                                "emit_systematic_f64", "emit_systematic_f64n"};
+const char* const kLblStr[4] = {"emit_stratified_f32", "emit_stratified_f32c",
+                                "emit_stratified_f64", "emit_stratified_f64n"};
+const char* const kLblW[4] = {"emit_W_f32", "emit_W_f32c", "emit_W_f64", "emit_W_f64n"};
+const char* const kLblSearch[4] = {"search_f32", "search_f32c", "search_f64", "search_f64n"};
 
 template <typename T, typename V>
 cudaError_t run_scan(const Scratch& s, int scheme, const T* lw, int64_t N, uint64_t seed,
@@ -538,7 +639,7 @@ cudaError_t run_scan(const Scratch& s, int scheme, const T* lw, int64_t N, uint6
   double2* s_rec = s.rec;
   double2* P_rec = s.rec + (s.max_tiles + 2);
   const Keys keys = make_keys(seed, step, filter, static_cast<uint32_t>(scheme));
-  constexpr int ai = AccName<V>::i;
+  constexpr int ai = Path<T, V>::id;
   trace_mark(s.trace, kLblMax[ai], st);
   max_kernel<T><<<max_grid(N, s.max_blocks), kBlock, 0, st>>>(
       lw, N, s.glob, s.blockmax, s.err, scheme == RS_MULTINOMIAL ? d : nullptr);
@@ -569,7 +670,7 @@ cudaError_t run_cumw(const Scratch& s, const T* lw, int64_t N, OUT* W_out, doubl
   const int tiles = static_cast<int>((N + kTile - 1) / kTile);
   double2* s_rec = s.rec;
   double2* P_rec = s.rec + (s.max_tiles + 2);
-  constexpr int ai = AccName<V>::i;
+  constexpr int ai = Path<T, V>::id;
   trace_mark(s.trace, kLblMax[ai], st);
   max_kernel<T><<<max_grid(N, s.max_blocks), kBlock, 0, st>>>(lw, N, s.glob, s.blockmax, s.err,
                                                               nullptr);
@@ -594,6 +695,9 @@ cudaError_t launch_scan_resample(const Scratch& s, int scheme, Acc acc, const vo
       return run_scan<float, float2>(s, scheme, static_cast<const float*>(logw), N, seed, step,
                                      filter, a_out, d, st);
     case Acc::F64:
+      return run_scan<double, float2>(s, scheme, static_cast<const double*>(logw), N, seed,
+                                      step, filter, a_out, d, st);
+    case Acc::F64N:
       return run_scan<double, double>(s, scheme, static_cast<const double*>(logw), N, seed,
                                       step, filter, a_out, d, st);
   }
@@ -610,6 +714,9 @@ cudaError_t launch_cumulative_weights(const Scratch& s, Acc acc, const void* log
       return run_cumw<float, float2, float>(s, static_cast<const float*>(logw), N,
                                             static_cast<float*>(W_out), log_total, st);
     case Acc::F64:
+      return run_cumw<double, float2, double>(s, static_cast<const double*>(logw), N,
+                                              static_cast<double*>(W_out), log_total, st);
+    case Acc::F64N:
       return run_cumw<double, double, double>(s, static_cast<const double*>(logw), N,
                                               static_cast<double*>(W_out), log_total, st);
   }

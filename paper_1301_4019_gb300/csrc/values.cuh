@@ -58,6 +58,7 @@ __device__ __forceinline__ bool vle(float2 a, float2 b) {
   return a.x < b.x || (a.x == b.x && a.y <= b.y);
 }
 __device__ __forceinline__ float2 vfrom_w(float w, float2) { return make_float2(w, 0.0f); }
+__device__ __forceinline__ float2 vfrom_w(float2 w, float2) { return w; }
 __device__ __forceinline__ double vto_double(float2 a) {
   return __dadd_rn(static_cast<double>(a.x), static_cast<double>(a.y));
 }
@@ -122,5 +123,8 @@ __device__ __forceinline__ float2 vplus_u(float2 r, float u) { return add21(r, u
 __device__ __forceinline__ float vtimes_u(float S, float U) { return __fmul_rn(S, U); }
 __device__ __forceinline__ double vtimes_u(double S, double U) { return __dmul_rn(S, U); }
 __device__ __forceinline__ float2 vtimes_u(float2 S, float U) { return mul21(S, U); }
+// double-float path: the 53-bit uniform as a two-float
+__device__ __forceinline__ float2 vplus_u(float2 r, float2 u) { return vadd(r, u); }
+__device__ __forceinline__ float2 vtimes_u(float2 S, float2 U) { return mul22(S, U); }
 
 }  // namespace rsk

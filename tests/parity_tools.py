@@ -5,10 +5,11 @@ bit. The multinomial, stratified and systematic resamplers add the weights in a 
 order than the oracle's sequential sum, so an output may differ only where the draw lies
 within the rounding bound of a cumulative-weight boundary. The bound used here:
 
-  kernel:  |W_i - W*_i| <= KERNEL_C * eps_acc * W^N     (W* = exact prefix of the same
+  kernel:  |W_i - W*_i| <= KERNEL_C * eps_acc * W^N     (W* = exact prefix of the oracle's
            weights; KERNEL_C covers the <= 30 roundings on any path of the tile scan, the
            tile-prefix rounding and the final add; eps_acc = 2^-24 binary32, 2^-44 two-float,
-           2^-53 binary64)
+           2^-43 double-float over binary64 inputs (which also covers the 2^-40-relative
+           weights of its exp), 2^-53 native binary64)
   oracle:  |W^o_i - W*_i| <= i * eps_dtype * W*_i        (sequential sum, Higham's bound)
 
 and r = N W / W^N inherits N times these relative bounds (plus a few roundings of the
@@ -21,8 +22,8 @@ import numpy as np
 import oracle
 
 KERNEL_C = 40.0
-EPS = {"f32": 2.0 ** -24, "f32c": 2.0 ** -44, "f64": 2.0 ** -53}
-EPS_DTYPE = {"f32": 2.0 ** -24, "f32c": 2.0 ** -24, "f64": 2.0 ** -53}
+EPS = {"f32": 2.0 ** -24, "f32c": 2.0 ** -44, "f64": 2.0 ** -43, "f64n": 2.0 ** -53}
+EPS_DTYPE = {"f32": 2.0 ** -24, "f32c": 2.0 ** -24, "f64": 2.0 ** -53, "f64n": 2.0 ** -53}
 
 
 def truth_prefix(lw: np.ndarray):

@@ -106,7 +106,8 @@ def test_scale_invariance_bit_exact(rs, h):
 # ---------------------------------------------------------------------------------------
 # Scan-based resamplers: equal except near boundaries (counted)
 # ---------------------------------------------------------------------------------------
-KINDS = [("f32", np.float32, 0), ("f32c", np.float32, 1), ("f64", np.float64, 0)]
+KINDS = [("f32", np.float32, 0), ("f32c", np.float32, 1), ("f64", np.float64, 0),
+         ("f64n", np.float64, 2)]
 
 
 def _check_valid_ancestry(a, lw, sorted_expected):
@@ -145,7 +146,7 @@ def test_systematic_stratified_parity(rs, h, kind, dtype, prec, scheme, N):
         st, c = _run(rs, h, sch, lw, seed=21, step=2, prec=prec, permute=True)
         assert st == rs.RS_OK
         assert np.array_equal(c, oracle.permute(a))
-    if kind == "f64" or N <= 5:
+    if kind in ("f64", "f64n") or N <= 5:
         assert total_mis <= 2
 
 
@@ -170,7 +171,7 @@ def test_multinomial_parity(rs, h, kind, dtype, prec, N):
         st, c = _run(rs, h, rs.MULTINOMIAL, lw, seed=8, step=4, prec=prec, permute=True)
         assert st == rs.RS_OK
         assert np.array_equal(c, oracle.permute(a))
-    if kind == "f64":
+    if kind in ("f64", "f64n"):
         assert total_mis <= 2
 
 
@@ -274,7 +275,8 @@ def test_conversion_errors_flagged(rs, h):
 # ---------------------------------------------------------------------------------------
 @pytest.mark.parametrize("kind,dtype,prec,tol", [("f32", np.float32, 0, 1e-5),
                                                  ("f32c", np.float32, 1, 1e-6),
-                                                 ("f64", np.float64, 0, 1e-12)])
+                                                 ("f64", np.float64, 0, 1e-12),
+                                                 ("f64n", np.float64, 2, 1e-12)])
 @pytest.mark.parametrize("N", [1, 3, 4096, 4097, 100003])
 def test_cumulative_weights(rs, h, kind, dtype, prec, tol, N):
     lw = _lw(N, 3.0, dtype)
@@ -333,3 +335,46 @@ def test_full_size_scan_schemes(rs, kind, dtype, prec):
         _, want = oracle.multinomial(lw, 5, prec=1)
         n, bad = multinomial_mismatches(kind, lw, a, want, seed=5, oracle_is_sequential=False)
         assert bad == 0
+
+
+def test_f64_decisions_on_binary32_pipes_edge_cases(rs, h):
+    """The binary64 Metropolis / rejection kernels decide on the binary32 pipes and fall back
+    to exact binary64 evaluation inside the uncertainty band; inputs that force every branch
+    (magnitudes where the bound is too loose, values outside the binary32 range, subnormals,
+    signed zeros, near-equal log-weights) must still match the oracle bit for bit."""
+    rng = np.random.default_rng(12)
+    N = 5000
+    cases = {
+        "huge": -1e5 + rng.normal(0, 3, N),
+        "outside_f32": np.where(rng.random(N) < 0.3, -1e39, rng.normal(-3, 1, N)),
+        "subnormal": np.where(rng.random(N) < 0.5, 1e-310, -rng.exponential(1.0, N)),
+        "signed_zero": np.where(rng.random(N) < 0.5, 0.0, -0.0),
+        "near_equal": -2.0 + rng.integers(-3, 4, N) * 2.0 ** -40,
+        "tiny_ratio": np.where(rng.random(N) < 0.5, 0.0, -80.0 - rng.random(N) * 20),
+        "mixed_inf": np.where(rng.random(N) < 0.2, -np.inf, rng.normal(-1, 2, N)),
+    }
+    for name, lw in cases.items():
+        lw = np.ascontiguousarray(lw, dtype=np.float64)
+        st, a = _run(rs, h, rs.METROPOLIS, lw, B=24, seed=77)
+        assert st == rs.RS_OK, name
+        assert np.array_equal(a, oracle.metropolis(lw, 24, seed=77)[1]), name
+        lwr = lw - max(0.0, float(lw.max()))  # keep the rejection bound log w_max = 0 valid
+        st, a = _run(rs, h, rs.REJECTION, lwr, seed=78, log_wmax=0.0, max_trials=4096)
+        ost, want = oracle.rejection(lwr, 0.0, seed=78, max_trials=4096)
+        assert st == (rs.RS_OK if ost == oracle.OK else rs.RS_ERR_REJECTION_CAP), name
+        assert np.array_equal(a, want), name
+
+
+@pytest.mark.parametrize("dtype", [np.float32, np.float64])
+def test_log_normaliser_uses_true_maximum(rs, h, dtype):
+    """All log-weights negative and far from 0: the maximum used for renormalisation must be
+    the true maximum (the first weight of a maximal particle is exactly 1)."""
+    lw = np.array([-7.25, -3.5, -9.0, -3.5, -100.0], dtype=dtype)
+    t = torch.from_numpy(lw).to(DEV)
+    for prec in ([0, 1] if dtype == np.float32 else [0, 2]):
+        W, lt = rs.rs_cumulative_weights(h, t, prec=prec)
+        assert rs.rs_last_error(h) == rs.RS_OK
+        W = W.cpu().numpy().astype(np.float64)
+        assert W[1] - W[0] == pytest.approx(1.0, rel=1e-6)
+        tol = 1e-12 if dtype == np.float64 else 1e-6
+        assert lt.item() == pytest.approx(np.log(np.sum(np.exp(lw.astype(np.float64)))), rel=tol)
