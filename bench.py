@@ -56,6 +56,11 @@ def parse_args():
     p.add_argument("--y", type=float, default=2.0)
     p.add_argument("--pool", type=int, default=40, help="weight vectors per dtype")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-batched", action="store_true")
+    p.add_argument("--batched-filters", type=int, default=4096)
+    p.add_argument("--single", default=None,
+                   help="profile one call: scheme:dtype[:prec], e.g. metropolis:f32 "
+                        "(runs warmup + steps calls with Permute, prints one JSON line)")
     return p.parse_args()
 
 
@@ -350,6 +355,11 @@ def run_ours(args):
     roof["share_of_step"] = round(sum(by_label[dom_label]) / total_kernel_ms, 4)
     roof["avg_launch_ms"] = round(dom_ms, 5)
 
+    per_kernel = {lab: {"mean_us": round(1e3 * statistics.mean(ds), 2),
+                        "launches_per_step": round(len(ds) / args.steps, 2),
+                        "share": round(sum(ds) / total_kernel_ms, 4)}
+                  for lab, ds in sorted(by_label.items(), key=lambda kv: -sum(kv[1]))}
+
     # per resampler breakdown: sum of the kernels of each resample call
     per_call = {}
     for (ci, lab), ds in durations.items():
@@ -403,6 +413,8 @@ def run_ours(args):
     h2d = sum(t.numel() * t.element_size() for p in host_in.values() for t in p)
     d2h = sum(t.numel() * t.element_size() for p in host_out.values() for t in p)
 
+    batched = None if args.no_batched else run_batched(args, dev, world)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(N, B, args.y, budget_s=20.0)
@@ -426,6 +438,7 @@ def run_ours(args):
                     "ms_per_step": round(ms_e2e, 5)},
             "roofline": roof,
             "per_scheme": per_scheme,
+            "per_kernel": per_kernel,
             "gpu_launches": gpu_launches_per_step * args.steps,
             "gpu_launches_per_step": gpu_launches_per_step,
             "traced_ms_per_step": round(ms_traced_total / args.steps, 5),
@@ -433,9 +446,90 @@ def run_ours(args):
             "clocks": {"sm_mhz": clk["sm_mhz"], "sm_max_mhz": clk["sm_max_mhz"],
                        "reasons": clk["reasons"], "samples": clk["samples"]},
             "cpu_baseline": cpu,
+            "batched": batched,
         }
         print(json.dumps(line))
     h.close()
+
+
+# ---------------------------------------------------------------------------------------
+# batched workload: many filters of uneven size in one launch
+# ---------------------------------------------------------------------------------------
+def run_batched(args, dev, world):
+    """F filters, sizes log-uniform in [256, 65536], y_f ~ U[0,4], binary32; systematic and
+    Metropolis (per-filter B from Eq. B) each with Permute, one launch per scheme per step,
+    replayed from a CUDA graph. Returns filters/s and particles/s."""
+    import torch
+    import oracle
+    import paper_1301_4019_gb300 as rs
+    F = args.batched_filters
+    sizes = workload.ragged_sizes(F, 256, 65536, seed=SEED)
+    offsets, lw, y = workload.ragged_logw(sizes, seed=SEED, dtype=np.float32)
+    total = int(offsets[-1])
+    Bs = np.array([oracle.metropolis_B(0.01, workload.beta_estimate(v)) for v in y], np.int32)
+    t = torch.from_numpy(lw).to(dev)
+    off = torch.from_numpy(offsets).to(dev)
+    Bt = torch.from_numpy(Bs).to(dev)
+    outs = [torch.empty(total, dtype=torch.int32, device=dev) for _ in range(2)]
+    h = rs.Handle(total)
+
+    def step(k):
+        rs.rs_resample_batched(h, rs.SYSTEMATIC, t, off, seed=SEED, step=k, out=outs[0],
+                               permute=True)
+        rs.rs_resample_batched(h, rs.METROPOLIS, t, off, B_per_filter=Bt, seed=SEED, step=k,
+                               out=outs[1], permute=True)
+
+    for k in range(args.warmup):
+        step(k)
+    st = rs.rs_last_error(h)
+    if st != rs.RS_OK:
+        raise SystemExit(f"batched device status: {rs.rs_strerror(st)}")
+    # per-kernel durations of one traced step
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(16)]
+    for e in evs:
+        e.record()
+    torch.cuda.synchronize()
+    rs.rs_trace(h, evs)
+    step(0)
+    labels = rs.rs_trace_labels(h)
+    rs.rs_trace(h, [])
+    torch.cuda.synchronize()
+    kern = {}
+    call = 0
+    for i, lab in enumerate(labels[:-1]):
+        if lab == "end":
+            call += 1
+            continue
+        name = f"{lab}:{['systematic', 'metropolis'][call]}"
+        kern[name] = round(evs[i].elapsed_time(evs[i + 1]) * 1e3, 2)
+    cs = torch.cuda.Stream()
+    cs.wait_stream(torch.cuda.current_stream())
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(cs):
+        with torch.cuda.graph(g, stream=cs):
+            step(0)
+    torch.cuda.current_stream().wait_stream(cs)
+    g.replay()
+    torch.cuda.synchronize()
+    barrier(world)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        g.replay()
+    e1.record()
+    torch.cuda.synchronize()
+    ms = reduce_max(e0.elapsed_time(e1) / args.steps, world, dev)
+    st = rs.rs_last_error(h)
+    h.close()
+    if st != rs.RS_OK:
+        raise SystemExit(f"batched device status: {rs.rs_strerror(st)}")
+    return {"workload": f"{F} filters, N_f log-uniform in [256, 65536] ({total} particles), "
+                        "y_f ~ U[0,4], binary32; systematic + Metropolis (B from Eq. B per "
+                        "filter), each with Permute",
+            "filters_per_s": round(world * 2 * F / (ms * 1e-3), 1),
+            "G_particles_per_s": round(world * 2 * total / (ms * 1e-3) / 1e9, 3),
+            "ms_per_step": round(ms, 4), "particles": total, "kernel_us": kern,
+            "launches_per_step": 4}
 
 
 # ---------------------------------------------------------------------------------------
@@ -507,9 +601,40 @@ def run_reference(args):
     print(json.dumps(line))
 
 
+def run_single(args):
+    """One resample configuration on one input, for profilers: warmup + steps calls."""
+    import torch
+    import paper_1301_4019_gb300 as rs
+    parts = args.single.split(":")
+    scheme = rs.SCHEMES[parts[0]]
+    npdt = {"f32": np.float32, "f64": np.float64}[parts[1]]
+    prec = int(parts[2]) if len(parts) > 2 else 0
+    N, B = workload_params(args)
+    lw = torch.from_numpy(workload.synthetic_logw(N, args.y, seed=SEED, dtype=npdt)).cuda()
+    out = torch.empty(N, dtype=torch.int32, device="cuda")
+    with rs.Handle(N) as h:
+        for k in range(args.warmup):
+            rs.rs_resample(h, scheme, lw, B=B, seed=SEED, step=k, out=out, permute=True, prec=prec)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for k in range(args.steps):
+            rs.rs_resample(h, scheme, lw, B=B, seed=SEED, step=k, out=out, permute=True, prec=prec)
+        e1.record()
+        torch.cuda.synchronize()
+        st = rs.rs_last_error(h)
+    if st != 0:
+        raise SystemExit(f"device status {st}")
+    ms = e0.elapsed_time(e1) / args.steps
+    print(json.dumps({"single": args.single, "N": N, "ms_per_call": round(ms, 5),
+                      "G_ancestors_per_s": round(N / (ms * 1e-3) / 1e9, 3)}))
+
+
 def main():
     args = parse_args()
-    if args.impl == "reference":
+    if args.single:
+        run_single(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)

@@ -119,6 +119,21 @@ int rs_resample(rs_handle* h, int scheme, int dtype, const void* logw_dev, int64
                 int32_t B, uint64_t seed, uint64_t step, int32_t* ancestors_dev, int permute,
                 const rs_opts* opts, void* stream);
 
+/* Many independent filters in one launch. F filters in CSR layout: offsets_dev holds F + 1
+ * int64 offsets (device), filter f owning the particles offsets[f] .. offsets[f+1]-1 of
+ * logw_dev and ancestors_dev; every filter has at most 2^20 particles (empty filters are
+ * skipped) and offsets[F] <= the handle's max_n (violations: RS_ERR_ARG via rs_last_error).
+ * ancestors_dev receives, for each filter, local ancestor indices 0..N_f-1. B_dev: NULL
+ * (every filter uses B) or F int32 Metropolis step counts. The filter index f is the filter
+ * of the random-number counter, so filter f equals rs_resample on its slice with
+ * opts->filter = f, bit for bit; opts->filter is ignored. Other arguments as rs_resample.
+ * F <= max(1024, max_n / 16) (RS_ERR_CAPACITY otherwise). The work units are the tiles and
+ * particles of all filters together, so uneven sizes and per-filter B balance across the GPU. */
+int rs_resample_batched(rs_handle* h, int scheme, int dtype, const void* logw_dev,
+                        const int64_t* offsets_dev, int32_t F, const int32_t* B_dev, int32_t B,
+                        uint64_t seed, uint64_t step, int32_t* ancestors_dev, int permute,
+                        const rs_opts* opts, void* stream);
+
 /* Cumulative weights (Code 4 Inclusive-Prefix-Sum of the max-shifted weights, Appendix E):
  * W_dev[i] = sum_{j<=i} exp(logw[j] - max logw) in `dtype` (compensated sums are rounded to
  * binary32 on output), and *log_total_dev (one binary64 on the device) =

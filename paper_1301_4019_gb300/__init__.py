@@ -39,6 +39,7 @@ EXPORTED = [
     "rs_cumulative_offspring", "rs_adjacent_difference", "rs_cumulative_offspring_to_ancestors",
     "rs_prepermute", "rs_permute", "rs_metropolis_B", "rs_last_error", "rs_strerror",
     "rs_trace", "rs_trace_count", "rs_trace_label", "rs_systematic_noalloc",
+    "rs_resample_batched",
 ]
 NOALLOC_MAX_N = 1 << 22
 
@@ -94,6 +95,8 @@ def _declare(lib):
         "rs_trace_count": (I, [P]),
         "rs_trace_label": (C.c_char_p, [P, I]),
         "rs_systematic_noalloc": (I, [I, P, I64, U64, U64, P, P, P]),
+        "rs_resample_batched": (I, [P, I, I, P, P, I32, P, I32, U64, U64, P, I,
+                                    C.POINTER(_Opts), P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -180,6 +183,28 @@ def rs_resample(h: Handle, scheme: int, logw: torch.Tensor, B: int = 0, seed: in
                               int(seed) & 0xFFFFFFFFFFFFFFFF, int(step) & 0xFFFFFFFFFFFFFFFF,
                               _dev(out, torch.int32, "out"), 1 if permute else 0,
                               C.byref(opts), _stream(stream)), "rs_resample")
+    return out
+
+
+def rs_resample_batched(h: Handle, scheme: int, logw: torch.Tensor, offsets: torch.Tensor,
+                        B: int = 0, B_per_filter: torch.Tensor | None = None, seed: int = 0,
+                        step: int = 0, out: torch.Tensor | None = None, permute: bool = False,
+                        prec: int = PREC_PLAIN, log_wmax: float = 0.0,
+                        max_trials: int = 1 << 20, stream=None) -> torch.Tensor:
+    """Resample F filters in CSR layout (offsets: F+1 int64) in one launch; returns the local
+    ancestors of every filter, concatenated."""
+    F = offsets.numel() - 1
+    if out is None:
+        out = torch.empty(logw.numel(), dtype=torch.int32, device=logw.device)
+    opts = _Opts(prec, float(log_wmax), int(max_trials), 0)
+    bptr = _dev(B_per_filter, torch.int32, "B_per_filter") if B_per_filter is not None else None
+    _check(load().rs_resample_batched(h.ptr, int(scheme), _dtype_code(logw),
+                                      _dev(logw, (torch.float32, torch.float64), "logw"),
+                                      _dev(offsets, torch.int64, "offsets"), F, bptr, int(B),
+                                      int(seed) & 0xFFFFFFFFFFFFFFFF,
+                                      int(step) & 0xFFFFFFFFFFFFFFFF,
+                                      _dev(out, torch.int32, "out"), 1 if permute else 0,
+                                      C.byref(opts), _stream(stream)), "rs_resample_batched")
     return out
 
 

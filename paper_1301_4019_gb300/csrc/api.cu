@@ -61,6 +61,13 @@ void free_scratch(rsk::Scratch& s) {
   cudaFree(s.irec);
   cudaFree(s.glob);
   cudaFree(s.err);
+  cudaFree(s.batch_tile_start);
+  cudaFree(s.batch_fmax);
+  cudaFree(s.batch_fS);
+  cudaFree(s.batch_fscale);
+  cudaFree(s.batch_fSd);
+  cudaFree(s.batch_s_rec);
+  cudaFree(s.batch_P_rec);
   std::memset(&s, 0, sizeof(s));
 }
 
@@ -88,6 +95,17 @@ int rs_create(rs_handle** out, int64_t max_n, int device) {
   ok &= cudaMalloc(&s.blockmax, sizeof(double) * s.max_blocks) == cudaSuccess;
   ok &= cudaMalloc(&s.irec, sizeof(long long) * 2 * (s.max_tiles + 2)) == cudaSuccess;
   ok &= cudaMalloc(&s.glob, sizeof(rsk::ScanGlob)) == cudaSuccess;
+  s.max_filters = max_n / 16 > 1024 ? max_n / 16 : 1024;
+  s.batch_tile_cap = max_n / rsk::kTile + s.max_filters + 1;
+  const size_t mf = static_cast<size_t>(s.max_filters);
+  const size_t tc = static_cast<size_t>(s.batch_tile_cap);
+  ok &= cudaMalloc(&s.batch_tile_start, sizeof(int32_t) * (mf + 1)) == cudaSuccess;
+  ok &= cudaMalloc(&s.batch_fmax, sizeof(long long) * mf) == cudaSuccess;
+  ok &= cudaMalloc(&s.batch_fS, sizeof(double2) * mf) == cudaSuccess;
+  ok &= cudaMalloc(&s.batch_fscale, sizeof(double2) * mf) == cudaSuccess;
+  ok &= cudaMalloc(&s.batch_fSd, sizeof(double) * mf) == cudaSuccess;
+  ok &= cudaMalloc(&s.batch_s_rec, sizeof(double2) * tc) == cudaSuccess;
+  ok &= cudaMalloc(&s.batch_P_rec, sizeof(double2) * (tc + mf)) == cudaSuccess;
   ok &= cudaMalloc(&s.err, sizeof(int)) == cudaSuccess;
   if (ok) {
     ok &= cudaMemset(s.glob, 0, sizeof(rsk::ScanGlob)) == cudaSuccess;
@@ -196,6 +214,38 @@ int rs_resample(rs_handle* h, int scheme, int dtype, const void* logw_dev, int64
       break;
   }
   if (e == cudaSuccess && permute) e = rsk::launch_permute(h->s, a_out, d, N, ancestors_dev, s);
+  end_mark(h, s);
+  return cuda_status(e);
+}
+
+int rs_resample_batched(rs_handle* h, int scheme, int dtype, const void* logw_dev,
+                        const int64_t* offsets_dev, int32_t F, const int32_t* B_dev, int32_t B,
+                        uint64_t seed, uint64_t step, int32_t* ancestors_dev, int permute,
+                        const rs_opts* opts, void* stream) {
+  if (!h || !logw_dev || !offsets_dev || !ancestors_dev) return RS_ERR_ARG;
+  if (F < 1) return RS_ERR_ARG;
+  if (F > h->s.max_filters) return RS_ERR_CAPACITY;
+  if (scheme < RS_MULTINOMIAL || scheme > RS_REJECTION) return RS_ERR_ARG;
+  if (dtype != RS_F32 && dtype != RS_F64) return RS_ERR_ARG;
+  if (permute != 0 && permute != 1) return RS_ERR_ARG;
+  rs_opts o;
+  o.prec = RS_PREC_PLAIN;
+  o.log_wmax = 0.0;
+  o.max_trials = 1 << 20;
+  o.filter = 0;
+  if (opts) o = *opts;
+  if (o.prec != RS_PREC_PLAIN && o.prec != RS_PREC_COMPENSATED && o.prec != RS_PREC_BINARY64)
+    return RS_ERR_ARG;
+  if (o.prec == RS_PREC_BINARY64 && dtype != RS_F64) return RS_ERR_ARG;
+  if (!std::isfinite(o.log_wmax)) return RS_ERR_ARG;
+  if (o.max_trials < 1 || o.max_trials > 0xFFFFFFFFLL) return RS_ERR_ARG;
+  if (scheme == RS_METROPOLIS && !B_dev && B < 0) return RS_ERR_ARG;
+  int st = set_device(h);
+  if (st != RS_OK) return st;
+  const cudaStream_t s = as_stream(stream);
+  const cudaError_t e = rsk::launch_batched(h->s, scheme, accumulation(dtype, o.prec), logw_dev,
+                                            offsets_dev, F, B_dev, B, seed, step, o.log_wmax,
+                                            o.max_trials, ancestors_dev, permute, s);
   end_mark(h, s);
   return cuda_status(e);
 }

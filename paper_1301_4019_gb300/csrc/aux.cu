@@ -3,6 +3,7 @@
 // sm_103a. Integer work only: every result is exact.
 #include "common.cuh"
 #include "internal.h"
+#include "permute.cuh"
 
 namespace rsk {
 namespace {
@@ -26,39 +27,13 @@ prepermute_kernel(const int32_t* __restrict__ a, int64_t N, int32_t* __restrict_
   atomicMin(d + ai, static_cast<int32_t>(i));
 }
 
-// Permute (second procedure of Code 10) fused with its gather c^i = a^{d^i}:
-//  - a claimed slot i (d_i < N) keeps its own particle: c_i = a[d_i] = i;
-//  - a particle whose claim failed (d[a_i] != i) walks x = i, d[x], d[d[x]], ... to the
-//    first unclaimed slot x and writes c_x = a_i there.
-// The walks start at indices absent from d and d is injective on claimed slots, so the
-// walks are disjoint and end at distinct unclaimed slots (the termination argument of
-// Appendix C): they only read d, and every slot of c is written exactly once, in any order.
+// Permute (second procedure of Code 10), one slot per thread (permute.cuh).
 __global__ void __launch_bounds__(kBlock)
 permute_kernel(const int32_t* __restrict__ a, const int32_t* __restrict__ d, int64_t N,
                int32_t* __restrict__ c, int* err) {
   const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
   if (i >= N) return;
-  const int32_t sentinel = static_cast<int32_t>(N);
-  const int32_t ai = a[i];
-  if (ai < 0 || ai >= N) {
-    flag_error(err, RS_ERR_ARG);
-    return;
-  }
-  if (d[i] != sentinel) c[i] = static_cast<int32_t>(i);
-  if (d[ai] != static_cast<int32_t>(i)) {
-    int64_t x = i;
-    int64_t steps = 0;
-    for (;;) {
-      const int32_t dx = d[x];
-      if (dx == sentinel) break;
-      if (dx < 0 || dx > sentinel || ++steps > N) {  // only a corrupted d can get here
-        flag_error(err, RS_ERR_ARG);
-        return;
-      }
-      x = dx;
-    }
-    c[x] = ai;
-  }
+  permute_one(a, d, N, c, i, err);
 }
 
 // Ancestors-to-Offspring (Code 12).

@@ -1,0 +1,453 @@
+// batched.cu -- many independent filters of uneven sizes resampled in a handful of launches
+// (F filters in CSR layout: filter f holds the particles offsets[f] .. offsets[f+1]-1).
+//
+// The paper resamples one filter per call; resampling thousands of small filters one call at a
+// time is launch-bound, and giving each filter to one CTA serialises its passes and leaves the
+// largest (or, for Metropolis, the highest-B) filters as a long tail. Here the work units are
+// the tiles and the particles of all filters together:
+//   plan    : tiles per filter (4096 particles, starting at the filter's first particle) and
+//             their prefix over filters; per-filter maxima reset            (1 CTA)
+//   max     : per tile, maximum log-weight, combined per filter by an atomic max of keys
+//   sums    : per tile, the tile scan total                               (tile-parallel)
+//   prefix  : per filter, tile prefixes, W^N and N / W^N                  (CTA per filter)
+//   emit    : per tile, cumulative offspring + Code-11 scatter + claims, or stored W
+//   search / Metropolis / rejection / Permute: one thread per particle, its filter found by a
+//             binary search of the offsets.
+// Every unit runs the same device functions as the single-filter kernels on the same tile
+// structure (relative to the filter's first particle), with the filter index in the
+// random-number counter: filter f of a batched call equals rs_resample on that filter's slice
+// with filter = f, bit for bit.
+#include <climits>
+
+#include "common.cuh"
+#include "internal.h"
+#include "mcmc.cuh"
+#include "permute.cuh"
+#include "tile.cuh"
+#include "values.cuh"
+
+namespace rsk {
+namespace {
+
+__device__ __forceinline__ long long key_of(float v) {
+  const int b = __float_as_int(v);
+  return static_cast<long long>(b >= 0 ? b : (b ^ 0x7fffffff));
+}
+__device__ __forceinline__ long long key_of(double v) {
+  const long long b = __double_as_longlong(v);
+  return b >= 0 ? b : (b ^ 0x7fffffffffffffffLL);
+}
+__device__ __forceinline__ double value_of(long long k, float) {
+  const int b = static_cast<int>(k);
+  return static_cast<double>(__int_as_float(b >= 0 ? b : (b ^ 0x7fffffff)));
+}
+__device__ __forceinline__ double value_of(long long k, double) {
+  return __longlong_as_double(k >= 0 ? k : (k ^ 0x7fffffffffffffffLL));
+}
+
+// Particle g of the batch -> (filter f, its first particle lo, its size n, local index i).
+// Returns false for positions past offsets[F] and for filters the plan rejected.
+struct PartLoc {
+  int f;
+  int64_t lo, n, i;
+};
+__device__ __forceinline__ int filter_of(const int64_t* __restrict__ off, int F, int64_t g);
+__device__ __forceinline__ bool locate_particle(const int64_t* __restrict__ off, int F,
+                                                int64_t max_n, int64_t g, PartLoc& P) {
+  if (g >= __ldg(off + F)) return false;
+  P.f = filter_of(off, F, g);
+  P.lo = __ldg(off + P.f);
+  const int64_t hi = __ldg(off + P.f + 1);
+  P.n = hi - P.lo;
+  P.i = g - P.lo;
+  return P.lo >= 0 && hi <= max_n && P.n > 0 &&
+         P.n <= static_cast<int64_t>(kBatchMaxTiles) * kTile && P.i >= 0 && P.i < P.n;
+}
+
+// Filter holding global position g: the last f with off[f] <= g (off has F + 1 entries).
+__device__ __forceinline__ int filter_of(const int64_t* __restrict__ off, int F, int64_t g) {
+  int lo = 0, hi = F;  // invariant: off[lo] <= g < off[hi]
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (__ldg(off + mid) <= g) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
+// Tile t of the batch -> its filter (the last f with tile_start[f] <= t).
+__device__ __forceinline__ int filter_of_tile(const int32_t* __restrict__ ts, int F, int t) {
+  int lo = 0, hi = F;
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (__ldg(ts + mid) <= t) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
+struct Batch {
+  const int64_t* off;
+  int F;
+  int64_t max_n;
+  int32_t* tile_start;   // F + 1
+  long long* fmax;       // F, keys of the per-filter maxima
+  double2* fS;           // F: total (accumulator type)
+  double2* fscale;       // F: N / total
+  double* fSd;           // F: total in binary64
+  double2* s_rec;        // tile totals, indexed by batch tile
+  double2* P_rec;        // tile prefixes, filter f at tile_start[f] + f
+  int* err;
+};
+
+// Plan: tiles per filter and their exclusive prefix; per-filter maxima reset; offsets checked.
+__global__ void __launch_bounds__(1024) batch_plan_kernel(Batch b) {
+  __shared__ int sh[32];
+  const int F = b.F;
+  const int chunk = (F + blockDim.x - 1) / blockDim.x;
+  const int f0 = min(F, static_cast<int>(threadIdx.x) * chunk), f1 = min(F, f0 + chunk);
+  int local = 0;
+  for (int f = f0; f < f1; ++f) {
+    const int64_t lo = b.off[f], hi = b.off[f + 1], n = hi - lo;
+    const bool ok = lo >= 0 && n >= 0 && hi <= b.max_n &&
+                    n <= static_cast<int64_t>(kBatchMaxTiles) * kTile;
+    if (!ok) flag_error(b.err, RS_ERR_ARG);
+    local += ok ? static_cast<int>((n + kTile - 1) / kTile) : 0;
+    b.fmax[f] = LLONG_MIN;
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int incl = local;
+#pragma unroll
+  for (int dd = 1; dd < 32; dd <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, incl, dd);
+    if (lane >= dd) incl += y;
+  }
+  if (lane == 31) sh[warp] = incl;
+  __syncthreads();
+  int p = incl - local;
+  for (int k = 0; k < warp; ++k) p += sh[k];
+  for (int f = f0; f < f1; ++f) {
+    b.tile_start[f] = p;
+    const int64_t lo = b.off[f], hi = b.off[f + 1], n = hi - lo;
+    const bool ok = lo >= 0 && n >= 0 && hi <= b.max_n &&
+                    n <= static_cast<int64_t>(kBatchMaxTiles) * kTile;
+    p += ok ? static_cast<int>((n + kTile - 1) / kTile) : 0;
+  }
+  if (f1 == F && f0 < F) b.tile_start[F] = p;
+  if (F == 0 && threadIdx.x == 0) b.tile_start[0] = 0;
+}
+
+// Locates batch tile t: its filter f, the filter's bounds and the tile's first particle.
+struct TileLoc {
+  int f;
+  int t;       // tile index inside the filter
+  int64_t lo, hi, base;
+};
+__device__ __forceinline__ bool locate_tile(const Batch& b, int tile, TileLoc& L) {
+  if (tile >= __ldg(b.tile_start + b.F)) return false;
+  L.f = filter_of_tile(b.tile_start, b.F, tile);
+  L.t = tile - __ldg(b.tile_start + L.f);
+  L.lo = __ldg(b.off + L.f);
+  L.hi = __ldg(b.off + L.f + 1);
+  L.base = L.lo + static_cast<int64_t>(L.t) * kTile;
+  return true;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kBlock) batch_max_kernel(const T* __restrict__ lw, Batch b) {
+  __shared__ long long sh[kWarps];
+  TileLoc L;
+  if (!locate_tile(b, blockIdx.x, L)) return;
+  const bool vec = (reinterpret_cast<uintptr_t>(lw) & 15u) == 0;
+  const int64_t end = min(L.hi, L.base + kTile);
+  long long m = key_of(neg_inf<T>());
+  bool bad = false;
+  for (int64_t i0 = L.base + 4 * static_cast<int64_t>(threadIdx.x); i0 < end; i0 += 4 * kBlock) {
+    T x[4];
+    load4(lw, i0, L.lo, end, vec, x);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const bool nan = x[q] != x[q];
+      bad |= nan || x[q] == static_cast<T>(INFINITY);
+      const long long k = key_of(x[q]);
+      if (!nan && k > m) m = k;
+    }
+  }
+  if (bad) flag_error(b.err, RS_ERR_NONFINITE);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const long long y = __shfl_xor_sync(0xffffffffu, m, o);
+    m = y > m ? y : m;
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) sh[warp] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    long long bm = sh[0];
+    for (int k = 1; k < kWarps; ++k) bm = sh[k] > bm ? sh[k] : bm;
+    // stored as the key of the binary64 value, comparable across both input types
+    atomicMax(b.fmax + L.f, key_of(value_of(bm, T())));
+  }
+}
+
+__device__ __forceinline__ double filter_M(const Batch& b, int f) {
+  return value_of(__ldcg(b.fmax + f), 0.0);
+}
+
+template <typename T, typename V>
+__global__ void __launch_bounds__(kBlock) batch_sum_kernel(const T* __restrict__ lw, Batch b) {
+  __shared__ V sh_tot[kWarps];
+  __shared__ V sh_max[kWarps];
+  __shared__ float2 sh_tab[64];
+  TileLoc L;
+  if (!locate_tile(b, blockIdx.x, L)) return;
+  const double M = filter_M(b, L.f);
+  V tm = vzero(V());
+  if (M > -DBL_MAX) {
+    const WeightCtx wc = make_ctx<T, V>(M, sh_tab);
+    const bool vec = (reinterpret_cast<uintptr_t>(lw) & 15u) == 0;
+    V val[kRows][4];
+    tile_raw_values<T, V>(lw, L.lo, L.hi, L.base, wc, vec, val, sh_tot);
+    tm = tile_total<V>(val, L.base, L.lo, L.hi, sh_max);
+  }
+  if (threadIdx.x == 0) store_v<V>(b.s_rec + blockIdx.x, tm);
+}
+
+template <typename V>
+__global__ void __launch_bounds__(kBlock) batch_prefix_kernel(Batch b) {
+  const int f = blockIdx.x;
+  const int64_t lo = b.off[f], hi = b.off[f + 1], n = hi - lo;
+  const int t0 = b.tile_start[f], T = b.tile_start[f + 1] - t0;
+  if (T <= 0 || n <= 0) return;
+  if (!(filter_M(b, f) > -DBL_MAX)) {
+    if (threadIdx.x == 0) {
+      b.fSd[f] = 0.0;
+      flag_error(b.err, RS_ERR_ZERO_WEIGHT);
+    }
+    return;
+  }
+  tile_prefix_compute<V>(b.s_rec + t0, b.P_rec + t0 + f, T, n,
+                         reinterpret_cast<V*>(b.fS + f), reinterpret_cast<V*>(b.fscale + f),
+                         b.fSd + f);
+}
+
+template <typename T, typename V, int SCHEME>
+__global__ void __launch_bounds__(kBlock)
+batch_emit_kernel(const T* __restrict__ lw, Batch b, uint64_t seed, uint64_t step,
+                  int32_t* __restrict__ a, int32_t* __restrict__ d, V* __restrict__ W) {
+  __shared__ V sh_tot[kWarps];
+  __shared__ V sh_max[kWarps];
+  __shared__ float2 sh_tab[64];
+  TileLoc L;
+  if (!locate_tile(b, blockIdx.x, L)) return;
+  const int64_t n = L.hi - L.lo;
+  const double M = filter_M(b, L.f);
+  const double Sd = __ldcg(b.fSd + L.f);
+  if (!(M > -DBL_MAX) || !(Sd > 0.0)) {  // all weights zero: flagged; identity
+    for (int64_t e = L.base + threadIdx.x; e < L.hi && e < L.base + kTile; e += kBlock) {
+      a[e] = static_cast<int32_t>(e - L.lo);
+      if (d) d[e] = static_cast<int32_t>(e - L.lo);
+      if (W) W[e] = vzero(V());
+    }
+    return;
+  }
+  const WeightCtx wc = make_ctx<T, V>(M, sh_tab);
+  const bool vec = (reinterpret_cast<uintptr_t>(lw) & 15u) == 0;
+  const double2* P = b.P_rec + __ldg(b.tile_start + L.f) + L.f;
+  const double2* s = b.s_rec + __ldg(b.tile_start + L.f);
+  const V Pt = load_v_cg<V>(P + L.t), Pn = load_v_cg<V>(P + L.t + 1);
+  if constexpr (SCHEME == RS_MULTINOMIAL) {
+    if (d)  // claims of the search kernel start from the sentinel n
+      for (int64_t e = L.base + threadIdx.x; e < L.hi && e < L.base + kTile; e += kBlock)
+        d[e] = static_cast<int32_t>(n);
+    emit_tile_W<T, V, V>(lw, L.lo, L.hi, L.base, wc, vec, Pt, Pn, W, sh_tot, sh_max);
+  } else {
+    const Keys keys = make_keys(seed, step, static_cast<uint32_t>(L.f), SCHEME);
+    const V Pm = L.t > 0 ? load_v_cg<V>(P + L.t - 1) : vzero(V());
+    const V sm = L.t > 0 ? load_v_cg<V>(s + L.t - 1) : vzero(V());
+    emit_tile_cumoff<T, V, SCHEME == RS_STRATIFIED>(
+        lw, L.lo, L.hi, L.base, wc, vec, Pt, Pn, L.t > 0, Pm, sm,
+        load_v_cg<V>(b.fS + L.f), load_v_cg<V>(b.fscale + L.f), keys, a, d, sh_tot, sh_max);
+  }
+}
+
+template <typename T, typename V>
+__global__ void __launch_bounds__(kBlock)
+batch_search_kernel(const V* __restrict__ W, Batch b, int64_t total, uint64_t seed,
+                    uint64_t step, int32_t* __restrict__ a, int32_t* __restrict__ d) {
+  const int64_t g = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  PartLoc P;
+  if (g >= total || !locate_particle(b.off, b.F, b.max_n, g, P)) return;
+  if (!(__ldcg(b.fSd + P.f) > 0.0) || !(filter_M(b, P.f) > -DBL_MAX)) return;  // identity
+  const Keys keys = make_keys(seed, step, static_cast<uint32_t>(P.f), RS_MULTINOMIAL);
+  const int32_t k = search_one<T, V>(W + P.lo, P.n, keys, P.i);
+  a[g] = k;
+  if (d) atomicMin(d + P.lo + k, static_cast<int32_t>(P.i));
+}
+
+// Claims start from the sentinel n of each particle's filter.
+__global__ void __launch_bounds__(kBlock)
+batch_fill_sentinel_kernel(const int64_t* __restrict__ off, int F, int64_t total,
+                           int32_t* __restrict__ d) {
+  const int64_t g = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  PartLoc P;
+  if (g >= total || !locate_particle(off, F, total, g, P)) return;
+  d[g] = static_cast<int32_t>(P.n);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kBlock)
+batch_mcmc_kernel(const T* __restrict__ lw, const int64_t* __restrict__ off, int F,
+                  int64_t total, int scheme, const int32_t* __restrict__ Bf, int32_t B,
+                  uint64_t seed, uint64_t step, double log_wmax, int64_t max_trials,
+                  int32_t* __restrict__ a, int32_t* __restrict__ d, int* err) {
+  const int64_t g = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  PartLoc P;
+  if (g >= total) return;
+  if (!locate_particle(off, F, total, g, P)) {
+    if (g < __ldg(off + F)) flag_error(err, RS_ERR_ARG);
+    return;
+  }
+  int32_t k;
+  if (scheme == RS_METROPOLIS) {
+    int32_t Bv = Bf ? __ldg(Bf + P.f) : B;
+    if (Bv < 0) {
+      flag_error(err, RS_ERR_ARG);
+      Bv = 0;
+    }
+    const Keys keys = make_keys(seed, step, static_cast<uint32_t>(P.f), RS_METROPOLIS);
+    k = metropolis_one(lw + P.lo, P.n, Bv, keys, P.i, err);
+  } else {
+    const Keys keys = make_keys(seed, step, static_cast<uint32_t>(P.f), RS_REJECTION);
+    k = rejection_one(lw + P.lo, P.n, log_wmax, max_trials, keys, P.i, err);
+  }
+  a[g] = k;
+  if (d) atomicMin(d + P.lo + k, static_cast<int32_t>(P.i));
+}
+
+__global__ void __launch_bounds__(kBlock)
+batch_permute_kernel(const int64_t* __restrict__ off, int F, int64_t total,
+                     const int32_t* __restrict__ a, const int32_t* __restrict__ d,
+                     int32_t* __restrict__ c, int* err) {
+  const int64_t g = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  PartLoc P;
+  if (g >= total || !locate_particle(off, F, total, g, P)) return;
+  permute_one(a + P.lo, d + P.lo, P.n, c + P.lo, P.i, err);
+}
+
+// Total number of particles of the batch (offsets[F]) is not known on the host without a
+// synchronisation, so grids are sized for the handle's capacity and surplus CTAs exit at once.
+inline int grid_particles(int64_t cap) { return static_cast<int>((cap + kBlock - 1) / kBlock); }
+
+const char* const kLblSum[4] = {"batch_sum_f32", "batch_sum_f32c", "batch_sum_f64", "batch_sum_f64n"};
+const char* const kLblEmit[4] = {"batch_emit_f32", "batch_emit_f32c", "batch_emit_f64",
+                                 "batch_emit_f64n"};
+const char* const kLblSearch[4] = {"batch_search_f32", "batch_search_f32c", "batch_search_f64",
+                                   "batch_search_f64n"};
+
+template <typename T, typename V>
+cudaError_t run_batched_scan(const Scratch& s, int scheme, const T* lw, const Batch& b,
+                             int64_t cap_tiles, uint64_t seed, uint64_t step, int32_t* a,
+                             int32_t* d, cudaStream_t st) {
+  constexpr int ai = Path<T, V>::id;
+  const int tiles = static_cast<int>(cap_tiles);
+  trace_mark(s.trace, "batch_max", st);
+  batch_max_kernel<T><<<tiles, kBlock, 0, st>>>(lw, b);
+  trace_mark(s.trace, kLblSum[ai], st);
+  batch_sum_kernel<T, V><<<tiles, kBlock, 0, st>>>(lw, b);
+  trace_mark(s.trace, "batch_prefix", st);
+  batch_prefix_kernel<V><<<b.F, kBlock, 0, st>>>(b);
+  V* W = static_cast<V*>(s.W);
+  trace_mark(s.trace, kLblEmit[ai], st);
+  switch (scheme) {
+    case RS_MULTINOMIAL:
+      batch_emit_kernel<T, V, RS_MULTINOMIAL><<<tiles, kBlock, 0, st>>>(lw, b, seed, step, a, d, W);
+      trace_mark(s.trace, kLblSearch[ai], st);
+      batch_search_kernel<T, V><<<grid_particles(s.max_n), kBlock, 0, st>>>(W, b, s.max_n, seed,
+                                                                            step, a, d);
+      break;
+    case RS_STRATIFIED:
+      batch_emit_kernel<T, V, RS_STRATIFIED><<<tiles, kBlock, 0, st>>>(lw, b, seed, step, a, d,
+                                                                      nullptr);
+      break;
+    default:
+      batch_emit_kernel<T, V, RS_SYSTEMATIC><<<tiles, kBlock, 0, st>>>(lw, b, seed, step, a, d,
+                                                                      nullptr);
+      break;
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_batched(const Scratch& s, int scheme, Acc acc, const void* logw,
+                           const int64_t* offsets, int F, const int32_t* Bf, int32_t B,
+                           uint64_t seed, uint64_t step, double log_wmax, int64_t max_trials,
+                           int32_t* out, int permute, cudaStream_t st) {
+  int32_t* a = permute ? s.a_tmp : out;
+  int32_t* d = permute ? s.d : nullptr;
+  const bool f64 = acc == Acc::F64 || acc == Acc::F64N;
+  // particles are bounded by the capacity; the true total is offsets[F] (checked per filter)
+  const int64_t total = s.max_n;
+  cudaError_t e = cudaSuccess;
+  if (scheme == RS_METROPOLIS || scheme == RS_REJECTION) {
+    if (d) {
+      trace_mark(s.trace, "batch_fill", st);
+      batch_fill_sentinel_kernel<<<grid_particles(total), kBlock, 0, st>>>(offsets, F, total, d);
+    }
+    trace_mark(s.trace, scheme == RS_METROPOLIS ? (f64 ? "batch_metropolis_f64" : "batch_metropolis_f32")
+                                                : (f64 ? "batch_rejection_f64" : "batch_rejection_f32"),
+               st);
+    if (f64)
+      batch_mcmc_kernel<double><<<grid_particles(total), kBlock, 0, st>>>(
+          static_cast<const double*>(logw), offsets, F, total, scheme, Bf, B, seed, step,
+          log_wmax, max_trials, a, d, s.err);
+    else
+      batch_mcmc_kernel<float><<<grid_particles(total), kBlock, 0, st>>>(
+          static_cast<const float*>(logw), offsets, F, total, scheme, Bf, B, seed, step,
+          log_wmax, max_trials, a, d, s.err);
+  } else {
+    Batch b;
+    b.off = offsets;
+    b.F = F;
+    b.max_n = s.max_n;
+    b.tile_start = s.batch_tile_start;
+    b.fmax = s.batch_fmax;
+    b.fS = s.batch_fS;
+    b.fscale = s.batch_fscale;
+    b.fSd = s.batch_fSd;
+    b.s_rec = s.batch_s_rec;
+    b.P_rec = s.batch_P_rec;
+    b.err = s.err;
+    trace_mark(s.trace, "batch_plan", st);
+    batch_plan_kernel<<<1, 1024, 0, st>>>(b);
+    // every filter adds at most one partial tile to the max_n / 4096 full ones
+    const int64_t cap_tiles = s.max_n / kTile + F + 1;
+    switch (acc) {
+      case Acc::F32:
+        e = run_batched_scan<float, float>(s, scheme, static_cast<const float*>(logw), b,
+                                           cap_tiles, seed, step, a, d, st);
+        break;
+      case Acc::F32C:
+        e = run_batched_scan<float, float2>(s, scheme, static_cast<const float*>(logw), b,
+                                            cap_tiles, seed, step, a, d, st);
+        break;
+      case Acc::F64:
+        e = run_batched_scan<double, float2>(s, scheme, static_cast<const double*>(logw), b,
+                                             cap_tiles, seed, step, a, d, st);
+        break;
+      case Acc::F64N:
+        e = run_batched_scan<double, double>(s, scheme, static_cast<const double*>(logw), b,
+                                             cap_tiles, seed, step, a, d, st);
+        break;
+    }
+  }
+  if (e == cudaSuccess) e = cudaGetLastError();
+  if (e == cudaSuccess && permute) {
+    trace_mark(s.trace, "batch_permute", st);
+    batch_permute_kernel<<<grid_particles(total), kBlock, 0, st>>>(offsets, F, total, s.a_tmp,
+                                                                    s.d, out, s.err);
+    e = cudaGetLastError();
+  }
+  return e;
+}
+
+}  // namespace rsk

@@ -13,7 +13,9 @@ struct ScanGlob {
   unsigned int ticket_max;   // last-CTA counters (self-resetting)
   unsigned int ticket_tile;
   unsigned int ticket_iscan;
-  unsigned int pad;
+  unsigned int batch_next;   // work counter of the batched kernel (self-resetting)
+  unsigned int batch_ticket;
+  unsigned int pad[3];
   double2 S_raw;             // total, in the accumulator type of the call
   double2 scale_raw;         // N / total, in the accumulator type of the call
 };
@@ -34,6 +36,8 @@ inline void trace_mark(Trace* t, const char* label, cudaStream_t st) {
   }
 }
 
+constexpr int kBatchMaxTiles = 256;  // batched filters hold at most 256 * 4096 = 2^20 particles
+
 struct Scratch {
   Trace* trace;      // nullptr unless tracing is enabled
   int32_t* d;        // claim vector (Prepermute), max_n
@@ -44,6 +48,16 @@ struct Scratch {
   long long* irec;   // per-tile records of the integer scan (2 * (max_tiles + 2))
   ScanGlob* glob;
   int* err;          // device status word
+  // batched resampling: per-filter and per-tile records
+  int32_t* batch_tile_start;  // max_filters + 1
+  long long* batch_fmax;      // max_filters
+  double2* batch_fS;          // max_filters
+  double2* batch_fscale;      // max_filters
+  double* batch_fSd;          // max_filters
+  double2* batch_s_rec;       // batch_tile_cap
+  double2* batch_P_rec;       // batch_tile_cap + max_filters
+  int64_t max_filters;        // max(1024, max_n / 16)
+  int64_t batch_tile_cap;     // max_n / 4096 + max_filters + 1
   int64_t max_n;
   int64_t max_tiles;
   int max_blocks;    // grid of the max pass
@@ -59,6 +73,12 @@ cudaError_t launch_scan_resample(const Scratch& s, int scheme, Acc acc, const vo
                                  int32_t* a_out, int32_t* d_or_null, cudaStream_t st);
 cudaError_t launch_cumulative_weights(const Scratch& s, Acc acc, const void* logw, int64_t N,
                                       void* W_out, double* log_total, cudaStream_t st);
+
+// batched.cu
+cudaError_t launch_batched(const Scratch& s, int scheme, Acc acc, const void* logw,
+                           const int64_t* offsets, int F, const int32_t* Bf, int32_t B,
+                           uint64_t seed, uint64_t step, double log_wmax, int64_t max_trials,
+                           int32_t* out, int permute, cudaStream_t st);
 
 // mcmc.cu
 cudaError_t launch_metropolis(const Scratch& s, bool f64, const void* logw, int64_t N,

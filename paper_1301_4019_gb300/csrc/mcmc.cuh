@@ -1,0 +1,250 @@
+// mcmc.cuh -- per-particle bodies of the collective-free resamplers of Section 2: the
+// Metropolis chain of Code 2 and the rejection loop of Code 3, shared by the single-filter
+// and batched kernels. Binary64 decisions are made on the binary32 pipes with an exact
+// fallback (same outcome as the binary64 definition).
+#pragma once
+
+#include <cstdint>
+
+#include "common.cuh"
+
+namespace rsk {
+namespace {
+
+// u < w^j / w^k from log-weights: a ratio >= 1 or a zero-weight current state accepts.
+template <typename T>
+__device__ __forceinline__ bool metropolis_accept(T lwk, T lwj, T u) {
+  if (lwk == neg_inf<T>()) return true;
+  const T delta = lwj - lwk;
+  if (delta >= T(0)) return true;
+  return u < exp_pinned(delta);
+}
+
+// ---------------------------------------------------------------------------------------
+// Binary64 decisions on the binary32 pipes. GB300 runs binary64 arithmetic at 1/57 of the
+// binary32 rate, so the binary64 test  u < exp(lw_j - lw_k)  is first decided with binary32
+// arithmetic and a rigorous error bound, and evaluated exactly (binary64 subtraction,
+// pinned binary64 exp, 53-bit u) only when u falls inside the uncertainty band. The outcome
+// is therefore identical to the binary64 definition; the band has relative width about
+// 2^-21 + 2^-23 (|lw_j| + |lw_k|), so the exact path runs for a few draws per million.
+// ---------------------------------------------------------------------------------------
+
+// Truncation of a finite binary64 to binary32 with integer operations only: |x - f| <
+// 2^-23 |x| + 2^-126. Returns false (f unusable) for inf, NaN or |x| >= 2^128.
+__device__ __forceinline__ bool f64_to_f32_trunc(double x, float& f) {
+  const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(x));
+  const unsigned int sign = static_cast<unsigned int>(b >> 32) & 0x80000000u;
+  const int e = static_cast<int>((b >> 52) & 0x7ffu);
+  if (e == 0x7ff) return false;
+  const int fe = e - 1023 + 127;
+  if (fe >= 255) return false;
+  if (fe <= 0) {  // below the binary32 normal range (or zero): 0, absolute error < 2^-126
+    f = __uint_as_float(sign);
+    return true;
+  }
+  const unsigned int m = static_cast<unsigned int>((b >> 29) & 0x7fffffu);
+  f = __uint_as_float(sign | (static_cast<unsigned int>(fe) << 23) | m);
+  return true;
+}
+
+// Order-preserving signed key of a binary64 (for exact comparisons without the FP64 pipe).
+__device__ __forceinline__ long long f64_key(double x) {
+  const long long b = __double_as_longlong(x);
+  return b >= 0 ? b : (b ^ 0x7fffffffffffffffLL);
+}
+
+// Decides u < exp_pinned(lwj - lwk) for lwj < lwk, lwk > -inf, with u = 53-bit u01 of x.
+// lwj_f / lwk_f are binary32 truncations (valid flags as returned above).
+__device__ __noinline__ bool exact_f64_less_exp(double lwj, double lwk, uint4 x) {
+  return u01_f64(x) < exp_pinned(__dsub_rn(lwj, lwk));
+}
+
+__device__ __forceinline__ bool f64_accept_lt(double lwj, float lwj_f, bool okj, double lwk,
+                                              float lwk_f, bool okk, uint4 x) {
+  if (!(okj && okk)) return exact_f64_less_exp(lwj, lwk, x);
+  const float df = __fsub_rn(lwj_f, lwk_f);  // <= 0 up to rounding
+  // bound on |df - (lwj - lwk)|: both truncations, the subtraction's rounding, margin
+  const float E = __fmaf_ru(fabsf(lwj_f) + fabsf(lwk_f), 0x1p-23f,
+                            __fmaf_ru(fabsf(df), 0x1p-24f, 0x1p-124f));
+  if (!(E < 0.01f)) return exact_f64_less_exp(lwj, lwk, x);
+  // u lies in [x0 2^-32, (x0 + 1) 2^-32)
+  const float u_lo = __fmul_rn(__uint2float_rd(x.x), 0x1p-32f);
+  const float u_hi = __fmul_rn(__fadd_ru(__uint2float_ru(x.x), 1.0f), 0x1p-32f);
+  const float ef = exp_pinned(df);
+  if (ef == 0.0f) {  // exp(df) < 2^-124: the binary64 ratio is below e^-86 < 2^-32 <= u
+    if (x.x != 0u) return false;
+    return exact_f64_less_exp(lwj, lwk, x);
+  }
+  // exp(lwj - lwk) within ef * exp(+-E) * (1 +- 2^-23) (1 +- 2^-52); m bounds all of it
+  const float m = __fmaf_ru(E, 1.02f, 0x1p-21f);
+  const float lo = __fmul_rd(ef, __fsub_rd(1.0f, m));
+  const float hi = __fmul_ru(ef, __fadd_ru(1.0f, m));
+  if (u_hi < lo) return true;
+  if (u_lo >= hi) return false;
+  return exact_f64_less_exp(lwj, lwk, x);
+}
+
+constexpr int kUnroll = 4;
+
+// Metropolis chain of particle i over n log-weights lw (Code 2): B steps, step s proposes j
+// and draws u from counter (i, s). Returns the ancestor.
+__device__ __forceinline__ int32_t metropolis_one(const float* __restrict__ lw, int64_t n,
+                                                  int32_t B, const Keys& keys, int64_t i,
+                                                  int* err) {
+  float lwk = __ldg(lw + i);
+  if (nonfinite_logw(lwk)) flag_error(err, RS_ERR_NONFINITE);
+  int64_t k = i;
+  const uint32_t ii = static_cast<uint32_t>(i);
+  int32_t s = 0;
+  for (; s + kUnroll <= B; s += kUnroll) {
+    float u[kUnroll], lwj[kUnroll];
+    int64_t j[kUnroll];
+#pragma unroll
+    for (int q = 0; q < kUnroll; ++q) {
+      const uint4 x = draw(keys, ii, static_cast<uint32_t>(s + q));
+      j[q] = uniform_index(x, n);
+      u[q] = u01_f32(x);
+      lwj[q] = __ldg(lw + j[q]);
+    }
+#pragma unroll
+    for (int q = 0; q < kUnroll; ++q) {
+      if (metropolis_accept(lwk, lwj[q], u[q])) {
+        k = j[q];
+        lwk = lwj[q];
+      }
+    }
+  }
+  for (; s < B; ++s) {
+    const uint4 x = draw(keys, ii, static_cast<uint32_t>(s));
+    const int64_t j = uniform_index(x, n);
+    const float lwj = __ldg(lw + j);
+    if (metropolis_accept(lwk, lwj, u01_f32(x))) {
+      k = j;
+      lwk = lwj;
+    }
+  }
+  return static_cast<int32_t>(k);
+}
+
+__device__ __forceinline__ bool f64_step_accept(double lwk, float lwk_f, bool okk, long long kk,
+                                                double lwj, float lwj_f, bool okj, long long kj,
+                                                uint4 x) {
+  const long long kNegInf = f64_key(-INFINITY);
+  if (kk == kNegInf || kj >= kk) return true;  // zero-weight state, or ratio >= 1
+  if (kj == kNegInf) return false;             // zero-weight proposal
+  return f64_accept_lt(lwj, lwj_f, okj, lwk, lwk_f, okk, x);
+}
+
+__device__ __forceinline__ int32_t metropolis_one(const double* __restrict__ lw, int64_t n,
+                                                  int32_t B, const Keys& keys, int64_t i,
+                                                  int* err) {
+  double lwk = __ldg(lw + i);
+  if (nonfinite_logw(lwk)) flag_error(err, RS_ERR_NONFINITE);
+  float lwk_f;
+  bool okk = f64_to_f32_trunc(lwk, lwk_f);
+  long long kk = f64_key(lwk);
+  int64_t k = i;
+  const uint32_t ii = static_cast<uint32_t>(i);
+  int32_t s = 0;
+  for (; s + kUnroll <= B; s += kUnroll) {
+    uint4 x[kUnroll];
+    double lwj[kUnroll];
+    int64_t j[kUnroll];
+#pragma unroll
+    for (int q = 0; q < kUnroll; ++q) {
+      x[q] = draw(keys, ii, static_cast<uint32_t>(s + q));
+      j[q] = uniform_index(x[q], n);
+      lwj[q] = __ldg(lw + j[q]);
+    }
+#pragma unroll
+    for (int q = 0; q < kUnroll; ++q) {
+      const long long kj = f64_key(lwj[q]);
+      float lwj_f;
+      const bool okj = f64_to_f32_trunc(lwj[q], lwj_f);
+      if (f64_step_accept(lwk, lwk_f, okk, kk, lwj[q], lwj_f, okj, kj, x[q])) {
+        k = j[q];
+        lwk = lwj[q];
+        lwk_f = lwj_f;
+        okk = okj;
+        kk = kj;
+      }
+    }
+  }
+  for (; s < B; ++s) {
+    const uint4 x = draw(keys, ii, static_cast<uint32_t>(s));
+    const int64_t j = uniform_index(x, n);
+    const double lwj = __ldg(lw + j);
+    const long long kj = f64_key(lwj);
+    float lwj_f;
+    const bool okj = f64_to_f32_trunc(lwj, lwj_f);
+    if (f64_step_accept(lwk, lwk_f, okk, kk, lwj, lwj_f, okj, kj, x)) {
+      k = j;
+      lwk = lwj;
+      lwk_f = lwj_f;
+      okk = okj;
+      kk = kj;
+    }
+  }
+  return static_cast<int32_t>(k);
+}
+
+// Rejection loop of particle i (Code 3): attempt 0 proposes j = i, attempt s >= 1 a uniform
+// j; both draw u from counter (i, s); accept when u < exp(lw^j - log w_max). A log-weight
+// above the bound is flagged and accepted; max_trials attempts without acceptance keep i and
+// flag the cap. *trials receives the attempts made.
+__device__ __forceinline__ int32_t rejection_one(const float* __restrict__ lw, int64_t n,
+                                                 double log_wmax, int64_t max_trials,
+                                                 const Keys& keys, int64_t i, int* err) {
+  const float lwmax = static_cast<float>(log_wmax);
+  const float lwi = __ldg(lw + i);
+  if (nonfinite_logw(lwi)) flag_error(err, RS_ERR_NONFINITE);
+  const uint32_t ii = static_cast<uint32_t>(i);
+  int64_t j = i;
+  for (int64_t s = 0; s < max_trials; ++s) {
+    const uint4 x = draw(keys, ii, static_cast<uint32_t>(s));
+    if (s > 0) j = uniform_index(x, n);
+    const float u = u01_f32(x);
+    const float lwj = (s == 0) ? lwi : __ldg(lw + j);
+    const float delta = lwj - lwmax;
+    if (delta > 0.0f) {
+      flag_error(err, RS_ERR_BOUND_VIOLATED);
+      return static_cast<int32_t>(j);
+    }
+    if (delta == 0.0f || u < exp_pinned(delta)) return static_cast<int32_t>(j);
+  }
+  flag_error(err, RS_ERR_REJECTION_CAP);
+  return static_cast<int32_t>(i);
+}
+
+__device__ __forceinline__ int32_t rejection_one(const double* __restrict__ lw, int64_t n,
+                                                 double lwmax, int64_t max_trials,
+                                                 const Keys& keys, int64_t i, int* err) {
+  const double lwi = __ldg(lw + i);
+  if (nonfinite_logw(lwi)) flag_error(err, RS_ERR_NONFINITE);
+  float lwmax_f;
+  const bool okm = f64_to_f32_trunc(lwmax, lwmax_f);
+  const long long km = f64_key(lwmax);
+  const long long kNegInf = f64_key(-INFINITY);
+  const uint32_t ii = static_cast<uint32_t>(i);
+  int64_t j = i;
+  for (int64_t s = 0; s < max_trials; ++s) {
+    const uint4 x = draw(keys, ii, static_cast<uint32_t>(s));
+    if (s > 0) j = uniform_index(x, n);
+    const double lwj = (s == 0) ? lwi : __ldg(lw + j);
+    const long long kj = f64_key(lwj);
+    if (kj > km && lwj == lwj) {  // above the bound (NaN never compares)
+      flag_error(err, RS_ERR_BOUND_VIOLATED);
+      return static_cast<int32_t>(j);
+    }
+    if (kj == km) return static_cast<int32_t>(j);  // ratio exactly 1
+    if (kj == kNegInf || lwj != lwj) continue;
+    float lwj_f;
+    const bool okj = f64_to_f32_trunc(lwj, lwj_f);
+    if (f64_accept_lt(lwj, lwj_f, okj, lwmax, lwmax_f, okm, x)) return static_cast<int32_t>(j);
+  }
+  flag_error(err, RS_ERR_REJECTION_CAP);
+  return static_cast<int32_t>(i);
+}
+
+}  // namespace
+}  // namespace rsk

@@ -31,207 +31,11 @@
 #include "common.cuh"
 #include "dfexp.cuh"
 #include "internal.h"
+#include "tile.cuh"
 #include "values.cuh"
 
 namespace rsk {
 namespace {
-
-// ---------------------------------------------------------------------------------------
-// Weights and uniforms per (input type, accumulator type)
-// ---------------------------------------------------------------------------------------
-struct WeightCtx {
-  double Md;          // maximum log-weight
-  float Mf;           // as binary32 (binary32 inputs: exact)
-  float2 M2;          // as two-float (double-float path)
-  const float2* tab;  // 2^(j/64) table in shared memory (double-float path)
-};
-
-template <typename T, typename V> struct Path;
-template <> struct Path<float, float> {
-  using U = float;
-  static constexpr int id = 0;
-  static constexpr bool kTable = false;
-  __device__ static float weight(float x, const WeightCtx& c) {
-    return (x == neg_inf<float>()) ? 0.0f : exp_pinned(__fsub_rn(x, c.Mf));
-  }
-  __device__ static U draw_u(uint4 x) { return u01_f32(x); }
-};
-template <> struct Path<float, float2> {
-  using U = float;
-  static constexpr int id = 1;
-  static constexpr bool kTable = false;
-  __device__ static float2 weight(float x, const WeightCtx& c) {
-    return make_float2((x == neg_inf<float>()) ? 0.0f : exp_pinned(__fsub_rn(x, c.Mf)), 0.0f);
-  }
-  __device__ static U draw_u(uint4 x) { return u01_f32(x); }
-};
-template <> struct Path<double, float2> {
-  using U = float2;
-  static constexpr int id = 2;
-  static constexpr bool kTable = true;
-  __device__ static float2 weight(double x, const WeightCtx& c) {
-    if (x == neg_inf<double>()) return make_float2(0.0f, 0.0f);
-    return exp_df(add22_accurate(split_f64(x), neg2(c.M2)), c.tab);
-  }
-  __device__ static U draw_u(uint4 x) { return u01_f2(x); }
-};
-template <> struct Path<double, double> {
-  using U = double;
-  static constexpr int id = 3;
-  static constexpr bool kTable = false;
-  __device__ static double weight(double x, const WeightCtx& c) {
-    return (x == neg_inf<double>()) ? 0.0 : exp_pinned(__dsub_rn(x, c.Md));
-  }
-  __device__ static U draw_u(uint4 x) { return u01_f64(x); }
-};
-
-// Builds the weight context (and stages the exp table in shared memory when needed).
-template <typename T, typename V>
-__device__ __forceinline__ WeightCtx make_ctx(double Md, float2* sh_tab) {
-  WeightCtx c;
-  c.Md = Md;
-  c.Mf = static_cast<float>(Md);
-  c.M2 = split_f64(Md);
-  c.tab = sh_tab;
-  if constexpr (Path<T, V>::kTable) {
-    if (threadIdx.x < 64) sh_tab[threadIdx.x] = kExp2Frac64[threadIdx.x];
-    __syncthreads();
-  }
-  return c;
-}
-
-// Reads the 4 consecutive log-weights idx..idx+3 (positions >= N read as -inf).
-template <typename T>
-__device__ __forceinline__ void load4(const T* __restrict__ lw, int64_t idx, int64_t N, bool vec,
-                                      T (&x)[4]) {
-  if (vec) {
-    if constexpr (sizeof(T) == 4) {
-      const float4 v = __ldg(reinterpret_cast<const float4*>(lw + idx));
-      x[0] = v.x; x[1] = v.y; x[2] = v.z; x[3] = v.w;
-    } else {
-      const double2 v0 = __ldg(reinterpret_cast<const double2*>(lw + idx));
-      const double2 v1 = __ldg(reinterpret_cast<const double2*>(lw + idx + 2));
-      x[0] = v0.x; x[1] = v0.y; x[2] = v1.x; x[3] = v1.y;
-    }
-  } else {
-#pragma unroll
-    for (int q = 0; q < 4; ++q) x[q] = (idx + q < N) ? lw[idx + q] : neg_inf<T>();
-  }
-}
-
-// Element e of the tile owned by (warp, row, lane, q): warp*512 + row*128 + lane*4 + q.
-__device__ __forceinline__ int tile_offset(int warp, int r, int lane, int q) {
-  return warp * 512 + r * 128 + lane * 4 + q;
-}
-
-// The tile scan shared by the tile-sum and emit passes: val[r][q] = sum of the weights of
-// the tile up to and including the element (r, q) of this thread, as computed by a fixed
-// tree: sequential inside a lane, Hillis-Steele across the 32 lanes of a row, a running
-// carry across the 4 rows of a warp, and a sequential prefix over the 8 warps. Elements at
-// positions >= N have weight 0. All four rows are loaded before any arithmetic.
-template <typename T, typename V>
-__device__ __forceinline__ void tile_raw_values(const T* __restrict__ lw, int64_t N, int64_t base,
-                                                const WeightCtx& wc, bool vec,
-                                                V (&val)[kRows][4], V* sh_tot) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  T x[kRows][4];
-#pragma unroll
-  for (int r = 0; r < kRows; ++r) load4(lw, base + tile_offset(warp, r, lane, 0), N, vec, x[r]);
-  V carry = vzero(V());
-#pragma unroll
-  for (int r = 0; r < kRows; ++r) {
-    V loc[4];
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const V wv = vfrom_w(Path<T, V>::weight(x[r][q], wc), V());
-      loc[q] = (q == 0) ? wv : vadd(loc[q - 1], wv);
-    }
-    V incl = loc[3];
-#pragma unroll
-    for (int dd = 1; dd < 32; dd <<= 1) {
-      const V y = vshfl_up(incl, dd);
-      if (lane >= dd) incl = vadd(y, incl);
-    }
-    V excl = vshfl_up(incl, 1);
-    if (lane == 0) excl = vzero(V());
-    const V rowtot = vshfl(incl, 31);
-#pragma unroll
-    for (int q = 0; q < 4; ++q) val[r][q] = vadd(carry, vadd(excl, loc[q]));
-    carry = vadd(carry, rowtot);
-  }
-  if (lane == 0) sh_tot[warp] = carry;
-  __syncthreads();
-  V pw = vzero(V());
-  for (int k = 0; k < warp; ++k) pw = vadd(pw, sh_tot[k]);
-#pragma unroll
-  for (int r = 0; r < kRows; ++r)
-#pragma unroll
-    for (int q = 0; q < 4; ++q) val[r][q] = vadd(pw, val[r][q]);
-}
-
-// Running maximum of the tile values in element order (exact), restricted to positions < N
-// (later positions keep their raw value and are never used). Returns, through sh_max, the
-// maximum of each warp's valid values; prevmax = maximum over the previous warps.
-template <typename V>
-__device__ __forceinline__ void tile_running_max(V (&val)[kRows][4], int64_t base, int64_t N,
-                                                 V* sh_max, V& prevmax) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  V cm = vzero(V());
-#pragma unroll
-  for (int r = 0; r < kRows; ++r) {
-    V x[4];
-    V m = vzero(V());
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const bool valid = base + tile_offset(warp, r, lane, q) < N;
-      if (valid) m = vmax(m, val[r][q]);
-      x[q] = m;
-    }
-    V im = m;
-#pragma unroll
-    for (int dd = 1; dd < 32; dd <<= 1) {
-      const V y = vshfl_up(im, dd);
-      if (lane >= dd) im = vmax(y, im);
-    }
-    V em = vshfl_up(im, 1);
-    if (lane == 0) em = vzero(V());
-    const V before = vmax(em, cm);
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const bool valid = base + tile_offset(warp, r, lane, q) < N;
-      if (valid) val[r][q] = vmax(x[q], before);
-    }
-    cm = vmax(cm, vshfl(im, 31));
-  }
-  if (lane == 0) sh_max[warp] = cm;
-  __syncthreads();
-  prevmax = vzero(V());
-  for (int k = 0; k < warp; ++k) prevmax = vmax(prevmax, sh_max[k]);
-#pragma unroll
-  for (int r = 0; r < kRows; ++r)
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const bool valid = base + tile_offset(warp, r, lane, q) < N;
-      if (valid) val[r][q] = vmax(val[r][q], prevmax);
-    }
-}
-
-template <typename V> __device__ __forceinline__ V load_v(const double2* p) {
-  return *reinterpret_cast<const V*>(p);
-}
-template <typename V> __device__ __forceinline__ void store_v(double2* p, V v) {
-  *reinterpret_cast<V*>(p) = v;
-}
-template <typename V> __device__ __forceinline__ V load_v_cg(const double2* p);
-template <> __device__ __forceinline__ float load_v_cg<float>(const double2* p) {
-  return __ldcg(reinterpret_cast<const float*>(p));
-}
-template <> __device__ __forceinline__ double load_v_cg<double>(const double2* p) {
-  return __ldcg(reinterpret_cast<const double*>(p));
-}
-template <> __device__ __forceinline__ float2 load_v_cg<float2>(const double2* p) {
-  return __ldcg(reinterpret_cast<const float2*>(p));
-}
 
 // ---------------------------------------------------------------------------------------
 // Pass 1: maximum log-weight, compared through order-preserving integer keys (exact, and
@@ -267,7 +71,7 @@ max_kernel(const T* __restrict__ lw, int64_t N, ScanGlob* g, double* blockmax, i
   for (int64_t i0 = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) * 4; i0 < N;
        i0 += stride) {
     T x[4];
-    load4(lw, i0, N, vec && i0 + 4 <= N, x);
+    load4(lw, i0, 0, N, vec && i0 + 4 <= N, x);
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       const bool nan = x[q] != x[q];
@@ -321,73 +125,6 @@ max_kernel(const T* __restrict__ lw, int64_t N, ScanGlob* g, double* blockmax, i
 }
 
 // ---------------------------------------------------------------------------------------
-// Tile prefixes (run by the last CTA of the tile-sum pass): P_0 = 0, P_{t+1} = P_t + s_t
-// in binary64 with a running maximum, rounded monotonically to the accumulator type. The
-// total used by the emit pass is the cumulative weight of the last particle exactly as the
-// emit pass computes it, so that the last particle receives O = N.
-// ---------------------------------------------------------------------------------------
-template <typename V>
-__device__ void tile_prefix_scan(const double2* s_rec, double2* P_rec, int T, ScanGlob* g,
-                                 int64_t N, int* err, double* log_total_out) {
-  __shared__ double sh_sum[kWarps];
-  __shared__ double sh_max[kWarps];
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int chunk = (T + kBlock - 1) / kBlock;
-  const int t0 = min(T, tid * chunk), t1 = min(T, t0 + chunk);
-  double local = 0.0;
-  for (int t = t0; t < t1; ++t) local = __dadd_rn(local, vto_double(load_v_cg<V>(s_rec + t)));
-  double incl = local;
-#pragma unroll
-  for (int dd = 1; dd < 32; dd <<= 1) {
-    const double y = __shfl_up_sync(0xffffffffu, incl, dd);
-    if (lane >= dd) incl = __dadd_rn(y, incl);
-  }
-  double excl = __shfl_up_sync(0xffffffffu, incl, 1);
-  if (lane == 0) excl = 0.0;
-  if (lane == 31) sh_sum[warp] = incl;
-  __syncthreads();
-  double wp = 0.0;
-  for (int k = 0; k < warp; ++k) wp = __dadd_rn(wp, sh_sum[k]);
-  const double start = __dadd_rn(wp, excl);
-  // end value of this thread's chunk (sequential), for the running maximum across threads
-  double endv = start;
-  for (int t = t0; t < t1; ++t) endv = __dadd_rn(endv, vto_double(load_v_cg<V>(s_rec + t)));
-  double im = endv;
-#pragma unroll
-  for (int dd = 1; dd < 32; dd <<= 1) {
-    const double y = __shfl_up_sync(0xffffffffu, im, dd);
-    if (lane >= dd) im = y > im ? y : im;
-  }
-  double em = __shfl_up_sync(0xffffffffu, im, 1);
-  if (lane == 0) em = 0.0;
-  if (lane == 31) sh_max[warp] = im;
-  __syncthreads();
-  double prevmax = em;
-  for (int k = 0; k < warp; ++k) prevmax = sh_max[k] > prevmax ? sh_max[k] : prevmax;
-  double p = start;
-  for (int t = t0; t < t1; ++t) {
-    store_v<V>(P_rec + t, vfrom_double(p > prevmax ? p : prevmax, V()));
-    p = __dadd_rn(p, vto_double(load_v_cg<V>(s_rec + t)));
-  }
-  if (t1 == T && t0 < T) store_v<V>(P_rec + T, vfrom_double(p > prevmax ? p : prevmax, V()));
-  __syncthreads();
-  if (tid == 0) {
-    // the total is the cumulative weight of the last particle exactly as the emit pass
-    // computes it: clamp(P_{T-1} + s_{T-1}, P_{T-1}, P_T)
-    const V Pm = load_v_cg<V>(P_rec + (T - 1));
-    const V Pn = load_v_cg<V>(P_rec + T);
-    const V st = load_v_cg<V>(s_rec + (T - 1));
-    const V S = vclamp(vadd(Pm, st), Pm, Pn);
-    const double Sd = vto_double(S);
-    store_v<V>(&g->S_raw, S);
-    store_v<V>(&g->scale_raw, vfrom_double(__ddiv_rn(static_cast<double>(N), Sd), V()));
-    g->S_d = Sd;
-    if (!(Sd > 0.0)) flag_error(err, RS_ERR_ZERO_WEIGHT);
-    if (log_total_out) *log_total_out = __dadd_rn(g->M, log(Sd));
-  }
-}
-
-// ---------------------------------------------------------------------------------------
 // Pass 2: tile sums and, in the last CTA, tile prefixes.
 // ---------------------------------------------------------------------------------------
 template <typename T, typename V>
@@ -401,27 +138,15 @@ tile_sum_kernel(const T* __restrict__ lw, int64_t N, ScanGlob* g, double2* s_rec
   const double Md = g->M;
   const bool zero = !(Md > -DBL_MAX);
   const int64_t base = static_cast<int64_t>(blockIdx.x) * kTile;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  V m = vzero(V());
+  V tm = vzero(V());
   if (!zero) {
     const WeightCtx wc = make_ctx<T, V>(Md, sh_tab);
-    const bool vec = ((reinterpret_cast<uintptr_t>(lw) & 15u) == 0) && (base + kTile <= N);
+    const bool vec = (reinterpret_cast<uintptr_t>(lw) & 15u) == 0;
     V val[kRows][4];
-    tile_raw_values<T, V>(lw, N, base, wc, vec, val, sh_tot);
-#pragma unroll
-    for (int r = 0; r < kRows; ++r)
-#pragma unroll
-      for (int q = 0; q < 4; ++q)
-        if (base + tile_offset(warp, r, lane, q) < N) m = vmax(m, val[r][q]);
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) m = vmax(m, vshfl_xor(m, o));
-    if (lane == 0) sh_max[warp] = m;
-    __syncthreads();
+    tile_raw_values<T, V>(lw, 0, N, base, wc, vec, val, sh_tot);
+    tm = tile_total<V>(val, base, 0, N, sh_max);
   }
   if (threadIdx.x == 0) {
-    V tm = vzero(V());
-    if (!zero)
-      for (int k = 0; k < kWarps; ++k) tm = vmax(tm, sh_max[k]);
     store_v<V>(s_rec + blockIdx.x, tm);
     __threadfence();
     const unsigned t = atomicAdd(&g->ticket_tile, 1u);
@@ -430,36 +155,19 @@ tile_sum_kernel(const T* __restrict__ lw, int64_t N, ScanGlob* g, double2* s_rec
   __syncthreads();
   if (!am_last) return;
   __threadfence();
-  tile_prefix_scan<V>(s_rec, P_rec, static_cast<int>(gridDim.x), g, N, err, log_total_out);
-  if (threadIdx.x == 0) g->ticket_tile = 0u;
-}
-
-// Cumulative offspring of a cumulative weight W (Codes 7 and 8 with r = W * N / W^N).
-template <typename T, typename V, bool STRAT>
-__device__ __forceinline__ int32_t cum_offspring(V W, V S, V scale,
-                                                 typename Path<T, V>::U u_sys,
-                                                 const Keys& keys, int64_t N) {
-  if (veq(W, S)) return static_cast<int32_t>(N);
-  const V r = vscale(W, scale);
-  int64_t o;
-  if constexpr (STRAT) {
-    int64_t k = floor_to_i64(r);
-    k = k < N - 1 ? k : N - 1;
-    const auto uk = Path<T, V>::draw_u(draw(keys, static_cast<uint32_t>(k), 0u));
-    o = floor_to_i64(vplus_u(r, uk));
-    o = o < k + 1 ? o : k + 1;
-  } else {
-    o = floor_to_i64(vplus_u(r, u_sys));
+  tile_prefix_compute<V>(s_rec, P_rec, static_cast<int>(gridDim.x), N,
+                         reinterpret_cast<V*>(&g->S_raw), reinterpret_cast<V*>(&g->scale_raw),
+                         &g->S_d);
+  if (threadIdx.x == 0) {
+    const double Sd = g->S_d;
+    if (!(Sd > 0.0)) flag_error(err, RS_ERR_ZERO_WEIGHT);
+    if (log_total_out) *log_total_out = __dadd_rn(g->M, log(Sd));
+    g->ticket_tile = 0u;
   }
-  o = o < N ? o : N;
-  o = o > 0 ? o : 0;
-  return static_cast<int32_t>(o);
 }
 
 // ---------------------------------------------------------------------------------------
-// Pass 3a: systematic / stratified emission. Writes a (Code 11) and, when d is given, the
-// Prepermute claims d_i = O_{i-1} if particle i has offspring, else N (for a
-// non-decreasing ancestry the lowest claimant of slot i is the first position of its run).
+// Pass 3a: systematic / stratified emission, one tile per CTA.
 // ---------------------------------------------------------------------------------------
 template <typename T, typename V, bool STRAT>
 __global__ void __launch_bounds__(kBlock)
@@ -470,89 +178,29 @@ emit_cumoff_kernel(const T* __restrict__ lw, int64_t N, const ScanGlob* g, const
   __shared__ V sh_max[kWarps];
   __shared__ float2 sh_tab[64];
   const int64_t base = static_cast<int64_t>(blockIdx.x) * kTile;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const double Md = g->M;
-  const V S = load_v<V>(&g->S_raw);
   if (!(Md > -DBL_MAX) || !(g->S_d > 0.0)) {  // all weights zero: flagged; emit identity
-#pragma unroll
-    for (int r = 0; r < kRows; ++r)
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const int64_t i = base + tile_offset(warp, r, lane, q);
-        if (i < N) {
-          a[i] = static_cast<int32_t>(i);
-          if (d) d[i] = static_cast<int32_t>(i);
-        }
-      }
+    for (int64_t i = base + threadIdx.x; i < N && i < base + kTile; i += kBlock) {
+      a[i] = static_cast<int32_t>(i);
+      if (d) d[i] = static_cast<int32_t>(i);
+    }
     return;
   }
   const WeightCtx wc = make_ctx<T, V>(Md, sh_tab);
-  const V scale = load_v<V>(&g->scale_raw);
-  using U = typename Path<T, V>::U;
-  const U u_sys = Path<T, V>::draw_u(draw(keys, 0u, 0u));
-  const bool vec = ((reinterpret_cast<uintptr_t>(lw) & 15u) == 0) && (base + kTile <= N);
-  V val[kRows][4];
-  tile_raw_values<T, V>(lw, N, base, wc, vec, val, sh_tot);
-  V prevmax;
-  tile_running_max<V>(val, base, N, sh_max, prevmax);
+  const bool vec = (reinterpret_cast<uintptr_t>(lw) & 15u) == 0;
   const int t = blockIdx.x;
   const V Pt = load_v<V>(P_rec + t), Pn = load_v<V>(P_rec + t + 1);
-  int32_t O[kRows][4];
-#pragma unroll
-  for (int r = 0; r < kRows; ++r)
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const V W = vclamp(vadd(Pt, val[r][q]), Pt, Pn);
-      O[r][q] = cum_offspring<T, V, STRAT>(W, S, scale, u_sys, keys, N);
-    }
-  // cumulative offspring just before this warp's first element
-  int32_t Obefore = 0;
-  if (lane == 0) {
-    if (warp > 0) {
-      const V W = vclamp(vadd(Pt, prevmax), Pt, Pn);
-      Obefore = cum_offspring<T, V, STRAT>(W, S, scale, u_sys, keys, N);
-    } else if (t > 0) {
-      const V Pm = load_v<V>(P_rec + t - 1), sm = load_v<V>(s_rec + t - 1);
-      const V W = vclamp(vadd(Pm, sm), Pm, Pt);
-      Obefore = cum_offspring<T, V, STRAT>(W, S, scale, u_sys, keys, N);
-    }
-  }
-#pragma unroll
-  for (int r = 0; r < kRows; ++r) {
-    int32_t prev = __shfl_up_sync(0xffffffffu, O[r][3], 1);
-    if (r > 0) {
-      const int32_t rowprev = __shfl_sync(0xffffffffu, O[r - 1][3], 31);
-      if (lane == 0) prev = rowprev;
-    } else if (lane == 0) {
-      prev = Obefore;
-    }
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int64_t i = base + tile_offset(warp, r, lane, q);
-      int32_t Oc = O[r][q];
-      if (i == N - 1) Oc = static_cast<int32_t>(N);
-      if (i < N) {
-        for (int32_t j = prev; j < Oc; ++j) a[j] = static_cast<int32_t>(i);
-        if (d) d[i] = (Oc > prev) ? prev : static_cast<int32_t>(N);
-      }
-      prev = Oc;
-    }
-  }
+  const V Pm = t > 0 ? load_v<V>(P_rec + t - 1) : vzero(V());
+  const V sm = t > 0 ? load_v<V>(s_rec + t - 1) : vzero(V());
+  emit_tile_cumoff<T, V, STRAT>(lw, 0, N, base, wc, vec, Pt, Pn, t > 0, Pm, sm,
+                                load_v<V>(&g->S_raw), load_v<V>(&g->scale_raw), keys, a, d,
+                                sh_tot, sh_max);
 }
 
 // ---------------------------------------------------------------------------------------
 // Pass 3b: stored cumulative weights (multinomial search input, or rs_cumulative_weights
-// output converted to the element type).
+// output converted to the element type), one tile per CTA.
 // ---------------------------------------------------------------------------------------
-template <typename V, typename OUT> __device__ __forceinline__ OUT convert_out(V v);
-template <> __device__ __forceinline__ float convert_out<float, float>(float v) { return v; }
-template <> __device__ __forceinline__ double convert_out<double, double>(double v) { return v; }
-template <> __device__ __forceinline__ float2 convert_out<float2, float2>(float2 v) { return v; }
-template <> __device__ __forceinline__ float convert_out<float2, float>(float2 v) { return v.x; }
-template <> __device__ __forceinline__ double convert_out<float2, double>(float2 v) {
-  return vto_double(v);
-}
-
 template <typename T, typename V, typename OUT>
 __global__ void __launch_bounds__(kBlock)
 emit_W_kernel(const T* __restrict__ lw, int64_t N, const ScanGlob* g, const double2* P_rec,
@@ -561,37 +209,22 @@ emit_W_kernel(const T* __restrict__ lw, int64_t N, const ScanGlob* g, const doub
   __shared__ V sh_max[kWarps];
   __shared__ float2 sh_tab[64];
   const int64_t base = static_cast<int64_t>(blockIdx.x) * kTile;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const double Md = g->M;
   if (!(Md > -DBL_MAX) || !(g->S_d > 0.0)) {
-    for (int r = 0; r < kRows; ++r)
-      for (int q = 0; q < 4; ++q) {
-        const int64_t i = base + tile_offset(warp, r, lane, q);
-        if (i < N) Wout[i] = convert_out<V, OUT>(vzero(V()));
-      }
+    for (int64_t i = base + threadIdx.x; i < N && i < base + kTile; i += kBlock)
+      Wout[i] = convert_out<V, OUT>(vzero(V()));
     return;
   }
   const WeightCtx wc = make_ctx<T, V>(Md, sh_tab);
-  const bool vec = ((reinterpret_cast<uintptr_t>(lw) & 15u) == 0) && (base + kTile <= N);
-  V val[kRows][4];
-  tile_raw_values<T, V>(lw, N, base, wc, vec, val, sh_tot);
-  V prevmax;
-  tile_running_max<V>(val, base, N, sh_max, prevmax);
+  const bool vec = (reinterpret_cast<uintptr_t>(lw) & 15u) == 0;
   const int t = blockIdx.x;
-  const V Pt = load_v<V>(P_rec + t), Pn = load_v<V>(P_rec + t + 1);
-#pragma unroll
-  for (int r = 0; r < kRows; ++r)
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int64_t i = base + tile_offset(warp, r, lane, q);
-      if (i < N) Wout[i] = convert_out<V, OUT>(vclamp(vadd(Pt, val[r][q]), Pt, Pn));
-    }
+  emit_tile_W<T, V, OUT>(lw, 0, N, base, wc, vec, load_v<V>(P_rec + t), load_v<V>(P_rec + t + 1),
+                         Wout, sh_tot, sh_max);
 }
 
 // ---------------------------------------------------------------------------------------
-// Multinomial search (Code 5): u_i = U_i * W^N with U_i from counter (i, 0); a_i = the first
-// j with W_j > u_i (the particle whose half-open interval holds u_i); then the Prepermute
-// claim atomicMin(d[a_i], i) when d is given.
+// Multinomial search (Code 5), one particle per thread, with the Prepermute claim
+// atomicMin(d[a_i], i) when d is given.
 // ---------------------------------------------------------------------------------------
 template <typename T, typename V>
 __global__ void __launch_bounds__(kBlock)
@@ -604,15 +237,7 @@ search_kernel(const V* __restrict__ W, int64_t N, const ScanGlob* g, Keys keys,
     if (d) atomicMin(d + i, static_cast<int32_t>(i));
     return;
   }
-  const V S = W[N - 1];
-  const auto U = Path<T, V>::draw_u(draw(keys, static_cast<uint32_t>(i), 0u));
-  const V u = vtimes_u(S, U);
-  int64_t lo = 0, hi = N;
-  while (lo < hi) {
-    const int64_t mid = lo + ((hi - lo) >> 1);
-    if (vle(W[mid], u)) lo = mid + 1; else hi = mid;
-  }
-  const int32_t k = static_cast<int32_t>(lo < N ? lo : N - 1);
+  const int32_t k = search_one<T, V>(W, N, keys, i);
   a[i] = k;
   if (d) atomicMin(d + k, static_cast<int32_t>(i));
 }

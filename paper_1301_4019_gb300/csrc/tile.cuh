@@ -1,0 +1,442 @@
+// tile.cuh -- the tile scan shared by the single-filter and batched scan-based resamplers:
+// weights per (input type, accumulator type), the 4096-particle tile prefix sum with its
+// exact running maximum, and the cumulative offspring of Codes 7 and 8.
+#pragma once
+
+#include <cfloat>
+#include <cstdint>
+
+#include "common.cuh"
+#include "dfexp.cuh"
+#include "values.cuh"
+
+namespace rsk {
+namespace {
+
+// ---------------------------------------------------------------------------------------
+// Weights and uniforms per (input type, accumulator type)
+// ---------------------------------------------------------------------------------------
+struct WeightCtx {
+  double Md;          // maximum log-weight
+  float Mf;           // as binary32 (binary32 inputs: exact)
+  float2 M2;          // as two-float (double-float path)
+  const float2* tab;  // 2^(j/64) table in shared memory (double-float path)
+};
+
+template <typename T, typename V> struct Path;
+template <> struct Path<float, float> {
+  using U = float;
+  static constexpr int id = 0;
+  static constexpr bool kTable = false;
+  __device__ static float weight(float x, const WeightCtx& c) {
+    return (x == neg_inf<float>()) ? 0.0f : exp_pinned(__fsub_rn(x, c.Mf));
+  }
+  __device__ static U draw_u(uint4 x) { return u01_f32(x); }
+};
+template <> struct Path<float, float2> {
+  using U = float;
+  static constexpr int id = 1;
+  static constexpr bool kTable = false;
+  __device__ static float2 weight(float x, const WeightCtx& c) {
+    return make_float2((x == neg_inf<float>()) ? 0.0f : exp_pinned(__fsub_rn(x, c.Mf)), 0.0f);
+  }
+  __device__ static U draw_u(uint4 x) { return u01_f32(x); }
+};
+template <> struct Path<double, float2> {
+  using U = float2;
+  static constexpr int id = 2;
+  static constexpr bool kTable = true;
+  __device__ static float2 weight(double x, const WeightCtx& c) {
+    if (x == neg_inf<double>()) return make_float2(0.0f, 0.0f);
+    return exp_df(add22_accurate(split_f64(x), neg2(c.M2)), c.tab);
+  }
+  __device__ static U draw_u(uint4 x) { return u01_f2(x); }
+};
+template <> struct Path<double, double> {
+  using U = double;
+  static constexpr int id = 3;
+  static constexpr bool kTable = false;
+  __device__ static double weight(double x, const WeightCtx& c) {
+    return (x == neg_inf<double>()) ? 0.0 : exp_pinned(__dsub_rn(x, c.Md));
+  }
+  __device__ static U draw_u(uint4 x) { return u01_f64(x); }
+};
+
+// Builds the weight context (and stages the exp table in shared memory when needed).
+template <typename T, typename V>
+__device__ __forceinline__ WeightCtx make_ctx(double Md, float2* sh_tab) {
+  WeightCtx c;
+  c.Md = Md;
+  c.Mf = static_cast<float>(Md);
+  c.M2 = split_f64(Md);
+  c.tab = sh_tab;
+  if constexpr (Path<T, V>::kTable) {
+    if (threadIdx.x < 64) sh_tab[threadIdx.x] = kExp2Frac64[threadIdx.x];
+    __syncthreads();
+  }
+  return c;
+}
+
+// Reads the 4 consecutive log-weights idx..idx+3; positions outside [lo, N) read as -inf.
+// `vec` says the base pointer is 16-byte aligned; the 128-bit path is taken when all four
+// positions are inside and the first is 16-byte aligned, else four guarded scalar loads.
+template <typename T>
+__device__ __forceinline__ void load4(const T* __restrict__ lw, int64_t idx, int64_t lo,
+                                      int64_t N, bool vec, T (&x)[4]) {
+  constexpr int64_t kAlign = sizeof(T) == 4 ? 3 : 1;  // 16-byte alignment of the first load
+  if (vec && idx >= lo && idx + 4 <= N && (idx & kAlign) == 0) {
+    if constexpr (sizeof(T) == 4) {
+      const float4 v = __ldg(reinterpret_cast<const float4*>(lw + idx));
+      x[0] = v.x; x[1] = v.y; x[2] = v.z; x[3] = v.w;
+    } else {
+      const double2 v0 = __ldg(reinterpret_cast<const double2*>(lw + idx));
+      const double2 v1 = __ldg(reinterpret_cast<const double2*>(lw + idx + 2));
+      x[0] = v0.x; x[1] = v0.y; x[2] = v1.x; x[3] = v1.y;
+    }
+  } else {
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+      x[q] = (idx + q >= lo && idx + q < N) ? lw[idx + q] : neg_inf<T>();
+  }
+}
+
+template <typename V> __device__ __forceinline__ V load_v(const double2* p) {
+  return *reinterpret_cast<const V*>(p);
+}
+template <typename V> __device__ __forceinline__ void store_v(double2* p, V v) {
+  *reinterpret_cast<V*>(p) = v;
+}
+template <typename V> __device__ __forceinline__ V load_v_cg(const double2* p);
+template <> __device__ __forceinline__ float load_v_cg<float>(const double2* p) {
+  return __ldcg(reinterpret_cast<const float*>(p));
+}
+template <> __device__ __forceinline__ double load_v_cg<double>(const double2* p) {
+  return __ldcg(reinterpret_cast<const double*>(p));
+}
+template <> __device__ __forceinline__ float2 load_v_cg<float2>(const double2* p) {
+  return __ldcg(reinterpret_cast<const float2*>(p));
+}
+
+// Element e of the tile owned by (warp, row, lane, q): warp*512 + row*128 + lane*4 + q.
+__device__ __forceinline__ int tile_offset(int warp, int r, int lane, int q) {
+  return warp * 512 + r * 128 + lane * 4 + q;
+}
+
+// The tile scan shared by the tile-sum and emit passes: val[r][q] = sum of the weights of
+// the tile up to and including the element (r, q) of this thread, as computed by a fixed
+// tree: sequential inside a lane, Hillis-Steele across the 32 lanes of a row, a running
+// carry across the 4 rows of a warp, and a sequential prefix over the 8 warps. Elements
+// outside [lo, N) have weight 0. All four rows are loaded before any arithmetic.
+template <typename T, typename V>
+__device__ __forceinline__ void tile_raw_values(const T* __restrict__ lw, int64_t lo, int64_t N,
+                                                int64_t base, const WeightCtx& wc, bool vec,
+                                                V (&val)[kRows][4], V* sh_tot) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  T x[kRows][4];
+#pragma unroll
+  for (int r = 0; r < kRows; ++r)
+    load4(lw, base + tile_offset(warp, r, lane, 0), lo, N, vec, x[r]);
+  V carry = vzero(V());
+#pragma unroll
+  for (int r = 0; r < kRows; ++r) {
+    V loc[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const V wv = vfrom_w(Path<T, V>::weight(x[r][q], wc), V());
+      loc[q] = (q == 0) ? wv : vadd(loc[q - 1], wv);
+    }
+    V incl = loc[3];
+#pragma unroll
+    for (int dd = 1; dd < 32; dd <<= 1) {
+      const V y = vshfl_up(incl, dd);
+      if (lane >= dd) incl = vadd(y, incl);
+    }
+    V excl = vshfl_up(incl, 1);
+    if (lane == 0) excl = vzero(V());
+    const V rowtot = vshfl(incl, 31);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) val[r][q] = vadd(carry, vadd(excl, loc[q]));
+    carry = vadd(carry, rowtot);
+  }
+  if (lane == 0) sh_tot[warp] = carry;
+  __syncthreads();
+  V pw = vzero(V());
+  for (int k = 0; k < warp; ++k) pw = vadd(pw, sh_tot[k]);
+#pragma unroll
+  for (int r = 0; r < kRows; ++r)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) val[r][q] = vadd(pw, val[r][q]);
+}
+
+// Running maximum of the tile values in element order (exact), restricted to positions in
+// [lo, N) (other positions keep their raw value and are never used). Returns, through sh_max, the
+// maximum of each warp's valid values; prevmax = maximum over the previous warps.
+template <typename V>
+__device__ __forceinline__ void tile_running_max(V (&val)[kRows][4], int64_t base, int64_t lo,
+                                                 int64_t N, V* sh_max, V& prevmax) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  V cm = vzero(V());
+#pragma unroll
+  for (int r = 0; r < kRows; ++r) {
+    V x[4];
+    V m = vzero(V());
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int64_t e = base + tile_offset(warp, r, lane, q);
+      const bool valid = e >= lo && e < N;
+      if (valid) m = vmax(m, val[r][q]);
+      x[q] = m;
+    }
+    V im = m;
+#pragma unroll
+    for (int dd = 1; dd < 32; dd <<= 1) {
+      const V y = vshfl_up(im, dd);
+      if (lane >= dd) im = vmax(y, im);
+    }
+    V em = vshfl_up(im, 1);
+    if (lane == 0) em = vzero(V());
+    const V before = vmax(em, cm);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int64_t e = base + tile_offset(warp, r, lane, q);
+      const bool valid = e >= lo && e < N;
+      if (valid) val[r][q] = vmax(x[q], before);
+    }
+    cm = vmax(cm, vshfl(im, 31));
+  }
+  if (lane == 0) sh_max[warp] = cm;
+  __syncthreads();
+  prevmax = vzero(V());
+  for (int k = 0; k < warp; ++k) prevmax = vmax(prevmax, sh_max[k]);
+#pragma unroll
+  for (int r = 0; r < kRows; ++r)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int64_t e = base + tile_offset(warp, r, lane, q);
+      const bool valid = e >= lo && e < N;
+      if (valid) val[r][q] = vmax(val[r][q], prevmax);
+    }
+}
+
+// Cumulative offspring of a cumulative weight W (Codes 7 and 8 with r = W * N / W^N).
+template <typename T, typename V, bool STRAT>
+__device__ __forceinline__ int32_t cum_offspring(V W, V S, V scale,
+                                                 typename Path<T, V>::U u_sys,
+                                                 const Keys& keys, int64_t N) {
+  if (veq(W, S)) return static_cast<int32_t>(N);
+  const V r = vscale(W, scale);
+  int64_t o;
+  if constexpr (STRAT) {
+    int64_t k = floor_to_i64(r);
+    k = k < N - 1 ? k : N - 1;
+    const auto uk = Path<T, V>::draw_u(draw(keys, static_cast<uint32_t>(k), 0u));
+    o = floor_to_i64(vplus_u(r, uk));
+    o = o < k + 1 ? o : k + 1;
+  } else {
+    o = floor_to_i64(vplus_u(r, u_sys));
+  }
+  o = o < N ? o : N;
+  o = o > 0 ? o : 0;
+  return static_cast<int32_t>(o);
+}
+
+// Totals of one sequence of tiles (block-level, every thread of the CTA calls it):
+// P_0 = 0, P_{t+1} = P_t + s_t in binary64 over T tile totals s_t (each thread sums a
+// contiguous chunk, then a warp and a warp-sequential scan), made monotone by a running
+// maximum and rounded monotonically to the accumulator type. The total S is the cumulative
+// weight of the last particle exactly as the emit pass computes it,
+// clamp(P_{T-1} + s_{T-1}, P_{T-1}, P_T), so that particle receives O = N. Thread 0 writes
+// S, N / S and S (binary64) to the given pointers, then the CTA synchronises.
+template <typename V>
+__device__ void tile_prefix_compute(const double2* s_rec, double2* P_rec, int T, int64_t N,
+                                    V* S_out, V* scale_out, double* Sd_out) {
+  __shared__ double sh_sum[kWarps];
+  __shared__ double sh_max[kWarps];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int chunk = (T + kBlock - 1) / kBlock;
+  const int t0 = min(T, tid * chunk), t1 = min(T, t0 + chunk);
+  double local = 0.0;
+  for (int t = t0; t < t1; ++t) local = __dadd_rn(local, vto_double(load_v_cg<V>(s_rec + t)));
+  double incl = local;
+#pragma unroll
+  for (int dd = 1; dd < 32; dd <<= 1) {
+    const double y = __shfl_up_sync(0xffffffffu, incl, dd);
+    if (lane >= dd) incl = __dadd_rn(y, incl);
+  }
+  double excl = __shfl_up_sync(0xffffffffu, incl, 1);
+  if (lane == 0) excl = 0.0;
+  if (lane == 31) sh_sum[warp] = incl;
+  __syncthreads();
+  double wp = 0.0;
+  for (int k = 0; k < warp; ++k) wp = __dadd_rn(wp, sh_sum[k]);
+  const double start = __dadd_rn(wp, excl);
+  double endv = start;  // end value of this thread's chunk, for the running maximum
+  for (int t = t0; t < t1; ++t) endv = __dadd_rn(endv, vto_double(load_v_cg<V>(s_rec + t)));
+  double im = endv;
+#pragma unroll
+  for (int dd = 1; dd < 32; dd <<= 1) {
+    const double y = __shfl_up_sync(0xffffffffu, im, dd);
+    if (lane >= dd) im = y > im ? y : im;
+  }
+  double em = __shfl_up_sync(0xffffffffu, im, 1);
+  if (lane == 0) em = 0.0;
+  if (lane == 31) sh_max[warp] = im;
+  __syncthreads();
+  double prevmax = em;
+  for (int k = 0; k < warp; ++k) prevmax = sh_max[k] > prevmax ? sh_max[k] : prevmax;
+  double p = start;
+  for (int t = t0; t < t1; ++t) {
+    store_v<V>(P_rec + t, vfrom_double(p > prevmax ? p : prevmax, V()));
+    p = __dadd_rn(p, vto_double(load_v_cg<V>(s_rec + t)));
+  }
+  if (t1 == T && t0 < T) store_v<V>(P_rec + T, vfrom_double(p > prevmax ? p : prevmax, V()));
+  __syncthreads();
+  if (tid == 0) {
+    const V Pm = load_v_cg<V>(P_rec + (T - 1));
+    const V Pn = load_v_cg<V>(P_rec + T);
+    const V st = load_v_cg<V>(s_rec + (T - 1));
+    const V S = vclamp(vadd(Pm, st), Pm, Pn);
+    const double Sd = vto_double(S);
+    *S_out = S;
+    *scale_out = vfrom_double(__ddiv_rn(static_cast<double>(N), Sd), V());
+    *Sd_out = Sd;
+  }
+  __syncthreads();
+}
+
+// The tile total (block-level): maximum of the tile values over valid positions, which is
+// also the value of the tile's last valid particle after the running maximum.
+template <typename V>
+__device__ __forceinline__ V tile_total(const V (&val)[kRows][4], int64_t base, int64_t lo,
+                                        int64_t N, V* sh_max) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  V m = vzero(V());
+#pragma unroll
+  for (int r = 0; r < kRows; ++r)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int64_t e = base + tile_offset(warp, r, lane, q);
+      if (e >= lo && e < N) m = vmax(m, val[r][q]);
+    }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = vmax(m, vshfl_xor(m, o));
+  __syncthreads();
+  if (lane == 0) sh_max[warp] = m;
+  __syncthreads();
+  V tm = vzero(V());
+  for (int k = 0; k < kWarps; ++k) tm = vmax(tm, sh_max[k]);
+  return tm;
+}
+
+// Systematic / stratified emission of one tile starting at `base` of the sequence [lo, N)
+// (block-level): cumulative offspring O of every particle, the Code-11 scatter of local
+// ancestor indices into a[lo + j] and, when d is given, the Prepermute claims
+// d[lo + i] = O_{i-1} if particle i has offspring, else n (for a non-decreasing ancestry
+// the lowest claimant of slot i is the first position of its run). Pt, Pn: prefixes of this
+// tile; Pm, sm: prefix and total of the previous tile (has_prev false for the first tile).
+template <typename T, typename V, bool STRAT>
+__device__ __forceinline__ void emit_tile_cumoff(const T* __restrict__ lw, int64_t lo, int64_t N,
+                                                 int64_t base, const WeightCtx& wc, bool vec,
+                                                 V Pt, V Pn, bool has_prev, V Pm, V sm, V S,
+                                                 V scale, const Keys& keys,
+                                                 int32_t* __restrict__ a,
+                                                 int32_t* __restrict__ d, V* sh_tot, V* sh_max) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t n = N - lo;
+  using U = typename Path<T, V>::U;
+  const U u_sys = Path<T, V>::draw_u(draw(keys, 0u, 0u));
+  V val[kRows][4];
+  tile_raw_values<T, V>(lw, lo, N, base, wc, vec, val, sh_tot);
+  V prevmax;
+  tile_running_max<V>(val, base, lo, N, sh_max, prevmax);
+  int32_t O[kRows][4];
+#pragma unroll
+  for (int r = 0; r < kRows; ++r)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const V W = vclamp(vadd(Pt, val[r][q]), Pt, Pn);
+      O[r][q] = cum_offspring<T, V, STRAT>(W, S, scale, u_sys, keys, n);
+    }
+  // cumulative offspring just before this warp's first element
+  int32_t Obefore = 0;
+  if (lane == 0) {
+    if (warp > 0) {
+      const V W = vclamp(vadd(Pt, prevmax), Pt, Pn);
+      Obefore = cum_offspring<T, V, STRAT>(W, S, scale, u_sys, keys, n);
+    } else if (has_prev) {
+      const V W = vclamp(vadd(Pm, sm), Pm, Pt);
+      Obefore = cum_offspring<T, V, STRAT>(W, S, scale, u_sys, keys, n);
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < kRows; ++r) {
+    int32_t prev = __shfl_up_sync(0xffffffffu, O[r][3], 1);
+    if (r > 0) {
+      const int32_t rowprev = __shfl_sync(0xffffffffu, O[r - 1][3], 31);
+      if (lane == 0) prev = rowprev;
+    } else if (lane == 0) {
+      prev = Obefore;
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int64_t e = base + tile_offset(warp, r, lane, q);
+      const int64_t i = e - lo;
+      int32_t Oc = O[r][q];
+      if (i == n - 1) Oc = static_cast<int32_t>(n);
+      if (e >= lo && e < N) {
+        for (int32_t j = prev; j < Oc; ++j) a[lo + j] = static_cast<int32_t>(i);
+        if (d) d[lo + i] = (Oc > prev) ? prev : static_cast<int32_t>(n);
+      }
+      prev = Oc;
+    }
+  }
+}
+
+// Stored cumulative weights of one tile (block-level): W[e] for e in [lo, N).
+template <typename V, typename OUT> __device__ __forceinline__ OUT convert_out(V v);
+template <> __device__ __forceinline__ float convert_out<float, float>(float v) { return v; }
+template <> __device__ __forceinline__ double convert_out<double, double>(double v) { return v; }
+template <> __device__ __forceinline__ float2 convert_out<float2, float2>(float2 v) { return v; }
+template <> __device__ __forceinline__ float convert_out<float2, float>(float2 v) { return v.x; }
+template <> __device__ __forceinline__ double convert_out<float2, double>(float2 v) {
+  return vto_double(v);
+}
+
+template <typename T, typename V, typename OUT>
+__device__ __forceinline__ void emit_tile_W(const T* __restrict__ lw, int64_t lo, int64_t N,
+                                            int64_t base, const WeightCtx& wc, bool vec, V Pt,
+                                            V Pn, OUT* __restrict__ Wout, V* sh_tot,
+                                            V* sh_max) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  V val[kRows][4];
+  tile_raw_values<T, V>(lw, lo, N, base, wc, vec, val, sh_tot);
+  V prevmax;
+  tile_running_max<V>(val, base, lo, N, sh_max, prevmax);
+#pragma unroll
+  for (int r = 0; r < kRows; ++r)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int64_t e = base + tile_offset(warp, r, lane, q);
+      if (e >= lo && e < N) Wout[e] = convert_out<V, OUT>(vclamp(vadd(Pt, val[r][q]), Pt, Pn));
+    }
+}
+
+// Multinomial search (Code 5) for output i of a sequence of n cumulative weights W: u =
+// U_i * W^N with U_i from counter (i, 0); the first j with W_j > u (the particle whose
+// half-open interval holds u).
+template <typename T, typename V>
+__device__ __forceinline__ int32_t search_one(const V* __restrict__ W, int64_t n,
+                                              const Keys& keys, int64_t i) {
+  const V S = W[n - 1];
+  const auto U = Path<T, V>::draw_u(draw(keys, static_cast<uint32_t>(i), 0u));
+  const V u = vtimes_u(S, U);
+  int64_t lo = 0, hi = n;
+  while (lo < hi) {
+    const int64_t mid = lo + ((hi - lo) >> 1);
+    if (vle(W[mid], u)) lo = mid + 1; else hi = mid;
+  }
+  return static_cast<int32_t>(lo < n ? lo : n - 1);
+}
+
+}  // namespace
+}  // namespace rsk
