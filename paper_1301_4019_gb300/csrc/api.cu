@@ -56,6 +56,7 @@ void free_scratch(rsk::Scratch& s) {
   cudaFree(s.d);
   cudaFree(s.a_tmp);
   cudaFree(s.W);
+  cudaFree(s.guide);
   cudaFree(s.rec);
   cudaFree(s.blockmax);
   cudaFree(s.irec);
@@ -91,6 +92,7 @@ int rs_create(rs_handle** out, int64_t max_n, int device) {
   ok &= cudaMalloc(&s.d, sizeof(int32_t) * max_n) == cudaSuccess;
   ok &= cudaMalloc(&s.a_tmp, sizeof(int32_t) * max_n) == cudaSuccess;
   ok &= cudaMalloc(&s.W, 8 * static_cast<size_t>(max_n)) == cudaSuccess;
+  ok &= cudaMalloc(&s.guide, sizeof(int32_t) * (max_n + 1)) == cudaSuccess;
   ok &= cudaMalloc(&s.rec, sizeof(double2) * 2 * (s.max_tiles + 2)) == cudaSuccess;
   ok &= cudaMalloc(&s.blockmax, sizeof(double) * s.max_blocks) == cudaSuccess;
   ok &= cudaMalloc(&s.irec, sizeof(long long) * 2 * (s.max_tiles + 2)) == cudaSuccess;

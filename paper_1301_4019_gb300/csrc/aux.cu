@@ -8,10 +8,18 @@
 namespace rsk {
 namespace {
 
+// p[0..N) = v with 128-bit stores where p is 16-byte aligned.
 __global__ void __launch_bounds__(kBlock) fill_kernel(int32_t* __restrict__ p, int64_t N, int32_t v) {
   const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
-  for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < N; i += stride)
-    p[i] = v;
+  const int64_t t0 = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  const int64_t head = ((16 - (reinterpret_cast<uintptr_t>(p) & 15u)) & 15u) / 4;  // to alignment
+  const int64_t h = head < N ? head : N;
+  for (int64_t i = t0; i < h; i += stride) p[i] = v;
+  int4* q = reinterpret_cast<int4*>(p + h);
+  const int64_t nv = (N - h) / 4;
+  const int4 vv = make_int4(v, v, v, v);
+  for (int64_t i = t0; i < nv; i += stride) q[i] = vv;
+  for (int64_t i = h + 4 * nv + t0; i < N; i += stride) p[i] = v;
 }
 
 // Prepermute: d[a_i] = min(d[a_i], i) (d initialised to the sentinel N beforehand).
@@ -165,7 +173,8 @@ inline int grid_for(int64_t N) { return static_cast<int>((N + kBlock - 1) / kBlo
 }  // namespace
 
 cudaError_t launch_fill(int32_t* p, int64_t N, int32_t v, cudaStream_t st) {
-  int64_t g = (N + kBlock - 1) / kBlock;
+  int64_t g = (N / 4 + kBlock - 1) / kBlock;
+  if (g < 1) g = 1;
   if (g > 152 * 16) g = 152 * 16;
   fill_kernel<<<static_cast<int>(g), kBlock, 0, st>>>(p, N, v);
   return cudaGetLastError();

@@ -231,7 +231,7 @@ __global__ void __launch_bounds__(kBlock) batch_prefix_kernel(Batch b) {
 
 template <typename T, typename V, int SCHEME>
 __global__ void __launch_bounds__(kBlock)
-batch_emit_kernel(const T* __restrict__ lw, Batch b, uint64_t seed, uint64_t step,
+batch_emit_kernel(const T* __restrict__ lw, Batch b, Keys base_keys,
                   int32_t* __restrict__ a, int32_t* __restrict__ d, V* __restrict__ W) {
   __shared__ V sh_tot[kWarps];
   __shared__ V sh_max[kWarps];
@@ -260,7 +260,7 @@ batch_emit_kernel(const T* __restrict__ lw, Batch b, uint64_t seed, uint64_t ste
         d[e] = static_cast<int32_t>(n);
     emit_tile_W<T, V, V>(lw, L.lo, L.hi, L.base, wc, vec, Pt, Pn, W, sh_tot, sh_max);
   } else {
-    const Keys keys = make_keys(seed, step, static_cast<uint32_t>(L.f), SCHEME);
+    const Keys keys = with_tag(base_keys, static_cast<uint32_t>(L.f), SCHEME);
     const V Pm = L.t > 0 ? load_v_cg<V>(P + L.t - 1) : vzero(V());
     const V sm = L.t > 0 ? load_v_cg<V>(s + L.t - 1) : vzero(V());
     emit_tile_cumoff<T, V, SCHEME == RS_STRATIFIED>(
@@ -271,13 +271,13 @@ batch_emit_kernel(const T* __restrict__ lw, Batch b, uint64_t seed, uint64_t ste
 
 template <typename T, typename V>
 __global__ void __launch_bounds__(kBlock)
-batch_search_kernel(const V* __restrict__ W, Batch b, int64_t total, uint64_t seed,
-                    uint64_t step, int32_t* __restrict__ a, int32_t* __restrict__ d) {
+batch_search_kernel(const V* __restrict__ W, Batch b, int64_t total, Keys base_keys,
+                    int32_t* __restrict__ a, int32_t* __restrict__ d) {
   const int64_t g = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
   PartLoc P;
   if (g >= total || !locate_particle(b.off, b.F, b.max_n, g, P)) return;
   if (!(__ldcg(b.fSd + P.f) > 0.0) || !(filter_M(b, P.f) > -DBL_MAX)) return;  // identity
-  const Keys keys = make_keys(seed, step, static_cast<uint32_t>(P.f), RS_MULTINOMIAL);
+  const Keys keys = with_tag(base_keys, static_cast<uint32_t>(P.f), RS_MULTINOMIAL);
   const int32_t k = search_one<T, V>(W + P.lo, P.n, keys, P.i);
   a[g] = k;
   if (d) atomicMin(d + P.lo + k, static_cast<int32_t>(P.i));
@@ -297,7 +297,7 @@ template <typename T>
 __global__ void __launch_bounds__(kBlock)
 batch_mcmc_kernel(const T* __restrict__ lw, const int64_t* __restrict__ off, int F,
                   int64_t total, int scheme, const int32_t* __restrict__ Bf, int32_t B,
-                  uint64_t seed, uint64_t step, double log_wmax, int64_t max_trials,
+                  Keys base_keys, double log_wmax, int64_t max_trials,
                   int32_t* __restrict__ a, int32_t* __restrict__ d, int* err) {
   const int64_t g = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
   PartLoc P;
@@ -313,14 +313,75 @@ batch_mcmc_kernel(const T* __restrict__ lw, const int64_t* __restrict__ off, int
       flag_error(err, RS_ERR_ARG);
       Bv = 0;
     }
-    const Keys keys = make_keys(seed, step, static_cast<uint32_t>(P.f), RS_METROPOLIS);
+    const Keys keys = with_tag(base_keys, static_cast<uint32_t>(P.f), RS_METROPOLIS);
     k = metropolis_one(lw + P.lo, P.n, Bv, keys, P.i, err);
   } else {
-    const Keys keys = make_keys(seed, step, static_cast<uint32_t>(P.f), RS_REJECTION);
+    const Keys keys = with_tag(base_keys, static_cast<uint32_t>(P.f), RS_REJECTION);
     k = rejection_one(lw + P.lo, P.n, log_wmax, max_trials, keys, P.i, err);
   }
   a[g] = k;
   if (d) atomicMin(d + P.lo + k, static_cast<int32_t>(P.i));
+}
+
+// Rejection with warp refill over the particles of all filters (mcmc.cuh); a lane looks up
+// the filter of every particle it takes.
+template <typename T>
+__global__ void __launch_bounds__(kBlock)
+batch_rejection_kernel(const T* __restrict__ lw, const int64_t* __restrict__ off, int F,
+                       int64_t total, Keys base_keys, double log_wmax, int64_t max_trials,
+                       int32_t* __restrict__ a, int32_t* __restrict__ d, int* err) {
+  const int lane = threadIdx.x & 31;
+  const int64_t run = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+  const int64_t start = run * kRejRun;
+  const int64_t limit = __ldg(off + F) < total ? __ldg(off + F) : total;
+  if (start >= limit) return;  // uniform across the warp
+  const int64_t end = start + kRejRun < limit ? start + kRejRun : limit;
+  const RejBound rb = make_bound(log_wmax);
+  int64_t g = start + lane;
+  bool active = false;
+  PartLoc P;
+  Keys keys = base_keys;
+  T lwi = T(0);
+  auto take = [&](int64_t gg) {
+    g = gg;
+    active = false;
+    if (gg >= end) return;
+    if (!locate_particle(off, F, total, gg, P)) {
+      flag_error(err, RS_ERR_ARG);
+      return;
+    }
+    active = true;
+    keys = with_tag(base_keys, static_cast<uint32_t>(P.f), RS_REJECTION);
+    lwi = __ldg(lw + gg);
+    if (nonfinite_logw(lwi)) flag_error(err, RS_ERR_NONFINITE);
+  };
+  take(g);
+  int64_t head = start + 32;
+  uint32_t s = 0;
+  for (;;) {
+    bool settled = false;
+    if (active) {
+      int64_t j;
+      settled = rejection_attempt(lw + P.lo, P.n, rb, keys, P.i, s, lwi, j, err);
+      ++s;
+      if (!settled && s >= static_cast<uint64_t>(max_trials)) {
+        flag_error(err, RS_ERR_REJECTION_CAP);
+        j = P.i;
+        settled = true;
+      }
+      if (settled) {
+        a[g] = static_cast<int32_t>(j);
+        if (d) atomicMin(d + P.lo + j, static_cast<int32_t>(P.i));
+      }
+    }
+    const unsigned done = __ballot_sync(0xffffffffu, settled);
+    if (settled) {
+      take(head + __popc(done & ((1u << lane) - 1u)));
+      s = 0;
+    }
+    head += __popc(done);
+    if (!__any_sync(0xffffffffu, active)) break;
+  }
 }
 
 __global__ void __launch_bounds__(kBlock)
@@ -345,8 +406,8 @@ const char* const kLblSearch[4] = {"batch_search_f32", "batch_search_f32c", "bat
 
 template <typename T, typename V>
 cudaError_t run_batched_scan(const Scratch& s, int scheme, const T* lw, const Batch& b,
-                             int64_t cap_tiles, uint64_t seed, uint64_t step, int32_t* a,
-                             int32_t* d, cudaStream_t st) {
+                             int64_t cap_tiles, const Keys& keys, int32_t* a, int32_t* d,
+                             cudaStream_t st) {
   constexpr int ai = Path<T, V>::id;
   const int tiles = static_cast<int>(cap_tiles);
   trace_mark(s.trace, "batch_max", st);
@@ -359,18 +420,16 @@ cudaError_t run_batched_scan(const Scratch& s, int scheme, const T* lw, const Ba
   trace_mark(s.trace, kLblEmit[ai], st);
   switch (scheme) {
     case RS_MULTINOMIAL:
-      batch_emit_kernel<T, V, RS_MULTINOMIAL><<<tiles, kBlock, 0, st>>>(lw, b, seed, step, a, d, W);
+      batch_emit_kernel<T, V, RS_MULTINOMIAL><<<tiles, kBlock, 0, st>>>(lw, b, keys, a, d, W);
       trace_mark(s.trace, kLblSearch[ai], st);
-      batch_search_kernel<T, V><<<grid_particles(s.max_n), kBlock, 0, st>>>(W, b, s.max_n, seed,
-                                                                            step, a, d);
+      batch_search_kernel<T, V><<<grid_particles(s.max_n), kBlock, 0, st>>>(W, b, s.max_n, keys,
+                                                                            a, d);
       break;
     case RS_STRATIFIED:
-      batch_emit_kernel<T, V, RS_STRATIFIED><<<tiles, kBlock, 0, st>>>(lw, b, seed, step, a, d,
-                                                                      nullptr);
+      batch_emit_kernel<T, V, RS_STRATIFIED><<<tiles, kBlock, 0, st>>>(lw, b, keys, a, d, nullptr);
       break;
     default:
-      batch_emit_kernel<T, V, RS_SYSTEMATIC><<<tiles, kBlock, 0, st>>>(lw, b, seed, step, a, d,
-                                                                      nullptr);
+      batch_emit_kernel<T, V, RS_SYSTEMATIC><<<tiles, kBlock, 0, st>>>(lw, b, keys, a, d, nullptr);
       break;
   }
   return cudaGetLastError();
@@ -385,6 +444,7 @@ cudaError_t launch_batched(const Scratch& s, int scheme, Acc acc, const void* lo
   int32_t* a = permute ? s.a_tmp : out;
   int32_t* d = permute ? s.d : nullptr;
   const bool f64 = acc == Acc::F64 || acc == Acc::F64N;
+  const Keys keys = make_keys(seed, step, 0u, static_cast<uint32_t>(scheme));
   // particles are bounded by the capacity; the true total is offsets[F] (checked per filter)
   const int64_t total = s.max_n;
   cudaError_t e = cudaSuccess;
@@ -396,14 +456,26 @@ cudaError_t launch_batched(const Scratch& s, int scheme, Acc acc, const void* lo
     trace_mark(s.trace, scheme == RS_METROPOLIS ? (f64 ? "batch_metropolis_f64" : "batch_metropolis_f32")
                                                 : (f64 ? "batch_rejection_f64" : "batch_rejection_f32"),
                st);
-    if (f64)
+    const int grid_runs = static_cast<int>(((total + kRejRun - 1) / kRejRun * 32 + kBlock - 1) /
+                                           kBlock);
+    if (scheme == RS_REJECTION) {
+      if (f64)
+        batch_rejection_kernel<double><<<grid_runs, kBlock, 0, st>>>(
+            static_cast<const double*>(logw), offsets, F, total, keys, log_wmax, max_trials, a,
+            d, s.err);
+      else
+        batch_rejection_kernel<float><<<grid_runs, kBlock, 0, st>>>(
+            static_cast<const float*>(logw), offsets, F, total, keys, log_wmax, max_trials, a,
+            d, s.err);
+    } else if (f64) {
       batch_mcmc_kernel<double><<<grid_particles(total), kBlock, 0, st>>>(
-          static_cast<const double*>(logw), offsets, F, total, scheme, Bf, B, seed, step,
-          log_wmax, max_trials, a, d, s.err);
-    else
+          static_cast<const double*>(logw), offsets, F, total, scheme, Bf, B, keys, log_wmax,
+          max_trials, a, d, s.err);
+    } else {
       batch_mcmc_kernel<float><<<grid_particles(total), kBlock, 0, st>>>(
-          static_cast<const float*>(logw), offsets, F, total, scheme, Bf, B, seed, step,
-          log_wmax, max_trials, a, d, s.err);
+          static_cast<const float*>(logw), offsets, F, total, scheme, Bf, B, keys, log_wmax,
+          max_trials, a, d, s.err);
+    }
   } else {
     Batch b;
     b.off = offsets;
@@ -424,19 +496,19 @@ cudaError_t launch_batched(const Scratch& s, int scheme, Acc acc, const void* lo
     switch (acc) {
       case Acc::F32:
         e = run_batched_scan<float, float>(s, scheme, static_cast<const float*>(logw), b,
-                                           cap_tiles, seed, step, a, d, st);
+                                           cap_tiles, keys, a, d, st);
         break;
       case Acc::F32C:
         e = run_batched_scan<float, float2>(s, scheme, static_cast<const float*>(logw), b,
-                                            cap_tiles, seed, step, a, d, st);
+                                            cap_tiles, keys, a, d, st);
         break;
       case Acc::F64:
         e = run_batched_scan<double, float2>(s, scheme, static_cast<const double*>(logw), b,
-                                             cap_tiles, seed, step, a, d, st);
+                                             cap_tiles, keys, a, d, st);
         break;
       case Acc::F64N:
         e = run_batched_scan<double, double>(s, scheme, static_cast<const double*>(logw), b,
-                                             cap_tiles, seed, step, a, d, st);
+                                             cap_tiles, keys, a, d, st);
         break;
     }
   }

@@ -26,38 +26,46 @@ __device__ __forceinline__ void flag_error(int* err, int status) { atomicMin(err
 // ---------------------------------------------------------------------------------------
 // Philox4x32-10 (Salmon, Moraes, Dror & Shaw, SC'11): 10 rounds of two 32x32->64 products
 // on counter words 0 and 2, xor-mixed with the other words and the round key; the key is
-// bumped by the golden-ratio and sqrt(3)-1 Weyl constants between rounds.
+// bumped by the golden-ratio and sqrt(3)-1 Weyl constants between rounds. The 10 round keys
+// depend on the seed only, so they are computed once per call (on the host) and read from
+// the kernel parameters.
 // ---------------------------------------------------------------------------------------
-__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1) {
-#pragma unroll
-  for (int round = 0; round < 10; ++round) {
-    const uint64_t p0 = static_cast<uint64_t>(0xD2511F53u) * c.x;
-    const uint64_t p1 = static_cast<uint64_t>(0xCD9E8D57u) * c.z;
-    c = make_uint4(static_cast<uint32_t>(p1 >> 32) ^ c.y ^ k0, static_cast<uint32_t>(p1),
-                   static_cast<uint32_t>(p0 >> 32) ^ c.w ^ k1, static_cast<uint32_t>(p0));
-    k0 += 0x9E3779B9u;
-    k1 += 0xBB67AE85u;
-  }
-  return c;
-}
-
 // The draw keying of the library: key = seed; counter = (index, n, step, filter*8+scheme).
 struct Keys {
-  uint32_t k0, k1;  // seed low / high word
-  uint32_t step;    // SMC step mod 2^32
-  uint32_t tag;     // filter * 8 + scheme
+  uint32_t rk0[10], rk1[10];  // round keys: seed words plus r times the Weyl constants
+  uint32_t step;              // SMC step mod 2^32
+  uint32_t tag;               // filter * 8 + scheme
 };
 __host__ __device__ inline Keys make_keys(uint64_t seed, uint64_t step, uint32_t filter,
                                           uint32_t scheme) {
   Keys k;
-  k.k0 = static_cast<uint32_t>(seed);
-  k.k1 = static_cast<uint32_t>(seed >> 32);
+  const uint32_t k0 = static_cast<uint32_t>(seed), k1 = static_cast<uint32_t>(seed >> 32);
+  for (uint32_t r = 0; r < 10; ++r) {
+    k.rk0[r] = k0 + r * 0x9E3779B9u;
+    k.rk1[r] = k1 + r * 0xBB67AE85u;
+  }
   k.step = static_cast<uint32_t>(step);
   k.tag = (filter << 3) | (scheme & 7u);
   return k;
 }
+// The same keys for another filter and scheme (the round keys do not change).
+__host__ __device__ inline Keys with_tag(const Keys& base, uint32_t filter, uint32_t scheme) {
+  Keys k = base;
+  k.tag = (filter << 3) | (scheme & 7u);
+  return k;
+}
 __device__ __forceinline__ uint4 draw(const Keys& k, uint32_t index, uint32_t n) {
-  return philox4x32_10(make_uint4(index, n, k.step, k.tag), k.k0, k.k1);
+  uint4 c = make_uint4(index, n, k.step, k.tag);
+#pragma unroll
+  for (int round = 0; round < 10; ++round) {
+    const uint64_t p0 = static_cast<uint64_t>(0xD2511F53u) * c.x;
+    const uint64_t p1 = static_cast<uint64_t>(0xCD9E8D57u) * c.z;
+    c = make_uint4(static_cast<uint32_t>(p1 >> 32) ^ c.y ^ k.rk0[round],
+                   static_cast<uint32_t>(p1),
+                   static_cast<uint32_t>(p0 >> 32) ^ c.w ^ k.rk1[round],
+                   static_cast<uint32_t>(p0));
+  }
+  return c;
 }
 
 // U[0,1) with 24 (binary32) or 53 (binary64) random bits; both conversions are exact.
@@ -73,9 +81,13 @@ template <> __device__ __forceinline__ float u01<float>(uint4 x) { return u01_f3
 template <> __device__ __forceinline__ double u01<double>(uint4 x) { return u01_f64(x); }
 
 // Uniform index on {0..N-1}: the high 64 bits of V * N, V = words 2,3 as a 64-bit integer.
+// For N < 2^32 this is (x2 N + floor(x3 N / 2^32)) / 2^32 rounded down (the discarded low
+// part cannot carry), two 32x32->64 products with no overflow.
 __device__ __forceinline__ int64_t uniform_index(uint4 x, int64_t N) {
-  const uint64_t v = (static_cast<uint64_t>(x.z) << 32) | x.w;
-  return static_cast<int64_t>(__umul64hi(v, static_cast<uint64_t>(N)));
+  const uint64_t n = static_cast<uint64_t>(N);
+  const uint64_t lo = static_cast<uint64_t>(x.w) * n;
+  const uint64_t hi = static_cast<uint64_t>(x.z) * n + (lo >> 32);
+  return static_cast<int64_t>(hi >> 32);
 }
 
 // ---------------------------------------------------------------------------------------

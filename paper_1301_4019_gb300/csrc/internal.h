@@ -43,6 +43,7 @@ struct Scratch {
   int32_t* d;        // claim vector (Prepermute), max_n
   int32_t* a_tmp;    // unpermuted ancestors, max_n
   void* W;           // cumulative weights of the multinomial scheme, 8 * max_n bytes
+  int32_t* guide;    // guide table of the multinomial search, max_n + 1
   double2* rec;      // per-tile records: sums then prefixes (two blocks of max_tiles + 2)
   double* blockmax;  // per-CTA maxima of the max pass
   long long* irec;   // per-tile records of the integer scan (2 * (max_tiles + 2))

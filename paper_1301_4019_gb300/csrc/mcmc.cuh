@@ -246,5 +246,65 @@ __device__ __forceinline__ int32_t rejection_one(const double* __restrict__ lw, 
   return static_cast<int32_t>(i);
 }
 
+// ---------------------------------------------------------------------------------------
+// Rejection with warp refill. Trial counts vary per particle (a geometric tail, Section 2.2),
+// and a warp would wait for its slowest lane. Instead every warp owns a run of particles and
+// a lane that settles its particle takes the next unstarted one of the run, so all lanes stay
+// busy. Attempt s of particle i always uses counter (i, s): the result does not depend on
+// the schedule and equals rejection_one.
+// ---------------------------------------------------------------------------------------
+constexpr int kRejRun = 32 * 8;  // particles per warp run
+
+struct RejBound {  // the bound log w_max in the forms the attempts compare against
+  double lwmax;
+  float lwmax_f;
+  bool okm;
+  long long km;
+};
+__device__ __forceinline__ RejBound make_bound(double log_wmax) {
+  RejBound r;
+  r.lwmax = log_wmax;
+  r.okm = f64_to_f32_trunc(log_wmax, r.lwmax_f);
+  r.km = f64_key(log_wmax);
+  return r;
+}
+
+// Attempt s of particle i with its own log-weight lwi; j receives the proposal. Returns true
+// when the proposal is accepted (or above the bound: flagged and accepted).
+__device__ __forceinline__ bool rejection_attempt(const float* __restrict__ lw, int64_t n,
+                                                  const RejBound& rb, const Keys& keys,
+                                                  int64_t i, uint32_t s, float lwi, int64_t& j,
+                                                  int* err) {
+  const uint4 x = draw(keys, static_cast<uint32_t>(i), s);
+  j = (s > 0) ? uniform_index(x, n) : i;
+  const float u = u01_f32(x);
+  const float lwj = (s == 0) ? lwi : __ldg(lw + j);
+  const float delta = lwj - static_cast<float>(rb.lwmax);
+  if (delta > 0.0f) {
+    flag_error(err, RS_ERR_BOUND_VIOLATED);
+    return true;
+  }
+  return delta == 0.0f || u < exp_pinned(delta);
+}
+
+__device__ __forceinline__ bool rejection_attempt(const double* __restrict__ lw, int64_t n,
+                                                  const RejBound& rb, const Keys& keys,
+                                                  int64_t i, uint32_t s, double lwi,
+                                                  int64_t& j, int* err) {
+  const uint4 x = draw(keys, static_cast<uint32_t>(i), s);
+  j = (s > 0) ? uniform_index(x, n) : i;
+  const double lwj = (s == 0) ? lwi : __ldg(lw + j);
+  const long long kj = f64_key(lwj);
+  if (kj > rb.km && lwj == lwj) {  // above the bound (NaN never compares)
+    flag_error(err, RS_ERR_BOUND_VIOLATED);
+    return true;
+  }
+  if (kj == rb.km) return true;  // ratio exactly 1
+  if (kj == f64_key(-INFINITY) || lwj != lwj) return false;
+  float lwj_f;
+  const bool okj = f64_to_f32_trunc(lwj, lwj_f);
+  return f64_accept_lt(lwj, lwj_f, okj, rb.lwmax, rb.lwmax_f, rb.okm, x);
+}
+
 }  // namespace
 }  // namespace rsk

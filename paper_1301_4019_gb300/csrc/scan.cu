@@ -222,14 +222,37 @@ emit_W_kernel(const T* __restrict__ lw, int64_t N, const ScanGlob* g, const doub
                          Wout, sh_tot, sh_max);
 }
 
+// Pass 3b for the multinomial scheme: stored cumulative weights plus the guide table.
+template <typename T, typename V>
+__global__ void __launch_bounds__(kBlock)
+emit_W_guide_kernel(const T* __restrict__ lw, int64_t N, const ScanGlob* g, const double2* s_rec,
+                    const double2* P_rec, V* __restrict__ Wout, int32_t* __restrict__ G) {
+  __shared__ V sh_tot[kWarps];
+  __shared__ V sh_max[kWarps];
+  __shared__ float2 sh_tab[64];
+  const int64_t base = static_cast<int64_t>(blockIdx.x) * kTile;
+  const double Md = g->M;
+  if (!(Md > -DBL_MAX) || !(g->S_d > 0.0)) return;  // the search writes the identity
+  const WeightCtx wc = make_ctx<T, V>(Md, sh_tab);
+  const bool vec = (reinterpret_cast<uintptr_t>(lw) & 15u) == 0;
+  const int t = blockIdx.x;
+  const V Pm = t > 0 ? load_v<V>(P_rec + t - 1) : vzero(V());
+  const V sm = t > 0 ? load_v<V>(s_rec + t - 1) : vzero(V());
+  emit_tile_W_guide<T, V>(lw, 0, N, base, wc, vec, load_v<V>(P_rec + t), load_v<V>(P_rec + t + 1),
+                          t > 0, Pm, sm, make_guide(g->S_d, N), Wout, G, sh_tot, sh_max);
+}
+
 // ---------------------------------------------------------------------------------------
 // Multinomial search (Code 5), one particle per thread, with the Prepermute claim
 // atomicMin(d[a_i], i) when d is given.
 // ---------------------------------------------------------------------------------------
 template <typename T, typename V>
 __global__ void __launch_bounds__(kBlock)
-search_kernel(const V* __restrict__ W, int64_t N, const ScanGlob* g, Keys keys,
-              int32_t* __restrict__ a, int32_t* __restrict__ d) {
+search_kernel(const V* __restrict__ W, const int32_t* __restrict__ G, int64_t N,
+              const ScanGlob* g, Keys keys, int32_t* __restrict__ a, int32_t* __restrict__ d) {
+  __shared__ Guide sh_gd;
+  if (threadIdx.x == 0) sh_gd = make_guide(g->S_d, N);
+  __syncthreads();
   const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
   if (i >= N) return;
   if (!(g->M > -DBL_MAX) || !(g->S_d > 0.0)) {
@@ -237,13 +260,13 @@ search_kernel(const V* __restrict__ W, int64_t N, const ScanGlob* g, Keys keys,
     if (d) atomicMin(d + i, static_cast<int32_t>(i));
     return;
   }
-  const int32_t k = search_one<T, V>(W, N, keys, i);
+  const int32_t k = search_one_guided<T, V>(W, G, N, sh_gd, keys, i);
   a[i] = k;
   if (d) atomicMin(d + k, static_cast<int32_t>(i));
 }
 
 int max_grid(int64_t N, int max_blocks) {
-  const int64_t want = (N + kTile - 1) / kTile;
+  const int64_t want = (N + 4 * kBlock - 1) / (4 * kBlock);  // one 1024-element slice per CTA
   return static_cast<int>(want < max_blocks ? want : max_blocks);
 }
 
@@ -281,10 +304,10 @@ cudaError_t run_scan(const Scratch& s, int scheme, const T* lw, int64_t N, uint6
   } else {
     V* W = static_cast<V*>(s.W);
     trace_mark(s.trace, kLblW[ai], st);
-    emit_W_kernel<T, V, V><<<tiles, kBlock, 0, st>>>(lw, N, s.glob, P_rec, W);
+    emit_W_guide_kernel<T, V><<<tiles, kBlock, 0, st>>>(lw, N, s.glob, s_rec, P_rec, W, s.guide);
     const int grid = static_cast<int>((N + kBlock - 1) / kBlock);
     trace_mark(s.trace, kLblSearch[ai], st);
-    search_kernel<T, V><<<grid, kBlock, 0, st>>>(W, N, s.glob, keys, a_out, d);
+    search_kernel<T, V><<<grid, kBlock, 0, st>>>(W, s.guide, N, s.glob, keys, a_out, d);
   }
   return cudaGetLastError();
 }

@@ -438,5 +438,136 @@ __device__ __forceinline__ int32_t search_one(const V* __restrict__ W, int64_t n
   return static_cast<int32_t>(lo < n ? lo : n - 1);
 }
 
+// ---------------------------------------------------------------------------------------
+// Guide table of the multinomial search. Bucket edges e_b = float(b) * step (b = 0..n-1,
+// step = W^N / n in binary32, e_n = +inf) are non-decreasing in b; G[b] = the first particle
+// j with W_j > e_b, b = 0..n (G[n] = n - 1). Particle j owns the buckets b with
+// C_{j-1} <= b < C_j, C_j = the first b with e_b >= W_j, so G is written by a Code-11-style
+// scatter in the emit pass. For a draw u with e_b <= u < e_{b+1} the answer (the first j with
+// W_j > u) lies in [G[b], G[b+1]], so a binary search of that range returns exactly what a
+// binary search of the whole array returns, after about three loads instead of log2 n.
+// ---------------------------------------------------------------------------------------
+struct Guide {
+  float step;      // W^N / n
+  float inv_step;  // n / W^N (estimates only)
+};
+__device__ __forceinline__ Guide make_guide(double Sd, int64_t n) {
+  Guide g;
+  g.step = __double2float_rn(__ddiv_rn(Sd, static_cast<double>(n)));
+  g.inv_step = __double2float_rn(__ddiv_rn(static_cast<double>(n), Sd));
+  return g;
+}
+__device__ __forceinline__ float guide_edge(int64_t b, const Guide& g, int64_t n) {
+  if (b >= n) return INFINITY;
+  return __fmul_rn(__ll2float_rn(b), g.step);
+}
+template <typename V> __device__ __forceinline__ V edge_as(float e);
+template <> __device__ __forceinline__ float edge_as<float>(float e) { return e; }
+template <> __device__ __forceinline__ double edge_as<double>(float e) { return e; }
+template <> __device__ __forceinline__ float2 edge_as<float2>(float e) { return make_float2(e, 0.0f); }
+
+// C(W) = the first b in [0, n] with e_b >= W.
+template <typename V>
+__device__ __forceinline__ int64_t guide_count(V W, const Guide& g, int64_t n) {
+  const float est = ceilf(__fmul_rn(vhi(W), g.inv_step));
+  int64_t b = est > 0.0f ? (est < static_cast<float>(n) ? static_cast<int64_t>(est) : n) : 0;
+  int steps = 0;
+  while (b > 0 && vle(W, edge_as<V>(guide_edge(b - 1, g, n))) && ++steps < 64) --b;
+  while (b < n && !vle(W, edge_as<V>(guide_edge(b, g, n))) && ++steps < 64) ++b;
+  if (steps >= 64) {  // far from the estimate: bisect the edges
+    int64_t lo = 0, hi = n;
+    while (lo < hi) {
+      const int64_t mid = lo + ((hi - lo) >> 1);
+      if (vle(W, edge_as<V>(guide_edge(mid, g, n)))) hi = mid; else lo = mid + 1;
+    }
+    b = lo;
+  }
+  return b;
+}
+
+// Stored cumulative weights of one tile plus the guide-table scatter of its particles
+// (block-level; same cumulative-count pattern as emit_tile_cumoff).
+template <typename T, typename V>
+__device__ __forceinline__ void emit_tile_W_guide(const T* __restrict__ lw, int64_t lo, int64_t N,
+                                                  int64_t base, const WeightCtx& wc, bool vec,
+                                                  V Pt, V Pn, bool has_prev, V Pm, V sm,
+                                                  const Guide& gd, V* __restrict__ Wout,
+                                                  int32_t* __restrict__ G, V* sh_tot,
+                                                  V* sh_max) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t n = N - lo;
+  V val[kRows][4];
+  tile_raw_values<T, V>(lw, lo, N, base, wc, vec, val, sh_tot);
+  V prevmax;
+  tile_running_max<V>(val, base, lo, N, sh_max, prevmax);
+  int64_t C[kRows][4];
+#pragma unroll
+  for (int r = 0; r < kRows; ++r)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int64_t e = base + tile_offset(warp, r, lane, q);
+      const V W = vclamp(vadd(Pt, val[r][q]), Pt, Pn);
+      if (e >= lo && e < N) Wout[e] = W;
+      C[r][q] = guide_count<V>(W, gd, n);
+    }
+  int64_t Cbefore = 0;
+  if (lane == 0) {
+    if (warp > 0) {
+      Cbefore = guide_count<V>(vclamp(vadd(Pt, prevmax), Pt, Pn), gd, n);
+    } else if (has_prev) {
+      Cbefore = guide_count<V>(vclamp(vadd(Pm, sm), Pm, Pt), gd, n);
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < kRows; ++r) {
+    int64_t prev = __shfl_up_sync(0xffffffffu, C[r][3], 1);
+    if (r > 0) {
+      const int64_t rowprev = __shfl_sync(0xffffffffu, C[r - 1][3], 31);
+      if (lane == 0) prev = rowprev;
+    } else if (lane == 0) {
+      prev = Cbefore;
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int64_t e = base + tile_offset(warp, r, lane, q);
+      const int64_t j = e - lo;
+      int64_t Cc = C[r][q];
+      if (j == n - 1) Cc = n;
+      if (e >= lo && e < N) {
+        for (int64_t b = prev; b < Cc; ++b) G[lo + b] = static_cast<int32_t>(j);
+        if (j == n - 1) G[lo + n] = static_cast<int32_t>(n - 1);
+      }
+      prev = Cc;
+    }
+  }
+}
+
+// Multinomial search of output i through the guide table (same result as search_one).
+template <typename T, typename V>
+__device__ __forceinline__ int32_t search_one_guided(const V* __restrict__ W,
+                                                     const int32_t* __restrict__ G, int64_t n,
+                                                     const Guide& gd, const Keys& keys,
+                                                     int64_t i) {
+  const V S = W[n - 1];
+  const auto U = Path<T, V>::draw_u(draw(keys, static_cast<uint32_t>(i), 0u));
+  const V u = vtimes_u(S, U);
+  // bucket b with e_b <= u < e_{b+1}
+  const float est = floorf(__fmul_rn(vhi(u), gd.inv_step));
+  int64_t b = est > 0.0f ? (est < static_cast<float>(n - 1) ? static_cast<int64_t>(est) : n - 1) : 0;
+  int steps = 0;
+  while (b > 0 && !vle(edge_as<V>(guide_edge(b, gd, n)), u) && ++steps < 64) --b;
+  while (b < n - 1 && vle(edge_as<V>(guide_edge(b + 1, gd, n)), u) && ++steps < 64) ++b;
+  int64_t lo = 0, hi = n;
+  if (steps < 64) {
+    lo = __ldg(G + b);
+    hi = static_cast<int64_t>(__ldg(G + b + 1)) + 1;
+  }
+  while (lo < hi) {
+    const int64_t mid = lo + ((hi - lo) >> 1);
+    if (vle(W[mid], u)) lo = mid + 1; else hi = mid;
+  }
+  return static_cast<int32_t>(lo < n ? lo : n - 1);
+}
+
 }  // namespace
 }  // namespace rsk
