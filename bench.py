@@ -44,6 +44,7 @@ UNIT = "G ancestors/s"
 SCHEME_NAMES = ["multinomial", "stratified", "systematic", "metropolis", "rejection"]
 SEED = 20130115
 L2_BYTES = 129 * 2**20
+LAUNCH_MODES = {"auto": 0, "fused": 1, "separate": 2}  # rs_set_launch_mode
 
 
 def parse_args():
@@ -58,6 +59,8 @@ def parse_args():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-batched", action="store_true")
     p.add_argument("--batched-filters", type=int, default=4096)
+    p.add_argument("--launch-mode", choices=["auto", "fused", "separate"], default="auto",
+                   help="launch structure of the scan-based schemes (results are identical)")
     p.add_argument("--single", default=None,
                    help="profile one call: scheme:dtype[:prec], e.g. metropolis:f32 "
                         "(runs warmup + steps calls with Permute, prints one JSON line)")
@@ -167,8 +170,14 @@ class ClockSampler:
 # ---------------------------------------------------------------------------------------
 def kernel_roofline_units(label: str, N: int, B: int):
     """(bound, algorithmic amount per launch, unit) for a traced kernel label."""
-    S = 8 if label.endswith("_f64") else 4
-    V = 8 if (label.endswith("_f64") or label.endswith("_f32c")) else 4
+    S = 8 if ("_f64" in label) else 4
+    V = 8 if ("_f64" in label or label.endswith("_f32c")) else 4
+    if label.startswith("fused_systematic_") or label.startswith("fused_stratified_"):
+        # two reads of logw (the normaliser precedes every O_i), write a, then Permute:
+        # write and read the claims d, read a, write c
+        return "hbm", (2 * S + 4 + 16) * N, "B"
+    if label.startswith("fused_multinomial_"):
+        return "hbm", (2 * S + V + 4 + 16) * N, "B"  # as above plus the stored W
     if label.startswith("max_") or label.startswith("tile_sum_"):
         return "hbm", S * N, "B"
     if label.startswith("emit_systematic_") or label.startswith("emit_stratified_"):
@@ -224,6 +233,7 @@ def run_ours(args):
     conv = {name: [torch.empty(N, dtype=torch.int32, device=dev) for _ in range(4)]
             for name, _, _ in dtypes}
     h = rs.Handle(N)
+    rs.rs_set_launch_mode(h, LAUNCH_MODES[args.launch_mode])
 
     def step(k):
         for name, _, _ in dtypes:
@@ -432,7 +442,8 @@ def run_ours(args):
                        "parallelism": f"replicas x{world}",
                        "l2": f"inputs rotate through a {pool_bytes / 2**20:.0f} MiB pool "
                              f"(> L2 {L2_BYTES // 2**20} MiB); no flush",
-                       "timing": "CUDA-graph replay of K steps, CUDA events"},
+                       "timing": "CUDA-graph replay of K steps, CUDA events",
+                       "launch_mode": args.launch_mode},
             "e2e": {"value": round(world * ancestors_per_step / (ms_e2e * 1e-3) / 1e9, 3),
                     "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                     "ms_per_step": round(ms_e2e, 5)},
@@ -613,6 +624,7 @@ def run_single(args):
     lw = torch.from_numpy(workload.synthetic_logw(N, args.y, seed=SEED, dtype=npdt)).cuda()
     out = torch.empty(N, dtype=torch.int32, device="cuda")
     with rs.Handle(N) as h:
+        rs.rs_set_launch_mode(h, LAUNCH_MODES[args.launch_mode])
         for k in range(args.warmup):
             rs.rs_resample(h, scheme, lw, B=B, seed=SEED, step=k, out=out, permute=True, prec=prec)
         torch.cuda.synchronize()

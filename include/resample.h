@@ -166,6 +166,23 @@ int rs_prepermute(rs_handle* h, const int32_t* a_dev, int64_t N, int32_t* d_dev,
  * c_dev must not overlap a_dev. */
 int rs_permute(rs_handle* h, const int32_t* a_dev, int64_t N, int32_t* c_dev, void* stream);
 
+/* How rs_resample launches the multinomial, stratified and systematic schemes. The result is
+ * the same bit for bit in every mode; only the launch structure differs:
+ *   RS_LAUNCH_SEPARATE : one kernel per pass (max, tile sums, emission, search, Permute).
+ *   RS_LAUNCH_FUSED    : all passes in one cooperative kernel whose CTAs are co-resident and
+ *                        meet at grid-wide barriers (bounded waits: RS_ERR_TIMEOUT through
+ *                        rs_last_error); used when the device supports cooperative launches,
+ *                        else the separate kernels run.
+ *   RS_LAUNCH_AUTO     : (default) fused up to RS_FUSED_AUTO_MAX_N particles, where launch
+ *                        latency dominates, separate kernels above (where the separate
+ *                        kernels' larger grids hide more memory latency).
+ * Host-only; RS_ERR_ARG for an unknown mode. The setting belongs to the handle. */
+#define RS_LAUNCH_AUTO 0
+#define RS_LAUNCH_FUSED 1
+#define RS_LAUNCH_SEPARATE 2
+#define RS_FUSED_AUTO_MAX_N (1 << 16)
+int rs_set_launch_mode(rs_handle* h, int mode);
+
 /* B* = log(eps) / log(1 - beta) of Eq. (B) (Section 2.1), rounded up: the number of
  * Metropolis steps that bounds the total-variation distance of every chain by eps, for a
  * lower bound beta on min_i(mean(w)/w^i) (Eq. beta), e.g. E(w)/w_max (Eq. beta2).

@@ -39,9 +39,11 @@ EXPORTED = [
     "rs_cumulative_offspring", "rs_adjacent_difference", "rs_cumulative_offspring_to_ancestors",
     "rs_prepermute", "rs_permute", "rs_metropolis_B", "rs_last_error", "rs_strerror",
     "rs_trace", "rs_trace_count", "rs_trace_label", "rs_systematic_noalloc",
-    "rs_resample_batched",
+    "rs_resample_batched", "rs_set_launch_mode",
 ]
 NOALLOC_MAX_N = 1 << 22
+LAUNCH_AUTO, LAUNCH_FUSED, LAUNCH_SEPARATE = 0, 1, 2
+FUSED_AUTO_MAX_N = 1 << 16
 
 _lock = threading.Lock()
 _lib = None
@@ -97,6 +99,7 @@ def _declare(lib):
         "rs_systematic_noalloc": (I, [I, P, I64, U64, U64, P, P, P]),
         "rs_resample_batched": (I, [P, I, I, P, P, I32, P, I32, U64, U64, P, I,
                                     C.POINTER(_Opts), P]),
+        "rs_set_launch_mode": (I, [P, I]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -289,6 +292,12 @@ def rs_permute(h: Handle, a: torch.Tensor, c: torch.Tensor | None = None, stream
     _check(load().rs_permute(h.ptr, _dev(a, torch.int32, "a"), N, _dev(c, torch.int32, "c"),
                              _stream(stream)), "rs_permute")
     return c
+
+
+def rs_set_launch_mode(h: Handle, mode: int) -> None:
+    """LAUNCH_AUTO, LAUNCH_FUSED (one cooperative kernel) or LAUNCH_SEPARATE (one kernel per
+    pass) for the scan-based schemes of rs_resample; results are identical in every mode."""
+    _check(load().rs_set_launch_mode(h.ptr, int(mode)), "rs_set_launch_mode")
 
 
 def rs_metropolis_B(eps: float, beta: float) -> int:

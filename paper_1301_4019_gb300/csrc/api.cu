@@ -88,6 +88,10 @@ int rs_create(rs_handle** out, int64_t max_n, int device) {
   s.max_n = max_n;
   s.max_tiles = (max_n + rsk::kTile - 1) / rsk::kTile;
   s.max_blocks = 152 * 8;
+  s.launch_mode = RS_LAUNCH_AUTO;
+  int coop = 0;
+  if (cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, device) != cudaSuccess) coop = 0;
+  s.coop = coop;
   bool ok = true;
   ok &= cudaMalloc(&s.d, sizeof(int32_t) * max_n) == cudaSuccess;
   ok &= cudaMalloc(&s.a_tmp, sizeof(int32_t) * max_n) == cudaSuccess;
@@ -193,8 +197,12 @@ int rs_resample(rs_handle* h, int scheme, int dtype, const void* logw_dev, int64
     case RS_STRATIFIED:
     case RS_SYSTEMATIC: {
       const rsk::Acc acc = accumulation(dtype, o.prec);
+      const int mode = h->s.launch_mode;
+      const bool fused = mode != RS_LAUNCH_SEPARATE &&
+                         (mode == RS_LAUNCH_FUSED || N <= RS_FUSED_AUTO_MAX_N) &&
+                         rsk::fused_available(h->s, scheme, acc);
       e = rsk::launch_scan_resample(h->s, scheme, acc, logw_dev, N, seed, step, o.filter, a_out,
-                                    d, s);
+                                    d, fused, s);
       break;
     }
     case RS_METROPOLIS:
@@ -215,7 +223,12 @@ int rs_resample(rs_handle* h, int scheme, int dtype, const void* logw_dev, int64
                                   o.filter, a_out, d, s);
       break;
   }
-  if (e == cudaSuccess && permute) e = rsk::launch_permute(h->s, a_out, d, N, ancestors_dev, s);
+  if (e == cudaSuccess && permute) {
+    if (scheme == RS_STRATIFIED || scheme == RS_SYSTEMATIC)  // non-decreasing ancestry
+      e = rsk::launch_permute_sorted(h->s, a_out, d, N, ancestors_dev, s);
+    else
+      e = rsk::launch_permute(h->s, a_out, d, N, ancestors_dev, s);
+  }
   end_mark(h, s);
   return cuda_status(e);
 }
@@ -335,6 +348,13 @@ int rs_permute(rs_handle* h, const int32_t* a_dev, int64_t N, int32_t* c_dev, vo
   return cuda_status(e);
 }
 
+int rs_set_launch_mode(rs_handle* h, int mode) {
+  if (!h || (mode != RS_LAUNCH_AUTO && mode != RS_LAUNCH_FUSED && mode != RS_LAUNCH_SEPARATE))
+    return RS_ERR_ARG;
+  h->s.launch_mode = mode;
+  return RS_OK;
+}
+
 int rs_metropolis_B(double eps, double beta, int32_t* B) {
   if (!B || !(eps > 0.0 && eps < 1.0) || !(beta > 0.0 && beta <= 1.0)) return RS_ERR_ARG;
   if (beta >= 1.0) {
@@ -359,6 +379,11 @@ int rs_last_error(rs_handle* h, void* stream) {
     return RS_ERR_CUDA;
   if (cudaMemcpy(h->s.err, &none, sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess)
     return RS_ERR_CUDA;
+  if (v == -RS_ERR_TIMEOUT) {  // a grid barrier gave up: its arrival counter may be stale
+    if (cudaMemset(&h->s.glob->bar_count, 0, sizeof(unsigned int)) != cudaSuccess ||
+        cudaDeviceSynchronize() != cudaSuccess)
+      return RS_ERR_CUDA;
+  }
   return v == rsk::kNoError ? RS_OK : -v;
 }
 

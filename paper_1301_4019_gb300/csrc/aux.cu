@@ -44,6 +44,15 @@ permute_kernel(const int32_t* __restrict__ a, const int32_t* __restrict__ d, int
   permute_one(a, d, N, c, i, err);
 }
 
+// The same for a non-decreasing ancestry with its claims (permute_sorted_one).
+__global__ void __launch_bounds__(kBlock)
+permute_sorted_kernel(const int32_t* __restrict__ a, const int32_t* __restrict__ d, int64_t N,
+                      int32_t* __restrict__ c, int* err) {
+  const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  permute_sorted_one(a, d, N, c, i, err);
+}
+
 // Ancestors-to-Offspring (Code 12).
 __global__ void __launch_bounds__(kBlock)
 offspring_kernel(const int32_t* __restrict__ a, int64_t N, int32_t* __restrict__ o, int* err) {
@@ -83,6 +92,8 @@ cumoff_to_ancestors_kernel(const int32_t* __restrict__ O, int64_t N, int32_t* __
 // Integer inclusive prefix sum, reduce-then-scan over tiles of 4096 (exact in int64):
 // pass 1 writes tile totals and the last CTA scans them; pass 2 scans each tile again and
 // adds its prefix.
+constexpr int kIscanTile = 16 * kBlock;  // elements per CTA of the integer scan
+
 __device__ __forceinline__ long long block_tile_scan(const int32_t* __restrict__ in, int64_t N,
                                                      int64_t base, long long (&v)[16],
                                                      long long* sh) {
@@ -120,7 +131,8 @@ iscan_sum_kernel(const int32_t* __restrict__ in, int64_t N, long long* tot, long
   __shared__ long long sh[kWarps];
   __shared__ bool am_last;
   long long v[16];
-  const long long total = block_tile_scan(in, N, static_cast<int64_t>(blockIdx.x) * kTile, v, sh);
+  const long long total =
+      block_tile_scan(in, N, static_cast<int64_t>(blockIdx.x) * kIscanTile, v, sh);
   if (threadIdx.x == 0) {
     tot[blockIdx.x] = total;
     __threadfence();
@@ -159,7 +171,7 @@ iscan_emit_kernel(const int32_t* __restrict__ in, int64_t N, const long long* pr
                   int32_t* __restrict__ out) {
   __shared__ long long sh[kWarps];
   long long v[16];
-  const int64_t base = static_cast<int64_t>(blockIdx.x) * kTile;
+  const int64_t base = static_cast<int64_t>(blockIdx.x) * kIscanTile;
   block_tile_scan(in, N, base, v, sh);
   const long long p = pre[blockIdx.x];
   const int64_t idx = base + 16 * threadIdx.x;
@@ -199,6 +211,13 @@ cudaError_t launch_permute(const Scratch& s, const int32_t* a, const int32_t* d,
   return cudaGetLastError();
 }
 
+cudaError_t launch_permute_sorted(const Scratch& s, const int32_t* a, const int32_t* d, int64_t N,
+                                  int32_t* c, cudaStream_t st) {
+  trace_mark(s.trace, "permute_sorted", st);
+  permute_sorted_kernel<<<grid_for(N), kBlock, 0, st>>>(a, d, N, c, s.err);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_offspring(const Scratch& s, const int32_t* a, int64_t N, int32_t* o,
                              cudaStream_t st) {
   trace_mark(s.trace, "fill", st);
@@ -211,7 +230,7 @@ cudaError_t launch_offspring(const Scratch& s, const int32_t* a, int64_t N, int3
 
 cudaError_t launch_inclusive_scan_i32(const Scratch& s, const int32_t* o, int64_t N,
                                       int32_t* O, cudaStream_t st) {
-  const int tiles = static_cast<int>((N + kTile - 1) / kTile);
+  const int tiles = static_cast<int>((N + kIscanTile - 1) / kIscanTile);
   long long* tot = s.irec;
   long long* pre = s.irec + (s.max_tiles + 2);
   trace_mark(s.trace, "iscan_sum", st);

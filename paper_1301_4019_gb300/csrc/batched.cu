@@ -61,7 +61,7 @@ __device__ __forceinline__ bool locate_particle(const int64_t* __restrict__ off,
   P.n = hi - P.lo;
   P.i = g - P.lo;
   return P.lo >= 0 && hi <= max_n && P.n > 0 &&
-         P.n <= static_cast<int64_t>(kBatchMaxTiles) * kTile && P.i >= 0 && P.i < P.n;
+         P.n <= kBatchMaxN && P.i >= 0 && P.i < P.n;
 }
 
 // Filter holding global position g: the last f with off[f] <= g (off has F + 1 entries).
@@ -108,7 +108,7 @@ __global__ void __launch_bounds__(1024) batch_plan_kernel(Batch b) {
   for (int f = f0; f < f1; ++f) {
     const int64_t lo = b.off[f], hi = b.off[f + 1], n = hi - lo;
     const bool ok = lo >= 0 && n >= 0 && hi <= b.max_n &&
-                    n <= static_cast<int64_t>(kBatchMaxTiles) * kTile;
+                    n <= kBatchMaxN;
     if (!ok) flag_error(b.err, RS_ERR_ARG);
     local += ok ? static_cast<int>((n + kTile - 1) / kTile) : 0;
     b.fmax[f] = LLONG_MIN;
@@ -128,7 +128,7 @@ __global__ void __launch_bounds__(1024) batch_plan_kernel(Batch b) {
     b.tile_start[f] = p;
     const int64_t lo = b.off[f], hi = b.off[f + 1], n = hi - lo;
     const bool ok = lo >= 0 && n >= 0 && hi <= b.max_n &&
-                    n <= static_cast<int64_t>(kBatchMaxTiles) * kTile;
+                    n <= kBatchMaxN;
     p += ok ? static_cast<int>((n + kTile - 1) / kTile) : 0;
   }
   if (f1 == F && f0 < F) b.tile_start[F] = p;

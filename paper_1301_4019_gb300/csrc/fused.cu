@@ -1,0 +1,337 @@
+// fused.cu -- the three passes of the multinomial, stratified and systematic resamplers of
+// one filter (max, tile sums with tile prefixes, emission) as one persistent cooperative
+// kernel.
+//
+// At the sizes of a particle filter (N ~ 2^20) each pass over the weights is short, so a chain
+// of three launches is dominated by per-launch latency and tails. Here one CTA set, all
+// resident at once (cooperative launch), runs the phases back to back, separated by
+// grid-wide barriers:  max -> tile sums -> tile prefixes (CTA 0) -> emission.
+// Each phase calls the same device functions as the multi-launch kernels on the same tiles,
+// so the results are identical. The latency-bound particle-parallel steps that follow (the
+// multinomial search, Permute) stay separate full-occupancy kernels: inside this grid, sized
+// by the emission's registers, they would run with a quarter of the threads in flight.
+// A barrier waits at most kBarrierTimeoutNs (then it records RS_ERR_TIMEOUT and proceeds;
+// every phase stays bounds-checked, so the kernel still ends); the barrier counter returns
+// to 0 at the end of every launch.
+#include <cfloat>
+#include <climits>
+
+#include "common.cuh"
+#include "internal.h"
+#include "tile.cuh"
+#include "values.cuh"
+
+namespace rsk {
+namespace {
+
+constexpr unsigned long long kBarrierTimeoutNs = 10ull * 1000 * 1000 * 1000;  // 10 s
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Grid-wide barrier over all CTAs of the (cooperative, hence co-resident) launch, on one
+// arrival counter in the handle's ScanGlob that counts up through the launch: barrier k is
+// passed when the counter reaches k * gridDim.x. Thread 0 of each CTA arrives with a release
+// reduction and polls with acquire loads (the CTA's writes are ordered before the arrival by
+// the preceding __syncthreads, and every later read after the poll by the following one).
+// The wait is bounded: after kBarrierTimeoutNs it records RS_ERR_TIMEOUT and goes on.
+__device__ __forceinline__ void grid_barrier(unsigned int* count, unsigned int& target, int* err) {
+  target += gridDim.x;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(count) : "memory");
+    unsigned int cur;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(cur) : "l"(count) : "memory");
+    if (static_cast<int>(cur - target) < 0) {
+      const unsigned long long t0 = global_ns();
+      for (;;) {
+        __nanosleep(20);
+        asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(cur) : "l"(count) : "memory");
+        if (static_cast<int>(cur - target) >= 0) break;
+        if (global_ns() - t0 > kBarrierTimeoutNs) {
+          flag_error(err, RS_ERR_TIMEOUT);
+          break;
+        }
+      }
+    }
+  }
+  __syncthreads();
+}
+
+// Last act of every CTA: one more arrival; the CTA that completes it returns the counter to
+// 0 for the next launch (stream order makes the reset visible to it).
+__device__ __forceinline__ void grid_exit(unsigned int* count, unsigned int target) {
+  if (threadIdx.x == 0 && atomicAdd(count, 1u) == target + gridDim.x - 1) atomicExch(count, 0u);
+}
+
+// Order-preserving integer keys of the log-weights (exact comparisons, no binary64 ALU).
+__device__ __forceinline__ long long fkey(float v) {
+  const int b = __float_as_int(v);
+  return static_cast<long long>(b >= 0 ? b : (b ^ 0x7fffffff));
+}
+__device__ __forceinline__ long long fkey(double v) {
+  const long long b = __double_as_longlong(v);
+  return b >= 0 ? b : (b ^ 0x7fffffffffffffffLL);
+}
+__device__ __forceinline__ double fvalue(long long k, float) {
+  const int b = static_cast<int>(k);
+  return static_cast<double>(__int_as_float(b >= 0 ? b : (b ^ 0x7fffffff)));
+}
+__device__ __forceinline__ double fvalue(long long k, double) {
+  return __longlong_as_double(k >= 0 ? k : (k ^ 0x7fffffffffffffffLL));
+}
+
+// Block-wide maximum of a key (every thread gets the result).
+__device__ __forceinline__ long long block_max_key(long long m, long long* sh) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const long long y = __shfl_xor_sync(0xffffffffu, m, o);
+    m = y > m ? y : m;
+  }
+  __syncthreads();
+  if (lane == 0) sh[warp] = m;
+  __syncthreads();
+  long long bm = sh[0];
+  for (int k = 1; k < kWarps; ++k) bm = sh[k] > bm ? sh[k] : bm;
+  return bm;
+}
+
+struct FusedArgs {
+  int64_t N;
+  Keys keys;
+  int32_t* a;      // ancestors (systematic / stratified)
+  int32_t* d;      // Prepermute claims, or nullptr
+  void* W;         // multinomial cumulative weights
+  int32_t* guide;  // multinomial guide table
+  double2* s_rec;
+  double2* P_rec;
+  ScanGlob* g;
+  double* blockmax;  // per-CTA maxima (gridDim.x entries)
+  int* err;
+};
+
+template <typename T, typename V, int SCHEME>
+__device__ __forceinline__ void fused_body(const T* __restrict__ lw, const FusedArgs& A,
+                                           unsigned int& target) {
+  __shared__ V sh_tot[kWarps];
+  __shared__ V sh_max[kWarps];
+  __shared__ float2 sh_tab[64];
+  __shared__ long long sh_key[kWarps];
+  __shared__ Guide sh_gd;
+  const int64_t N = A.N;
+  const int T_tiles = static_cast<int>((N + kTile - 1) / kTile);
+  const bool vec = (reinterpret_cast<uintptr_t>(lw) & 15u) == 0;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+
+  // ---- phase 1: maximum log-weight (and the Prepermute sentinel of the multinomial claims) --
+  {
+    long long m = fkey(neg_inf<T>());
+    bool bad = false;
+    for (int64_t i0 = 4 * (static_cast<int64_t>(blockIdx.x) * kBlock + threadIdx.x); i0 < N;
+         i0 += 4 * static_cast<int64_t>(gridDim.x) * kBlock) {
+      T x[4];
+      load4(lw, i0, 0, N, vec, x);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const bool nan = x[q] != x[q];
+        bad |= nan || x[q] == static_cast<T>(INFINITY);
+        const long long k = fkey(x[q]);
+        if (!nan && k > m) m = k;
+        if constexpr (SCHEME == RS_MULTINOMIAL) {
+          if (A.d && i0 + q < N) A.d[i0 + q] = static_cast<int32_t>(N);
+        }
+      }
+    }
+    if (bad) flag_error(A.err, RS_ERR_NONFINITE);
+    const long long bm = block_max_key(m, sh_key);
+    if (threadIdx.x == 0) A.blockmax[blockIdx.x] = fvalue(bm, T());
+  }
+  grid_barrier(&A.g->bar_count, target, A.err);
+  double M;
+  {
+    long long m = fkey(-static_cast<double>(INFINITY));
+    for (int b = threadIdx.x; b < static_cast<int>(gridDim.x); b += kBlock) {
+      const long long y = fkey(__ldcg(A.blockmax + b));
+      m = y > m ? y : m;
+    }
+    M = fvalue(block_max_key(m, sh_key), 0.0);
+  }
+  const bool zero = !(M > -DBL_MAX);
+
+  // ---- phase 2: tile sums -----------------------------------------------------------------
+  const WeightCtx wc = make_ctx<T, V>(zero ? 0.0 : M, sh_tab);
+  if (!zero) {
+    for (int t = blockIdx.x; t < T_tiles; t += gridDim.x) {
+      const int64_t base = static_cast<int64_t>(t) * kTile;
+      V val[kRows][4];
+      tile_raw_values<T, V>(lw, 0, N, base, wc, vec, val, sh_tot);
+      const V tm = tile_total<V>(val, base, 0, N, sh_max);
+      if (threadIdx.x == 0) store_v<V>(A.s_rec + t, tm);
+    }
+  }
+  grid_barrier(&A.g->bar_count, target, A.err);
+
+  // ---- phase 3: tile prefixes, W^N, N / W^N (CTA 0) ------------------------------------------
+  if (blockIdx.x == 0) {
+    if (zero) {
+      if (threadIdx.x == 0) {
+        A.g->S_d = 0.0;
+        flag_error(A.err, RS_ERR_ZERO_WEIGHT);
+      }
+    } else {
+      tile_prefix_compute<V>(A.s_rec, A.P_rec, T_tiles, N, reinterpret_cast<V*>(&A.g->S_raw),
+                             reinterpret_cast<V*>(&A.g->scale_raw), &A.g->S_d);
+      if (threadIdx.x == 0 && !(A.g->S_d > 0.0)) flag_error(A.err, RS_ERR_ZERO_WEIGHT);
+    }
+    if (threadIdx.x == 0) A.g->M = M;  // read by the search kernel
+  }
+  grid_barrier(&A.g->bar_count, target, A.err);
+  const double Sd = __ldcg(&A.g->S_d);
+
+  // ---- phase 4: emission ------------------------------------------------------------------------
+  if (zero || !(Sd > 0.0)) {  // all weights zero (flagged): every particle keeps itself
+    if constexpr (SCHEME != RS_MULTINOMIAL) {  // (the search kernel writes the identity)
+      for (int64_t i = static_cast<int64_t>(blockIdx.x) * kBlock + threadIdx.x; i < N;
+           i += static_cast<int64_t>(gridDim.x) * kBlock) {
+        A.a[i] = static_cast<int32_t>(i);
+        if (A.d) A.d[i] = static_cast<int32_t>(i);
+      }
+    }
+    return;  // uniform over the grid
+  }
+  const V S = load_v_cg<V>(&A.g->S_raw), scale = load_v_cg<V>(&A.g->scale_raw);
+  if constexpr (SCHEME == RS_MULTINOMIAL) {
+    if (threadIdx.x == 0) sh_gd = make_guide(Sd, N);
+    __syncthreads();
+  }
+  for (int t = blockIdx.x; t < T_tiles; t += gridDim.x) {
+    const int64_t base = static_cast<int64_t>(t) * kTile;
+    const V Pt = load_v_cg<V>(A.P_rec + t), Pn = load_v_cg<V>(A.P_rec + t + 1);
+    const V Pm = t > 0 ? load_v_cg<V>(A.P_rec + t - 1) : vzero(V());
+    const V sm = t > 0 ? load_v_cg<V>(A.s_rec + t - 1) : vzero(V());
+    if constexpr (SCHEME == RS_MULTINOMIAL) {
+      emit_tile_W_guide<T, V>(lw, 0, N, base, wc, vec, Pt, Pn, t > 0, Pm, sm, sh_gd,
+                              static_cast<V*>(A.W), A.guide, sh_tot, sh_max);
+    } else {
+      emit_tile_cumoff<T, V, SCHEME == RS_STRATIFIED>(lw, 0, N, base, wc, vec, Pt, Pn, t > 0, Pm,
+                                                       sm, S, scale, A.keys, A.a, A.d, sh_tot,
+                                                       sh_max);
+    }
+  }
+
+}
+
+template <typename T, typename V, int SCHEME>
+__global__ void __launch_bounds__(kBlock) fused_scan_kernel(const T* __restrict__ lw, FusedArgs A) {
+  unsigned int target = 0;
+  fused_body<T, V, SCHEME>(lw, A, target);
+  grid_exit(&A.g->bar_count, target);
+}
+
+template <typename T, typename V, int SCHEME>
+int fused_capacity() {
+  static int cap = -1;  // identical devices assumed
+  if (cap < 0) {
+    int dev = 0, sms = 0, per_sm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fused_scan_kernel<T, V, SCHEME>,
+                                                      kBlock, 0) != cudaSuccess)
+      return 0;
+    cap = per_sm * sms;
+  }
+  return cap;
+}
+
+template <typename T, typename V, int SCHEME>
+cudaError_t launch_fused(const Scratch& s, const T* lw, const FusedArgs& A, cudaStream_t st) {
+  int64_t grid = fused_capacity<T, V, SCHEME>();
+  if (grid > s.max_blocks) grid = s.max_blocks;
+  const int64_t tiles = (A.N + kTile - 1) / kTile;
+  if (grid > tiles) grid = tiles;
+  if (grid < 1) return cudaErrorCooperativeLaunchTooLarge;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(static_cast<unsigned>(grid));
+  cfg.blockDim = dim3(kBlock);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, fused_scan_kernel<T, V, SCHEME>, lw, A);
+}
+
+template <typename T, typename V>
+int capacity(int scheme) {
+  switch (scheme) {
+    case RS_MULTINOMIAL: return fused_capacity<T, V, RS_MULTINOMIAL>();
+    case RS_STRATIFIED: return fused_capacity<T, V, RS_STRATIFIED>();
+    default: return fused_capacity<T, V, RS_SYSTEMATIC>();
+  }
+}
+
+template <typename T, typename V>
+cudaError_t dispatch(const Scratch& s, int scheme, const T* lw, const FusedArgs& A,
+                     cudaStream_t st) {
+  switch (scheme) {
+    case RS_MULTINOMIAL: return launch_fused<T, V, RS_MULTINOMIAL>(s, lw, A, st);
+    case RS_STRATIFIED: return launch_fused<T, V, RS_STRATIFIED>(s, lw, A, st);
+    default: return launch_fused<T, V, RS_SYSTEMATIC>(s, lw, A, st);
+  }
+}
+
+const char* const kLblFused[4][3] = {
+    {"fused_multinomial_f32", "fused_stratified_f32", "fused_systematic_f32"},
+    {"fused_multinomial_f32c", "fused_stratified_f32c", "fused_systematic_f32c"},
+    {"fused_multinomial_f64", "fused_stratified_f64", "fused_systematic_f64"},
+    {"fused_multinomial_f64n", "fused_stratified_f64n", "fused_systematic_f64n"}};
+
+}  // namespace
+
+bool fused_available(const Scratch& s, int scheme, Acc acc) {
+  if (!s.coop) return false;
+  switch (acc) {
+    case Acc::F32: return capacity<float, float>(scheme) > 0;
+    case Acc::F32C: return capacity<float, float2>(scheme) > 0;
+    case Acc::F64: return capacity<double, float2>(scheme) > 0;
+    case Acc::F64N: return capacity<double, double>(scheme) > 0;
+  }
+  return false;
+}
+
+cudaError_t launch_fused_passes(const Scratch& s, int scheme, Acc acc, const void* logw,
+                                int64_t N, const Keys& keys, int32_t* a_out, int32_t* d,
+                                cudaStream_t st) {
+  FusedArgs A;
+  A.N = N;
+  A.keys = keys;
+  A.a = a_out;
+  A.d = d;
+  A.W = s.W;
+  A.guide = s.guide;
+  A.s_rec = s.rec;
+  A.P_rec = s.rec + (s.max_tiles + 2);
+  A.g = s.glob;
+  A.blockmax = s.blockmax;
+  A.err = s.err;
+  trace_mark(s.trace, kLblFused[static_cast<int>(acc)][scheme], st);
+  switch (acc) {
+    case Acc::F32:
+      return dispatch<float, float>(s, scheme, static_cast<const float*>(logw), A, st);
+    case Acc::F32C:
+      return dispatch<float, float2>(s, scheme, static_cast<const float*>(logw), A, st);
+    case Acc::F64:
+      return dispatch<double, float2>(s, scheme, static_cast<const double*>(logw), A, st);
+    case Acc::F64N:
+      return dispatch<double, double>(s, scheme, static_cast<const double*>(logw), A, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace rsk

@@ -15,7 +15,8 @@ struct ScanGlob {
   unsigned int ticket_iscan;
   unsigned int batch_next;   // work counter of the batched kernel (self-resetting)
   unsigned int batch_ticket;
-  unsigned int pad[3];
+  unsigned int bar_count;    // grid-barrier arrivals of the fused kernel (0 between launches)
+  unsigned int pad[2];
   double2 S_raw;             // total, in the accumulator type of the call
   double2 scale_raw;         // N / total, in the accumulator type of the call
 };
@@ -36,7 +37,7 @@ inline void trace_mark(Trace* t, const char* label, cudaStream_t st) {
   }
 }
 
-constexpr int kBatchMaxTiles = 256;  // batched filters hold at most 256 * 4096 = 2^20 particles
+constexpr int64_t kBatchMaxN = 1 << 20;  // particles of one filter of a batched call, at most
 
 struct Scratch {
   Trace* trace;      // nullptr unless tracing is enabled
@@ -62,18 +63,30 @@ struct Scratch {
   int64_t max_n;
   int64_t max_tiles;
   int max_blocks;    // grid of the max pass
+  int coop;          // the device supports cooperative launches
+  int launch_mode;   // RS_LAUNCH_AUTO / RS_LAUNCH_FUSED / RS_LAUNCH_SEPARATE
 };
 
 // Accumulation of the scan-based schemes: binary32, two-float over binary32 inputs,
 // double-float over binary64 inputs (binary32 pipes), native binary64 (FP64 pipe).
 enum class Acc { F32, F32C, F64, F64N };
 
-// scan.cu
+struct Keys;
+
+// scan.cu (fused: the three passes as one cooperative kernel, see fused.cu)
 cudaError_t launch_scan_resample(const Scratch& s, int scheme, Acc acc, const void* logw,
                                  int64_t N, uint64_t seed, uint64_t step, uint32_t filter,
-                                 int32_t* a_out, int32_t* d_or_null, cudaStream_t st);
+                                 int32_t* a_out, int32_t* d_or_null, bool fused,
+                                 cudaStream_t st);
 cudaError_t launch_cumulative_weights(const Scratch& s, Acc acc, const void* logw, int64_t N,
                                       void* W_out, double* log_total, cudaStream_t st);
+
+// fused.cu: max, tile sums, tile prefixes and emission in one cooperative launch;
+// fused_available is false when the device cannot launch it.
+bool fused_available(const Scratch& s, int scheme, Acc acc);
+cudaError_t launch_fused_passes(const Scratch& s, int scheme, Acc acc, const void* logw,
+                                int64_t N, const Keys& keys, int32_t* a_out, int32_t* d,
+                                cudaStream_t st);
 
 // batched.cu
 cudaError_t launch_batched(const Scratch& s, int scheme, Acc acc, const void* logw,
@@ -96,6 +109,8 @@ cudaError_t launch_prepermute(const Scratch& s, const int32_t* a, int64_t N, int
                               bool init, cudaStream_t st);
 cudaError_t launch_permute(const Scratch& s, const int32_t* a, const int32_t* d, int64_t N,
                            int32_t* c, cudaStream_t st);
+cudaError_t launch_permute_sorted(const Scratch& s, const int32_t* a, const int32_t* d, int64_t N,
+                                  int32_t* c, cudaStream_t st);
 cudaError_t launch_offspring(const Scratch& s, const int32_t* a, int64_t N, int32_t* o,
                              cudaStream_t st);
 cudaError_t launch_inclusive_scan_i32(const Scratch& s, const int32_t* o, int64_t N,

@@ -95,7 +95,7 @@ extern "C" int rs_systematic_noalloc(int dtype, const void* logw_dev, int64_t N,
   cudaError_t e = cudaGetLastError();
   if (e == cudaSuccess)
     e = launch_scan_resample(s, RS_SYSTEMATIC, dtype == RS_F64 ? Acc::F64 : Acc::F32, logw_dev, N,
-                             seed, step, 0u, ancestors_dev, nullptr, cs);
+                             seed, step, 0u, ancestors_dev, nullptr, false, cs);
   if (e == cudaSuccess && status_dev) {
     noalloc_end_kernel<<<1, 1, 0, cs>>>(status_dev);
     e = cudaGetLastError();

@@ -18,27 +18,65 @@ namespace {
 // The walks start at indices absent from d and d is injective on claimed slots, so the
 // walks are disjoint and end at distinct unclaimed slots (the termination argument of
 // Appendix C): they only read d, and every slot of c is written exactly once, in any order.
+// kCoherent: a and d were written earlier in the same kernel launch (by other CTAs), so they
+// are read through L2 only.
+template <bool kCoherent>
+__device__ __forceinline__ int32_t ld_i32(const int32_t* p) {
+  if constexpr (kCoherent) return __ldcg(p); else return *p;
+}
+template <bool kCoherent = false>
 __device__ __forceinline__ void permute_one(const int32_t* __restrict__ a,
                                             const int32_t* __restrict__ d, int64_t n,
                                             int32_t* __restrict__ c, int64_t i, int* err) {
   const int32_t sentinel = static_cast<int32_t>(n);
-  const int32_t ai = a[i];
+  const int32_t ai = ld_i32<kCoherent>(a + i);
   if (ai < 0 || ai >= n) {
     flag_error(err, RS_ERR_ARG);
     return;
   }
-  if (d[i] != sentinel) c[i] = static_cast<int32_t>(i);
-  if (d[ai] != static_cast<int32_t>(i)) {
+  if (ld_i32<kCoherent>(d + i) != sentinel) c[i] = static_cast<int32_t>(i);
+  if (ld_i32<kCoherent>(d + ai) != static_cast<int32_t>(i)) {
     int64_t x = i;
     int64_t steps = 0;
     for (;;) {
-      const int32_t dx = d[x];
+      const int32_t dx = ld_i32<kCoherent>(d + x);
       if (dx == sentinel) break;
       if (dx < 0 || dx > sentinel || ++steps > n) {  // only a corrupted d can get here
         flag_error(err, RS_ERR_ARG);
         return;
       }
       x = dx;
+    }
+    c[x] = ai;
+  }
+}
+
+// The same slot when a is non-decreasing and d holds its claims (the systematic and stratified
+// ancestries of Code 11): the lowest claimant of particle a_i is the first position of its
+// run, so the claim of position i failed exactly when i > 0 and a_{i-1} = a_i. That replaces
+// the dependent load of d[a_i] by a load next to a_i; the writes are those of permute_one.
+__device__ __forceinline__ void permute_sorted_one(const int32_t* __restrict__ a,
+                                                   const int32_t* __restrict__ d, int64_t n,
+                                                   int32_t* __restrict__ c, int64_t i, int* err) {
+  const int32_t sentinel = static_cast<int32_t>(n);
+  const int32_t ai = a[i];
+  if (ai < 0 || ai >= n) {
+    flag_error(err, RS_ERR_ARG);
+    return;
+  }
+  const int32_t di = d[i];
+  if (di != sentinel) c[i] = static_cast<int32_t>(i);
+  if (i > 0 && a[i - 1] == ai) {
+    int64_t x = i;
+    int32_t dx = di;
+    int64_t steps = 0;
+    while (dx != sentinel) {
+      if (dx < 0 || dx > sentinel || ++steps > n) {  // only a corrupted d can get here
+        flag_error(err, RS_ERR_ARG);
+        return;
+      }
+      x = dx;
+      dx = d[x];
     }
     c[x] = ai;
   }

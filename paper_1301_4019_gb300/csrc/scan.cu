@@ -280,14 +280,22 @@ const char* const kLblW[4] = {"emit_W_f32", "emit_W_f32c", "emit_W_f64", "emit_W
 const char* const kLblSearch[4] = {"search_f32", "search_f32c", "search_f64", "search_f64n"};
 
 template <typename T, typename V>
-cudaError_t run_scan(const Scratch& s, int scheme, const T* lw, int64_t N, uint64_t seed,
-                     uint64_t step, uint32_t filter, int32_t* a_out, int32_t* d,
-                     cudaStream_t st) {
+cudaError_t run_scan(const Scratch& s, int scheme, Acc acc, const T* lw, int64_t N,
+                     uint64_t seed, uint64_t step, uint32_t filter, int32_t* a_out, int32_t* d,
+                     bool fused, cudaStream_t st) {
   const int tiles = static_cast<int>((N + kTile - 1) / kTile);
   double2* s_rec = s.rec;
   double2* P_rec = s.rec + (s.max_tiles + 2);
   const Keys keys = make_keys(seed, step, filter, static_cast<uint32_t>(scheme));
   constexpr int ai = Path<T, V>::id;
+  if (fused) {
+    cudaError_t e = launch_fused_passes(s, scheme, acc, lw, N, keys, a_out, d, st);
+    if (e != cudaSuccess || scheme != RS_MULTINOMIAL) return e;
+    trace_mark(s.trace, kLblSearch[ai], st);
+    search_kernel<T, V><<<static_cast<int>((N + kBlock - 1) / kBlock), kBlock, 0, st>>>(
+        static_cast<const V*>(s.W), s.guide, N, s.glob, keys, a_out, d);
+    return cudaGetLastError();
+  }
   trace_mark(s.trace, kLblMax[ai], st);
   max_kernel<T><<<max_grid(N, s.max_blocks), kBlock, 0, st>>>(
       lw, N, s.glob, s.blockmax, s.err, scheme == RS_MULTINOMIAL ? d : nullptr);
@@ -334,20 +342,20 @@ cudaError_t run_cumw(const Scratch& s, const T* lw, int64_t N, OUT* W_out, doubl
 
 cudaError_t launch_scan_resample(const Scratch& s, int scheme, Acc acc, const void* logw,
                                  int64_t N, uint64_t seed, uint64_t step, uint32_t filter,
-                                 int32_t* a_out, int32_t* d, cudaStream_t st) {
+                                 int32_t* a_out, int32_t* d, bool fused, cudaStream_t st) {
   switch (acc) {
     case Acc::F32:
-      return run_scan<float, float>(s, scheme, static_cast<const float*>(logw), N, seed, step,
-                                    filter, a_out, d, st);
+      return run_scan<float, float>(s, scheme, acc, static_cast<const float*>(logw), N, seed,
+                                    step, filter, a_out, d, fused, st);
     case Acc::F32C:
-      return run_scan<float, float2>(s, scheme, static_cast<const float*>(logw), N, seed, step,
-                                     filter, a_out, d, st);
+      return run_scan<float, float2>(s, scheme, acc, static_cast<const float*>(logw), N, seed,
+                                     step, filter, a_out, d, fused, st);
     case Acc::F64:
-      return run_scan<double, float2>(s, scheme, static_cast<const double*>(logw), N, seed,
-                                      step, filter, a_out, d, st);
+      return run_scan<double, float2>(s, scheme, acc, static_cast<const double*>(logw), N, seed,
+                                      step, filter, a_out, d, fused, st);
     case Acc::F64N:
-      return run_scan<double, double>(s, scheme, static_cast<const double*>(logw), N, seed,
-                                      step, filter, a_out, d, st);
+      return run_scan<double, double>(s, scheme, acc, static_cast<const double*>(logw), N, seed,
+                                      step, filter, a_out, d, fused, st);
   }
   return cudaErrorInvalidValue;
 }

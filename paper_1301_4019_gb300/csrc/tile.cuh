@@ -117,9 +117,9 @@ template <> __device__ __forceinline__ float2 load_v_cg<float2>(const double2* p
   return __ldcg(reinterpret_cast<const float2*>(p));
 }
 
-// Element e of the tile owned by (warp, row, lane, q): warp*512 + row*128 + lane*4 + q.
+// Element e of the tile owned by (warp, row, lane, q): warp*kRows*128 + row*128 + lane*4 + q.
 __device__ __forceinline__ int tile_offset(int warp, int r, int lane, int q) {
-  return warp * 512 + r * 128 + lane * 4 + q;
+  return warp * (kRows * 128) + r * 128 + lane * 4 + q;
 }
 
 // The tile scan shared by the tile-sum and emit passes: val[r][q] = sum of the weights of
@@ -255,8 +255,22 @@ __device__ void tile_prefix_compute(const double2* s_rec, double2* P_rec, int T,
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int chunk = (T + kBlock - 1) / kBlock;
   const int t0 = min(T, tid * chunk), t1 = min(T, t0 + chunk);
+  // the first kCache tile totals of the chunk stay in registers (T <= 4 * kBlock: all)
+  constexpr int kCache = 4;
+  double cache[kCache];
+#pragma unroll
+  for (int k = 0; k < kCache; ++k)
+    cache[k] = (t0 + k < t1) ? vto_double(load_v_cg<V>(s_rec + t0 + k)) : 0.0;
+  auto tot = [&](int t) -> double {
+    const int k = t - t0;
+    double v = 0.0;
+#pragma unroll
+    for (int q = 0; q < kCache; ++q)
+      if (q == k) v = cache[q];
+    return k < kCache ? v : vto_double(load_v_cg<V>(s_rec + t));
+  };
   double local = 0.0;
-  for (int t = t0; t < t1; ++t) local = __dadd_rn(local, vto_double(load_v_cg<V>(s_rec + t)));
+  for (int t = t0; t < t1; ++t) local = __dadd_rn(local, tot(t));
   double incl = local;
 #pragma unroll
   for (int dd = 1; dd < 32; dd <<= 1) {
@@ -271,7 +285,7 @@ __device__ void tile_prefix_compute(const double2* s_rec, double2* P_rec, int T,
   for (int k = 0; k < warp; ++k) wp = __dadd_rn(wp, sh_sum[k]);
   const double start = __dadd_rn(wp, excl);
   double endv = start;  // end value of this thread's chunk, for the running maximum
-  for (int t = t0; t < t1; ++t) endv = __dadd_rn(endv, vto_double(load_v_cg<V>(s_rec + t)));
+  for (int t = t0; t < t1; ++t) endv = __dadd_rn(endv, tot(t));
   double im = endv;
 #pragma unroll
   for (int dd = 1; dd < 32; dd <<= 1) {
@@ -287,7 +301,7 @@ __device__ void tile_prefix_compute(const double2* s_rec, double2* P_rec, int T,
   double p = start;
   for (int t = t0; t < t1; ++t) {
     store_v<V>(P_rec + t, vfrom_double(p > prevmax ? p : prevmax, V()));
-    p = __dadd_rn(p, vto_double(load_v_cg<V>(s_rec + t)));
+    p = __dadd_rn(p, tot(t));
   }
   if (t1 == T && t0 < T) store_v<V>(P_rec + T, vfrom_double(p > prevmax ? p : prevmax, V()));
   __syncthreads();
@@ -542,13 +556,18 @@ __device__ __forceinline__ void emit_tile_W_guide(const T* __restrict__ lw, int6
   }
 }
 
+// Loads of W and G; kCoherent: written earlier in the same kernel launch, read through L2.
+template <bool kCoherent, typename X> __device__ __forceinline__ X ld_val(const X* p) {
+  if constexpr (kCoherent) return __ldcg(p); else return __ldg(p);
+}
+
 // Multinomial search of output i through the guide table (same result as search_one).
-template <typename T, typename V>
+template <typename T, typename V, bool kCoherent = false>
 __device__ __forceinline__ int32_t search_one_guided(const V* __restrict__ W,
                                                      const int32_t* __restrict__ G, int64_t n,
                                                      const Guide& gd, const Keys& keys,
                                                      int64_t i) {
-  const V S = W[n - 1];
+  const V S = ld_val<kCoherent>(W + (n - 1));
   const auto U = Path<T, V>::draw_u(draw(keys, static_cast<uint32_t>(i), 0u));
   const V u = vtimes_u(S, U);
   // bucket b with e_b <= u < e_{b+1}
@@ -559,12 +578,12 @@ __device__ __forceinline__ int32_t search_one_guided(const V* __restrict__ W,
   while (b < n - 1 && vle(edge_as<V>(guide_edge(b + 1, gd, n)), u) && ++steps < 64) ++b;
   int64_t lo = 0, hi = n;
   if (steps < 64) {
-    lo = __ldg(G + b);
-    hi = static_cast<int64_t>(__ldg(G + b + 1)) + 1;
+    lo = ld_val<kCoherent>(G + b);
+    hi = static_cast<int64_t>(ld_val<kCoherent>(G + b + 1)) + 1;
   }
   while (lo < hi) {
     const int64_t mid = lo + ((hi - lo) >> 1);
-    if (vle(W[mid], u)) lo = mid + 1; else hi = mid;
+    if (vle(ld_val<kCoherent>(W + mid), u)) lo = mid + 1; else hi = mid;
   }
   return static_cast<int32_t>(lo < n ? lo : n - 1);
 }
