@@ -173,14 +173,11 @@ int rs_permute(rs_handle* h, const int32_t* a_dev, int64_t N, int32_t* c_dev, vo
  *                        meet at grid-wide barriers (bounded waits: RS_ERR_TIMEOUT through
  *                        rs_last_error); used when the device supports cooperative launches,
  *                        else the separate kernels run.
- *   RS_LAUNCH_AUTO     : (default) fused up to RS_FUSED_AUTO_MAX_N particles, where launch
- *                        latency dominates, separate kernels above (where the separate
- *                        kernels' larger grids hide more memory latency).
+ *   RS_LAUNCH_AUTO     : (default) fused when the device supports cooperative launches.
  * Host-only; RS_ERR_ARG for an unknown mode. The setting belongs to the handle. */
 #define RS_LAUNCH_AUTO 0
 #define RS_LAUNCH_FUSED 1
 #define RS_LAUNCH_SEPARATE 2
-#define RS_FUSED_AUTO_MAX_N (1 << 16)
 int rs_set_launch_mode(rs_handle* h, int mode);
 
 /* B* = log(eps) / log(1 - beta) of Eq. (B) (Section 2.1), rounded up: the number of
@@ -210,7 +207,7 @@ const char* rs_trace_label(const rs_handle* h, int i);
  * device memory -- code running under another framework's memory pool or allocator hooks,
  * plugins whose host forbids cudaMalloc after start-up, real-time loops that must never wait
  * on the allocator. It computes exactly what rs_resample(RS_SYSTEMATIC, permute = 0) computes
- * (same kernels, same results) without a handle: its scratch (about 43 KB) is a static
+ * (same kernels, same results) without a handle: its scratch (about 140 KB) is a static
  * device array of the library, which every GPU that loads the library keeps until the
  * process exits. The caller passes only inputs and outputs:
  *   dtype, logw_dev, N : as for rs_resample; 1 <= N <= RS_NOALLOC_MAX_N, larger N returns

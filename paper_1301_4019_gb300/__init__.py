@@ -43,7 +43,6 @@ EXPORTED = [
 ]
 NOALLOC_MAX_N = 1 << 22
 LAUNCH_AUTO, LAUNCH_FUSED, LAUNCH_SEPARATE = 0, 1, 2
-FUSED_AUTO_MAX_N = 1 << 16
 
 _lock = threading.Lock()
 _lib = None

@@ -198,9 +198,7 @@ int rs_resample(rs_handle* h, int scheme, int dtype, const void* logw_dev, int64
     case RS_SYSTEMATIC: {
       const rsk::Acc acc = accumulation(dtype, o.prec);
       const int mode = h->s.launch_mode;
-      const bool fused = mode != RS_LAUNCH_SEPARATE &&
-                         (mode == RS_LAUNCH_FUSED || N <= RS_FUSED_AUTO_MAX_N) &&
-                         rsk::fused_available(h->s, scheme, acc);
+      const bool fused = mode != RS_LAUNCH_SEPARATE && rsk::fused_available(h->s, scheme, acc);
       e = rsk::launch_scan_resample(h->s, scheme, acc, logw_dev, N, seed, step, o.filter, a_out,
                                     d, fused, s);
       break;

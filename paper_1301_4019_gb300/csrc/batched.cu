@@ -5,7 +5,7 @@
 // time is launch-bound, and giving each filter to one CTA serialises its passes and leaves the
 // largest (or, for Metropolis, the highest-B) filters as a long tail. Here the work units are
 // the tiles and the particles of all filters together:
-//   plan    : tiles per filter (4096 particles, starting at the filter's first particle) and
+//   plan    : tiles per filter (1024 particles, starting at the filter's first particle) and
 //             their prefix over filters; per-filter maxima reset            (1 CTA)
 //   max     : per tile, maximum log-weight, combined per filter by an atomic max of keys
 //   sums    : per tile, the tile scan total                               (tile-parallel)
@@ -491,7 +491,7 @@ cudaError_t launch_batched(const Scratch& s, int scheme, Acc acc, const void* lo
     b.err = s.err;
     trace_mark(s.trace, "batch_plan", st);
     batch_plan_kernel<<<1, 1024, 0, st>>>(b);
-    // every filter adds at most one partial tile to the max_n / 4096 full ones
+    // every filter adds at most one partial tile to the max_n / kTile full ones
     const int64_t cap_tiles = s.max_n / kTile + F + 1;
     switch (acc) {
       case Acc::F32:

@@ -1,15 +1,13 @@
-// fused.cu -- the three passes of the multinomial, stratified and systematic resamplers of
-// one filter (max, tile sums with tile prefixes, emission) as one persistent cooperative
-// kernel.
+// fused.cu -- the passes of the multinomial, stratified and systematic resamplers of one filter
+// (max, tile totals, tile prefixes, emission) as one persistent cooperative kernel.
 //
-// At the sizes of a particle filter (N ~ 2^20) each pass over the weights is short, so a chain
-// of three launches is dominated by per-launch latency and tails. Here one CTA set, all
-// resident at once (cooperative launch), runs the phases back to back, separated by
-// grid-wide barriers:  max -> tile sums -> tile prefixes (CTA 0) -> emission.
-// Each phase calls the same device functions as the multi-launch kernels on the same tiles,
-// so the results are identical. The latency-bound particle-parallel steps that follow (the
-// multinomial search, Permute) stay separate full-occupancy kernels: inside this grid, sized
-// by the emission's registers, they would run with a quarter of the threads in flight.
+// Each CTA owns a contiguous range of tiles; the CTAs are all resident at once (cooperative
+// launch) and meet at grid-wide barriers between the phases (see fused_body). The tile
+// prefixes are exact fixed-point sums, so they can be assembled in parallel from per-CTA
+// totals instead of by one CTA, and each phase calls the same device functions as the
+// separate kernels on the same tiles: the results are identical. The latency-bound
+// particle-parallel steps that follow (the multinomial search, Permute) stay separate
+// full-occupancy kernels.
 // A barrier waits at most kBarrierTimeoutNs (then it records RS_ERR_TIMEOUT and proceeds;
 // every phase stays bounds-checked, so the kernel still ends); the barrier counter returns
 // to 0 at the end of every launch.
@@ -107,13 +105,50 @@ struct FusedArgs {
   int32_t* d;      // Prepermute claims, or nullptr
   void* W;         // multinomial cumulative weights
   int32_t* guide;  // multinomial guide table
-  double2* s_rec;
-  double2* P_rec;
+  double2* s_rec;  // tile totals (accumulator type)
+  double2* P_rec;  // tile prefixes: exact in-range prefixes (u128), then rounded P_t
+  u128* agg;       // per-CTA exact totals (gridDim.x entries)
   ScanGlob* g;
   double* blockmax;  // per-CTA maxima (gridDim.x entries)
   int* err;
 };
 
+__device__ __forceinline__ u128 shfl_xor_u128(u128 v, int m) {
+  const uint64_t hi = __shfl_xor_sync(0xffffffffu, static_cast<uint64_t>(v >> 64), m);
+  const uint64_t lo = __shfl_xor_sync(0xffffffffu, static_cast<uint64_t>(v), m);
+  return (static_cast<u128>(hi) << 64) | lo;
+}
+__device__ __forceinline__ u128 ld_u128_cg(const u128* p) {
+  const ulonglong2 v = __ldcg(reinterpret_cast<const ulonglong2*>(p));
+  return (static_cast<u128>(v.y) << 64) | v.x;
+}
+__device__ __forceinline__ void st_u128(u128* p, u128 v) {
+  *reinterpret_cast<ulonglong2*>(p) =
+      make_ulonglong2(static_cast<uint64_t>(v), static_cast<uint64_t>(v >> 64));
+}
+
+// Block-wide sum of u128 (every thread gets the result).
+__device__ __forceinline__ u128 block_sum_u128(u128 v, u128* sh) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += shfl_xor_u128(v, o);
+  __syncthreads();
+  if (lane == 0) sh[warp] = v;
+  __syncthreads();
+  u128 t = 0;
+  for (int k = 0; k < kWarps; ++k) t += sh[k];
+  return t;
+}
+
+// CTA c owns the contiguous tiles [c T / G, (c+1) T / G) of the T tiles (G = gridDim.x <= T):
+//   phase 1  maximum over its particles -> barrier -> M = maximum over the CTAs;
+//   phase 2  tile totals s_t of its tiles, in order, and their exact running sum in fixed
+//            point (the in-range prefix of each tile, and the CTA total) -> barrier;
+//   phase 3  exclusive sum of the totals of the CTAs before it, then P_t = RN(that + in-range
+//            prefix) for its tiles (the last CTA also P_T and W^N, N / W^N) -> barrier;
+//   phase 4  emission of its tiles.
+// P_t is the exact sum of the tile totals before t rounded once, as in tile_prefix_compute, so
+// the results equal those of the separate kernels.
 template <typename T, typename V, int SCHEME>
 __device__ __forceinline__ void fused_body(const T* __restrict__ lw, const FusedArgs& A,
                                            unsigned int& target) {
@@ -121,20 +156,24 @@ __device__ __forceinline__ void fused_body(const T* __restrict__ lw, const Fused
   __shared__ V sh_max[kWarps];
   __shared__ float2 sh_tab[64];
   __shared__ long long sh_key[kWarps];
+  __shared__ u128 sh_sum[kWarps];
   __shared__ Guide sh_gd;
   const int64_t N = A.N;
   const int T_tiles = static_cast<int>((N + kTile - 1) / kTile);
+  const int G = static_cast<int>(gridDim.x), c = static_cast<int>(blockIdx.x);
+  const int t0 = static_cast<int>(static_cast<int64_t>(c) * T_tiles / G);
+  const int t1 = static_cast<int>(static_cast<int64_t>(c + 1) * T_tiles / G);
+  const int64_t e0 = static_cast<int64_t>(t0) * kTile;
+  const int64_t e1 = min(static_cast<int64_t>(t1) * kTile, N);
   const bool vec = (reinterpret_cast<uintptr_t>(lw) & 15u) == 0;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 
   // ---- phase 1: maximum log-weight (and the Prepermute sentinel of the multinomial claims) --
   {
     long long m = fkey(neg_inf<T>());
     bool bad = false;
-    for (int64_t i0 = 4 * (static_cast<int64_t>(blockIdx.x) * kBlock + threadIdx.x); i0 < N;
-         i0 += 4 * static_cast<int64_t>(gridDim.x) * kBlock) {
+    for (int64_t i0 = e0 + 4 * static_cast<int64_t>(threadIdx.x); i0 < e1; i0 += 4 * kBlock) {
       T x[4];
-      load4(lw, i0, 0, N, vec, x);
+      load4(lw, i0, 0, e1, vec, x);
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
         const bool nan = x[q] != x[q];
@@ -142,61 +181,86 @@ __device__ __forceinline__ void fused_body(const T* __restrict__ lw, const Fused
         const long long k = fkey(x[q]);
         if (!nan && k > m) m = k;
         if constexpr (SCHEME == RS_MULTINOMIAL) {
-          if (A.d && i0 + q < N) A.d[i0 + q] = static_cast<int32_t>(N);
+          if (A.d && i0 + q < e1) A.d[i0 + q] = static_cast<int32_t>(N);
         }
       }
     }
     if (bad) flag_error(A.err, RS_ERR_NONFINITE);
     const long long bm = block_max_key(m, sh_key);
-    if (threadIdx.x == 0) A.blockmax[blockIdx.x] = fvalue(bm, T());
+    if (threadIdx.x == 0) A.blockmax[c] = fvalue(bm, T());
   }
   grid_barrier(&A.g->bar_count, target, A.err);
   double M;
   {
     long long m = fkey(-static_cast<double>(INFINITY));
-    for (int b = threadIdx.x; b < static_cast<int>(gridDim.x); b += kBlock) {
+    for (int b = threadIdx.x; b < G; b += kBlock) {
       const long long y = fkey(__ldcg(A.blockmax + b));
       m = y > m ? y : m;
     }
     M = fvalue(block_max_key(m, sh_key), 0.0);
   }
   const bool zero = !(M > -DBL_MAX);
+  u128* LP = reinterpret_cast<u128*>(A.P_rec);
 
-  // ---- phase 2: tile sums -----------------------------------------------------------------
+  // ---- phase 2: tile totals and their exact running sum ---------------------------------
   const WeightCtx wc = make_ctx<T, V>(zero ? 0.0 : M, sh_tab);
   if (!zero) {
-    for (int t = blockIdx.x; t < T_tiles; t += gridDim.x) {
+    u128 run = 0;  // meaningful in thread 0
+    for (int t = t0; t < t1; ++t) {
       const int64_t base = static_cast<int64_t>(t) * kTile;
       V val[kRows][4];
       tile_raw_values<T, V>(lw, 0, N, base, wc, vec, val, sh_tot);
       const V tm = tile_total<V>(val, base, 0, N, sh_max);
-      if (threadIdx.x == 0) store_v<V>(A.s_rec + t, tm);
+      if (threadIdx.x == 0) {
+        store_v<V>(A.s_rec + t, tm);
+        st_u128(LP + t, run);
+        run += to_fixed(tm);
+      }
     }
+    if (threadIdx.x == 0) st_u128(A.agg + c, run);
   }
   grid_barrier(&A.g->bar_count, target, A.err);
 
-  // ---- phase 3: tile prefixes, W^N, N / W^N (CTA 0) ------------------------------------------
-  if (blockIdx.x == 0) {
-    if (zero) {
-      if (threadIdx.x == 0) {
-        A.g->S_d = 0.0;
-        flag_error(A.err, RS_ERR_ZERO_WEIGHT);
-      }
-    } else {
-      tile_prefix_compute<V>(A.s_rec, A.P_rec, T_tiles, N, reinterpret_cast<V*>(&A.g->S_raw),
-                             reinterpret_cast<V*>(&A.g->scale_raw), &A.g->S_d);
-      if (threadIdx.x == 0 && !(A.g->S_d > 0.0)) flag_error(A.err, RS_ERR_ZERO_WEIGHT);
+  // ---- phase 3: tile prefixes P_t of this CTA's tiles (the last CTA: P_T, W^N, N / W^N) ----
+  if (zero) {
+    if (c == 0 && threadIdx.x == 0) {
+      A.g->S_d = 0.0;
+      A.g->M = M;
+      flag_error(A.err, RS_ERR_ZERO_WEIGHT);
     }
-    if (threadIdx.x == 0) A.g->M = M;  // read by the search kernel
+  } else {
+    u128 part = 0;
+    for (int k = threadIdx.x; k < c; k += kBlock) part += ld_u128_cg(A.agg + k);
+    const u128 CP = block_sum_u128(part, sh_sum);
+    for (int t = t0 + threadIdx.x; t < t1; t += kBlock) {
+      const u128 lp = ld_u128_cg(LP + t);
+      store_v<V>(A.P_rec + t, fixed_to(CP + lp, V()));
+    }
+    if (c == G - 1) {
+      if (threadIdx.x == 0)
+        store_v<V>(A.P_rec + T_tiles, fixed_to(CP + ld_u128_cg(A.agg + c), V()));
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        const V Pm = load_v_cg<V>(A.P_rec + (T_tiles - 1));
+        const V Pn = load_v_cg<V>(A.P_rec + T_tiles);
+        const V st = load_v_cg<V>(A.s_rec + (T_tiles - 1));
+        const V S = vclamp(vadd(Pm, st), Pm, Pn);
+        const double Sd = vto_double(S);
+        store_v<V>(&A.g->S_raw, S);
+        store_v<V>(&A.g->scale_raw, vfrom_double(__ddiv_rn(static_cast<double>(N), Sd), V()));
+        A.g->S_d = Sd;
+        A.g->M = M;  // read by the search kernel
+        if (!(Sd > 0.0)) flag_error(A.err, RS_ERR_ZERO_WEIGHT);
+      }
+    }
   }
   grid_barrier(&A.g->bar_count, target, A.err);
   const double Sd = __ldcg(&A.g->S_d);
 
-  // ---- phase 4: emission ------------------------------------------------------------------------
+  // ---- phase 4: emission of this CTA's tiles -----------------------------------------------
   if (zero || !(Sd > 0.0)) {  // all weights zero (flagged): every particle keeps itself
     if constexpr (SCHEME != RS_MULTINOMIAL) {  // (the search kernel writes the identity)
-      for (int64_t i = static_cast<int64_t>(blockIdx.x) * kBlock + threadIdx.x; i < N;
-           i += static_cast<int64_t>(gridDim.x) * kBlock) {
+      for (int64_t i = e0 + threadIdx.x; i < e1; i += kBlock) {
         A.a[i] = static_cast<int32_t>(i);
         if (A.d) A.d[i] = static_cast<int32_t>(i);
       }
@@ -208,7 +272,7 @@ __device__ __forceinline__ void fused_body(const T* __restrict__ lw, const Fused
     if (threadIdx.x == 0) sh_gd = make_guide(Sd, N);
     __syncthreads();
   }
-  for (int t = blockIdx.x; t < T_tiles; t += gridDim.x) {
+  for (int t = t0; t < t1; ++t) {
     const int64_t base = static_cast<int64_t>(t) * kTile;
     const V Pt = load_v_cg<V>(A.P_rec + t), Pn = load_v_cg<V>(A.P_rec + t + 1);
     const V Pm = t > 0 ? load_v_cg<V>(A.P_rec + t - 1) : vzero(V());
@@ -222,7 +286,6 @@ __device__ __forceinline__ void fused_body(const T* __restrict__ lw, const Fused
                                                        sh_max);
     }
   }
-
 }
 
 template <typename T, typename V, int SCHEME>
@@ -317,6 +380,7 @@ cudaError_t launch_fused_passes(const Scratch& s, int scheme, Acc acc, const voi
   A.guide = s.guide;
   A.s_rec = s.rec;
   A.P_rec = s.rec + (s.max_tiles + 2);
+  A.agg = reinterpret_cast<u128*>(s.irec);  // (max_tiles + 2) entries >= gridDim.x
   A.g = s.glob;
   A.blockmax = s.blockmax;
   A.err = s.err;

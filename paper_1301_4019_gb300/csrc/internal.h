@@ -59,7 +59,7 @@ struct Scratch {
   double2* batch_s_rec;       // batch_tile_cap
   double2* batch_P_rec;       // batch_tile_cap + max_filters
   int64_t max_filters;        // max(1024, max_n / 16)
-  int64_t batch_tile_cap;     // max_n / 4096 + max_filters + 1
+  int64_t batch_tile_cap;     // max_n / kTile + max_filters + 1
   int64_t max_n;
   int64_t max_tiles;
   int max_blocks;    // grid of the max pass

@@ -4,10 +4,10 @@
 // Each call makes three passes over the log-weights (Appendix E renormalisation, Code 4
 // primitives):
 //   1. max pass      : M = max_i lw_i (last-CTA reduction), NaN/+inf detection.
-//   2. tile-sum pass : per tile of 4096 particles, the weights w_i = exp(lw_i - M) are
+//   2. tile-sum pass : per tile of 1024 particles, the weights w_i = exp(lw_i - M) are
 //                      prefix-summed in the accumulator type; the tile total is written and
-//                      the last CTA to finish scans the tile totals (binary64) into tile
-//                      prefixes P_t and the total W^N.
+//                      the last CTA to finish sums the tile totals exactly (128-bit fixed
+//                      point) into tile prefixes P_t, each rounded once, and the total W^N.
 //   3. emit pass     : the same tile scan is recomputed bit for bit, offset by P_t, and
 //                      turned into cumulative offspring O_i (systematic / stratified) with a
 //                      direct Code-11 scatter of the ancestors and the Prepermute claims; or

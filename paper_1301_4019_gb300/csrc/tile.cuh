@@ -1,5 +1,5 @@
 // tile.cuh -- the tile scan shared by the single-filter and batched scan-based resamplers:
-// weights per (input type, accumulator type), the 4096-particle tile prefix sum with its
+// weights per (input type, accumulator type), the 1024-particle tile prefix sum with its
 // exact running maximum, and the cumulative offspring of Codes 7 and 8.
 #pragma once
 
@@ -121,6 +121,12 @@ template <> __device__ __forceinline__ float2 load_v_cg<float2>(const double2* p
 __device__ __forceinline__ int tile_offset(int warp, int r, int lane, int q) {
   return warp * (kRows * 128) + r * 128 + lane * 4 + q;
 }
+// Valid elements of the tile starting at `base` of a sequence ending at N (tiles start at or
+// after the sequence start): offsets 0 .. count-1.
+__device__ __forceinline__ int tile_count(int64_t base, int64_t N) {
+  const int64_t c = N - base;
+  return c < kTile ? static_cast<int>(c) : kTile;
+}
 
 // The tile scan shared by the tile-sum and emit passes: val[r][q] = sum of the weights of
 // the tile up to and including the element (r, q) of this thread, as computed by a fixed
@@ -168,13 +174,14 @@ __device__ __forceinline__ void tile_raw_values(const T* __restrict__ lw, int64_
     for (int q = 0; q < 4; ++q) val[r][q] = vadd(pw, val[r][q]);
 }
 
-// Running maximum of the tile values in element order (exact), restricted to positions in
-// [lo, N) (other positions keep their raw value and are never used). Returns, through sh_max, the
+// Running maximum of the tile values in element order (exact), restricted to the tile's valid
+// positions (tile_count; other positions keep their raw value and are never used). Returns, through sh_max, the
 // maximum of each warp's valid values; prevmax = maximum over the previous warps.
 template <typename V>
 __device__ __forceinline__ void tile_running_max(V (&val)[kRows][4], int64_t base, int64_t lo,
                                                  int64_t N, V* sh_max, V& prevmax) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int cnt = tile_count(base, N);
   V cm = vzero(V());
 #pragma unroll
   for (int r = 0; r < kRows; ++r) {
@@ -182,8 +189,7 @@ __device__ __forceinline__ void tile_running_max(V (&val)[kRows][4], int64_t bas
     V m = vzero(V());
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-      const int64_t e = base + tile_offset(warp, r, lane, q);
-      const bool valid = e >= lo && e < N;
+      const bool valid = tile_offset(warp, r, lane, q) < cnt;
       if (valid) m = vmax(m, val[r][q]);
       x[q] = m;
     }
@@ -198,8 +204,7 @@ __device__ __forceinline__ void tile_running_max(V (&val)[kRows][4], int64_t bas
     const V before = vmax(em, cm);
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-      const int64_t e = base + tile_offset(warp, r, lane, q);
-      const bool valid = e >= lo && e < N;
+      const bool valid = tile_offset(warp, r, lane, q) < cnt;
       if (valid) val[r][q] = vmax(x[q], before);
     }
     cm = vmax(cm, vshfl(im, 31));
@@ -212,8 +217,7 @@ __device__ __forceinline__ void tile_running_max(V (&val)[kRows][4], int64_t bas
   for (int r = 0; r < kRows; ++r)
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-      const int64_t e = base + tile_offset(warp, r, lane, q);
-      const bool valid = e >= lo && e < N;
+      const bool valid = tile_offset(warp, r, lane, q) < cnt;
       if (valid) val[r][q] = vmax(val[r][q], prevmax);
     }
 }
@@ -240,70 +244,135 @@ __device__ __forceinline__ int32_t cum_offspring(V W, V S, V scale,
   return static_cast<int32_t>(o);
 }
 
-// Totals of one sequence of tiles (block-level, every thread of the CTA calls it):
-// P_0 = 0, P_{t+1} = P_t + s_t in binary64 over T tile totals s_t (each thread sums a
-// contiguous chunk, then a warp and a warp-sequential scan), made monotone by a running
-// maximum and rounded monotonically to the accumulator type. The total S is the cumulative
-// weight of the last particle exactly as the emit pass computes it,
-// clamp(P_{T-1} + s_{T-1}, P_{T-1}, P_T), so that particle receives O = N. Thread 0 writes
-// S, N / S and S (binary64) to the given pointers, then the CTA synchronises.
+// ---------------------------------------------------------------------------------------
+// Exact tile prefixes. Tile totals are non-negative and below 2^31 (each weight is at most
+// 1), so they are summed exactly in 128-bit fixed point with 96 fractional bits (only parts
+// below 2^-96 are dropped: at most T * 2^-96 in all, against a total of at least 1) and each
+// prefix is rounded once, to nearest, to the accumulator type. Integer arithmetic only: the
+// binary64 pipe of GB300 runs at 1/57 of the binary32 rate.
+// ---------------------------------------------------------------------------------------
+using u128 = unsigned __int128;
+constexpr int kFixFrac = 96;
+
+// m * 2^E (m < 2^53) as fixed point, truncated; negative when neg (two's complement).
+__device__ __forceinline__ u128 fixed_from_parts(uint64_t m, int E, bool neg) {
+  const int sh = E + kFixFrac;
+  u128 F = 0;
+  if (sh >= 0) F = static_cast<u128>(m) << sh;
+  else if (sh > -64) F = static_cast<u128>(m >> (-sh));
+  return neg ? static_cast<u128>(0) - F : F;
+}
+__device__ __forceinline__ u128 to_fixed(float v) {
+  const uint32_t b = __float_as_uint(v);
+  const int e = static_cast<int>((b >> 23) & 0xffu);
+  if (e == 0) return 0;  // zero (subnormals: below 2^-126, dropped)
+  return fixed_from_parts((b & 0x7fffffu) | 0x800000u, e - 150, (b >> 31) != 0);
+}
+__device__ __forceinline__ u128 to_fixed(double v) {
+  const uint64_t b = static_cast<uint64_t>(__double_as_longlong(v));
+  const int e = static_cast<int>((b >> 52) & 0x7ffu);
+  if (e == 0) return 0;
+  return fixed_from_parts((b & 0xfffffffffffffull) | 0x10000000000000ull, e - 1075,
+                          (b >> 63) != 0);
+}
+__device__ __forceinline__ u128 to_fixed(float2 v) { return to_fixed(v.x) + to_fixed(v.y); }
+
+// Round a non-negative fixed-point value to nearest (ties to even) with `bits` significant
+// bits: returns the IEEE bit pattern for the given exponent bias and fraction width.
+__device__ __forceinline__ uint64_t fixed_round_bits(u128 F, int bits, int bias) {
+  if (F == 0) return 0;
+  const uint64_t hi = static_cast<uint64_t>(F >> 64), lo = static_cast<uint64_t>(F);
+  const int p = hi ? 127 - __clzll(static_cast<long long>(hi)) : 63 - __clzll(static_cast<long long>(lo));
+  const int r = p - (bits - 1);  // bits below the kept significand
+  uint64_t mant;
+  bool up = false;
+  if (r <= 0) {
+    mant = static_cast<uint64_t>(F) << (-r);
+  } else {
+    mant = static_cast<uint64_t>(F >> r);
+    const bool half = ((F >> (r - 1)) & 1) != 0;
+    const bool sticky = r > 1 && (F & ((static_cast<u128>(1) << (r - 1)) - 1)) != 0;
+    up = half && (sticky || (mant & 1));
+  }
+  const uint64_t frac_mask = (1ull << (bits - 1)) - 1;
+  const uint64_t expo = static_cast<uint64_t>(p - kFixFrac + bias);
+  return ((expo << (bits - 1)) | (mant & frac_mask)) + (up ? 1 : 0);
+}
+__device__ __forceinline__ float fixed_to_float(u128 F) {
+  return __uint_as_float(static_cast<uint32_t>(fixed_round_bits(F, 24, 127)));
+}
+__device__ __forceinline__ double fixed_to_double(u128 F) {
+  return __longlong_as_double(static_cast<long long>(fixed_round_bits(F, 53, 1023)));
+}
+__device__ __forceinline__ float fixed_to_float_signed(u128 F) {
+  const bool neg = static_cast<int64_t>(static_cast<uint64_t>(F >> 64)) < 0;
+  const float x = fixed_to_float(neg ? static_cast<u128>(0) - F : F);
+  return neg ? -x : x;
+}
+__device__ __forceinline__ float fixed_to(u128 F, float) { return fixed_to_float(F); }
+__device__ __forceinline__ double fixed_to(u128 F, double) { return fixed_to_double(F); }
+__device__ __forceinline__ float2 fixed_to(u128 F, float2) {  // hi + lo, hi = RN(F)
+  const float hi = fixed_to_float(F);
+  return make_float2(hi, fixed_to_float_signed(F - to_fixed(hi)));
+}
+__device__ __forceinline__ u128 shfl_up_u128(u128 v, int d) {
+  const uint64_t hi = __shfl_up_sync(0xffffffffu, static_cast<uint64_t>(v >> 64), d);
+  const uint64_t lo = __shfl_up_sync(0xffffffffu, static_cast<uint64_t>(v), d);
+  return (static_cast<u128>(hi) << 64) | lo;
+}
+
+// Prefixes of one sequence of T tile totals s_t (block-level, every thread of the CTA calls
+// it): P_t = RN(s_0 + ... + s_{t-1}) for t = 0..T, the exact sums taken in fixed point (each
+// thread a contiguous chunk of tiles, then a warp scan and a scan over the warps: integer
+// adds, so the order does not matter). P is non-decreasing because the exact prefixes are and
+// rounding is monotone. The total S is the cumulative weight of the last particle exactly as
+// the emit pass computes it, clamp(P_{T-1} + s_{T-1}, P_{T-1}, P_T), so that particle
+// receives O = N. Thread 0 writes S, N / S and S (binary64) to the given pointers, then the
+// CTA synchronises.
 template <typename V>
 __device__ void tile_prefix_compute(const double2* s_rec, double2* P_rec, int T, int64_t N,
                                     V* S_out, V* scale_out, double* Sd_out) {
-  __shared__ double sh_sum[kWarps];
-  __shared__ double sh_max[kWarps];
+  __shared__ u128 sh_sum[kWarps];
+  constexpr int kGroup = 8;  // tile totals loaded together
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int chunk = (T + kBlock - 1) / kBlock;
   const int t0 = min(T, tid * chunk), t1 = min(T, t0 + chunk);
-  // the first kCache tile totals of the chunk stay in registers (T <= 4 * kBlock: all)
-  constexpr int kCache = 4;
-  double cache[kCache];
+  u128 cache[kGroup];  // the first group stays in registers
+  u128 local = 0;
+  for (int g = t0; g < t1; g += kGroup) {
+    u128 f[kGroup];
 #pragma unroll
-  for (int k = 0; k < kCache; ++k)
-    cache[k] = (t0 + k < t1) ? vto_double(load_v_cg<V>(s_rec + t0 + k)) : 0.0;
-  auto tot = [&](int t) -> double {
-    const int k = t - t0;
-    double v = 0.0;
+    for (int k = 0; k < kGroup; ++k) f[k] = (g + k < t1) ? to_fixed(load_v_cg<V>(s_rec + g + k)) : 0;
 #pragma unroll
-    for (int q = 0; q < kCache; ++q)
-      if (q == k) v = cache[q];
-    return k < kCache ? v : vto_double(load_v_cg<V>(s_rec + t));
-  };
-  double local = 0.0;
-  for (int t = t0; t < t1; ++t) local = __dadd_rn(local, tot(t));
-  double incl = local;
+    for (int k = 0; k < kGroup; ++k) {
+      local += f[k];
+      if (g == t0) cache[k] = f[k];
+    }
+  }
+  u128 incl = local;
 #pragma unroll
   for (int dd = 1; dd < 32; dd <<= 1) {
-    const double y = __shfl_up_sync(0xffffffffu, incl, dd);
-    if (lane >= dd) incl = __dadd_rn(y, incl);
+    const u128 y = shfl_up_u128(incl, dd);
+    if (lane >= dd) incl += y;
   }
-  double excl = __shfl_up_sync(0xffffffffu, incl, 1);
-  if (lane == 0) excl = 0.0;
   if (lane == 31) sh_sum[warp] = incl;
   __syncthreads();
-  double wp = 0.0;
-  for (int k = 0; k < warp; ++k) wp = __dadd_rn(wp, sh_sum[k]);
-  const double start = __dadd_rn(wp, excl);
-  double endv = start;  // end value of this thread's chunk, for the running maximum
-  for (int t = t0; t < t1; ++t) endv = __dadd_rn(endv, tot(t));
-  double im = endv;
+  u128 p = incl - local;
+  for (int k = 0; k < warp; ++k) p += sh_sum[k];
+  for (int g = t0; g < t1; g += kGroup) {
+    u128 f[kGroup];
 #pragma unroll
-  for (int dd = 1; dd < 32; dd <<= 1) {
-    const double y = __shfl_up_sync(0xffffffffu, im, dd);
-    if (lane >= dd) im = y > im ? y : im;
+    for (int k = 0; k < kGroup; ++k)
+      f[k] = (g == t0) ? cache[k] : ((g + k < t1) ? to_fixed(load_v_cg<V>(s_rec + g + k)) : 0);
+#pragma unroll
+    for (int k = 0; k < kGroup; ++k) {
+      if (g + k < t1) {
+        store_v<V>(P_rec + g + k, fixed_to(p, V()));
+        p += f[k];
+      }
+    }
   }
-  double em = __shfl_up_sync(0xffffffffu, im, 1);
-  if (lane == 0) em = 0.0;
-  if (lane == 31) sh_max[warp] = im;
-  __syncthreads();
-  double prevmax = em;
-  for (int k = 0; k < warp; ++k) prevmax = sh_max[k] > prevmax ? sh_max[k] : prevmax;
-  double p = start;
-  for (int t = t0; t < t1; ++t) {
-    store_v<V>(P_rec + t, vfrom_double(p > prevmax ? p : prevmax, V()));
-    p = __dadd_rn(p, tot(t));
-  }
-  if (t1 == T && t0 < T) store_v<V>(P_rec + T, vfrom_double(p > prevmax ? p : prevmax, V()));
+  if (t1 == T && t0 < T) store_v<V>(P_rec + T, fixed_to(p, V()));
   __syncthreads();
   if (tid == 0) {
     const V Pm = load_v_cg<V>(P_rec + (T - 1));
@@ -324,13 +393,13 @@ template <typename V>
 __device__ __forceinline__ V tile_total(const V (&val)[kRows][4], int64_t base, int64_t lo,
                                         int64_t N, V* sh_max) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int cnt = tile_count(base, N);
   V m = vzero(V());
 #pragma unroll
   for (int r = 0; r < kRows; ++r)
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-      const int64_t e = base + tile_offset(warp, r, lane, q);
-      if (e >= lo && e < N) m = vmax(m, val[r][q]);
+      if (tile_offset(warp, r, lane, q) < cnt) m = vmax(m, val[r][q]);
     }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) m = vmax(m, vshfl_xor(m, o));
@@ -357,6 +426,7 @@ __device__ __forceinline__ void emit_tile_cumoff(const T* __restrict__ lw, int64
                                                  int32_t* __restrict__ d, V* sh_tot, V* sh_max) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t n = N - lo;
+  const int cnt = tile_count(base, N);
   using U = typename Path<T, V>::U;
   const U u_sys = Path<T, V>::draw_u(draw(keys, 0u, 0u));
   V val[kRows][4];
@@ -393,11 +463,11 @@ __device__ __forceinline__ void emit_tile_cumoff(const T* __restrict__ lw, int64
     }
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-      const int64_t e = base + tile_offset(warp, r, lane, q);
-      const int64_t i = e - lo;
+      const int off = tile_offset(warp, r, lane, q);
+      const int64_t i = base + off - lo;
       int32_t Oc = O[r][q];
       if (i == n - 1) Oc = static_cast<int32_t>(n);
-      if (e >= lo && e < N) {
+      if (off < cnt) {
         for (int32_t j = prev; j < Oc; ++j) a[lo + j] = static_cast<int32_t>(i);
         if (d) d[lo + i] = (Oc > prev) ? prev : static_cast<int32_t>(n);
       }
@@ -422,6 +492,7 @@ __device__ __forceinline__ void emit_tile_W(const T* __restrict__ lw, int64_t lo
                                             V Pn, OUT* __restrict__ Wout, V* sh_tot,
                                             V* sh_max) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int cnt = tile_count(base, N);
   V val[kRows][4];
   tile_raw_values<T, V>(lw, lo, N, base, wc, vec, val, sh_tot);
   V prevmax;
@@ -430,8 +501,8 @@ __device__ __forceinline__ void emit_tile_W(const T* __restrict__ lw, int64_t lo
   for (int r = 0; r < kRows; ++r)
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-      const int64_t e = base + tile_offset(warp, r, lane, q);
-      if (e >= lo && e < N) Wout[e] = convert_out<V, OUT>(vclamp(vadd(Pt, val[r][q]), Pt, Pn));
+      const int off = tile_offset(warp, r, lane, q);
+      if (off < cnt) Wout[base + off] = convert_out<V, OUT>(vclamp(vadd(Pt, val[r][q]), Pt, Pn));
     }
 }
 
@@ -510,6 +581,7 @@ __device__ __forceinline__ void emit_tile_W_guide(const T* __restrict__ lw, int6
                                                   V* sh_max) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t n = N - lo;
+  const int cnt = tile_count(base, N);
   V val[kRows][4];
   tile_raw_values<T, V>(lw, lo, N, base, wc, vec, val, sh_tot);
   V prevmax;
@@ -519,9 +591,9 @@ __device__ __forceinline__ void emit_tile_W_guide(const T* __restrict__ lw, int6
   for (int r = 0; r < kRows; ++r)
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-      const int64_t e = base + tile_offset(warp, r, lane, q);
+      const int off = tile_offset(warp, r, lane, q);
       const V W = vclamp(vadd(Pt, val[r][q]), Pt, Pn);
-      if (e >= lo && e < N) Wout[e] = W;
+      if (off < cnt) Wout[base + off] = W;
       C[r][q] = guide_count<V>(W, gd, n);
     }
   int64_t Cbefore = 0;
@@ -543,11 +615,11 @@ __device__ __forceinline__ void emit_tile_W_guide(const T* __restrict__ lw, int6
     }
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-      const int64_t e = base + tile_offset(warp, r, lane, q);
-      const int64_t j = e - lo;
+      const int off = tile_offset(warp, r, lane, q);
+      const int64_t j = base + off - lo;
       int64_t Cc = C[r][q];
       if (j == n - 1) Cc = n;
-      if (e >= lo && e < N) {
+      if (off < cnt) {
         for (int64_t b = prev; b < Cc; ++b) G[lo + b] = static_cast<int32_t>(j);
         if (j == n - 1) G[lo + n] = static_cast<int32_t>(n - 1);
       }

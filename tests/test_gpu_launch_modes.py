@@ -1,8 +1,8 @@
 """GPU tests of the two launch structures of the scan-based resamplers: one cooperative kernel
 with grid barriers (LAUNCH_FUSED) and one kernel per pass (LAUNCH_SEPARATE) must give the same
 ancestors bit for bit and the same device status, for every accumulation mode, with and
-without Permute, at sizes spanning one tile, several tiles with a ragged tail, more tiles
-than the fused grid has CTAs, and the automatic switch-over size. Each mode is also checked
+without Permute, at sizes spanning one tile, several tiles with a ragged tail and more tiles
+than the fused grid has CTAs. Each mode is also checked
 against the oracle in test_gpu_parity.py (the default mode runs the fused kernel there)."""
 import numpy as np
 import pytest
@@ -51,11 +51,11 @@ def test_fused_equals_separate(rs, h, kind, dtype, prec, N):
             assert np.array_equal(a1, a2), (scheme, permute)
 
 
-def test_fused_equals_separate_at_auto_threshold_and_misaligned(rs, h):
-    """Around the automatic switch-over (FUSED_AUTO_MAX_N) and with a log-weight pointer that
-    is not 16-byte aligned; the systematic result at the threshold is also checked against
-    the oracle's double-double cumulative offspring."""
-    for N in (rs.FUSED_AUTO_MAX_N, rs.FUSED_AUTO_MAX_N + 1):
+def test_fused_equals_separate_large_and_misaligned(rs, h):
+    """Sizes with more tiles than the fused grid has CTAs, a ragged tail, and a log-weight
+    pointer that is not 16-byte aligned; the systematic result of the default mode is also
+    checked against the oracle's double-double cumulative offspring."""
+    for N in (1 << 22, (1 << 22) + 4097):
         lw = workload.synthetic_logw(N + 1, 1.0, seed=5, dtype=np.float32)
         base = torch.from_numpy(lw).to(DEV)
         view = base[1:]
