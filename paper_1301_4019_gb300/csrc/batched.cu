@@ -194,29 +194,26 @@ __device__ __forceinline__ double filter_M(const Batch& b, int f) {
 
 template <typename T, typename V>
 __global__ void __launch_bounds__(kBlock) batch_sum_kernel(const T* __restrict__ lw, Batch b) {
-  __shared__ V sh_tot[kWarps];
-  __shared__ V sh_max[kWarps];
+  __shared__ TileSh<V> sh;
   __shared__ float2 sh_tab[64];
   TileLoc L;
   if (!locate_tile(b, blockIdx.x, L)) return;
   const double M = filter_M(b, L.f);
-  V tm = vzero(V());
   if (M > -DBL_MAX) {
     const WeightCtx wc = make_ctx<T, V>(M, sh_tab);
     const bool vec = (reinterpret_cast<uintptr_t>(lw) & 15u) == 0;
-    V val[kRows][4];
-    tile_raw_values<T, V>(lw, L.lo, L.hi, L.base, wc, vec, val, sh_tot);
-    tm = tile_total<V>(val, L.base, L.lo, L.hi, sh_max);
+    tile_record<T, V>(lw, L.lo, L.hi, L.base, wc, vec, b.s_rec + blockIdx.x, sh);
+  } else if (threadIdx.x == 0) {
+    store_v<V>(b.s_rec + blockIdx.x, vzero(V()));
   }
-  if (threadIdx.x == 0) store_v<V>(b.s_rec + blockIdx.x, tm);
 }
 
-template <typename V>
+template <typename T, typename V>
 __global__ void __launch_bounds__(kBlock) batch_prefix_kernel(Batch b) {
   const int f = blockIdx.x;
   const int64_t lo = b.off[f], hi = b.off[f + 1], n = hi - lo;
-  const int t0 = b.tile_start[f], T = b.tile_start[f + 1] - t0;
-  if (T <= 0 || n <= 0) return;
+  const int t0 = b.tile_start[f], nt = b.tile_start[f + 1] - t0;
+  if (nt <= 0 || n <= 0) return;
   if (!(filter_M(b, f) > -DBL_MAX)) {
     if (threadIdx.x == 0) {
       b.fSd[f] = 0.0;
@@ -224,17 +221,16 @@ __global__ void __launch_bounds__(kBlock) batch_prefix_kernel(Batch b) {
     }
     return;
   }
-  tile_prefix_compute<V>(b.s_rec + t0, b.P_rec + t0 + f, T, n,
-                         reinterpret_cast<V*>(b.fS + f), reinterpret_cast<V*>(b.fscale + f),
-                         b.fSd + f);
+  tile_prefix_compute<V>(b.s_rec + t0, b.P_rec + t0 + f, nt, n,
+                            reinterpret_cast<V*>(b.fS + f), reinterpret_cast<V*>(b.fscale + f),
+                            b.fSd + f);
 }
 
 template <typename T, typename V, int SCHEME>
 __global__ void __launch_bounds__(kBlock)
 batch_emit_kernel(const T* __restrict__ lw, Batch b, Keys base_keys,
                   int32_t* __restrict__ a, int32_t* __restrict__ d, V* __restrict__ W) {
-  __shared__ V sh_tot[kWarps];
-  __shared__ V sh_max[kWarps];
+  __shared__ TileSh<V> sh;
   __shared__ float2 sh_tab[64];
   TileLoc L;
   if (!locate_tile(b, blockIdx.x, L)) return;
@@ -258,14 +254,15 @@ batch_emit_kernel(const T* __restrict__ lw, Batch b, Keys base_keys,
     if (d)  // claims of the search kernel start from the sentinel n
       for (int64_t e = L.base + threadIdx.x; e < L.hi && e < L.base + kTile; e += kBlock)
         d[e] = static_cast<int32_t>(n);
-    emit_tile_W<T, V, V>(lw, L.lo, L.hi, L.base, wc, vec, Pt, Pn, W, sh_tot, sh_max);
+    emit_tile_W<T, V, V>(lw, L.lo, L.hi, L.base, wc, vec, Pt, Pn, W, sh);
   } else {
     const Keys keys = with_tag(base_keys, static_cast<uint32_t>(L.f), SCHEME);
+    const typename Path<T, V>::U u_sys =
+        SCHEME == RS_STRATIFIED ? typename Path<T, V>::U() : cta_uniform0<T, V>(keys);
     const V Pm = L.t > 0 ? load_v_cg<V>(P + L.t - 1) : vzero(V());
-    const V sm = L.t > 0 ? load_v_cg<V>(s + L.t - 1) : vzero(V());
     emit_tile_cumoff<T, V, SCHEME == RS_STRATIFIED>(
-        lw, L.lo, L.hi, L.base, wc, vec, Pt, Pn, L.t > 0, Pm, sm,
-        load_v_cg<V>(b.fS + L.f), load_v_cg<V>(b.fscale + L.f), keys, a, d, sh_tot, sh_max);
+        lw, L.lo, L.hi, L.base, wc, vec, Pt, Pn, L.t > 0 ? s + L.t - 1 : nullptr, Pm,
+        load_v_cg<V>(b.fS + L.f), load_v_cg<V>(b.fscale + L.f), u_sys, keys, a, d, sh);
   }
 }
 
@@ -415,7 +412,7 @@ cudaError_t run_batched_scan(const Scratch& s, int scheme, const T* lw, const Ba
   trace_mark(s.trace, kLblSum[ai], st);
   batch_sum_kernel<T, V><<<tiles, kBlock, 0, st>>>(lw, b);
   trace_mark(s.trace, "batch_prefix", st);
-  batch_prefix_kernel<V><<<b.F, kBlock, 0, st>>>(b);
+  batch_prefix_kernel<T, V><<<b.F, kBlock, 0, st>>>(b);
   V* W = static_cast<V*>(s.W);
   trace_mark(s.trace, kLblEmit[ai], st);
   switch (scheme) {

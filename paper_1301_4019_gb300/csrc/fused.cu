@@ -152,8 +152,7 @@ __device__ __forceinline__ u128 block_sum_u128(u128 v, u128* sh) {
 template <typename T, typename V, int SCHEME>
 __device__ __forceinline__ void fused_body(const T* __restrict__ lw, const FusedArgs& A,
                                            unsigned int& target) {
-  __shared__ V sh_tot[kWarps];
-  __shared__ V sh_max[kWarps];
+  __shared__ TileSh<V> sh;
   __shared__ float2 sh_tab[64];
   __shared__ long long sh_key[kWarps];
   __shared__ u128 sh_sum[kWarps];
@@ -208,13 +207,10 @@ __device__ __forceinline__ void fused_body(const T* __restrict__ lw, const Fused
     u128 run = 0;  // meaningful in thread 0
     for (int t = t0; t < t1; ++t) {
       const int64_t base = static_cast<int64_t>(t) * kTile;
-      V val[kRows][4];
-      tile_raw_values<T, V>(lw, 0, N, base, wc, vec, val, sh_tot);
-      const V tm = tile_total<V>(val, base, 0, N, sh_max);
+      const u128 f = tile_record<T, V>(lw, 0, N, base, wc, vec, A.s_rec + t, sh);
       if (threadIdx.x == 0) {
-        store_v<V>(A.s_rec + t, tm);
         st_u128(LP + t, run);
-        run += to_fixed(tm);
+        run += f;
       }
     }
     if (threadIdx.x == 0) st_u128(A.agg + c, run);
@@ -234,17 +230,16 @@ __device__ __forceinline__ void fused_body(const T* __restrict__ lw, const Fused
     const u128 CP = block_sum_u128(part, sh_sum);
     for (int t = t0 + threadIdx.x; t < t1; t += kBlock) {
       const u128 lp = ld_u128_cg(LP + t);
-      store_v<V>(A.P_rec + t, fixed_to(CP + lp, V()));
+      store_v<V>(A.P_rec + t, fixed_to(CP + lp, V(), kFixFrac));
     }
     if (c == G - 1) {
       if (threadIdx.x == 0)
-        store_v<V>(A.P_rec + T_tiles, fixed_to(CP + ld_u128_cg(A.agg + c), V()));
+        store_v<V>(A.P_rec + T_tiles, fixed_to(CP + ld_u128_cg(A.agg + c), V(), kFixFrac));
       __syncthreads();
       if (threadIdx.x == 0) {
         const V Pm = load_v_cg<V>(A.P_rec + (T_tiles - 1));
         const V Pn = load_v_cg<V>(A.P_rec + T_tiles);
-        const V st = load_v_cg<V>(A.s_rec + (T_tiles - 1));
-        const V S = vclamp(vadd(Pm, st), Pm, Pn);
+        const V S = vclamp(vadd(Pm, load_v_cg<V>(A.s_rec + (T_tiles - 1))), Pm, Pn);
         const double Sd = vto_double(S);
         store_v<V>(&A.g->S_raw, S);
         store_v<V>(&A.g->scale_raw, vfrom_double(__ddiv_rn(static_cast<double>(N), Sd), V()));
@@ -268,22 +263,24 @@ __device__ __forceinline__ void fused_body(const T* __restrict__ lw, const Fused
     return;  // uniform over the grid
   }
   const V S = load_v_cg<V>(&A.g->S_raw), scale = load_v_cg<V>(&A.g->scale_raw);
+  typename Path<T, V>::U u_sys = typename Path<T, V>::U();
   if constexpr (SCHEME == RS_MULTINOMIAL) {
     if (threadIdx.x == 0) sh_gd = make_guide(Sd, N);
     __syncthreads();
+  } else if constexpr (SCHEME == RS_SYSTEMATIC) {
+    u_sys = cta_uniform0<T, V>(A.keys);
   }
   for (int t = t0; t < t1; ++t) {
     const int64_t base = static_cast<int64_t>(t) * kTile;
     const V Pt = load_v_cg<V>(A.P_rec + t), Pn = load_v_cg<V>(A.P_rec + t + 1);
     const V Pm = t > 0 ? load_v_cg<V>(A.P_rec + t - 1) : vzero(V());
-    const V sm = t > 0 ? load_v_cg<V>(A.s_rec + t - 1) : vzero(V());
+    const double2* prev = t > 0 ? A.s_rec + t - 1 : nullptr;
     if constexpr (SCHEME == RS_MULTINOMIAL) {
-      emit_tile_W_guide<T, V>(lw, 0, N, base, wc, vec, Pt, Pn, t > 0, Pm, sm, sh_gd,
-                              static_cast<V*>(A.W), A.guide, sh_tot, sh_max);
+      emit_tile_W_guide<T, V>(lw, 0, N, base, wc, vec, Pt, Pn, prev, Pm, sh_gd,
+                              static_cast<V*>(A.W), A.guide, sh);
     } else {
-      emit_tile_cumoff<T, V, SCHEME == RS_STRATIFIED>(lw, 0, N, base, wc, vec, Pt, Pn, t > 0, Pm,
-                                                       sm, S, scale, A.keys, A.a, A.d, sh_tot,
-                                                       sh_max);
+      emit_tile_cumoff<T, V, SCHEME == RS_STRATIFIED>(lw, 0, N, base, wc, vec, Pt, Pn, prev, Pm,
+                                                       S, scale, u_sys, A.keys, A.a, A.d, sh);
     }
   }
 }

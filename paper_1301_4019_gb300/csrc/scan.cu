@@ -127,27 +127,40 @@ max_kernel(const T* __restrict__ lw, int64_t N, ScanGlob* g, double* blockmax, i
 // ---------------------------------------------------------------------------------------
 // Pass 2: tile sums and, in the last CTA, tile prefixes.
 // ---------------------------------------------------------------------------------------
+// The last CTA's work, kept out of line so that its registers do not limit the occupancy of
+// the tile work.
 template <typename T, typename V>
-__global__ void __launch_bounds__(kBlock)
+__device__ __noinline__ void tile_prefix_last_cta(const double2* s_rec, double2* P_rec, int nt,
+                                                  int64_t N, ScanGlob* g, int* err,
+                                                  double* log_total_out) {
+  tile_prefix_compute<V>(s_rec, P_rec, nt, N, reinterpret_cast<V*>(&g->S_raw),
+                            reinterpret_cast<V*>(&g->scale_raw), &g->S_d);
+  if (threadIdx.x == 0) {
+    const double Sd = g->S_d;
+    if (!(Sd > 0.0)) flag_error(err, RS_ERR_ZERO_WEIGHT);
+    if (log_total_out) *log_total_out = __dadd_rn(g->M, log(Sd));
+    g->ticket_tile = 0u;
+  }
+}
+
+template <typename T, typename V>
+__global__ void __launch_bounds__(kBlock, 4)
 tile_sum_kernel(const T* __restrict__ lw, int64_t N, ScanGlob* g, double2* s_rec,
                 double2* P_rec, int* err, double* log_total_out) {
-  __shared__ V sh_tot[kWarps];
-  __shared__ V sh_max[kWarps];
+  __shared__ TileSh<V> sh;
   __shared__ float2 sh_tab[64];
   __shared__ bool am_last;
   const double Md = g->M;
   const bool zero = !(Md > -DBL_MAX);
   const int64_t base = static_cast<int64_t>(blockIdx.x) * kTile;
-  V tm = vzero(V());
   if (!zero) {
     const WeightCtx wc = make_ctx<T, V>(Md, sh_tab);
     const bool vec = (reinterpret_cast<uintptr_t>(lw) & 15u) == 0;
-    V val[kRows][4];
-    tile_raw_values<T, V>(lw, 0, N, base, wc, vec, val, sh_tot);
-    tm = tile_total<V>(val, base, 0, N, sh_max);
+    tile_record<T, V>(lw, 0, N, base, wc, vec, s_rec + blockIdx.x, sh);
+  } else if (threadIdx.x == 0) {
+    store_v<V>(s_rec + blockIdx.x, vzero(V()));
   }
   if (threadIdx.x == 0) {
-    store_v<V>(s_rec + blockIdx.x, tm);
     __threadfence();
     const unsigned t = atomicAdd(&g->ticket_tile, 1u);
     am_last = (t == gridDim.x - 1);
@@ -155,15 +168,7 @@ tile_sum_kernel(const T* __restrict__ lw, int64_t N, ScanGlob* g, double2* s_rec
   __syncthreads();
   if (!am_last) return;
   __threadfence();
-  tile_prefix_compute<V>(s_rec, P_rec, static_cast<int>(gridDim.x), N,
-                         reinterpret_cast<V*>(&g->S_raw), reinterpret_cast<V*>(&g->scale_raw),
-                         &g->S_d);
-  if (threadIdx.x == 0) {
-    const double Sd = g->S_d;
-    if (!(Sd > 0.0)) flag_error(err, RS_ERR_ZERO_WEIGHT);
-    if (log_total_out) *log_total_out = __dadd_rn(g->M, log(Sd));
-    g->ticket_tile = 0u;
-  }
+  tile_prefix_last_cta<T, V>(s_rec, P_rec, static_cast<int>(gridDim.x), N, g, err, log_total_out);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -174,8 +179,7 @@ __global__ void __launch_bounds__(kBlock)
 emit_cumoff_kernel(const T* __restrict__ lw, int64_t N, const ScanGlob* g, const double2* s_rec,
                    const double2* P_rec, Keys keys, int32_t* __restrict__ a,
                    int32_t* __restrict__ d) {
-  __shared__ V sh_tot[kWarps];
-  __shared__ V sh_max[kWarps];
+  __shared__ TileSh<V> sh;
   __shared__ float2 sh_tab[64];
   const int64_t base = static_cast<int64_t>(blockIdx.x) * kTile;
   const double Md = g->M;
@@ -187,14 +191,14 @@ emit_cumoff_kernel(const T* __restrict__ lw, int64_t N, const ScanGlob* g, const
     return;
   }
   const WeightCtx wc = make_ctx<T, V>(Md, sh_tab);
+  const typename Path<T, V>::U u_sys = STRAT ? typename Path<T, V>::U() : cta_uniform0<T, V>(keys);
   const bool vec = (reinterpret_cast<uintptr_t>(lw) & 15u) == 0;
   const int t = blockIdx.x;
   const V Pt = load_v<V>(P_rec + t), Pn = load_v<V>(P_rec + t + 1);
   const V Pm = t > 0 ? load_v<V>(P_rec + t - 1) : vzero(V());
-  const V sm = t > 0 ? load_v<V>(s_rec + t - 1) : vzero(V());
-  emit_tile_cumoff<T, V, STRAT>(lw, 0, N, base, wc, vec, Pt, Pn, t > 0, Pm, sm,
-                                load_v<V>(&g->S_raw), load_v<V>(&g->scale_raw), keys, a, d,
-                                sh_tot, sh_max);
+  emit_tile_cumoff<T, V, STRAT>(lw, 0, N, base, wc, vec, Pt, Pn, t > 0 ? s_rec + t - 1 : nullptr,
+                                Pm, load_v<V>(&g->S_raw), load_v<V>(&g->scale_raw), u_sys, keys,
+                                a, d, sh);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -205,8 +209,7 @@ template <typename T, typename V, typename OUT>
 __global__ void __launch_bounds__(kBlock)
 emit_W_kernel(const T* __restrict__ lw, int64_t N, const ScanGlob* g, const double2* P_rec,
               OUT* __restrict__ Wout) {
-  __shared__ V sh_tot[kWarps];
-  __shared__ V sh_max[kWarps];
+  __shared__ TileSh<V> sh;
   __shared__ float2 sh_tab[64];
   const int64_t base = static_cast<int64_t>(blockIdx.x) * kTile;
   const double Md = g->M;
@@ -219,7 +222,7 @@ emit_W_kernel(const T* __restrict__ lw, int64_t N, const ScanGlob* g, const doub
   const bool vec = (reinterpret_cast<uintptr_t>(lw) & 15u) == 0;
   const int t = blockIdx.x;
   emit_tile_W<T, V, OUT>(lw, 0, N, base, wc, vec, load_v<V>(P_rec + t), load_v<V>(P_rec + t + 1),
-                         Wout, sh_tot, sh_max);
+                         Wout, sh);
 }
 
 // Pass 3b for the multinomial scheme: stored cumulative weights plus the guide table.
@@ -227,8 +230,7 @@ template <typename T, typename V>
 __global__ void __launch_bounds__(kBlock)
 emit_W_guide_kernel(const T* __restrict__ lw, int64_t N, const ScanGlob* g, const double2* s_rec,
                     const double2* P_rec, V* __restrict__ Wout, int32_t* __restrict__ G) {
-  __shared__ V sh_tot[kWarps];
-  __shared__ V sh_max[kWarps];
+  __shared__ TileSh<V> sh;
   __shared__ float2 sh_tab[64];
   const int64_t base = static_cast<int64_t>(blockIdx.x) * kTile;
   const double Md = g->M;
@@ -237,9 +239,9 @@ emit_W_guide_kernel(const T* __restrict__ lw, int64_t N, const ScanGlob* g, cons
   const bool vec = (reinterpret_cast<uintptr_t>(lw) & 15u) == 0;
   const int t = blockIdx.x;
   const V Pm = t > 0 ? load_v<V>(P_rec + t - 1) : vzero(V());
-  const V sm = t > 0 ? load_v<V>(s_rec + t - 1) : vzero(V());
   emit_tile_W_guide<T, V>(lw, 0, N, base, wc, vec, load_v<V>(P_rec + t), load_v<V>(P_rec + t + 1),
-                          t > 0, Pm, sm, make_guide(g->S_d, N), Wout, G, sh_tot, sh_max);
+                          t > 0 ? s_rec + t - 1 : nullptr, Pm, make_guide(g->S_d, N), Wout, G,
+                          sh);
 }
 
 // ---------------------------------------------------------------------------------------

@@ -277,9 +277,9 @@ __device__ __forceinline__ u128 to_fixed(double v) {
 }
 __device__ __forceinline__ u128 to_fixed(float2 v) { return to_fixed(v.x) + to_fixed(v.y); }
 
-// Round a non-negative fixed-point value to nearest (ties to even) with `bits` significant
-// bits: returns the IEEE bit pattern for the given exponent bias and fraction width.
-__device__ __forceinline__ uint64_t fixed_round_bits(u128 F, int bits, int bias) {
+// Round a non-negative fixed-point value (frac fractional bits) to nearest, ties to even, with
+// `bits` significant bits: returns the IEEE bit pattern for the given exponent bias.
+__device__ __forceinline__ uint64_t fixed_round_bits(u128 F, int bits, int bias, int frac) {
   if (F == 0) return 0;
   const uint64_t hi = static_cast<uint64_t>(F >> 64), lo = static_cast<uint64_t>(F);
   const int p = hi ? 127 - __clzll(static_cast<long long>(hi)) : 63 - __clzll(static_cast<long long>(lo));
@@ -295,25 +295,36 @@ __device__ __forceinline__ uint64_t fixed_round_bits(u128 F, int bits, int bias)
     up = half && (sticky || (mant & 1));
   }
   const uint64_t frac_mask = (1ull << (bits - 1)) - 1;
-  const uint64_t expo = static_cast<uint64_t>(p - kFixFrac + bias);
+  const uint64_t expo = static_cast<uint64_t>(p - frac + bias);
   return ((expo << (bits - 1)) | (mant & frac_mask)) + (up ? 1 : 0);
 }
-__device__ __forceinline__ float fixed_to_float(u128 F) {
-  return __uint_as_float(static_cast<uint32_t>(fixed_round_bits(F, 24, 127)));
+__device__ __forceinline__ float fixed_to_float(u128 F, int frac) {
+  return __uint_as_float(static_cast<uint32_t>(fixed_round_bits(F, 24, 127, frac)));
 }
-__device__ __forceinline__ double fixed_to_double(u128 F) {
-  return __longlong_as_double(static_cast<long long>(fixed_round_bits(F, 53, 1023)));
+__device__ __forceinline__ double fixed_to_double(u128 F, int frac) {
+  return __longlong_as_double(static_cast<long long>(fixed_round_bits(F, 53, 1023, frac)));
 }
-__device__ __forceinline__ float fixed_to_float_signed(u128 F) {
+__device__ __forceinline__ float fixed_to_float_signed(u128 F, int frac) {
   const bool neg = static_cast<int64_t>(static_cast<uint64_t>(F >> 64)) < 0;
-  const float x = fixed_to_float(neg ? static_cast<u128>(0) - F : F);
+  const float x = fixed_to_float(neg ? static_cast<u128>(0) - F : F, frac);
   return neg ? -x : x;
 }
-__device__ __forceinline__ float fixed_to(u128 F, float) { return fixed_to_float(F); }
-__device__ __forceinline__ double fixed_to(u128 F, double) { return fixed_to_double(F); }
-__device__ __forceinline__ float2 fixed_to(u128 F, float2) {  // hi + lo, hi = RN(F)
-  const float hi = fixed_to_float(F);
-  return make_float2(hi, fixed_to_float_signed(F - to_fixed(hi)));
+__device__ __forceinline__ float fixed_to(u128 F, float, int frac) { return fixed_to_float(F, frac); }
+__device__ __forceinline__ double fixed_to(u128 F, double, int frac) {
+  return fixed_to_double(F, frac);
+}
+__device__ __forceinline__ float2 fixed_to(u128 F, float2, int frac) {  // hi + lo, hi = RN(F)
+  const float hi = fixed_to_float(F, frac);
+  // hi as fixed point: its bits are a subset of F's (|hi - F| < ulp(hi)), shifted into place
+  const uint32_t b = __float_as_uint(hi);
+  const int e = static_cast<int>((b >> 23) & 0xffu);
+  u128 H = 0;
+  if (e != 0) {
+    const int sh = e - 150 + frac;
+    const u128 m = (b & 0x7fffffu) | 0x800000u;
+    H = sh >= 0 ? (m << sh) : (m >> (-sh));
+  }
+  return make_float2(hi, fixed_to_float_signed(F - H, frac));
 }
 __device__ __forceinline__ u128 shfl_up_u128(u128 v, int d) {
   const uint64_t hi = __shfl_up_sync(0xffffffffu, static_cast<uint64_t>(v >> 64), d);
@@ -321,28 +332,33 @@ __device__ __forceinline__ u128 shfl_up_u128(u128 v, int d) {
   return (static_cast<u128>(hi) << 64) | lo;
 }
 
-// Prefixes of one sequence of T tile totals s_t (block-level, every thread of the CTA calls
-// it): P_t = RN(s_0 + ... + s_{t-1}) for t = 0..T, the exact sums taken in fixed point (each
+// A tile's record: its total in the accumulator type; rec_fixed returns it in fixed point.
+template <typename V> __device__ __forceinline__ u128 rec_fixed(const double2* p) {
+  return to_fixed(load_v_cg<V>(p));
+}
+
+// Prefixes of one sequence of nt tile totals s_t (block-level, every thread of the CTA calls
+// it): P_t = RN(s_0 + ... + s_{t-1}) for t = 0..nt, the exact sums taken in fixed point (each
 // thread a contiguous chunk of tiles, then a warp scan and a scan over the warps: integer
 // adds, so the order does not matter). P is non-decreasing because the exact prefixes are and
 // rounding is monotone. The total S is the cumulative weight of the last particle exactly as
-// the emit pass computes it, clamp(P_{T-1} + s_{T-1}, P_{T-1}, P_T), so that particle
-// receives O = N. Thread 0 writes S, N / S and S (binary64) to the given pointers, then the
-// CTA synchronises.
+// the emit pass computes it, clamp(P_{nt-1} + s_{nt-1}, P_{nt-1}, P_nt), so that particle
+// receives O = N.
+// Thread 0 writes S, N / S and S (binary64) to the given pointers, then the CTA synchronises.
 template <typename V>
-__device__ void tile_prefix_compute(const double2* s_rec, double2* P_rec, int T, int64_t N,
+__device__ void tile_prefix_compute(const double2* s_rec, double2* P_rec, int nt, int64_t N,
                                     V* S_out, V* scale_out, double* Sd_out) {
   __shared__ u128 sh_sum[kWarps];
-  constexpr int kGroup = 8;  // tile totals loaded together
+  constexpr int kGroup = 4;  // tile totals loaded together
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int chunk = (T + kBlock - 1) / kBlock;
-  const int t0 = min(T, tid * chunk), t1 = min(T, t0 + chunk);
+  const int chunk = (nt + kBlock - 1) / kBlock;
+  const int t0 = min(nt, tid * chunk), t1 = min(nt, t0 + chunk);
   u128 cache[kGroup];  // the first group stays in registers
   u128 local = 0;
   for (int g = t0; g < t1; g += kGroup) {
     u128 f[kGroup];
 #pragma unroll
-    for (int k = 0; k < kGroup; ++k) f[k] = (g + k < t1) ? to_fixed(load_v_cg<V>(s_rec + g + k)) : 0;
+    for (int k = 0; k < kGroup; ++k) f[k] = (g + k < t1) ? rec_fixed<V>(s_rec + g + k) : 0;
 #pragma unroll
     for (int k = 0; k < kGroup; ++k) {
       local += f[k];
@@ -363,22 +379,21 @@ __device__ void tile_prefix_compute(const double2* s_rec, double2* P_rec, int T,
     u128 f[kGroup];
 #pragma unroll
     for (int k = 0; k < kGroup; ++k)
-      f[k] = (g == t0) ? cache[k] : ((g + k < t1) ? to_fixed(load_v_cg<V>(s_rec + g + k)) : 0);
+      f[k] = (g == t0) ? cache[k] : ((g + k < t1) ? rec_fixed<V>(s_rec + g + k) : 0);
 #pragma unroll
     for (int k = 0; k < kGroup; ++k) {
       if (g + k < t1) {
-        store_v<V>(P_rec + g + k, fixed_to(p, V()));
+        store_v<V>(P_rec + g + k, fixed_to(p, V(), kFixFrac));
         p += f[k];
       }
     }
   }
-  if (t1 == T && t0 < T) store_v<V>(P_rec + T, fixed_to(p, V()));
+  if (t1 == nt && t0 < nt) store_v<V>(P_rec + nt, fixed_to(p, V(), kFixFrac));
   __syncthreads();
   if (tid == 0) {
-    const V Pm = load_v_cg<V>(P_rec + (T - 1));
-    const V Pn = load_v_cg<V>(P_rec + T);
-    const V st = load_v_cg<V>(s_rec + (T - 1));
-    const V S = vclamp(vadd(Pm, st), Pm, Pn);
+    const V Pm = load_v_cg<V>(P_rec + (nt - 1));
+    const V Pn = load_v_cg<V>(P_rec + nt);
+    const V S = vclamp(vadd(Pm, load_v_cg<V>(s_rec + (nt - 1))), Pm, Pn);
     const double Sd = vto_double(S);
     *S_out = S;
     *scale_out = vfrom_double(__ddiv_rn(static_cast<double>(N), Sd), V());
@@ -411,46 +426,93 @@ __device__ __forceinline__ V tile_total(const V (&val)[kRows][4], int64_t base, 
   return tm;
 }
 
+// Shared scratch of the block-level tile functions.
+template <typename V> struct TileSh {
+  V tot[kWarps];
+  V max[kWarps];
+};
+
+// The tile's total (its record), stored by thread 0 at rec; returned as fixed point in every
+// thread.
+template <typename T, typename V>
+__device__ __forceinline__ u128 tile_record(const T* __restrict__ lw, int64_t lo, int64_t N,
+                                            int64_t base, const WeightCtx& wc, bool vec,
+                                            double2* rec, TileSh<V>& sh) {
+  V val[kRows][4];
+  tile_raw_values<T, V>(lw, lo, N, base, wc, vec, val, sh.tot);
+  const V tm = tile_total<V>(val, base, lo, N, sh.max);
+  if (threadIdx.x == 0) store_v<V>(rec, tm);
+  return to_fixed(tm);
+}
+
+// Cumulative weights W[r][q] of this thread's elements of the tile (clamped into [Pt, Pn])
+// and Wwarp, the cumulative weight just before this warp's first element.
+template <typename T, typename V>
+__device__ __forceinline__ void tile_cum_weights(const T* __restrict__ lw, int64_t lo, int64_t N,
+                                                 int64_t base, const WeightCtx& wc, bool vec,
+                                                 V Pt, V Pn, V (&W)[kRows][4], V& Wwarp,
+                                                 TileSh<V>& sh) {
+  V val[kRows][4];
+  tile_raw_values<T, V>(lw, lo, N, base, wc, vec, val, sh.tot);
+  V prevmax;
+  tile_running_max<V>(val, base, lo, N, sh.max, prevmax);
+#pragma unroll
+  for (int r = 0; r < kRows; ++r)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) W[r][q] = vclamp(vadd(Pt, val[r][q]), Pt, Pn);
+  Wwarp = vclamp(vadd(Pt, prevmax), Pt, Pn);
+}
+
+// The cumulative weight of the previous tile's last particle (prefix Pm, record prev_rec),
+// as its own emission computes it.
+template <typename V>
+__device__ __forceinline__ V tile_W_last(const double2* prev_rec, V Pm, V Pt) {
+  return vclamp(vadd(Pm, load_v_cg<V>(prev_rec)), Pm, Pt);
+}
+
+// The systematic uniform u (counter (0, 0)), drawn once per CTA.
+template <typename T, typename V>
+__device__ __forceinline__ typename Path<T, V>::U cta_uniform0(const Keys& keys) {
+  __shared__ typename Path<T, V>::U sh_u;
+  __syncthreads();
+  if (threadIdx.x == 0) sh_u = Path<T, V>::draw_u(draw(keys, 0u, 0u));
+  __syncthreads();
+  return sh_u;
+}
+
 // Systematic / stratified emission of one tile starting at `base` of the sequence [lo, N)
 // (block-level): cumulative offspring O of every particle, the Code-11 scatter of local
 // ancestor indices into a[lo + j] and, when d is given, the Prepermute claims
 // d[lo + i] = O_{i-1} if particle i has offspring, else n (for a non-decreasing ancestry
 // the lowest claimant of slot i is the first position of its run). Pt, Pn: prefixes of this
-// tile; Pm, sm: prefix and total of the previous tile (has_prev false for the first tile).
+// tile; prev_rec, Pm: record and prefix of the previous tile (prev_rec null for the first).
+// u_sys: the systematic uniform (cta_uniform0; unused when STRAT).
 template <typename T, typename V, bool STRAT>
 __device__ __forceinline__ void emit_tile_cumoff(const T* __restrict__ lw, int64_t lo, int64_t N,
                                                  int64_t base, const WeightCtx& wc, bool vec,
-                                                 V Pt, V Pn, bool has_prev, V Pm, V sm, V S,
-                                                 V scale, const Keys& keys,
-                                                 int32_t* __restrict__ a,
-                                                 int32_t* __restrict__ d, V* sh_tot, V* sh_max) {
+                                                 V Pt, V Pn, const double2* prev_rec, V Pm, V S,
+                                                 V scale, typename Path<T, V>::U u_sys,
+                                                 const Keys& keys, int32_t* __restrict__ a,
+                                                 int32_t* __restrict__ d, TileSh<V>& sh) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t n = N - lo;
   const int cnt = tile_count(base, N);
-  using U = typename Path<T, V>::U;
-  const U u_sys = Path<T, V>::draw_u(draw(keys, 0u, 0u));
-  V val[kRows][4];
-  tile_raw_values<T, V>(lw, lo, N, base, wc, vec, val, sh_tot);
-  V prevmax;
-  tile_running_max<V>(val, base, lo, N, sh_max, prevmax);
+  V W[kRows][4], Wwarp;
+  tile_cum_weights<T, V>(lw, lo, N, base, wc, vec, Pt, Pn, W, Wwarp, sh);
   int32_t O[kRows][4];
 #pragma unroll
   for (int r = 0; r < kRows; ++r)
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const V W = vclamp(vadd(Pt, val[r][q]), Pt, Pn);
-      O[r][q] = cum_offspring<T, V, STRAT>(W, S, scale, u_sys, keys, n);
-    }
+    for (int q = 0; q < 4; ++q)
+      O[r][q] = cum_offspring<T, V, STRAT>(W[r][q], S, scale, u_sys, keys, n);
   // cumulative offspring just before this warp's first element
   int32_t Obefore = 0;
   if (lane == 0) {
-    if (warp > 0) {
-      const V W = vclamp(vadd(Pt, prevmax), Pt, Pn);
-      Obefore = cum_offspring<T, V, STRAT>(W, S, scale, u_sys, keys, n);
-    } else if (has_prev) {
-      const V W = vclamp(vadd(Pm, sm), Pm, Pt);
-      Obefore = cum_offspring<T, V, STRAT>(W, S, scale, u_sys, keys, n);
-    }
+    if (warp > 0)
+      Obefore = cum_offspring<T, V, STRAT>(Wwarp, S, scale, u_sys, keys, n);
+    else if (prev_rec)
+      Obefore = cum_offspring<T, V, STRAT>(tile_W_last<V>(prev_rec, Pm, Pt), S, scale, u_sys,
+                                           keys, n);
   }
 #pragma unroll
   for (int r = 0; r < kRows; ++r) {
@@ -489,20 +551,17 @@ template <> __device__ __forceinline__ double convert_out<float2, double>(float2
 template <typename T, typename V, typename OUT>
 __device__ __forceinline__ void emit_tile_W(const T* __restrict__ lw, int64_t lo, int64_t N,
                                             int64_t base, const WeightCtx& wc, bool vec, V Pt,
-                                            V Pn, OUT* __restrict__ Wout, V* sh_tot,
-                                            V* sh_max) {
+                                            V Pn, OUT* __restrict__ Wout, TileSh<V>& sh) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int cnt = tile_count(base, N);
-  V val[kRows][4];
-  tile_raw_values<T, V>(lw, lo, N, base, wc, vec, val, sh_tot);
-  V prevmax;
-  tile_running_max<V>(val, base, lo, N, sh_max, prevmax);
+  V W[kRows][4], Wwarp;
+  tile_cum_weights<T, V>(lw, lo, N, base, wc, vec, Pt, Pn, W, Wwarp, sh);
 #pragma unroll
   for (int r = 0; r < kRows; ++r)
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       const int off = tile_offset(warp, r, lane, q);
-      if (off < cnt) Wout[base + off] = convert_out<V, OUT>(vclamp(vadd(Pt, val[r][q]), Pt, Pn));
+      if (off < cnt) Wout[base + off] = convert_out<V, OUT>(W[r][q]);
     }
 }
 
@@ -575,34 +634,29 @@ __device__ __forceinline__ int64_t guide_count(V W, const Guide& g, int64_t n) {
 template <typename T, typename V>
 __device__ __forceinline__ void emit_tile_W_guide(const T* __restrict__ lw, int64_t lo, int64_t N,
                                                   int64_t base, const WeightCtx& wc, bool vec,
-                                                  V Pt, V Pn, bool has_prev, V Pm, V sm,
+                                                  V Pt, V Pn, const double2* prev_rec, V Pm,
                                                   const Guide& gd, V* __restrict__ Wout,
-                                                  int32_t* __restrict__ G, V* sh_tot,
-                                                  V* sh_max) {
+                                                  int32_t* __restrict__ G, TileSh<V>& sh) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t n = N - lo;
   const int cnt = tile_count(base, N);
-  V val[kRows][4];
-  tile_raw_values<T, V>(lw, lo, N, base, wc, vec, val, sh_tot);
-  V prevmax;
-  tile_running_max<V>(val, base, lo, N, sh_max, prevmax);
+  V W[kRows][4], Wwarp;
+  tile_cum_weights<T, V>(lw, lo, N, base, wc, vec, Pt, Pn, W, Wwarp, sh);
   int64_t C[kRows][4];
 #pragma unroll
   for (int r = 0; r < kRows; ++r)
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       const int off = tile_offset(warp, r, lane, q);
-      const V W = vclamp(vadd(Pt, val[r][q]), Pt, Pn);
-      if (off < cnt) Wout[base + off] = W;
-      C[r][q] = guide_count<V>(W, gd, n);
+      if (off < cnt) Wout[base + off] = W[r][q];
+      C[r][q] = guide_count<V>(W[r][q], gd, n);
     }
   int64_t Cbefore = 0;
   if (lane == 0) {
-    if (warp > 0) {
-      Cbefore = guide_count<V>(vclamp(vadd(Pt, prevmax), Pt, Pn), gd, n);
-    } else if (has_prev) {
-      Cbefore = guide_count<V>(vclamp(vadd(Pm, sm), Pm, Pt), gd, n);
-    }
+    if (warp > 0)
+      Cbefore = guide_count<V>(Wwarp, gd, n);
+    else if (prev_rec)
+      Cbefore = guide_count<V>(tile_W_last<V>(prev_rec, Pm, Pt), gd, n);
   }
 #pragma unroll
   for (int r = 0; r < kRows; ++r) {
