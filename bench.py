@@ -50,7 +50,7 @@ LAUNCH_MODES = {"auto": 0, "fused": 1, "separate": 2}  # rs_set_launch_mode
 def parse_args():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=30)
+    p.add_argument("--steps", type=int, default=200)
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--log2n", type=int, default=20)
@@ -61,16 +61,29 @@ def parse_args():
     p.add_argument("--batched-filters", type=int, default=4096)
     p.add_argument("--launch-mode", choices=["auto", "fused", "separate"], default="auto",
                    help="launch structure of the scan-based schemes (results are identical)")
+    p.add_argument("--sweep", action="store_true",
+                   help="per-call times of the five resamplers (with Permute) for N = 2^10 .. "
+                        "2^24, binary32 and binary64, L2 flushed before every call; one JSON "
+                        "line")
+    p.add_argument("--sweep-reps", type=int, default=15)
+    p.add_argument("--precision", action="store_true",
+                   help="offspring bias of the scan schemes: binary32 plain vs compensated vs "
+                        "binary64, N = 2^16 .. 2^24, y in {0, 2, 4}; one JSON line")
+    p.add_argument("--precision-reps", type=int, default=400)
     p.add_argument("--single", default=None,
                    help="profile one call: scheme:dtype[:prec], e.g. metropolis:f32 "
                         "(runs warmup + steps calls with Permute, prints one JSON line)")
     return p.parse_args()
 
 
-def workload_params(args):
-    import oracle  # only for B; same formula as the library's rs_metropolis_B
+def workload_params(args, metropolis_B=None):
+    """N and the Metropolis step count of Eq. (B) (eps = 0.01, beta = E(w)/w_max). Our arm
+    passes the library's rs_metropolis_B; the reference arm the oracle's."""
+    if metropolis_B is None:
+        import paper_1301_4019_gb300 as rs
+        metropolis_B = rs.rs_metropolis_B
     N = 1 << args.log2n
-    B = oracle.metropolis_B(0.01, workload.beta_estimate(args.y))
+    B = metropolis_B(0.01, workload.beta_estimate(args.y))
     return N, B
 
 
@@ -110,6 +123,29 @@ def barrier(world):
         dist.barrier()
 
 
+def aggregate_replicas(ms_local: float, units_per_rank: float, world: int, device):
+    """Whole-job throughput of `world` independent replicas: every rank processed
+    units_per_rank units per step; the job's step time is the slowest rank's. Returns
+    (ms_per_step of the job, units per second of the job)."""
+    ms = reduce_max(ms_local, world, device)
+    return ms, world * units_per_rank / (ms * 1e-3)
+
+
+def workload_config(args, N, B):
+    """The workload both arms are measured on (the reference arm reports the same dict)."""
+    return {"workload": f"N=2^{args.log2n} single filter, y={args.y}, B={B}, "
+                        "5 resamplers x {f32, f64} + Permute + offspring conversions",
+            "N": N, "y": args.y, "metropolis_B": B, "log_wmax": 0.0,
+            "f32_prefix_sum": "plain binary32",
+            "parallelism": f"replicas x{max(1, args.gpus)}",
+            "l2": (f"inputs rotate through a pool of {args.pool} weight vectors per dtype "
+                   f"({args.pool * N * 12 / 2**20:.0f} MiB, "
+                   f"{'>' if args.pool * N * 12 > L2_BYTES else '<='} L2 {L2_BYTES // 2**20} MiB)"
+                   "; no flush"),
+            "timing": "CUDA-graph replay of K steps, CUDA events",
+            "launch_mode": args.launch_mode}
+
+
 # ---------------------------------------------------------------------------------------
 # clocks during the timed region
 # ---------------------------------------------------------------------------------------
@@ -129,7 +165,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "100"],
                 stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except (OSError, FileNotFoundError):
             self.proc = None
@@ -383,9 +419,9 @@ def run_ours(args):
                 "ms": round(t_ms, 5), "G_ancestors_per_s": round(N / (t_ms * 1e-3) / 1e9, 3)}
             ci += 1
 
-    ms_per_step = ms_total / args.steps
-    ms_per_step = reduce_max(ms_per_step, world, dev)
-    value = world * ancestors_per_step / (ms_per_step * 1e-3) / 1e9
+    ms_per_step, value = aggregate_replicas(ms_total / args.steps, ancestors_per_step, world,
+                                            dev)
+    value /= 1e9
 
     # --- end-to-end through the public API with pinned host buffers ---------------------
     host_in = {name: [torch.from_numpy(workload.synthetic_logw(
@@ -435,15 +471,8 @@ def run_ours(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_per_step, 5),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32+f64", "data": "synthetic",
-            "config": {"workload": f"N=2^{args.log2n} single filter, y={args.y}, B={B}, "
-                                   "5 resamplers x {f32, f64} + Permute + offspring conversions",
-                       "N": N, "y": args.y, "metropolis_B": B, "log_wmax": 0.0,
-                       "f32_prefix_sum": "plain binary32",
-                       "parallelism": f"replicas x{world}",
-                       "l2": f"inputs rotate through a {pool_bytes / 2**20:.0f} MiB pool "
-                             f"(> L2 {L2_BYTES // 2**20} MiB); no flush",
-                       "timing": "CUDA-graph replay of K steps, CUDA events",
-                       "launch_mode": args.launch_mode},
+            "config": workload_config(args, N, B),
+            "l2_pool_mib": round(pool_bytes / 2**20),
             "e2e": {"value": round(world * ancestors_per_step / (ms_e2e * 1e-3) / 1e9, 3),
                     "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                     "ms_per_step": round(ms_e2e, 5)},
@@ -471,13 +500,12 @@ def run_batched(args, dev, world):
     Metropolis (per-filter B from Eq. B) each with Permute, one launch per scheme per step,
     replayed from a CUDA graph. Returns filters/s and particles/s."""
     import torch
-    import oracle
     import paper_1301_4019_gb300 as rs
     F = args.batched_filters
     sizes = workload.ragged_sizes(F, 256, 65536, seed=SEED)
     offsets, lw, y = workload.ragged_logw(sizes, seed=SEED, dtype=np.float32)
     total = int(offsets[-1])
-    Bs = np.array([oracle.metropolis_B(0.01, workload.beta_estimate(v)) for v in y], np.int32)
+    Bs = np.array([rs.rs_metropolis_B(0.01, workload.beta_estimate(v)) for v in y], np.int32)
     t = torch.from_numpy(lw).to(dev)
     off = torch.from_numpy(offsets).to(dev)
     Bt = torch.from_numpy(Bs).to(dev)
@@ -582,7 +610,7 @@ def run_reference(args):
         return
     import oracle
     oracle.build()
-    N, B = workload_params(args)
+    N, B = workload_params(args, oracle.metropolis_B)
     n_sample = min(N, 1 << 18)
     lws = [workload.synthetic_logw(n_sample, args.y, seed=SEED + 5, dtype=np.float32),
            workload.synthetic_logw(n_sample, args.y, seed=SEED + 5, dtype=np.float64)]
@@ -601,15 +629,124 @@ def run_reference(args):
         "n_gpus": 0, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": round(el / args.steps * 1e3, 3), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
-        "config": {"workload": f"N=2^{args.log2n} single filter, y={args.y}, B={B}, "
-                               "5 resamplers x {f32, f64} + Permute + offspring conversions",
-                   "sample_N": n_sample},
+        "config": workload_config(args, N, B),
         "cpu_baseline": {"value": round(value, 6), "unit": UNIT, "cores": 1, "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": round(value, 6), "unit": UNIT, "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line))
+
+
+def sweep_hbm_bytes(scheme: int, S: int, N: int) -> int:
+    """Algorithmic HBM bytes of one call with Permute: scan schemes read the log-weights twice
+    and write the ancestors (the multinomial also writes and re-reads its cumulative weights,
+    S bytes each), Metropolis / rejection read each particle's own log-weight and write its
+    ancestor; Permute writes and reads the claims, reads the ancestors, writes the result."""
+    per = {0: 3 * S + 4, 1: 2 * S + 4, 2: 2 * S + 4, 3: S + 4, 4: S + 4}[scheme]
+    return (per + 16) * N
+
+
+def run_sweep(args):
+    import statistics
+    import torch
+    import paper_1301_4019_gb300 as rs
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) \
+        if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device="cuda")
+    rows = []
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    with rs.Handle(1 << 24) as h:
+        rs.rs_set_launch_mode(h, LAUNCH_MODES[args.launch_mode])
+        for log2n in range(10, 25):
+            N = 1 << log2n
+            B = workload_params(argparse.Namespace(log2n=log2n, y=args.y))[1]
+            out = torch.empty(N, dtype=torch.int32, device="cuda")
+            for name, npdt in (("f32", np.float32), ("f64", np.float64)):
+                lw = torch.from_numpy(workload.synthetic_logw(N, args.y, seed=SEED + log2n,
+                                                              dtype=npdt)).cuda()
+                S = 4 if name == "f32" else 8
+                for scheme in range(5):
+                    for k in range(3):
+                        rs.rs_resample(h, scheme, lw, B=B, seed=SEED, step=k, out=out,
+                                       permute=True, log_wmax=0.0)
+                    ts = []
+                    for k in range(args.sweep_reps):
+                        flush.fill_(float(k))
+                        e0 = torch.cuda.Event(enable_timing=True)
+                        e1 = torch.cuda.Event(enable_timing=True)
+                        e0.record()
+                        rs.rs_resample(h, scheme, lw, B=B, seed=SEED, step=k, out=out,
+                                       permute=True, log_wmax=0.0)
+                        e1.record()
+                        torch.cuda.synchronize()
+                        ts.append(e0.elapsed_time(e1))
+                    ms = statistics.median(ts)
+                    gbs = sweep_hbm_bytes(scheme, S, N) / (ms * 1e-3) / 1e9
+                    rows.append({"log2n": log2n, "dtype": name, "scheme": SCHEME_NAMES[scheme],
+                                 "us": round(ms * 1e3, 2),
+                                 "G_ancestors_per_s": round(N / (ms * 1e-3) / 1e9, 3),
+                                 "hbm_frac": round(gbs / hbm_peak, 4)})
+                del lw
+        st = rs.rs_last_error(h)
+    clk = clocks.stop()
+    if st != rs.RS_OK:
+        raise SystemExit(f"device status after sweep: {rs.rs_strerror(st)}")
+    print(json.dumps({"sweep": "N = 2^10 .. 2^24, y = %g, B from Eq. B, log_wmax = 0, with "
+                      "Permute; median of %d calls, each after writing %d MiB (L2 flush); "
+                      "hbm_frac = algorithmic bytes (sweep_hbm_bytes) / time / %.1f GB/s "
+                      "(measured)" % (args.y, args.sweep_reps, 2 * L2_BYTES // 2**20, hbm_peak),
+                      "launch_mode": args.launch_mode, "clocks": clk, "rows": rows}))
+
+
+def run_precision(args):
+    """Mean absolute offspring bias mean_i |mean_r o_i - N pi_i| over R repeats (seeds differ
+    by the step counter) of one weight set, against the Monte Carlo noise floor
+    sqrt(mean_i Var(o_i) / R); pi from the input log-weights in binary64 (numpy). The
+    offspring are counted on the GPU (rs_offspring) and summed there."""
+    import torch
+    import paper_1301_4019_gb300 as rs
+    R = args.precision_reps
+    modes = [("f32 plain", np.float32, rs.PREC_PLAIN), ("f32 compensated", np.float32,
+              rs.PREC_COMPENSATED), ("f64", np.float64, rs.PREC_PLAIN)]
+    rows = []
+    with rs.Handle(1 << 24) as h:
+        for log2n in (16, 18, 20, 22, 24):
+            N = 1 << log2n
+            out = torch.empty(N, dtype=torch.int32, device="cuda")
+            o = torch.empty(N, dtype=torch.int32, device="cuda")
+            for y in (0.0, 2.0, 4.0):
+                lw64 = workload.synthetic_logw(N, y, seed=SEED + 300 + log2n, dtype=np.float64)
+                for label, npdt, prec in modes:
+                    lw_in = lw64.astype(npdt)
+                    w = np.exp(lw_in.astype(np.float64) - lw_in.max())
+                    Npi = torch.from_numpy(N * w / math.fsum(w)).cuda()
+                    lw = torch.from_numpy(lw_in).cuda()
+                    for scheme in (rs.MULTINOMIAL, rs.STRATIFIED, rs.SYSTEMATIC):
+                        s1 = torch.zeros(N, dtype=torch.float64, device="cuda")
+                        s2 = torch.zeros(N, dtype=torch.float64, device="cuda")
+                        for r in range(R):
+                            rs.rs_resample(h, scheme, lw, seed=SEED + 7, step=r, out=out,
+                                           prec=prec)
+                            rs.rs_offspring(h, out, o)
+                            od = o.double()
+                            s1 += od
+                            s2 += od * od
+                        mean = s1 / R
+                        var = (s2 / R - mean * mean).clamp_min(0) * R / max(R - 1, 1)
+                        rows.append({"log2n": log2n, "y": y, "mode": label,
+                                     "scheme": SCHEME_NAMES[scheme],
+                                     "mean_abs_bias": float((mean - Npi).abs().mean()),
+                                     "noise_floor": float(torch.sqrt(var.mean() / R))})
+                    del lw, Npi
+        st = rs.rs_last_error(h)
+    if st != rs.RS_OK:
+        raise SystemExit(f"device status after precision study: {rs.rs_strerror(st)}")
+    print(json.dumps({"precision": f"{R} repeats per row (seed fixed, step = repeat index); "
+                      "bias = mean_i |mean o_i - N pi_i|, pi from the input log-weights in "
+                      "binary64; noise floor = sqrt(mean_i Var(o_i) / R)", "rows": rows}))
 
 
 def run_single(args):
@@ -646,6 +783,10 @@ def main():
     args = parse_args()
     if args.single:
         run_single(args)
+    elif args.sweep:
+        run_sweep(args)
+    elif args.precision:
+        run_precision(args)
     elif args.impl == "reference":
         run_reference(args)
     else:
