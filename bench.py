@@ -70,6 +70,9 @@ def parse_args():
                    help="offspring bias of the scan schemes: binary32 plain vs compensated vs "
                         "binary64, N = 2^16 .. 2^24, y in {0, 2, 4}; one JSON line")
     p.add_argument("--precision-reps", type=int, default=400)
+    p.add_argument("--smc", action="store_true",
+                   help="full bootstrap SMC loop (Code 1) on the linear-Gaussian model, "
+                        "N = 2^20, T = 100, systematic / Metropolis / rejection; one JSON line")
     p.add_argument("--single", default=None,
                    help="profile one call: scheme:dtype[:prec], e.g. metropolis:f32 "
                         "(runs warmup + steps calls with Permute, prints one JSON line)")
@@ -749,6 +752,63 @@ def run_precision(args):
                       "binary64; noise floor = sqrt(mean_i Var(o_i) / R)", "rows": rows}))
 
 
+def run_smc(args):
+    """Time the bootstrap filter (resample with Permute, in-place copy, propagate + weight,
+    log-sum of the weights) over T = 100 observations of the linear-Gaussian model, captured
+    as one CUDA graph per scheme and replayed; also report the filter's log-likelihood
+    estimates over a few seeds (the tests check them against the Kalman filter)."""
+    import statistics
+    import torch
+    import paper_1301_4019_gb300 as rs
+    from paper_1301_4019_gb300 import smc
+    N, T, reps = 1 << args.log2n, 100, 5
+    phi, sx, sy = workload.LGSSM_PHI, workload.LGSSM_SIGMA_X, workload.LGSSM_SIGMA_Y
+    _, y = workload.lgssm_simulate(T, phi, sx, sy, seed=SEED)
+    rows = []
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    with rs.Handle(N) as h:
+        rs.rs_set_launch_mode(h, LAUNCH_MODES[args.launch_mode])
+        for scheme in (rs.SYSTEMATIC, rs.METROPOLIS, rs.REJECTION):
+            lls = [smc.lgssm_bootstrap(h, y, N, scheme, phi, sx, sy, seed=s, B=64)
+                   for s in range(4)]
+            bufs = smc.LgssmBuffers(N, T)
+            cs = torch.cuda.Stream()
+            cs.wait_stream(torch.cuda.current_stream())
+            with torch.cuda.stream(cs):
+                smc.lgssm_bootstrap_launch(h, y, N, scheme, phi, sx, sy, seed=7, bufs=bufs,
+                                           stream=cs)
+                torch.cuda.synchronize()
+                g = torch.cuda.CUDAGraph()
+                with torch.cuda.graph(g, stream=cs):
+                    smc.lgssm_bootstrap_launch(h, y, N, scheme, phi, sx, sy, seed=7,
+                                               bufs=bufs, stream=cs)
+            torch.cuda.current_stream().wait_stream(cs)
+            g.replay()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(reps):
+                g.replay()
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / reps
+            rows.append({"scheme": SCHEME_NAMES[scheme], "ms_per_filter": round(ms, 3),
+                         "us_per_step": round(1e3 * ms / T, 2),
+                         "G_particle_steps_per_s": round(N * T / (ms * 1e-3) / 1e9, 3),
+                         "loglik_mean": round(statistics.mean(lls), 4),
+                         "loglik_sd": round(statistics.stdev(lls), 4)})
+        st = rs.rs_last_error(h)
+    clk = clocks.stop()
+    if st != rs.RS_OK:
+        raise SystemExit(f"device status after SMC study: {rs.rs_strerror(st)}")
+    print(json.dumps({"smc": f"bootstrap filter, N = 2^{args.log2n}, T = {T}, model "
+                      f"x_t = {phi} x_t-1 + N(0, {sx}^2), y_t = x_t + N(0, {sy}^2); per step: "
+                      "resample (compensated binary32, Permute), in-place copy, propagate + "
+                      "weight, log-sum of the weights; Metropolis B = 64; one CUDA graph per "
+                      f"filter run, {reps} replays", "clocks": clk, "rows": rows}))
+
+
 def run_single(args):
     """One resample configuration on one input, for profilers: warmup + steps calls."""
     import torch
@@ -787,6 +847,8 @@ def main():
         run_sweep(args)
     elif args.precision:
         run_precision(args)
+    elif args.smc:
+        run_smc(args)
     elif args.impl == "reference":
         run_reference(args)
     else:

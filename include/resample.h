@@ -180,6 +180,28 @@ int rs_permute(rs_handle* h, const int32_t* a_dev, int64_t N, int32_t* c_dev, vo
 #define RS_LAUNCH_SEPARATE 2
 int rs_set_launch_mode(rs_handle* h, int mode);
 
+/* ---- the SMC loop around the resampler (Code 1) ---------------------------------------
+ * In-place copy by a permuted ancestry (Section 2.3): x_dev holds N rows of D floats
+ * (row-major, device); row i becomes row c_dev[i]. c must satisfy the predicate of Permute
+ * (o_j > 0 implies c_j = j, as rs_resample(permute = 1) returns): then every row that is read
+ * is one that is not written, and the copy runs in place. Rows i with c_i outside 0..N-1 or
+ * c_{c_i} != c_i are left unchanged and reported as RS_ERR_ARG through rs_last_error. */
+int rs_copy_ancestors(rs_handle* h, float* x_dev, int32_t D, const int32_t* c_dev, int64_t N,
+                      void* stream);
+
+/* Propagate and weight N particles of the 1-D linear-Gaussian state-space model
+ *   x_1 ~ N(0, sigma_x^2 / (1 - phi^2)),  x_t = phi x_{t-1} + sigma_x eps_t,
+ *   y_t = x_t + sigma_y eta_t
+ * (the model of the full SMC loop; Code 1 lines "propagate" and "weight"). init = 1 draws x
+ * from the stationary law, init = 0 propagates x in place. Writes logw_dev[i] =
+ * -(y - x_i)^2 / (2 sigma_y^2) (the constant -log(2 pi sigma_y^2)/2 is dropped, so
+ * log w_max = 0). The noise of particle i is one Box-Muller normal from the Philox words 0
+ * and 1 of counter (i, 0, step, filter * 8 + 5). |phi| < 1, sigma_x, sigma_y > 0 and y finite
+ * (RS_ERR_ARG otherwise). */
+int rs_lgssm_step(rs_handle* h, float* x_dev, int64_t N, int init, float phi, float sigma_x,
+                  float y, float sigma_y, uint64_t seed, uint64_t step, uint32_t filter,
+                  float* logw_dev, void* stream);
+
 /* B* = log(eps) / log(1 - beta) of Eq. (B) (Section 2.1), rounded up: the number of
  * Metropolis steps that bounds the total-variation distance of every chain by eps, for a
  * lower bound beta on min_i(mean(w)/w^i) (Eq. beta), e.g. E(w)/w_max (Eq. beta2).

@@ -39,7 +39,7 @@ EXPORTED = [
     "rs_cumulative_offspring", "rs_adjacent_difference", "rs_cumulative_offspring_to_ancestors",
     "rs_prepermute", "rs_permute", "rs_metropolis_B", "rs_last_error", "rs_strerror",
     "rs_trace", "rs_trace_count", "rs_trace_label", "rs_systematic_noalloc",
-    "rs_resample_batched", "rs_set_launch_mode",
+    "rs_resample_batched", "rs_set_launch_mode", "rs_copy_ancestors", "rs_lgssm_step",
 ]
 NOALLOC_MAX_N = 1 << 22
 LAUNCH_AUTO, LAUNCH_FUSED, LAUNCH_SEPARATE = 0, 1, 2
@@ -99,6 +99,9 @@ def _declare(lib):
         "rs_resample_batched": (I, [P, I, I, P, P, I32, P, I32, U64, U64, P, I,
                                     C.POINTER(_Opts), P]),
         "rs_set_launch_mode": (I, [P, I]),
+        "rs_copy_ancestors": (I, [P, P, I32, P, I64, P]),
+        "rs_lgssm_step": (I, [P, P, I64, I, C.c_float, C.c_float, C.c_float, C.c_float, U64,
+                              U64, C.c_uint32, P, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -297,6 +300,33 @@ def rs_set_launch_mode(h: Handle, mode: int) -> None:
     """LAUNCH_AUTO, LAUNCH_FUSED (one cooperative kernel) or LAUNCH_SEPARATE (one kernel per
     pass) for the scan-based schemes of rs_resample; results are identical in every mode."""
     _check(load().rs_set_launch_mode(h.ptr, int(mode)), "rs_set_launch_mode")
+
+
+def rs_copy_ancestors(h: Handle, x: torch.Tensor, c: torch.Tensor, stream=None) -> torch.Tensor:
+    """In place: row i of x ([N] or [N, D] float32) becomes row c[i] (c from Permute)."""
+    N = c.numel()
+    D = 1 if x.dim() == 1 else x.shape[1]
+    if x.shape[0] != N:
+        raise ValueError("x and c disagree on N")
+    _check(load().rs_copy_ancestors(h.ptr, _dev(x, torch.float32, "x"), D,
+                                    _dev(c, torch.int32, "c"), N, _stream(stream)),
+           "rs_copy_ancestors")
+    return x
+
+
+def rs_lgssm_step(h: Handle, x: torch.Tensor, init: bool, phi: float, sigma_x: float, y: float,
+                  sigma_y: float, seed: int = 0, step: int = 0, filter: int = 0,
+                  logw: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """Propagate x in place (or draw it from the stationary law) and return the log-weights."""
+    N = x.numel()
+    if logw is None:
+        logw = torch.empty(N, dtype=torch.float32, device=x.device)
+    _check(load().rs_lgssm_step(h.ptr, _dev(x, torch.float32, "x"), N, int(bool(init)),
+                                float(phi), float(sigma_x), float(y), float(sigma_y),
+                                int(seed), int(step), int(filter),
+                                _dev(logw, torch.float32, "logw"), _stream(stream)),
+           "rs_lgssm_step")
+    return logw
 
 
 def rs_metropolis_B(eps: float, beta: float) -> int:

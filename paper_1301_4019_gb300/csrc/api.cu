@@ -353,6 +353,35 @@ int rs_set_launch_mode(rs_handle* h, int mode) {
   return RS_OK;
 }
 
+int rs_copy_ancestors(rs_handle* h, float* x_dev, int32_t D, const int32_t* c_dev, int64_t N,
+                      void* stream) {
+  if (!h || !x_dev || !c_dev || D < 1) return RS_ERR_ARG;
+  int st = check_n(nullptr, N);
+  if (st != RS_OK) return st;
+  if (N > INT64_MAX / D) return RS_ERR_ARG;
+  if ((st = set_device(h)) != RS_OK) return st;
+  const cudaError_t e = rsk::launch_copy_ancestors(h->s, x_dev, D, c_dev, N, as_stream(stream));
+  end_mark(h, as_stream(stream));
+  return cuda_status(e);
+}
+
+int rs_lgssm_step(rs_handle* h, float* x_dev, int64_t N, int init, float phi, float sigma_x,
+                  float y, float sigma_y, uint64_t seed, uint64_t step, uint32_t filter,
+                  float* logw_dev, void* stream) {
+  if (!h || !x_dev || !logw_dev) return RS_ERR_ARG;
+  int st = check_n(nullptr, N);
+  if (st != RS_OK) return st;
+  if (init != 0 && init != 1) return RS_ERR_ARG;
+  if (!(std::fabs(phi) < 1.0f) || !(sigma_x > 0.0f) || !(sigma_y > 0.0f) || !std::isfinite(y) ||
+      !std::isfinite(sigma_x) || !std::isfinite(sigma_y) || filter >= (1u << 29))
+    return RS_ERR_ARG;
+  if ((st = set_device(h)) != RS_OK) return st;
+  const cudaError_t e = rsk::launch_lgssm_step(h->s, x_dev, N, init, phi, sigma_x, y, sigma_y,
+                                               seed, step, filter, logw_dev, as_stream(stream));
+  end_mark(h, as_stream(stream));
+  return cuda_status(e);
+}
+
 int rs_metropolis_B(double eps, double beta, int32_t* B) {
   if (!B || !(eps > 0.0 && eps < 1.0) || !(beta > 0.0 && beta <= 1.0)) return RS_ERR_ARG;
   if (beta >= 1.0) {

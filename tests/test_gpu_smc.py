@@ -1,0 +1,91 @@
+"""GPU tests of the full SMC loop (Code 1) around the resampler: the in-place copy by a permuted
+ancestry equals the gather x[c]; the linear-Gaussian propagate-and-weight kernel equals its
+formula evaluated on the host from the oracle's Philox words; and the bootstrap filter's log
+marginal likelihood agrees with the Kalman filter's closed form (oracle/kalman.py) within
+4 seed-to-seed standard deviations, for the systematic, Metropolis and rejection resamplers."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import workload
+from oracle import kalman
+
+pytestmark = pytest.mark.gpu
+DEV = "cuda:0"
+PHI, SX, SY = workload.LGSSM_PHI, workload.LGSSM_SIGMA_X, workload.LGSSM_SIGMA_Y
+
+
+@pytest.fixture(scope="module")
+def h(rs):
+    handle = rs.Handle(1 << 20)
+    yield handle
+    handle.close()
+
+
+@pytest.mark.parametrize("scheme", [2, 3, 0])
+@pytest.mark.parametrize("D", [1, 3])
+def test_copy_in_place_equals_gather(rs, h, scheme, D):
+    N = 50003
+    lw = torch.from_numpy(workload.synthetic_logw(N, 2.5, seed=4, dtype=np.float32)).to(DEV)
+    c = rs.rs_resample(h, scheme, lw, B=32, seed=9, permute=True)
+    rng = np.random.default_rng(D)
+    x0 = rng.standard_normal((N, D)).astype(np.float32)
+    x = torch.from_numpy(x0.copy() if D > 1 else x0[:, 0].copy()).to(DEV)
+    rs.rs_copy_ancestors(h, x, c)
+    assert rs.rs_last_error(h) == rs.RS_OK
+    want = x0[c.cpu().numpy()]
+    got = x.cpu().numpy().reshape(N, D)
+    assert np.array_equal(got, want)
+
+
+def test_copy_rejects_an_ancestry_without_the_predicate(rs, h):
+    N = 1000
+    c = torch.arange(N - 1, -1, -1, dtype=torch.int32, device=DEV)  # c[c_i] != c_i mostly
+    x = torch.arange(N, dtype=torch.float32, device=DEV)
+    rs.rs_copy_ancestors(h, x, c)
+    assert rs.rs_last_error(h) == rs.RS_ERR_ARG
+
+
+def _normal_host(seed, i, step, filt=0):
+    w = oracle.draw(seed, int(i), 0, step, filt, 5)
+    u1 = 1.0 - float(int(w[0]) >> 8) * 2.0 ** -24
+    u2 = float(int(w[1]) >> 8) * 2.0 ** -24
+    return math.sqrt(-2.0 * math.log(u1)) * math.cos(2.0 * math.pi * u2)
+
+
+def test_lgssm_step_matches_host_formula(rs, h):
+    N = 4099
+    x = torch.empty(N, dtype=torch.float32, device=DEV)
+    logw = rs.rs_lgssm_step(h, x, True, PHI, SX, 0.7, SY, seed=3, step=0)
+    x0 = x.cpu().numpy().astype(np.float64)
+    s0 = SX / math.sqrt(1 - PHI * PHI)
+    idx = np.arange(0, N, 37)
+    want0 = np.array([s0 * _normal_host(3, i, 0) for i in idx])
+    assert np.allclose(x0[idx], want0, rtol=2e-6, atol=2e-6)
+    assert np.allclose(logw.cpu().numpy()[idx], -(0.7 - x0[idx]) ** 2 / (2 * SY * SY),
+                       rtol=1e-5, atol=1e-6)
+    logw = rs.rs_lgssm_step(h, x, False, PHI, SX, -1.3, SY, seed=3, step=5)
+    x1 = x.cpu().numpy().astype(np.float64)
+    want1 = np.array([PHI * x0[i] + SX * _normal_host(3, i, 5) for i in idx])
+    assert np.allclose(x1[idx], want1, rtol=2e-6, atol=4e-6)
+    assert rs.rs_last_error(h) == rs.RS_OK
+
+
+@pytest.mark.parametrize("scheme", [2, 3, 4])
+def test_bootstrap_loglik_matches_kalman(rs, h, scheme):
+    from paper_1301_4019_gb300 import smc
+    T, N = 100, 1 << 16
+    _, y = workload.lgssm_simulate(T, PHI, SX, SY, seed=21)
+    want = kalman.lgssm_loglik(y, PHI, SX, SY)
+    lls = [smc.lgssm_bootstrap(h, y, N, scheme, PHI, SX, SY, seed=s, B=64) for s in range(16)]
+    assert rs.rs_last_error(h) == rs.RS_OK
+    lls = np.array(lls)
+    sd = lls.std(ddof=1)
+    assert sd < 0.5
+    assert abs(lls.mean() - want) < 4 * sd, (lls.mean(), want, sd)
+    # the full-size filter (N = 2^20): its own spread is a quarter of the 2^16 one
+    ll = smc.lgssm_bootstrap(h, y, 1 << 20, scheme, PHI, SX, SY, seed=99, B=64)
+    assert abs(ll - want) < 4 * sd / 4 + 0.02, (ll, want, sd)

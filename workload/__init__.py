@@ -69,3 +69,23 @@ def ragged_logw(sizes: np.ndarray, y_lo: float = 0.0, y_hi: float = 4.0,
     yy = np.repeat(y, sizes)
     lw = (-0.5 * (x - yy) ** 2).astype(dtype)
     return offsets, lw, y
+
+
+# ---------------------------------------------------------------------------------------
+# The state-space model of the full SMC loop (Code 1): a 1-D linear-Gaussian model
+#   x_1 ~ N(0, sigma_x^2 / (1 - phi^2))  (the stationary law),
+#   x_t = phi x_{t-1} + sigma_x eps_t,   y_t = x_t + sigma_y eta_t,   eps, eta ~ N(0, 1).
+# ---------------------------------------------------------------------------------------
+LGSSM_PHI, LGSSM_SIGMA_X, LGSSM_SIGMA_Y = 0.9, 1.0, 0.5
+
+
+def lgssm_simulate(T: int, phi: float = LGSSM_PHI, sigma_x: float = LGSSM_SIGMA_X,
+                   sigma_y: float = LGSSM_SIGMA_Y, seed: int = DEFAULT_SEED):
+    """T steps of the model: (x, y), float64 arrays."""
+    rng = np.random.Generator(np.random.PCG64(seed + 7))
+    x = np.empty(T)
+    x[0] = rng.standard_normal() * sigma_x / math.sqrt(1.0 - phi * phi)
+    for t in range(1, T):
+        x[t] = phi * x[t - 1] + sigma_x * rng.standard_normal()
+    y = x + sigma_y * rng.standard_normal(T)
+    return x, y
