@@ -10,6 +10,7 @@ namespace {
 
 // p[0..N) = v with 128-bit stores where p is 16-byte aligned.
 __global__ void __launch_bounds__(kBlock) fill_kernel(int32_t* __restrict__ p, int64_t N, int32_t v) {
+  pdl_wait();
   const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
   const int64_t t0 = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
   const int64_t head = ((16 - (reinterpret_cast<uintptr_t>(p) & 15u)) & 15u) / 4;  // to alignment
@@ -25,6 +26,7 @@ __global__ void __launch_bounds__(kBlock) fill_kernel(int32_t* __restrict__ p, i
 // Prepermute: d[a_i] = min(d[a_i], i) (d initialised to the sentinel N beforehand).
 __global__ void __launch_bounds__(kBlock)
 prepermute_kernel(const int32_t* __restrict__ a, int64_t N, int32_t* __restrict__ d, int* err) {
+  pdl_wait();
   const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
   if (i >= N) return;
   const int32_t ai = a[i];
@@ -39,6 +41,7 @@ prepermute_kernel(const int32_t* __restrict__ a, int64_t N, int32_t* __restrict_
 __global__ void __launch_bounds__(kBlock)
 permute_kernel(const int32_t* __restrict__ a, const int32_t* __restrict__ d, int64_t N,
                int32_t* __restrict__ c, int* err) {
+  pdl_wait();
   const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
   if (i >= N) return;
   permute_one(a, d, N, c, i, err);
@@ -48,6 +51,7 @@ permute_kernel(const int32_t* __restrict__ a, const int32_t* __restrict__ d, int
 __global__ void __launch_bounds__(kBlock)
 permute_sorted_kernel(const int32_t* __restrict__ a, const int32_t* __restrict__ d, int64_t N,
                       int32_t* __restrict__ c, int* err) {
+  pdl_wait();
   const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
   if (i >= N) return;
   permute_sorted_one(a, d, N, c, i, err);
@@ -56,6 +60,7 @@ permute_sorted_kernel(const int32_t* __restrict__ a, const int32_t* __restrict__
 // Ancestors-to-Offspring (Code 12).
 __global__ void __launch_bounds__(kBlock)
 offspring_kernel(const int32_t* __restrict__ a, int64_t N, int32_t* __restrict__ o, int* err) {
+  pdl_wait();
   const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
   if (i >= N) return;
   const int32_t ai = a[i];
@@ -69,6 +74,7 @@ offspring_kernel(const int32_t* __restrict__ a, int64_t N, int32_t* __restrict__
 // Adjacent-Difference: o_i = O_i - O_{i-1} (o_0 = O_0).
 __global__ void __launch_bounds__(kBlock)
 adjacent_difference_kernel(const int32_t* __restrict__ O, int64_t N, int32_t* __restrict__ o) {
+  pdl_wait();
   const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
   if (i >= N) return;
   o[i] = i == 0 ? O[0] : O[i] - O[i - 1];
@@ -78,6 +84,7 @@ adjacent_difference_kernel(const int32_t* __restrict__ O, int64_t N, int32_t* __
 __global__ void __launch_bounds__(kBlock)
 cumoff_to_ancestors_kernel(const int32_t* __restrict__ O, int64_t N, int32_t* __restrict__ a,
                            int* err) {
+  pdl_wait();
   const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
   if (i >= N) return;
   const int64_t start = i == 0 ? 0 : O[i - 1];
@@ -128,6 +135,7 @@ __device__ __forceinline__ long long block_tile_scan(const int32_t* __restrict__
 __global__ void __launch_bounds__(kBlock)
 iscan_sum_kernel(const int32_t* __restrict__ in, int64_t N, long long* tot, long long* pre,
                  unsigned int* ticket) {
+  pdl_wait();
   __shared__ long long sh[kWarps];
   __shared__ bool am_last;
   long long v[16];
@@ -169,6 +177,7 @@ iscan_sum_kernel(const int32_t* __restrict__ in, int64_t N, long long* tot, long
 __global__ void __launch_bounds__(kBlock)
 iscan_emit_kernel(const int32_t* __restrict__ in, int64_t N, const long long* pre,
                   int32_t* __restrict__ out) {
+  pdl_wait();
   __shared__ long long sh[kWarps];
   long long v[16];
   const int64_t base = static_cast<int64_t>(blockIdx.x) * kIscanTile;
@@ -188,7 +197,7 @@ cudaError_t launch_fill(int32_t* p, int64_t N, int32_t v, cudaStream_t st) {
   int64_t g = (N / 4 + kBlock - 1) / kBlock;
   if (g < 1) g = 1;
   if (g > 152 * 16) g = 152 * 16;
-  fill_kernel<<<static_cast<int>(g), kBlock, 0, st>>>(p, N, v);
+  launch_pdl(fill_kernel, static_cast<int>(g), kBlock, st, p, N, v);
   return cudaGetLastError();
 }
 
@@ -200,21 +209,21 @@ cudaError_t launch_prepermute(const Scratch& s, const int32_t* a, int64_t N, int
     if (e != cudaSuccess) return e;
   }
   trace_mark(s.trace, "prepermute", st);
-  prepermute_kernel<<<grid_for(N), kBlock, 0, st>>>(a, N, d, s.err);
+  launch_pdl(prepermute_kernel, grid_for(N), kBlock, st, a, N, d, s.err);
   return cudaGetLastError();
 }
 
 cudaError_t launch_permute(const Scratch& s, const int32_t* a, const int32_t* d, int64_t N,
                            int32_t* c, cudaStream_t st) {
   trace_mark(s.trace, "permute", st);
-  permute_kernel<<<grid_for(N), kBlock, 0, st>>>(a, d, N, c, s.err);
+  launch_pdl(permute_kernel, grid_for(N), kBlock, st, a, d, N, c, s.err);
   return cudaGetLastError();
 }
 
 cudaError_t launch_permute_sorted(const Scratch& s, const int32_t* a, const int32_t* d, int64_t N,
                                   int32_t* c, cudaStream_t st) {
   trace_mark(s.trace, "permute_sorted", st);
-  permute_sorted_kernel<<<grid_for(N), kBlock, 0, st>>>(a, d, N, c, s.err);
+  launch_pdl(permute_sorted_kernel, grid_for(N), kBlock, st, a, d, N, c, s.err);
   return cudaGetLastError();
 }
 
@@ -224,7 +233,7 @@ cudaError_t launch_offspring(const Scratch& s, const int32_t* a, int64_t N, int3
   cudaError_t e = launch_fill(o, N, 0, st);
   if (e != cudaSuccess) return e;
   trace_mark(s.trace, "offspring", st);
-  offspring_kernel<<<grid_for(N), kBlock, 0, st>>>(a, N, o, s.err);
+  launch_pdl(offspring_kernel, grid_for(N), kBlock, st, a, N, o, s.err);
   return cudaGetLastError();
 }
 
@@ -234,22 +243,22 @@ cudaError_t launch_inclusive_scan_i32(const Scratch& s, const int32_t* o, int64_
   long long* tot = s.irec;
   long long* pre = s.irec + (s.max_tiles + 2);
   trace_mark(s.trace, "iscan_sum", st);
-  iscan_sum_kernel<<<tiles, kBlock, 0, st>>>(o, N, tot, pre, &s.glob->ticket_iscan);
+  launch_pdl(iscan_sum_kernel, tiles, kBlock, st, o, N, tot, pre, &s.glob->ticket_iscan);
   trace_mark(s.trace, "iscan_emit", st);
-  iscan_emit_kernel<<<tiles, kBlock, 0, st>>>(o, N, pre, O);
+  launch_pdl(iscan_emit_kernel, tiles, kBlock, st, o, N, pre, O);
   return cudaGetLastError();
 }
 
 cudaError_t launch_adjacent_difference(const int32_t* O, int64_t N, int32_t* o,
                                        cudaStream_t st) {
-  adjacent_difference_kernel<<<grid_for(N), kBlock, 0, st>>>(O, N, o);
+  launch_pdl(adjacent_difference_kernel, grid_for(N), kBlock, st, O, N, o);
   return cudaGetLastError();
 }
 
 cudaError_t launch_cumoff_to_ancestors(const Scratch& s, const int32_t* O, int64_t N,
                                        int32_t* a, cudaStream_t st) {
   trace_mark(s.trace, "cumoff_to_ancestors", st);
-  cumoff_to_ancestors_kernel<<<grid_for(N), kBlock, 0, st>>>(O, N, a, s.err);
+  launch_pdl(cumoff_to_ancestors_kernel, grid_for(N), kBlock, st, O, N, a, s.err);
   return cudaGetLastError();
 }
 

@@ -100,6 +100,7 @@ struct Batch {
 
 // Plan: tiles per filter and their exclusive prefix; per-filter maxima reset; offsets checked.
 __global__ void __launch_bounds__(1024) batch_plan_kernel(Batch b) {
+  pdl_wait();
   __shared__ int sh[32];
   const int F = b.F;
   const int chunk = (F + blockDim.x - 1) / blockDim.x;
@@ -153,6 +154,7 @@ __device__ __forceinline__ bool locate_tile(const Batch& b, int tile, TileLoc& L
 
 template <typename T>
 __global__ void __launch_bounds__(kBlock) batch_max_kernel(const T* __restrict__ lw, Batch b) {
+  pdl_wait();
   __shared__ long long sh[kWarps];
   TileLoc L;
   if (!locate_tile(b, blockIdx.x, L)) return;
@@ -194,6 +196,7 @@ __device__ __forceinline__ double filter_M(const Batch& b, int f) {
 
 template <typename T, typename V>
 __global__ void __launch_bounds__(kBlock) batch_sum_kernel(const T* __restrict__ lw, Batch b) {
+  pdl_wait();
   __shared__ TileSh<V> sh;
   __shared__ float2 sh_tab[64];
   TileLoc L;
@@ -210,6 +213,7 @@ __global__ void __launch_bounds__(kBlock) batch_sum_kernel(const T* __restrict__
 
 template <typename T, typename V>
 __global__ void __launch_bounds__(kBlock) batch_prefix_kernel(Batch b) {
+  pdl_wait();
   const int f = blockIdx.x;
   const int64_t lo = b.off[f], hi = b.off[f + 1], n = hi - lo;
   const int t0 = b.tile_start[f], nt = b.tile_start[f + 1] - t0;
@@ -230,6 +234,7 @@ template <typename T, typename V, int SCHEME>
 __global__ void __launch_bounds__(kBlock)
 batch_emit_kernel(const T* __restrict__ lw, Batch b, Keys base_keys,
                   int32_t* __restrict__ a, int32_t* __restrict__ d, V* __restrict__ W) {
+  pdl_wait();
   __shared__ TileSh<V> sh;
   __shared__ float2 sh_tab[64];
   TileLoc L;
@@ -270,6 +275,7 @@ template <typename T, typename V>
 __global__ void __launch_bounds__(kBlock)
 batch_search_kernel(const V* __restrict__ W, Batch b, int64_t total, Keys base_keys,
                     int32_t* __restrict__ a, int32_t* __restrict__ d) {
+  pdl_wait();
   const int64_t g = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
   PartLoc P;
   if (g >= total || !locate_particle(b.off, b.F, b.max_n, g, P)) return;
@@ -284,6 +290,7 @@ batch_search_kernel(const V* __restrict__ W, Batch b, int64_t total, Keys base_k
 __global__ void __launch_bounds__(kBlock)
 batch_fill_sentinel_kernel(const int64_t* __restrict__ off, int F, int64_t total,
                            int32_t* __restrict__ d) {
+  pdl_wait();
   const int64_t g = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
   PartLoc P;
   if (g >= total || !locate_particle(off, F, total, g, P)) return;
@@ -296,6 +303,7 @@ batch_mcmc_kernel(const T* __restrict__ lw, const int64_t* __restrict__ off, int
                   int64_t total, int scheme, const int32_t* __restrict__ Bf, int32_t B,
                   Keys base_keys, double log_wmax, int64_t max_trials,
                   int32_t* __restrict__ a, int32_t* __restrict__ d, int* err) {
+  pdl_wait();
   const int64_t g = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
   PartLoc P;
   if (g >= total) return;
@@ -327,6 +335,7 @@ __global__ void __launch_bounds__(kBlock)
 batch_rejection_kernel(const T* __restrict__ lw, const int64_t* __restrict__ off, int F,
                        int64_t total, Keys base_keys, double log_wmax, int64_t max_trials,
                        int32_t* __restrict__ a, int32_t* __restrict__ d, int* err) {
+  pdl_wait();
   const int lane = threadIdx.x & 31;
   const int64_t run = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
   const int64_t start = run * kRejRun;
@@ -385,6 +394,7 @@ __global__ void __launch_bounds__(kBlock)
 batch_permute_kernel(const int64_t* __restrict__ off, int F, int64_t total,
                      const int32_t* __restrict__ a, const int32_t* __restrict__ d,
                      int32_t* __restrict__ c, int* err) {
+  pdl_wait();
   const int64_t g = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
   PartLoc P;
   if (g >= total || !locate_particle(off, F, total, g, P)) return;
@@ -408,25 +418,25 @@ cudaError_t run_batched_scan(const Scratch& s, int scheme, const T* lw, const Ba
   constexpr int ai = Path<T, V>::id;
   const int tiles = static_cast<int>(cap_tiles);
   trace_mark(s.trace, "batch_max", st);
-  batch_max_kernel<T><<<tiles, kBlock, 0, st>>>(lw, b);
+  launch_pdl(batch_max_kernel<T>, tiles, kBlock, st, lw, b);
   trace_mark(s.trace, kLblSum[ai], st);
-  batch_sum_kernel<T, V><<<tiles, kBlock, 0, st>>>(lw, b);
+  launch_pdl(batch_sum_kernel<T, V>, tiles, kBlock, st, lw, b);
   trace_mark(s.trace, "batch_prefix", st);
-  batch_prefix_kernel<T, V><<<b.F, kBlock, 0, st>>>(b);
+  launch_pdl(batch_prefix_kernel<T, V>, b.F, kBlock, st, b);
   V* W = static_cast<V*>(s.W);
   trace_mark(s.trace, kLblEmit[ai], st);
   switch (scheme) {
     case RS_MULTINOMIAL:
-      batch_emit_kernel<T, V, RS_MULTINOMIAL><<<tiles, kBlock, 0, st>>>(lw, b, keys, a, d, W);
+      launch_pdl(batch_emit_kernel<T, V, RS_MULTINOMIAL>, tiles, kBlock, st, lw, b, keys, a, d, W);
       trace_mark(s.trace, kLblSearch[ai], st);
-      batch_search_kernel<T, V><<<grid_particles(s.max_n), kBlock, 0, st>>>(W, b, s.max_n, keys,
+      launch_pdl(batch_search_kernel<T, V>, grid_particles(s.max_n), kBlock, st, W, b, s.max_n, keys,
                                                                             a, d);
       break;
     case RS_STRATIFIED:
-      batch_emit_kernel<T, V, RS_STRATIFIED><<<tiles, kBlock, 0, st>>>(lw, b, keys, a, d, nullptr);
+      launch_pdl(batch_emit_kernel<T, V, RS_STRATIFIED>, tiles, kBlock, st, lw, b, keys, a, d, nullptr);
       break;
     default:
-      batch_emit_kernel<T, V, RS_SYSTEMATIC><<<tiles, kBlock, 0, st>>>(lw, b, keys, a, d, nullptr);
+      launch_pdl(batch_emit_kernel<T, V, RS_SYSTEMATIC>, tiles, kBlock, st, lw, b, keys, a, d, nullptr);
       break;
   }
   return cudaGetLastError();
@@ -448,7 +458,7 @@ cudaError_t launch_batched(const Scratch& s, int scheme, Acc acc, const void* lo
   if (scheme == RS_METROPOLIS || scheme == RS_REJECTION) {
     if (d) {
       trace_mark(s.trace, "batch_fill", st);
-      batch_fill_sentinel_kernel<<<grid_particles(total), kBlock, 0, st>>>(offsets, F, total, d);
+      launch_pdl(batch_fill_sentinel_kernel, grid_particles(total), kBlock, st, offsets, F, total, d);
     }
     trace_mark(s.trace, scheme == RS_METROPOLIS ? (f64 ? "batch_metropolis_f64" : "batch_metropolis_f32")
                                                 : (f64 ? "batch_rejection_f64" : "batch_rejection_f32"),
@@ -457,19 +467,19 @@ cudaError_t launch_batched(const Scratch& s, int scheme, Acc acc, const void* lo
                                            kBlock);
     if (scheme == RS_REJECTION) {
       if (f64)
-        batch_rejection_kernel<double><<<grid_runs, kBlock, 0, st>>>(
+        launch_pdl(batch_rejection_kernel<double>, grid_runs, kBlock, st,
             static_cast<const double*>(logw), offsets, F, total, keys, log_wmax, max_trials, a,
             d, s.err);
       else
-        batch_rejection_kernel<float><<<grid_runs, kBlock, 0, st>>>(
+        launch_pdl(batch_rejection_kernel<float>, grid_runs, kBlock, st,
             static_cast<const float*>(logw), offsets, F, total, keys, log_wmax, max_trials, a,
             d, s.err);
     } else if (f64) {
-      batch_mcmc_kernel<double><<<grid_particles(total), kBlock, 0, st>>>(
+      launch_pdl(batch_mcmc_kernel<double>, grid_particles(total), kBlock, st,
           static_cast<const double*>(logw), offsets, F, total, scheme, Bf, B, keys, log_wmax,
           max_trials, a, d, s.err);
     } else {
-      batch_mcmc_kernel<float><<<grid_particles(total), kBlock, 0, st>>>(
+      launch_pdl(batch_mcmc_kernel<float>, grid_particles(total), kBlock, st,
           static_cast<const float*>(logw), offsets, F, total, scheme, Bf, B, keys, log_wmax,
           max_trials, a, d, s.err);
     }
@@ -487,7 +497,7 @@ cudaError_t launch_batched(const Scratch& s, int scheme, Acc acc, const void* lo
     b.P_rec = s.batch_P_rec;
     b.err = s.err;
     trace_mark(s.trace, "batch_plan", st);
-    batch_plan_kernel<<<1, 1024, 0, st>>>(b);
+    launch_pdl(batch_plan_kernel, 1, 1024, st, b);
     // every filter adds at most one partial tile to the max_n / kTile full ones
     const int64_t cap_tiles = s.max_n / kTile + F + 1;
     switch (acc) {
@@ -512,7 +522,7 @@ cudaError_t launch_batched(const Scratch& s, int scheme, Acc acc, const void* lo
   if (e == cudaSuccess) e = cudaGetLastError();
   if (e == cudaSuccess && permute) {
     trace_mark(s.trace, "batch_permute", st);
-    batch_permute_kernel<<<grid_particles(total), kBlock, 0, st>>>(offsets, F, total, s.a_tmp,
+    launch_pdl(batch_permute_kernel, grid_particles(total), kBlock, st, offsets, F, total, s.a_tmp,
                                                                     s.d, out, s.err);
     e = cudaGetLastError();
   }

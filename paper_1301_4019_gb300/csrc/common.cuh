@@ -143,6 +143,31 @@ __device__ __forceinline__ double exp_pinned(double x) {
 }
 
 // ---------------------------------------------------------------------------------------
+// Programmatic dependent launch. Kernels of a call are launched with programmatic stream
+// serialization, so a kernel is set up while its predecessor drains; it waits here, before
+// touching memory, until the predecessor has completed and its writes are visible. (No
+// kernel triggers its dependents early: dependents parked on an SM during a multi-wave
+// predecessor measured slower.) A no-op for a kernel launched without the attribute.
+// ---------------------------------------------------------------------------------------
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, cudaStream_t st,
+                              Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, static_cast<Args&&>(args)...);
+}
+
+// ---------------------------------------------------------------------------------------
 // Log-weight classification.
 // ---------------------------------------------------------------------------------------
 template <typename T> __device__ __forceinline__ bool nonfinite_logw(T v) {

@@ -251,6 +251,8 @@ __device__ __forceinline__ void fused_body(const T* __restrict__ lw, const Fused
   }
   grid_barrier(&A.g->bar_count, target, A.err);
   const double Sd = __ldcg(&A.g->S_d);
+  // the kernels that follow (search, Permute) may launch now; they wait for this grid's end
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 
   // ---- phase 4: emission of this CTA's tiles -----------------------------------------------
   if (zero || !(Sd > 0.0)) {  // all weights zero (flagged): every particle keeps itself

@@ -18,6 +18,7 @@ template <typename T>
 __global__ void __launch_bounds__(kBlock)
 metropolis_kernel(const T* __restrict__ lw, int64_t N, int32_t B, Keys keys,
                   int32_t* __restrict__ a, int32_t* __restrict__ d, int* err) {
+  pdl_wait();
   const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
   if (i >= N) return;
   const int32_t k = metropolis_one(lw, N, B, keys, i, err);
@@ -30,6 +31,7 @@ template <typename T>
 __global__ void __launch_bounds__(kBlock)
 rejection_kernel(const T* __restrict__ lw, int64_t N, double log_wmax, int64_t max_trials,
                  Keys keys, int32_t* __restrict__ a, int32_t* __restrict__ d, int* err) {
+  pdl_wait();
   const int lane = threadIdx.x & 31;
   const int64_t run = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
   const int64_t start = run * kRejRun;
@@ -82,10 +84,10 @@ cudaError_t launch_metropolis(const Scratch& s, bool f64, const void* logw, int6
   const int grid = static_cast<int>((N + kBlock - 1) / kBlock);
   trace_mark(s.trace, f64 ? "metropolis_f64" : "metropolis_f32", st);
   if (f64)
-    metropolis_kernel<double><<<grid, kBlock, 0, st>>>(static_cast<const double*>(logw), N, B,
+    launch_pdl(metropolis_kernel<double>, grid, kBlock, st, static_cast<const double*>(logw), N, B,
                                                        keys, a_out, d, s.err);
   else
-    metropolis_kernel<float><<<grid, kBlock, 0, st>>>(static_cast<const float*>(logw), N, B,
+    launch_pdl(metropolis_kernel<float>, grid, kBlock, st, static_cast<const float*>(logw), N, B,
                                                       keys, a_out, d, s.err);
   return cudaGetLastError();
 }
@@ -99,11 +101,11 @@ cudaError_t launch_rejection(const Scratch& s, bool f64, const void* logw, int64
   const int grid = static_cast<int>((runs * 32 + kBlock - 1) / kBlock);
   trace_mark(s.trace, f64 ? "rejection_f64" : "rejection_f32", st);
   if (f64)
-    rejection_kernel<double><<<grid, kBlock, 0, st>>>(static_cast<const double*>(logw), N,
+    launch_pdl(rejection_kernel<double>, grid, kBlock, st, static_cast<const double*>(logw), N,
                                                       log_wmax, max_trials, keys, a_out, d,
                                                       s.err);
   else
-    rejection_kernel<float><<<grid, kBlock, 0, st>>>(static_cast<const float*>(logw), N,
+    launch_pdl(rejection_kernel<float>, grid, kBlock, st, static_cast<const float*>(logw), N,
                                                      log_wmax, max_trials, keys, a_out, d,
                                                      s.err);
   return cudaGetLastError();

@@ -16,6 +16,7 @@ namespace {
 __global__ void __launch_bounds__(kBlock)
 copy_ancestors_kernel(float* __restrict__ x, int D, const int32_t* __restrict__ c, int64_t N,
                       int* err) {
+  pdl_wait();
   const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
   if (i >= N) return;
   const int32_t ci = c[i];
@@ -39,6 +40,7 @@ __device__ __forceinline__ float normal_draw(const Keys& keys, int64_t i) {
 __global__ void __launch_bounds__(kBlock)
 lgssm_step_kernel(float* __restrict__ x, int64_t N, int init, float phi, float sigma_x,
                   float sigma_0, float y, float inv_2vy, Keys keys, float* __restrict__ logw) {
+  pdl_wait();
   const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
   if (i >= N) return;
   const float z = normal_draw(keys, i);
@@ -55,7 +57,7 @@ inline int grid_for(int64_t N) { return static_cast<int>((N + kBlock - 1) / kBlo
 cudaError_t launch_copy_ancestors(const Scratch& s, float* x, int D, const int32_t* c, int64_t N,
                                   cudaStream_t st) {
   trace_mark(s.trace, "copy_ancestors", st);
-  copy_ancestors_kernel<<<grid_for(N), kBlock, 0, st>>>(x, D, c, N, s.err);
+  launch_pdl(copy_ancestors_kernel, grid_for(N), kBlock, st, x, D, c, N, s.err);
   return cudaGetLastError();
 }
 
@@ -65,7 +67,7 @@ cudaError_t launch_lgssm_step(const Scratch& s, float* x, int64_t N, int init, f
   const double s0 = static_cast<double>(sigma_x) / std::sqrt(1.0 - static_cast<double>(phi) * phi);
   const float inv_2vy = static_cast<float>(0.5 / (static_cast<double>(sigma_y) * sigma_y));
   trace_mark(s.trace, "lgssm_step", st);
-  lgssm_step_kernel<<<grid_for(N), kBlock, 0, st>>>(x, N, init, phi, sigma_x,
+  launch_pdl(lgssm_step_kernel, grid_for(N), kBlock, st, x, N, init, phi, sigma_x,
                                                    static_cast<float>(s0), y, inv_2vy,
                                                    make_keys(seed, step, filter, 5u), logw);
   return cudaGetLastError();

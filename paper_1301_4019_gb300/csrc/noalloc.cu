@@ -35,6 +35,7 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 
 // Resets the state that must start clean: the status word and the last-CTA counters.
 __global__ void noalloc_begin_kernel() {
+  pdl_wait();
   ScanGlob* g = reinterpret_cast<ScanGlob*>(g_noalloc_scratch + kOffGlob);
   g->ticket_max = 0u;
   g->ticket_tile = 0u;
@@ -44,6 +45,7 @@ __global__ void noalloc_begin_kernel() {
 
 // Copies the call's device-side status to the caller's output word.
 __global__ void noalloc_end_kernel(int32_t* status) {
+  pdl_wait();
   const int v = *reinterpret_cast<const int*>(g_noalloc_scratch + kOffErr);
   *status = (v == kNoError) ? RS_OK : -v;
 }
@@ -91,13 +93,13 @@ extern "C" int rs_systematic_noalloc(int dtype, const void* logw_dev, int64_t N,
   s.max_tiles = kNoAllocMaxTiles;
   s.max_blocks = kNoAllocMaxBlocks;
   const cudaStream_t cs = static_cast<cudaStream_t>(stream);
-  noalloc_begin_kernel<<<1, 1, 0, cs>>>();
+  launch_pdl(noalloc_begin_kernel, 1, 1, cs);
   cudaError_t e = cudaGetLastError();
   if (e == cudaSuccess)
     e = launch_scan_resample(s, RS_SYSTEMATIC, dtype == RS_F64 ? Acc::F64 : Acc::F32, logw_dev, N,
                              seed, step, 0u, ancestors_dev, nullptr, false, cs);
   if (e == cudaSuccess && status_dev) {
-    noalloc_end_kernel<<<1, 1, 0, cs>>>(status_dev);
+    launch_pdl(noalloc_end_kernel, 1, 1, cs, status_dev);
     e = cudaGetLastError();
   }
   return e == cudaSuccess ? RS_OK : RS_ERR_CUDA;

@@ -61,6 +61,7 @@ template <typename T>
 __global__ void __launch_bounds__(kBlock)
 max_kernel(const T* __restrict__ lw, int64_t N, ScanGlob* g, double* blockmax, int* err,
            int32_t* d_init) {
+  pdl_wait();
   __shared__ long long sh[kWarps];
   __shared__ bool am_last;
   const long long kMin = max_key(neg_inf<T>());
@@ -147,6 +148,7 @@ template <typename T, typename V>
 __global__ void __launch_bounds__(kBlock, 4)
 tile_sum_kernel(const T* __restrict__ lw, int64_t N, ScanGlob* g, double2* s_rec,
                 double2* P_rec, int* err, double* log_total_out) {
+  pdl_wait();
   __shared__ TileSh<V> sh;
   __shared__ float2 sh_tab[64];
   __shared__ bool am_last;
@@ -179,6 +181,7 @@ __global__ void __launch_bounds__(kBlock)
 emit_cumoff_kernel(const T* __restrict__ lw, int64_t N, const ScanGlob* g, const double2* s_rec,
                    const double2* P_rec, Keys keys, int32_t* __restrict__ a,
                    int32_t* __restrict__ d) {
+  pdl_wait();
   __shared__ TileSh<V> sh;
   __shared__ float2 sh_tab[64];
   const int64_t base = static_cast<int64_t>(blockIdx.x) * kTile;
@@ -209,6 +212,7 @@ template <typename T, typename V, typename OUT>
 __global__ void __launch_bounds__(kBlock)
 emit_W_kernel(const T* __restrict__ lw, int64_t N, const ScanGlob* g, const double2* P_rec,
               OUT* __restrict__ Wout) {
+  pdl_wait();
   __shared__ TileSh<V> sh;
   __shared__ float2 sh_tab[64];
   const int64_t base = static_cast<int64_t>(blockIdx.x) * kTile;
@@ -230,6 +234,7 @@ template <typename T, typename V>
 __global__ void __launch_bounds__(kBlock)
 emit_W_guide_kernel(const T* __restrict__ lw, int64_t N, const ScanGlob* g, const double2* s_rec,
                     const double2* P_rec, V* __restrict__ Wout, int32_t* __restrict__ G) {
+  pdl_wait();
   __shared__ TileSh<V> sh;
   __shared__ float2 sh_tab[64];
   const int64_t base = static_cast<int64_t>(blockIdx.x) * kTile;
@@ -252,6 +257,7 @@ template <typename T, typename V>
 __global__ void __launch_bounds__(kBlock)
 search_kernel(const V* __restrict__ W, const int32_t* __restrict__ G, int64_t N,
               const ScanGlob* g, Keys keys, int32_t* __restrict__ a, int32_t* __restrict__ d) {
+  pdl_wait();
   __shared__ Guide sh_gd;
   if (threadIdx.x == 0) sh_gd = make_guide(g->S_d, N);
   __syncthreads();
@@ -294,30 +300,30 @@ cudaError_t run_scan(const Scratch& s, int scheme, Acc acc, const T* lw, int64_t
     cudaError_t e = launch_fused_passes(s, scheme, acc, lw, N, keys, a_out, d, st);
     if (e != cudaSuccess || scheme != RS_MULTINOMIAL) return e;
     trace_mark(s.trace, kLblSearch[ai], st);
-    search_kernel<T, V><<<static_cast<int>((N + kBlock - 1) / kBlock), kBlock, 0, st>>>(
-        static_cast<const V*>(s.W), s.guide, N, s.glob, keys, a_out, d);
+    launch_pdl(search_kernel<T, V>, static_cast<int>((N + kBlock - 1) / kBlock), kBlock, st,
+               static_cast<const V*>(s.W), s.guide, N, s.glob, keys, a_out, d);
     return cudaGetLastError();
   }
   trace_mark(s.trace, kLblMax[ai], st);
-  max_kernel<T><<<max_grid(N, s.max_blocks), kBlock, 0, st>>>(
+  launch_pdl(max_kernel<T>, max_grid(N, s.max_blocks), kBlock, st,
       lw, N, s.glob, s.blockmax, s.err, scheme == RS_MULTINOMIAL ? d : nullptr);
   trace_mark(s.trace, kLblTile[ai], st);
-  tile_sum_kernel<T, V><<<tiles, kBlock, 0, st>>>(lw, N, s.glob, s_rec, P_rec, s.err, nullptr);
+  launch_pdl(tile_sum_kernel<T, V>, tiles, kBlock, st, lw, N, s.glob, s_rec, P_rec, s.err, nullptr);
   if (scheme == RS_SYSTEMATIC) {
     trace_mark(s.trace, kLblSys[ai], st);
-    emit_cumoff_kernel<T, V, false><<<tiles, kBlock, 0, st>>>(lw, N, s.glob, s_rec, P_rec, keys,
+    launch_pdl(emit_cumoff_kernel<T, V, false>, tiles, kBlock, st, lw, N, s.glob, s_rec, P_rec, keys,
                                                              a_out, d);
   } else if (scheme == RS_STRATIFIED) {
     trace_mark(s.trace, kLblStr[ai], st);
-    emit_cumoff_kernel<T, V, true><<<tiles, kBlock, 0, st>>>(lw, N, s.glob, s_rec, P_rec, keys,
+    launch_pdl(emit_cumoff_kernel<T, V, true>, tiles, kBlock, st, lw, N, s.glob, s_rec, P_rec, keys,
                                                             a_out, d);
   } else {
     V* W = static_cast<V*>(s.W);
     trace_mark(s.trace, kLblW[ai], st);
-    emit_W_guide_kernel<T, V><<<tiles, kBlock, 0, st>>>(lw, N, s.glob, s_rec, P_rec, W, s.guide);
+    launch_pdl(emit_W_guide_kernel<T, V>, tiles, kBlock, st, lw, N, s.glob, s_rec, P_rec, W, s.guide);
     const int grid = static_cast<int>((N + kBlock - 1) / kBlock);
     trace_mark(s.trace, kLblSearch[ai], st);
-    search_kernel<T, V><<<grid, kBlock, 0, st>>>(W, s.guide, N, s.glob, keys, a_out, d);
+    launch_pdl(search_kernel<T, V>, grid, kBlock, st, W, s.guide, N, s.glob, keys, a_out, d);
   }
   return cudaGetLastError();
 }
@@ -330,13 +336,13 @@ cudaError_t run_cumw(const Scratch& s, const T* lw, int64_t N, OUT* W_out, doubl
   double2* P_rec = s.rec + (s.max_tiles + 2);
   constexpr int ai = Path<T, V>::id;
   trace_mark(s.trace, kLblMax[ai], st);
-  max_kernel<T><<<max_grid(N, s.max_blocks), kBlock, 0, st>>>(lw, N, s.glob, s.blockmax, s.err,
+  launch_pdl(max_kernel<T>, max_grid(N, s.max_blocks), kBlock, st, lw, N, s.glob, s.blockmax, s.err,
                                                               nullptr);
   trace_mark(s.trace, kLblTile[ai], st);
-  tile_sum_kernel<T, V><<<tiles, kBlock, 0, st>>>(lw, N, s.glob, s_rec, P_rec, s.err,
+  launch_pdl(tile_sum_kernel<T, V>, tiles, kBlock, st, lw, N, s.glob, s_rec, P_rec, s.err,
                                                   log_total);
   trace_mark(s.trace, kLblW[ai], st);
-  emit_W_kernel<T, V, OUT><<<tiles, kBlock, 0, st>>>(lw, N, s.glob, P_rec, W_out);
+  launch_pdl(emit_W_kernel<T, V, OUT>, tiles, kBlock, st, lw, N, s.glob, P_rec, W_out);
   return cudaGetLastError();
 }
 
