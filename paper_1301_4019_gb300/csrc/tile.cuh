@@ -707,9 +707,18 @@ __device__ __forceinline__ int32_t search_one_guided(const V* __restrict__ W,
     lo = ld_val<kCoherent>(G + b);
     hi = static_cast<int64_t>(ld_val<kCoherent>(G + b + 1)) + 1;
   }
-  while (lo < hi) {
-    const int64_t mid = lo + ((hi - lo) >> 1);
-    if (vle(ld_val<kCoherent>(W + mid), u)) lo = mid + 1; else hi = mid;
+  if (hi - lo <= 8) {  // the usual case: count W_j <= u over the range, loads in parallel
+    const int64_t len = hi - lo;
+    int cnt = 0;
+#pragma unroll
+    for (int q = 0; q < 8; ++q)
+      if (q < len && vle(ld_val<kCoherent>(W + lo + q), u)) ++cnt;
+    lo += cnt;
+  } else {
+    while (lo < hi) {
+      const int64_t mid = lo + ((hi - lo) >> 1);
+      if (vle(ld_val<kCoherent>(W + mid), u)) lo = mid + 1; else hi = mid;
+    }
   }
   return static_cast<int32_t>(lo < n ? lo : n - 1);
 }
