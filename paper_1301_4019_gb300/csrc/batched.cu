@@ -253,7 +253,6 @@ batch_emit_kernel(const T* __restrict__ lw, Batch b, Keys base_keys,
   const WeightCtx wc = make_ctx<T, V>(M, sh_tab);
   const bool vec = (reinterpret_cast<uintptr_t>(lw) & 15u) == 0;
   const double2* P = b.P_rec + __ldg(b.tile_start + L.f) + L.f;
-  const double2* s = b.s_rec + __ldg(b.tile_start + L.f);
   const V Pt = load_v_cg<V>(P + L.t), Pn = load_v_cg<V>(P + L.t + 1);
   if constexpr (SCHEME == RS_MULTINOMIAL) {
     if (d)  // claims of the search kernel start from the sentinel n
@@ -264,10 +263,9 @@ batch_emit_kernel(const T* __restrict__ lw, Batch b, Keys base_keys,
     const Keys keys = with_tag(base_keys, static_cast<uint32_t>(L.f), SCHEME);
     const typename Path<T, V>::U u_sys =
         SCHEME == RS_STRATIFIED ? typename Path<T, V>::U() : cta_uniform0<T, V>(keys);
-    const V Pm = L.t > 0 ? load_v_cg<V>(P + L.t - 1) : vzero(V());
     emit_tile_cumoff<T, V, SCHEME == RS_STRATIFIED>(
-        lw, L.lo, L.hi, L.base, wc, vec, Pt, Pn, L.t > 0 ? s + L.t - 1 : nullptr, Pm,
-        load_v_cg<V>(b.fS + L.f), load_v_cg<V>(b.fscale + L.f), u_sys, keys, a, d, sh);
+        lw, L.lo, L.hi, L.base, wc, vec, Pt, Pn, L.t > 0, load_v_cg<V>(b.fS + L.f),
+        load_v_cg<V>(b.fscale + L.f), u_sys, keys, a, d, sh);
   }
 }
 

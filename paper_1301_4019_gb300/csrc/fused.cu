@@ -237,9 +237,7 @@ __device__ __forceinline__ void fused_body(const T* __restrict__ lw, const Fused
         store_v<V>(A.P_rec + T_tiles, fixed_to(CP + ld_u128_cg(A.agg + c), V(), kFixFrac));
       __syncthreads();
       if (threadIdx.x == 0) {
-        const V Pm = load_v_cg<V>(A.P_rec + (T_tiles - 1));
-        const V Pn = load_v_cg<V>(A.P_rec + T_tiles);
-        const V S = vclamp(vadd(Pm, load_v_cg<V>(A.s_rec + (T_tiles - 1))), Pm, Pn);
+        const V S = load_v_cg<V>(A.P_rec + T_tiles);  // as in tile_prefix_compute
         const double Sd = vto_double(S);
         store_v<V>(&A.g->S_raw, S);
         store_v<V>(&A.g->scale_raw, vfrom_double(__ddiv_rn(static_cast<double>(N), Sd), V()));
@@ -275,14 +273,12 @@ __device__ __forceinline__ void fused_body(const T* __restrict__ lw, const Fused
   for (int t = t0; t < t1; ++t) {
     const int64_t base = static_cast<int64_t>(t) * kTile;
     const V Pt = load_v_cg<V>(A.P_rec + t), Pn = load_v_cg<V>(A.P_rec + t + 1);
-    const V Pm = t > 0 ? load_v_cg<V>(A.P_rec + t - 1) : vzero(V());
-    const double2* prev = t > 0 ? A.s_rec + t - 1 : nullptr;
     if constexpr (SCHEME == RS_MULTINOMIAL) {
-      emit_tile_W_guide<T, V>(lw, 0, N, base, wc, vec, Pt, Pn, prev, Pm, sh_gd,
+      emit_tile_W_guide<T, V>(lw, 0, N, base, wc, vec, Pt, Pn, t > 0, sh_gd,
                               static_cast<V*>(A.W), A.guide, sh);
     } else {
-      emit_tile_cumoff<T, V, SCHEME == RS_STRATIFIED>(lw, 0, N, base, wc, vec, Pt, Pn, prev, Pm,
-                                                       S, scale, u_sys, A.keys, A.a, A.d, sh);
+      emit_tile_cumoff<T, V, SCHEME == RS_STRATIFIED>(lw, 0, N, base, wc, vec, Pt, Pn, t > 0, S,
+                                                       scale, u_sys, A.keys, A.a, A.d, sh);
     }
   }
 }

@@ -198,10 +198,8 @@ emit_cumoff_kernel(const T* __restrict__ lw, int64_t N, const ScanGlob* g, const
   const bool vec = (reinterpret_cast<uintptr_t>(lw) & 15u) == 0;
   const int t = blockIdx.x;
   const V Pt = load_v<V>(P_rec + t), Pn = load_v<V>(P_rec + t + 1);
-  const V Pm = t > 0 ? load_v<V>(P_rec + t - 1) : vzero(V());
-  emit_tile_cumoff<T, V, STRAT>(lw, 0, N, base, wc, vec, Pt, Pn, t > 0 ? s_rec + t - 1 : nullptr,
-                                Pm, load_v<V>(&g->S_raw), load_v<V>(&g->scale_raw), u_sys, keys,
-                                a, d, sh);
+  emit_tile_cumoff<T, V, STRAT>(lw, 0, N, base, wc, vec, Pt, Pn, t > 0, load_v<V>(&g->S_raw),
+                                load_v<V>(&g->scale_raw), u_sys, keys, a, d, sh);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -243,10 +241,8 @@ emit_W_guide_kernel(const T* __restrict__ lw, int64_t N, const ScanGlob* g, cons
   const WeightCtx wc = make_ctx<T, V>(Md, sh_tab);
   const bool vec = (reinterpret_cast<uintptr_t>(lw) & 15u) == 0;
   const int t = blockIdx.x;
-  const V Pm = t > 0 ? load_v<V>(P_rec + t - 1) : vzero(V());
   emit_tile_W_guide<T, V>(lw, 0, N, base, wc, vec, load_v<V>(P_rec + t), load_v<V>(P_rec + t + 1),
-                          t > 0 ? s_rec + t - 1 : nullptr, Pm, make_guide(g->S_d, N), Wout, G,
-                          sh);
+                          t > 0, make_guide(g->S_d, N), Wout, G, sh);
 }
 
 // ---------------------------------------------------------------------------------------

@@ -341,9 +341,8 @@ template <typename V> __device__ __forceinline__ u128 rec_fixed(const double2* p
 // it): P_t = RN(s_0 + ... + s_{t-1}) for t = 0..nt, the exact sums taken in fixed point (each
 // thread a contiguous chunk of tiles, then a warp scan and a scan over the warps: integer
 // adds, so the order does not matter). P is non-decreasing because the exact prefixes are and
-// rounding is monotone. The total S is the cumulative weight of the last particle exactly as
-// the emit pass computes it, clamp(P_{nt-1} + s_{nt-1}, P_{nt-1}, P_nt), so that particle
-// receives O = N.
+// rounding is monotone. The total S is P_nt, the cumulative weight the emission gives the
+// last particle (tile_cum_weights), so that particle receives O = N.
 // Thread 0 writes S, N / S and S (binary64) to the given pointers, then the CTA synchronises.
 template <typename V>
 __device__ void tile_prefix_compute(const double2* s_rec, double2* P_rec, int nt, int64_t N,
@@ -391,39 +390,13 @@ __device__ void tile_prefix_compute(const double2* s_rec, double2* P_rec, int nt
   if (t1 == nt && t0 < nt) store_v<V>(P_rec + nt, fixed_to(p, V(), kFixFrac));
   __syncthreads();
   if (tid == 0) {
-    const V Pm = load_v_cg<V>(P_rec + (nt - 1));
-    const V Pn = load_v_cg<V>(P_rec + nt);
-    const V S = vclamp(vadd(Pm, load_v_cg<V>(s_rec + (nt - 1))), Pm, Pn);
+    const V S = load_v_cg<V>(P_rec + nt);
     const double Sd = vto_double(S);
     *S_out = S;
     *scale_out = vfrom_double(__ddiv_rn(static_cast<double>(N), Sd), V());
     *Sd_out = Sd;
   }
   __syncthreads();
-}
-
-// The tile total (block-level): maximum of the tile values over valid positions, which is
-// also the value of the tile's last valid particle after the running maximum.
-template <typename V>
-__device__ __forceinline__ V tile_total(const V (&val)[kRows][4], int64_t base, int64_t lo,
-                                        int64_t N, V* sh_max) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int cnt = tile_count(base, N);
-  V m = vzero(V());
-#pragma unroll
-  for (int r = 0; r < kRows; ++r)
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      if (tile_offset(warp, r, lane, q) < cnt) m = vmax(m, val[r][q]);
-    }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) m = vmax(m, vshfl_xor(m, o));
-  __syncthreads();
-  if (lane == 0) sh_max[warp] = m;
-  __syncthreads();
-  V tm = vzero(V());
-  for (int k = 0; k < kWarps; ++k) tm = vmax(tm, sh_max[k]);
-  return tm;
 }
 
 // Shared scratch of the block-level tile functions.
@@ -433,25 +406,46 @@ template <typename V> struct TileSh {
 };
 
 // The tile's total (its record), stored by thread 0 at rec; returned as fixed point in every
-// thread.
+// thread. A plain block reduction (sequential over a thread's elements, butterfly over the
+// warp, sequential over the warps): the tile prefixes only need an accurate total, because
+// the emission pins every tile's last particle to the next prefix (tile_cum_weights).
 template <typename T, typename V>
 __device__ __forceinline__ u128 tile_record(const T* __restrict__ lw, int64_t lo, int64_t N,
                                             int64_t base, const WeightCtx& wc, bool vec,
                                             double2* rec, TileSh<V>& sh) {
-  V val[kRows][4];
-  tile_raw_values<T, V>(lw, lo, N, base, wc, vec, val, sh.tot);
-  const V tm = tile_total<V>(val, base, lo, N, sh.max);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  T x[kRows][4];
+#pragma unroll
+  for (int r = 0; r < kRows; ++r)
+    load4(lw, base + tile_offset(warp, r, lane, 0), lo, N, vec, x[r]);
+  V t = vzero(V());
+#pragma unroll
+  for (int r = 0; r < kRows; ++r)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) t = vadd(t, vfrom_w(Path<T, V>::weight(x[r][q], wc), V()));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) t = vadd(t, vshfl_xor(t, o));  // same value in every lane
+  __syncthreads();  // sh.tot may still be read from the previous tile
+  if (lane == 0) sh.tot[warp] = t;
+  __syncthreads();
+  V tm = sh.tot[0];
+  for (int k = 1; k < kWarps; ++k) tm = vadd(tm, sh.tot[k]);
   if (threadIdx.x == 0) store_v<V>(rec, tm);
   return to_fixed(tm);
 }
 
 // Cumulative weights W[r][q] of this thread's elements of the tile (clamped into [Pt, Pn])
 // and Wwarp, the cumulative weight just before this warp's first element.
+// The tile's last valid particle gets exactly Pn, the next tile's prefix, so the cumulative
+// weight just before any tile is its own prefix Pt and tiles need nothing from each other's
+// scans (the total W^N is then the last prefix).
 template <typename T, typename V>
 __device__ __forceinline__ void tile_cum_weights(const T* __restrict__ lw, int64_t lo, int64_t N,
                                                  int64_t base, const WeightCtx& wc, bool vec,
                                                  V Pt, V Pn, V (&W)[kRows][4], V& Wwarp,
                                                  TileSh<V>& sh) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int last = tile_count(base, N) - 1;
   V val[kRows][4];
   tile_raw_values<T, V>(lw, lo, N, base, wc, vec, val, sh.tot);
   V prevmax;
@@ -459,15 +453,9 @@ __device__ __forceinline__ void tile_cum_weights(const T* __restrict__ lw, int64
 #pragma unroll
   for (int r = 0; r < kRows; ++r)
 #pragma unroll
-    for (int q = 0; q < 4; ++q) W[r][q] = vclamp(vadd(Pt, val[r][q]), Pt, Pn);
+    for (int q = 0; q < 4; ++q)
+      W[r][q] = tile_offset(warp, r, lane, q) == last ? Pn : vclamp(vadd(Pt, val[r][q]), Pt, Pn);
   Wwarp = vclamp(vadd(Pt, prevmax), Pt, Pn);
-}
-
-// The cumulative weight of the previous tile's last particle (prefix Pm, record prev_rec),
-// as its own emission computes it.
-template <typename V>
-__device__ __forceinline__ V tile_W_last(const double2* prev_rec, V Pm, V Pt) {
-  return vclamp(vadd(Pm, load_v_cg<V>(prev_rec)), Pm, Pt);
 }
 
 // The systematic uniform u (counter (0, 0)), drawn once per CTA.
@@ -485,12 +473,12 @@ __device__ __forceinline__ typename Path<T, V>::U cta_uniform0(const Keys& keys)
 // ancestor indices into a[lo + j] and, when d is given, the Prepermute claims
 // d[lo + i] = O_{i-1} if particle i has offspring, else n (for a non-decreasing ancestry
 // the lowest claimant of slot i is the first position of its run). Pt, Pn: prefixes of this
-// tile; prev_rec, Pm: record and prefix of the previous tile (prev_rec null for the first).
-// u_sys: the systematic uniform (cta_uniform0; unused when STRAT).
+// tile; has_prev: a tile precedes this one in the sequence (its last particle's cumulative
+// weight is Pt). u_sys: the systematic uniform (cta_uniform0; unused when STRAT).
 template <typename T, typename V, bool STRAT>
 __device__ __forceinline__ void emit_tile_cumoff(const T* __restrict__ lw, int64_t lo, int64_t N,
                                                  int64_t base, const WeightCtx& wc, bool vec,
-                                                 V Pt, V Pn, const double2* prev_rec, V Pm, V S,
+                                                 V Pt, V Pn, bool has_prev, V S,
                                                  V scale, typename Path<T, V>::U u_sys,
                                                  const Keys& keys, int32_t* __restrict__ a,
                                                  int32_t* __restrict__ d, TileSh<V>& sh) {
@@ -510,9 +498,8 @@ __device__ __forceinline__ void emit_tile_cumoff(const T* __restrict__ lw, int64
   if (lane == 0) {
     if (warp > 0)
       Obefore = cum_offspring<T, V, STRAT>(Wwarp, S, scale, u_sys, keys, n);
-    else if (prev_rec)
-      Obefore = cum_offspring<T, V, STRAT>(tile_W_last<V>(prev_rec, Pm, Pt), S, scale, u_sys,
-                                           keys, n);
+    else if (has_prev)
+      Obefore = cum_offspring<T, V, STRAT>(Pt, S, scale, u_sys, keys, n);
   }
 #pragma unroll
   for (int r = 0; r < kRows; ++r) {
@@ -634,7 +621,7 @@ __device__ __forceinline__ int64_t guide_count(V W, const Guide& g, int64_t n) {
 template <typename T, typename V>
 __device__ __forceinline__ void emit_tile_W_guide(const T* __restrict__ lw, int64_t lo, int64_t N,
                                                   int64_t base, const WeightCtx& wc, bool vec,
-                                                  V Pt, V Pn, const double2* prev_rec, V Pm,
+                                                  V Pt, V Pn, bool has_prev,
                                                   const Guide& gd, V* __restrict__ Wout,
                                                   int32_t* __restrict__ G, TileSh<V>& sh) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -655,8 +642,8 @@ __device__ __forceinline__ void emit_tile_W_guide(const T* __restrict__ lw, int6
   if (lane == 0) {
     if (warp > 0)
       Cbefore = guide_count<V>(Wwarp, gd, n);
-    else if (prev_rec)
-      Cbefore = guide_count<V>(tile_W_last<V>(prev_rec, Pm, Pt), gd, n);
+    else if (has_prev)
+      Cbefore = guide_count<V>(Pt, gd, n);
   }
 #pragma unroll
   for (int r = 0; r < kRows; ++r) {
