@@ -222,6 +222,7 @@ __device__ __forceinline__ void fused_body(const T* __restrict__ lw, const Fused
     if (c == 0 && threadIdx.x == 0) {
       A.g->S_d = 0.0;
       A.g->M = M;
+      A.g->all_zero = 1;
       flag_error(A.err, RS_ERR_ZERO_WEIGHT);
     }
   } else {
@@ -243,17 +244,21 @@ __device__ __forceinline__ void fused_body(const T* __restrict__ lw, const Fused
         store_v<V>(&A.g->scale_raw, vfrom_double(__ddiv_rn(static_cast<double>(N), Sd), V()));
         A.g->S_d = Sd;
         A.g->M = M;  // read by the search kernel
+        A.g->all_zero = !(Sd > 0.0);
+        const Guide gd = make_guide(Sd, N);
+        A.g->guide_step = gd.step;
+        A.g->guide_inv_step = gd.inv_step;
         if (!(Sd > 0.0)) flag_error(A.err, RS_ERR_ZERO_WEIGHT);
       }
     }
   }
   grid_barrier(&A.g->bar_count, target, A.err);
-  const double Sd = __ldcg(&A.g->S_d);
+  const bool all_zero = __ldcg(&A.g->all_zero) != 0;
   // the kernels that follow (search, Permute) may launch now; they wait for this grid's end
   asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 
   // ---- phase 4: emission of this CTA's tiles -----------------------------------------------
-  if (zero || !(Sd > 0.0)) {  // all weights zero (flagged): every particle keeps itself
+  if (all_zero) {  // all weights zero (flagged): every particle keeps itself
     if constexpr (SCHEME != RS_MULTINOMIAL) {  // (the search kernel writes the identity)
       for (int64_t i = e0 + threadIdx.x; i < e1; i += kBlock) {
         A.a[i] = static_cast<int32_t>(i);
@@ -265,7 +270,7 @@ __device__ __forceinline__ void fused_body(const T* __restrict__ lw, const Fused
   const V S = load_v_cg<V>(&A.g->S_raw), scale = load_v_cg<V>(&A.g->scale_raw);
   typename Path<T, V>::U u_sys = typename Path<T, V>::U();
   if constexpr (SCHEME == RS_MULTINOMIAL) {
-    if (threadIdx.x == 0) sh_gd = make_guide(Sd, N);
+    if (threadIdx.x == 0) sh_gd = Guide{__ldcg(&A.g->guide_step), __ldcg(&A.g->guide_inv_step)};
     __syncthreads();
   } else if constexpr (SCHEME == RS_SYSTEMATIC) {
     u_sys = cta_uniform0<T, V>(A.keys);

@@ -16,7 +16,10 @@ struct ScanGlob {
   unsigned int batch_next;   // work counter of the batched kernel (self-resetting)
   unsigned int batch_ticket;
   unsigned int bar_count;    // grid-barrier arrivals of the fused kernel (0 between launches)
-  unsigned int pad[2];
+  int all_zero;              // every weight of the call is zero (set with the total)
+  float guide_step;          // W^N / N and N / W^N in binary32 (multinomial guide table),
+  float guide_inv_step;      //   set with the total so that no later kernel divides
+  unsigned int pad[3];
   double2 S_raw;             // total, in the accumulator type of the call
   double2 scale_raw;         // N / total, in the accumulator type of the call
 };

@@ -140,6 +140,10 @@ __device__ __noinline__ void tile_prefix_last_cta(const double2* s_rec, double2*
     const double Sd = g->S_d;
     if (!(Sd > 0.0)) flag_error(err, RS_ERR_ZERO_WEIGHT);
     if (log_total_out) *log_total_out = __dadd_rn(g->M, log(Sd));
+    g->all_zero = !(g->M > -DBL_MAX) || !(Sd > 0.0);
+    const Guide gd = make_guide(Sd, N);
+    g->guide_step = gd.step;
+    g->guide_inv_step = gd.inv_step;
     g->ticket_tile = 0u;
   }
 }
@@ -185,15 +189,14 @@ emit_cumoff_kernel(const T* __restrict__ lw, int64_t N, const ScanGlob* g, const
   __shared__ TileSh<V> sh;
   __shared__ float2 sh_tab[64];
   const int64_t base = static_cast<int64_t>(blockIdx.x) * kTile;
-  const double Md = g->M;
-  if (!(Md > -DBL_MAX) || !(g->S_d > 0.0)) {  // all weights zero: flagged; emit identity
+  if (g->all_zero) {  // all weights zero: flagged; emit identity
     for (int64_t i = base + threadIdx.x; i < N && i < base + kTile; i += kBlock) {
       a[i] = static_cast<int32_t>(i);
       if (d) d[i] = static_cast<int32_t>(i);
     }
     return;
   }
-  const WeightCtx wc = make_ctx<T, V>(Md, sh_tab);
+  const WeightCtx wc = make_ctx<T, V>(g->M, sh_tab);
   const typename Path<T, V>::U u_sys = STRAT ? typename Path<T, V>::U() : cta_uniform0<T, V>(keys);
   const bool vec = (reinterpret_cast<uintptr_t>(lw) & 15u) == 0;
   const int t = blockIdx.x;
@@ -214,13 +217,12 @@ emit_W_kernel(const T* __restrict__ lw, int64_t N, const ScanGlob* g, const doub
   __shared__ TileSh<V> sh;
   __shared__ float2 sh_tab[64];
   const int64_t base = static_cast<int64_t>(blockIdx.x) * kTile;
-  const double Md = g->M;
-  if (!(Md > -DBL_MAX) || !(g->S_d > 0.0)) {
+  if (g->all_zero) {
     for (int64_t i = base + threadIdx.x; i < N && i < base + kTile; i += kBlock)
       Wout[i] = convert_out<V, OUT>(vzero(V()));
     return;
   }
-  const WeightCtx wc = make_ctx<T, V>(Md, sh_tab);
+  const WeightCtx wc = make_ctx<T, V>(g->M, sh_tab);
   const bool vec = (reinterpret_cast<uintptr_t>(lw) & 15u) == 0;
   const int t = blockIdx.x;
   emit_tile_W<T, V, OUT>(lw, 0, N, base, wc, vec, load_v<V>(P_rec + t), load_v<V>(P_rec + t + 1),
@@ -236,13 +238,12 @@ emit_W_guide_kernel(const T* __restrict__ lw, int64_t N, const ScanGlob* g, cons
   __shared__ TileSh<V> sh;
   __shared__ float2 sh_tab[64];
   const int64_t base = static_cast<int64_t>(blockIdx.x) * kTile;
-  const double Md = g->M;
-  if (!(Md > -DBL_MAX) || !(g->S_d > 0.0)) return;  // the search writes the identity
-  const WeightCtx wc = make_ctx<T, V>(Md, sh_tab);
+  if (g->all_zero) return;  // the search writes the identity
+  const WeightCtx wc = make_ctx<T, V>(g->M, sh_tab);
   const bool vec = (reinterpret_cast<uintptr_t>(lw) & 15u) == 0;
   const int t = blockIdx.x;
   emit_tile_W_guide<T, V>(lw, 0, N, base, wc, vec, load_v<V>(P_rec + t), load_v<V>(P_rec + t + 1),
-                          t > 0, make_guide(g->S_d, N), Wout, G, sh);
+                          t > 0, Guide{g->guide_step, g->guide_inv_step}, Wout, G, sh);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -254,17 +255,15 @@ __global__ void __launch_bounds__(kBlock)
 search_kernel(const V* __restrict__ W, const int32_t* __restrict__ G, int64_t N,
               const ScanGlob* g, Keys keys, int32_t* __restrict__ a, int32_t* __restrict__ d) {
   pdl_wait();
-  __shared__ Guide sh_gd;
-  if (threadIdx.x == 0) sh_gd = make_guide(g->S_d, N);
-  __syncthreads();
   const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
   if (i >= N) return;
-  if (!(g->M > -DBL_MAX) || !(g->S_d > 0.0)) {
+  if (g->all_zero) {
     a[i] = static_cast<int32_t>(i);
     if (d) atomicMin(d + i, static_cast<int32_t>(i));
     return;
   }
-  const int32_t k = search_one_guided<T, V>(W, G, N, sh_gd, keys, i);
+  const Guide gd{g->guide_step, g->guide_inv_step};
+  const int32_t k = search_one_guided<T, V>(W, G, N, gd, keys, i);
   a[i] = k;
   if (d) atomicMin(d + k, static_cast<int32_t>(i));
 }
