@@ -167,8 +167,8 @@ __global__ void __launch_bounds__(kBlock) batch_max_kernel(const T* __restrict__
     load4(lw, i0, L.lo, end, vec, x);
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-      const bool nan = x[q] != x[q];
-      bad |= nan || x[q] == static_cast<T>(INFINITY);
+      const bool nan = is_nan(x[q]);
+      bad |= nan || is_pos_inf(x[q]);
       const long long k = key_of(x[q]);
       if (!nan && k > m) m = k;
     }

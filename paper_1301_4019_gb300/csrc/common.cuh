@@ -170,8 +170,22 @@ inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, c
 // ---------------------------------------------------------------------------------------
 // Log-weight classification.
 // ---------------------------------------------------------------------------------------
+// Binary64 classification by the bit pattern (integer pipe; GB300 runs binary64 compares at
+// the 1/57 binary64 rate). Binary32 tests compare directly.
+__device__ __forceinline__ bool is_nan(float v) { return v != v; }
+__device__ __forceinline__ bool is_nan(double v) {
+  return (static_cast<unsigned long long>(__double_as_longlong(v)) << 1) > 0xffe0000000000000ull;
+}
+__device__ __forceinline__ bool is_pos_inf(float v) { return v == INFINITY; }
+__device__ __forceinline__ bool is_pos_inf(double v) {
+  return __double_as_longlong(v) == 0x7ff0000000000000LL;
+}
+__device__ __forceinline__ bool is_neg_inf(float v) { return v == -INFINITY; }
+__device__ __forceinline__ bool is_neg_inf(double v) {
+  return static_cast<unsigned long long>(__double_as_longlong(v)) == 0xfff0000000000000ull;
+}
 template <typename T> __device__ __forceinline__ bool nonfinite_logw(T v) {
-  return v != v || v == static_cast<T>(INFINITY);
+  return is_nan(v) || is_pos_inf(v);
 }
 template <typename T> __device__ __forceinline__ T neg_inf() { return -static_cast<T>(INFINITY); }
 

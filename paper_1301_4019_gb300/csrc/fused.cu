@@ -175,8 +175,8 @@ __device__ __forceinline__ void fused_body(const T* __restrict__ lw, const Fused
       load4(lw, i0, 0, e1, vec, x);
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
-        const bool nan = x[q] != x[q];
-        bad |= nan || x[q] == static_cast<T>(INFINITY);
+        const bool nan = is_nan(x[q]);
+        bad |= nan || is_pos_inf(x[q]);
         const long long k = fkey(x[q]);
         if (!nan && k > m) m = k;
         if constexpr (SCHEME == RS_MULTINOMIAL) {

@@ -232,12 +232,12 @@ __device__ __forceinline__ int32_t rejection_one(const double* __restrict__ lw, 
     if (s > 0) j = uniform_index(x, n);
     const double lwj = (s == 0) ? lwi : __ldg(lw + j);
     const long long kj = f64_key(lwj);
-    if (kj > km && lwj == lwj) {  // above the bound (NaN never compares)
+    if (kj > km && !is_nan(lwj)) {  // above the bound (NaN never compares)
       flag_error(err, RS_ERR_BOUND_VIOLATED);
       return static_cast<int32_t>(j);
     }
     if (kj == km) return static_cast<int32_t>(j);  // ratio exactly 1
-    if (kj == kNegInf || lwj != lwj) continue;
+    if (kj == kNegInf || is_nan(lwj)) continue;
     float lwj_f;
     const bool okj = f64_to_f32_trunc(lwj, lwj_f);
     if (f64_accept_lt(lwj, lwj_f, okj, lwmax, lwmax_f, okm, x)) return static_cast<int32_t>(j);
@@ -257,13 +257,15 @@ constexpr int kRejRun = 32 * 8;  // particles per warp run
 
 struct RejBound {  // the bound log w_max in the forms the attempts compare against
   double lwmax;
-  float lwmax_f;
+  float lwmax_rn;  // RN(log w_max) in binary32 (the binary32 scheme's bound)
+  float lwmax_f;   // truncation (the binary64 scheme's filter)
   bool okm;
   long long km;
 };
 __device__ __forceinline__ RejBound make_bound(double log_wmax) {
   RejBound r;
   r.lwmax = log_wmax;
+  r.lwmax_rn = static_cast<float>(log_wmax);
   r.okm = f64_to_f32_trunc(log_wmax, r.lwmax_f);
   r.km = f64_key(log_wmax);
   return r;
@@ -279,7 +281,7 @@ __device__ __forceinline__ bool rejection_attempt(const float* __restrict__ lw, 
   j = (s > 0) ? uniform_index(x, n) : i;
   const float u = u01_f32(x);
   const float lwj = (s == 0) ? lwi : __ldg(lw + j);
-  const float delta = lwj - static_cast<float>(rb.lwmax);
+  const float delta = lwj - rb.lwmax_rn;
   if (delta > 0.0f) {
     flag_error(err, RS_ERR_BOUND_VIOLATED);
     return true;
@@ -295,12 +297,12 @@ __device__ __forceinline__ bool rejection_attempt(const double* __restrict__ lw,
   j = (s > 0) ? uniform_index(x, n) : i;
   const double lwj = (s == 0) ? lwi : __ldg(lw + j);
   const long long kj = f64_key(lwj);
-  if (kj > rb.km && lwj == lwj) {  // above the bound (NaN never compares)
+  if (kj > rb.km && !is_nan(lwj)) {  // above the bound (NaN never compares)
     flag_error(err, RS_ERR_BOUND_VIOLATED);
     return true;
   }
   if (kj == rb.km) return true;  // ratio exactly 1
-  if (kj == f64_key(-INFINITY) || lwj != lwj) return false;
+  if (kj == f64_key(-INFINITY) || is_nan(lwj)) return false;
   float lwj_f;
   const bool okj = f64_to_f32_trunc(lwj, lwj_f);
   return f64_accept_lt(lwj, lwj_f, okj, rb.lwmax, rb.lwmax_f, rb.okm, x);

@@ -75,8 +75,8 @@ max_kernel(const T* __restrict__ lw, int64_t N, ScanGlob* g, double* blockmax, i
     load4(lw, i0, 0, N, vec && i0 + 4 <= N, x);
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-      const bool nan = x[q] != x[q];
-      bad |= nan || x[q] == static_cast<T>(INFINITY);
+      const bool nan = is_nan(x[q]);
+      bad |= nan || is_pos_inf(x[q]);
       const long long k = max_key(x[q]);
       if (!nan && k > m) m = k;
       if (d_init && i0 + q < N) d_init[i0 + q] = static_cast<int32_t>(N);

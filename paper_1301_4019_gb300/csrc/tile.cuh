@@ -47,7 +47,7 @@ template <> struct Path<double, float2> {
   static constexpr int id = 2;
   static constexpr bool kTable = true;
   __device__ static float2 weight(double x, const WeightCtx& c) {
-    if (x == neg_inf<double>()) return make_float2(0.0f, 0.0f);
+    if (is_neg_inf(x)) return make_float2(0.0f, 0.0f);
     return exp_df(add22_accurate(split_f64(x), neg2(c.M2)), c.tab);
   }
   __device__ static U draw_u(uint4 x) { return u01_f2(x); }
