@@ -203,22 +203,12 @@ int rs_resample(rs_handle* h, int scheme, int dtype, const void* logw_dev, int64
                                     d, fused, s);
       break;
     }
-    case RS_METROPOLIS:
-      if (d) {
-        rsk::trace_mark(h->s.trace, "fill", s);
-        e = rsk::launch_fill(d, N, static_cast<int32_t>(N), s);
-      }
-      if (e == cudaSuccess)
-        e = rsk::launch_metropolis(h->s, f64, logw_dev, N, B, seed, step, o.filter, a_out, d, s);
+    case RS_METROPOLIS:  // (the launch also sets the claims d to the sentinel N)
+      e = rsk::launch_metropolis(h->s, f64, logw_dev, N, B, seed, step, o.filter, a_out, d, s);
       break;
     case RS_REJECTION:
-      if (d) {
-        rsk::trace_mark(h->s.trace, "fill", s);
-        e = rsk::launch_fill(d, N, static_cast<int32_t>(N), s);
-      }
-      if (e == cudaSuccess)
-        e = rsk::launch_rejection(h->s, f64, logw_dev, N, o.log_wmax, o.max_trials, seed, step,
-                                  o.filter, a_out, d, s);
+      e = rsk::launch_rejection(h->s, f64, logw_dev, N, o.log_wmax, o.max_trials, seed, step,
+                                o.filter, a_out, d, s);
       break;
   }
   if (e == cudaSuccess && permute) {

@@ -2,6 +2,7 @@
 // Appendix D (Codes 11 and 12, Inclusive-Prefix-Sum and Adjacent-Difference of Code 4) on
 // sm_103a. Integer work only: every result is exact.
 #include "common.cuh"
+#include "grid.cuh"
 #include "internal.h"
 #include "permute.cuh"
 
@@ -189,6 +190,56 @@ iscan_emit_kernel(const int32_t* __restrict__ in, int64_t N, const long long* pr
     if (idx + q < N) out[idx + q] = static_cast<int32_t>(v[q] + p);
 }
 
+// The same scan as one cooperative launch: CTA c owns the contiguous tiles
+// [c T / G, (c+1) T / G); it scans them in order (keeping each tile's exclusive in-range
+// prefix and its range total), meets the others at a grid barrier, adds the totals of the
+// ranges before its own (exact integers: any order gives the same sums) and writes its tiles.
+__device__ __forceinline__ long long block_sum_ll(long long v, long long* sh) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  __syncthreads();
+  if (lane == 0) sh[warp] = v;
+  __syncthreads();
+  long long t = 0;
+  for (int k = 0; k < kWarps; ++k) t += sh[k];
+  return t;
+}
+
+__global__ void __launch_bounds__(kBlock)
+iscan_coop_kernel(const int32_t* __restrict__ in, int64_t N, int T, long long* tot,
+                  long long* pre, int32_t* __restrict__ out, unsigned int* bar, int* err) {
+  __shared__ long long sh[kWarps];
+  unsigned int target = 0;
+  const int G = static_cast<int>(gridDim.x), c = static_cast<int>(blockIdx.x);
+  const int t0 = static_cast<int>(static_cast<int64_t>(c) * T / G);
+  const int t1 = static_cast<int>(static_cast<int64_t>(c + 1) * T / G);
+  long long v[16];
+  long long run = 0;
+  for (int t = t0; t < t1; ++t) {
+    const long long total = block_tile_scan(in, N, static_cast<int64_t>(t) * kIscanTile, v, sh);
+    if (threadIdx.x == 0) pre[t] = run;
+    run += total;
+    __syncthreads();  // sh is rewritten by the next tile
+  }
+  if (threadIdx.x == 0) tot[c] = run;
+  grid_barrier(bar, target, err);
+  long long part = 0;
+  for (int k = threadIdx.x; k < c; k += kBlock) part += __ldcg(tot + k);
+  const long long CP = block_sum_ll(part, sh);
+  for (int t = t0; t < t1; ++t) {
+    __syncthreads();
+    const int64_t base = static_cast<int64_t>(t) * kIscanTile;
+    block_tile_scan(in, N, base, v, sh);
+    const long long p = CP + __ldcg(pre + t);
+    const int64_t idx = base + 16 * threadIdx.x;
+#pragma unroll
+    for (int q = 0; q < 16; ++q)
+      if (idx + q < N) out[idx + q] = static_cast<int32_t>(v[q] + p);
+  }
+  grid_exit(bar, target);
+}
+
 inline int grid_for(int64_t N) { return static_cast<int>((N + kBlock - 1) / kBlock); }
 
 }  // namespace
@@ -242,6 +293,15 @@ cudaError_t launch_inclusive_scan_i32(const Scratch& s, const int32_t* o, int64_
   const int tiles = static_cast<int>((N + kIscanTile - 1) / kIscanTile);
   long long* tot = s.irec;
   long long* pre = s.irec + (s.max_tiles + 2);
+  if (s.coop && s.launch_mode != RS_LAUNCH_SEPARATE) {
+    const int cap = coop_capacity(reinterpret_cast<const void*>(iscan_coop_kernel));
+    if (cap > 0) {
+      const int grid = tiles < cap ? tiles : cap;
+      trace_mark(s.trace, "iscan", st);
+      return coop_launch(iscan_coop_kernel, grid, st, o, N, tiles, tot, pre, O,
+                         &s.glob->bar_count, s.err);
+    }
+  }
   trace_mark(s.trace, "iscan_sum", st);
   launch_pdl(iscan_sum_kernel, tiles, kBlock, st, o, N, tot, pre, &s.glob->ticket_iscan);
   trace_mark(s.trace, "iscan_emit", st);

@@ -15,55 +15,13 @@
 #include <climits>
 
 #include "common.cuh"
+#include "grid.cuh"
 #include "internal.h"
 #include "tile.cuh"
 #include "values.cuh"
 
 namespace rsk {
 namespace {
-
-constexpr unsigned long long kBarrierTimeoutNs = 10ull * 1000 * 1000 * 1000;  // 10 s
-
-__device__ __forceinline__ unsigned long long global_ns() {
-  unsigned long long t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-
-// Grid-wide barrier over all CTAs of the (cooperative, hence co-resident) launch, on one
-// arrival counter in the handle's ScanGlob that counts up through the launch: barrier k is
-// passed when the counter reaches k * gridDim.x. Thread 0 of each CTA arrives with a release
-// reduction and polls with acquire loads (the CTA's writes are ordered before the arrival by
-// the preceding __syncthreads, and every later read after the poll by the following one).
-// The wait is bounded: after kBarrierTimeoutNs it records RS_ERR_TIMEOUT and goes on.
-__device__ __forceinline__ void grid_barrier(unsigned int* count, unsigned int& target, int* err) {
-  target += gridDim.x;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(count) : "memory");
-    unsigned int cur;
-    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(cur) : "l"(count) : "memory");
-    if (static_cast<int>(cur - target) < 0) {
-      const unsigned long long t0 = global_ns();
-      for (;;) {
-        __nanosleep(20);
-        asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(cur) : "l"(count) : "memory");
-        if (static_cast<int>(cur - target) >= 0) break;
-        if (global_ns() - t0 > kBarrierTimeoutNs) {
-          flag_error(err, RS_ERR_TIMEOUT);
-          break;
-        }
-      }
-    }
-  }
-  __syncthreads();
-}
-
-// Last act of every CTA: one more arrival; the CTA that completes it returns the counter to
-// 0 for the next launch (stream order makes the reset visible to it).
-__device__ __forceinline__ void grid_exit(unsigned int* count, unsigned int target) {
-  if (threadIdx.x == 0 && atomicAdd(count, 1u) == target + gridDim.x - 1) atomicExch(count, 0u);
-}
 
 // Order-preserving integer keys of the log-weights (exact comparisons, no binary64 ALU).
 __device__ __forceinline__ long long fkey(float v) {

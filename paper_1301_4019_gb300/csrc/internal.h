@@ -97,7 +97,7 @@ cudaError_t launch_batched(const Scratch& s, int scheme, Acc acc, const void* lo
                            uint64_t seed, uint64_t step, double log_wmax, int64_t max_trials,
                            int32_t* out, int permute, cudaStream_t st);
 
-// mcmc.cu
+// mcmc.cu (d, when given, is set to the sentinel N by the launch itself)
 cudaError_t launch_metropolis(const Scratch& s, bool f64, const void* logw, int64_t N,
                               int32_t B, uint64_t seed, uint64_t step, uint32_t filter,
                               int32_t* a_out, int32_t* d_or_null, cudaStream_t st);

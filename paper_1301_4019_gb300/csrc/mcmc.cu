@@ -8,36 +8,45 @@
 // gathers of several steps are issued together and only the accept decisions run in
 // sequence (mcmc.cuh).
 #include "common.cuh"
+#include "grid.cuh"
 #include "internal.h"
 #include "mcmc.cuh"
 
 namespace rsk {
 namespace {
 
-template <typename T>
+// One thread per particle. COOP: a persistent cooperative grid that first sets the claims to
+// the sentinel N (the Prepermute initialisation), meets at a grid barrier, then runs the
+// chains over a grid-stride loop -- one launch instead of a fill and the chains.
+template <typename T, bool COOP>
 __global__ void __launch_bounds__(kBlock)
 metropolis_kernel(const T* __restrict__ lw, int64_t N, int32_t B, Keys keys,
-                  int32_t* __restrict__ a, int32_t* __restrict__ d, int* err) {
+                  int32_t* __restrict__ a, int32_t* __restrict__ d, unsigned int* bar, int* err) {
   pdl_wait();
-  const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (i >= N) return;
-  const int32_t k = metropolis_one(lw, N, B, keys, i, err);
-  a[i] = k;
-  if (d) atomicMin(d + k, static_cast<int32_t>(i));
+  const int64_t t0 = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  const int64_t stride = COOP ? static_cast<int64_t>(gridDim.x) * blockDim.x : N;
+  unsigned int target = 0;
+  if constexpr (COOP) {
+    if (d)
+      for (int64_t i = t0; i < N; i += stride) d[i] = static_cast<int32_t>(N);
+    grid_barrier(bar, target, err);
+  }
+  for (int64_t i = t0; i < N; i += stride) {
+    const int32_t k = metropolis_one(lw, N, B, keys, i, err);
+    a[i] = k;
+    if (d) atomicMin(d + k, static_cast<int32_t>(i));
+  }
+  if constexpr (COOP) grid_exit(bar, target);
 }
 
-// Rejection with warp refill (mcmc.cuh): warp w owns particles [w * kRejRun, ...).
+// Rejection with warp refill (mcmc.cuh) over the particles [start, end) of one warp run.
 template <typename T>
-__global__ void __launch_bounds__(kBlock)
-rejection_kernel(const T* __restrict__ lw, int64_t N, double log_wmax, int64_t max_trials,
-                 Keys keys, int32_t* __restrict__ a, int32_t* __restrict__ d, int* err) {
-  pdl_wait();
+__device__ __forceinline__ void rejection_run(const T* __restrict__ lw, int64_t N, int64_t start,
+                                              int64_t end, const RejBound& rb,
+                                              int64_t max_trials, const Keys& keys,
+                                              int32_t* __restrict__ a, int32_t* __restrict__ d,
+                                              int* err) {
   const int lane = threadIdx.x & 31;
-  const int64_t run = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
-  const int64_t start = run * kRejRun;
-  if (start >= N) return;  // uniform across the warp
-  const int64_t end = start + kRejRun < N ? start + kRejRun : N;
-  const RejBound rb = make_bound(log_wmax);
   int64_t i = start + lane;
   bool active = i < end;
   int64_t head = start + 32;
@@ -75,21 +84,92 @@ rejection_kernel(const T* __restrict__ lw, int64_t N, double log_wmax, int64_t m
   }
 }
 
+// Warp w takes the runs w, w + W, ... of kRejRun particles (W = warps of the grid; one run per
+// warp unless COOP, see metropolis_kernel).
+template <typename T, bool COOP>
+__global__ void __launch_bounds__(kBlock)
+rejection_kernel(const T* __restrict__ lw, int64_t N, double log_wmax, int64_t max_trials,
+                 Keys keys, int32_t* __restrict__ a, int32_t* __restrict__ d, unsigned int* bar,
+                 int* err) {
+  pdl_wait();
+  unsigned int target = 0;
+  if constexpr (COOP) {
+    if (d) {
+      const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+      for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < N;
+           i += stride)
+        d[i] = static_cast<int32_t>(N);
+    }
+    grid_barrier(bar, target, err);
+  }
+  const RejBound rb = make_bound(log_wmax);
+  const int64_t warps = (static_cast<int64_t>(gridDim.x) * blockDim.x) >> 5;
+  for (int64_t run = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+       run * kRejRun < N; run += warps) {  // uniform across the warp
+    const int64_t start = run * kRejRun;
+    const int64_t end = start + kRejRun < N ? start + kRejRun : N;
+    rejection_run(lw, N, start, end, rb, max_trials, keys, a, d, err);
+  }
+  if constexpr (COOP) grid_exit(bar, target);
+}
+
 }  // namespace
+
+// d, when given, is first set to the sentinel N (the Prepermute initialisation): inside the
+// cooperative rejection kernel when the device allows it, else by a fill launch.
+template <typename T>
+cudaError_t launch_metropolis_t(const Scratch& s, const T* lw, int64_t N, int32_t B,
+                                const Keys& keys, int32_t* a_out, int32_t* d, bool f64,
+                                cudaStream_t st) {
+  // (The cooperative form, fill and chains in one launch, measured slower than a fill launch
+  // followed by one thread per particle: the chains hide their gathers better in waves.)
+  unsigned int* bar = &s.glob->bar_count;
+  if (d) {
+    trace_mark(s.trace, "fill", st);
+    const cudaError_t e = launch_fill(d, N, static_cast<int32_t>(N), st);
+    if (e != cudaSuccess) return e;
+  }
+  trace_mark(s.trace, f64 ? "metropolis_f64" : "metropolis_f32", st);
+  launch_pdl(metropolis_kernel<T, false>, static_cast<int>((N + kBlock - 1) / kBlock), kBlock,
+             st, lw, N, B, keys, a_out, d, bar, s.err);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_rejection_t(const Scratch& s, const T* lw, int64_t N, double log_wmax,
+                               int64_t max_trials, const Keys& keys, int32_t* a_out, int32_t* d,
+                               bool f64, cudaStream_t st) {
+  unsigned int* bar = &s.glob->bar_count;
+  const int64_t runs = (N + kRejRun - 1) / kRejRun;
+  const int64_t want = (runs * 32 + kBlock - 1) / kBlock;
+  if (s.coop && s.launch_mode != RS_LAUNCH_SEPARATE) {
+    const int cap = coop_capacity(reinterpret_cast<const void*>(rejection_kernel<T, true>));
+    if (cap > 0) {
+      trace_mark(s.trace, f64 ? "rejection_f64" : "rejection_f32", st);
+      return coop_launch(rejection_kernel<T, true>, static_cast<int>(want < cap ? want : cap),
+                         st, lw, N, log_wmax, max_trials, keys, a_out, d, bar, s.err);
+    }
+  }
+  if (d) {
+    trace_mark(s.trace, "fill", st);
+    const cudaError_t e = launch_fill(d, N, static_cast<int32_t>(N), st);
+    if (e != cudaSuccess) return e;
+  }
+  trace_mark(s.trace, f64 ? "rejection_f64" : "rejection_f32", st);
+  launch_pdl(rejection_kernel<T, false>, static_cast<int>(want), kBlock, st, lw, N, log_wmax,
+             max_trials, keys, a_out, d, bar, s.err);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_metropolis(const Scratch& s, bool f64, const void* logw, int64_t N,
                               int32_t B, uint64_t seed, uint64_t step, uint32_t filter,
                               int32_t* a_out, int32_t* d, cudaStream_t st) {
   const Keys keys = make_keys(seed, step, filter, RS_METROPOLIS);
-  const int grid = static_cast<int>((N + kBlock - 1) / kBlock);
-  trace_mark(s.trace, f64 ? "metropolis_f64" : "metropolis_f32", st);
   if (f64)
-    launch_pdl(metropolis_kernel<double>, grid, kBlock, st, static_cast<const double*>(logw), N, B,
-                                                       keys, a_out, d, s.err);
-  else
-    launch_pdl(metropolis_kernel<float>, grid, kBlock, st, static_cast<const float*>(logw), N, B,
-                                                      keys, a_out, d, s.err);
-  return cudaGetLastError();
+    return launch_metropolis_t(s, static_cast<const double*>(logw), N, B, keys, a_out, d, true,
+                               st);
+  return launch_metropolis_t(s, static_cast<const float*>(logw), N, B, keys, a_out, d, false,
+                             st);
 }
 
 cudaError_t launch_rejection(const Scratch& s, bool f64, const void* logw, int64_t N,
@@ -97,18 +177,11 @@ cudaError_t launch_rejection(const Scratch& s, bool f64, const void* logw, int64
                              uint64_t step, uint32_t filter, int32_t* a_out, int32_t* d,
                              cudaStream_t st) {
   const Keys keys = make_keys(seed, step, filter, RS_REJECTION);
-  const int64_t runs = (N + kRejRun - 1) / kRejRun;
-  const int grid = static_cast<int>((runs * 32 + kBlock - 1) / kBlock);
-  trace_mark(s.trace, f64 ? "rejection_f64" : "rejection_f32", st);
   if (f64)
-    launch_pdl(rejection_kernel<double>, grid, kBlock, st, static_cast<const double*>(logw), N,
-                                                      log_wmax, max_trials, keys, a_out, d,
-                                                      s.err);
-  else
-    launch_pdl(rejection_kernel<float>, grid, kBlock, st, static_cast<const float*>(logw), N,
-                                                     log_wmax, max_trials, keys, a_out, d,
-                                                     s.err);
-  return cudaGetLastError();
+    return launch_rejection_t(s, static_cast<const double*>(logw), N, log_wmax, max_trials,
+                              keys, a_out, d, true, st);
+  return launch_rejection_t(s, static_cast<const float*>(logw), N, log_wmax, max_trials, keys,
+                            a_out, d, false, st);
 }
 
 }  // namespace rsk

@@ -130,3 +130,30 @@ def test_fused_repeated_calls_and_graph_replay(rs, h):
 def test_launch_mode_argument_checked(rs, h):
     with pytest.raises(rs.RsError):
         rs.rs_set_launch_mode(h, 3)
+
+
+@pytest.mark.parametrize("N", [1, 1000, 70001, 1310723])
+def test_mcmc_and_conversions_equal_across_launch_modes(rs, h, N):
+    """Metropolis and rejection (rejection's claim initialisation runs inside one cooperative
+    launch by default) and the offspring / integer-scan conversions (the scan is one
+    cooperative launch by default) equal their one-kernel-per-step forms bit for bit."""
+    for dtype in (np.float32, np.float64):
+        t = torch.from_numpy(workload.synthetic_logw(N, 2.5, seed=N + 1, dtype=dtype)).to(DEV)
+        for scheme in (rs.METROPOLIS, rs.REJECTION):
+            for permute in (False, True):
+                (s1, a1), (s2, a2) = _both(rs, h, scheme, t, B=12, seed=5, step=2,
+                                           permute=permute, log_wmax=0.0)
+                assert s1 == s2 == rs.RS_OK
+                assert np.array_equal(a1, a2), (dtype, scheme, permute)
+    a = rs.rs_resample(h, rs.MULTINOMIAL, t, seed=3)
+    res = []
+    for mode in (rs.LAUNCH_FUSED, rs.LAUNCH_SEPARATE):
+        rs.rs_set_launch_mode(h, mode)
+        o = rs.rs_offspring(h, a)
+        O = rs.rs_cumulative_offspring(h, o)
+        res.append((rs.rs_last_error(h), o.cpu().numpy(), O.cpu().numpy()))
+    rs.rs_set_launch_mode(h, rs.LAUNCH_AUTO)
+    assert res[0][0] == res[1][0] == rs.RS_OK
+    assert np.array_equal(res[0][1], res[1][1]) and np.array_equal(res[0][2], res[1][2])
+    assert np.array_equal(res[0][1], np.bincount(a.cpu().numpy(), minlength=N))
+    assert np.array_equal(res[0][2], np.cumsum(res[0][1]))
