@@ -205,6 +205,34 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------------------------------
+# DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) from the ncu
+# captures summarised in profiles/*_ncu.md (N = 2^20; ncu replays with cold caches). They
+# hold for the kernel sources they were taken with: `traffic` is reported only while the
+# sources still hash to SOURCE_HASH, and is null once a kernel has changed.
+# ---------------------------------------------------------------------------------------
+NCU_TRAFFIC = {"SOURCE_HASH": "a0dad40459d1d738",
+               "permute": 8393216, "permute_sorted": 8392960, "metropolis_f64": 12597248,
+               "fused_systematic_f32": 4275456, "fused_multinomial_f64": 8492032,
+               "search_f64": 16784384}
+
+
+def kernel_sources_hash() -> str:
+    import hashlib
+    import glob
+    h = hashlib.sha256()
+    for p in sorted(glob.glob(os.path.join(ROOT, "paper_1301_4019_gb300", "csrc", "*"))):
+        h.update(os.path.basename(p).encode())
+        h.update(open(p, "rb").read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(label: str, N: int):
+    if N != 1 << 20 or kernel_sources_hash() != NCU_TRAFFIC["SOURCE_HASH"]:
+        return None
+    return NCU_TRAFFIC.get(label)
+
+
+# ---------------------------------------------------------------------------------------
 # algorithmic bytes / operations per kernel launch (roofline numerators)
 # ---------------------------------------------------------------------------------------
 def kernel_roofline_units(label: str, N: int, B: int):
@@ -391,7 +419,8 @@ def run_ours(args):
         achieved = amount / (dom_ms * 1e-3) / 1e9
         roof = {"bound": "hbm", "kernel": dom_label, "achieved": round(achieved, 1),
                 "peak": hbm_peak, "unit": "GB/s", "frac": round(achieved / hbm_peak, 4),
-                "peak_source": peak_src, "traffic": None,
+                "peak_source": peak_src, "traffic": ncu_traffic(dom_label, N),
+                "traffic_note": "ncu dram bytes per launch, cold-cache replay (profiles/)",
                 "algorithmic_bytes_per_launch": amount}
     else:
         # G Philox4x32-10 draws/s: 152 SMs x 2070 MHz x 32 IMAD.WIDE/clk/SM / 20 per draw
@@ -400,7 +429,8 @@ def run_ours(args):
         roof = {"bound": "alu", "kernel": dom_label, "achieved": round(achieved, 1),
                 "peak": philox_peak, "unit": "G Philox/s",
                 "frac": round(achieved / philox_peak, 4), "peak_source": "derived",
-                "traffic": None}
+                "traffic": ncu_traffic(dom_label, N),
+                "traffic_note": "ncu dram bytes per launch, cold-cache replay (profiles/)"}
     roof["share_of_step"] = round(sum(by_label[dom_label]) / total_kernel_ms, 4)
     roof["avg_launch_ms"] = round(dom_ms, 5)
 
