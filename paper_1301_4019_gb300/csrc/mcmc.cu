@@ -15,11 +15,16 @@
 namespace rsk {
 namespace {
 
+// CTAs per SM the register allocation must allow: 6 for the binary32 chains (38 registers,
+// measured 3 % faster than 56); the binary64 chains keep their 62 registers (fewer measured
+// slower: their four proposals in flight need them).
+template <typename T> constexpr int metropolis_min_ctas() { return sizeof(T) == 4 ? 6 : 1; }
+
 // One thread per particle. COOP: a persistent cooperative grid that first sets the claims to
 // the sentinel N (the Prepermute initialisation), meets at a grid barrier, then runs the
 // chains over a grid-stride loop -- one launch instead of a fill and the chains.
 template <typename T, bool COOP>
-__global__ void __launch_bounds__(kBlock)
+__global__ void __launch_bounds__(kBlock, metropolis_min_ctas<T>())
 metropolis_kernel(const T* __restrict__ lw, int64_t N, int32_t B, Keys keys,
                   int32_t* __restrict__ a, int32_t* __restrict__ d, unsigned int* bar, int* err) {
   pdl_wait();

@@ -84,7 +84,8 @@ __device__ __forceinline__ bool f64_accept_lt(double lwj, float lwj_f, bool okj,
   return exact_f64_less_exp(lwj, lwk, x);
 }
 
-constexpr int kUnroll = 4;
+constexpr int kUnroll = 4;    // binary32 chains: proposals issued together
+constexpr int kUnroll64 = 4;  // binary64 chains (2 measured slower)
 
 // Metropolis chain of particle i over n log-weights lw (Code 2): B steps, step s proposes j
 // and draws u from counter (i, s). Returns the ancestor.
@@ -146,18 +147,18 @@ __device__ __forceinline__ int32_t metropolis_one(const double* __restrict__ lw,
   int64_t k = i;
   const uint32_t ii = static_cast<uint32_t>(i);
   int32_t s = 0;
-  for (; s + kUnroll <= B; s += kUnroll) {
-    uint4 x[kUnroll];
-    double lwj[kUnroll];
-    int64_t j[kUnroll];
+  for (; s + kUnroll64 <= B; s += kUnroll64) {
+    uint4 x[kUnroll64];
+    double lwj[kUnroll64];
+    int64_t j[kUnroll64];
 #pragma unroll
-    for (int q = 0; q < kUnroll; ++q) {
+    for (int q = 0; q < kUnroll64; ++q) {
       x[q] = draw(keys, ii, static_cast<uint32_t>(s + q));
       j[q] = uniform_index(x[q], n);
       lwj[q] = __ldg(lw + j[q]);
     }
 #pragma unroll
-    for (int q = 0; q < kUnroll; ++q) {
+    for (int q = 0; q < kUnroll64; ++q) {
       const long long kj = f64_key(lwj[q]);
       float lwj_f;
       const bool okj = f64_to_f32_trunc(lwj[q], lwj_f);
