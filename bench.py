@@ -448,8 +448,10 @@ def run_ours(args):
     for name, _, _ in dtypes:
         for s in range(5):
             t_ms = sum(per_call.get(ci, {}).values())
+            S = 4 if name == "f32" else 8
             per_scheme[f"{SCHEME_NAMES[s]}_{name}"] = {
-                "ms": round(t_ms, 5), "G_ancestors_per_s": round(N / (t_ms * 1e-3) / 1e9, 3)}
+                "ms": round(t_ms, 5), "G_ancestors_per_s": round(N / (t_ms * 1e-3) / 1e9, 3),
+                "hbm_frac": round(sweep_hbm_bytes(s, S, N) / (t_ms * 1e-3) / 1e9 / hbm_peak, 4)}
             ci += 1
 
     ms_per_step, value = aggregate_replicas(ms_total / args.steps, ancestors_per_step, world,
@@ -547,6 +549,8 @@ def run_ours(args):
                               "overlapping the kernels of neighbouring calls"},
             "roofline": roof,
             "per_scheme": per_scheme,
+            "per_scheme_note": "one call with Permute, traced (kernel-to-kernel events); "
+                               "hbm_frac = algorithmic bytes (sweep_hbm_bytes) / time / peak",
             "per_kernel": per_kernel,
             "gpu_launches": gpu_launches_per_step * args.steps,
             "gpu_launches_per_step": gpu_launches_per_step,
