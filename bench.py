@@ -66,6 +66,8 @@ def parse_args():
                         "2^24, binary32 and binary64, L2 flushed before every call; one JSON "
                         "line")
     p.add_argument("--sweep-reps", type=int, default=15)
+    p.add_argument("--sweep-y", default="0,1,2,3,4",
+                   help="comma-separated y values of the sweep (weight skew)")
     p.add_argument("--precision", action="store_true",
                    help="offspring bias of the scan schemes: binary32 plain vs compensated vs "
                         "binary64, N = 2^16 .. 2^24, y in {0, 2, 4}; one JSON line")
@@ -731,14 +733,15 @@ def run_sweep(args):
     rows = []
     clocks = ClockSampler(torch.cuda.current_device())
     clocks.start()
+    ys = [float(v) for v in args.sweep_y.split(",")]
     with rs.Handle(1 << 24) as h:
         rs.rs_set_launch_mode(h, LAUNCH_MODES[args.launch_mode])
-        for log2n in range(10, 25):
+        for y, log2n in ((y, n) for y in ys for n in range(10, 25)):
             N = 1 << log2n
-            B = workload_params(argparse.Namespace(log2n=log2n, y=args.y))[1]
+            B = workload_params(argparse.Namespace(log2n=log2n, y=y))[1]
             out = torch.empty(N, dtype=torch.int32, device="cuda")
             for name, npdt in (("f32", np.float32), ("f64", np.float64)):
-                lw = torch.from_numpy(workload.synthetic_logw(N, args.y, seed=SEED + log2n,
+                lw = torch.from_numpy(workload.synthetic_logw(N, y, seed=SEED + log2n,
                                                               dtype=npdt)).cuda()
                 S = 4 if name == "f32" else 8
                 for scheme in range(5):
@@ -758,7 +761,8 @@ def run_sweep(args):
                         ts.append(e0.elapsed_time(e1))
                     ms = statistics.median(ts)
                     gbs = sweep_hbm_bytes(scheme, S, N) / (ms * 1e-3) / 1e9
-                    rows.append({"log2n": log2n, "dtype": name, "scheme": SCHEME_NAMES[scheme],
+                    rows.append({"y": y, "B": B, "log2n": log2n, "dtype": name,
+                                 "scheme": SCHEME_NAMES[scheme],
                                  "us": round(ms * 1e3, 2),
                                  "G_ancestors_per_s": round(N / (ms * 1e-3) / 1e9, 3),
                                  "hbm_frac": round(gbs / hbm_peak, 4)})
@@ -767,10 +771,11 @@ def run_sweep(args):
     clk = clocks.stop()
     if st != rs.RS_OK:
         raise SystemExit(f"device status after sweep: {rs.rs_strerror(st)}")
-    print(json.dumps({"sweep": "N = 2^10 .. 2^24, y = %g, B from Eq. B, log_wmax = 0, with "
+    print(json.dumps({"sweep": "N = 2^10 .. 2^24, y in {%s}, B from Eq. B, log_wmax = 0, with "
                       "Permute; median of %d calls, each after writing %d MiB (L2 flush); "
                       "hbm_frac = algorithmic bytes (sweep_hbm_bytes) / time / %.1f GB/s "
-                      "(measured)" % (args.y, args.sweep_reps, 2 * L2_BYTES // 2**20, hbm_peak),
+                      "(measured)" % (args.sweep_y, args.sweep_reps, 2 * L2_BYTES // 2**20,
+                                      hbm_peak),
                       "launch_mode": args.launch_mode, "clocks": clk, "rows": rows}))
 
 
