@@ -180,6 +180,15 @@ int rs_permute(rs_handle* h, const int32_t* a_dev, int64_t N, int32_t* c_dev, vo
 #define RS_LAUNCH_SEPARATE 2
 int rs_set_launch_mode(rs_handle* h, int mode);
 
+/* Effective sample size of N log-weights: *ess_dev (one binary64 on the device) =
+ * (sum_i w_i)^2 / sum_i w_i^2 with w_i = exp(logw_i - max logw) (Appendix E), between 1 and N
+ * -- the statistic an adaptive particle filter compares with a threshold to decide whether to
+ * resample at a step (Section 4.3). Weights in binary32 (relative error about 2^-23), sums in
+ * two-float per CTA and exact across CTAs. NaN/+inf flag RS_ERR_NONFINITE, all weights zero
+ * RS_ERR_ZERO_WEIGHT (ess 0). One cooperative launch: RS_ERR_CUDA where the device cannot. */
+int rs_ess(rs_handle* h, int dtype, const void* logw_dev, int64_t N, double* ess_dev,
+           void* stream);
+
 /* ---- the SMC loop around the resampler (Code 1) ---------------------------------------
  * In-place copy by a permuted ancestry (Section 2.3): x_dev holds N rows of D floats
  * (row-major, device); row i becomes row c_dev[i]. c must satisfy the predicate of Permute
@@ -193,14 +202,16 @@ int rs_copy_ancestors(rs_handle* h, float* x_dev, int32_t D, const int32_t* c_de
  *   x_1 ~ N(0, sigma_x^2 / (1 - phi^2)),  x_t = phi x_{t-1} + sigma_x eps_t,
  *   y_t = x_t + sigma_y eta_t
  * (the model of the full SMC loop; Code 1 lines "propagate" and "weight"). init = 1 draws x
- * from the stationary law, init = 0 propagates x in place. Writes logw_dev[i] =
- * -(y - x_i)^2 / (2 sigma_y^2) (the constant -log(2 pi sigma_y^2)/2 is dropped, so
- * log w_max = 0). The noise of particle i is one Box-Muller normal from the Philox words 0
- * and 1 of counter (i, 0, step, filter * 8 + 5). |phi| < 1, sigma_x, sigma_y > 0 and y finite
- * (RS_ERR_ARG otherwise). */
-int rs_lgssm_step(rs_handle* h, float* x_dev, int64_t N, int init, float phi, float sigma_x,
-                  float y, float sigma_y, uint64_t seed, uint64_t step, uint32_t filter,
-                  float* logw_dev, void* stream);
+ * from the stationary law, init = 0 propagates x in place. With l_i = -(y - x_i)^2 /
+ * (2 sigma_y^2) (the constant -log(2 pi sigma_y^2)/2 is dropped, so log w_max = 0 for one
+ * step), logw_dev[i] = l_i (accumulate = 0, after resampling) or logw_dev[i] + l_i
+ * (accumulate = 1: the weights carried over a step without resampling). The noise of
+ * particle i is one Box-Muller normal from the Philox words 0 and 1 of counter
+ * (i, 0, step, filter * 8 + 5). |phi| < 1, sigma_x, sigma_y > 0 and y finite (RS_ERR_ARG
+ * otherwise). */
+int rs_lgssm_step(rs_handle* h, float* x_dev, int64_t N, int init, int accumulate, float phi,
+                  float sigma_x, float y, float sigma_y, uint64_t seed, uint64_t step,
+                  uint32_t filter, float* logw_dev, void* stream);
 
 /* B* = log(eps) / log(1 - beta) of Eq. (B) (Section 2.1), rounded up: the number of
  * Metropolis steps that bounds the total-variation distance of every chain by eps, for a

@@ -40,6 +40,7 @@ EXPORTED = [
     "rs_prepermute", "rs_permute", "rs_metropolis_B", "rs_last_error", "rs_strerror",
     "rs_trace", "rs_trace_count", "rs_trace_label", "rs_systematic_noalloc",
     "rs_resample_batched", "rs_set_launch_mode", "rs_copy_ancestors", "rs_lgssm_step",
+    "rs_ess",
 ]
 NOALLOC_MAX_N = 1 << 22
 LAUNCH_AUTO, LAUNCH_FUSED, LAUNCH_SEPARATE = 0, 1, 2
@@ -100,8 +101,9 @@ def _declare(lib):
                                     C.POINTER(_Opts), P]),
         "rs_set_launch_mode": (I, [P, I]),
         "rs_copy_ancestors": (I, [P, P, I32, P, I64, P]),
-        "rs_lgssm_step": (I, [P, P, I64, I, C.c_float, C.c_float, C.c_float, C.c_float, U64,
-                              U64, C.c_uint32, P, P]),
+        "rs_ess": (I, [P, I, P, I64, P, P]),
+        "rs_lgssm_step": (I, [P, P, I64, I, I, C.c_float, C.c_float, C.c_float, C.c_float,
+                              U64, U64, C.c_uint32, P, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -302,6 +304,17 @@ def rs_set_launch_mode(h: Handle, mode: int) -> None:
     _check(load().rs_set_launch_mode(h.ptr, int(mode)), "rs_set_launch_mode")
 
 
+def rs_ess(h: Handle, logw: torch.Tensor, out: torch.Tensor | None = None,
+           stream=None) -> torch.Tensor:
+    """Effective sample size (sum w)^2 / sum w^2 of the max-shifted weights (one float64 on
+    the device)."""
+    if out is None:
+        out = torch.empty(1, dtype=torch.float64, device=logw.device)
+    _check(load().rs_ess(h.ptr, _dtype_code(logw), _dev(logw, None, "logw"), logw.numel(),
+                         _dev(out, torch.float64, "ess"), _stream(stream)), "rs_ess")
+    return out
+
+
 def rs_copy_ancestors(h: Handle, x: torch.Tensor, c: torch.Tensor, stream=None) -> torch.Tensor:
     """In place: row i of x ([N] or [N, D] float32) becomes row c[i] (c from Permute)."""
     N = c.numel()
@@ -316,12 +329,15 @@ def rs_copy_ancestors(h: Handle, x: torch.Tensor, c: torch.Tensor, stream=None) 
 
 def rs_lgssm_step(h: Handle, x: torch.Tensor, init: bool, phi: float, sigma_x: float, y: float,
                   sigma_y: float, seed: int = 0, step: int = 0, filter: int = 0,
-                  logw: torch.Tensor | None = None, stream=None) -> torch.Tensor:
-    """Propagate x in place (or draw it from the stationary law) and return the log-weights."""
+                  logw: torch.Tensor | None = None, accumulate: bool = False,
+                  stream=None) -> torch.Tensor:
+    """Propagate x in place (or draw it from the stationary law) and return the log-weights
+    (added to the given ones when accumulate)."""
     N = x.numel()
     if logw is None:
         logw = torch.empty(N, dtype=torch.float32, device=x.device)
     _check(load().rs_lgssm_step(h.ptr, _dev(x, torch.float32, "x"), N, int(bool(init)),
+                                int(bool(accumulate)),
                                 float(phi), float(sigma_x), float(y), float(sigma_y),
                                 int(seed), int(step), int(filter),
                                 _dev(logw, torch.float32, "logw"), _stream(stream)),

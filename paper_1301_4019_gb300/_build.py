@@ -12,7 +12,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB_NAME = "libgb300resample.so"
 LIB_PATH = os.path.join(OUT_DIR, LIB_NAME)
-SOURCES = ["scan.cu", "mcmc.cu", "aux.cu", "api.cu", "noalloc.cu", "batched.cu", "fused.cu", "model.cu"]
+SOURCES = ["scan.cu", "mcmc.cu", "aux.cu", "api.cu", "noalloc.cu", "batched.cu", "fused.cu", "model.cu", "ess.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
               "--expt-relaxed-constexpr"]

@@ -343,6 +343,19 @@ int rs_set_launch_mode(rs_handle* h, int mode) {
   return RS_OK;
 }
 
+int rs_ess(rs_handle* h, int dtype, const void* logw_dev, int64_t N, double* ess_dev,
+           void* stream) {
+  if (!h || !logw_dev || !ess_dev) return RS_ERR_ARG;
+  int st = check_n(h, N);
+  if (st != RS_OK) return st;
+  if (dtype != RS_F32 && dtype != RS_F64) return RS_ERR_ARG;
+  if ((st = set_device(h)) != RS_OK) return st;
+  const cudaError_t e = rsk::launch_ess(h->s, dtype == RS_F64, logw_dev, N, ess_dev,
+                                        as_stream(stream));
+  end_mark(h, as_stream(stream));
+  return cuda_status(e);
+}
+
 int rs_copy_ancestors(rs_handle* h, float* x_dev, int32_t D, const int32_t* c_dev, int64_t N,
                       void* stream) {
   if (!h || !x_dev || !c_dev || D < 1) return RS_ERR_ARG;
@@ -355,19 +368,20 @@ int rs_copy_ancestors(rs_handle* h, float* x_dev, int32_t D, const int32_t* c_de
   return cuda_status(e);
 }
 
-int rs_lgssm_step(rs_handle* h, float* x_dev, int64_t N, int init, float phi, float sigma_x,
-                  float y, float sigma_y, uint64_t seed, uint64_t step, uint32_t filter,
-                  float* logw_dev, void* stream) {
+int rs_lgssm_step(rs_handle* h, float* x_dev, int64_t N, int init, int accumulate, float phi,
+                  float sigma_x, float y, float sigma_y, uint64_t seed, uint64_t step,
+                  uint32_t filter, float* logw_dev, void* stream) {
   if (!h || !x_dev || !logw_dev) return RS_ERR_ARG;
   int st = check_n(nullptr, N);
   if (st != RS_OK) return st;
-  if (init != 0 && init != 1) return RS_ERR_ARG;
+  if ((init != 0 && init != 1) || (accumulate != 0 && accumulate != 1)) return RS_ERR_ARG;
   if (!(std::fabs(phi) < 1.0f) || !(sigma_x > 0.0f) || !(sigma_y > 0.0f) || !std::isfinite(y) ||
       !std::isfinite(sigma_x) || !std::isfinite(sigma_y) || filter >= (1u << 29))
     return RS_ERR_ARG;
   if ((st = set_device(h)) != RS_OK) return st;
-  const cudaError_t e = rsk::launch_lgssm_step(h->s, x_dev, N, init, phi, sigma_x, y, sigma_y,
-                                               seed, step, filter, logw_dev, as_stream(stream));
+  const cudaError_t e = rsk::launch_lgssm_step(h->s, x_dev, N, init, accumulate, phi, sigma_x,
+                                               y, sigma_y, seed, step, filter, logw_dev,
+                                               as_stream(stream));
   end_mark(h, as_stream(stream));
   return cuda_status(e);
 }

@@ -123,11 +123,15 @@ cudaError_t launch_adjacent_difference(const int32_t* O, int64_t N, int32_t* o,
 cudaError_t launch_cumoff_to_ancestors(const Scratch& s, const int32_t* O, int64_t N,
                                        int32_t* a, cudaStream_t st);
 
+// ess.cu (cooperative; cudaErrorNotSupported without cooperative launches)
+cudaError_t launch_ess(const Scratch& s, bool f64, const void* logw, int64_t N, double* ess,
+                       cudaStream_t st);
+
 // model.cu
 cudaError_t launch_copy_ancestors(const Scratch& s, float* x, int D, const int32_t* c, int64_t N,
                                   cudaStream_t st);
-cudaError_t launch_lgssm_step(const Scratch& s, float* x, int64_t N, int init, float phi,
-                              float sigma_x, float y, float sigma_y, uint64_t seed,
+cudaError_t launch_lgssm_step(const Scratch& s, float* x, int64_t N, int init, int accumulate,
+                              float phi, float sigma_x, float y, float sigma_y, uint64_t seed,
                               uint64_t step, uint32_t filter, float* logw, cudaStream_t st);
 
 }  // namespace rsk

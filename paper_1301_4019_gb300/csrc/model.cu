@@ -38,8 +38,9 @@ __device__ __forceinline__ float normal_draw(const Keys& keys, int64_t i) {
 }
 
 __global__ void __launch_bounds__(kBlock)
-lgssm_step_kernel(float* __restrict__ x, int64_t N, int init, float phi, float sigma_x,
-                  float sigma_0, float y, float inv_2vy, Keys keys, float* __restrict__ logw) {
+lgssm_step_kernel(float* __restrict__ x, int64_t N, int init, int accumulate, float phi,
+                  float sigma_x, float sigma_0, float y, float inv_2vy, Keys keys,
+                  float* __restrict__ logw) {
   pdl_wait();
   const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
   if (i >= N) return;
@@ -47,7 +48,8 @@ lgssm_step_kernel(float* __restrict__ x, int64_t N, int init, float phi, float s
   const float xi = init ? sigma_0 * z : fmaf(phi, x[i], sigma_x * z);
   x[i] = xi;
   const float e = y - xi;
-  logw[i] = -(e * e) * inv_2vy;
+  const float l = -(e * e) * inv_2vy;
+  logw[i] = accumulate ? logw[i] + l : l;
 }
 
 inline int grid_for(int64_t N) { return static_cast<int>((N + kBlock - 1) / kBlock); }
@@ -61,13 +63,13 @@ cudaError_t launch_copy_ancestors(const Scratch& s, float* x, int D, const int32
   return cudaGetLastError();
 }
 
-cudaError_t launch_lgssm_step(const Scratch& s, float* x, int64_t N, int init, float phi,
-                              float sigma_x, float y, float sigma_y, uint64_t seed,
+cudaError_t launch_lgssm_step(const Scratch& s, float* x, int64_t N, int init, int accumulate,
+                              float phi, float sigma_x, float y, float sigma_y, uint64_t seed,
                               uint64_t step, uint32_t filter, float* logw, cudaStream_t st) {
   const double s0 = static_cast<double>(sigma_x) / std::sqrt(1.0 - static_cast<double>(phi) * phi);
   const float inv_2vy = static_cast<float>(0.5 / (static_cast<double>(sigma_y) * sigma_y));
   trace_mark(s.trace, "lgssm_step", st);
-  launch_pdl(lgssm_step_kernel, grid_for(N), kBlock, st, x, N, init, phi, sigma_x,
+  launch_pdl(lgssm_step_kernel, grid_for(N), kBlock, st, x, N, init, accumulate, phi, sigma_x,
                                                    static_cast<float>(s0), y, inv_2vy,
                                                    make_keys(seed, step, filter, 5u), logw);
   return cudaGetLastError();

@@ -3,6 +3,8 @@ through the library's C ABI: for t = 1..T, resample (t > 1, with Permute so that
 run in place, Section 2.3), copy in place, propagate and weight, and accumulate the log of the
 mean weight (the filter's estimate of log p(y_t | y_1:t-1), computed with the max-shift of
 Appendix E). Every step runs in the library's kernels; this module only sequences the calls.
+The adaptive form resamples only when the effective sample size falls below a threshold
+(rs_ess) and carries the weights over the other steps.
 """
 from __future__ import annotations
 
@@ -11,7 +13,7 @@ import math
 import numpy as np
 import torch
 
-from . import (PREC_COMPENSATED, Handle, rs_copy_ancestors, rs_cumulative_weights,
+from . import (PREC_COMPENSATED, Handle, rs_copy_ancestors, rs_cumulative_weights, rs_ess,
                rs_lgssm_step, rs_resample)
 
 
@@ -60,3 +62,37 @@ def lgssm_bootstrap(h: Handle, y, N: int, scheme: int, phi: float, sigma_x: floa
     b = lgssm_bootstrap_launch(h, y, N, scheme, phi, sigma_x, sigma_y, seed, B, prec,
                                stream=stream)
     return lgssm_loglik_from(b, N, sigma_y)
+
+
+def lgssm_adaptive(h: Handle, y, N: int, scheme: int, phi: float, sigma_x: float,
+                   sigma_y: float, ess_fraction: float = 0.5, seed: int = 0, B: int = 64,
+                   prec: int = PREC_COMPENSATED, stream=None):
+    """The bootstrap filter with resampling on demand: after weighting step t, resample at
+    step t + 1 only if ESS_t < ess_fraction * N; otherwise the weights carry over and the next
+    step adds its log-likelihood to them. Returns (log p-hat(y_1:T), number of resamplings).
+    The increment of step t is log sum w_t - log sum w_{t-1} (log N after a resampling). The
+    host reads the ESS every step to decide."""
+    T = len(y)
+    b = LgssmBuffers(N, T)
+    ess = torch.empty(1, dtype=torch.float64, device=b.x.device)
+    base = math.log(N)
+    resample = False
+    n_res = 0
+    ll = 0.0
+    for t in range(T):
+        if resample:
+            rs_resample(h, scheme, b.logw, B=B, seed=seed, step=t, out=b.c, permute=True,
+                        prec=prec, log_wmax=0.0, stream=stream)
+            rs_copy_ancestors(h, b.x, b.c, stream=stream)
+            base = math.log(N)
+            n_res += 1
+        rs_lgssm_step(h, b.x, t == 0, phi, sigma_x, float(y[t]), sigma_y, seed=seed, step=t,
+                      logw=b.logw, accumulate=(t > 0 and not resample), stream=stream)
+        rs_cumulative_weights(h, b.logw, prec=prec, W=b.W, log_total=b.log_total[t:t + 1],
+                              stream=stream)
+        rs_ess(h, b.logw, out=ess, stream=stream)
+        lse = float(b.log_total[t].item())
+        ll += lse - base - 0.5 * math.log(2 * math.pi * sigma_y ** 2)
+        base = lse
+        resample = float(ess.item()) < ess_fraction * N
+    return ll, n_res

@@ -89,3 +89,36 @@ def test_bootstrap_loglik_matches_kalman(rs, h, scheme):
     # the full-size filter (N = 2^20): its own spread is a quarter of the 2^16 one
     ll = smc.lgssm_bootstrap(h, y, 1 << 20, scheme, PHI, SX, SY, seed=99, B=64)
     assert abs(ll - want) < 4 * sd / 4 + 0.02, (ll, want, sd)
+
+
+def test_ess_matches_host(rs, h):
+    for dtype in (np.float32, np.float64):
+        for N, y in ((1, 0.0), (1000, 2.0), (300007, 3.5)):
+            lw = workload.synthetic_logw(N, y, seed=N, dtype=dtype)
+            if N > 10:
+                lw[::7] = -np.inf
+            e = rs.rs_ess(h, torch.from_numpy(lw).to(DEV)).item()
+            assert rs.rs_last_error(h) == rs.RS_OK
+            w = np.exp(lw.astype(np.float64) - lw.max())
+            want = w.sum() ** 2 / (w * w).sum()
+            assert abs(e - want) <= 1e-5 * want, (dtype, N, e, want)
+    z = torch.full((100,), -np.inf, dtype=torch.float32, device=DEV)
+    assert rs.rs_ess(h, z).item() == 0.0
+    assert rs.rs_last_error(h) == rs.RS_ERR_ZERO_WEIGHT
+
+
+@pytest.mark.parametrize("scheme", [2, 4])
+def test_adaptive_filter_matches_kalman(rs, h, scheme):
+    """Resampling on demand (ESS < N/2): the log-likelihood still agrees with the Kalman
+    filter within 4 seed-to-seed standard deviations, with fewer resamplings than steps."""
+    from paper_1301_4019_gb300 import smc
+    T, N = 100, 1 << 16
+    _, y = workload.lgssm_simulate(T, PHI, SX, SY, seed=21)
+    want = kalman.lgssm_loglik(y, PHI, SX, SY)
+    runs = [smc.lgssm_adaptive(h, y, N, scheme, PHI, SX, SY, 0.5, seed=s) for s in range(16)]
+    assert rs.rs_last_error(h) == rs.RS_OK
+    lls = np.array([r[0] for r in runs])
+    n_res = [r[1] for r in runs]
+    assert 0 < min(n_res) and max(n_res) < T - 1
+    sd = lls.std(ddof=1)
+    assert abs(lls.mean() - want) < 4 * sd, (lls.mean(), want, sd, n_res)
