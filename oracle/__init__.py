@@ -82,6 +82,10 @@ def _declare(lib):
         "orc_metropolis_B": (_I32, [C.c_double, C.c_double]),
         "orc_rejection_f32": (C.c_int, [_P, _I64, C.c_double, _I64, _U64, _U64, _U32, _P, _P]),
         "orc_rejection_f64": (C.c_int, [_P, _I64, C.c_double, _I64, _U64, _U64, _U32, _P, _P]),
+        "orc_prc_f32": (C.c_int, [_P, _I64, C.c_double, _I64, _U64, _U64, _U32, _P, _P]),
+        "orc_prc_f64": (C.c_int, [_P, _I64, C.c_double, _I64, _U64, _U64, _U32, _P, _P]),
+        "orc_prc_weights_f32": (C.c_int, [_P, _P, _I64, C.c_double, _P]),
+        "orc_prc_weights_f64": (C.c_int, [_P, _P, _I64, C.c_double, _P]),
         "orc_weights_f32": (C.c_int, [_P, _I64, _P, _P]),
         "orc_weights_f64": (C.c_int, [_P, _I64, _P, _P]),
         "orc_inclusive_prefix_sum_f32": (None, [_P, _I64, _P]),
@@ -200,6 +204,30 @@ def rejection(lw: np.ndarray, log_wmax: float, seed: int, step: int = 0, filter_
                                                      max_trials, seed, step, filter_,
                                                      _ptr(a), _ptr(t))
     return (st, a, t) if with_trials else (st, a)
+
+
+def partial_rejection_control(lw: np.ndarray, log_vmax: float, seed: int, step: int = 0,
+                              filter_: int = 0, max_trials: int = 1 << 20,
+                              permuted: bool = False, with_trials: bool = False):
+    """Partial rejection control (Section 2.2): rejection sampling (Code 3) from
+    v = min(w, v_max) with the bound v_max, optionally followed by Permute (Code 10), and
+    the log-weights log(w/v) of the delivered ancestors. Returns (status, a, lw_out[, trials])."""
+    lib = _load()
+    lw = np.ascontiguousarray(lw)
+    N = len(lw)
+    a = np.zeros(N, np.int32)
+    t = np.zeros(N, np.int64)
+    st = getattr(lib, "orc_prc_" + _sfx(lw))(_ptr(lw), N, float(log_vmax), max_trials, seed,
+                                              step, filter_, _ptr(a), _ptr(t))
+    if permuted and st == OK:
+        a = permute(a)
+    out = np.zeros_like(lw)
+    if st in (OK, ERR_REJECTION_CAP):
+        st2 = getattr(lib, "orc_prc_weights_" + _sfx(lw))(_ptr(lw), _ptr(a), N,
+                                                           float(log_vmax), _ptr(out))
+        if st2 != OK:
+            raise ValueError("ancestor index out of range")
+    return (st, a, out, t) if with_trials else (st, a, out)
 
 
 def weights(lw: np.ndarray):

@@ -316,6 +316,107 @@ int orc_rejection_f64(const double* lw, int64_t N, double log_wmax, int64_t max_
     return status;
 }
 
+/* Partial rejection control (Section 2.2, last paragraph, after Liu et al. 1998): pick
+ * v_max below the weight bound, set v^i = min(w^i, v_max) and run the rejection sampler of
+ * Code 3 on v with the bound v_max; the outcome stays weighted, particle i carrying
+ * w^{a^i} / v^{a^i} (orc_prc_weights_*). In the log domain lv^j = min(lw^j, log v_max), and the
+ * attempt accepts when u < exp(lv^j - log v_max); a proposal with w^j >= v_max has ratio 1.
+ * No weight can violate the bound, so the only error statuses are the argument checks, a
+ * non-finite log-weight and the trial cap. */
+int orc_prc_f32(const float* lw, int64_t N, double log_vmax, int64_t max_trials,
+                uint64_t seed, uint64_t step, uint32_t filter, int32_t* a, int64_t* trials) {
+    if (check_n(N) != ORC_OK || max_trials < 1 || !isfinite(log_vmax)) return ORC_ERR_ARG;
+    if (check_finite_f32(lw, N) != ORC_OK) return ORC_ERR_NONFINITE;
+    float lvmax = (float)log_vmax;
+    int status = ORC_OK;
+    for (int64_t i = 0; i < N; ++i) {
+        int64_t j = i;
+        int64_t n = 0;
+        int accepted = 0;
+        while (n < max_trials) {
+            uint32_t x[4];
+            orc_draw(seed, (uint32_t)i, (uint32_t)n, step, filter, ORC_REJECTION, x);
+            if (n > 0) j = orc_uniform_index(x, N);
+            float u = orc_u01_f32(x);
+            float lv = lw[j] < lvmax ? lw[j] : lvmax;
+            float delta = lv - lvmax;
+            n += 1;
+            if (delta == 0.0f || u < orc_exp_f32(delta)) {
+                accepted = 1;
+                break;
+            }
+        }
+        if (!accepted) {
+            j = i;
+            status = ORC_ERR_REJECTION_CAP;
+        }
+        a[i] = (int32_t)j;
+        if (trials) trials[i] = n;
+    }
+    return status;
+}
+
+int orc_prc_f64(const double* lw, int64_t N, double log_vmax, int64_t max_trials,
+                uint64_t seed, uint64_t step, uint32_t filter, int32_t* a, int64_t* trials) {
+    if (check_n(N) != ORC_OK || max_trials < 1 || !isfinite(log_vmax)) return ORC_ERR_ARG;
+    if (check_finite_f64(lw, N) != ORC_OK) return ORC_ERR_NONFINITE;
+    int status = ORC_OK;
+    for (int64_t i = 0; i < N; ++i) {
+        int64_t j = i;
+        int64_t n = 0;
+        int accepted = 0;
+        while (n < max_trials) {
+            uint32_t x[4];
+            orc_draw(seed, (uint32_t)i, (uint32_t)n, step, filter, ORC_REJECTION, x);
+            if (n > 0) j = orc_uniform_index(x, N);
+            double u = orc_u01_f64(x);
+            double lv = lw[j] < log_vmax ? lw[j] : log_vmax;
+            double delta = lv - log_vmax;
+            n += 1;
+            if (delta == 0.0 || u < orc_exp_f64(delta)) {
+                accepted = 1;
+                break;
+            }
+        }
+        if (!accepted) {
+            j = i;
+            status = ORC_ERR_REJECTION_CAP;
+        }
+        a[i] = (int32_t)j;
+        if (trials) trials[i] = n;
+    }
+    return status;
+}
+
+/* The log-weights of the outcome of partial rejection control for a delivered ancestry c
+ * (the sampler's a, or its permutation by Code 10): out^i = log(w^{c^i} / v^{c^i}) =
+ * lw^{c^i} - min(lw^{c^i}, log v_max), which is 0 unless w^{c^i} > v_max. A zero weight has
+ * v = w = 0 and is given the ratio 1 (log 0), the limit of w / min(w, v_max) as w -> 0. */
+int orc_prc_weights_f32(const float* lw, const int32_t* c, int64_t N, double log_vmax,
+                        float* out) {
+    if (check_n(N) != ORC_OK || !isfinite(log_vmax)) return ORC_ERR_ARG;
+    float lvmax = (float)log_vmax;
+    for (int64_t i = 0; i < N; ++i) {
+        if (c[i] < 0 || c[i] >= N) return ORC_ERR_ARG;
+        float w = lw[c[i]];
+        float lv = w < lvmax ? w : lvmax;
+        out[i] = (w == -INFINITY) ? 0.0f : w - lv;
+    }
+    return ORC_OK;
+}
+
+int orc_prc_weights_f64(const double* lw, const int32_t* c, int64_t N, double log_vmax,
+                        double* out) {
+    if (check_n(N) != ORC_OK || !isfinite(log_vmax)) return ORC_ERR_ARG;
+    for (int64_t i = 0; i < N; ++i) {
+        if (c[i] < 0 || c[i] >= N) return ORC_ERR_ARG;
+        double w = lw[c[i]];
+        double lv = w < log_vmax ? w : log_vmax;
+        out[i] = (w == -INFINITY) ? 0.0 : w - lv;
+    }
+    return ORC_OK;
+}
+
 /* ------------------------------------------------------------------------------------ */
 /* Weights from log-weights, prefix sums (Appendix A primitives, Appendix E)             */
 /* ------------------------------------------------------------------------------------ */
