@@ -75,6 +75,10 @@ def parse_args():
     p.add_argument("--smc", action="store_true",
                    help="full bootstrap SMC loop (Code 1) on the linear-Gaussian model, "
                         "N = 2^20, T = 100, systematic / Metropolis / rejection; one JSON line")
+    p.add_argument("--prc", action="store_true",
+                   help="partial rejection control: time, trials and outcome ESS over v_max")
+    p.add_argument("--metropolis-b", action="store_true",
+                   help="Metropolis time and offspring bias over B (fractions of B*)")
     p.add_argument("--single", default=None,
                    help="profile one call: scheme:dtype[:prec], e.g. metropolis:f32 "
                         "(runs warmup + steps calls with Permute, prints one JSON line)")
@@ -207,31 +211,69 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------------------------------
-# DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) from the ncu
-# captures summarised in profiles/*_ncu.md (N = 2^20; ncu replays with cold caches). They
-# hold for the kernel sources they were taken with: `traffic` is reported only while the
-# sources still hash to SOURCE_HASH, and is null once a kernel has changed.
+# DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) from the ncu launch
+# capture summarised in profiles/bench_step_N2e20_launches.md (N = 2^20; ncu replays with cold
+# caches). Each figure holds for the sources it was taken with: the kernel's .cu file and the
+# headers it includes, hashed; `traffic` is null once any of them has changed.
 # ---------------------------------------------------------------------------------------
-NCU_TRAFFIC = {"SOURCE_HASH": "a0dad40459d1d738",
-               "permute": 8393216, "permute_sorted": 8392960, "metropolis_f64": 12597248,
-               "fused_systematic_f32": 4275456, "fused_multinomial_f64": 8492032,
-               "search_f64": 16784384}
+NCU_TRAFFIC = {  # label: (bytes per launch, source hash)
+               "permute": (8393032, "d843f8cce47d7140"),
+               "metropolis_f64": (12600393, "8d2e64858da167eb"),
+               "metropolis_f32": (8403648, "8d2e64858da167eb"),
+               "permute_sorted": (8393552, "d843f8cce47d7140"),
+               "rejection_f64": (8405175, "8d2e64858da167eb"),
+               "rejection_f32": (4207840, "8d2e64858da167eb"),
+               "fused_stratified_f64": (8487648, "94f993b4fadcc3a9"),
+               "fused_multinomial_f64": (8493344, "94f993b4fadcc3a9"),
+               "fused_systematic_f64": (8481216, "94f993b4fadcc3a9"),
+               "fused_multinomial_f32": (4274304, "94f993b4fadcc3a9"),
+               "fused_stratified_f32": (4261568, "94f993b4fadcc3a9"),
+               "fused_systematic_f32": (4257728, "94f993b4fadcc3a9"),
+               "iscan": (4213467, "d843f8cce47d7140"),
+               "search_f64": (16783744, "f6c13cfce2c52bbc"),
+               "search_f32": (12593152, "f6c13cfce2c52bbc"),
+               "fill": (8482, "d843f8cce47d7140"),
+               "cumoff_to_ancestors": (4199339, "d843f8cce47d7140"),
+               "offspring": (8391205, "d843f8cce47d7140"),
+               "adjacent_difference": (4197444, "d843f8cce47d7140")}
+
+_LABEL_FILES = (("fused_", "fused.cu"), ("permute", "aux.cu"), ("iscan", "aux.cu"),
+                ("fill", "aux.cu"), ("offspring", "aux.cu"), ("adjacent", "aux.cu"),
+                ("cumoff", "aux.cu"), ("metropolis", "mcmc.cu"), ("rejection", "mcmc.cu"),
+                ("prc_", "mcmc.cu"), ("max_", "scan.cu"), ("tile_sum", "scan.cu"),
+                ("emit_", "scan.cu"), ("search_", "scan.cu"))
 
 
-def kernel_sources_hash() -> str:
+def kernel_source_hash(label: str):
+    """Hash of the .cu file that defines the kernel behind a traced label and of every
+    header it includes (transitively)."""
     import hashlib
-    import glob
+    import re
+    src = next((f for pre, f in _LABEL_FILES if label.startswith(pre)), None)
+    if src is None:
+        return None
+    csrc = os.path.join(ROOT, "paper_1301_4019_gb300", "csrc")
+    seen, todo = set(), [os.path.join(csrc, src)]
+    while todo:
+        path = os.path.normpath(todo.pop())
+        if path in seen or not os.path.exists(path):
+            continue
+        seen.add(path)
+        text = open(path, "rb").read()
+        for inc in re.findall(rb'#include "([^"]+)"', text):
+            todo.append(os.path.join(os.path.dirname(path), inc.decode()))
     h = hashlib.sha256()
-    for p in sorted(glob.glob(os.path.join(ROOT, "paper_1301_4019_gb300", "csrc", "*"))):
-        h.update(os.path.basename(p).encode())
-        h.update(open(p, "rb").read())
+    for path in sorted(seen):
+        h.update(os.path.basename(path).encode())
+        h.update(open(path, "rb").read())
     return h.hexdigest()[:16]
 
 
 def ncu_traffic(label: str, N: int):
-    if N != 1 << 20 or kernel_sources_hash() != NCU_TRAFFIC["SOURCE_HASH"]:
+    entry = NCU_TRAFFIC.get(label)
+    if N != 1 << 20 or entry is None or kernel_source_hash(label) != entry[1]:
         return None
-    return NCU_TRAFFIC.get(label)
+    return entry[0]
 
 
 # ---------------------------------------------------------------------------------------
@@ -890,6 +932,42 @@ def run_smc(args):
                          "loglik_sd": round(statistics.stdev(lls), 4),
                          "timing": "host clock; the host reads the ESS every step"})
         st = rs.rs_last_error(h)
+    # many filters: 256 filters of N_f log-uniform on [2^14, 2^18], one graph per run
+    rng = np.random.default_rng(SEED + 256)
+    sizes = np.floor(np.exp(rng.uniform(math.log(2 ** 14), math.log(2 ** 18), 256)))
+    sizes = sizes.astype(np.int64)
+    total = int(sizes.sum())
+    with rs.Handle(total) as hb:
+        for scheme in (rs.SYSTEMATIC, rs.METROPOLIS):
+            bufs = smc.BatchedLgssmBuffers(sizes, np.repeat(np.asarray(y)[:, None], 256, axis=1))
+            cs = torch.cuda.Stream()
+            cs.wait_stream(torch.cuda.current_stream())
+            with torch.cuda.stream(cs):
+                smc.lgssm_batched_launch(hb, bufs, scheme, phi, sx, sy, seed=3, B=64, stream=cs)
+                torch.cuda.synchronize()
+                lls = smc.lgssm_batched_loglik_from(bufs, sy)
+                g = torch.cuda.CUDAGraph()
+                with torch.cuda.graph(g, stream=cs):
+                    smc.lgssm_batched_launch(hb, bufs, scheme, phi, sx, sy, seed=3, B=64,
+                                             stream=cs)
+            torch.cuda.current_stream().wait_stream(cs)
+            g.replay()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(reps):
+                g.replay()
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / reps
+            rows.append({"scheme": SCHEME_NAMES[scheme] + " (256 filters, batched)",
+                         "filters": 256, "particles": total,
+                         "ms_per_filter": round(ms, 3), "us_per_step": round(1e3 * ms / T, 2),
+                         "G_particle_steps_per_s": round(total * T / (ms * 1e-3) / 1e9, 3),
+                         "loglik_mean": round(float(np.mean(lls)), 4),
+                         "loglik_sd": round(float(np.std(lls, ddof=1)), 4)})
+        st2 = rs.rs_last_error(hb)
+    st = st if st != rs.RS_OK else st2
     clk = clocks.stop()
     if st != rs.RS_OK:
         raise SystemExit(f"device status after SMC study: {rs.rs_strerror(st)}")
@@ -897,7 +975,127 @@ def run_smc(args):
                       f"x_t = {phi} x_t-1 + N(0, {sx}^2), y_t = x_t + N(0, {sy}^2); per step: "
                       "resample (compensated binary32, Permute), in-place copy, propagate + "
                       "weight, log-sum of the weights; Metropolis B = 64; one CUDA graph per "
-                      f"filter run, {reps} replays", "clocks": clk, "rows": rows}))
+                      f"filter run, {reps} replays; batched rows: 256 filters, N_f "
+                      "log-uniform on [2^14, 2^18], all on the same observations "
+                      "(log-likelihood mean / sd over the filters)", "clocks": clk,
+                      "rows": rows}))
+
+
+def _median_call_ms(fn, reps, flush):
+    import statistics
+    import torch
+    for k in range(3):
+        fn(k)
+    ts = []
+    for k in range(reps):
+        flush.fill_(float(k))
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        fn(k)
+        e1.record()
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    return statistics.median(ts)
+
+
+def run_prc(args):
+    """Partial rejection control (Section 2.2): per-call time with Permute and the outcome
+    weights, the expected trials per particle 1 + (1 - v_i/v_max)/p with p = mean(v)/v_max
+    (closed form from the weights), and the ESS of the weighted outcome (rs_ess on the
+    outcome log-weights), for v_max at quantiles of the weights; "bound" is v_max = 1, the
+    a-priori bound of the workload, where the call equals the rejection resampler."""
+    import torch
+    import paper_1301_4019_gb300 as rs
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device="cuda")
+    rows = []
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    with rs.Handle(1 << 24) as h:
+        ess = torch.empty(1, dtype=torch.float64, device="cuda")
+        for log2n in (20, 24):
+            N = 1 << log2n
+            out = torch.empty(N, dtype=torch.int32, device="cuda")
+            for y in (2.0, 3.0, 4.0):
+                lw64 = workload.synthetic_logw(N, y, seed=SEED + 500 + log2n, dtype=np.float64)
+                for name, npdt in (("f32", np.float32), ("f64", np.float64)):
+                    lw_np = lw64.astype(npdt)
+                    lw = torch.from_numpy(lw_np).cuda()
+                    lo = torch.empty_like(lw)
+                    for q in ("bound", 0.999, 0.99, 0.9, 0.5):
+                        lvmax = 0.0 if q == "bound" else float(np.quantile(lw_np, q))
+                        ms = _median_call_ms(
+                            lambda k: rs.rs_resample_prc(h, lw, lvmax, seed=SEED, step=k,
+                                                         permute=True, out=out, logw_out=lo),
+                            args.sweep_reps, flush)
+                        rs.rs_ess(h, lo, out=ess)
+                        v = np.minimum(np.exp(lw_np.astype(np.float64) - lvmax), 1.0)
+                        p = v.mean()
+                        rows.append({"log2n": log2n, "y": y, "dtype": name, "v_max": q,
+                                     "log_vmax": round(lvmax, 4), "us": round(ms * 1e3, 2),
+                                     "G_ancestors_per_s": round(N / (ms * 1e-3) / 1e9, 3),
+                                     "expected_trials": round(float(np.mean(1 + (1 - v) / p)),
+                                                              3),
+                                     "outcome_ess_frac": round(float(ess.item()) / N, 4)})
+                    del lw, lo
+        st = rs.rs_last_error(h)
+    clk = clocks.stop()
+    if st != rs.RS_OK:
+        raise SystemExit(f"device status after PRC study: {rs.rs_strerror(st)}")
+    print(json.dumps({"prc": "partial rejection control with Permute and outcome weights; "
+                      f"median of {args.sweep_reps} calls, each after writing "
+                      f"{2 * L2_BYTES // 2**20} MiB (L2 flush); v_max at quantiles of the "
+                      "weights", "clocks": clk, "rows": rows}))
+
+
+def run_metropolis_b(args):
+    """Metropolis resampler over B (Section 4.4, the time / bias trade-off of Eq. B): per-call
+    time with Permute, and the offspring bias mean_i |mean_r o_i - N pi_i| over R repeats
+    against the Monte Carlo noise floor sqrt(mean_i Var(o_i) / R), with the TV bound
+    (1 - beta)^B of Section 2.1 beside it."""
+    import torch
+    import paper_1301_4019_gb300 as rs
+    R = args.precision_reps
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device="cuda")
+    rows = []
+    N = 1 << 20
+    with rs.Handle(N) as h:
+        out = torch.empty(N, dtype=torch.int32, device="cuda")
+        o = torch.empty(N, dtype=torch.int32, device="cuda")
+        for y in (1.0, 2.0, 3.0):
+            beta = workload.beta_estimate(y)
+            Bstar = rs.rs_metropolis_B(0.01, beta)
+            lw64 = workload.synthetic_logw(N, y, seed=SEED + 600, dtype=np.float64)
+            w = np.exp(lw64 - lw64.max())
+            Npi = torch.from_numpy(N * w / math.fsum(w)).cuda()
+            lw = torch.from_numpy(lw64.astype(np.float32)).cuda()
+            for frac in (0.125, 0.25, 0.5, 1.0, 2.0, 4.0):
+                B = max(1, int(round(Bstar * frac)))
+                ms = _median_call_ms(
+                    lambda k: rs.rs_resample(h, rs.METROPOLIS, lw, B=B, seed=SEED, step=k,
+                                             out=out, permute=True),
+                    args.sweep_reps, flush)
+                s1 = torch.zeros(N, dtype=torch.float64, device="cuda")
+                s2 = torch.zeros(N, dtype=torch.float64, device="cuda")
+                for r in range(R):
+                    rs.rs_resample(h, rs.METROPOLIS, lw, B=B, seed=SEED + 9, step=r, out=out)
+                    rs.rs_offspring(h, out, o)
+                    od = o.double()
+                    s1 += od
+                    s2 += od * od
+                mean = s1 / R
+                var = (s2 / R - mean * mean).clamp_min(0) * R / max(R - 1, 1)
+                rows.append({"y": y, "B_star": Bstar, "B": B, "us": round(ms * 1e3, 2),
+                             "tv_bound": float((1 - beta) ** B),
+                             "mean_abs_bias": float((mean - Npi).abs().mean()),
+                             "noise_floor": float(torch.sqrt(var.mean() / R))})
+            del lw, Npi
+        st = rs.rs_last_error(h)
+    if st != rs.RS_OK:
+        raise SystemExit(f"device status after Metropolis B study: {rs.rs_strerror(st)}")
+    print(json.dumps({"metropolis_b": f"N = 2^20, binary32, with Permute; time: median of "
+                      f"{args.sweep_reps} calls after an L2 flush; bias over {R} repeats "
+                      "(step = repeat index); B* from Eq. B with eps = 0.01 and the closed-form "
+                      "beta of the workload", "rows": rows}))
 
 
 def run_single(args):
@@ -940,6 +1138,10 @@ def main():
         run_precision(args)
     elif args.smc:
         run_smc(args)
+    elif args.prc:
+        run_prc(args)
+    elif args.metropolis_b:
+        run_metropolis_b(args)
     elif args.impl == "reference":
         run_reference(args)
     else:

@@ -119,6 +119,23 @@ int rs_resample(rs_handle* h, int scheme, int dtype, const void* logw_dev, int64
                 int32_t B, uint64_t seed, uint64_t step, int32_t* ancestors_dev, int permute,
                 const rs_opts* opts, void* stream);
 
+/* Partial rejection control (Section 2.2, last paragraph): the rejection resampler of Code 3
+ * applied to the clamped weights v^i = min(w^i, v_max) with the bound v_max = exp(log_vmax),
+ * for a v_max chosen below the weights' bound (or where no bound is known). The outcome stays
+ * weighted: logw_out_dev[i] = log(w^{a^i} / v^{a^i}) = max(lw^{a^i} - log_vmax, 0) for the
+ * delivered ancestry a (after Permute when permute = 1), in the dtype of the log-weights
+ * (binary32: log_vmax rounded to binary32 first, as the attempts compare against it).
+ * The draws are those of RS_REJECTION with opts->log_wmax = log_vmax, so the ancestry equals
+ * rs_resample(RS_REJECTION) bit for bit; a weight above v_max is accepted as the clamped
+ * weight, not flagged. A smaller v_max raises the acceptance probability E(v)/v_max and
+ * lowers the trial count. Statuses via rs_last_error: RS_ERR_NONFINITE, RS_ERR_REJECTION_CAP
+ * (max_trials, 1 .. 2^32-1, reached; the particle keeps itself). filter < 2^29 is counter
+ * word 3 as in rs_opts. logw_out_dev (N elements of dtype) must not overlap logw_dev or
+ * ancestors_dev; the caller owns all three buffers. */
+int rs_resample_prc(rs_handle* h, int dtype, const void* logw_dev, int64_t N, double log_vmax,
+                    int64_t max_trials, uint64_t seed, uint64_t step, uint32_t filter,
+                    int32_t* ancestors_dev, void* logw_out_dev, int permute, void* stream);
+
 /* Many independent filters in one launch. F filters in CSR layout: offsets_dev holds F + 1
  * int64 offsets (device), filter f owning the particles offsets[f] .. offsets[f+1]-1 of
  * logw_dev and ancestors_dev; every filter has at most 2^20 particles (empty filters are
@@ -212,6 +229,37 @@ int rs_copy_ancestors(rs_handle* h, float* x_dev, int32_t D, const int32_t* c_de
 int rs_lgssm_step(rs_handle* h, float* x_dev, int64_t N, int init, int accumulate, float phi,
                   float sigma_x, float y, float sigma_y, uint64_t seed, uint64_t step,
                   uint32_t filter, float* logw_dev, void* stream);
+
+/* ---- many independent filters (the CSR layout of rs_resample_batched) ------------------
+ * F filters, filter f owning the particles offsets_dev[f] .. offsets_dev[f+1]-1 (F + 1 int64
+ * on the device, non-decreasing, offsets[F] <= the handle's max_n). Filter f of each call
+ * below computes exactly what the single-filter call computes on its slice with filter = f
+ * (bit for bit), so a batched filter equals F single filters. Particles of a malformed
+ * filter are skipped (and RS_ERR_ARG reported where the call checks indices). F >= 1. */
+
+/* rs_copy_ancestors per filter: c_dev holds every filter's local ancestors (0..N_f-1), as
+ * rs_resample_batched(permute = 1) returns them; row g of x_dev (D floats) becomes row
+ * offsets[f] + c_dev[g] of its filter. */
+int rs_copy_ancestors_batched(rs_handle* h, float* x_dev, int32_t D, const int32_t* c_dev,
+                              const int64_t* offsets_dev, int32_t F, void* stream);
+
+/* rs_lgssm_step per filter: y_dev holds F floats (device), filter f's observation of this
+ * step; particle g of filter f draws its noise from counter (g - offsets[f], 0, step,
+ * f * 8 + 5). Other arguments as rs_lgssm_step. */
+int rs_lgssm_step_batched(rs_handle* h, float* x_dev, const int64_t* offsets_dev, int32_t F,
+                          int init, int accumulate, float phi, float sigma_x,
+                          const float* y_dev, float sigma_y, uint64_t seed, uint64_t step,
+                          float* logw_dev, void* stream);
+
+/* out_dev[f] = log sum_{g in filter f} exp(logw_dev[g]) (F float64, device): the log of the
+ * filter's unnormalised weight total, the ingredient of its marginal-likelihood estimate
+ * (Code 1). Computed with the max-shift of Appendix E: m_f + log sum exp(lw - m_f), the
+ * exponentials in the dtype and the sum in binary64 (not bit-compatible with
+ * rs_cumulative_weights' total). -inf for an empty or all-zero filter; NaN/+inf flag
+ * RS_ERR_NONFINITE. */
+int rs_log_sum_weights_batched(rs_handle* h, int dtype, const void* logw_dev,
+                               const int64_t* offsets_dev, int32_t F, double* out_dev,
+                               void* stream);
 
 /* B* = log(eps) / log(1 - beta) of Eq. (B) (Section 2.1), rounded up: the number of
  * Metropolis steps that bounds the total-variation distance of every chain by eps, for a

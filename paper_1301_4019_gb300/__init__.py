@@ -13,6 +13,7 @@ from __future__ import annotations
 import ctypes as C
 import threading
 
+import numpy as np
 import torch
 
 from . import _build
@@ -40,7 +41,8 @@ EXPORTED = [
     "rs_prepermute", "rs_permute", "rs_metropolis_B", "rs_last_error", "rs_strerror",
     "rs_trace", "rs_trace_count", "rs_trace_label", "rs_systematic_noalloc",
     "rs_resample_batched", "rs_set_launch_mode", "rs_copy_ancestors", "rs_lgssm_step",
-    "rs_ess",
+    "rs_ess", "rs_resample_prc", "rs_copy_ancestors_batched", "rs_lgssm_step_batched",
+    "rs_log_sum_weights_batched",
 ]
 NOALLOC_MAX_N = 1 << 22
 LAUNCH_AUTO, LAUNCH_FUSED, LAUNCH_SEPARATE = 0, 1, 2
@@ -102,6 +104,12 @@ def _declare(lib):
         "rs_set_launch_mode": (I, [P, I]),
         "rs_copy_ancestors": (I, [P, P, I32, P, I64, P]),
         "rs_ess": (I, [P, I, P, I64, P, P]),
+        "rs_copy_ancestors_batched": (I, [P, P, I32, P, P, I32, P]),
+        "rs_lgssm_step_batched": (I, [P, P, P, I32, I, I, C.c_float, C.c_float, P, C.c_float,
+                                      U64, U64, P, P]),
+        "rs_log_sum_weights_batched": (I, [P, I, P, P, I32, P, P]),
+        "rs_resample_prc": (I, [P, I, P, I64, C.c_double, I64, U64, U64, C.c_uint32, P, P, I,
+                                P]),
         "rs_lgssm_step": (I, [P, P, I64, I, I, C.c_float, C.c_float, C.c_float, C.c_float,
                               U64, U64, C.c_uint32, P, P]),
     }
@@ -191,6 +199,27 @@ def rs_resample(h: Handle, scheme: int, logw: torch.Tensor, B: int = 0, seed: in
                               _dev(out, torch.int32, "out"), 1 if permute else 0,
                               C.byref(opts), _stream(stream)), "rs_resample")
     return out
+
+
+def rs_resample_prc(h: Handle, logw: torch.Tensor, log_vmax: float, seed: int = 0,
+                    step: int = 0, permute: bool = False, out: torch.Tensor | None = None,
+                    logw_out: torch.Tensor | None = None, max_trials: int = 1 << 20,
+                    filter: int = 0, stream=None):
+    """Partial rejection control (Section 2.2): rejection resampling from min(w, v_max) with
+    the bound v_max; returns (ancestors, log-weights log(w/v) of the delivered ancestors)."""
+    N = logw.numel()
+    if out is None:
+        out = torch.empty(N, dtype=torch.int32, device=logw.device)
+    if logw_out is None:
+        logw_out = torch.empty_like(logw)
+    _check(load().rs_resample_prc(h.ptr, _dtype_code(logw),
+                                  _dev(logw, (torch.float32, torch.float64), "logw"), N,
+                                  float(log_vmax), int(max_trials),
+                                  int(seed) & 0xFFFFFFFFFFFFFFFF, int(step) & 0xFFFFFFFFFFFFFFFF,
+                                  int(filter), _dev(out, torch.int32, "out"),
+                                  _dev(logw_out, logw.dtype, "logw_out"), 1 if permute else 0,
+                                  _stream(stream)), "rs_resample_prc")
+    return out, logw_out
 
 
 def rs_resample_batched(h: Handle, scheme: int, logw: torch.Tensor, offsets: torch.Tensor,
@@ -343,6 +372,51 @@ def rs_lgssm_step(h: Handle, x: torch.Tensor, init: bool, phi: float, sigma_x: f
                                 _dev(logw, torch.float32, "logw"), _stream(stream)),
            "rs_lgssm_step")
     return logw
+
+
+def rs_copy_ancestors_batched(h: Handle, x: torch.Tensor, c: torch.Tensor,
+                              offsets: torch.Tensor, stream=None) -> torch.Tensor:
+    """In-place copy x[g] <- x[offsets[f] + c[g]] of every filter f (c: local ancestors)."""
+    D = 1 if x.dim() == 1 else int(np.prod(x.shape[1:]))
+    _check(load().rs_copy_ancestors_batched(h.ptr, _dev(x, torch.float32, "x"), D,
+                                            _dev(c, torch.int32, "c"),
+                                            _dev(offsets, torch.int64, "offsets"),
+                                            offsets.numel() - 1, _stream(stream)),
+           "rs_copy_ancestors_batched")
+    return x
+
+
+def rs_lgssm_step_batched(h: Handle, x: torch.Tensor, offsets: torch.Tensor, init: bool,
+                          phi: float, sigma_x: float, y: torch.Tensor, sigma_y: float,
+                          seed: int = 0, step: int = 0, logw: torch.Tensor | None = None,
+                          accumulate: bool = False, stream=None) -> torch.Tensor:
+    """Propagate and weight every filter of the batch (y: this step's observation per
+    filter, float32 on the device)."""
+    if logw is None:
+        logw = torch.empty_like(x)
+    _check(load().rs_lgssm_step_batched(h.ptr, _dev(x, torch.float32, "x"),
+                                        _dev(offsets, torch.int64, "offsets"),
+                                        offsets.numel() - 1, 1 if init else 0,
+                                        1 if accumulate else 0, float(phi), float(sigma_x),
+                                        _dev(y, torch.float32, "y"), float(sigma_y),
+                                        int(seed) & 0xFFFFFFFFFFFFFFFF,
+                                        int(step) & 0xFFFFFFFFFFFFFFFF,
+                                        _dev(logw, torch.float32, "logw"), _stream(stream)),
+           "rs_lgssm_step_batched")
+    return logw
+
+
+def rs_log_sum_weights_batched(h: Handle, logw: torch.Tensor, offsets: torch.Tensor,
+                               out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """log sum exp(logw) of every filter (float64, one per filter)."""
+    F = offsets.numel() - 1
+    if out is None:
+        out = torch.empty(F, dtype=torch.float64, device=logw.device)
+    _check(load().rs_log_sum_weights_batched(h.ptr, _dtype_code(logw), _dev(logw, None, "logw"),
+                                             _dev(offsets, torch.int64, "offsets"), F,
+                                             _dev(out, torch.float64, "out"), _stream(stream)),
+           "rs_log_sum_weights_batched")
+    return out
 
 
 def rs_metropolis_B(eps: float, beta: float) -> int:

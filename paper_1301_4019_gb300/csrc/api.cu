@@ -207,8 +207,8 @@ int rs_resample(rs_handle* h, int scheme, int dtype, const void* logw_dev, int64
       e = rsk::launch_metropolis(h->s, f64, logw_dev, N, B, seed, step, o.filter, a_out, d, s);
       break;
     case RS_REJECTION:
-      e = rsk::launch_rejection(h->s, f64, logw_dev, N, o.log_wmax, o.max_trials, seed, step,
-                                o.filter, a_out, d, s);
+      e = rsk::launch_rejection(h->s, f64, logw_dev, N, o.log_wmax, false, o.max_trials, seed,
+                                step, o.filter, a_out, d, s);
       break;
   }
   if (e == cudaSuccess && permute) {
@@ -217,6 +217,34 @@ int rs_resample(rs_handle* h, int scheme, int dtype, const void* logw_dev, int64
     else
       e = rsk::launch_permute(h->s, a_out, d, N, ancestors_dev, s);
   }
+  end_mark(h, s);
+  return cuda_status(e);
+}
+
+int rs_resample_prc(rs_handle* h, int dtype, const void* logw_dev, int64_t N, double log_vmax,
+                    int64_t max_trials, uint64_t seed, uint64_t step, uint32_t filter,
+                    int32_t* ancestors_dev, void* logw_out_dev, int permute, void* stream) {
+  if (!h || !logw_dev || !ancestors_dev || !logw_out_dev) return RS_ERR_ARG;
+  int st = check_n(h, N);
+  if (st != RS_OK) return st;
+  if (dtype != RS_F32 && dtype != RS_F64) return RS_ERR_ARG;
+  if (permute != 0 && permute != 1) return RS_ERR_ARG;
+  if (!std::isfinite(log_vmax)) return RS_ERR_ARG;
+  if (max_trials < 1 || max_trials > 0xFFFFFFFFLL) return RS_ERR_ARG;
+  if (filter >= (1u << 29)) return RS_ERR_ARG;
+  if (logw_out_dev == logw_dev) return RS_ERR_ARG;
+  if ((st = set_device(h)) != RS_OK) return st;
+  const cudaStream_t s = as_stream(stream);
+  const bool f64 = dtype == RS_F64;
+  int32_t* a_out = permute ? h->s.a_tmp : ancestors_dev;
+  int32_t* d = permute ? h->s.d : nullptr;
+  cudaError_t e = rsk::launch_rejection(h->s, f64, logw_dev, N, log_vmax, true, max_trials,
+                                        seed, step, filter, a_out, d, s);
+  if (e == cudaSuccess && permute)
+    e = rsk::launch_permute(h->s, a_out, d, N, ancestors_dev, s);
+  if (e == cudaSuccess)
+    e = rsk::launch_prc_weights(h->s, f64, logw_dev, ancestors_dev, N, log_vmax, logw_out_dev,
+                                s);
   end_mark(h, s);
   return cuda_status(e);
 }
@@ -382,6 +410,51 @@ int rs_lgssm_step(rs_handle* h, float* x_dev, int64_t N, int init, int accumulat
   const cudaError_t e = rsk::launch_lgssm_step(h->s, x_dev, N, init, accumulate, phi, sigma_x,
                                                y, sigma_y, seed, step, filter, logw_dev,
                                                as_stream(stream));
+  end_mark(h, as_stream(stream));
+  return cuda_status(e);
+}
+
+int rs_copy_ancestors_batched(rs_handle* h, float* x_dev, int32_t D, const int32_t* c_dev,
+                              const int64_t* offsets_dev, int32_t F, void* stream) {
+  if (!h || !x_dev || !c_dev || !offsets_dev || D < 1 || F < 1) return RS_ERR_ARG;
+  if (h->s.max_n > INT64_MAX / D) return RS_ERR_ARG;
+  int st = set_device(h);
+  if (st != RS_OK) return st;
+  const cudaError_t e = rsk::launch_copy_ancestors_batched(h->s, x_dev, D, c_dev, offsets_dev,
+                                                           F, as_stream(stream));
+  end_mark(h, as_stream(stream));
+  return cuda_status(e);
+}
+
+int rs_lgssm_step_batched(rs_handle* h, float* x_dev, const int64_t* offsets_dev, int32_t F,
+                          int init, int accumulate, float phi, float sigma_x,
+                          const float* y_dev, float sigma_y, uint64_t seed, uint64_t step,
+                          float* logw_dev, void* stream) {
+  if (!h || !x_dev || !offsets_dev || !y_dev || !logw_dev || F < 1) return RS_ERR_ARG;
+  if (F > (1 << 29)) return RS_ERR_ARG;  // the filter index must fit counter word 3
+  if ((init != 0 && init != 1) || (accumulate != 0 && accumulate != 1)) return RS_ERR_ARG;
+  if (!(std::fabs(phi) < 1.0f) || !(sigma_x > 0.0f) || !(sigma_y > 0.0f) ||
+      !std::isfinite(sigma_x) || !std::isfinite(sigma_y))
+    return RS_ERR_ARG;
+  int st = set_device(h);
+  if (st != RS_OK) return st;
+  const cudaError_t e = rsk::launch_lgssm_step_batched(h->s, x_dev, offsets_dev, F, init,
+                                                       accumulate, phi, sigma_x, y_dev, sigma_y,
+                                                       seed, step, logw_dev, as_stream(stream));
+  end_mark(h, as_stream(stream));
+  return cuda_status(e);
+}
+
+int rs_log_sum_weights_batched(rs_handle* h, int dtype, const void* logw_dev,
+                               const int64_t* offsets_dev, int32_t F, double* out_dev,
+                               void* stream) {
+  if (!h || !logw_dev || !offsets_dev || !out_dev || F < 1) return RS_ERR_ARG;
+  if (dtype != RS_F32 && dtype != RS_F64) return RS_ERR_ARG;
+  if (F > INT_MAX / 2) return RS_ERR_ARG;
+  int st = set_device(h);
+  if (st != RS_OK) return st;
+  const cudaError_t e = rsk::launch_log_sum_batched(h->s, dtype == RS_F64, logw_dev, offsets_dev,
+                                                    F, out_dev, as_stream(stream));
   end_mark(h, as_stream(stream));
   return cuda_status(e);
 }

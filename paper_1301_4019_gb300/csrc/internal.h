@@ -102,9 +102,11 @@ cudaError_t launch_metropolis(const Scratch& s, bool f64, const void* logw, int6
                               int32_t B, uint64_t seed, uint64_t step, uint32_t filter,
                               int32_t* a_out, int32_t* d_or_null, cudaStream_t st);
 cudaError_t launch_rejection(const Scratch& s, bool f64, const void* logw, int64_t N,
-                             double log_wmax, int64_t max_trials, uint64_t seed,
+                             double log_wmax, bool clamp, int64_t max_trials, uint64_t seed,
                              uint64_t step, uint32_t filter, int32_t* a_out,
                              int32_t* d_or_null, cudaStream_t st);
+cudaError_t launch_prc_weights(const Scratch& s, bool f64, const void* logw, const int32_t* c,
+                               int64_t N, double log_vmax, void* out, cudaStream_t st);
 
 // aux.cu
 cudaError_t launch_fill(int32_t* p, int64_t N, int32_t v, cudaStream_t st);
@@ -128,6 +130,14 @@ cudaError_t launch_ess(const Scratch& s, bool f64, const void* logw, int64_t N, 
                        cudaStream_t st);
 
 // model.cu
+cudaError_t launch_copy_ancestors_batched(const Scratch& s, float* x, int D, const int32_t* c,
+                                          const int64_t* offsets, int F, cudaStream_t st);
+cudaError_t launch_lgssm_step_batched(const Scratch& s, float* x, const int64_t* offsets, int F,
+                                      int init, int accumulate, float phi, float sigma_x,
+                                      const float* y, float sigma_y, uint64_t seed,
+                                      uint64_t step, float* logw, cudaStream_t st);
+cudaError_t launch_log_sum_batched(const Scratch& s, bool f64, const void* logw,
+                                   const int64_t* offsets, int F, double* out, cudaStream_t st);
 cudaError_t launch_copy_ancestors(const Scratch& s, float* x, int D, const int32_t* c, int64_t N,
                                   cudaStream_t st);
 cudaError_t launch_lgssm_step(const Scratch& s, float* x, int64_t N, int init, int accumulate,

@@ -93,9 +93,9 @@ __device__ __forceinline__ void rejection_run(const T* __restrict__ lw, int64_t 
 // warp unless COOP, see metropolis_kernel).
 template <typename T, bool COOP>
 __global__ void __launch_bounds__(kBlock)
-rejection_kernel(const T* __restrict__ lw, int64_t N, double log_wmax, int64_t max_trials,
-                 Keys keys, int32_t* __restrict__ a, int32_t* __restrict__ d, unsigned int* bar,
-                 int* err) {
+rejection_kernel(const T* __restrict__ lw, int64_t N, double log_wmax, bool clamp,
+                 int64_t max_trials, Keys keys, int32_t* __restrict__ a,
+                 int32_t* __restrict__ d, unsigned int* bar, int* err) {
   pdl_wait();
   unsigned int target = 0;
   if constexpr (COOP) {
@@ -107,7 +107,7 @@ rejection_kernel(const T* __restrict__ lw, int64_t N, double log_wmax, int64_t m
     }
     grid_barrier(bar, target, err);
   }
-  const RejBound rb = make_bound(log_wmax);
+  const RejBound rb = make_bound(log_wmax, clamp);
   const int64_t warps = (static_cast<int64_t>(gridDim.x) * blockDim.x) >> 5;
   for (int64_t run = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
        run * kRejRun < N; run += warps) {  // uniform across the warp
@@ -116,6 +116,25 @@ rejection_kernel(const T* __restrict__ lw, int64_t N, double log_wmax, int64_t m
     rejection_run(lw, N, start, end, rb, max_trials, keys, a, d, err);
   }
   if constexpr (COOP) grid_exit(bar, target);
+}
+
+// Log-weights of the outcome of partial rejection control for the delivered ancestry c:
+// out_i = lw[c_i] - min(lw[c_i], log v_max), in the log-weights' type (0 unless the ancestor's
+// weight exceeds v_max; 0 for a zero weight, which only the trial cap can deliver).
+template <typename T>
+__global__ void __launch_bounds__(kBlock)
+prc_weights_kernel(const T* __restrict__ lw, const int32_t* __restrict__ c, int64_t N, T lvmax,
+                   T* __restrict__ out, int* err) {
+  pdl_wait();
+  const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  const int32_t ci = c[i];
+  if (ci < 0 || ci >= N) {
+    flag_error(err, RS_ERR_ARG);
+    return;
+  }
+  const T w = __ldg(lw + ci);
+  out[i] = w > lvmax ? w - lvmax : T(0);
 }
 
 }  // namespace
@@ -142,8 +161,8 @@ cudaError_t launch_metropolis_t(const Scratch& s, const T* lw, int64_t N, int32_
 
 template <typename T>
 cudaError_t launch_rejection_t(const Scratch& s, const T* lw, int64_t N, double log_wmax,
-                               int64_t max_trials, const Keys& keys, int32_t* a_out, int32_t* d,
-                               bool f64, cudaStream_t st) {
+                               bool clamp, int64_t max_trials, const Keys& keys, int32_t* a_out,
+                               int32_t* d, bool f64, cudaStream_t st) {
   unsigned int* bar = &s.glob->bar_count;
   const int64_t runs = (N + kRejRun - 1) / kRejRun;
   const int64_t want = (runs * 32 + kBlock - 1) / kBlock;
@@ -152,7 +171,7 @@ cudaError_t launch_rejection_t(const Scratch& s, const T* lw, int64_t N, double 
     if (cap > 0) {
       trace_mark(s.trace, f64 ? "rejection_f64" : "rejection_f32", st);
       return coop_launch(rejection_kernel<T, true>, static_cast<int>(want < cap ? want : cap),
-                         st, lw, N, log_wmax, max_trials, keys, a_out, d, bar, s.err);
+                         st, lw, N, log_wmax, clamp, max_trials, keys, a_out, d, bar, s.err);
     }
   }
   if (d) {
@@ -162,7 +181,7 @@ cudaError_t launch_rejection_t(const Scratch& s, const T* lw, int64_t N, double 
   }
   trace_mark(s.trace, f64 ? "rejection_f64" : "rejection_f32", st);
   launch_pdl(rejection_kernel<T, false>, static_cast<int>(want), kBlock, st, lw, N, log_wmax,
-             max_trials, keys, a_out, d, bar, s.err);
+             clamp, max_trials, keys, a_out, d, bar, s.err);
   return cudaGetLastError();
 }
 
@@ -178,15 +197,28 @@ cudaError_t launch_metropolis(const Scratch& s, bool f64, const void* logw, int6
 }
 
 cudaError_t launch_rejection(const Scratch& s, bool f64, const void* logw, int64_t N,
-                             double log_wmax, int64_t max_trials, uint64_t seed,
+                             double log_wmax, bool clamp, int64_t max_trials, uint64_t seed,
                              uint64_t step, uint32_t filter, int32_t* a_out, int32_t* d,
                              cudaStream_t st) {
   const Keys keys = make_keys(seed, step, filter, RS_REJECTION);
   if (f64)
-    return launch_rejection_t(s, static_cast<const double*>(logw), N, log_wmax, max_trials,
-                              keys, a_out, d, true, st);
-  return launch_rejection_t(s, static_cast<const float*>(logw), N, log_wmax, max_trials, keys,
-                            a_out, d, false, st);
+    return launch_rejection_t(s, static_cast<const double*>(logw), N, log_wmax, clamp,
+                              max_trials, keys, a_out, d, true, st);
+  return launch_rejection_t(s, static_cast<const float*>(logw), N, log_wmax, clamp, max_trials,
+                            keys, a_out, d, false, st);
+}
+
+cudaError_t launch_prc_weights(const Scratch& s, bool f64, const void* logw, const int32_t* c,
+                               int64_t N, double log_vmax, void* out, cudaStream_t st) {
+  trace_mark(s.trace, "prc_weights", st);
+  const int grid = static_cast<int>((N + kBlock - 1) / kBlock);
+  if (f64)
+    launch_pdl(prc_weights_kernel<double>, grid, kBlock, st, static_cast<const double*>(logw),
+               c, N, log_vmax, static_cast<double*>(out), s.err);
+  else  // the bound in binary32 as the binary32 attempts use it: RN(log v_max)
+    launch_pdl(prc_weights_kernel<float>, grid, kBlock, st, static_cast<const float*>(logw), c,
+               N, static_cast<float>(log_vmax), static_cast<float*>(out), s.err);
+  return cudaGetLastError();
 }
 
 }  // namespace rsk

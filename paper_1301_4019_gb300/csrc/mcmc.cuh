@@ -256,15 +256,20 @@ __device__ __forceinline__ int32_t rejection_one(const double* __restrict__ lw, 
 // ---------------------------------------------------------------------------------------
 constexpr int kRejRun = 32 * 8;  // particles per warp run
 
-struct RejBound {  // the bound log w_max in the forms the attempts compare against
+// The bound log w_max in the forms the attempts compare against. clamp: partial rejection
+// control (Section 2.2): the attempts sample v = min(w, v_max) with v_max = the bound, so a
+// weight above it is the clamped weight v_max (ratio 1, accepted, not an error).
+struct RejBound {
   double lwmax;
   float lwmax_rn;  // RN(log w_max) in binary32 (the binary32 scheme's bound)
   float lwmax_f;   // truncation (the binary64 scheme's filter)
   bool okm;
   long long km;
+  bool clamp;
 };
-__device__ __forceinline__ RejBound make_bound(double log_wmax) {
+__device__ __forceinline__ RejBound make_bound(double log_wmax, bool clamp = false) {
   RejBound r;
+  r.clamp = clamp;
   r.lwmax = log_wmax;
   r.lwmax_rn = static_cast<float>(log_wmax);
   r.okm = f64_to_f32_trunc(log_wmax, r.lwmax_f);
@@ -273,7 +278,7 @@ __device__ __forceinline__ RejBound make_bound(double log_wmax) {
 }
 
 // Attempt s of particle i with its own log-weight lwi; j receives the proposal. Returns true
-// when the proposal is accepted (or above the bound: flagged and accepted).
+// when the proposal is accepted (or above the bound: flagged, unless clamped, and accepted).
 __device__ __forceinline__ bool rejection_attempt(const float* __restrict__ lw, int64_t n,
                                                   const RejBound& rb, const Keys& keys,
                                                   int64_t i, uint32_t s, float lwi, int64_t& j,
@@ -284,7 +289,7 @@ __device__ __forceinline__ bool rejection_attempt(const float* __restrict__ lw, 
   const float lwj = (s == 0) ? lwi : __ldg(lw + j);
   const float delta = lwj - rb.lwmax_rn;
   if (delta > 0.0f) {
-    flag_error(err, RS_ERR_BOUND_VIOLATED);
+    if (!rb.clamp) flag_error(err, RS_ERR_BOUND_VIOLATED);
     return true;
   }
   return delta == 0.0f || u < exp_pinned(delta);
@@ -299,7 +304,7 @@ __device__ __forceinline__ bool rejection_attempt(const double* __restrict__ lw,
   const double lwj = (s == 0) ? lwi : __ldg(lw + j);
   const long long kj = f64_key(lwj);
   if (kj > rb.km && !is_nan(lwj)) {  // above the bound (NaN never compares)
-    flag_error(err, RS_ERR_BOUND_VIOLATED);
+    if (!rb.clamp) flag_error(err, RS_ERR_BOUND_VIOLATED);
     return true;
   }
   if (kj == rb.km) return true;  // ratio exactly 1

@@ -52,6 +52,117 @@ lgssm_step_kernel(float* __restrict__ x, int64_t N, int init, int accumulate, fl
   logw[i] = accumulate ? logw[i] + l : l;
 }
 
+// ---------------------------------------------------------------------------------------
+// Many independent filters (F filters in CSR layout, filter f owning the particles
+// offsets[f] .. offsets[f+1]-1, the layout of rs_resample_batched). Filter f runs the
+// single-filter kernels' arithmetic on its slice with f in the random-number counter, so a
+// batched step equals the single-filter step on that slice with filter = f, bit for bit.
+// ---------------------------------------------------------------------------------------
+
+// Filter holding global position g: the last f with off[f] <= g (off has F + 1 entries).
+// Returns -1 past offsets[F] or for a filter whose offsets are out of order or range.
+__device__ __forceinline__ int locate(const int64_t* __restrict__ off, int F, int64_t cap,
+                                      int64_t g, int64_t& lo, int64_t& n) {
+  if (g >= __ldg(off + F) || g < __ldg(off)) return -1;
+  int a = 0, b = F;  // invariant: off[a] <= g < off[b]
+  while (b - a > 1) {
+    const int mid = (a + b) >> 1;
+    if (__ldg(off + mid) <= g) a = mid; else b = mid;
+  }
+  lo = __ldg(off + a);
+  const int64_t hi = __ldg(off + a + 1);
+  n = hi - lo;
+  if (lo < 0 || hi > cap || n <= 0 || n > 0x7fffffffLL) return -1;
+  return a;
+}
+
+__global__ void __launch_bounds__(kBlock)
+copy_ancestors_batched_kernel(float* __restrict__ x, int D, const int32_t* __restrict__ c,
+                              const int64_t* __restrict__ off, int F, int64_t cap, int* err) {
+  pdl_wait();
+  const int64_t g = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  int64_t lo, n;
+  if (g >= cap || locate(off, F, cap, g, lo, n) < 0) return;
+  const int32_t ci = c[g];
+  if (ci < 0 || ci >= n || c[lo + ci] != ci) {
+    flag_error(err, RS_ERR_ARG);
+    return;
+  }
+  const int64_t src = lo + ci;
+  if (src == g) return;
+  for (int k = 0; k < D; ++k) x[g * D + k] = x[src * D + k];
+}
+
+__global__ void __launch_bounds__(kBlock)
+lgssm_step_batched_kernel(float* __restrict__ x, const int64_t* __restrict__ off, int F,
+                          int64_t cap, int init, int accumulate, float phi, float sigma_x,
+                          float sigma_0, const float* __restrict__ y, float inv_2vy, Keys keys,
+                          float* __restrict__ logw) {
+  pdl_wait();
+  const int64_t g = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  int64_t lo, n;
+  const int f = g < cap ? locate(off, F, cap, g, lo, n) : -1;
+  if (f < 0) return;
+  keys.tag = (static_cast<uint32_t>(f) << 3) | 5u;
+  const float z = normal_draw(keys, g - lo);
+  const float xi = init ? sigma_0 * z : fmaf(phi, x[g], sigma_x * z);
+  x[g] = xi;
+  const float e = __ldg(y + f) - xi;
+  const float l = -(e * e) * inv_2vy;
+  logw[g] = accumulate ? logw[g] + l : l;
+}
+
+// log sum_{i in filter f} exp(lw_i), one CTA per filter: the maximum m, then
+// m + log sum exp(lw_i - m) with the exponentials in the log-weights' type and the sum in
+// binary64 (Appendix E's max-shift). -inf for a filter whose weights are all zero; NaN / +inf
+// log-weights are flagged.
+template <typename T>
+__global__ void __launch_bounds__(kBlock)
+log_sum_batched_kernel(const T* __restrict__ lw, const int64_t* __restrict__ off, int F,
+                       int64_t cap, double* __restrict__ out, int* err) {
+  pdl_wait();
+  const int f = blockIdx.x;
+  const int64_t lo = __ldg(off + f), hi = __ldg(off + f + 1);
+  if (lo < 0 || hi > cap || hi < lo) {
+    if (threadIdx.x == 0) flag_error(err, RS_ERR_ARG);
+    return;
+  }
+  __shared__ double sh[kBlock / 32];
+  T m = neg_inf<T>();
+  bool bad = false;
+  for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+    const T v = __ldg(lw + i);
+    bad |= nonfinite_logw(v);
+    m = v > m ? v : m;
+  }
+  if (__syncthreads_or(bad) && threadIdx.x == 0) flag_error(err, RS_ERR_NONFINITE);
+  double md = static_cast<double>(m);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) md = fmax(md, __shfl_xor_sync(0xffffffffu, md, o));
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = md;
+  __syncthreads();
+  md = sh[0];
+  for (int k = 1; k < kBlock / 32; ++k) md = fmax(md, sh[k]);
+  __syncthreads();
+  if (md == -INFINITY) {
+    if (threadIdx.x == 0) out[f] = -INFINITY;
+    return;
+  }
+  const T mt = static_cast<T>(md);
+  double sum = 0.0;
+  for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x)
+    sum += static_cast<double>(exp(__ldg(lw + i) - mt));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = sum;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int k = 0; k < kBlock / 32; ++k) t += sh[k];
+    out[f] = md + log(t);
+  }
+}
+
 inline int grid_for(int64_t N) { return static_cast<int>((N + kBlock - 1) / kBlock); }
 
 }  // namespace
@@ -72,6 +183,40 @@ cudaError_t launch_lgssm_step(const Scratch& s, float* x, int64_t N, int init, i
   launch_pdl(lgssm_step_kernel, grid_for(N), kBlock, st, x, N, init, accumulate, phi, sigma_x,
                                                    static_cast<float>(s0), y, inv_2vy,
                                                    make_keys(seed, step, filter, 5u), logw);
+  return cudaGetLastError();
+}
+
+// Grids of the batched kernels cover the handle's capacity: offsets[F] is on the device.
+cudaError_t launch_copy_ancestors_batched(const Scratch& s, float* x, int D, const int32_t* c,
+                                          const int64_t* offsets, int F, cudaStream_t st) {
+  trace_mark(s.trace, "copy_ancestors_batched", st);
+  launch_pdl(copy_ancestors_batched_kernel, grid_for(s.max_n), kBlock, st, x, D, c, offsets, F,
+             s.max_n, s.err);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_lgssm_step_batched(const Scratch& s, float* x, const int64_t* offsets, int F,
+                                      int init, int accumulate, float phi, float sigma_x,
+                                      const float* y, float sigma_y, uint64_t seed,
+                                      uint64_t step, float* logw, cudaStream_t st) {
+  const double s0 = static_cast<double>(sigma_x) / std::sqrt(1.0 - static_cast<double>(phi) * phi);
+  const float inv_2vy = static_cast<float>(0.5 / (static_cast<double>(sigma_y) * sigma_y));
+  trace_mark(s.trace, "lgssm_step_batched", st);
+  launch_pdl(lgssm_step_batched_kernel, grid_for(s.max_n), kBlock, st, x, offsets, F, s.max_n,
+             init, accumulate, phi, sigma_x, static_cast<float>(s0), y, inv_2vy,
+             make_keys(seed, step, 0u, 5u), logw);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_log_sum_batched(const Scratch& s, bool f64, const void* logw,
+                                   const int64_t* offsets, int F, double* out, cudaStream_t st) {
+  trace_mark(s.trace, "log_sum_batched", st);
+  if (f64)
+    launch_pdl(log_sum_batched_kernel<double>, F, kBlock, st, static_cast<const double*>(logw),
+               offsets, F, s.max_n, out, s.err);
+  else
+    launch_pdl(log_sum_batched_kernel<float>, F, kBlock, st, static_cast<const float*>(logw),
+               offsets, F, s.max_n, out, s.err);
   return cudaGetLastError();
 }
 

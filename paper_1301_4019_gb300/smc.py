@@ -4,7 +4,8 @@ run in place, Section 2.3), copy in place, propagate and weight, and accumulate 
 mean weight (the filter's estimate of log p(y_t | y_1:t-1), computed with the max-shift of
 Appendix E). Every step runs in the library's kernels; this module only sequences the calls.
 The adaptive form resamples only when the effective sample size falls below a threshold
-(rs_ess) and carries the weights over the other steps.
+(rs_ess) and carries the weights over the other steps. The batched form runs many independent
+filters of different sizes in the CSR layout of rs_resample_batched, one launch per stage.
 """
 from __future__ import annotations
 
@@ -13,8 +14,9 @@ import math
 import numpy as np
 import torch
 
-from . import (PREC_COMPENSATED, Handle, rs_copy_ancestors, rs_cumulative_weights, rs_ess,
-               rs_lgssm_step, rs_resample)
+from . import (PREC_COMPENSATED, Handle, rs_copy_ancestors, rs_copy_ancestors_batched,
+               rs_cumulative_weights, rs_ess, rs_lgssm_step, rs_lgssm_step_batched,
+               rs_log_sum_weights_batched, rs_resample, rs_resample_batched)
 
 
 class LgssmBuffers:
@@ -32,18 +34,19 @@ class LgssmBuffers:
 def lgssm_bootstrap_launch(h: Handle, y, N: int, scheme: int, phi: float, sigma_x: float,
                            sigma_y: float, seed: int = 0, B: int = 64,
                            prec: int = PREC_COMPENSATED, bufs: LgssmBuffers | None = None,
-                           stream=None) -> LgssmBuffers:
+                           stream=None, filter: int = 0) -> LgssmBuffers:
     """Enqueue the whole filter on the stream (no synchronisation); returns the buffers, whose
-    log_total[t] receives log sum_i w_t^i (max-shifted weights, shift added back)."""
+    log_total[t] receives log sum_i w_t^i (max-shifted weights, shift added back). ``filter``
+    is the filter index of every random-number counter."""
     T = len(y)
     b = bufs or LgssmBuffers(N, T)
     for t in range(T):
         if t > 0:
             rs_resample(h, scheme, b.logw, B=B, seed=seed, step=t, out=b.c, permute=True,
-                        prec=prec, log_wmax=0.0, stream=stream)
+                        prec=prec, log_wmax=0.0, filter=filter, stream=stream)
             rs_copy_ancestors(h, b.x, b.c, stream=stream)
         rs_lgssm_step(h, b.x, t == 0, phi, sigma_x, float(y[t]), sigma_y, seed=seed, step=t,
-                      logw=b.logw, stream=stream)
+                      filter=filter, logw=b.logw, stream=stream)
         rs_cumulative_weights(h, b.logw, prec=prec, W=b.W, log_total=b.log_total[t:t + 1],
                               stream=stream)
     return b
@@ -96,3 +99,46 @@ def lgssm_adaptive(h: Handle, y, N: int, scheme: int, phi: float, sigma_x: float
         base = lse
         resample = float(ess.item()) < ess_fraction * N
     return ll, n_res
+
+
+class BatchedLgssmBuffers:
+    """Device buffers of F filters (sizes N_f, CSR offsets) over T steps; Y is T x F."""
+
+    def __init__(self, sizes, Y, device=None):
+        device = device or torch.device("cuda", torch.cuda.current_device())
+        sizes = np.asarray(sizes, dtype=np.int64)
+        total = int(sizes.sum())
+        self.sizes = sizes
+        self.offsets = torch.from_numpy(np.concatenate([[0], np.cumsum(sizes)])).to(device)
+        self.x = torch.empty(total, dtype=torch.float32, device=device)
+        self.logw = torch.empty(total, dtype=torch.float32, device=device)
+        self.c = torch.empty(total, dtype=torch.int32, device=device)
+        self.y = torch.as_tensor(np.asarray(Y, dtype=np.float32), device=device).contiguous()
+        self.log_total = torch.empty(self.y.shape, dtype=torch.float64, device=device)
+
+
+def lgssm_batched_launch(h: Handle, bufs: BatchedLgssmBuffers, scheme: int, phi: float,
+                         sigma_x: float, sigma_y: float, seed: int = 0, B: int = 64,
+                         prec: int = PREC_COMPENSATED, stream=None) -> BatchedLgssmBuffers:
+    """Enqueue F bootstrap filters, filter f observing column f of Y: per step one batched
+    resample with Permute, one in-place copy, one propagate-and-weight and one per-filter
+    log-sum of the weights (log_total[t, f]). Filter f equals lgssm_bootstrap_launch on its
+    own with filter = f in every state it computes (x, weights, ancestors)."""
+    b = bufs
+    for t in range(b.y.shape[0]):
+        if t > 0:
+            rs_resample_batched(h, scheme, b.logw, b.offsets, B=B, seed=seed, step=t, out=b.c,
+                                permute=True, prec=prec, log_wmax=0.0, stream=stream)
+            rs_copy_ancestors_batched(h, b.x, b.c, b.offsets, stream=stream)
+        rs_lgssm_step_batched(h, b.x, b.offsets, t == 0, phi, sigma_x, b.y[t], sigma_y,
+                              seed=seed, step=t, logw=b.logw, stream=stream)
+        rs_log_sum_weights_batched(h, b.logw, b.offsets, out=b.log_total[t], stream=stream)
+    return b
+
+
+def lgssm_batched_loglik_from(bufs: BatchedLgssmBuffers, sigma_y: float) -> np.ndarray:
+    """Per-filter log p-hat(y_1:T) from the per-step log weight totals."""
+    lt = bufs.log_total.cpu().numpy()
+    T = lt.shape[0]
+    return (lt.sum(axis=0) - T * (np.log(bufs.sizes.astype(np.float64))
+                                  + 0.5 * math.log(2 * math.pi * sigma_y ** 2)))

@@ -122,3 +122,73 @@ def test_adaptive_filter_matches_kalman(rs, h, scheme):
     assert 0 < min(n_res) and max(n_res) < T - 1
     sd = lls.std(ddof=1)
     assert abs(lls.mean() - want) < 4 * sd, (lls.mean(), want, sd, n_res)
+
+
+# ---------------------------------------------------------------------------------------
+# many filters at once (the CSR layout of rs_resample_batched)
+# ---------------------------------------------------------------------------------------
+@pytest.mark.parametrize("scheme", [2, 3, 4])
+def test_batched_filter_equals_single_filters(rs, h, scheme):
+    """Every state of filter f of the batched loop (particles, log-weights) equals the
+    single-filter loop run on its own with filter = f, bit for bit; the per-filter log-sums
+    agree with the single filter's scan-based totals to rounding."""
+    from paper_1301_4019_gb300 import smc
+    T = 8
+    sizes = [1000, 4097, 1, 70001, 12289, 2]
+    F = len(sizes)
+    Y = np.stack([workload.lgssm_simulate(T, PHI, SX, SY, seed=40 + f)[1] for f in range(F)],
+                 axis=1)
+    b = smc.BatchedLgssmBuffers(sizes, Y)
+    smc.lgssm_batched_launch(h, b, scheme, PHI, SX, SY, seed=6, B=16)
+    assert rs.rs_last_error(h) == rs.RS_OK
+    x_b, lw_b = b.x.cpu().numpy(), b.logw.cpu().numpy()
+    lt_b = b.log_total.cpu().numpy()
+    off = np.concatenate([[0], np.cumsum(sizes)])
+    for f, N in enumerate(sizes):
+        s = smc.lgssm_bootstrap_launch(h, Y[:, f], N, scheme, PHI, SX, SY, seed=6, B=16,
+                                       filter=f)
+        assert rs.rs_last_error(h) == rs.RS_OK
+        assert np.array_equal(s.x.cpu().numpy(), x_b[off[f]:off[f + 1]]), f
+        assert np.array_equal(s.logw.cpu().numpy(), lw_b[off[f]:off[f + 1]]), f
+        assert np.allclose(s.log_total.cpu().numpy(), lt_b[:, f], rtol=0, atol=2e-5), f
+
+
+def test_log_sum_batched_matches_host(rs, h):
+    rng = np.random.default_rng(3)
+    sizes = [5, 0, 1, 1 << 15, 3000, 70001, 4]
+    off = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+    for dtype in (np.float32, np.float64):
+        lw = (rng.standard_normal(off[-1]) * 4 - 30).astype(dtype)
+        lw[off[2]:off[3]] = -np.inf           # an all-zero filter of one particle
+        lw[off[4]:off[4] + 100] = -np.inf     # zero weights inside a filter
+        out = rs.rs_log_sum_weights_batched(h, torch.from_numpy(lw).to(DEV),
+                                            torch.from_numpy(off).to(DEV)).cpu().numpy()
+        assert rs.rs_last_error(h) == rs.RS_OK
+        for f in range(len(sizes)):
+            seg = lw[off[f]:off[f + 1]].astype(np.float64)
+            if seg.size == 0 or np.all(seg == -np.inf):
+                assert out[f] == -np.inf, f
+                continue
+            m = seg.max()
+            want = m + math.log(math.fsum(np.exp(seg - m)))
+            tol = 4e-7 if dtype == np.float32 else 1e-12
+            assert abs(out[f] - want) <= tol * max(1.0, abs(want)), (dtype, f, out[f], want)
+    bad = torch.tensor([0.0, float("nan")], dtype=torch.float32, device=DEV)
+    rs.rs_log_sum_weights_batched(h, bad, torch.tensor([0, 2], dtype=torch.int64, device=DEV))
+    assert rs.rs_last_error(h) == rs.RS_ERR_NONFINITE
+
+
+def test_batched_loglik_matches_kalman(rs, h):
+    """32 independent filters of N = 2^14 on the same observations: their log-likelihood
+    estimates centre on the Kalman filter's value (4 standard errors of the mean)."""
+    from paper_1301_4019_gb300 import smc
+    T, F, N = 100, 32, 1 << 14
+    _, y = workload.lgssm_simulate(T, PHI, SX, SY, seed=21)
+    want = kalman.lgssm_loglik(y, PHI, SX, SY)
+    b = smc.BatchedLgssmBuffers([N] * F, np.repeat(y[:, None], F, axis=1))
+    smc.lgssm_batched_launch(h, b, 2, PHI, SX, SY, seed=12)
+    lls = smc.lgssm_batched_loglik_from(b, SY)
+    assert rs.rs_last_error(h) == rs.RS_OK
+    sd = lls.std(ddof=1)
+    assert sd < 1.0
+    assert abs(lls.mean() - want) < 4 * sd / math.sqrt(F), (lls.mean(), want, sd)
