@@ -1,0 +1,96 @@
+"""Choice of resampler from measured GB300 times: the decision matrices of the paper's
+Section 4.4 (Figure 6: the fastest scheme over N and the weight skew y) turned into a lookup.
+
+``decision_gb300.json`` holds the median time per call (with Permute, L2 flushed) of every
+scheme over N = 2^10 .. 2^24 and y = 0 .. 4 in binary32 and binary64, as measured by
+``bench.py --sweep`` on a GB300 (Metropolis with B from Eq. B, rejection with the a-priori
+bound). ``choose_scheme`` interpolates those times to the requested (N, y) and returns the
+fastest scheme; with ``unbiased=True`` (the default) the Metropolis resampler, which is biased
+for finite B (Section 2.1), is not considered. The skew can be given as y (the workload's
+observation, log w = -(y - x)^2 / 2 with x ~ N(0, 1)) or as beta = E(w)/w_max (Eq. beta2),
+which for that workload is exp(-y^2/4)/sqrt(2). Host-only, no GPU needed.
+"""
+from __future__ import annotations
+
+import bisect
+import json
+import math
+import os
+
+_TABLE = None
+SCHEME_ORDER = ("multinomial", "stratified", "systematic", "metropolis", "rejection")
+
+
+def _table():
+    global _TABLE
+    if _TABLE is None:
+        with open(os.path.join(os.path.dirname(os.path.abspath(__file__)),
+                               "decision_gb300.json")) as f:
+            _TABLE = json.load(f)
+    return _TABLE
+
+
+def beta_of_y(y: float) -> float:
+    """beta = E(w)/w_max for log w = -(y - x)^2/2, x ~ N(0, 1), w_max = 1 (Section 4.1)."""
+    return math.exp(-y * y / 4.0) / math.sqrt(2.0)
+
+
+def y_of_beta(beta: float) -> float:
+    """Inverse of beta_of_y (0 for beta >= 1/sqrt(2), the flattest weights of the workload)."""
+    if not beta > 0.0:
+        raise ValueError("beta must be positive")
+    r = beta * math.sqrt(2.0)
+    return 0.0 if r >= 1.0 else 2.0 * math.sqrt(-math.log(r))
+
+
+def _interp(xs, ys, x):
+    """Piecewise-linear interpolation, clamped at the ends."""
+    if x <= xs[0]:
+        return ys[0]
+    if x >= xs[-1]:
+        return ys[-1]
+    k = bisect.bisect_right(xs, x) - 1
+    t = (x - xs[k]) / (xs[k + 1] - xs[k])
+    return ys[k] + t * (ys[k + 1] - ys[k])
+
+
+def estimated_us(scheme: str, N: int, y: float, dtype: str = "f32") -> float:
+    """Time per call interpolated from the measured table: linear in N between measured sizes
+    (proportional to N above the largest, flat below the smallest) and linear in y."""
+    if N < 1:
+        raise ValueError("N must be positive")
+    tab = _table()["us"][dtype]
+    ygrid = sorted(float(v) for v in tab)
+    per_y = []
+    for yv in ygrid:
+        row = tab[repr(yv) if repr(yv) in tab else str(yv)]
+        ns = sorted(int(k) for k in row)
+        sizes = [float(1 << n) for n in ns]
+        times = [row[str(n)][scheme] for n in ns]
+        if N > sizes[-1]:
+            per_y.append(times[-1] * N / sizes[-1])
+        else:
+            per_y.append(_interp(sizes, times, float(N)))
+    return _interp(ygrid, per_y, float(y))
+
+
+def choose_scheme(N: int, y: float | None = None, beta: float | None = None,
+                  dtype: str = "f32", unbiased: bool = True):
+    """The fastest resampler for N particles and the given skew. Returns (scheme name,
+    estimated microseconds per call with Permute)."""
+    if (y is None) == (beta is None):
+        raise ValueError("give exactly one of y and beta")
+    if dtype not in ("f32", "f64"):
+        raise ValueError("dtype must be 'f32' or 'f64'")
+    if y is None:
+        y = y_of_beta(beta)
+    if y < 0:
+        raise ValueError("y must be non-negative")
+    best = None
+    for s in SCHEME_ORDER:
+        if unbiased and s == "metropolis":
+            continue
+        t = estimated_us(s, N, y, dtype)
+        if best is None or t < best[1]:
+            best = (s, t)
+    return best
