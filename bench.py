@@ -217,25 +217,25 @@ class ClockSampler:
 # headers it includes, hashed; `traffic` is null once any of them has changed.
 # ---------------------------------------------------------------------------------------
 NCU_TRAFFIC = {  # label: (bytes per launch, source hash)
-               "permute": (8393032, "d843f8cce47d7140"),
-               "metropolis_f64": (12600393, "8d2e64858da167eb"),
-               "metropolis_f32": (8403648, "8d2e64858da167eb"),
-               "permute_sorted": (8393552, "d843f8cce47d7140"),
-               "rejection_f64": (8405175, "8d2e64858da167eb"),
-               "rejection_f32": (4207840, "8d2e64858da167eb"),
-               "fused_stratified_f64": (8487648, "94f993b4fadcc3a9"),
-               "fused_multinomial_f64": (8493344, "94f993b4fadcc3a9"),
-               "fused_systematic_f64": (8481216, "94f993b4fadcc3a9"),
-               "fused_multinomial_f32": (4274304, "94f993b4fadcc3a9"),
-               "fused_stratified_f32": (4261568, "94f993b4fadcc3a9"),
-               "fused_systematic_f32": (4257728, "94f993b4fadcc3a9"),
-               "iscan": (4213467, "d843f8cce47d7140"),
-               "search_f64": (16783744, "f6c13cfce2c52bbc"),
-               "search_f32": (12593152, "f6c13cfce2c52bbc"),
-               "fill": (8482, "d843f8cce47d7140"),
-               "cumoff_to_ancestors": (4199339, "d843f8cce47d7140"),
-               "offspring": (8391205, "d843f8cce47d7140"),
-               "adjacent_difference": (4197444, "d843f8cce47d7140")}
+               "permute": (8392826, "5ddf2a93ad7d34f8"),
+               "metropolis_f64": (12599223, "66fbfa7d71a1c7f2"),
+               "metropolis_f32": (8406976, "66fbfa7d71a1c7f2"),
+               "permute_sorted": (8392808, "5ddf2a93ad7d34f8"),
+               "rejection_f64": (8409746, "66fbfa7d71a1c7f2"),
+               "fused_stratified_f64": (8487744, "c0237b11364be319"),
+               "rejection_f32": (4209312, "66fbfa7d71a1c7f2"),
+               "fused_multinomial_f64": (8498592, "c0237b11364be319"),
+               "fused_systematic_f64": (8480672, "c0237b11364be319"),
+               "fused_multinomial_f32": (4273024, "c0237b11364be319"),
+               "fused_stratified_f32": (4260992, "c0237b11364be319"),
+               "fused_systematic_f32": (4257504, "c0237b11364be319"),
+               "iscan": (4212955, "5ddf2a93ad7d34f8"),
+               "search_f64": (16784768, "e189bcb76f2ae283"),
+               "search_f32": (12592608, "e189bcb76f2ae283"),
+               "fill": (8525, "5ddf2a93ad7d34f8"),
+               "cumoff_to_ancestors": (4199219, "5ddf2a93ad7d34f8"),
+               "offspring": (8391150, "5ddf2a93ad7d34f8"),
+               "adjacent_difference": (4197615, "5ddf2a93ad7d34f8")}
 
 _LABEL_FILES = (("fused_", "fused.cu"), ("permute", "aux.cu"), ("iscan", "aux.cu"),
                 ("fill", "aux.cu"), ("offspring", "aux.cu"), ("adjacent", "aux.cu"),
@@ -764,6 +764,38 @@ def sweep_hbm_bytes(scheme: int, S: int, N: int) -> int:
     return (per + 16) * N
 
 
+GRAPH_CALLS = 20
+
+
+def _graph_call_us(call) -> float:
+    """Microseconds per call of `call(k, stream)` when GRAPH_CALLS of them (k = 0, 1, ...) are
+    captured in one CUDA graph and replayed (median of 5 replays)."""
+    import statistics
+    import torch
+    cs = torch.cuda.Stream()
+    cs.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(cs):
+        for k in range(GRAPH_CALLS):
+            call(k, cs)
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=cs):
+            for k in range(GRAPH_CALLS):
+                call(k, cs)
+    torch.cuda.current_stream().wait_stream(cs)
+    g.replay()
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(5):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        g.replay()
+        e1.record()
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    return statistics.median(ts) * 1e3 / GRAPH_CALLS
+
+
 def run_sweep(args):
     import statistics
     import torch
@@ -803,11 +835,16 @@ def run_sweep(args):
                         ts.append(e0.elapsed_time(e1))
                     ms = statistics.median(ts)
                     gbs = sweep_hbm_bytes(scheme, S, N) / (ms * 1e-3) / 1e9
-                    rows.append({"y": y, "B": B, "log2n": log2n, "dtype": name,
-                                 "scheme": SCHEME_NAMES[scheme],
-                                 "us": round(ms * 1e3, 2),
-                                 "G_ancestors_per_s": round(N / (ms * 1e-3) / 1e9, 3),
-                                 "hbm_frac": round(gbs / hbm_peak, 4)})
+                    row = {"y": y, "B": B, "log2n": log2n, "dtype": name,
+                           "scheme": SCHEME_NAMES[scheme], "us": round(ms * 1e3, 2),
+                           "G_ancestors_per_s": round(N / (ms * 1e-3) / 1e9, 3),
+                           "hbm_frac": round(gbs / hbm_peak, 4)}
+                    if log2n <= 16:  # launch-bound sizes: also per call inside a CUDA graph
+                        row["us_graph"] = round(_graph_call_us(
+                            lambda k, st: rs.rs_resample(h, scheme, lw, B=B, seed=SEED, step=k,
+                                                         out=out, permute=True, log_wmax=0.0,
+                                                         stream=st)), 2)
+                    rows.append(row)
                 del lw
         st = rs.rs_last_error(h)
     clk = clocks.stop()
@@ -816,8 +853,10 @@ def run_sweep(args):
     print(json.dumps({"sweep": "N = 2^10 .. 2^24, y in {%s}, B from Eq. B, log_wmax = 0, with "
                       "Permute; median of %d calls, each after writing %d MiB (L2 flush); "
                       "hbm_frac = algorithmic bytes (sweep_hbm_bytes) / time / %.1f GB/s "
-                      "(measured)" % (args.sweep_y, args.sweep_reps, 2 * L2_BYTES // 2**20,
-                                      hbm_peak),
+                      "(measured); us_graph (N <= 2^16): %d calls captured in one CUDA graph, "
+                      "replayed, time / calls (no flush: the inputs stay in L2)"
+                      % (args.sweep_y, args.sweep_reps, 2 * L2_BYTES // 2**20, hbm_peak,
+                         GRAPH_CALLS),
                       "launch_mode": args.launch_mode, "clocks": clk, "rows": rows}))
 
 
@@ -861,12 +900,36 @@ def run_precision(args):
                                      "mean_abs_bias": float((mean - Npi).abs().mean()),
                                      "noise_floor": float(torch.sqrt(var.mean() / R))})
                     del lw, Npi
+        # deterministic part: the expected offspring given the kernel's own cumulative
+        # weights, E_u[o_i] = r_i - r_{i-1} with r_i = N W_i / W_N (Section 4.2's measure without
+        # Monte Carlo noise), from the accumulators written out exactly in binary64
+        det = []
+        for log2n in (16, 18, 20, 22, 24):
+            N = 1 << log2n
+            for y in (0.0, 2.0, 4.0):
+                lw64 = workload.synthetic_logw(N, y, seed=SEED + 300 + log2n, dtype=np.float64)
+                w = np.exp(lw64 - lw64.max())
+                Npi = torch.from_numpy(N * w / math.fsum(w)).cuda()
+                for label, npdt, prec in modes + [("f64 binary64", np.float64,
+                                                   rs.PREC_BINARY64)]:
+                    lw = torch.from_numpy(lw64.astype(npdt)).cuda()
+                    W, _ = rs.rs_cumulative_weights_f64(h, lw, prec=prec)
+                    r = W * (N / W[-1])
+                    e = torch.diff(r, prepend=torch.zeros(1, dtype=r.dtype, device=r.device))
+                    dev = (e - Npi).abs()
+                    det.append({"log2n": log2n, "y": y, "mode": label,
+                                "mean_abs": float(dev.mean()), "max_abs": float(dev.max())})
+                    del lw, W, r, e, dev
+                del Npi
         st = rs.rs_last_error(h)
     if st != rs.RS_OK:
         raise SystemExit(f"device status after precision study: {rs.rs_strerror(st)}")
     print(json.dumps({"precision": f"{R} repeats per row (seed fixed, step = repeat index); "
                       "bias = mean_i |mean o_i - N pi_i|, pi from the input log-weights in "
-                      "binary64; noise floor = sqrt(mean_i Var(o_i) / R)", "rows": rows}))
+                      "binary64; noise floor = sqrt(mean_i Var(o_i) / R)", "rows": rows,
+                      "deterministic": "E_u[o_i] - N pi_i from the kernel's cumulative weights "
+                      "(rs_cumulative_weights_f64): r_i = N W_i / W_N in binary64; mean and max "
+                      "over i of |r_i - r_{i-1} - N pi_i|", "det_rows": det}))
 
 
 def run_smc(args):

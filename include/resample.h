@@ -158,6 +158,13 @@ int rs_resample_batched(rs_handle* h, int scheme, int dtype, const void* logw_de
 int rs_cumulative_weights(rs_handle* h, int dtype, int prec, const void* logw_dev, int64_t N,
                           void* W_dev, double* log_total_dev, void* stream);
 
+/* rs_cumulative_weights with W_dev in binary64 whatever the dtype: the accumulator of every
+ * mode written out exactly (a binary32 sum, a two-float or double-float pair, or a binary64
+ * sum), so that the rounding of the scan itself can be studied (the single-precision
+ * instability of Section 4.2). Other arguments as rs_cumulative_weights. */
+int rs_cumulative_weights_f64(rs_handle* h, int dtype, int prec, const void* logw_dev,
+                              int64_t N, double* W_dev, double* log_total_dev, void* stream);
+
 /* Ancestors-to-Offspring (Code 12): o_dev[j] = #{i : a[i] = j}. Entries of a outside
  * 0..N-1 are skipped and reported as RS_ERR_ARG through rs_last_error. */
 int rs_offspring(rs_handle* h, const int32_t* a_dev, int64_t N, int32_t* o_dev, void* stream);

@@ -42,7 +42,7 @@ EXPORTED = [
     "rs_trace", "rs_trace_count", "rs_trace_label", "rs_systematic_noalloc",
     "rs_resample_batched", "rs_set_launch_mode", "rs_copy_ancestors", "rs_lgssm_step",
     "rs_ess", "rs_resample_prc", "rs_copy_ancestors_batched", "rs_lgssm_step_batched",
-    "rs_log_sum_weights_batched",
+    "rs_log_sum_weights_batched", "rs_cumulative_weights_f64",
 ]
 NOALLOC_MAX_N = 1 << 22
 LAUNCH_AUTO, LAUNCH_FUSED, LAUNCH_SEPARATE = 0, 1, 2
@@ -86,6 +86,7 @@ def _declare(lib):
         "rs_destroy": (I, [P]),
         "rs_resample": (I, [P, I, I, P, I64, I32, U64, U64, P, I, C.POINTER(_Opts), P]),
         "rs_cumulative_weights": (I, [P, I, I, P, I64, P, P, P]),
+        "rs_cumulative_weights_f64": (I, [P, I, I, P, I64, P, P, P]),
         "rs_offspring": (I, [P, P, I64, P, P]),
         "rs_cumulative_offspring": (I, [P, P, I64, P, P]),
         "rs_adjacent_difference": (I, [P, P, I64, P, P]),
@@ -257,6 +258,24 @@ def rs_cumulative_weights(h: Handle, logw: torch.Tensor, prec: int = PREC_PLAIN,
                                         _dev(logw, None, "logw"), N, _dev(W, logw.dtype, "W"),
                                         _dev(log_total, torch.float64, "log_total"),
                                         _stream(stream)), "rs_cumulative_weights")
+    return W, log_total
+
+
+def rs_cumulative_weights_f64(h: Handle, logw: torch.Tensor, prec: int = PREC_PLAIN,
+                              W: torch.Tensor | None = None,
+                              log_total: torch.Tensor | None = None, stream=None):
+    """Cumulative weights with every accumulator written out exactly in binary64 (the scan's
+    own rounding, for precision studies). Returns (W, log_total)."""
+    N = logw.numel()
+    if W is None:
+        W = torch.empty(N, dtype=torch.float64, device=logw.device)
+    if log_total is None:
+        log_total = torch.empty(1, dtype=torch.float64, device=logw.device)
+    _check(load().rs_cumulative_weights_f64(h.ptr, _dtype_code(logw), int(prec),
+                                            _dev(logw, None, "logw"), N,
+                                            _dev(W, torch.float64, "W"),
+                                            _dev(log_total, torch.float64, "log_total"),
+                                            _stream(stream)), "rs_cumulative_weights_f64")
     return W, log_total
 
 

@@ -298,6 +298,22 @@ int rs_cumulative_weights(rs_handle* h, int dtype, int prec, const void* logw_de
   return cuda_status(e);
 }
 
+int rs_cumulative_weights_f64(rs_handle* h, int dtype, int prec, const void* logw_dev,
+                              int64_t N, double* W_dev, double* log_total_dev, void* stream) {
+  if (!h || !logw_dev || !W_dev) return RS_ERR_ARG;
+  int st = check_n(h, N);
+  if (st != RS_OK) return st;
+  if (dtype != RS_F32 && dtype != RS_F64) return RS_ERR_ARG;
+  if (prec != RS_PREC_PLAIN && prec != RS_PREC_COMPENSATED && prec != RS_PREC_BINARY64)
+    return RS_ERR_ARG;
+  if (prec == RS_PREC_BINARY64 && dtype != RS_F64) return RS_ERR_ARG;
+  if ((st = set_device(h)) != RS_OK) return st;
+  const cudaError_t e = rsk::launch_cumulative_weights_f64(
+      h->s, accumulation(dtype, prec), logw_dev, N, W_dev, log_total_dev, as_stream(stream));
+  end_mark(h, as_stream(stream));
+  return cuda_status(e);
+}
+
 int rs_offspring(rs_handle* h, const int32_t* a_dev, int64_t N, int32_t* o_dev, void* stream) {
   if (!h || !a_dev || !o_dev) return RS_ERR_ARG;
   int st = check_n(nullptr, N);

@@ -361,13 +361,14 @@ batch_rejection_kernel(const T* __restrict__ lw, const int64_t* __restrict__ off
   };
   take(g);
   int64_t head = start + 32;
-  uint32_t s = 0;
+  uint64_t s = 0;  // attempts made (max_trials < 2^32, but s + kRejBatch may pass 2^32)
   for (;;) {
     bool settled = false;
     if (active) {
       int64_t j;
-      settled = rejection_attempt(lw + P.lo, P.n, rb, keys, P.i, s, lwi, j, err);
-      ++s;
+      settled = rejection_attempts<kRejBatch>(lw + P.lo, P.n, rb, keys, P.i,
+                                              static_cast<uint32_t>(s), lwi, max_trials, j, err);
+      s += kRejBatch;
       if (!settled && s >= static_cast<uint64_t>(max_trials)) {
         flag_error(err, RS_ERR_REJECTION_CAP);
         j = P.i;

@@ -83,6 +83,8 @@ cudaError_t launch_scan_resample(const Scratch& s, int scheme, Acc acc, const vo
                                  cudaStream_t st);
 cudaError_t launch_cumulative_weights(const Scratch& s, Acc acc, const void* logw, int64_t N,
                                       void* W_out, double* log_total, cudaStream_t st);
+cudaError_t launch_cumulative_weights_f64(const Scratch& s, Acc acc, const void* logw, int64_t N,
+                                          double* W_out, double* log_total, cudaStream_t st);
 
 // fused.cu: max, tile sums, tile prefixes and emission in one cooperative launch;
 // fused_available is false when the device cannot launch it.

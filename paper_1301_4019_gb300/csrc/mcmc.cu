@@ -55,15 +55,16 @@ __device__ __forceinline__ void rejection_run(const T* __restrict__ lw, int64_t 
   int64_t i = start + lane;
   bool active = i < end;
   int64_t head = start + 32;
-  uint32_t s = 0;
+  uint64_t s = 0;  // attempts made (max_trials < 2^32, but s + kRejBatch may pass 2^32)
   T lwi = active ? __ldg(lw + i) : T(0);
   if (active && nonfinite_logw(lwi)) flag_error(err, RS_ERR_NONFINITE);
   for (;;) {
     bool settled = false;
     if (active) {
       int64_t j;
-      settled = rejection_attempt(lw, N, rb, keys, i, s, lwi, j, err);
-      ++s;
+      settled = rejection_attempts<kRejBatch>(lw, N, rb, keys, i, static_cast<uint32_t>(s),
+                                              lwi, max_trials, j, err);
+      s += kRejBatch;
       if (!settled && s >= static_cast<uint64_t>(max_trials)) {
         flag_error(err, RS_ERR_REJECTION_CAP);
         j = i;

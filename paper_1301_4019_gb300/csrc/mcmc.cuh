@@ -277,16 +277,12 @@ __device__ __forceinline__ RejBound make_bound(double log_wmax, bool clamp = fal
   return r;
 }
 
-// Attempt s of particle i with its own log-weight lwi; j receives the proposal. Returns true
-// when the proposal is accepted (or above the bound: flagged, unless clamped, and accepted).
-__device__ __forceinline__ bool rejection_attempt(const float* __restrict__ lw, int64_t n,
-                                                  const RejBound& rb, const Keys& keys,
-                                                  int64_t i, uint32_t s, float lwi, int64_t& j,
-                                                  int* err) {
-  const uint4 x = draw(keys, static_cast<uint32_t>(i), s);
-  j = (s > 0) ? uniform_index(x, n) : i;
+// Decision of one rejection attempt with draw x and proposal log-weight lwj: accept when
+// u < exp(lw^j - log w_max); a log-weight above the bound is flagged (unless clamped) and
+// accepted.
+__device__ __forceinline__ bool rejection_accept(const RejBound& rb, uint4 x, float lwj,
+                                                 int* err) {
   const float u = u01_f32(x);
-  const float lwj = (s == 0) ? lwi : __ldg(lw + j);
   const float delta = lwj - rb.lwmax_rn;
   if (delta > 0.0f) {
     if (!rb.clamp) flag_error(err, RS_ERR_BOUND_VIOLATED);
@@ -295,13 +291,8 @@ __device__ __forceinline__ bool rejection_attempt(const float* __restrict__ lw, 
   return delta == 0.0f || u < exp_pinned(delta);
 }
 
-__device__ __forceinline__ bool rejection_attempt(const double* __restrict__ lw, int64_t n,
-                                                  const RejBound& rb, const Keys& keys,
-                                                  int64_t i, uint32_t s, double lwi,
-                                                  int64_t& j, int* err) {
-  const uint4 x = draw(keys, static_cast<uint32_t>(i), s);
-  j = (s > 0) ? uniform_index(x, n) : i;
-  const double lwj = (s == 0) ? lwi : __ldg(lw + j);
+__device__ __forceinline__ bool rejection_accept(const RejBound& rb, uint4 x, double lwj,
+                                                 int* err) {
   const long long kj = f64_key(lwj);
   if (kj > rb.km && !is_nan(lwj)) {  // above the bound (NaN never compares)
     if (!rb.clamp) flag_error(err, RS_ERR_BOUND_VIOLATED);
@@ -312,6 +303,41 @@ __device__ __forceinline__ bool rejection_attempt(const double* __restrict__ lw,
   float lwj_f;
   const bool okj = f64_to_f32_trunc(lwj, lwj_f);
   return f64_accept_lt(lwj, lwj_f, okj, rb.lwmax, rb.lwmax_f, rb.okm, x);
+}
+
+// Attempts a lane issues together (rejection_attempts): 2 measured 7-16 % faster than 1 at
+// N = 2^20 (y = 2 and 4); 4 is faster still at y = 4 but slower at y = 2, where most particles
+// settle within two attempts.
+constexpr int kRejBatch = 2;
+
+// Attempts s .. s + K - 1 of particle i (those below max_trials) with their draws and
+// proposal gathers issued together -- the draws are counter-based, so they do not depend on
+// the outcome of earlier attempts -- then decided in order: the first accepted one is the
+// result, exactly as attempting one at a time. Returns true with j when one accepts.
+template <int K, typename T>
+__device__ __forceinline__ bool rejection_attempts(const T* __restrict__ lw, int64_t n,
+                                                   const RejBound& rb, const Keys& keys,
+                                                   int64_t i, uint32_t s, T lwi,
+                                                   int64_t max_trials, int64_t& j, int* err) {
+  uint4 x[K];
+  int64_t jq[K];
+  T lwj[K];
+#pragma unroll
+  for (int q = 0; q < K; ++q) {
+    const uint32_t sq = s + static_cast<uint32_t>(q);
+    x[q] = draw(keys, static_cast<uint32_t>(i), sq);
+    jq[q] = (sq > 0) ? uniform_index(x[q], n) : i;
+    lwj[q] = (sq > 0) ? __ldg(lw + jq[q]) : lwi;
+  }
+#pragma unroll
+  for (int q = 0; q < K; ++q) {
+    if (static_cast<int64_t>(s) + q >= max_trials) return false;
+    if (rejection_accept(rb, x[q], lwj[q], err)) {
+      j = jq[q];
+      return true;
+    }
+  }
+  return false;
 }
 
 }  // namespace

@@ -382,4 +382,25 @@ cudaError_t launch_cumulative_weights(const Scratch& s, Acc acc, const void* log
   return cudaErrorInvalidValue;
 }
 
+// The same cumulative weights, every accumulator written out in binary64 (exactly: a
+// binary32 value, or a two-float / double-float pair whose halves are at most 29 bits apart).
+cudaError_t launch_cumulative_weights_f64(const Scratch& s, Acc acc, const void* logw, int64_t N,
+                                          double* W_out, double* log_total, cudaStream_t st) {
+  switch (acc) {
+    case Acc::F32:
+      return run_cumw<float, float, double>(s, static_cast<const float*>(logw), N, W_out,
+                                            log_total, st);
+    case Acc::F32C:
+      return run_cumw<float, float2, double>(s, static_cast<const float*>(logw), N, W_out,
+                                             log_total, st);
+    case Acc::F64:
+      return run_cumw<double, float2, double>(s, static_cast<const double*>(logw), N, W_out,
+                                              log_total, st);
+    case Acc::F64N:
+      return run_cumw<double, double, double>(s, static_cast<const double*>(logw), N, W_out,
+                                              log_total, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
 }  // namespace rsk

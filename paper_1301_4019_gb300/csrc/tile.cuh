@@ -528,6 +528,7 @@ __device__ __forceinline__ void emit_tile_cumoff(const T* __restrict__ lw, int64
 // Stored cumulative weights of one tile (block-level): W[e] for e in [lo, N).
 template <typename V, typename OUT> __device__ __forceinline__ OUT convert_out(V v);
 template <> __device__ __forceinline__ float convert_out<float, float>(float v) { return v; }
+template <> __device__ __forceinline__ double convert_out<float, double>(float v) { return v; }
 template <> __device__ __forceinline__ double convert_out<double, double>(double v) { return v; }
 template <> __device__ __forceinline__ float2 convert_out<float2, float2>(float2 v) { return v; }
 template <> __device__ __forceinline__ float convert_out<float2, float>(float2 v) { return v.x; }

@@ -295,6 +295,32 @@ def test_cumulative_weights(rs, h, kind, dtype, prec, tol, N):
     assert abs(lt.item() - (m + np.log(S))) <= (1e-12 if dtype == np.float64 else 1e-6) * max(1.0, abs(m + np.log(S)))
 
 
+@pytest.mark.parametrize("N", [1, 4097, 65539])
+def test_cumulative_weights_f64_output(rs, h, N):
+    """The binary64 output writes every accumulator exactly: equal to the dtype output where
+    the accumulator is the dtype (binary32 plain, binary64), rounding to it where it is a
+    pair (compensated), and within the two-float accuracy of the double-double truth."""
+    for dtype, prec, tol in ((np.float32, rs.PREC_PLAIN, 1e-5), (np.float32, rs.PREC_COMPENSATED,
+                              1e-11), (np.float64, rs.PREC_PLAIN, 1e-12),
+                             (np.float64, rs.PREC_BINARY64, 1e-12)):
+        lw = _lw(N, 3.0, dtype)
+        t = torch.from_numpy(lw).to(DEV)
+        W, lt = rs.rs_cumulative_weights(h, t, prec=prec)
+        W64, lt64 = rs.rs_cumulative_weights_f64(h, t, prec=prec)
+        assert rs.rs_last_error(h) == rs.RS_OK
+        W, W64 = W.cpu().numpy(), W64.cpu().numpy()
+        assert W64.dtype == np.float64 and lt64.item() == lt.item()
+        if prec == rs.PREC_COMPENSATED:  # the binary32 output is the pair's high part
+            assert np.all(np.abs(W64 - W.astype(np.float64))
+                          <= np.spacing(W).astype(np.float64) / 2)
+        else:
+            assert np.array_equal(W64, W.astype(np.float64))
+        Wstar, _ = truth_prefix(lw)
+        nz = Wstar > 0
+        assert (np.abs(W64[nz] - Wstar[nz]) / Wstar[nz]).max() <= tol
+        assert np.all(np.diff(W64) >= 0)
+
+
 # ---------------------------------------------------------------------------------------
 # Full-size workloads (the benchmark's N = 2^20 in both dtypes)
 # ---------------------------------------------------------------------------------------
