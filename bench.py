@@ -994,6 +994,24 @@ def run_smc(args):
                          "loglik_mean": round(statistics.mean(lls), 4),
                          "loglik_sd": round(statistics.stdev(lls), 4),
                          "timing": "host clock; the host reads the ESS every step"})
+        for scheme in (rs.SYSTEMATIC, rs.REJECTION):  # the same, decided on the device
+            ag = smc.AdaptiveGraph(h, y, N, scheme, phi, sx, sy, 0.5, seed=1)
+            ag.replay()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(reps):
+                ag.replay()
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / reps
+            ll, n_res = ag.result()
+            rows.append({"scheme": SCHEME_NAMES[scheme] + " (ESS < N/2, one graph)",
+                         "ms_per_filter": round(ms, 3), "us_per_step": round(1e3 * ms / T, 2),
+                         "G_particle_steps_per_s": round(N * T / (ms * 1e-3) / 1e9, 3),
+                         "resamplings": [n_res], "loglik_mean": round(ll, 4),
+                         "timing": "CUDA-graph replay; conditional nodes decide on the device"})
+            del ag
         st = rs.rs_last_error(h)
     # many filters: 256 filters of N_f log-uniform on [2^14, 2^18], one graph per run
     rng = np.random.default_rng(SEED + 256)

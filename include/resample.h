@@ -207,11 +207,14 @@ int rs_set_launch_mode(rs_handle* h, int mode);
 /* Effective sample size of N log-weights: *ess_dev (one binary64 on the device) =
  * (sum_i w_i)^2 / sum_i w_i^2 with w_i = exp(logw_i - max logw) (Appendix E), between 1 and N
  * -- the statistic an adaptive particle filter compares with a threshold to decide whether to
- * resample at a step (Section 4.3). Weights in binary32 (relative error about 2^-23), sums in
- * two-float per CTA and exact across CTAs. NaN/+inf flag RS_ERR_NONFINITE, all weights zero
- * RS_ERR_ZERO_WEIGHT (ess 0). One cooperative launch: RS_ERR_CUDA where the device cannot. */
+ * resample at a step (Section 4.3) -- and, from the same sums, *log_total_dev = max logw +
+ * log sum_i w_i, the log of the weight total (the SMC likelihood increment). Either pointer
+ * may be NULL, not both. Weights in binary32 (relative error about 2^-23), sums in two-float
+ * per CTA and exact across CTAs. NaN/+inf flag RS_ERR_NONFINITE, all weights zero
+ * RS_ERR_ZERO_WEIGHT (ess 0, log total -inf). One cooperative launch: RS_ERR_CUDA where the
+ * device cannot. */
 int rs_ess(rs_handle* h, int dtype, const void* logw_dev, int64_t N, double* ess_dev,
-           void* stream);
+           double* log_total_dev, void* stream);
 
 /* ---- the SMC loop around the resampler (Code 1) ---------------------------------------
  * In-place copy by a permuted ancestry (Section 2.3): x_dev holds N rows of D floats
@@ -236,6 +239,39 @@ int rs_copy_ancestors(rs_handle* h, float* x_dev, int32_t D, const int32_t* c_de
 int rs_lgssm_step(rs_handle* h, float* x_dev, int64_t N, int init, int accumulate, float phi,
                   float sigma_x, float y, float sigma_y, uint64_t seed, uint64_t step,
                   uint32_t filter, float* logw_dev, void* stream);
+
+/* ---- resampling on demand inside a CUDA graph ------------------------------------------
+ * The adaptive filter resamples only when the effective sample size falls below a threshold
+ * (Section 4 mentions the practice). To keep that decision on the device -- the whole filter
+ * one CUDA graph, no host round trip per step -- these calls build a conditional graph node:
+ *
+ * rs_capture_if_below: `stream` must be capturing into a CUDA graph (RS_ERR_ARG otherwise).
+ * Adds to that graph a one-thread kernel that compares *value_dev (binary64, device) with
+ * threshold when the graph runs, and after it an IF node whose body runs only when
+ * *value_dev < threshold. Starts capturing that body on a stream owned by the handle and
+ * returns it in *body_stream: the calls made on *body_stream (with any handle) until
+ * rs_capture_end_if form the body. While the body is captured, this handle's calls use the
+ * one-kernel-per-pass launch structure (RS_LAUNCH_SEPARATE) and no launch of this host
+ * thread carries a programmatic dependency. Not nestable (RS_ERR_ARG).
+ * rs_capture_end_if: ends the body (RS_ERR_ARG unless `stream` is the one given to
+ * rs_capture_if_below) and restores the launch structure; work captured on `stream`
+ * afterwards follows the conditional node. RS_ERR_CUDA if the runtime rejects a step (the
+ * capture is then invalid). */
+int rs_capture_if_below(rs_handle* h, const double* value_dev, double threshold, void* stream,
+                        void** body_stream);
+int rs_capture_end_if(rs_handle* h, void* stream);
+
+/* The adaptive filter's bookkeeping on the device. rs_smc_mark_resampled, after a resampling:
+ * logw_dev[0..N) = 0 (equal weights; the next rs_lgssm_step with accumulate = 1 then gives the
+ * fresh log-weights exactly), *base_dev = log_n, and *count_dev += 1 (int32; may be NULL).
+ * rs_smc_loglik_step, after the log weight total *lse_dev of step t (rs_cumulative_weights):
+ * first = 1: *ll_dev = (*lse_dev - log_n) - c and *count_dev = 0; first = 0:
+ * *ll_dev += (*lse_dev - *base_dev) - c; then *base_dev = *lse_dev. c is the constant dropped
+ * from the log-weights (log(2 pi sigma_y^2)/2 for rs_lgssm_step). All binary64, device. */
+int rs_smc_mark_resampled(rs_handle* h, float* logw_dev, int64_t N, double* base_dev,
+                          double log_n, int32_t* count_dev, void* stream);
+int rs_smc_loglik_step(rs_handle* h, const double* lse_dev, double* base_dev, double* ll_dev,
+                       int32_t* count_dev, double c, double log_n, int first, void* stream);
 
 /* ---- many independent filters (the CSR layout of rs_resample_batched) ------------------
  * F filters, filter f owning the particles offsets_dev[f] .. offsets_dev[f+1]-1 (F + 1 int64

@@ -42,7 +42,8 @@ EXPORTED = [
     "rs_trace", "rs_trace_count", "rs_trace_label", "rs_systematic_noalloc",
     "rs_resample_batched", "rs_set_launch_mode", "rs_copy_ancestors", "rs_lgssm_step",
     "rs_ess", "rs_resample_prc", "rs_copy_ancestors_batched", "rs_lgssm_step_batched",
-    "rs_log_sum_weights_batched", "rs_cumulative_weights_f64",
+    "rs_log_sum_weights_batched", "rs_cumulative_weights_f64", "rs_capture_if_below",
+    "rs_capture_end_if", "rs_smc_mark_resampled", "rs_smc_loglik_step",
 ]
 NOALLOC_MAX_N = 1 << 22
 LAUNCH_AUTO, LAUNCH_FUSED, LAUNCH_SEPARATE = 0, 1, 2
@@ -104,11 +105,15 @@ def _declare(lib):
                                     C.POINTER(_Opts), P]),
         "rs_set_launch_mode": (I, [P, I]),
         "rs_copy_ancestors": (I, [P, P, I32, P, I64, P]),
-        "rs_ess": (I, [P, I, P, I64, P, P]),
+        "rs_ess": (I, [P, I, P, I64, P, P, P]),
         "rs_copy_ancestors_batched": (I, [P, P, I32, P, P, I32, P]),
         "rs_lgssm_step_batched": (I, [P, P, P, I32, I, I, C.c_float, C.c_float, P, C.c_float,
                                       U64, U64, P, P]),
         "rs_log_sum_weights_batched": (I, [P, I, P, P, I32, P, P]),
+        "rs_capture_if_below": (I, [P, P, C.c_double, P, C.POINTER(P)]),
+        "rs_capture_end_if": (I, [P, P]),
+        "rs_smc_mark_resampled": (I, [P, P, I64, P, C.c_double, P, P]),
+        "rs_smc_loglik_step": (I, [P, P, P, P, P, C.c_double, C.c_double, I, P]),
         "rs_resample_prc": (I, [P, I, P, I64, C.c_double, I64, U64, U64, C.c_uint32, P, P, I,
                                 P]),
         "rs_lgssm_step": (I, [P, P, I64, I, I, C.c_float, C.c_float, C.c_float, C.c_float,
@@ -353,13 +358,14 @@ def rs_set_launch_mode(h: Handle, mode: int) -> None:
 
 
 def rs_ess(h: Handle, logw: torch.Tensor, out: torch.Tensor | None = None,
-           stream=None) -> torch.Tensor:
+           log_total: torch.Tensor | None = None, stream=None) -> torch.Tensor:
     """Effective sample size (sum w)^2 / sum w^2 of the max-shifted weights (one float64 on
-    the device)."""
+    the device); with ``log_total``, also max logw + log sum w there."""
     if out is None:
         out = torch.empty(1, dtype=torch.float64, device=logw.device)
+    lt = _dev(log_total, torch.float64, "log_total") if log_total is not None else None
     _check(load().rs_ess(h.ptr, _dtype_code(logw), _dev(logw, None, "logw"), logw.numel(),
-                         _dev(out, torch.float64, "ess"), _stream(stream)), "rs_ess")
+                         _dev(out, torch.float64, "ess"), lt, _stream(stream)), "rs_ess")
     return out
 
 
@@ -436,6 +442,42 @@ def rs_log_sum_weights_batched(h: Handle, logw: torch.Tensor, offsets: torch.Ten
                                              _dev(out, torch.float64, "out"), _stream(stream)),
            "rs_log_sum_weights_batched")
     return out
+
+
+def rs_capture_if_below(h: Handle, value: torch.Tensor, threshold: float, stream=None):
+    """Inside a CUDA graph capture on `stream`: open a conditional body that runs when
+    value[0] < threshold on the device; returns the stream to capture the body on."""
+    body = C.c_void_p()
+    _check(load().rs_capture_if_below(h.ptr, _dev(value, torch.float64, "value"),
+                                      float(threshold), _stream(stream), C.byref(body)),
+           "rs_capture_if_below")
+    return torch.cuda.ExternalStream(body.value)
+
+
+def rs_capture_end_if(h: Handle, stream=None) -> None:
+    _check(load().rs_capture_end_if(h.ptr, _stream(stream)), "rs_capture_end_if")
+
+
+def rs_smc_mark_resampled(h: Handle, logw: torch.Tensor, base: torch.Tensor, log_n: float,
+                          count: torch.Tensor | None = None, stream=None) -> None:
+    """After a resampling: log-weights 0, likelihood base log N, resampling count + 1."""
+    _check(load().rs_smc_mark_resampled(h.ptr, _dev(logw, torch.float32, "logw"), logw.numel(),
+                                        _dev(base, torch.float64, "base"), float(log_n),
+                                        _dev(count, torch.int32, "count")
+                                        if count is not None else None, _stream(stream)),
+           "rs_smc_mark_resampled")
+
+
+def rs_smc_loglik_step(h: Handle, lse: torch.Tensor, base: torch.Tensor, ll: torch.Tensor,
+                       c: float, log_n: float, first: bool, count: torch.Tensor | None = None,
+                       stream=None) -> None:
+    """ll += (lse - base) - c, base = lse (first step: ll = (lse - log N) - c, count = 0)."""
+    _check(load().rs_smc_loglik_step(h.ptr, _dev(lse, torch.float64, "lse"),
+                                     _dev(base, torch.float64, "base"),
+                                     _dev(ll, torch.float64, "ll"),
+                                     _dev(count, torch.int32, "count")
+                                     if count is not None else None, float(c), float(log_n),
+                                     1 if first else 0, _stream(stream)), "rs_smc_loglik_step")
 
 
 def rs_metropolis_B(eps: float, beta: float) -> int:

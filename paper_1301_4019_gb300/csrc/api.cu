@@ -14,6 +14,11 @@ struct rs_handle {
   int device;
   rsk::Scratch s;
   rsk::Trace trace;
+  // conditional capture (rs_capture_if_below .. rs_capture_end_if)
+  cudaStream_t body_stream;
+  cudaStream_t cap_stream;
+  bool cap_active;
+  int saved_mode;
 };
 
 namespace {
@@ -119,7 +124,9 @@ int rs_create(rs_handle** out, int64_t max_n, int device) {
     ok &= cudaMemcpy(s.err, &none, sizeof(int), cudaMemcpyHostToDevice) == cudaSuccess;
     ok &= cudaDeviceSynchronize() == cudaSuccess;
   }
+  if (ok) ok &= cudaStreamCreateWithFlags(&h->body_stream, cudaStreamNonBlocking) == cudaSuccess;
   if (!ok) {
+    if (h->body_stream) cudaStreamDestroy(h->body_stream);
     free_scratch(s);
     delete h;
     return RS_ERR_CUDA;
@@ -132,6 +139,7 @@ int rs_destroy(rs_handle* h) {
   if (!h) return RS_OK;
   const int st = set_device(h);
   clear_trace(h);
+  if (h->body_stream) cudaStreamDestroy(h->body_stream);
   free_scratch(h->s);
   delete h;
   return st;
@@ -388,14 +396,14 @@ int rs_set_launch_mode(rs_handle* h, int mode) {
 }
 
 int rs_ess(rs_handle* h, int dtype, const void* logw_dev, int64_t N, double* ess_dev,
-           void* stream) {
-  if (!h || !logw_dev || !ess_dev) return RS_ERR_ARG;
+           double* log_total_dev, void* stream) {
+  if (!h || !logw_dev || (!ess_dev && !log_total_dev)) return RS_ERR_ARG;
   int st = check_n(h, N);
   if (st != RS_OK) return st;
   if (dtype != RS_F32 && dtype != RS_F64) return RS_ERR_ARG;
   if ((st = set_device(h)) != RS_OK) return st;
   const cudaError_t e = rsk::launch_ess(h->s, dtype == RS_F64, logw_dev, N, ess_dev,
-                                        as_stream(stream));
+                                        log_total_dev, as_stream(stream));
   end_mark(h, as_stream(stream));
   return cuda_status(e);
 }
@@ -471,6 +479,84 @@ int rs_log_sum_weights_batched(rs_handle* h, int dtype, const void* logw_dev,
   if (st != RS_OK) return st;
   const cudaError_t e = rsk::launch_log_sum_batched(h->s, dtype == RS_F64, logw_dev, offsets_dev,
                                                     F, out_dev, as_stream(stream));
+  end_mark(h, as_stream(stream));
+  return cuda_status(e);
+}
+
+int rs_capture_if_below(rs_handle* h, const double* value_dev, double threshold, void* stream,
+                        void** body_stream) {
+  if (!h || !value_dev || !body_stream || !stream || h->cap_active) return RS_ERR_ARG;
+  int st = set_device(h);
+  if (st != RS_OK) return st;
+  const cudaStream_t s = as_stream(stream);
+  cudaStreamCaptureStatus status = cudaStreamCaptureStatusNone;
+  cudaGraph_t graph = nullptr;
+  const cudaGraphNode_t* deps = nullptr;
+  const cudaGraphEdgeData* edata = nullptr;
+  size_t nd = 0;
+  if (cudaStreamGetCaptureInfo(s, &status, nullptr, &graph, &deps, &edata, &nd) != cudaSuccess)
+    return RS_ERR_CUDA;
+  if (status != cudaStreamCaptureStatusActive) return RS_ERR_ARG;
+  cudaGraphConditionalHandle hnd;
+  if (cudaGraphConditionalHandleCreate(&hnd, graph, 0, cudaGraphCondAssignDefault) != cudaSuccess)
+    return RS_ERR_CUDA;
+  if (rsk::launch_set_if_below(hnd, value_dev, threshold, s) != cudaSuccess) return RS_ERR_CUDA;
+  if (cudaStreamGetCaptureInfo(s, &status, nullptr, &graph, &deps, &edata, &nd) != cudaSuccess)
+    return RS_ERR_CUDA;
+  cudaGraphNodeParams p = {};
+  p.type = cudaGraphNodeTypeConditional;
+  p.conditional.handle = hnd;
+  p.conditional.type = cudaGraphCondTypeIf;
+  p.conditional.size = 1;
+  cudaGraphNode_t node;
+  if (cudaGraphAddNode(&node, graph, deps, edata, nd, &p) != cudaSuccess) return RS_ERR_CUDA;
+  if (cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1,
+                                          cudaStreamSetCaptureDependencies) != cudaSuccess)
+    return RS_ERR_CUDA;
+  if (cudaStreamBeginCaptureToGraph(h->body_stream, p.conditional.phGraph_out[0], nullptr,
+                                    nullptr, 0, cudaStreamCaptureModeRelaxed) != cudaSuccess)
+    return RS_ERR_CUDA;
+  h->cap_active = true;
+  h->cap_stream = s;
+  h->saved_mode = h->s.launch_mode;
+  h->s.launch_mode = RS_LAUNCH_SEPARATE;  // no cooperative launches inside the body
+  rsk::pdl_disabled() = true;
+  *body_stream = h->body_stream;
+  return RS_OK;
+}
+
+int rs_capture_end_if(rs_handle* h, void* stream) {
+  if (!h || !h->cap_active || as_stream(stream) != h->cap_stream) return RS_ERR_ARG;
+  cudaGraph_t body = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(h->body_stream, &body);
+  h->cap_active = false;
+  h->s.launch_mode = h->saved_mode;
+  rsk::pdl_disabled() = false;
+  if (e != cudaSuccess) return RS_ERR_CUDA;
+  // a plain kernel node after the conditional node: the next launch on the stream may carry a
+  // programmatic dependency, which must follow a kernel
+  return cuda_status(rsk::launch_noop(as_stream(stream)));
+}
+
+int rs_smc_mark_resampled(rs_handle* h, float* logw_dev, int64_t N, double* base_dev,
+                          double log_n, int32_t* count_dev, void* stream) {
+  if (!h || !logw_dev || !base_dev) return RS_ERR_ARG;
+  int st = check_n(nullptr, N);
+  if (st != RS_OK) return st;
+  if ((st = set_device(h)) != RS_OK) return st;
+  const cudaError_t e = rsk::launch_mark_resampled(h->s, logw_dev, N, base_dev, log_n, count_dev,
+                                                   as_stream(stream));
+  end_mark(h, as_stream(stream));
+  return cuda_status(e);
+}
+
+int rs_smc_loglik_step(rs_handle* h, const double* lse_dev, double* base_dev, double* ll_dev,
+                       int32_t* count_dev, double c, double log_n, int first, void* stream) {
+  if (!h || !lse_dev || !base_dev || !ll_dev || (first != 0 && first != 1)) return RS_ERR_ARG;
+  int st = set_device(h);
+  if (st != RS_OK) return st;
+  const cudaError_t e = rsk::launch_loglik_step(h->s, lse_dev, base_dev, ll_dev, count_dev, c,
+                                                log_n, first, as_stream(stream));
   end_mark(h, as_stream(stream));
   return cuda_status(e);
 }

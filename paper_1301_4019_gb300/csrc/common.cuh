@@ -151,6 +151,13 @@ __device__ __forceinline__ double exp_pinned(double x) {
 // ---------------------------------------------------------------------------------------
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 
+// Set (per host thread) while a conditional graph body is being captured: launches then go
+// without the programmatic-serialization attribute (rs_capture_if_below).
+inline bool& pdl_disabled() {
+  static thread_local bool off = false;
+  return off;
+}
+
 template <typename... KArgs, typename... Args>
 inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, cudaStream_t st,
                               Args&&... args) {
@@ -163,7 +170,7 @@ inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, c
   attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
   attr[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
-  cfg.numAttrs = 1;
+  cfg.numAttrs = pdl_disabled() ? 0 : 1;
   return cudaLaunchKernelEx(&cfg, kernel, static_cast<Args&&>(args)...);
 }
 

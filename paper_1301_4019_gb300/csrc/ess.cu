@@ -2,7 +2,8 @@
 // weights w_i = exp(lw_i - max lw) of Appendix E, the quantity that decides when an adaptive
 // particle filter resamples (Section 4.3 discusses resampling every step against on demand).
 // One cooperative launch: maximum -> grid barrier -> per-CTA sums of w and w^2 -> grid
-// barrier -> CTA 0 adds the per-CTA totals exactly (128-bit fixed point) and divides.
+// barrier -> CTA 0 adds the per-CTA totals exactly (128-bit fixed point, all its threads) and
+// divides; the same sums give the log of the weight total, M + log sum w.
 #include <cfloat>
 
 #include "common.cuh"
@@ -35,12 +36,36 @@ __device__ __forceinline__ float ess_weight(double x, float, float2 M2) {
   return is_neg_inf(x) ? 0.0f : exp_pinned(add22_accurate(split_f64(x), neg2(M2)).x);
 }
 
+// A u128 written by another CTA of the same launch (before a grid barrier), read through L2.
+__device__ __forceinline__ u128 ld_u128_cg(const u128* p) {
+  const unsigned long long* q = reinterpret_cast<const unsigned long long*>(p);
+  return static_cast<u128>(__ldcg(q)) | (static_cast<u128>(__ldcg(q + 1)) << 64);
+}
+
+// Sum over the CTA of one u128 per thread (exact), returned to every thread.
+__device__ __forceinline__ u128 block_sum_u128(u128 v, u128* sh) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const uint64_t hi = __shfl_xor_sync(0xffffffffu, static_cast<uint64_t>(v >> 64), o);
+    const uint64_t lo = __shfl_xor_sync(0xffffffffu, static_cast<uint64_t>(v), o);
+    v += (static_cast<u128>(hi) << 64) | lo;
+  }
+  __syncthreads();
+  if (lane == 0) sh[warp] = v;
+  __syncthreads();
+  u128 t = 0;
+  for (int k = 0; k < kWarps; ++k) t += sh[k];
+  return t;
+}
+
 template <typename T>
 __global__ void __launch_bounds__(kBlock)
 ess_kernel(const T* __restrict__ lw, int64_t N, double* blockmax, u128* agg, unsigned int* bar,
-           double* ess_out, int* err) {
+           double* ess_out, double* log_total_out, int* err) {
   __shared__ long long sh_key[kWarps];
   __shared__ float2 sh_s[kWarps][2];
+  __shared__ u128 sh_u[kWarps];
   unsigned int target = 0;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
@@ -118,18 +143,24 @@ ess_kernel(const T* __restrict__ lw, int64_t N, double* blockmax, u128* agg, uns
     agg[2 * blockIdx.x + 1] = a2;
   }
   grid_barrier(bar, target, err);
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
+  if (blockIdx.x == 0) {  // the per-CTA totals, added by the whole CTA (exact, any order)
     u128 a1 = 0, a2 = 0;
-    for (int b = 0; b < static_cast<int>(gridDim.x); ++b) {
-      a1 += agg[2 * b];
-      a2 += agg[2 * b + 1];
+    for (int b = threadIdx.x; b < static_cast<int>(gridDim.x); b += kBlock) {
+      a1 += ld_u128_cg(agg + 2 * b);
+      a2 += ld_u128_cg(agg + 2 * b + 1);
     }
-    const double S1 = fixed_to_double(a1, kFixFrac), S2 = fixed_to_double(a2, kFixFrac);
-    if (zero || !(S2 > 0.0)) {
-      flag_error(err, RS_ERR_ZERO_WEIGHT);
-      *ess_out = 0.0;
-    } else {
-      *ess_out = __ddiv_rn(__dmul_rn(S1, S1), S2);
+    a1 = block_sum_u128(a1, sh_u);
+    a2 = block_sum_u128(a2, sh_u);
+    if (threadIdx.x == 0) {
+      const double S1 = fixed_to_double(a1, kFixFrac), S2 = fixed_to_double(a2, kFixFrac);
+      if (zero || !(S2 > 0.0)) {
+        flag_error(err, RS_ERR_ZERO_WEIGHT);
+        if (ess_out) *ess_out = 0.0;
+        if (log_total_out) *log_total_out = -static_cast<double>(INFINITY);
+      } else {
+        if (ess_out) *ess_out = __ddiv_rn(__dmul_rn(S1, S1), S2);
+        if (log_total_out) *log_total_out = M + log(S1);
+      }
     }
   }
   grid_exit(bar, target);
@@ -138,7 +169,7 @@ ess_kernel(const T* __restrict__ lw, int64_t N, double* blockmax, u128* agg, uns
 }  // namespace
 
 cudaError_t launch_ess(const Scratch& s, bool f64, const void* logw, int64_t N, double* ess,
-                       cudaStream_t st) {
+                       double* log_total, cudaStream_t st) {
   const void* k = f64 ? reinterpret_cast<const void*>(ess_kernel<double>)
                       : reinterpret_cast<const void*>(ess_kernel<float>);
   int cap = coop_capacity(k);
@@ -151,9 +182,9 @@ cudaError_t launch_ess(const Scratch& s, bool f64, const void* logw, int64_t N, 
   trace_mark(s.trace, f64 ? "ess_f64" : "ess_f32", st);
   if (f64)
     return coop_launch(ess_kernel<double>, grid, st, static_cast<const double*>(logw), N,
-                       s.blockmax, agg, &s.glob->bar_count, ess, s.err);
+                       s.blockmax, agg, &s.glob->bar_count, ess, log_total, s.err);
   return coop_launch(ess_kernel<float>, grid, st, static_cast<const float*>(logw), N,
-                     s.blockmax, agg, &s.glob->bar_count, ess, s.err);
+                     s.blockmax, agg, &s.glob->bar_count, ess, log_total, s.err);
 }
 
 }  // namespace rsk

@@ -129,7 +129,7 @@ cudaError_t launch_cumoff_to_ancestors(const Scratch& s, const int32_t* O, int64
 
 // ess.cu (cooperative; cudaErrorNotSupported without cooperative launches)
 cudaError_t launch_ess(const Scratch& s, bool f64, const void* logw, int64_t N, double* ess,
-                       cudaStream_t st);
+                       double* log_total, cudaStream_t st);
 
 // model.cu
 cudaError_t launch_copy_ancestors_batched(const Scratch& s, float* x, int D, const int32_t* c,
@@ -138,6 +138,14 @@ cudaError_t launch_lgssm_step_batched(const Scratch& s, float* x, const int64_t*
                                       int init, int accumulate, float phi, float sigma_x,
                                       const float* y, float sigma_y, uint64_t seed,
                                       uint64_t step, float* logw, cudaStream_t st);
+cudaError_t launch_set_if_below(cudaGraphConditionalHandle hnd, const double* v, double thr,
+                                cudaStream_t st);
+cudaError_t launch_noop(cudaStream_t st);
+cudaError_t launch_mark_resampled(const Scratch& s, float* logw, int64_t N, double* base,
+                                  double log_n, int32_t* count, cudaStream_t st);
+cudaError_t launch_loglik_step(const Scratch& s, const double* lse, double* base, double* ll,
+                               int32_t* count, double c, double log_n, int first,
+                               cudaStream_t st);
 cudaError_t launch_log_sum_batched(const Scratch& s, bool f64, const void* logw,
                                    const int64_t* offsets, int F, double* out, cudaStream_t st);
 cudaError_t launch_copy_ancestors(const Scratch& s, float* x, int D, const int32_t* c, int64_t N,

@@ -163,9 +163,74 @@ log_sum_batched_kernel(const T* __restrict__ lw, const int64_t* __restrict__ off
   }
 }
 
+// ---------------------------------------------------------------------------------------
+// Resampling on demand inside a CUDA graph: the decision, and the bookkeeping of the
+// adaptive filter's likelihood, on the device.
+// ---------------------------------------------------------------------------------------
+__global__ void set_if_below_kernel(cudaGraphConditionalHandle hnd, const double* v, double thr) {
+  cudaGraphSetConditional(hnd, *v < thr ? 1u : 0u);
+}
+
+__global__ void noop_kernel() {}
+
+// After a resampling: equal weights (log w = 0), likelihood base log N, one more resampling.
+__global__ void __launch_bounds__(kBlock)
+mark_resampled_kernel(float* __restrict__ logw, int64_t N, double* base, double log_n,
+                      int32_t* count) {
+  pdl_wait();
+  const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i < N) logw[i] = 0.0f;
+  if (i == 0) {
+    *base = log_n;
+    if (count) *count += 1;
+  }
+}
+
+// The adaptive filter's likelihood: ll += (log W_t - base) - c, base = log W_t (first step:
+// ll = (log W_0 - log N) - c and the resampling count reset).
+__global__ void loglik_step_kernel(const double* lse, double* base, double* ll, int32_t* count,
+                                   double c, double log_n, int first) {
+  pdl_wait();
+  if (blockIdx.x != 0 || threadIdx.x != 0) return;
+  const double l = *lse;
+  if (first) {
+    *ll = (l - log_n) - c;
+    if (count) *count = 0;
+  } else {
+    *ll = *ll + ((l - *base) - c);
+  }
+  *base = l;
+}
+
 inline int grid_for(int64_t N) { return static_cast<int>((N + kBlock - 1) / kBlock); }
 
 }  // namespace
+
+cudaError_t launch_set_if_below(cudaGraphConditionalHandle hnd, const double* v, double thr,
+                                cudaStream_t st) {
+  set_if_below_kernel<<<1, 1, 0, st>>>(hnd, v, thr);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_noop(cudaStream_t st) {
+  noop_kernel<<<1, 1, 0, st>>>();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_mark_resampled(const Scratch& s, float* logw, int64_t N, double* base,
+                                  double log_n, int32_t* count, cudaStream_t st) {
+  trace_mark(s.trace, "mark_resampled", st);
+  launch_pdl(mark_resampled_kernel, grid_for(N), kBlock, st, logw, N, base, log_n, count);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_loglik_step(const Scratch& s, const double* lse, double* base, double* ll,
+                               int32_t* count, double c, double log_n, int first,
+                               cudaStream_t st) {
+  trace_mark(s.trace, "loglik_step", st);
+  launch_pdl(loglik_step_kernel, 1, 32, st, lse, base, ll, count, c, log_n, first);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_copy_ancestors(const Scratch& s, float* x, int D, const int32_t* c, int64_t N,
                                   cudaStream_t st) {

@@ -14,9 +14,10 @@ import math
 import numpy as np
 import torch
 
-from . import (PREC_COMPENSATED, Handle, rs_copy_ancestors, rs_copy_ancestors_batched,
-               rs_cumulative_weights, rs_ess, rs_lgssm_step, rs_lgssm_step_batched,
-               rs_log_sum_weights_batched, rs_resample, rs_resample_batched)
+from . import (PREC_COMPENSATED, Handle, rs_capture_end_if, rs_capture_if_below,
+               rs_copy_ancestors, rs_copy_ancestors_batched, rs_ess,
+               rs_lgssm_step, rs_lgssm_step_batched, rs_log_sum_weights_batched, rs_resample,
+               rs_resample_batched, rs_smc_loglik_step, rs_smc_mark_resampled)
 
 
 class LgssmBuffers:
@@ -27,7 +28,7 @@ class LgssmBuffers:
         self.x = torch.empty(N, dtype=torch.float32, device=device)
         self.logw = torch.empty(N, dtype=torch.float32, device=device)
         self.c = torch.empty(N, dtype=torch.int32, device=device)
-        self.W = torch.empty(N, dtype=torch.float32, device=device)
+        self.ess = torch.empty(1, dtype=torch.float64, device=device)
         self.log_total = torch.empty(T, dtype=torch.float64, device=device)
 
 
@@ -36,8 +37,8 @@ def lgssm_bootstrap_launch(h: Handle, y, N: int, scheme: int, phi: float, sigma_
                            prec: int = PREC_COMPENSATED, bufs: LgssmBuffers | None = None,
                            stream=None, filter: int = 0) -> LgssmBuffers:
     """Enqueue the whole filter on the stream (no synchronisation); returns the buffers, whose
-    log_total[t] receives log sum_i w_t^i (max-shifted weights, shift added back). ``filter``
-    is the filter index of every random-number counter."""
+    log_total[t] receives log sum_i w_t^i (max-shifted weights, shift added back, from rs_ess).
+    ``filter`` is the filter index of every random-number counter."""
     T = len(y)
     b = bufs or LgssmBuffers(N, T)
     for t in range(T):
@@ -47,8 +48,7 @@ def lgssm_bootstrap_launch(h: Handle, y, N: int, scheme: int, phi: float, sigma_
             rs_copy_ancestors(h, b.x, b.c, stream=stream)
         rs_lgssm_step(h, b.x, t == 0, phi, sigma_x, float(y[t]), sigma_y, seed=seed, step=t,
                       filter=filter, logw=b.logw, stream=stream)
-        rs_cumulative_weights(h, b.logw, prec=prec, W=b.W, log_total=b.log_total[t:t + 1],
-                              stream=stream)
+        rs_ess(h, b.logw, out=b.ess, log_total=b.log_total[t:t + 1], stream=stream)
     return b
 
 
@@ -91,14 +91,63 @@ def lgssm_adaptive(h: Handle, y, N: int, scheme: int, phi: float, sigma_x: float
             n_res += 1
         rs_lgssm_step(h, b.x, t == 0, phi, sigma_x, float(y[t]), sigma_y, seed=seed, step=t,
                       logw=b.logw, accumulate=(t > 0 and not resample), stream=stream)
-        rs_cumulative_weights(h, b.logw, prec=prec, W=b.W, log_total=b.log_total[t:t + 1],
-                              stream=stream)
-        rs_ess(h, b.logw, out=ess, stream=stream)
+        rs_ess(h, b.logw, out=ess, log_total=b.log_total[t:t + 1], stream=stream)
         lse = float(b.log_total[t].item())
         ll += lse - base - 0.5 * math.log(2 * math.pi * sigma_y ** 2)
         base = lse
         resample = float(ess.item()) < ess_fraction * N
     return ll, n_res
+
+
+class AdaptiveGraph:
+    """The adaptive filter as one CUDA graph: every resampling decision is a conditional node
+    (rs_capture_if_below on the device-side ESS), the likelihood and the resampling count are
+    kept on the device (rs_smc_loglik_step, rs_smc_mark_resampled). Same arithmetic and the
+    same decisions as lgssm_adaptive, without a host round trip per step; replay() reruns the
+    whole filter."""
+
+    def __init__(self, h: Handle, y, N: int, scheme: int, phi: float, sigma_x: float,
+                 sigma_y: float, ess_fraction: float = 0.5, seed: int = 0, B: int = 64,
+                 prec: int = PREC_COMPENSATED):
+        T = len(y)
+        self.b = b = LgssmBuffers(N, T)
+        dev = b.x.device
+        self.ess = torch.empty(1, dtype=torch.float64, device=dev)
+        self.base = torch.empty(1, dtype=torch.float64, device=dev)
+        self.ll = torch.empty(1, dtype=torch.float64, device=dev)
+        self.count = torch.zeros(1, dtype=torch.int32, device=dev)
+        log_n = math.log(N)
+        c = 0.5 * math.log(2 * math.pi * sigma_y ** 2)
+
+        def enqueue(stream):
+            for t in range(T):
+                if t > 0:
+                    body = rs_capture_if_below(h, self.ess, ess_fraction * N, stream=stream)
+                    rs_resample(h, scheme, b.logw, B=B, seed=seed, step=t, out=b.c,
+                                permute=True, prec=prec, log_wmax=0.0, stream=body)
+                    rs_copy_ancestors(h, b.x, b.c, stream=body)
+                    rs_smc_mark_resampled(h, b.logw, self.base, log_n, self.count, stream=body)
+                    rs_capture_end_if(h, stream=stream)
+                rs_lgssm_step(h, b.x, t == 0, phi, sigma_x, float(y[t]), sigma_y, seed=seed,
+                              step=t, logw=b.logw, accumulate=t > 0, stream=stream)
+                rs_ess(h, b.logw, out=self.ess, log_total=b.log_total[t:t + 1], stream=stream)
+                rs_smc_loglik_step(h, b.log_total[t:t + 1], self.base, self.ll, c, log_n,
+                                   t == 0, self.count, stream=stream)
+
+        cs = torch.cuda.Stream()
+        cs.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(cs):
+            self.graph = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(self.graph, stream=cs):
+                enqueue(cs)
+        torch.cuda.current_stream().wait_stream(cs)
+
+    def replay(self):
+        self.graph.replay()
+
+    def result(self):
+        """(log p-hat(y_1:T), number of resamplings) of the last replay (synchronises)."""
+        return float(self.ll.item()), int(self.count.item())
 
 
 class BatchedLgssmBuffers:

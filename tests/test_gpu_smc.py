@@ -97,13 +97,19 @@ def test_ess_matches_host(rs, h):
             lw = workload.synthetic_logw(N, y, seed=N, dtype=dtype)
             if N > 10:
                 lw[::7] = -np.inf
-            e = rs.rs_ess(h, torch.from_numpy(lw).to(DEV)).item()
+            lt = torch.empty(1, dtype=torch.float64, device=DEV)
+            e = rs.rs_ess(h, torch.from_numpy(lw).to(DEV), log_total=lt).item()
             assert rs.rs_last_error(h) == rs.RS_OK
-            w = np.exp(lw.astype(np.float64) - lw.max())
+            m = float(lw.max())
+            w = np.exp(lw.astype(np.float64) - m)
             want = w.sum() ** 2 / (w * w).sum()
             assert abs(e - want) <= 1e-5 * want, (dtype, N, e, want)
+            want_lt = m + math.log(math.fsum(w))
+            assert abs(lt.item() - want_lt) <= 2e-7 * max(1.0, abs(want_lt)), (lt.item(), want_lt)
     z = torch.full((100,), -np.inf, dtype=torch.float32, device=DEV)
-    assert rs.rs_ess(h, z).item() == 0.0
+    lt = torch.empty(1, dtype=torch.float64, device=DEV)
+    assert rs.rs_ess(h, z, log_total=lt).item() == 0.0
+    assert lt.item() == -np.inf
     assert rs.rs_last_error(h) == rs.RS_ERR_ZERO_WEIGHT
 
 
@@ -122,6 +128,46 @@ def test_adaptive_filter_matches_kalman(rs, h, scheme):
     assert 0 < min(n_res) and max(n_res) < T - 1
     sd = lls.std(ddof=1)
     assert abs(lls.mean() - want) < 4 * sd, (lls.mean(), want, sd, n_res)
+
+
+@pytest.mark.parametrize("scheme", [2, 4])
+def test_adaptive_graph_equals_host_decisions(rs, h, scheme):
+    """The adaptive filter captured as one CUDA graph (conditional nodes decide on the device)
+    takes the same resampling decisions as the host-driven loop and computes the same
+    particles, weights and log-likelihood, bit for bit, on every replay."""
+    from paper_1301_4019_gb300 import smc
+    T, N = 60, 1 << 16
+    _, y = workload.lgssm_simulate(T, PHI, SX, SY, seed=23)
+    ll_host, n_host = smc.lgssm_adaptive(h, y, N, scheme, PHI, SX, SY, 0.5, seed=8)
+    assert rs.rs_last_error(h) == rs.RS_OK
+    g = smc.AdaptiveGraph(h, y, N, scheme, PHI, SX, SY, 0.5, seed=8)
+    for _ in range(3):
+        g.replay()
+        ll, n = g.result()
+        assert rs.rs_last_error(h) == rs.RS_OK
+        assert n == n_host and 0 < n < T - 1
+        assert ll == ll_host, (ll, ll_host)
+    # the graph's particles equal a host-driven run's
+    b = smc.LgssmBuffers(N, T)
+    ess = torch.empty(1, dtype=torch.float64, device=DEV)
+    resample = False
+    for t in range(T):
+        if resample:
+            rs.rs_resample(h, scheme, b.logw, B=64, seed=8, step=t, out=b.c, permute=True,
+                           prec=rs.PREC_COMPENSATED, log_wmax=0.0)
+            rs.rs_copy_ancestors(h, b.x, b.c)
+        rs.rs_lgssm_step(h, b.x, t == 0, PHI, SX, float(y[t]), SY, seed=8, step=t, logw=b.logw,
+                         accumulate=(t > 0 and not resample))
+        resample = rs.rs_ess(h, b.logw, out=ess).item() < 0.5 * N
+    assert torch.equal(g.b.x, b.x) and torch.equal(g.b.logw, b.logw)
+
+
+def test_capture_if_below_needs_a_capturing_stream(rs, h):
+    v = torch.zeros(1, dtype=torch.float64, device=DEV)
+    with pytest.raises(rs.RsError):
+        rs.rs_capture_if_below(h, v, 1.0)
+    with pytest.raises(rs.RsError):
+        rs.rs_capture_end_if(h)
 
 
 # ---------------------------------------------------------------------------------------
