@@ -36,29 +36,6 @@ __device__ __forceinline__ float ess_weight(double x, float, float2 M2) {
   return is_neg_inf(x) ? 0.0f : exp_pinned(add22_accurate(split_f64(x), neg2(M2)).x);
 }
 
-// A u128 written by another CTA of the same launch (before a grid barrier), read through L2.
-__device__ __forceinline__ u128 ld_u128_cg(const u128* p) {
-  const unsigned long long* q = reinterpret_cast<const unsigned long long*>(p);
-  return static_cast<u128>(__ldcg(q)) | (static_cast<u128>(__ldcg(q + 1)) << 64);
-}
-
-// Sum over the CTA of one u128 per thread (exact), returned to every thread.
-__device__ __forceinline__ u128 block_sum_u128(u128 v, u128* sh) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    const uint64_t hi = __shfl_xor_sync(0xffffffffu, static_cast<uint64_t>(v >> 64), o);
-    const uint64_t lo = __shfl_xor_sync(0xffffffffu, static_cast<uint64_t>(v), o);
-    v += (static_cast<u128>(hi) << 64) | lo;
-  }
-  __syncthreads();
-  if (lane == 0) sh[warp] = v;
-  __syncthreads();
-  u128 t = 0;
-  for (int k = 0; k < kWarps; ++k) t += sh[k];
-  return t;
-}
-
 template <typename T>
 __global__ void __launch_bounds__(kBlock)
 ess_kernel(const T* __restrict__ lw, int64_t N, double* blockmax, u128* agg, unsigned int* bar,

@@ -71,33 +71,6 @@ struct FusedArgs {
   int* err;
 };
 
-__device__ __forceinline__ u128 shfl_xor_u128(u128 v, int m) {
-  const uint64_t hi = __shfl_xor_sync(0xffffffffu, static_cast<uint64_t>(v >> 64), m);
-  const uint64_t lo = __shfl_xor_sync(0xffffffffu, static_cast<uint64_t>(v), m);
-  return (static_cast<u128>(hi) << 64) | lo;
-}
-__device__ __forceinline__ u128 ld_u128_cg(const u128* p) {
-  const ulonglong2 v = __ldcg(reinterpret_cast<const ulonglong2*>(p));
-  return (static_cast<u128>(v.y) << 64) | v.x;
-}
-__device__ __forceinline__ void st_u128(u128* p, u128 v) {
-  *reinterpret_cast<ulonglong2*>(p) =
-      make_ulonglong2(static_cast<uint64_t>(v), static_cast<uint64_t>(v >> 64));
-}
-
-// Block-wide sum of u128 (every thread gets the result).
-__device__ __forceinline__ u128 block_sum_u128(u128 v, u128* sh) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += shfl_xor_u128(v, o);
-  __syncthreads();
-  if (lane == 0) sh[warp] = v;
-  __syncthreads();
-  u128 t = 0;
-  for (int k = 0; k < kWarps; ++k) t += sh[k];
-  return t;
-}
-
 // CTA c owns the contiguous tiles [c T / G, (c+1) T / G) of the T tiles (G = gridDim.x <= T):
 //   phase 1  maximum over its particles -> barrier -> M = maximum over the CTAs;
 //   phase 2  tile totals s_t of its tiles, in order, and their exact running sum in fixed

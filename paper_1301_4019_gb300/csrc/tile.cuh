@@ -332,6 +332,35 @@ __device__ __forceinline__ u128 shfl_up_u128(u128 v, int d) {
   return (static_cast<u128>(hi) << 64) | lo;
 }
 
+// u128 helpers of the cooperative kernels: butterfly shuffle, a load through L2 of a value
+// another CTA of the same launch wrote before a grid barrier, a 16-byte store, and the
+// block-wide sum (every thread gets the result).
+__device__ __forceinline__ u128 shfl_xor_u128(u128 v, int m) {
+  const uint64_t hi = __shfl_xor_sync(0xffffffffu, static_cast<uint64_t>(v >> 64), m);
+  const uint64_t lo = __shfl_xor_sync(0xffffffffu, static_cast<uint64_t>(v), m);
+  return (static_cast<u128>(hi) << 64) | lo;
+}
+__device__ __forceinline__ u128 ld_u128_cg(const u128* p) {
+  const ulonglong2 v = __ldcg(reinterpret_cast<const ulonglong2*>(p));
+  return (static_cast<u128>(v.y) << 64) | v.x;
+}
+__device__ __forceinline__ void st_u128(u128* p, u128 v) {
+  *reinterpret_cast<ulonglong2*>(p) =
+      make_ulonglong2(static_cast<uint64_t>(v), static_cast<uint64_t>(v >> 64));
+}
+
+__device__ __forceinline__ u128 block_sum_u128(u128 v, u128* sh) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += shfl_xor_u128(v, o);
+  __syncthreads();
+  if (lane == 0) sh[warp] = v;
+  __syncthreads();
+  u128 t = 0;
+  for (int k = 0; k < kWarps; ++k) t += sh[k];
+  return t;
+}
+
 // A tile's record: its total in the accumulator type; rec_fixed returns it in fixed point.
 template <typename V> __device__ __forceinline__ u128 rec_fixed(const double2* p) {
   return to_fixed(load_v_cg<V>(p));
