@@ -703,6 +703,24 @@ def oracle_step(lw_by_dtype, B, seed, step):
     return n
 
 
+def host_info() -> dict:
+    """The host the CPU legs ran on: logical CPUs and the CPU model (from /proc/cpuinfo)."""
+    model = None
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                key = line.split(":")[0].strip().lower()
+                if key in ("model name", "cpu model", "hardware") and ":" in line:
+                    model = line.split(":", 1)[1].strip()
+                    break
+                if key == "cpu part" and model is None and ":" in line:
+                    model = "cpu part " + line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return {"nproc": os.cpu_count(), "cpu": model, "arch": platform.machine()}
+
+
 def cpu_baseline(N, B, y, budget_s=20.0):
     """The oracle as it stands, single-threaded, on a bounded sample of the workload."""
     import oracle
@@ -718,7 +736,8 @@ def cpu_baseline(N, B, y, budget_s=20.0):
     el = time.perf_counter() - t0
     return {"value": round(done / el / 1e9, 6), "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": f"{reps} pass(es) of the full step workload at N=2^{int(math.log2(N))} "
-                      f"(5 resamplers x 2 dtypes + Permute), single thread, {el:.1f} s"}
+                      f"(5 resamplers x 2 dtypes + Permute), single thread, {el:.1f} s",
+            "host": host_info()}
 
 
 def run_reference(args):
@@ -748,7 +767,7 @@ def run_reference(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
         "config": workload_config(args, N, B),
         "cpu_baseline": {"value": round(value, 6), "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": sample},
+                         "sample": sample, "host": host_info()},
         "e2e": {"value": round(value, 6), "unit": UNIT, "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }
