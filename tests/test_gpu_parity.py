@@ -404,3 +404,28 @@ def test_log_normaliser_uses_true_maximum(rs, h, dtype):
         assert W[1] - W[0] == pytest.approx(1.0, rel=1e-6)
         tol = 1e-12 if dtype == np.float64 else 1e-6
         assert lt.item() == pytest.approx(np.log(np.sum(np.exp(lw.astype(np.float64)))), rel=tol)
+
+
+def test_argument_checks_on_the_device_path(rs, h):
+    """Empty input, capacity, unknown scheme / precision and aliasing are refused on the host
+    (RsError), before any kernel runs; the handle stays usable."""
+    lw = torch.zeros(8, dtype=torch.float32, device=DEV)
+    out = torch.empty(8, dtype=torch.int32, device=DEV)
+    with pytest.raises(rs.RsError) as e:
+        rs.rs_resample(h, rs.SYSTEMATIC, lw[:0], out=out[:0])
+    assert e.value.status == rs.RS_ERR_ARG
+    with rs.Handle(4) as small:
+        with pytest.raises(rs.RsError) as e:
+            rs.rs_resample(small, rs.SYSTEMATIC, lw, out=out)
+        assert e.value.status == rs.RS_ERR_CAPACITY
+    with pytest.raises(rs.RsError):
+        rs.rs_resample(h, 5, lw, out=out)
+    with pytest.raises(rs.RsError):
+        rs.rs_resample(h, rs.SYSTEMATIC, lw, out=out, prec=rs.PREC_BINARY64)  # binary32 input
+    with pytest.raises(rs.RsError):
+        rs.rs_resample(h, rs.METROPOLIS, lw, B=-1, out=out)
+    with pytest.raises(rs.RsError):
+        rs.rs_permute(h, out, out)
+    a = rs.rs_resample(h, rs.SYSTEMATIC, lw, out=out)
+    assert rs.rs_last_error(h) == rs.RS_OK
+    assert a.cpu().tolist() == list(range(8))
