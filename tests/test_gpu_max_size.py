@@ -23,17 +23,21 @@ def big(rs):
 
 
 def _permute_ok(a, c):
+    """c is a permutation of a (same counts) with o_i > 0 => c_i = i (Code 10)."""
     o = np.bincount(a, minlength=len(a))
-    return np.array_equal(np.sort(c), np.sort(a)) and np.all(c[o > 0] == np.nonzero(o > 0)[0])
+    return np.array_equal(np.bincount(c, minlength=len(a)), o) and \
+        np.all(c[o > 0] == np.nonzero(o > 0)[0])
 
 
 @pytest.mark.parametrize("dtype", [np.float32, np.float64])
 def test_collective_free_bit_exact_at_max_size(rs, big, dtype):
-    lw = workload.synthetic_logw(N, 2.0, seed=26, dtype=dtype)
+    """Index arithmetic at the largest size: short chains (B = 2) and mild skew (y = 1) keep
+    the oracle's share of the test to seconds."""
+    lw = workload.synthetic_logw(N, 1.0, seed=26, dtype=dtype)
     t = torch.from_numpy(lw).to(DEV)
-    a = rs.rs_resample(big, rs.METROPOLIS, t, B=4, seed=3, step=1).cpu().numpy()
+    a = rs.rs_resample(big, rs.METROPOLIS, t, B=2, seed=3, step=1).cpu().numpy()
     assert rs.rs_last_error(big) == rs.RS_OK
-    st, want = oracle.metropolis(lw, 4, seed=3, step=1)
+    st, want = oracle.metropolis(lw, 2, seed=3, step=1)
     assert st == oracle.OK and np.array_equal(a, want)
     a = rs.rs_resample(big, rs.REJECTION, t, seed=3, step=1, log_wmax=0.0).cpu().numpy()
     assert rs.rs_last_error(big) == rs.RS_OK
