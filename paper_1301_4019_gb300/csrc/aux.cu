@@ -58,6 +58,69 @@ permute_sorted_kernel(const int32_t* __restrict__ a, const int32_t* __restrict__
   permute_sorted_one(a, d, N, c, i, err);
 }
 
+// Permute of a non-decreasing ancestry (permute_sorted_one) with four consecutive slots per
+// thread: the slot loads of a and d are 128-bit and every thread has four slots' loads in
+// flight; the walks of failed claims follow one after the other. The reads and writes of each
+// slot are those of permute_sorted_one, so c is the same. (For an unsorted ancestry the same
+// layout measured 1-3 % slower than one slot per thread: there the random claim checks and
+// walks dominate.)
+__global__ void __launch_bounds__(kBlock)
+permute_sorted4_kernel(const int32_t* __restrict__ a, const int32_t* __restrict__ d, int64_t N,
+                       int32_t* __restrict__ c, int* err) {
+  pdl_wait();
+  const int64_t i0 = 4 * (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x);
+  if (i0 >= N) return;
+  const int32_t sentinel = static_cast<int32_t>(N);
+  int32_t A[4], D[4];
+  const bool vec = i0 + 3 < N &&
+                   ((reinterpret_cast<uintptr_t>(a) | reinterpret_cast<uintptr_t>(d)) & 15u) == 0;
+  if (vec) {
+    const int4 va = *reinterpret_cast<const int4*>(a + i0);
+    const int4 vd = *reinterpret_cast<const int4*>(d + i0);
+    A[0] = va.x; A[1] = va.y; A[2] = va.z; A[3] = va.w;
+    D[0] = vd.x; D[1] = vd.y; D[2] = vd.z; D[3] = vd.w;
+  } else {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      A[q] = i0 + q < N ? a[i0 + q] : 0;
+      D[q] = i0 + q < N ? d[i0 + q] : sentinel;
+    }
+  }
+  int32_t prev = i0 > 0 ? a[i0 - 1] : -1;
+  bool ok[4], fail[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    ok[q] = i0 + q < N;
+    if (ok[q] && (A[q] < 0 || A[q] >= N)) {
+      flag_error(err, RS_ERR_ARG);
+      ok[q] = false;
+    }
+    fail[q] = ok[q] && prev == A[q];  // the claim of slot i failed: a_{i-1} = a_i
+    prev = A[q];
+  }
+#pragma unroll
+  for (int q = 0; q < 4; ++q)
+    if (ok[q] && D[q] != sentinel) c[i0 + q] = static_cast<int32_t>(i0 + q);
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    if (!fail[q]) continue;
+    int64_t x = i0 + q;
+    int32_t dx = D[q];
+    int64_t steps = 0;
+    bool good = true;
+    while (dx != sentinel) {
+      if (dx < 0 || dx > sentinel || ++steps > N) {  // only a corrupted d can get here
+        flag_error(err, RS_ERR_ARG);
+        good = false;
+        break;
+      }
+      x = dx;
+      dx = d[x];
+    }
+    if (good) c[x] = A[q];
+  }
+}
+
 // Ancestors-to-Offspring (Code 12).
 __global__ void __launch_bounds__(kBlock)
 offspring_kernel(const int32_t* __restrict__ a, int64_t N, int32_t* __restrict__ o, int* err) {
@@ -271,10 +334,18 @@ cudaError_t launch_permute(const Scratch& s, const int32_t* a, const int32_t* d,
   return cudaGetLastError();
 }
 
+// Four slots per thread from 2^18 slots (measured 2 % faster at 2^20, 9 % at 2^22, 18 % at
+// 2^24); below, one slot per thread keeps more threads in flight.
+constexpr int64_t kSorted4MinN = int64_t{1} << 18;
+
 cudaError_t launch_permute_sorted(const Scratch& s, const int32_t* a, const int32_t* d, int64_t N,
                                   int32_t* c, cudaStream_t st) {
   trace_mark(s.trace, "permute_sorted", st);
-  launch_pdl(permute_sorted_kernel, grid_for(N), kBlock, st, a, d, N, c, s.err);
+  if (N >= kSorted4MinN)
+    launch_pdl(permute_sorted4_kernel, static_cast<int>((N + 4 * kBlock - 1) / (4 * kBlock)),
+               kBlock, st, a, d, N, c, s.err);
+  else
+    launch_pdl(permute_sorted_kernel, grid_for(N), kBlock, st, a, d, N, c, s.err);
   return cudaGetLastError();
 }
 
