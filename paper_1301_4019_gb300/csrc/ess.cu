@@ -24,8 +24,12 @@ __device__ __forceinline__ long long ess_key(double v) {
   const long long b = __double_as_longlong(v);
   return b >= 0 ? b : (b ^ 0x7fffffffffffffffLL);
 }
-__device__ __forceinline__ double ess_value(long long k) {
+__device__ __forceinline__ double ess_value(long long k, double) {
   return __longlong_as_double(k >= 0 ? k : (k ^ 0x7fffffffffffffffLL));
+}
+__device__ __forceinline__ double ess_value(long long k, float) {
+  const int b = static_cast<int>(k);
+  return static_cast<double>(__int_as_float(b >= 0 ? b : (b ^ 0x7fffffff)));
 }
 
 // Binary32 weight of one log-weight given the maximum (the ESS needs no more precision).
@@ -48,13 +52,14 @@ ess_kernel(const T* __restrict__ lw, int64_t N, double* blockmax, u128* agg, uns
   const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
   const int64_t t0 = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
   // maximum (NaN skipped and flagged, as +inf)
-  long long m = ess_key(-static_cast<double>(INFINITY));
+  // keys of the log-weights' own type (no per-particle conversion to binary64)
+  long long m = ess_key(neg_inf<T>());
   bool bad = false;
   for (int64_t i = t0; i < N; i += stride) {
     const T x = lw[i];
     bad |= nonfinite_logw(x);
     if (!is_nan(x)) {
-      const long long k = ess_key(static_cast<double>(x));
+      const long long k = ess_key(x);
       m = k > m ? k : m;
     }
   }
@@ -69,10 +74,10 @@ ess_kernel(const T* __restrict__ lw, int64_t N, double* blockmax, u128* agg, uns
   if (threadIdx.x == 0) {
     long long bm = sh_key[0];
     for (int k = 1; k < kWarps; ++k) bm = sh_key[k] > bm ? sh_key[k] : bm;
-    blockmax[blockIdx.x] = ess_value(bm);
+    blockmax[blockIdx.x] = ess_value(bm, T());
   }
   grid_barrier(bar, target, err);
-  long long mk = ess_key(-static_cast<double>(INFINITY));
+  long long mk = ess_key(-static_cast<double>(INFINITY));  // binary64 keys of the CTA maxima
   for (int b = threadIdx.x; b < static_cast<int>(gridDim.x); b += kBlock) {
     const long long y = ess_key(__ldcg(blockmax + b));
     mk = y > mk ? y : mk;
@@ -87,7 +92,7 @@ ess_kernel(const T* __restrict__ lw, int64_t N, double* blockmax, u128* agg, uns
   __syncthreads();
   long long bm = sh_key[0];
   for (int k = 1; k < kWarps; ++k) bm = sh_key[k] > bm ? sh_key[k] : bm;
-  const double M = ess_value(bm);
+  const double M = ess_value(bm, 0.0);
   const bool zero = !(M > -DBL_MAX);
   // two-float sums of w and w^2 per thread, then per CTA
   float2 s1 = make_float2(0.0f, 0.0f), s2 = make_float2(0.0f, 0.0f);

@@ -3,9 +3,11 @@
 //  - the propagate-and-weight step of the 1-D linear-Gaussian state-space model used to run
 //    the full SMC loop: x_t = phi x_{t-1} + sigma_x eps, log w = -(y_t - x_t)^2 / (2 sigma_y^2).
 #include <cmath>
+#include <type_traits>
 
 #include "common.cuh"
 #include "internal.h"
+#include "values.cuh"
 
 namespace rsk {
 namespace {
@@ -112,10 +114,20 @@ lgssm_step_batched_kernel(float* __restrict__ x, const int64_t* __restrict__ off
   logw[g] = accumulate ? logw[g] + l : l;
 }
 
+// Per-thread sum of the max-shifted weights: two-float for binary32 log-weights (no binary64
+// arithmetic per particle), binary64 for binary64 ones.
+__device__ __forceinline__ void lse_acc(float2& acc, float x, float m) {
+  acc = add21(acc, expf(x - m));
+}
+__device__ __forceinline__ void lse_acc(double& acc, double x, double m) { acc += exp(x - m); }
+__device__ __forceinline__ double lse_to_double(float2 a) { return vto_double(a); }
+__device__ __forceinline__ double lse_to_double(double a) { return a; }
+
 // log sum_{i in filter f} exp(lw_i), one CTA per filter: the maximum m, then
-// m + log sum exp(lw_i - m) with the exponentials in the log-weights' type and the sum in
-// binary64 (Appendix E's max-shift). -inf for a filter whose weights are all zero; NaN / +inf
-// log-weights are flagged.
+// m + log sum exp(lw_i - m) with the exponentials in the log-weights' type, the per-thread
+// sums in two-float (binary32) or binary64, and the CTA's sum in binary64 (Appendix E's
+// max-shift). -inf for a filter whose weights are all zero; NaN / +inf log-weights are
+// flagged.
 template <typename T>
 __global__ void __launch_bounds__(kBlock)
 log_sum_batched_kernel(const T* __restrict__ lw, const int64_t* __restrict__ off, int F,
@@ -149,9 +161,10 @@ log_sum_batched_kernel(const T* __restrict__ lw, const int64_t* __restrict__ off
     return;
   }
   const T mt = static_cast<T>(md);
-  double sum = 0.0;
-  for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x)
-    sum += static_cast<double>(exp(__ldg(lw + i) - mt));
+  using Acc = typename std::conditional<sizeof(T) == 4, float2, double>::type;
+  Acc acc{};
+  for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) lse_acc(acc, __ldg(lw + i), mt);
+  double sum = lse_to_double(acc);
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
   if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = sum;
