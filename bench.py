@@ -217,25 +217,25 @@ class ClockSampler:
 # headers it includes, hashed; `traffic` is null once any of them has changed.
 # ---------------------------------------------------------------------------------------
 NCU_TRAFFIC = {  # label: (bytes per launch, source hash)
-               "permute": (8392826, "5ddf2a93ad7d34f8"),
-               "metropolis_f64": (12599223, "66fbfa7d71a1c7f2"),
-               "metropolis_f32": (8406976, "66fbfa7d71a1c7f2"),
-               "permute_sorted": (8392808, "5ddf2a93ad7d34f8"),
-               "rejection_f64": (8409746, "66fbfa7d71a1c7f2"),
-               "fused_stratified_f64": (8487744, "c0237b11364be319"),
-               "rejection_f32": (4209312, "66fbfa7d71a1c7f2"),
-               "fused_multinomial_f64": (8498592, "c0237b11364be319"),
-               "fused_systematic_f64": (8480672, "c0237b11364be319"),
-               "fused_multinomial_f32": (4273024, "c0237b11364be319"),
-               "fused_stratified_f32": (4260992, "c0237b11364be319"),
-               "fused_systematic_f32": (4257504, "c0237b11364be319"),
-               "iscan": (4212955, "5ddf2a93ad7d34f8"),
-               "search_f64": (16784768, "e189bcb76f2ae283"),
-               "search_f32": (12592608, "e189bcb76f2ae283"),
-               "fill": (8525, "5ddf2a93ad7d34f8"),
-               "cumoff_to_ancestors": (4199219, "5ddf2a93ad7d34f8"),
-               "offspring": (8391150, "5ddf2a93ad7d34f8"),
-               "adjacent_difference": (4197615, "5ddf2a93ad7d34f8")}
+               "permute": (8393633, "0684457ff7d53862"),
+               "metropolis_f64": (12600539, "33399ab6e0060ca2"),
+               "metropolis_f32": (8400864, "33399ab6e0060ca2"),
+               "rejection_f64": (8408686, "33399ab6e0060ca2"),
+               "permute_sorted": (8398568, "0684457ff7d53862"),
+               "fused_stratified_f64": (8487040, "a2b9eb1bf5073064"),
+               "rejection_f32": (4209056, "33399ab6e0060ca2"),
+               "fused_multinomial_f64": (8496992, "a2b9eb1bf5073064"),
+               "fused_systematic_f64": (8481664, "a2b9eb1bf5073064"),
+               "fused_stratified_f32": (4261408, "a2b9eb1bf5073064"),
+               "fused_multinomial_f32": (4278720, "a2b9eb1bf5073064"),
+               "fused_systematic_f32": (4260928, "a2b9eb1bf5073064"),
+               "iscan": (4213522, "0684457ff7d53862"),
+               "search_f64": (16783200, "a2d62d32474fc766"),
+               "search_f32": (12591712, "a2d62d32474fc766"),
+               "fill": (8380, "0684457ff7d53862"),
+               "cumoff_to_ancestors": (4199185, "0684457ff7d53862"),
+               "offspring": (8391424, "0684457ff7d53862"),
+               "adjacent_difference": (4197751, "0684457ff7d53862")}
 
 _LABEL_FILES = (("fused_", "fused.cu"), ("permute", "aux.cu"), ("iscan", "aux.cu"),
                 ("fill", "aux.cu"), ("offspring", "aux.cu"), ("adjacent", "aux.cu"),
