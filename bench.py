@@ -65,7 +65,7 @@ def parse_args():
                    help="per-call times of the five resamplers (with Permute) for N = 2^10 .. "
                         "2^24, binary32 and binary64, L2 flushed before every call; one JSON "
                         "line")
-    p.add_argument("--sweep-reps", type=int, default=15)
+    p.add_argument("--sweep-reps", type=int, default=21)
     p.add_argument("--sweep-y", default="0,1,2,3,4",
                    help="comma-separated y values of the sweep (weight skew)")
     p.add_argument("--precision", action="store_true",
@@ -890,8 +890,8 @@ def run_precision(args):
     modes = [("f32 plain", np.float32, rs.PREC_PLAIN), ("f32 compensated", np.float32,
               rs.PREC_COMPENSATED), ("f64", np.float64, rs.PREC_PLAIN)]
     rows = []
-    with rs.Handle(1 << 24) as h:
-        for log2n in (16, 18, 20, 22, 24):
+    with rs.Handle(1 << 26) as h:
+        for log2n in (16, 18, 20, 22, 24, 26):
             N = 1 << log2n
             out = torch.empty(N, dtype=torch.int32, device="cuda")
             o = torch.empty(N, dtype=torch.int32, device="cuda")
@@ -923,7 +923,7 @@ def run_precision(args):
         # weights, E_u[o_i] = r_i - r_{i-1} with r_i = N W_i / W_N (Section 4.2's measure without
         # Monte Carlo noise), from the accumulators written out exactly in binary64
         det = []
-        for log2n in (16, 18, 20, 22, 24):
+        for log2n in (16, 18, 20, 22, 24, 26):
             N = 1 << log2n
             for y in (0.0, 2.0, 4.0):
                 lw64 = workload.synthetic_logw(N, y, seed=SEED + 300 + log2n, dtype=np.float64)
