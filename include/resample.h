@@ -93,8 +93,11 @@ typedef struct {
 } rs_opts;
 
 /* A handle owns the device scratch of the calls that need it (claim vector d, unpermuted
- * ancestors, cumulative weights of the multinomial scheme, per-tile partial sums, the
- * device status word): about 20 bytes per particle of max_n, allocated once here. */
+ * ancestors, cumulative weights of the multinomial scheme, per-tile partial sums, the grid
+ * barrier counter, the device status word): about 20 bytes per particle of max_n, allocated
+ * once here. Calls on one handle share that scratch, so they must execute one after the
+ * other: issue them on one stream (or order the streams with events), and from one host
+ * thread at a time. Independent work in parallel uses one handle per stream. */
 typedef struct rs_handle rs_handle;
 
 /* Creates a handle for problems of up to max_n particles on `device` (made current).
