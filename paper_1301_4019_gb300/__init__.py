@@ -527,3 +527,30 @@ def rs_systematic_noalloc(logw: torch.Tensor, seed: int = 0, step: int = 0,
 def rs_strerror(status: int) -> str:
     lib = _lib if _lib is not None else load()
     return lib.rs_strerror(int(status)).decode()
+
+
+# ---- convenience: one call with a cached handle ---------------------------------------------
+_handles: dict = {}
+
+
+def resample(logw: torch.Tensor, scheme="systematic", *, B: int = 0, seed: int = 0,
+             step: int = 0, permute: bool = True, prec: int = PREC_PLAIN,
+             log_wmax: float = 0.0, check: bool = True, stream=None) -> torch.Tensor:
+    """Ancestors of `logw` in one call: `scheme` by name or code, a handle of sufficient
+    capacity kept per device (grown when a larger N arrives), Permute by default (so that the
+    particles can be copied in place). With `check`, synchronises and raises RsError on a
+    device-side status (NaN/inf log-weights, all-zero weights, ...). B: Metropolis steps
+    (see rs_metropolis_B for Eq. B); log_wmax: the rejection bound."""
+    code = SCHEMES[scheme] if isinstance(scheme, str) else int(scheme)
+    dev = logw.device.index if logw.device.index is not None else torch.cuda.current_device()
+    N = logw.numel()
+    h = _handles.get(dev)
+    if h is None or h.max_n < N:
+        if h is not None:
+            h.close()
+        h = _handles[dev] = Handle(max(N, 1024), device=dev)
+    a = rs_resample(h, code, logw, B=B, seed=seed, step=step, permute=permute, prec=prec,
+                    log_wmax=log_wmax, stream=stream)
+    if check:
+        _check(rs_last_error(h, stream), "resample")
+    return a

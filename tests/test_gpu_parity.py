@@ -429,3 +429,17 @@ def test_argument_checks_on_the_device_path(rs, h):
     a = rs.rs_resample(h, rs.SYSTEMATIC, lw, out=out)
     assert rs.rs_last_error(h) == rs.RS_OK
     assert a.cpu().tolist() == list(range(8))
+
+
+def test_convenience_resample_matches_the_handle_call(rs, h):
+    lw = torch.from_numpy(workload.synthetic_logw(70001, 2.0, seed=5)).to(DEV)
+    for name in ("multinomial", "stratified", "systematic", "metropolis", "rejection"):
+        a = rs.resample(lw, name, B=16, seed=3, step=2)
+        b = rs.rs_resample(h, rs.SCHEMES[name], lw, B=16, seed=3, step=2, permute=True)
+        assert rs.rs_last_error(h) == rs.RS_OK
+        assert torch.equal(a, b), name
+    bigger = torch.from_numpy(workload.synthetic_logw(3 << 20, 1.0, seed=6)).to(DEV)
+    assert rs.resample(bigger, "systematic").numel() == 3 << 20  # the cached handle grows
+    bad = torch.tensor([0.0, float("nan")], dtype=torch.float64, device=DEV)
+    with pytest.raises(rs.RsError):
+        rs.resample(bad, "metropolis", B=4)
