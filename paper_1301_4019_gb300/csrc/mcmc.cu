@@ -90,13 +90,14 @@ __device__ __forceinline__ void rejection_run(const T* __restrict__ lw, int64_t 
   }
 }
 
-// Warp w takes the runs w, w + W, ... of kRejRun particles (W = warps of the grid; one run per
-// warp unless COOP, see metropolis_kernel).
+// Warp w takes the runs w, w + W, ... of run_len particles (W = warps of the grid). The host
+// sizes run_len so that every warp gets exactly one run (a warp that took an extra run
+// would set the kernel's length).
 template <typename T, bool COOP>
 __global__ void __launch_bounds__(kBlock)
 rejection_kernel(const T* __restrict__ lw, int64_t N, double log_wmax, bool clamp,
                  int64_t max_trials, Keys keys, int32_t* __restrict__ a,
-                 int32_t* __restrict__ d, unsigned int* bar, int* err) {
+                 int32_t* __restrict__ d, int64_t run_len, unsigned int* bar, int* err) {
   pdl_wait();
   unsigned int target = 0;
   if constexpr (COOP) {
@@ -111,9 +112,9 @@ rejection_kernel(const T* __restrict__ lw, int64_t N, double log_wmax, bool clam
   const RejBound rb = make_bound(log_wmax, clamp);
   const int64_t warps = (static_cast<int64_t>(gridDim.x) * blockDim.x) >> 5;
   for (int64_t run = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
-       run * kRejRun < N; run += warps) {  // uniform across the warp
-    const int64_t start = run * kRejRun;
-    const int64_t end = start + kRejRun < N ? start + kRejRun : N;
+       run * run_len < N; run += warps) {  // uniform across the warp
+    const int64_t start = run * run_len;
+    const int64_t end = start + run_len < N ? start + run_len : N;
     rejection_run(lw, N, start, end, rb, max_trials, keys, a, d, err);
   }
   if constexpr (COOP) grid_exit(bar, target);
@@ -170,9 +171,16 @@ cudaError_t launch_rejection_t(const Scratch& s, const T* lw, int64_t N, double 
   if (s.coop && s.launch_mode != RS_LAUNCH_SEPARATE) {
     const int cap = coop_capacity(reinterpret_cast<const void*>(rejection_kernel<T, true>));
     if (cap > 0) {
+      // runs of at least kRejRun particles, one per warp of a grid of at most `cap` CTAs
+      // (with more runs than warps some warps take two and the kernel waits for them:
+      // measured 7-35 % slower at 2^22)
+      const int grid = static_cast<int>(want < cap ? want : cap);
+      const int64_t warps = static_cast<int64_t>(grid) * (kBlock / 32);
+      int64_t run_len = (N + warps - 1) / warps;
+      run_len = run_len > kRejRun ? run_len : kRejRun;
       trace_mark(s.trace, f64 ? "rejection_f64" : "rejection_f32", st);
-      return coop_launch(rejection_kernel<T, true>, static_cast<int>(want < cap ? want : cap),
-                         st, lw, N, log_wmax, clamp, max_trials, keys, a_out, d, bar, s.err);
+      return coop_launch(rejection_kernel<T, true>, grid, st, lw, N, log_wmax, clamp,
+                         max_trials, keys, a_out, d, run_len, bar, s.err);
     }
   }
   if (d) {
@@ -182,7 +190,7 @@ cudaError_t launch_rejection_t(const Scratch& s, const T* lw, int64_t N, double 
   }
   trace_mark(s.trace, f64 ? "rejection_f64" : "rejection_f32", st);
   launch_pdl(rejection_kernel<T, false>, static_cast<int>(want), kBlock, st, lw, N, log_wmax,
-             clamp, max_trials, keys, a_out, d, bar, s.err);
+             clamp, max_trials, keys, a_out, d, static_cast<int64_t>(kRejRun), bar, s.err);
   return cudaGetLastError();
 }
 
