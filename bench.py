@@ -217,25 +217,25 @@ class ClockSampler:
 # headers it includes, hashed; `traffic` is null once any of them has changed.
 # ---------------------------------------------------------------------------------------
 NCU_TRAFFIC = {  # label: (bytes per launch, source hash)
-               "permute": (8393633, "0684457ff7d53862"),
-               "metropolis_f64": (12600539, "33399ab6e0060ca2"),
-               "metropolis_f32": (8400864, "33399ab6e0060ca2"),
-               "rejection_f64": (8408686, "33399ab6e0060ca2"),
-               "permute_sorted": (8398568, "0684457ff7d53862"),
-               "fused_stratified_f64": (8487040, "a2b9eb1bf5073064"),
-               "rejection_f32": (4209056, "33399ab6e0060ca2"),
-               "fused_multinomial_f64": (8496992, "a2b9eb1bf5073064"),
-               "fused_systematic_f64": (8481664, "a2b9eb1bf5073064"),
-               "fused_stratified_f32": (4261408, "a2b9eb1bf5073064"),
-               "fused_multinomial_f32": (4278720, "a2b9eb1bf5073064"),
-               "fused_systematic_f32": (4260928, "a2b9eb1bf5073064"),
-               "iscan": (4213522, "0684457ff7d53862"),
-               "search_f64": (16783200, "a2d62d32474fc766"),
-               "search_f32": (12591712, "a2d62d32474fc766"),
-               "fill": (8380, "0684457ff7d53862"),
-               "cumoff_to_ancestors": (4199185, "0684457ff7d53862"),
-               "offspring": (8391424, "0684457ff7d53862"),
-               "adjacent_difference": (4197751, "0684457ff7d53862")}
+               "permute": (8392715, "ca0b710fb768ab55"),
+               "metropolis_f64": (12599333, "55e404ad0f565b9e"),
+               "metropolis_f32": (8402432, "55e404ad0f565b9e"),
+               "rejection_f64": (8409490, "55e404ad0f565b9e"),
+               "permute_sorted": (8396848, "ca0b710fb768ab55"),
+               "fused_stratified_f64": (8487360, "1e82f2cf13a41e5d"),
+               "rejection_f32": (4211872, "55e404ad0f565b9e"),
+               "fused_multinomial_f64": (8492960, "1e82f2cf13a41e5d"),
+               "fused_systematic_f64": (8483488, "1e82f2cf13a41e5d"),
+               "fused_stratified_f32": (4268288, "1e82f2cf13a41e5d"),
+               "fused_multinomial_f32": (4279680, "1e82f2cf13a41e5d"),
+               "fused_systematic_f32": (4257536, "1e82f2cf13a41e5d"),
+               "iscan": (4212974, "ca0b710fb768ab55"),
+               "search_f64": (16783552, "d0ae06ee35d821f6"),
+               "search_f32": (12591136, "d0ae06ee35d821f6"),
+               "fill": (8482, "ca0b710fb768ab55"),
+               "cumoff_to_ancestors": (4199782, "ca0b710fb768ab55"),
+               "offspring": (8391205, "ca0b710fb768ab55"),
+               "adjacent_difference": (4197513, "ca0b710fb768ab55")}
 
 _LABEL_FILES = (("fused_", "fused.cu"), ("permute", "aux.cu"), ("iscan", "aux.cu"),
                 ("fill", "aux.cu"), ("offspring", "aux.cu"), ("adjacent", "aux.cu"),
