@@ -301,16 +301,18 @@ def kernel_roofline_units(label: str, N: int, B: int):
         return "alu", B * N, "Philox"              # one Philox4x32-10 draw per step
     if label.startswith("rejection_"):
         return "alu", None, "Philox"
-    if label == "permute":
-        return "hbm", 16 * N, "B"                  # read a, d[i], d[a_i]; write c
+    if label in ("permute", "permute_sorted"):
+        return "hbm", 16 * N, "B"                  # read a, d (claims); write c; claims written
     if label == "fill":
         return "hbm", 4 * N, "B"
     if label == "offspring":
-        return "hbm", 12 * N, "B"
-    if label.startswith("iscan_"):
-        return "hbm", 8 * N, "B"
+        return "hbm", 12 * N, "B"                  # read a, read-modify-write o
+    if label.startswith("iscan"):
+        return "hbm", 8 * N, "B"                   # read o, write O
+    if label == "adjacent_difference":
+        return "hbm", 8 * N, "B"                   # read O, write o
     if label == "cumoff_to_ancestors":
-        return "hbm", 12 * N, "B"
+        return "hbm", 12 * N, "B"                  # read O, write a (and the neighbour read)
     return "hbm", None, "B"
 
 
@@ -459,10 +461,12 @@ def run_ours(args):
         # expected attempts per call: N + sum_i (1 - w_i/w_max) / p, p = mean(w)/w_max
         w = np.exp(pools["f64"][0].double().cpu().numpy())
         amount = int(N + np.sum(1.0 - w) / w.mean())
-    if bound == "hbm" and amount is not None:
-        achieved = amount / (dom_ms * 1e-3) / 1e9
-        roof = {"bound": "hbm", "kernel": dom_label, "achieved": round(achieved, 1),
-                "peak": hbm_peak, "unit": "GB/s", "frac": round(achieved / hbm_peak, 4),
+    if bound == "hbm":
+        achieved = amount / (dom_ms * 1e-3) / 1e9 if amount is not None else None
+        roof = {"bound": "hbm", "kernel": dom_label,
+                "achieved": round(achieved, 1) if achieved is not None else None,
+                "peak": hbm_peak, "unit": "GB/s",
+                "frac": round(achieved / hbm_peak, 4) if achieved is not None else None,
                 "peak_source": peak_src, "traffic": ncu_traffic(dom_label, N),
                 "traffic_note": "ncu dram bytes per launch, cold-cache replay (profiles/)",
                 "algorithmic_bytes_per_launch": amount}

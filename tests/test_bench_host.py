@@ -1,0 +1,45 @@
+"""Host logic of bench.py that needs no GPU: the algorithmic amount behind every roofline, the
+DRAM-traffic table's source hashing, and the sweep's byte counts."""
+import bench
+
+STEP_LABELS = ["fused_multinomial_f32", "fused_stratified_f32", "fused_systematic_f32",
+               "fused_multinomial_f64", "fused_stratified_f64", "fused_systematic_f64",
+               "search_f32", "search_f64", "metropolis_f32", "metropolis_f64",
+               "rejection_f32", "rejection_f64", "permute", "permute_sorted", "fill",
+               "offspring", "iscan", "adjacent_difference", "cumoff_to_ancestors"]
+
+
+def test_every_kernel_of_the_step_has_a_roofline_amount():
+    N, B = 1 << 20, 16
+    for lab in STEP_LABELS:
+        bound, amount, unit = bench.kernel_roofline_units(lab, N, B)
+        assert bound in ("hbm", "alu"), lab
+        if lab.startswith("rejection_"):
+            assert amount is None  # filled in from the expected trial count by run_ours
+        else:
+            assert amount is not None and amount > 0, lab
+    # binary64 inputs move twice the bytes of binary32 ones in the scan kernels
+    assert bench.kernel_roofline_units("fused_systematic_f64", N, B)[1] > \
+        bench.kernel_roofline_units("fused_systematic_f32", N, B)[1]
+    assert bench.kernel_roofline_units("metropolis_f32", N, B) == ("alu", B * N, "Philox")
+
+
+def test_traffic_table_is_keyed_by_the_kernel_sources():
+    for lab in STEP_LABELS:
+        h = bench.kernel_source_hash(lab)
+        assert h is not None and len(h) == 16, lab
+        assert h == bench.kernel_source_hash(lab)  # deterministic
+    # kernels defined in the same translation unit share a hash
+    assert bench.kernel_source_hash("permute") == bench.kernel_source_hash("iscan")
+    assert bench.kernel_source_hash("unknown_kernel") is None
+    assert bench.ncu_traffic("permute", 1 << 18) is None  # captured at 2^20 only
+    for lab, (nbytes, h) in bench.NCU_TRAFFIC.items():
+        assert nbytes > 0 and len(h) == 16, lab
+
+
+def test_sweep_bytes():
+    N = 1 << 10
+    for scheme in range(5):
+        for S in (4, 8):
+            assert bench.sweep_hbm_bytes(scheme, S, N) >= (S + 4 + 16) * N
+    assert bench.sweep_hbm_bytes(0, 4, N) > bench.sweep_hbm_bytes(2, 4, N)  # stored W
