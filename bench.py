@@ -79,6 +79,11 @@ def parse_args():
                    help="partial rejection control: time, trials and outcome ESS over v_max")
     p.add_argument("--metropolis-b", action="store_true",
                    help="Metropolis time and offspring bias over B (fractions of B*)")
+    p.add_argument("--accuracy", action="store_true",
+                   help="the paper's accuracy experiment (Section 4.2): bias share of the MSE "
+                   "and MSE / N of the five resamplers over N and y, binary32 and binary64")
+    p.add_argument("--accuracy-sizes", default="4,8,12,16,18,20,22",
+                   help="log2 N of the accuracy experiment")
     p.add_argument("--single", default=None,
                    help="profile one call: scheme:dtype[:prec], e.g. metropolis:f32 "
                         "(runs warmup + steps calls with Permute, prints one JSON line)")
@@ -581,6 +586,7 @@ def run_ours(args):
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(N, B, args.y, budget_s=20.0)
+        cpu["all_cores"] = cpu_all_cores(N, B, args.y)
 
     if rank == 0:
         line = {
@@ -618,8 +624,9 @@ def run_ours(args):
 # ---------------------------------------------------------------------------------------
 def run_batched(args, dev, world):
     """F filters, sizes log-uniform in [256, 65536], y_f ~ U[0,4], binary32; systematic and
-    Metropolis (per-filter B from Eq. B) each with Permute, one launch per scheme per step,
-    replayed from a CUDA graph. Returns filters/s and particles/s."""
+    Metropolis (per-filter B from Eq. B) each with Permute, one call per scheme per step (nine
+    kernels in all), replayed from a CUDA graph. Returns filters/s, particles/s and the
+    aggregate algorithmic HBM bandwidth."""
     import torch
     import paper_1301_4019_gb300 as rs
     F = args.batched_filters
@@ -688,8 +695,14 @@ def run_batched(args, dev, world):
                         "filter), each with Permute",
             "filters_per_s": round(world * 2 * F / (ms * 1e-3), 1),
             "G_particles_per_s": round(world * 2 * total / (ms * 1e-3) / 1e9, 3),
+            "hbm_GB_per_s": round(world * (sweep_hbm_bytes(2, 4, total)
+                                           + sweep_hbm_bytes(3, 4, total)) / (ms * 1e-3) / 1e9,
+                                  1),
+            "hbm_bytes_note": "algorithmic bytes of both calls with Permute (sweep_hbm_bytes: "
+                              "systematic 28 B, Metropolis 24 B per particle; the Metropolis "
+                              "gathers hit L2 and are not counted)",
             "ms_per_step": round(ms, 4), "particles": total, "kernel_us": kern,
-            "launches_per_step": 4}
+            "launches_per_step": len(kern)}
 
 
 # ---------------------------------------------------------------------------------------
@@ -742,6 +755,49 @@ def cpu_baseline(N, B, y, budget_s=20.0):
             "sample": f"{reps} pass(es) of the full step workload at N=2^{int(math.log2(N))} "
                       f"(5 resamplers x 2 dtypes + Permute), single thread, {el:.1f} s",
             "host": host_info()}
+
+
+_CPU_LW = {}
+
+
+def _cpu_worker_init(N, y):
+    """Process-pool initialiser: the step's two weight vectors, generated once per worker."""
+    _CPU_LW[4] = workload.synthetic_logw(N, y, seed=SEED + 99, dtype=np.float32)
+    _CPU_LW[8] = workload.synthetic_logw(N, y, seed=SEED + 99, dtype=np.float64)
+
+
+def _cpu_task(task):
+    """One resample with Permute by the oracle, single-threaded (scheme < 0: warm-up)."""
+    scheme, S, B, step = task
+    if scheme < 0:
+        return 0
+    import oracle
+    st, a = oracle.resample(scheme, _CPU_LW[S], B=B, seed=SEED, step=step, log_wmax=0.0,
+                            permuted=True)
+    if st != oracle.OK:
+        raise RuntimeError(f"oracle status {st}")
+    return len(a)
+
+
+def cpu_all_cores(N, B, y, steps=3):
+    """The oracle as it stands on every host core: the step's ten resamples are independent,
+    so `steps` steps' calls are spread over one spawned process per core (each call single-
+    threaded). Throughput = ancestors / wall time of the calls, pool start excluded."""
+    import multiprocessing as mp
+    import oracle
+    oracle.build()
+    cores = os.cpu_count() or 1
+    tasks = [(s, S, B, k) for k in range(steps) for S in (8, 4) for s in (3, 4, 0, 1, 2)]
+    ctx = mp.get_context("spawn")  # never fork a process that has used the GPU
+    with ctx.Pool(cores, initializer=_cpu_worker_init, initargs=(N, y)) as pool:
+        pool.map(_cpu_task, [(-1, 4, B, 0)] * (2 * cores), chunksize=1)
+        t0 = time.perf_counter()
+        done = sum(pool.map(_cpu_task, tasks, chunksize=1))
+        el = time.perf_counter() - t0
+    return {"value": round(done / el / 1e9, 6), "unit": UNIT, "cores": cores,
+            "sample": f"{steps} steps of the full step workload at N=2^{int(math.log2(N))} "
+                      f"({len(tasks)} independent oracle calls) over {cores} processes, "
+                      f"{el:.1f} s wall"}
 
 
 def run_reference(args):
@@ -1202,6 +1258,110 @@ def run_metropolis_b(args):
                       "beta of the workload", "rows": rows}))
 
 
+def bias_mse(s1, s2, Npi, R: int):
+    """The accuracy measures of Section 4.2 from R offspring vectors o_1..o_R of one weight
+    vector, given their sums s1_i = sum_r o_ri and s2_i = sum_r o_ri^2 (binary64 tensors or
+    arrays of integers) and N pi_i: ||Bias||^2 = sum_i (mean_r o_ri - N pi_i)^2, tr Var =
+    sum_i of the sample variance of o_i (divisor R), MSE = tr Var + ||Bias||^2 (= the mean
+    over r of sum_i (o_ri - N pi_i)^2). Returns (||Bias||^2, MSE). The variance numerator
+    R s2 - s1^2 is exact while it stays below 2^53."""
+    mean = s1 / R
+    bias2 = float(((mean - Npi) ** 2).sum())
+    trvar = float((R * s2 - s1 * s1).sum()) / (R * R)
+    return bias2, bias2 + trvar
+
+
+def run_accuracy(args):
+    """The accuracy experiment of Section 4.2 (the bias and MSE figures): for each N and y,
+    16 weight vectors, 256 offspring vectors of each resampler per vector; reports the squared
+    bias's share of the MSE and MSE / N, averaged over the 16 vectors, in binary32 (plain and
+    compensated sums) and binary64. Metropolis runs B* of Eq. B (eps = 0.01); the paper's
+    study of B = B*/C (y = 4, C = 1, 2, 4, 8) adds the per-call time (with Permute, L2
+    flushed). Offspring are counted with torch.bincount (statistics only)."""
+    import torch
+    import paper_1301_4019_gb300 as rs
+    V, K = 16, 256
+    sizes = [int(v) for v in args.accuracy_sizes.split(",")]
+    scan = (rs.MULTINOMIAL, rs.STRATIFIED, rs.SYSTEMATIC)
+    every = scan + (rs.METROPOLIS, rs.REJECTION)
+    modes = [("f32", np.float32, rs.PREC_PLAIN, every),
+             ("f32 compensated", np.float32, rs.PREC_COMPENSATED, scan),
+             ("f64", np.float64, rs.PREC_PLAIN, every)]
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device="cuda")
+    rows, brows = [], []
+    t_start = time.perf_counter()
+    with rs.Handle(1 << max(sizes)) as h:
+        for log2n in sizes:
+            N = 1 << log2n
+            CH = max(1, min(K, (1 << 24) // N))  # offspring vectors per counting chunk
+            A = torch.empty((CH, N), dtype=torch.int32, device="cuda")
+            offs = (torch.arange(CH, device="cuda", dtype=torch.int64) * N)[:, None]
+
+            def measure(lw, Npi, scheme, B, prec, v):
+                s1 = torch.zeros(N, dtype=torch.int64, device="cuda")
+                s2 = torch.zeros(N, dtype=torch.int64, device="cuda")
+                for r0 in range(0, K, CH):
+                    m = min(CH, K - r0)
+                    for r in range(m):
+                        rs.rs_resample(h, scheme, lw, B=B, seed=SEED + 13 + v, step=r0 + r,
+                                       out=A[r], prec=prec, log_wmax=0.0)
+                    cnt = torch.bincount((A[:m].long() + offs[:m]).view(-1),
+                                         minlength=m * N).view(m, N)
+                    s1 += cnt.sum(0)
+                    s2 += (cnt * cnt).sum(0)
+                return bias_mse(s1.double(), s2.double(), Npi, K)
+
+            for y in (0.0, 1.0, 2.0, 3.0, 4.0):
+                Bstar = rs.rs_metropolis_B(0.01, workload.beta_estimate(y))
+                Cs = (1, 2, 4, 8) if y == 4.0 else (1,)
+                acc = {}
+                for v in range(V):
+                    lw64 = workload.synthetic_logw(N, y, seed=SEED + 5000 + 131 * log2n
+                                                   + 17 * int(y) + v, dtype=np.float64)
+                    for label, npdt, prec, schemes in modes:
+                        lw = torch.from_numpy(lw64.astype(npdt)).cuda()
+                        lwd = lw.double()
+                        w = torch.exp(lwd - lwd.max())
+                        Npi = N * w / w.sum()
+                        for scheme in schemes:
+                            for Cdiv in (Cs if scheme == rs.METROPOLIS and label == "f32"
+                                         else (1,)):
+                                B = max(1, -(-Bstar // Cdiv))
+                                b2, mse = measure(lw, Npi, scheme, B, prec, v)
+                                acc.setdefault((label, scheme, Cdiv, B), []).append(
+                                    (b2 / mse if mse > 0 else 0.0, mse / N))
+                        del lw, lwd, w, Npi
+                for (label, scheme, Cdiv, B), vals in acc.items():
+                    fr = [a for a, _ in vals]
+                    row = {"log2n": log2n, "y": y, "mode": label,
+                           "scheme": SCHEME_NAMES[scheme], "B": B if scheme == rs.METROPOLIS
+                           else None, "bias_share": float(np.mean(fr)),
+                           "bias_share_max": float(np.max(fr)),
+                           "mse_per_n": float(np.mean([m for _, m in vals]))}
+                    if Cdiv == 1:
+                        rows.append(row)
+                    if scheme == rs.METROPOLIS and label == "f32" and y == 4.0:
+                        lw = torch.from_numpy(workload.synthetic_logw(
+                            N, y, seed=SEED + 5000 + 131 * log2n + 68,
+                            dtype=np.float64).astype(np.float32)).cuda()
+                        ms = _median_call_ms(
+                            lambda k: rs.rs_resample(h, rs.METROPOLIS, lw, B=B, seed=SEED,
+                                                     step=k, out=A[0], permute=True),
+                            11, flush)
+                        brows.append(dict(row, C=Cdiv, us=round(ms * 1e3, 2)))
+                        del lw
+            del A, offs
+        st = rs.rs_last_error(h)
+    if st != rs.RS_OK:
+        raise SystemExit(f"device status after the accuracy study: {rs.rs_strerror(st)}")
+    print(json.dumps({"accuracy": f"{V} weight vectors x {K} offspring vectors per (N, y, "
+                      "scheme, mode); bias_share = ||Bias||^2 / MSE and mse_per_n = MSE / N, "
+                      "means over the weight vectors (bias_share_max: the largest); "
+                      "Metropolis B = B* (Eq. B, eps = 0.01), rejection log w_max = 0",
+                      "seconds": round(time.perf_counter() - t_start, 1),
+                      "rows": rows, "metropolis_b_over_c": brows}))
+
+
 def run_single(args):
     """One resample configuration on one input, for profilers: warmup + steps calls."""
     import torch
@@ -1246,6 +1406,8 @@ def main():
         run_prc(args)
     elif args.metropolis_b:
         run_metropolis_b(args)
+    elif args.accuracy:
+        run_accuracy(args)
     elif args.impl == "reference":
         run_reference(args)
     else:

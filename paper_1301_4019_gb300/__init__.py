@@ -136,13 +136,20 @@ def _stream(stream) -> C.c_void_p:
     return C.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
 
 
-def _dev(t: torch.Tensor, dtype, name: str):
+def _dev(t: torch.Tensor, dtype, name: str, n: int | None = None, h=None):
+    """Device pointer of a contiguous CUDA tensor; with `n`, the tensor must hold at least n
+    elements (the kernels read or write n of them); with `h`, it must live on the handle's
+    device."""
     if not isinstance(t, torch.Tensor) or not t.is_cuda:
         raise TypeError(f"{name} must be a CUDA tensor")
     if dtype is not None and t.dtype not in (dtype if isinstance(dtype, tuple) else (dtype,)):
         raise TypeError(f"{name} has dtype {t.dtype}")
     if not t.is_contiguous():
         raise ValueError(f"{name} must be contiguous")
+    if n is not None and t.numel() < n:
+        raise ValueError(f"{name} holds {t.numel()} elements, {n} needed")
+    if h is not None and t.device.index != h.device:
+        raise ValueError(f"{name} is on {t.device}, the handle on cuda:{h.device}")
     return C.c_void_p(t.data_ptr())
 
 
@@ -200,9 +207,10 @@ def rs_resample(h: Handle, scheme: int, logw: torch.Tensor, B: int = 0, seed: in
         out = torch.empty(N, dtype=torch.int32, device=logw.device)
     opts = _Opts(prec, float(log_wmax), int(max_trials), int(filter))
     _check(load().rs_resample(h.ptr, int(scheme), _dtype_code(logw),
-                              _dev(logw, (torch.float32, torch.float64), "logw"), N, int(B),
-                              int(seed) & 0xFFFFFFFFFFFFFFFF, int(step) & 0xFFFFFFFFFFFFFFFF,
-                              _dev(out, torch.int32, "out"), 1 if permute else 0,
+                              _dev(logw, (torch.float32, torch.float64), "logw", h=h), N,
+                              int(B), int(seed) & 0xFFFFFFFFFFFFFFFF,
+                              int(step) & 0xFFFFFFFFFFFFFFFF,
+                              _dev(out, torch.int32, "out", N, h), 1 if permute else 0,
                               C.byref(opts), _stream(stream)), "rs_resample")
     return out
 
@@ -219,11 +227,12 @@ def rs_resample_prc(h: Handle, logw: torch.Tensor, log_vmax: float, seed: int = 
     if logw_out is None:
         logw_out = torch.empty_like(logw)
     _check(load().rs_resample_prc(h.ptr, _dtype_code(logw),
-                                  _dev(logw, (torch.float32, torch.float64), "logw"), N,
+                                  _dev(logw, (torch.float32, torch.float64), "logw", h=h), N,
                                   float(log_vmax), int(max_trials),
                                   int(seed) & 0xFFFFFFFFFFFFFFFF, int(step) & 0xFFFFFFFFFFFFFFFF,
-                                  int(filter), _dev(out, torch.int32, "out"),
-                                  _dev(logw_out, logw.dtype, "logw_out"), 1 if permute else 0,
+                                  int(filter), _dev(out, torch.int32, "out", N, h),
+                                  _dev(logw_out, logw.dtype, "logw_out", N, h),
+                                  1 if permute else 0,
                                   _stream(stream)), "rs_resample_prc")
     return out, logw_out
 
@@ -239,14 +248,17 @@ def rs_resample_batched(h: Handle, scheme: int, logw: torch.Tensor, offsets: tor
     if out is None:
         out = torch.empty(logw.numel(), dtype=torch.int32, device=logw.device)
     opts = _Opts(prec, float(log_wmax), int(max_trials), 0)
-    bptr = _dev(B_per_filter, torch.int32, "B_per_filter") if B_per_filter is not None else None
+    bptr = (_dev(B_per_filter, torch.int32, "B_per_filter", F, h)
+            if B_per_filter is not None else None)
     _check(load().rs_resample_batched(h.ptr, int(scheme), _dtype_code(logw),
-                                      _dev(logw, (torch.float32, torch.float64), "logw"),
-                                      _dev(offsets, torch.int64, "offsets"), F, bptr, int(B),
+                                      _dev(logw, (torch.float32, torch.float64), "logw", h=h),
+                                      _dev(offsets, torch.int64, "offsets", F + 1, h), F, bptr,
+                                      int(B),
                                       int(seed) & 0xFFFFFFFFFFFFFFFF,
                                       int(step) & 0xFFFFFFFFFFFFFFFF,
-                                      _dev(out, torch.int32, "out"), 1 if permute else 0,
-                                      C.byref(opts), _stream(stream)), "rs_resample_batched")
+                                      _dev(out, torch.int32, "out", logw.numel(), h),
+                                      1 if permute else 0, C.byref(opts), _stream(stream)),
+           "rs_resample_batched")
     return out
 
 
@@ -260,8 +272,9 @@ def rs_cumulative_weights(h: Handle, logw: torch.Tensor, prec: int = PREC_PLAIN,
     if log_total is None:
         log_total = torch.empty(1, dtype=torch.float64, device=logw.device)
     _check(load().rs_cumulative_weights(h.ptr, _dtype_code(logw), int(prec),
-                                        _dev(logw, None, "logw"), N, _dev(W, logw.dtype, "W"),
-                                        _dev(log_total, torch.float64, "log_total"),
+                                        _dev(logw, None, "logw", h=h), N,
+                                        _dev(W, logw.dtype, "W", N, h),
+                                        _dev(log_total, torch.float64, "log_total", 1, h),
                                         _stream(stream)), "rs_cumulative_weights")
     return W, log_total
 
@@ -277,9 +290,9 @@ def rs_cumulative_weights_f64(h: Handle, logw: torch.Tensor, prec: int = PREC_PL
     if log_total is None:
         log_total = torch.empty(1, dtype=torch.float64, device=logw.device)
     _check(load().rs_cumulative_weights_f64(h.ptr, _dtype_code(logw), int(prec),
-                                            _dev(logw, None, "logw"), N,
-                                            _dev(W, torch.float64, "W"),
-                                            _dev(log_total, torch.float64, "log_total"),
+                                            _dev(logw, None, "logw", h=h), N,
+                                            _dev(W, torch.float64, "W", N, h),
+                                            _dev(log_total, torch.float64, "log_total", 1, h),
                                             _stream(stream)), "rs_cumulative_weights_f64")
     return W, log_total
 
@@ -289,8 +302,8 @@ def rs_offspring(h: Handle, a: torch.Tensor, o: torch.Tensor | None = None, stre
     N = a.numel()
     if o is None:
         o = torch.empty(N, dtype=torch.int32, device=a.device)
-    _check(load().rs_offspring(h.ptr, _dev(a, torch.int32, "a"), N, _dev(o, torch.int32, "o"),
-                               _stream(stream)), "rs_offspring")
+    _check(load().rs_offspring(h.ptr, _dev(a, torch.int32, "a", h=h), N,
+                               _dev(o, torch.int32, "o", N, h), _stream(stream)), "rs_offspring")
     return o
 
 
@@ -300,8 +313,8 @@ def rs_cumulative_offspring(h: Handle, o: torch.Tensor, O: torch.Tensor | None =
     N = o.numel()
     if O is None:
         O = torch.empty(N, dtype=torch.int32, device=o.device)
-    _check(load().rs_cumulative_offspring(h.ptr, _dev(o, torch.int32, "o"), N,
-                                          _dev(O, torch.int32, "O"), _stream(stream)),
+    _check(load().rs_cumulative_offspring(h.ptr, _dev(o, torch.int32, "o", h=h), N,
+                                          _dev(O, torch.int32, "O", N, h), _stream(stream)),
            "rs_cumulative_offspring")
     return O
 
@@ -312,8 +325,8 @@ def rs_adjacent_difference(h: Handle, O: torch.Tensor, o: torch.Tensor | None = 
     N = O.numel()
     if o is None:
         o = torch.empty(N, dtype=torch.int32, device=O.device)
-    _check(load().rs_adjacent_difference(h.ptr, _dev(O, torch.int32, "O"), N,
-                                         _dev(o, torch.int32, "o"), _stream(stream)),
+    _check(load().rs_adjacent_difference(h.ptr, _dev(O, torch.int32, "O", h=h), N,
+                                         _dev(o, torch.int32, "o", N, h), _stream(stream)),
            "rs_adjacent_difference")
     return o
 
@@ -324,8 +337,8 @@ def rs_cumulative_offspring_to_ancestors(h: Handle, O: torch.Tensor,
     N = O.numel()
     if a is None:
         a = torch.empty(N, dtype=torch.int32, device=O.device)
-    _check(load().rs_cumulative_offspring_to_ancestors(h.ptr, _dev(O, torch.int32, "O"), N,
-                                                       _dev(a, torch.int32, "a"),
+    _check(load().rs_cumulative_offspring_to_ancestors(h.ptr, _dev(O, torch.int32, "O", h=h),
+                                                       N, _dev(a, torch.int32, "a", N, h),
                                                        _stream(stream)),
            "rs_cumulative_offspring_to_ancestors")
     return a
@@ -336,8 +349,9 @@ def rs_prepermute(h: Handle, a: torch.Tensor, d: torch.Tensor | None = None, str
     N = a.numel()
     if d is None:
         d = torch.empty(N, dtype=torch.int32, device=a.device)
-    _check(load().rs_prepermute(h.ptr, _dev(a, torch.int32, "a"), N, _dev(d, torch.int32, "d"),
-                                _stream(stream)), "rs_prepermute")
+    _check(load().rs_prepermute(h.ptr, _dev(a, torch.int32, "a", h=h), N,
+                                _dev(d, torch.int32, "d", N, h), _stream(stream)),
+           "rs_prepermute")
     return d
 
 
@@ -346,8 +360,8 @@ def rs_permute(h: Handle, a: torch.Tensor, c: torch.Tensor | None = None, stream
     N = a.numel()
     if c is None:
         c = torch.empty(N, dtype=torch.int32, device=a.device)
-    _check(load().rs_permute(h.ptr, _dev(a, torch.int32, "a"), N, _dev(c, torch.int32, "c"),
-                             _stream(stream)), "rs_permute")
+    _check(load().rs_permute(h.ptr, _dev(a, torch.int32, "a", h=h), N,
+                             _dev(c, torch.int32, "c", N, h), _stream(stream)), "rs_permute")
     return c
 
 
@@ -363,20 +377,22 @@ def rs_ess(h: Handle, logw: torch.Tensor, out: torch.Tensor | None = None,
     the device); with ``log_total``, also max logw + log sum w there."""
     if out is None:
         out = torch.empty(1, dtype=torch.float64, device=logw.device)
-    lt = _dev(log_total, torch.float64, "log_total") if log_total is not None else None
-    _check(load().rs_ess(h.ptr, _dtype_code(logw), _dev(logw, None, "logw"), logw.numel(),
-                         _dev(out, torch.float64, "ess"), lt, _stream(stream)), "rs_ess")
+    lt = _dev(log_total, torch.float64, "log_total", 1, h) if log_total is not None else None
+    _check(load().rs_ess(h.ptr, _dtype_code(logw), _dev(logw, None, "logw", h=h), logw.numel(),
+                         _dev(out, torch.float64, "ess", 1, h), lt, _stream(stream)), "rs_ess")
     return out
 
 
 def rs_copy_ancestors(h: Handle, x: torch.Tensor, c: torch.Tensor, stream=None) -> torch.Tensor:
     """In place: row i of x ([N] or [N, D] float32) becomes row c[i] (c from Permute)."""
     N = c.numel()
+    if x.dim() not in (1, 2):
+        raise ValueError("x must be [N] or [N, D]")
     D = 1 if x.dim() == 1 else x.shape[1]
     if x.shape[0] != N:
         raise ValueError("x and c disagree on N")
-    _check(load().rs_copy_ancestors(h.ptr, _dev(x, torch.float32, "x"), D,
-                                    _dev(c, torch.int32, "c"), N, _stream(stream)),
+    _check(load().rs_copy_ancestors(h.ptr, _dev(x, torch.float32, "x", h=h), D,
+                                    _dev(c, torch.int32, "c", h=h), N, _stream(stream)),
            "rs_copy_ancestors")
     return x
 
@@ -390,11 +406,11 @@ def rs_lgssm_step(h: Handle, x: torch.Tensor, init: bool, phi: float, sigma_x: f
     N = x.numel()
     if logw is None:
         logw = torch.empty(N, dtype=torch.float32, device=x.device)
-    _check(load().rs_lgssm_step(h.ptr, _dev(x, torch.float32, "x"), N, int(bool(init)),
+    _check(load().rs_lgssm_step(h.ptr, _dev(x, torch.float32, "x", h=h), N, int(bool(init)),
                                 int(bool(accumulate)),
                                 float(phi), float(sigma_x), float(y), float(sigma_y),
                                 int(seed), int(step), int(filter),
-                                _dev(logw, torch.float32, "logw"), _stream(stream)),
+                                _dev(logw, torch.float32, "logw", N, h), _stream(stream)),
            "rs_lgssm_step")
     return logw
 
@@ -403,9 +419,11 @@ def rs_copy_ancestors_batched(h: Handle, x: torch.Tensor, c: torch.Tensor,
                               offsets: torch.Tensor, stream=None) -> torch.Tensor:
     """In-place copy x[g] <- x[offsets[f] + c[g]] of every filter f (c: local ancestors)."""
     D = 1 if x.dim() == 1 else int(np.prod(x.shape[1:]))
-    _check(load().rs_copy_ancestors_batched(h.ptr, _dev(x, torch.float32, "x"), D,
-                                            _dev(c, torch.int32, "c"),
-                                            _dev(offsets, torch.int64, "offsets"),
+    if c.numel() != x.shape[0]:
+        raise ValueError("x and c disagree on the number of particles")
+    _check(load().rs_copy_ancestors_batched(h.ptr, _dev(x, torch.float32, "x", h=h), D,
+                                            _dev(c, torch.int32, "c", h=h),
+                                            _dev(offsets, torch.int64, "offsets", 1, h),
                                             offsets.numel() - 1, _stream(stream)),
            "rs_copy_ancestors_batched")
     return x
@@ -419,14 +437,16 @@ def rs_lgssm_step_batched(h: Handle, x: torch.Tensor, offsets: torch.Tensor, ini
     filter, float32 on the device)."""
     if logw is None:
         logw = torch.empty_like(x)
-    _check(load().rs_lgssm_step_batched(h.ptr, _dev(x, torch.float32, "x"),
-                                        _dev(offsets, torch.int64, "offsets"),
-                                        offsets.numel() - 1, 1 if init else 0,
+    F = offsets.numel() - 1
+    _check(load().rs_lgssm_step_batched(h.ptr, _dev(x, torch.float32, "x", h=h),
+                                        _dev(offsets, torch.int64, "offsets", 1, h),
+                                        F, 1 if init else 0,
                                         1 if accumulate else 0, float(phi), float(sigma_x),
-                                        _dev(y, torch.float32, "y"), float(sigma_y),
+                                        _dev(y, torch.float32, "y", F, h), float(sigma_y),
                                         int(seed) & 0xFFFFFFFFFFFFFFFF,
                                         int(step) & 0xFFFFFFFFFFFFFFFF,
-                                        _dev(logw, torch.float32, "logw"), _stream(stream)),
+                                        _dev(logw, torch.float32, "logw", x.numel(), h),
+                                        _stream(stream)),
            "rs_lgssm_step_batched")
     return logw
 
@@ -437,9 +457,11 @@ def rs_log_sum_weights_batched(h: Handle, logw: torch.Tensor, offsets: torch.Ten
     F = offsets.numel() - 1
     if out is None:
         out = torch.empty(F, dtype=torch.float64, device=logw.device)
-    _check(load().rs_log_sum_weights_batched(h.ptr, _dtype_code(logw), _dev(logw, None, "logw"),
-                                             _dev(offsets, torch.int64, "offsets"), F,
-                                             _dev(out, torch.float64, "out"), _stream(stream)),
+    _check(load().rs_log_sum_weights_batched(h.ptr, _dtype_code(logw),
+                                             _dev(logw, None, "logw", h=h),
+                                             _dev(offsets, torch.int64, "offsets", F + 1, h), F,
+                                             _dev(out, torch.float64, "out", F, h),
+                                             _stream(stream)),
            "rs_log_sum_weights_batched")
     return out
 
@@ -448,7 +470,7 @@ def rs_capture_if_below(h: Handle, value: torch.Tensor, threshold: float, stream
     """Inside a CUDA graph capture on `stream`: open a conditional body that runs when
     value[0] < threshold on the device; returns the stream to capture the body on."""
     body = C.c_void_p()
-    _check(load().rs_capture_if_below(h.ptr, _dev(value, torch.float64, "value"),
+    _check(load().rs_capture_if_below(h.ptr, _dev(value, torch.float64, "value", 1, h),
                                       float(threshold), _stream(stream), C.byref(body)),
            "rs_capture_if_below")
     return torch.cuda.ExternalStream(body.value)
@@ -461,9 +483,10 @@ def rs_capture_end_if(h: Handle, stream=None) -> None:
 def rs_smc_mark_resampled(h: Handle, logw: torch.Tensor, base: torch.Tensor, log_n: float,
                           count: torch.Tensor | None = None, stream=None) -> None:
     """After a resampling: log-weights 0, likelihood base log N, resampling count + 1."""
-    _check(load().rs_smc_mark_resampled(h.ptr, _dev(logw, torch.float32, "logw"), logw.numel(),
-                                        _dev(base, torch.float64, "base"), float(log_n),
-                                        _dev(count, torch.int32, "count")
+    _check(load().rs_smc_mark_resampled(h.ptr, _dev(logw, torch.float32, "logw", h=h),
+                                        logw.numel(),
+                                        _dev(base, torch.float64, "base", 1, h), float(log_n),
+                                        _dev(count, torch.int32, "count", 1, h)
                                         if count is not None else None, _stream(stream)),
            "rs_smc_mark_resampled")
 
@@ -472,10 +495,10 @@ def rs_smc_loglik_step(h: Handle, lse: torch.Tensor, base: torch.Tensor, ll: tor
                        c: float, log_n: float, first: bool, count: torch.Tensor | None = None,
                        stream=None) -> None:
     """ll += (lse - base) - c, base = lse (first step: ll = (lse - log N) - c, count = 0)."""
-    _check(load().rs_smc_loglik_step(h.ptr, _dev(lse, torch.float64, "lse"),
-                                     _dev(base, torch.float64, "base"),
-                                     _dev(ll, torch.float64, "ll"),
-                                     _dev(count, torch.int32, "count")
+    _check(load().rs_smc_loglik_step(h.ptr, _dev(lse, torch.float64, "lse", 1, h),
+                                     _dev(base, torch.float64, "base", 1, h),
+                                     _dev(ll, torch.float64, "ll", 1, h),
+                                     _dev(count, torch.int32, "count", 1, h)
                                      if count is not None else None, float(c), float(log_n),
                                      1 if first else 0, _stream(stream)), "rs_smc_loglik_step")
 
@@ -515,11 +538,12 @@ def rs_systematic_noalloc(logw: torch.Tensor, seed: int = 0, step: int = 0,
     N = logw.numel()
     if out is None:
         out = torch.empty(N, dtype=torch.int32, device=logw.device)
-    st_ptr = _dev(status, torch.int32, "status") if status is not None else None
+    st_ptr = _dev(status, torch.int32, "status", 1) if status is not None else None
     _check(load().rs_systematic_noalloc(_dtype_code(logw), _dev(logw, None, "logw"), N,
                                         int(seed) & 0xFFFFFFFFFFFFFFFF,
                                         int(step) & 0xFFFFFFFFFFFFFFFF,
-                                        _dev(out, torch.int32, "out"), st_ptr, _stream(stream)),
+                                        _dev(out, torch.int32, "out", N), st_ptr,
+                                        _stream(stream)),
            "rs_systematic_noalloc")
     return out
 

@@ -1,5 +1,7 @@
 """Host logic of bench.py that needs no GPU: the algorithmic amount behind every roofline, the
 DRAM-traffic table's source hashing, and the sweep's byte counts."""
+import pytest
+
 import bench
 
 STEP_LABELS = ["fused_multinomial_f32", "fused_stratified_f32", "fused_systematic_f32",
@@ -43,3 +45,26 @@ def test_sweep_bytes():
         for S in (4, 8):
             assert bench.sweep_hbm_bytes(scheme, S, N) >= (S + 4 + 16) * N
     assert bench.sweep_hbm_bytes(0, 4, N) > bench.sweep_hbm_bytes(2, 4, N)  # stored W
+
+
+def test_bias_mse_decomposition():
+    """||Bias||^2 + tr Var (divisor R) equals the mean squared error over the R vectors."""
+    import numpy as np
+    rng = np.random.default_rng(4)
+    R, N = 7, 5
+    o = rng.integers(0, 4, size=(R, N))
+    Npi = rng.uniform(0.5, 1.5, size=N)
+    b2, mse = bench.bias_mse(o.sum(0) * 1.0, (o * o).sum(0) * 1.0, Npi, R)
+    assert mse == pytest.approx(np.mean(((o - Npi) ** 2).sum(1)), rel=1e-12)
+    assert b2 == pytest.approx(((o.mean(0) - Npi) ** 2).sum(), rel=1e-12)
+    # identical vectors: no variance, the whole error is bias
+    same = np.tile(o[:1], (R, 1))
+    b2, mse = bench.bias_mse(same.sum(0) * 1.0, (same * same).sum(0) * 1.0, Npi, R)
+    assert b2 == pytest.approx(mse, rel=1e-12)
+
+
+def test_cpu_baseline_on_all_cores_runs_the_oracle():
+    import os
+    r = bench.cpu_all_cores(1 << 10, 4, 2.0, steps=1)
+    assert r["value"] > 0 and r["cores"] == (os.cpu_count() or 1)
+    assert "10 independent oracle calls" in r["sample"]

@@ -431,6 +431,34 @@ def test_argument_checks_on_the_device_path(rs, h):
     assert a.cpu().tolist() == list(range(8))
 
 
+def test_binding_refuses_short_output_buffers(rs, h):
+    """The binding checks every caller buffer's length against what the kernels write before
+    calling the library: a short buffer raises ValueError and nothing is launched."""
+    lw = torch.zeros(64, dtype=torch.float32, device=DEV)
+    short = torch.empty(63, dtype=torch.int32, device=DEV)
+    with pytest.raises(ValueError):
+        rs.rs_resample(h, rs.SYSTEMATIC, lw, out=short)
+    with pytest.raises(ValueError):
+        rs.rs_resample_prc(h, lw, -1.0, out=short)
+    with pytest.raises(ValueError):
+        rs.rs_offspring(h, torch.zeros(64, dtype=torch.int32, device=DEV), short)
+    with pytest.raises(ValueError):
+        rs.rs_permute(h, torch.zeros(64, dtype=torch.int32, device=DEV), short)
+    with pytest.raises(ValueError):
+        rs.rs_cumulative_weights(h, lw, W=torch.empty(63, dtype=torch.float32, device=DEV))
+    with pytest.raises(ValueError):
+        rs.rs_ess(h, lw, out=torch.empty(0, dtype=torch.float64, device=DEV))
+    offs = torch.tensor([0, 32, 64], dtype=torch.int64, device=DEV)
+    with pytest.raises(ValueError):
+        rs.rs_resample_batched(h, rs.SYSTEMATIC, lw, offs, out=short)
+    with pytest.raises(ValueError):
+        rs.rs_log_sum_weights_batched(h, lw, offs,
+                                      out=torch.empty(1, dtype=torch.float64, device=DEV))
+    a = rs.rs_resample(h, rs.SYSTEMATIC, lw)
+    assert rs.rs_last_error(h) == rs.RS_OK
+    assert a.cpu().tolist() == list(range(64))
+
+
 def test_convenience_resample_matches_the_handle_call(rs, h):
     lw = torch.from_numpy(workload.synthetic_logw(70001, 2.0, seed=5)).to(DEV)
     for name in ("multinomial", "stratified", "systematic", "metropolis", "rejection"):
