@@ -71,7 +71,8 @@ def parse_args():
     p.add_argument("--precision", action="store_true",
                    help="offspring bias of the scan schemes: binary32 plain vs compensated vs "
                         "binary64, N = 2^16 .. 2^24, y in {0, 2, 4}; one JSON line")
-    p.add_argument("--precision-reps", type=int, default=400)
+    p.add_argument("--precision-reps", type=int, default=1000)
+    p.add_argument("--metropolis-b-reps", type=int, default=400)
     p.add_argument("--smc", action="store_true",
                    help="full bootstrap SMC loop (Code 1) on the linear-Gaussian model, "
                         "N = 2^20, T = 100, systematic / Metropolis / rejection; one JSON line")
@@ -942,8 +943,10 @@ def run_sweep(args):
 def run_precision(args):
     """Mean absolute offspring bias mean_i |mean_r o_i - N pi_i| over R repeats (seeds differ
     by the step counter) of one weight set, against the Monte Carlo noise floor
-    sqrt(mean_i Var(o_i) / R); pi from the input log-weights in binary64 (numpy). The
-    offspring are counted on the GPU (rs_offspring) and summed there."""
+    sqrt(mean_i Var(o_i) / R), and the squared bias's share of the MSE (bias_mse); pi from
+    the input log-weights in binary64 (numpy). The scan-based schemes run in every precision
+    mode, Metropolis (B* of Eq. B) and rejection (log w_max = 0) in binary32. The offspring
+    are counted on the GPU (rs_offspring) and summed there."""
     import torch
     import paper_1301_4019_gb300 as rs
     R = args.precision_reps
@@ -962,22 +965,29 @@ def run_precision(args):
                     w = np.exp(lw_in.astype(np.float64) - lw_in.max())
                     Npi = torch.from_numpy(N * w / math.fsum(w)).cuda()
                     lw = torch.from_numpy(lw_in).cuda()
-                    for scheme in (rs.MULTINOMIAL, rs.STRATIFIED, rs.SYSTEMATIC):
+                    schemes = [rs.MULTINOMIAL, rs.STRATIFIED, rs.SYSTEMATIC]
+                    if label == "f32 plain":
+                        schemes += [rs.METROPOLIS, rs.REJECTION]
+                    B = rs.rs_metropolis_B(0.01, workload.beta_estimate(y))
+                    for scheme in schemes:
                         s1 = torch.zeros(N, dtype=torch.float64, device="cuda")
                         s2 = torch.zeros(N, dtype=torch.float64, device="cuda")
                         for r in range(R):
-                            rs.rs_resample(h, scheme, lw, seed=SEED + 7, step=r, out=out,
-                                           prec=prec)
+                            rs.rs_resample(h, scheme, lw, B=B, seed=SEED + 7, step=r, out=out,
+                                           prec=prec, log_wmax=0.0)
                             rs.rs_offspring(h, out, o)
                             od = o.double()
                             s1 += od
                             s2 += od * od
                         mean = s1 / R
                         var = (s2 / R - mean * mean).clamp_min(0) * R / max(R - 1, 1)
+                        b2, mse = bias_mse(s1, s2, Npi, R)
                         rows.append({"log2n": log2n, "y": y, "mode": label,
                                      "scheme": SCHEME_NAMES[scheme],
+                                     "B": B if scheme == rs.METROPOLIS else None,
                                      "mean_abs_bias": float((mean - Npi).abs().mean()),
-                                     "noise_floor": float(torch.sqrt(var.mean() / R))})
+                                     "noise_floor": float(torch.sqrt(var.mean() / R)),
+                                     "bias_share": b2 / mse if mse > 0 else 0.0})
                     del lw, Npi
         # deterministic part: the expected offspring given the kernel's own cumulative
         # weights, E_u[o_i] = r_i - r_{i-1} with r_i = N W_i / W_N (Section 4.2's measure without
@@ -1005,7 +1015,10 @@ def run_precision(args):
         raise SystemExit(f"device status after precision study: {rs.rs_strerror(st)}")
     print(json.dumps({"precision": f"{R} repeats per row (seed fixed, step = repeat index); "
                       "bias = mean_i |mean o_i - N pi_i|, pi from the input log-weights in "
-                      "binary64; noise floor = sqrt(mean_i Var(o_i) / R)", "rows": rows,
+                      "binary64; noise floor = sqrt(mean_i Var(o_i) / R); bias_share = "
+                      "||Bias||^2 / MSE (Section 4.2; about 1/R for an unbiased scheme); "
+                      "Metropolis B = B* (Eq. B), rejection log w_max = 0, both binary32",
+                      "rows": rows,
                       "deterministic": "E_u[o_i] - N pi_i from the kernel's cumulative weights "
                       "(rs_cumulative_weights_f64): r_i = N W_i / W_N in binary64; mean and max "
                       "over i of |r_i - r_{i-1} - N pi_i|", "det_rows": det}))
@@ -1214,7 +1227,7 @@ def run_metropolis_b(args):
     (1 - beta)^B of Section 2.1 beside it."""
     import torch
     import paper_1301_4019_gb300 as rs
-    R = args.precision_reps
+    R = args.metropolis_b_reps
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device="cuda")
     rows = []
     N = 1 << 20

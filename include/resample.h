@@ -307,6 +307,18 @@ int rs_log_sum_weights_batched(rs_handle* h, int dtype, const void* logw_dev,
                                const int64_t* offsets_dev, int32_t F, double* out_dev,
                                void* stream);
 
+/* The effective sample size of every filter of a batch (offsets_dev: F+1 int64 CSR bounds,
+ * as for rs_resample_batched): ess_dev[f] = (sum_g w_g)^2 / sum_g w_g^2 over the filter's
+ * particles g with w_g = exp(logw_g - max logw), the statistic that decides per filter
+ * whether an adaptive filter resamples at a step (Section 4.3), and log_total_dev[f] = the
+ * value rs_log_sum_weights_batched writes (same sums, bit for bit). F float64 each on the
+ * device; either pointer may be NULL, not both. One CTA per filter, the same arithmetic as
+ * rs_log_sum_weights_batched with the sum of squares beside the sum. An empty or all-zero
+ * filter gets ess 0 and log total -inf (no error); NaN/+inf flag RS_ERR_NONFINITE; offsets
+ * outside [0, the handle's max_n] flag RS_ERR_ARG. */
+int rs_ess_batched(rs_handle* h, int dtype, const void* logw_dev, const int64_t* offsets_dev,
+                   int32_t F, double* ess_dev, double* log_total_dev, void* stream);
+
 /* B* = log(eps) / log(1 - beta) of Eq. (B) (Section 2.1), rounded up: the number of
  * Metropolis steps that bounds the total-variation distance of every chain by eps, for a
  * lower bound beta on min_i(mean(w)/w^i) (Eq. beta), e.g. E(w)/w_max (Eq. beta2).

@@ -42,7 +42,8 @@ EXPORTED = [
     "rs_trace", "rs_trace_count", "rs_trace_label", "rs_systematic_noalloc",
     "rs_resample_batched", "rs_set_launch_mode", "rs_copy_ancestors", "rs_lgssm_step",
     "rs_ess", "rs_resample_prc", "rs_copy_ancestors_batched", "rs_lgssm_step_batched",
-    "rs_log_sum_weights_batched", "rs_cumulative_weights_f64", "rs_capture_if_below",
+    "rs_log_sum_weights_batched", "rs_ess_batched", "rs_cumulative_weights_f64",
+    "rs_capture_if_below",
     "rs_capture_end_if", "rs_smc_mark_resampled", "rs_smc_loglik_step",
 ]
 NOALLOC_MAX_N = 1 << 22
@@ -110,6 +111,7 @@ def _declare(lib):
         "rs_lgssm_step_batched": (I, [P, P, P, I32, I, I, C.c_float, C.c_float, P, C.c_float,
                                       U64, U64, P, P]),
         "rs_log_sum_weights_batched": (I, [P, I, P, P, I32, P, P]),
+        "rs_ess_batched": (I, [P, I, P, P, I32, P, P, P]),
         "rs_capture_if_below": (I, [P, P, C.c_double, P, C.POINTER(P)]),
         "rs_capture_end_if": (I, [P, P]),
         "rs_smc_mark_resampled": (I, [P, P, I64, P, C.c_double, P, P]),
@@ -463,6 +465,22 @@ def rs_log_sum_weights_batched(h: Handle, logw: torch.Tensor, offsets: torch.Ten
                                              _dev(out, torch.float64, "out", F, h),
                                              _stream(stream)),
            "rs_log_sum_weights_batched")
+    return out
+
+
+def rs_ess_batched(h: Handle, logw: torch.Tensor, offsets: torch.Tensor,
+                   out: torch.Tensor | None = None, log_total: torch.Tensor | None = None,
+                   stream=None) -> torch.Tensor:
+    """Effective sample size of every filter (float64, one per filter); with ``log_total``
+    (F float64), also each filter's log weight total (as rs_log_sum_weights_batched)."""
+    F = offsets.numel() - 1
+    if out is None:
+        out = torch.empty(F, dtype=torch.float64, device=logw.device)
+    lt = _dev(log_total, torch.float64, "log_total", F, h) if log_total is not None else None
+    _check(load().rs_ess_batched(h.ptr, _dtype_code(logw), _dev(logw, None, "logw", h=h),
+                                 _dev(offsets, torch.int64, "offsets", F + 1, h), F,
+                                 _dev(out, torch.float64, "ess", F, h), lt, _stream(stream)),
+           "rs_ess_batched")
     return out
 
 

@@ -478,7 +478,21 @@ int rs_log_sum_weights_batched(rs_handle* h, int dtype, const void* logw_dev,
   int st = set_device(h);
   if (st != RS_OK) return st;
   const cudaError_t e = rsk::launch_log_sum_batched(h->s, dtype == RS_F64, logw_dev, offsets_dev,
-                                                    F, out_dev, as_stream(stream));
+                                                    F, out_dev, nullptr, as_stream(stream));
+  end_mark(h, as_stream(stream));
+  return cuda_status(e);
+}
+
+int rs_ess_batched(rs_handle* h, int dtype, const void* logw_dev, const int64_t* offsets_dev,
+                   int32_t F, double* ess_dev, double* log_total_dev, void* stream) {
+  if (!h || !logw_dev || !offsets_dev || (!ess_dev && !log_total_dev) || F < 1)
+    return RS_ERR_ARG;
+  if (dtype != RS_F32 && dtype != RS_F64) return RS_ERR_ARG;
+  if (F > INT_MAX / 2) return RS_ERR_ARG;
+  int st = set_device(h);
+  if (st != RS_OK) return st;
+  const cudaError_t e = rsk::launch_log_sum_batched(h->s, dtype == RS_F64, logw_dev, offsets_dev,
+                                                    F, log_total_dev, ess_dev, as_stream(stream));
   end_mark(h, as_stream(stream));
   return cuda_status(e);
 }

@@ -147,7 +147,8 @@ cudaError_t launch_loglik_step(const Scratch& s, const double* lse, double* base
                                int32_t* count, double c, double log_n, int first,
                                cudaStream_t st);
 cudaError_t launch_log_sum_batched(const Scratch& s, bool f64, const void* logw,
-                                   const int64_t* offsets, int F, double* out, cudaStream_t st);
+                                   const int64_t* offsets, int F, double* out, double* ess,
+                                   cudaStream_t st);
 cudaError_t launch_copy_ancestors(const Scratch& s, float* x, int D, const int32_t* c, int64_t N,
                                   cudaStream_t st);
 cudaError_t launch_lgssm_step(const Scratch& s, float* x, int64_t N, int init, int accumulate,

@@ -114,24 +114,32 @@ lgssm_step_batched_kernel(float* __restrict__ x, const int64_t* __restrict__ off
   logw[g] = accumulate ? logw[g] + l : l;
 }
 
-// Per-thread sum of the max-shifted weights: two-float for binary32 log-weights (no binary64
-// arithmetic per particle), binary64 for binary64 ones.
-__device__ __forceinline__ void lse_acc(float2& acc, float x, float m) {
-  acc = add21(acc, expf(x - m));
+// Per-thread sums of the max-shifted weights w and of w^2: two-float for binary32
+// log-weights (no binary64 arithmetic per particle), binary64 for binary64 ones.
+__device__ __forceinline__ void lse_acc(float2& acc, float2& acc2, float x, float m) {
+  const float e = expf(x - m);
+  acc = add21(acc, e);
+  acc2 = add21(acc2, e * e);
 }
-__device__ __forceinline__ void lse_acc(double& acc, double x, double m) { acc += exp(x - m); }
+__device__ __forceinline__ void lse_acc(double& acc, double& acc2, double x, double m) {
+  const double e = exp(x - m);
+  acc += e;
+  acc2 += e * e;
+}
 __device__ __forceinline__ double lse_to_double(float2 a) { return vto_double(a); }
 __device__ __forceinline__ double lse_to_double(double a) { return a; }
 
-// log sum_{i in filter f} exp(lw_i), one CTA per filter: the maximum m, then
-// m + log sum exp(lw_i - m) with the exponentials in the log-weights' type, the per-thread
-// sums in two-float (binary32) or binary64, and the CTA's sum in binary64 (Appendix E's
-// max-shift). -inf for a filter whose weights are all zero; NaN / +inf log-weights are
-// flagged.
+// Per filter f (one CTA each): the maximum m of its log-weights, then with w = exp(lw - m)
+// out[f] = m + log sum w (Appendix E's max-shift) and ess[f] = (sum w)^2 / sum w^2 (the
+// effective sample size of Section 4.3); either output may be null. The exponentials in
+// the log-weights' type, the per-thread sums in two-float (binary32) or binary64, the CTA's
+// sums in binary64. A filter that is empty or whose weights are all zero gets -inf and 0;
+// NaN / +inf log-weights are flagged.
 template <typename T>
 __global__ void __launch_bounds__(kBlock)
 log_sum_batched_kernel(const T* __restrict__ lw, const int64_t* __restrict__ off, int F,
-                       int64_t cap, double* __restrict__ out, int* err) {
+                       int64_t cap, double* __restrict__ out, double* __restrict__ ess,
+                       int* err) {
   pdl_wait();
   const int f = blockIdx.x;
   const int64_t lo = __ldg(off + f), hi = __ldg(off + f + 1);
@@ -139,7 +147,7 @@ log_sum_batched_kernel(const T* __restrict__ lw, const int64_t* __restrict__ off
     if (threadIdx.x == 0) flag_error(err, RS_ERR_ARG);
     return;
   }
-  __shared__ double sh[kBlock / 32];
+  __shared__ double sh[kBlock / 32], sh2[kBlock / 32];
   T m = neg_inf<T>();
   bool bad = false;
   for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
@@ -157,22 +165,36 @@ log_sum_batched_kernel(const T* __restrict__ lw, const int64_t* __restrict__ off
   for (int k = 1; k < kBlock / 32; ++k) md = fmax(md, sh[k]);
   __syncthreads();
   if (md == -INFINITY) {
-    if (threadIdx.x == 0) out[f] = -INFINITY;
+    if (threadIdx.x == 0) {
+      if (out) out[f] = -INFINITY;
+      if (ess) ess[f] = 0.0;
+    }
     return;
   }
   const T mt = static_cast<T>(md);
   using Acc = typename std::conditional<sizeof(T) == 4, float2, double>::type;
-  Acc acc{};
-  for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) lse_acc(acc, __ldg(lw + i), mt);
-  double sum = lse_to_double(acc);
+  Acc acc{}, acc2{};
+  for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x)
+    lse_acc(acc, acc2, __ldg(lw + i), mt);
+  double sum = lse_to_double(acc), sum2 = lse_to_double(acc2);
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
-  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = sum;
+  for (int o = 16; o > 0; o >>= 1) {
+    sum += __shfl_xor_sync(0xffffffffu, sum, o);
+    sum2 += __shfl_xor_sync(0xffffffffu, sum2, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    sh[threadIdx.x >> 5] = sum;
+    sh2[threadIdx.x >> 5] = sum2;
+  }
   __syncthreads();
   if (threadIdx.x == 0) {
-    double t = 0.0;
-    for (int k = 0; k < kBlock / 32; ++k) t += sh[k];
-    out[f] = md + log(t);
+    double t = 0.0, t2 = 0.0;
+    for (int k = 0; k < kBlock / 32; ++k) {
+      t += sh[k];
+      t2 += sh2[k];
+    }
+    if (out) out[f] = md + log(t);
+    if (ess) ess[f] = t2 > 0.0 ? (t * t) / t2 : 0.0;
   }
 }
 
@@ -287,14 +309,15 @@ cudaError_t launch_lgssm_step_batched(const Scratch& s, float* x, const int64_t*
 }
 
 cudaError_t launch_log_sum_batched(const Scratch& s, bool f64, const void* logw,
-                                   const int64_t* offsets, int F, double* out, cudaStream_t st) {
-  trace_mark(s.trace, "log_sum_batched", st);
+                                   const int64_t* offsets, int F, double* out, double* ess,
+                                   cudaStream_t st) {
+  trace_mark(s.trace, ess ? "ess_batched" : "log_sum_batched", st);
   if (f64)
     launch_pdl(log_sum_batched_kernel<double>, F, kBlock, st, static_cast<const double*>(logw),
-               offsets, F, s.max_n, out, s.err);
+               offsets, F, s.max_n, out, ess, s.err);
   else
     launch_pdl(log_sum_batched_kernel<float>, F, kBlock, st, static_cast<const float*>(logw),
-               offsets, F, s.max_n, out, s.err);
+               offsets, F, s.max_n, out, ess, s.err);
   return cudaGetLastError();
 }
 

@@ -226,6 +226,49 @@ def test_log_sum_batched_matches_host(rs, h):
     assert rs.rs_last_error(h) == rs.RS_ERR_NONFINITE
 
 
+def test_ess_batched_matches_host(rs, h):
+    """rs_ess_batched: every filter's ESS within 1e-5 of the host's binary64 value, the log
+    totals bit-equal to rs_log_sum_weights_batched (same sums), 0 / -inf for empty and
+    all-zero filters, 1 for a single particle, and equal to rs_ess on the filter's slice."""
+    rng = np.random.default_rng(11)
+    sizes = [5, 0, 1, 1 << 15, 3000, 70001, 4, 1]
+    off = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+    offs = torch.from_numpy(off).to(DEV)
+    for dtype in (np.float32, np.float64):
+        lw = (rng.standard_normal(off[-1]) * 2 - 30).astype(dtype)
+        lw[off[2]:off[3]] = -np.inf           # an all-zero filter of one particle
+        lw[off[4]:off[4] + 100] = -np.inf     # zero weights inside a filter
+        t = torch.from_numpy(lw).to(DEV)
+        lt = torch.empty(len(sizes), dtype=torch.float64, device=DEV)
+        ess = rs.rs_ess_batched(h, t, offs, log_total=lt).cpu().numpy()
+        assert rs.rs_last_error(h) == rs.RS_OK
+        ls = rs.rs_log_sum_weights_batched(h, t, offs).cpu().numpy()
+        assert np.array_equal(lt.cpu().numpy(), ls)
+        only = rs.rs_ess_batched(h, t, offs).cpu().numpy()  # without the log totals
+        assert np.array_equal(only, ess)
+        for f in range(len(sizes)):
+            seg = lw[off[f]:off[f + 1]].astype(np.float64)
+            if seg.size == 0 or np.all(seg == -np.inf):
+                assert ess[f] == 0.0, f
+                continue
+            w = np.exp(seg - seg.max())
+            want = math.fsum(w) ** 2 / math.fsum(w * w)
+            assert abs(ess[f] - want) <= 1e-5 * want, (dtype, f, ess[f], want)
+            if seg.size == 1:
+                assert ess[f] == 1.0
+            if seg.size > 1000:
+                one = rs.rs_ess(h, t[off[f]:off[f + 1]]).item()
+                assert abs(one - ess[f]) <= 2e-5 * want, (dtype, f, one, ess[f])
+    # neither output: refused on the host before any launch
+    st = rs.load().rs_ess_batched(h.ptr, rs._dtype_code(t), rs._dev(t, None, "logw"),
+                                  rs._dev(offs, torch.int64, "offsets"), len(sizes), None,
+                                  None, None)
+    assert st == rs.RS_ERR_ARG
+    bad = torch.tensor([0.0, float("nan")], dtype=torch.float32, device=DEV)
+    rs.rs_ess_batched(h, bad, torch.tensor([0, 2], dtype=torch.int64, device=DEV))
+    assert rs.rs_last_error(h) == rs.RS_ERR_NONFINITE
+
+
 def test_batched_loglik_matches_kalman(rs, h):
     """32 independent filters of N = 2^14 on the same observations: their log-likelihood
     estimates centre on the Kalman filter's value (4 standard errors of the mean)."""
