@@ -223,25 +223,25 @@ class ClockSampler:
 # headers it includes, hashed; `traffic` is null once any of them has changed.
 # ---------------------------------------------------------------------------------------
 NCU_TRAFFIC = {  # label: (bytes per launch, source hash)
-               "permute": (8392715, "ca0b710fb768ab55"),
-               "metropolis_f64": (12599333, "55e404ad0f565b9e"),
-               "metropolis_f32": (8402432, "55e404ad0f565b9e"),
-               "rejection_f64": (8409490, "55e404ad0f565b9e"),
-               "permute_sorted": (8396848, "ca0b710fb768ab55"),
-               "fused_stratified_f64": (8487360, "1e82f2cf13a41e5d"),
-               "rejection_f32": (4211872, "55e404ad0f565b9e"),
-               "fused_multinomial_f64": (8492960, "1e82f2cf13a41e5d"),
-               "fused_systematic_f64": (8483488, "1e82f2cf13a41e5d"),
-               "fused_stratified_f32": (4268288, "1e82f2cf13a41e5d"),
-               "fused_multinomial_f32": (4279680, "1e82f2cf13a41e5d"),
-               "fused_systematic_f32": (4257536, "1e82f2cf13a41e5d"),
-               "iscan": (4212974, "ca0b710fb768ab55"),
-               "search_f64": (16783552, "d0ae06ee35d821f6"),
-               "search_f32": (12591136, "d0ae06ee35d821f6"),
-               "fill": (8482, "ca0b710fb768ab55"),
-               "cumoff_to_ancestors": (4199782, "ca0b710fb768ab55"),
-               "offspring": (8391205, "ca0b710fb768ab55"),
-               "adjacent_difference": (4197513, "ca0b710fb768ab55")}
+               "permute": (8393133, "765e5e59d38738cd"),
+               "metropolis_f64": (12602222, "2d3232679c892789"),
+               "metropolis_f32": (8401152, "2d3232679c892789"),
+               "rejection_f64": (8411904, "2d3232679c892789"),
+               "permute_sorted": (8396872, "765e5e59d38738cd"),
+               "fused_stratified_f64": (8488832, "f31552b7614ee07d"),
+               "rejection_f32": (4211648, "2d3232679c892789"),
+               "fused_multinomial_f64": (8491904, "f31552b7614ee07d"),
+               "fused_systematic_f64": (8480352, "f31552b7614ee07d"),
+               "fused_stratified_f32": (4261408, "f31552b7614ee07d"),
+               "fused_multinomial_f32": (4280032, "f31552b7614ee07d"),
+               "fused_systematic_f32": (4257984, "f31552b7614ee07d"),
+               "iscan": (4213138, "765e5e59d38738cd"),
+               "search_f64": (16784576, "bf2e8fb5665f79c9"),
+               "search_f32": (12591552, "bf2e8fb5665f79c9"),
+               "fill": (8687, "765e5e59d38738cd"),
+               "cumoff_to_ancestors": (4199100, "765e5e59d38738cd"),
+               "offspring": (8391333, "765e5e59d38738cd"),
+               "adjacent_difference": (4197495, "765e5e59d38738cd")}
 
 _LABEL_FILES = (("fused_", "fused.cu"), ("permute", "aux.cu"), ("iscan", "aux.cu"),
                 ("fill", "aux.cu"), ("offspring", "aux.cu"), ("adjacent", "aux.cu"),
