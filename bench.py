@@ -223,25 +223,25 @@ class ClockSampler:
 # headers it includes, hashed; `traffic` is null once any of them has changed.
 # ---------------------------------------------------------------------------------------
 NCU_TRAFFIC = {  # label: (bytes per launch, source hash)
-               "permute": (8393133, "765e5e59d38738cd"),
-               "metropolis_f64": (12602222, "2d3232679c892789"),
-               "metropolis_f32": (8401152, "2d3232679c892789"),
-               "rejection_f64": (8411904, "2d3232679c892789"),
-               "permute_sorted": (8396872, "765e5e59d38738cd"),
-               "fused_stratified_f64": (8488832, "f31552b7614ee07d"),
-               "rejection_f32": (4211648, "2d3232679c892789"),
-               "fused_multinomial_f64": (8491904, "f31552b7614ee07d"),
-               "fused_systematic_f64": (8480352, "f31552b7614ee07d"),
-               "fused_stratified_f32": (4261408, "f31552b7614ee07d"),
-               "fused_multinomial_f32": (4280032, "f31552b7614ee07d"),
-               "fused_systematic_f32": (4257984, "f31552b7614ee07d"),
-               "iscan": (4213138, "765e5e59d38738cd"),
-               "search_f64": (16784576, "bf2e8fb5665f79c9"),
-               "search_f32": (12591552, "bf2e8fb5665f79c9"),
-               "fill": (8687, "765e5e59d38738cd"),
-               "cumoff_to_ancestors": (4199100, "765e5e59d38738cd"),
-               "offspring": (8391333, "765e5e59d38738cd"),
-               "adjacent_difference": (4197495, "765e5e59d38738cd")}
+               "permute": (8393199, "d1bec482251ad289"),
+               "metropolis_f64": (12599771, "be5e05fb767d0792"),
+               "metropolis_f32": (8402560, "be5e05fb767d0792"),
+               "rejection_f64": (8412233, "be5e05fb767d0792"),
+               "permute_sorted": (8397408, "d1bec482251ad289"),
+               "rejection_f32": (4209856, "be5e05fb767d0792"),
+               "fused_stratified_f64": (8489856, "2d7ce1f5369a295d"),
+               "fused_multinomial_f64": (8492512, "2d7ce1f5369a295d"),
+               "fused_systematic_f64": (8482496, "2d7ce1f5369a295d"),
+               "fused_stratified_f32": (4261696, "2d7ce1f5369a295d"),
+               "fused_multinomial_f32": (4280064, "2d7ce1f5369a295d"),
+               "fused_systematic_f32": (4261376, "2d7ce1f5369a295d"),
+               "iscan": (4212864, "d1bec482251ad289"),
+               "search_f64": (16783360, "ca9fe6017c87627e"),
+               "search_f32": (12591968, "ca9fe6017c87627e"),
+               "fill": (8695, "d1bec482251ad289"),
+               "cumoff_to_ancestors": (4199185, "d1bec482251ad289"),
+               "offspring": (8391369, "d1bec482251ad289"),
+               "adjacent_difference": (4197410, "d1bec482251ad289")}
 
 _LABEL_FILES = (("fused_", "fused.cu"), ("permute", "aux.cu"), ("iscan", "aux.cu"),
                 ("fill", "aux.cu"), ("offspring", "aux.cu"), ("adjacent", "aux.cu"),
@@ -626,8 +626,9 @@ def run_ours(args):
 def run_batched(args, dev, world):
     """F filters, sizes log-uniform in [256, 65536], y_f ~ U[0,4], binary32; systematic and
     Metropolis (per-filter B from Eq. B) each with Permute, one call per scheme per step (nine
-    kernels in all), replayed from a CUDA graph. Returns filters/s, particles/s and the
-    aggregate algorithmic HBM bandwidth."""
+    kernels in all), replayed from a CUDA graph, first with the default launch shapes and then
+    with those the library's autotuner picks on this batch (rs_tune_batched). Returns
+    filters/s, particles/s and the aggregate algorithmic HBM bandwidth at the tuned shapes."""
     import torch
     import paper_1301_4019_gb300 as rs
     F = args.batched_filters
@@ -670,23 +671,30 @@ def run_batched(args, dev, world):
             continue
         name = f"{lab}:{['systematic', 'metropolis'][call]}"
         kern[name] = round(evs[i].elapsed_time(evs[i + 1]) * 1e3, 2)
-    cs = torch.cuda.Stream()
-    cs.wait_stream(torch.cuda.current_stream())
-    g = torch.cuda.CUDAGraph()
-    with torch.cuda.stream(cs):
-        with torch.cuda.graph(g, stream=cs):
-            step(0)
-    torch.cuda.current_stream().wait_stream(cs)
-    g.replay()
-    torch.cuda.synchronize()
-    barrier(world)
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record()
-    for _ in range(args.steps):
+    def graph_ms():
+        cs = torch.cuda.Stream()
+        cs.wait_stream(torch.cuda.current_stream())
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.stream(cs):
+            with torch.cuda.graph(g, stream=cs):
+                step(0)
+        torch.cuda.current_stream().wait_stream(cs)
         g.replay()
-    e1.record()
-    torch.cuda.synchronize()
-    ms = reduce_max(e0.elapsed_time(e1) / args.steps, world, dev)
+        torch.cuda.synchronize()
+        barrier(world)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(args.steps):
+            g.replay()
+        e1.record()
+        torch.cuda.synchronize()
+        return reduce_max(e0.elapsed_time(e1) / args.steps, world, dev)
+
+    ms_default = graph_ms()
+    # the library's autotuner on this batch (launch shapes of the Metropolis kernel and of
+    # Permute; the ancestors do not depend on them), then the same graph again
+    shapes = rs.rs_tune_batched(h, t, off, B_per_filter=Bt, reps=2)
+    ms = graph_ms()
     st = rs.rs_last_error(h)
     h.close()
     if st != rs.RS_OK:
@@ -703,7 +711,10 @@ def run_batched(args, dev, world):
                               "systematic 28 B, Metropolis 24 B per particle; the Metropolis "
                               "gathers hit L2 and are not counted)",
             "ms_per_step": round(ms, 4), "particles": total, "kernel_us": kern,
-            "launches_per_step": len(kern)}
+            "launches_per_step": len(kern),
+            "autotuned": {"metropolis_block_ipt": list(shapes["metropolis"]),
+                          "permute_block_ipt": list(shapes["permute"]),
+                          "ms_per_step_default_256x1": round(ms_default, 4)}}
 
 
 # ---------------------------------------------------------------------------------------

@@ -319,6 +319,42 @@ int rs_log_sum_weights_batched(rs_handle* h, int dtype, const void* logw_dev,
 int rs_ess_batched(rs_handle* h, int dtype, const void* logw_dev, const int64_t* offsets_dev,
                    int32_t F, double* ess_dev, double* log_total_dev, void* stream);
 
+/* Metropolis B picked per filter from its own weights: beta_dev[f] (may be NULL) = mean w /
+ * max w over the filter's particles (the ratio of Eq. beta2, evaluated on the weights rather
+ * than from the model) and B_dev[f] = B* of Eq. B (Section 2.1) for eps and that beta, i.e.
+ * ceil(log eps / log(1 - beta)), at least 1 (1 for beta = 1, and for an empty or all-zero
+ * filter, where beta is 0). F int32 / float64 on the device, ready to pass as B_dev to
+ * rs_resample_batched without a host round trip. Same sums as rs_log_sum_weights_batched;
+ * beta has the relative accuracy of those sums (about 1e-7 for binary32 weights), so B can
+ * differ by one from a binary64 host evaluation where log eps / log(1 - beta) lies that close
+ * to an integer. RS_ERR_ARG unless 0 < eps < 1; NaN/+inf flag RS_ERR_NONFINITE. */
+int rs_metropolis_B_batched(rs_handle* h, int dtype, const void* logw_dev,
+                            const int64_t* offsets_dev, int32_t F, double eps, int32_t* B_dev,
+                            double* beta_dev, void* stream);
+
+/* Launch shape of the particle-parallel kernels of rs_resample_batched: kernel
+ * RS_BATCHED_METROPOLIS_F32 / _F64 (the per-particle Metropolis chains) or
+ * RS_BATCHED_PERMUTE (Code 10 per filter); block = threads per CTA (a multiple of 32, 32 to
+ * 512), items_per_thread = particles per thread (1 to 16). The handle starts at 256 x 1. Only
+ * the speed depends on the shape: every particle's draws, chain, claim and slot are the same
+ * for any shape. RS_ERR_ARG for an unknown kernel or shape. Host-only. */
+#define RS_BATCHED_METROPOLIS_F32 0
+#define RS_BATCHED_METROPOLIS_F64 1
+#define RS_BATCHED_PERMUTE 2
+int rs_set_batched_launch(rs_handle* h, int kernel, int block, int items_per_thread);
+int rs_get_batched_launch(rs_handle* h, int kernel, int* block, int* items_per_thread);
+
+/* Autotuner of the batched Metropolis path on the caller's own batch (the arguments of
+ * rs_resample_batched with scheme RS_METROPOLIS): times every shape block in {128, 256, 512} x
+ * items per thread in {1, 2, 4} with CUDA events over `reps` calls (after one untimed call),
+ * first for the Metropolis kernel of `dtype` alone, then for Permute with that choice, and
+ * keeps the fastest of each in the handle (read them with rs_get_batched_launch). The calls
+ * write only the handle's scratch. Synchronises `stream` once per shape; RS_ERR_ARG on a
+ * stream being captured or reps outside 1..1000; the argument errors of rs_resample_batched;
+ * RS_ERR_CUDA if a timed call fails (the previous shapes are restored). */
+int rs_tune_batched(rs_handle* h, int dtype, const void* logw_dev, const int64_t* offsets_dev,
+                    int32_t F, const int32_t* B_dev, int32_t B, int reps, void* stream);
+
 /* B* = log(eps) / log(1 - beta) of Eq. (B) (Section 2.1), rounded up: the number of
  * Metropolis steps that bounds the total-variation distance of every chain by eps, for a
  * lower bound beta on min_i(mean(w)/w^i) (Eq. beta), e.g. E(w)/w_max (Eq. beta2).

@@ -42,11 +42,14 @@ EXPORTED = [
     "rs_trace", "rs_trace_count", "rs_trace_label", "rs_systematic_noalloc",
     "rs_resample_batched", "rs_set_launch_mode", "rs_copy_ancestors", "rs_lgssm_step",
     "rs_ess", "rs_resample_prc", "rs_copy_ancestors_batched", "rs_lgssm_step_batched",
-    "rs_log_sum_weights_batched", "rs_ess_batched", "rs_cumulative_weights_f64",
+    "rs_log_sum_weights_batched", "rs_ess_batched", "rs_metropolis_B_batched",
+    "rs_set_batched_launch", "rs_get_batched_launch", "rs_tune_batched",
+    "rs_cumulative_weights_f64",
     "rs_capture_if_below",
     "rs_capture_end_if", "rs_smc_mark_resampled", "rs_smc_loglik_step",
 ]
 NOALLOC_MAX_N = 1 << 22
+BATCHED_METROPOLIS_F32, BATCHED_METROPOLIS_F64, BATCHED_PERMUTE = 0, 1, 2
 LAUNCH_AUTO, LAUNCH_FUSED, LAUNCH_SEPARATE = 0, 1, 2
 
 _lock = threading.Lock()
@@ -112,6 +115,10 @@ def _declare(lib):
                                       U64, U64, P, P]),
         "rs_log_sum_weights_batched": (I, [P, I, P, P, I32, P, P]),
         "rs_ess_batched": (I, [P, I, P, P, I32, P, P, P]),
+        "rs_metropolis_B_batched": (I, [P, I, P, P, I32, C.c_double, P, P, P]),
+        "rs_set_batched_launch": (I, [P, I, I, I]),
+        "rs_get_batched_launch": (I, [P, I, C.POINTER(I), C.POINTER(I)]),
+        "rs_tune_batched": (I, [P, I, P, P, I32, P, I32, I, P]),
         "rs_capture_if_below": (I, [P, P, C.c_double, P, C.POINTER(P)]),
         "rs_capture_end_if": (I, [P, P]),
         "rs_smc_mark_resampled": (I, [P, P, I64, P, C.c_double, P, P]),
@@ -482,6 +489,52 @@ def rs_ess_batched(h: Handle, logw: torch.Tensor, offsets: torch.Tensor,
                                  _dev(out, torch.float64, "ess", F, h), lt, _stream(stream)),
            "rs_ess_batched")
     return out
+
+
+def rs_metropolis_B_batched(h: Handle, logw: torch.Tensor, offsets: torch.Tensor,
+                            eps: float = 0.01, out: torch.Tensor | None = None,
+                            beta: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """Per-filter Metropolis B (Eq. B) from each filter's own beta = mean w / max w (int32,
+    one per filter, on the device); with ``beta`` (F float64), also the betas."""
+    F = offsets.numel() - 1
+    if out is None:
+        out = torch.empty(F, dtype=torch.int32, device=logw.device)
+    bp = _dev(beta, torch.float64, "beta", F, h) if beta is not None else None
+    _check(load().rs_metropolis_B_batched(h.ptr, _dtype_code(logw), _dev(logw, None, "logw", h=h),
+                                          _dev(offsets, torch.int64, "offsets", F + 1, h), F,
+                                          float(eps), _dev(out, torch.int32, "B", F, h), bp,
+                                          _stream(stream)), "rs_metropolis_B_batched")
+    return out
+
+
+def rs_set_batched_launch(h: Handle, kernel: int, block: int, items_per_thread: int) -> None:
+    """Launch shape (threads per CTA, particles per thread) of a batched kernel:
+    BATCHED_METROPOLIS_F32 / _F64 or BATCHED_PERMUTE. Results never depend on it."""
+    _check(load().rs_set_batched_launch(h.ptr, int(kernel), int(block), int(items_per_thread)),
+           "rs_set_batched_launch")
+
+
+def rs_get_batched_launch(h: Handle, kernel: int) -> tuple:
+    b, q = C.c_int(), C.c_int()
+    _check(load().rs_get_batched_launch(h.ptr, int(kernel), C.byref(b), C.byref(q)),
+           "rs_get_batched_launch")
+    return b.value, q.value
+
+
+def rs_tune_batched(h: Handle, logw: torch.Tensor, offsets: torch.Tensor, B: int = 0,
+                    B_per_filter: torch.Tensor | None = None, reps: int = 3,
+                    stream=None) -> dict:
+    """Autotune the batched Metropolis path on this batch (every block x items-per-thread
+    shape timed, the fastest kept in the handle); returns the chosen shapes."""
+    F = offsets.numel() - 1
+    bptr = (_dev(B_per_filter, torch.int32, "B_per_filter", F, h)
+            if B_per_filter is not None else None)
+    _check(load().rs_tune_batched(h.ptr, _dtype_code(logw), _dev(logw, None, "logw", h=h),
+                                  _dev(offsets, torch.int64, "offsets", F + 1, h), F, bptr,
+                                  int(B), int(reps), _stream(stream)), "rs_tune_batched")
+    k = BATCHED_METROPOLIS_F64 if logw.dtype == torch.float64 else BATCHED_METROPOLIS_F32
+    return {"metropolis": rs_get_batched_launch(h, k),
+            "permute": rs_get_batched_launch(h, BATCHED_PERMUTE)}
 
 
 def rs_capture_if_below(h: Handle, value: torch.Tensor, threshold: float, stream=None):

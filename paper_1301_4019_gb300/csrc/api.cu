@@ -77,6 +77,32 @@ void free_scratch(rsk::Scratch& s) {
   std::memset(&s, 0, sizeof(s));
 }
 
+bool valid_launch(int block, int ipt) {
+  return block >= 32 && block <= rsk::kMaxTunedBlock && block % 32 == 0 && ipt >= 1 &&
+         ipt <= rsk::kMaxTunedIpt;
+}
+
+// Milliseconds of `reps` back-to-back calls of `call` on stream s (CUDA events), after one
+// untimed call; a negative value when a call or the timing failed.
+template <typename Call>
+float time_calls(cudaStream_t s, int reps, Call call) {
+  if (call() != RS_OK) return -1.0f;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaEventCreate(&e0) != cudaSuccess) return -1.0f;
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return -1.0f;
+  }
+  float ms = -1.0f;
+  bool ok = cudaEventRecord(e0, s) == cudaSuccess;
+  for (int r = 0; ok && r < reps; ++r) ok = call() == RS_OK;
+  ok = ok && cudaEventRecord(e1, s) == cudaSuccess && cudaEventSynchronize(e1) == cudaSuccess &&
+       cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return ok ? ms : -1.0f;
+}
+
 }  // namespace
 
 extern "C" {
@@ -94,6 +120,7 @@ int rs_create(rs_handle** out, int64_t max_n, int device) {
   s.max_tiles = (max_n + rsk::kTile - 1) / rsk::kTile;
   s.max_blocks = 152 * 8;
   s.launch_mode = RS_LAUNCH_AUTO;
+  for (int k = 0; k < rsk::kCfgCount; ++k) s.batch_cfg[k] = rsk::LaunchCfg{rsk::kBlock, 1};
   int coop = 0;
   if (cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, device) != cudaSuccess) coop = 0;
   s.coop = coop;
@@ -477,8 +504,10 @@ int rs_log_sum_weights_batched(rs_handle* h, int dtype, const void* logw_dev,
   if (F > INT_MAX / 2) return RS_ERR_ARG;
   int st = set_device(h);
   if (st != RS_OK) return st;
-  const cudaError_t e = rsk::launch_log_sum_batched(h->s, dtype == RS_F64, logw_dev, offsets_dev,
-                                                    F, out_dev, nullptr, as_stream(stream));
+  rsk::WeightStatsOut o{};
+  o.log_total = out_dev;
+  const cudaError_t e = rsk::launch_weight_stats_batched(h->s, dtype == RS_F64, logw_dev,
+                                                         offsets_dev, F, o, as_stream(stream));
   end_mark(h, as_stream(stream));
   return cuda_status(e);
 }
@@ -491,10 +520,94 @@ int rs_ess_batched(rs_handle* h, int dtype, const void* logw_dev, const int64_t*
   if (F > INT_MAX / 2) return RS_ERR_ARG;
   int st = set_device(h);
   if (st != RS_OK) return st;
-  const cudaError_t e = rsk::launch_log_sum_batched(h->s, dtype == RS_F64, logw_dev, offsets_dev,
-                                                    F, log_total_dev, ess_dev, as_stream(stream));
+  rsk::WeightStatsOut o{};
+  o.log_total = log_total_dev;
+  o.ess = ess_dev;
+  const cudaError_t e = rsk::launch_weight_stats_batched(h->s, dtype == RS_F64, logw_dev,
+                                                         offsets_dev, F, o, as_stream(stream));
   end_mark(h, as_stream(stream));
   return cuda_status(e);
+}
+
+int rs_metropolis_B_batched(rs_handle* h, int dtype, const void* logw_dev,
+                            const int64_t* offsets_dev, int32_t F, double eps, int32_t* B_dev,
+                            double* beta_dev, void* stream) {
+  if (!h || !logw_dev || !offsets_dev || !B_dev || F < 1) return RS_ERR_ARG;
+  if (dtype != RS_F32 && dtype != RS_F64) return RS_ERR_ARG;
+  if (!(eps > 0.0 && eps < 1.0)) return RS_ERR_ARG;
+  if (F > INT_MAX / 2) return RS_ERR_ARG;
+  int st = set_device(h);
+  if (st != RS_OK) return st;
+  rsk::WeightStatsOut o{};
+  o.B = B_dev;
+  o.beta = beta_dev;
+  o.log_eps = std::log(eps);
+  const cudaError_t e = rsk::launch_weight_stats_batched(h->s, dtype == RS_F64, logw_dev,
+                                                         offsets_dev, F, o, as_stream(stream));
+  end_mark(h, as_stream(stream));
+  return cuda_status(e);
+}
+
+
+int rs_set_batched_launch(rs_handle* h, int kernel, int block, int items_per_thread) {
+  if (!h || kernel < 0 || kernel >= rsk::kCfgCount) return RS_ERR_ARG;
+  if (!valid_launch(block, items_per_thread)) return RS_ERR_ARG;
+  h->s.batch_cfg[kernel] = rsk::LaunchCfg{block, items_per_thread};
+  return RS_OK;
+}
+
+int rs_get_batched_launch(rs_handle* h, int kernel, int* block, int* items_per_thread) {
+  if (!h || kernel < 0 || kernel >= rsk::kCfgCount || !block || !items_per_thread)
+    return RS_ERR_ARG;
+  *block = h->s.batch_cfg[kernel].block;
+  *items_per_thread = h->s.batch_cfg[kernel].ipt;
+  return RS_OK;
+}
+
+int rs_tune_batched(rs_handle* h, int dtype, const void* logw_dev, const int64_t* offsets_dev,
+                    int32_t F, const int32_t* B_dev, int32_t B, int reps, void* stream) {
+  if (!h || reps < 1 || reps > 1000) return RS_ERR_ARG;
+  if (dtype != RS_F32 && dtype != RS_F64) return RS_ERR_ARG;
+  const cudaStream_t s = as_stream(stream);
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone)
+    return RS_ERR_ARG;  // timing needs real executions
+  int st = set_device(h);
+  if (st != RS_OK) return st;
+  rsk::Scratch& sc = h->s;
+  const int which = dtype == RS_F64 ? rsk::kCfgMetropolisF64 : rsk::kCfgMetropolisF32;
+  const rsk::LaunchCfg saved_m = sc.batch_cfg[which], saved_p = sc.batch_cfg[rsk::kCfgPermute];
+  // The caller's Metropolis call, its outputs in the handle's scratch: without Permute into
+  // a_tmp (times the Metropolis kernel alone), with Permute into W (large enough for N int32).
+  int32_t* spare = static_cast<int32_t*>(sc.W);
+  auto run = [&](int permute) {
+    return rs_resample_batched(h, RS_METROPOLIS, dtype, logw_dev, offsets_dev, F, B_dev, B, 0,
+                               0, permute ? spare : sc.a_tmp, permute, nullptr, stream);
+  };
+  if ((st = run(0)) != RS_OK) return st;  // argument errors before any timing
+  static const int kBlocks[] = {128, 256, 512};
+  static const int kIpts[] = {1, 2, 4};
+  for (int stage = 0; stage < 2; ++stage) {
+    const int k = stage == 0 ? which : rsk::kCfgPermute;
+    float best = -1.0f;
+    rsk::LaunchCfg best_cfg = sc.batch_cfg[k];
+    for (int b : kBlocks)
+      for (int q : kIpts) {
+        sc.batch_cfg[k] = rsk::LaunchCfg{b, q};
+        const float ms = time_calls(s, reps, [&]() { return run(stage); });
+        if (ms < 0.0f) {
+          sc.batch_cfg[which] = saved_m;
+          sc.batch_cfg[rsk::kCfgPermute] = saved_p;
+          return RS_ERR_CUDA;
+        }
+        if (best < 0.0f || ms < best) {
+          best = ms;
+          best_cfg = sc.batch_cfg[k];
+        }
+      }
+    sc.batch_cfg[k] = best_cfg;
+  }
+  return RS_OK;
 }
 
 int rs_capture_if_below(rs_handle* h, const double* value_dev, double threshold, void* stream,

@@ -295,35 +295,46 @@ batch_fill_sentinel_kernel(const int64_t* __restrict__ off, int F, int64_t total
   d[g] = static_cast<int32_t>(P.n);
 }
 
+// First particle of item q of this thread when each CTA covers blockDim.x * ipt consecutive
+// particles, item q being the q-th blockDim.x-wide slice (coalesced for every q).
+__device__ __forceinline__ int64_t item_index(int ipt, int q) {
+  return (static_cast<int64_t>(blockIdx.x) * ipt + q) * blockDim.x + threadIdx.x;
+}
+
+// Metropolis (or one-particle-per-thread rejection) over the particles of all filters, ipt
+// particles per thread (the launch shape is tunable; every particle's chain and claim are the
+// same for any shape).
 template <typename T>
-__global__ void __launch_bounds__(kBlock)
+__global__ void __launch_bounds__(kMaxTunedBlock)
 batch_mcmc_kernel(const T* __restrict__ lw, const int64_t* __restrict__ off, int F,
                   int64_t total, int scheme, const int32_t* __restrict__ Bf, int32_t B,
                   Keys base_keys, double log_wmax, int64_t max_trials,
-                  int32_t* __restrict__ a, int32_t* __restrict__ d, int* err) {
+                  int32_t* __restrict__ a, int32_t* __restrict__ d, int ipt, int* err) {
   pdl_wait();
-  const int64_t g = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
-  PartLoc P;
-  if (g >= total) return;
-  if (!locate_particle(off, F, total, g, P)) {
-    if (g < __ldg(off + F)) flag_error(err, RS_ERR_ARG);
-    return;
-  }
-  int32_t k;
-  if (scheme == RS_METROPOLIS) {
-    int32_t Bv = Bf ? __ldg(Bf + P.f) : B;
-    if (Bv < 0) {
-      flag_error(err, RS_ERR_ARG);
-      Bv = 0;
+  for (int q = 0; q < ipt; ++q) {
+    const int64_t g = item_index(ipt, q);
+    if (g >= total) return;
+    PartLoc P;
+    if (!locate_particle(off, F, total, g, P)) {
+      if (g < __ldg(off + F)) flag_error(err, RS_ERR_ARG);
+      continue;
     }
-    const Keys keys = with_tag(base_keys, static_cast<uint32_t>(P.f), RS_METROPOLIS);
-    k = metropolis_one(lw + P.lo, P.n, Bv, keys, P.i, err);
-  } else {
-    const Keys keys = with_tag(base_keys, static_cast<uint32_t>(P.f), RS_REJECTION);
-    k = rejection_one(lw + P.lo, P.n, log_wmax, max_trials, keys, P.i, err);
+    int32_t k;
+    if (scheme == RS_METROPOLIS) {
+      int32_t Bv = Bf ? __ldg(Bf + P.f) : B;
+      if (Bv < 0) {
+        flag_error(err, RS_ERR_ARG);
+        Bv = 0;
+      }
+      const Keys keys = with_tag(base_keys, static_cast<uint32_t>(P.f), RS_METROPOLIS);
+      k = metropolis_one(lw + P.lo, P.n, Bv, keys, P.i, err);
+    } else {
+      const Keys keys = with_tag(base_keys, static_cast<uint32_t>(P.f), RS_REJECTION);
+      k = rejection_one(lw + P.lo, P.n, log_wmax, max_trials, keys, P.i, err);
+    }
+    a[g] = k;
+    if (d) atomicMin(d + P.lo + k, static_cast<int32_t>(P.i));
   }
-  a[g] = k;
-  if (d) atomicMin(d + P.lo + k, static_cast<int32_t>(P.i));
 }
 
 // Rejection with warp refill over the particles of all filters (mcmc.cuh); a lane looks up
@@ -389,20 +400,28 @@ batch_rejection_kernel(const T* __restrict__ lw, const int64_t* __restrict__ off
   }
 }
 
-__global__ void __launch_bounds__(kBlock)
+// Permute of every filter (permute.cuh), ipt slots per thread (tunable launch shape).
+__global__ void __launch_bounds__(kMaxTunedBlock)
 batch_permute_kernel(const int64_t* __restrict__ off, int F, int64_t total,
                      const int32_t* __restrict__ a, const int32_t* __restrict__ d,
-                     int32_t* __restrict__ c, int* err) {
+                     int32_t* __restrict__ c, int ipt, int* err) {
   pdl_wait();
-  const int64_t g = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
-  PartLoc P;
-  if (g >= total || !locate_particle(off, F, total, g, P)) return;
-  permute_one(a + P.lo, d + P.lo, P.n, c + P.lo, P.i, err);
+  for (int q = 0; q < ipt; ++q) {
+    const int64_t g = item_index(ipt, q);
+    if (g >= total) return;
+    PartLoc P;
+    if (!locate_particle(off, F, total, g, P)) continue;
+    permute_one(a + P.lo, d + P.lo, P.n, c + P.lo, P.i, err);
+  }
 }
 
 // Total number of particles of the batch (offsets[F]) is not known on the host without a
 // synchronisation, so grids are sized for the handle's capacity and surplus CTAs exit at once.
 inline int grid_particles(int64_t cap) { return static_cast<int>((cap + kBlock - 1) / kBlock); }
+inline int grid_shaped(int64_t cap, const LaunchCfg& c) {
+  const int64_t per = static_cast<int64_t>(c.block) * c.ipt;
+  return static_cast<int>((cap + per - 1) / per);
+}
 
 const char* const kLblSum[4] = {"batch_sum_f32", "batch_sum_f32c", "batch_sum_f64", "batch_sum_f64n"};
 const char* const kLblEmit[4] = {"batch_emit_f32", "batch_emit_f32c", "batch_emit_f64",
@@ -474,13 +493,15 @@ cudaError_t launch_batched(const Scratch& s, int scheme, Acc acc, const void* lo
             static_cast<const float*>(logw), offsets, F, total, keys, log_wmax, max_trials, a,
             d, s.err);
     } else if (f64) {
-      launch_pdl(batch_mcmc_kernel<double>, grid_particles(total), kBlock, st,
+      const LaunchCfg& c = s.batch_cfg[kCfgMetropolisF64];
+      launch_pdl(batch_mcmc_kernel<double>, grid_shaped(total, c), c.block, st,
           static_cast<const double*>(logw), offsets, F, total, scheme, Bf, B, keys, log_wmax,
-          max_trials, a, d, s.err);
+          max_trials, a, d, c.ipt, s.err);
     } else {
-      launch_pdl(batch_mcmc_kernel<float>, grid_particles(total), kBlock, st,
+      const LaunchCfg& c = s.batch_cfg[kCfgMetropolisF32];
+      launch_pdl(batch_mcmc_kernel<float>, grid_shaped(total, c), c.block, st,
           static_cast<const float*>(logw), offsets, F, total, scheme, Bf, B, keys, log_wmax,
-          max_trials, a, d, s.err);
+          max_trials, a, d, c.ipt, s.err);
     }
   } else {
     Batch b;
@@ -521,8 +542,9 @@ cudaError_t launch_batched(const Scratch& s, int scheme, Acc acc, const void* lo
   if (e == cudaSuccess) e = cudaGetLastError();
   if (e == cudaSuccess && permute) {
     trace_mark(s.trace, "batch_permute", st);
-    launch_pdl(batch_permute_kernel, grid_particles(total), kBlock, st, offsets, F, total, s.a_tmp,
-                                                                    s.d, out, s.err);
+    const LaunchCfg& c = s.batch_cfg[kCfgPermute];
+    launch_pdl(batch_permute_kernel, grid_shaped(total, c), c.block, st, offsets, F, total,
+               s.a_tmp, s.d, out, c.ipt, s.err);
     e = cudaGetLastError();
   }
   return e;

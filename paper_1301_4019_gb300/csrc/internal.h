@@ -42,6 +42,16 @@ inline void trace_mark(Trace* t, const char* label, cudaStream_t st) {
 
 constexpr int64_t kBatchMaxN = 1 << 20;  // particles of one filter of a batched call, at most
 
+// Launch shape of a particle-parallel batched kernel: threads per CTA and particles per thread
+// (rs_set_batched_launch / rs_tune_batched). The results never depend on it.
+struct LaunchCfg {
+  int block;
+  int ipt;
+};
+constexpr int kCfgMetropolisF32 = 0, kCfgMetropolisF64 = 1, kCfgPermute = 2, kCfgCount = 3;
+constexpr int kMaxTunedBlock = 512;
+constexpr int kMaxTunedIpt = 16;
+
 struct Scratch {
   Trace* trace;      // nullptr unless tracing is enabled
   int32_t* d;        // claim vector (Prepermute), max_n
@@ -68,6 +78,7 @@ struct Scratch {
   int max_blocks;    // grid of the max pass
   int coop;          // the device supports cooperative launches
   int launch_mode;   // RS_LAUNCH_AUTO / RS_LAUNCH_FUSED / RS_LAUNCH_SEPARATE
+  LaunchCfg batch_cfg[kCfgCount];  // batched Metropolis (binary32, binary64) and Permute
 };
 
 // Accumulation of the scan-based schemes: binary32, two-float over binary32 inputs,
@@ -146,9 +157,17 @@ cudaError_t launch_mark_resampled(const Scratch& s, float* logw, int64_t N, doub
 cudaError_t launch_loglik_step(const Scratch& s, const double* lse, double* base, double* ll,
                                int32_t* count, double c, double log_n, int first,
                                cudaStream_t st);
-cudaError_t launch_log_sum_batched(const Scratch& s, bool f64, const void* logw,
-                                   const int64_t* offsets, int F, double* out, double* ess,
-                                   cudaStream_t st);
+// Per-filter statistics of a batch's weights (one CTA per filter); null outputs are skipped.
+struct WeightStatsOut {
+  double* log_total;  // max logw + log sum w
+  double* ess;        // (sum w)^2 / sum w^2
+  double* beta;       // mean w / max w
+  int32_t* B;         // Eq. B for beta and log_eps
+  double log_eps;
+};
+cudaError_t launch_weight_stats_batched(const Scratch& s, bool f64, const void* logw,
+                                        const int64_t* offsets, int F, const WeightStatsOut& o,
+                                        cudaStream_t st);
 cudaError_t launch_copy_ancestors(const Scratch& s, float* x, int D, const int32_t* c, int64_t N,
                                   cudaStream_t st);
 cudaError_t launch_lgssm_step(const Scratch& s, float* x, int64_t N, int init, int accumulate,

@@ -129,17 +129,27 @@ __device__ __forceinline__ void lse_acc(double& acc, double& acc2, double x, dou
 __device__ __forceinline__ double lse_to_double(float2 a) { return vto_double(a); }
 __device__ __forceinline__ double lse_to_double(double a) { return a; }
 
-// Per filter f (one CTA each): the maximum m of its log-weights, then with w = exp(lw - m)
-// out[f] = m + log sum w (Appendix E's max-shift) and ess[f] = (sum w)^2 / sum w^2 (the
-// effective sample size of Section 4.3); either output may be null. The exponentials in
-// the log-weights' type, the per-thread sums in two-float (binary32) or binary64, the CTA's
-// sums in binary64. A filter that is empty or whose weights are all zero gets -inf and 0;
-// NaN / +inf log-weights are flagged.
+// B* of Eq. B for beta = mean w / max w (Section 2.1): ceil(log eps / log(1 - beta)), at
+// least 1; 1 for beta >= 1 (every proposal is accepted) or beta <= 0 (no weight: Metropolis
+// accepts any proposal from a zero-weight state); clamped to 2^31 - 1.
+__device__ __forceinline__ int32_t metropolis_B_of(double beta, double log_eps) {
+  if (!(beta > 0.0) || beta >= 1.0) return 1;
+  const double b = ceil(log_eps / log1p(-beta));
+  if (!(b <= 2147483647.0)) return 2147483647;
+  return b < 1.0 ? 1 : static_cast<int32_t>(b);
+}
+
+// Per filter f (one CTA each): the maximum m of its n log-weights, then with w = exp(lw - m)
+// (so max w = 1): log_total[f] = m + log sum w (Appendix E's max-shift), ess[f] = (sum w)^2 /
+// sum w^2 (the effective sample size of Section 4.3), beta[f] = sum w / n = mean w / max w
+// (Eq. beta2 evaluated on the filter's own weights) and B[f] = Eq. B for it; null outputs
+// are skipped. The exponentials in the log-weights' type, the per-thread sums in two-float
+// (binary32) or binary64, the CTA's sums in binary64. A filter that is empty or whose weights
+// are all zero gets -inf, 0, 0 and B = 1; NaN / +inf log-weights are flagged.
 template <typename T>
 __global__ void __launch_bounds__(kBlock)
 log_sum_batched_kernel(const T* __restrict__ lw, const int64_t* __restrict__ off, int F,
-                       int64_t cap, double* __restrict__ out, double* __restrict__ ess,
-                       int* err) {
+                       int64_t cap, WeightStatsOut o, int* err) {
   pdl_wait();
   const int f = blockIdx.x;
   const int64_t lo = __ldg(off + f), hi = __ldg(off + f + 1);
@@ -166,8 +176,10 @@ log_sum_batched_kernel(const T* __restrict__ lw, const int64_t* __restrict__ off
   __syncthreads();
   if (md == -INFINITY) {
     if (threadIdx.x == 0) {
-      if (out) out[f] = -INFINITY;
-      if (ess) ess[f] = 0.0;
+      if (o.log_total) o.log_total[f] = -INFINITY;
+      if (o.ess) o.ess[f] = 0.0;
+      if (o.beta) o.beta[f] = 0.0;
+      if (o.B) o.B[f] = 1;
     }
     return;
   }
@@ -193,8 +205,11 @@ log_sum_batched_kernel(const T* __restrict__ lw, const int64_t* __restrict__ off
       t += sh[k];
       t2 += sh2[k];
     }
-    if (out) out[f] = md + log(t);
-    if (ess) ess[f] = t2 > 0.0 ? (t * t) / t2 : 0.0;
+    if (o.log_total) o.log_total[f] = md + log(t);
+    if (o.ess) o.ess[f] = t2 > 0.0 ? (t * t) / t2 : 0.0;
+    const double beta = t / static_cast<double>(hi - lo);
+    if (o.beta) o.beta[f] = beta;
+    if (o.B) o.B[f] = metropolis_B_of(beta, o.log_eps);
   }
 }
 
@@ -308,16 +323,17 @@ cudaError_t launch_lgssm_step_batched(const Scratch& s, float* x, const int64_t*
   return cudaGetLastError();
 }
 
-cudaError_t launch_log_sum_batched(const Scratch& s, bool f64, const void* logw,
-                                   const int64_t* offsets, int F, double* out, double* ess,
-                                   cudaStream_t st) {
-  trace_mark(s.trace, ess ? "ess_batched" : "log_sum_batched", st);
+cudaError_t launch_weight_stats_batched(const Scratch& s, bool f64, const void* logw,
+                                        const int64_t* offsets, int F, const WeightStatsOut& o,
+                                        cudaStream_t st) {
+  trace_mark(s.trace, o.B ? "metropolis_B_batched" : o.ess ? "ess_batched" : "log_sum_batched",
+             st);
   if (f64)
     launch_pdl(log_sum_batched_kernel<double>, F, kBlock, st, static_cast<const double*>(logw),
-               offsets, F, s.max_n, out, ess, s.err);
+               offsets, F, s.max_n, o, s.err);
   else
     launch_pdl(log_sum_batched_kernel<float>, F, kBlock, st, static_cast<const float*>(logw),
-               offsets, F, s.max_n, out, ess, s.err);
+               offsets, F, s.max_n, o, s.err);
   return cudaGetLastError();
 }
 

@@ -123,3 +123,104 @@ def test_batched_full_workload_4096_filters(rs):
                     want = _single(rs, hh, scheme, lw[lo:hi], f, False, 0, B_f=int(Bs[f]),
                                    seed=5, step=0)
                     assert np.array_equal(af, want), f
+
+
+@pytest.mark.parametrize("dtype", [np.float32, np.float64])
+def test_launch_shapes_give_identical_ancestors(rs, dtype):
+    """Every launch shape of the batched Metropolis kernel and of the batched Permute (threads
+    per CTA x particles per thread) gives the same ancestors, bit for bit: the shape changes
+    which thread runs a particle, not its draws, chain, claim or slot."""
+    offsets, lw = _batch(SIZES, dtype, seed=12)
+    t = torch.from_numpy(lw).to(DEV)
+    off = torch.from_numpy(offsets).to(DEV)
+    kernel = rs.BATCHED_METROPOLIS_F64 if dtype == np.float64 else rs.BATCHED_METROPOLIS_F32
+    with rs.Handle(1 << 20) as hh:
+        assert rs.rs_get_batched_launch(hh, kernel) == (256, 1)
+        base = [rs.rs_resample_batched(hh, rs.METROPOLIS, t, off, B=9, seed=2, step=3,
+                                       permute=p).cpu().numpy() for p in (False, True)]
+        assert rs.rs_last_error(hh) == rs.RS_OK
+        for block, ipt in ((32, 1), (128, 4), (512, 2), (96, 3), (512, 16)):
+            rs.rs_set_batched_launch(hh, kernel, block, ipt)
+            rs.rs_set_batched_launch(hh, rs.BATCHED_PERMUTE, 640 - block if block > 128 else
+                                     block, 17 - ipt if ipt > 8 else ipt)
+            for p, want in zip((False, True), base):
+                got = rs.rs_resample_batched(hh, rs.METROPOLIS, t, off, B=9, seed=2, step=3,
+                                             permute=p).cpu().numpy()
+                assert rs.rs_last_error(hh) == rs.RS_OK
+                assert np.array_equal(got, want), (block, ipt, p)
+        for bad in ((0, 1), (48, 1), (1024, 1), (256, 0), (256, 17)):
+            with pytest.raises(rs.RsError):
+                rs.rs_set_batched_launch(hh, kernel, *bad)
+        with pytest.raises(rs.RsError):
+            rs.rs_set_batched_launch(hh, 3, 256, 1)
+
+
+def test_tuner_keeps_a_valid_shape_and_the_results(rs, tmp_path):
+    """rs_tune_batched leaves the fastest measured shapes in the handle (valid ones); the
+    ancestors after tuning equal those before; autotune_batched caches the choice and
+    re-applies it to a fresh handle without tuning."""
+    from paper_1301_4019_gb300 import tune
+    offsets, lw = _batch([5000, 17, 30000, 1, 4096] * 8, np.float32, seed=13)
+    t = torch.from_numpy(lw).to(DEV)
+    off = torch.from_numpy(offsets).to(DEV)
+    with rs.Handle(1 << 20) as hh:
+        before = rs.rs_resample_batched(hh, rs.METROPOLIS, t, off, B=12, seed=4,
+                                        permute=True).cpu().numpy()
+        shapes = rs.rs_tune_batched(hh, t, off, B=12, reps=2)
+        assert rs.rs_last_error(hh) == rs.RS_OK
+        for block, ipt in shapes.values():
+            assert block in (128, 256, 512) and ipt in (1, 2, 4)
+        after = rs.rs_resample_batched(hh, rs.METROPOLIS, t, off, B=12, seed=4,
+                                       permute=True).cpu().numpy()
+        assert rs.rs_last_error(hh) == rs.RS_OK
+        assert np.array_equal(before, after)
+        path = str(tmp_path / "shapes.json")
+        first = tune.autotune_batched(hh, t, off, B=12, reps=1, cache_path=path)
+        assert not first["cached"]
+    with rs.Handle(1 << 20) as fresh:
+        again = tune.autotune_batched(fresh, t, off, B=12, cache_path=path)
+        assert again["cached"] and again["metropolis"] == first["metropolis"]
+        assert rs.rs_get_batched_launch(fresh, rs.BATCHED_METROPOLIS_F32) == first["metropolis"]
+        assert rs.rs_get_batched_launch(fresh, rs.BATCHED_PERMUTE) == first["permute"]
+    cap = torch.cuda.Stream()
+    with torch.cuda.stream(cap), rs.Handle(1 << 20) as hh:
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=cap):
+            t2 = t + 0  # the graph is not empty
+            with pytest.raises(rs.RsError):  # timing needs real executions
+                rs.rs_tune_batched(hh, t, off, B=12, stream=cap)
+        del t2
+
+
+@pytest.mark.parametrize("dtype", [np.float32, np.float64])
+def test_metropolis_B_per_filter_from_the_weights(rs, h, dtype):
+    """rs_metropolis_B_batched: beta_f = mean w / max w within 1e-6 of the host's binary64
+    value, B_f = Eq. B for the device's beta (the host's rs_metropolis_B on it), B = 1 for
+    empty and all-zero filters; the B array drives rs_resample_batched directly."""
+    sizes = [1, 0, 5000, 300, 70001, 2, 4096]
+    offsets, lw = _batch(sizes, dtype, seed=21)
+    lw[offsets[5]:offsets[6]] = -np.inf   # an all-zero filter
+    t = torch.from_numpy(lw).to(DEV)
+    off = torch.from_numpy(offsets).to(DEV)
+    beta = torch.empty(len(sizes), dtype=torch.float64, device=DEV)
+    B = rs.rs_metropolis_B_batched(h, t, off, eps=0.01, beta=beta)
+    assert rs.rs_last_error(h) == rs.RS_OK
+    B, beta = B.cpu().numpy(), beta.cpu().numpy()
+    for f in range(len(sizes)):
+        seg = lw[offsets[f]:offsets[f + 1]].astype(np.float64)
+        if seg.size == 0 or np.all(seg == -np.inf):
+            assert B[f] == 1 and beta[f] == 0.0, f
+            continue
+        w = np.exp(seg - seg.max())
+        want_beta = w.mean()
+        assert abs(beta[f] - want_beta) <= 1e-6 * want_beta, (f, beta[f], want_beta)
+        assert B[f] == rs.rs_metropolis_B(0.01, float(beta[f])), (f, B[f], beta[f])
+    a = rs.rs_resample_batched(h, rs.METROPOLIS, t, off,
+                               B_per_filter=torch.from_numpy(B).to(DEV), seed=6)
+    assert rs.rs_last_error(h) == rs.RS_OK
+    a = a.cpu().numpy()
+    st, want = oracle.metropolis(lw[offsets[2]:offsets[3]], int(B[2]), seed=6, step=0,
+                                 filter_=2)
+    assert st == oracle.OK and np.array_equal(a[offsets[2]:offsets[3]], want)
+    with pytest.raises(rs.RsError):
+        rs.rs_metropolis_B_batched(h, t, off, eps=1.0)
