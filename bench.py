@@ -223,25 +223,25 @@ class ClockSampler:
 # headers it includes, hashed; `traffic` is null once any of them has changed.
 # ---------------------------------------------------------------------------------------
 NCU_TRAFFIC = {  # label: (bytes per launch, source hash)
-               "permute": (8393199, "d1bec482251ad289"),
-               "metropolis_f64": (12599771, "be5e05fb767d0792"),
-               "metropolis_f32": (8402560, "be5e05fb767d0792"),
-               "rejection_f64": (8412233, "be5e05fb767d0792"),
-               "permute_sorted": (8397408, "d1bec482251ad289"),
-               "rejection_f32": (4209856, "be5e05fb767d0792"),
-               "fused_stratified_f64": (8489856, "2d7ce1f5369a295d"),
-               "fused_multinomial_f64": (8492512, "2d7ce1f5369a295d"),
-               "fused_systematic_f64": (8482496, "2d7ce1f5369a295d"),
-               "fused_stratified_f32": (4261696, "2d7ce1f5369a295d"),
-               "fused_multinomial_f32": (4280064, "2d7ce1f5369a295d"),
-               "fused_systematic_f32": (4261376, "2d7ce1f5369a295d"),
-               "iscan": (4212864, "d1bec482251ad289"),
-               "search_f64": (16783360, "ca9fe6017c87627e"),
-               "search_f32": (12591968, "ca9fe6017c87627e"),
-               "fill": (8695, "d1bec482251ad289"),
-               "cumoff_to_ancestors": (4199185, "d1bec482251ad289"),
-               "offspring": (8391369, "d1bec482251ad289"),
-               "adjacent_difference": (4197410, "d1bec482251ad289")}
+               "permute": (8393383, "d1bec482251ad289"),
+               "metropolis_f64": (12606354, "ef0872bb78ac17a1"),
+               "metropolis_f32": (8403840, "ef0872bb78ac17a1"),
+               "permute_sorted": (8397120, "d1bec482251ad289"),
+               "rejection_f64": (8409271, "ef0872bb78ac17a1"),
+               "fused_stratified_f64": (8489376, "2d7ce1f5369a295d"),
+               "rejection_f32": (4213376, "ef0872bb78ac17a1"),
+               "fused_multinomial_f64": (8491808, "2d7ce1f5369a295d"),
+               "fused_systematic_f64": (8482656, "2d7ce1f5369a295d"),
+               "fused_multinomial_f32": (4278304, "2d7ce1f5369a295d"),
+               "fused_stratified_f32": (4261376, "2d7ce1f5369a295d"),
+               "fused_systematic_f32": (4259360, "2d7ce1f5369a295d"),
+               "iscan": (4213010, "d1bec482251ad289"),
+               "search_f64": (16785312, "ca9fe6017c87627e"),
+               "search_f32": (12591680, "ca9fe6017c87627e"),
+               "fill": (8764, "d1bec482251ad289"),
+               "cumoff_to_ancestors": (4199834, "d1bec482251ad289"),
+               "offspring": (8391259, "d1bec482251ad289"),
+               "adjacent_difference": (4197308, "d1bec482251ad289")}
 
 _LABEL_FILES = (("fused_", "fused.cu"), ("permute", "aux.cu"), ("iscan", "aux.cu"),
                 ("fill", "aux.cu"), ("offspring", "aux.cu"), ("adjacent", "aux.cu"),

@@ -11,6 +11,34 @@
 namespace rsk {
 namespace {
 
+// ---------------------------------------------------------------------------------------
+// The acceptance test u < exp_pinned(delta) (delta < 0) without evaluating the pinned
+// polynomial in almost every case. e = 2^(delta log2 e) from the hardware approximation
+// (PTX ex2.approx) is within a relative 1e-5 of exp(delta) for delta >= -86.5: rounding
+// delta * log2 e (relative 2^-24, plus 2^-25.6 for log2 e in binary32) moves the exponent by
+// at most 86.5 * 8e-8 = 7e-6 in relative terms of the result, the approximation itself is
+// accurate to about 2^-22, and exp_pinned is within 2^-22 of exp. exp_pinned(delta) therefore
+// lies in [e (1 - 2^-15), e (1 + 2^-15)] (a margin of about 4x), so u below the lower end
+// accepts, u at or above the upper end rejects, and only u inside the band (probability
+// about 6e-5 e) evaluates exp_pinned: the decision is that of u < exp_pinned(delta) always.
+// Below -86.5 exp_pinned is 0 and NaN compares false, so the test is false there.
+// ---------------------------------------------------------------------------------------
+constexpr float kExpBand = 0x1p-15f;
+
+__device__ __forceinline__ float exp_band_estimate(float delta) {
+  float e;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(e) : "f"(__fmul_rn(delta, 0x1.715476p+0f)));
+  return e;
+}
+
+__device__ __forceinline__ bool u_below_exp(float u, float delta) {
+  if (!(delta >= -86.5f)) return false;
+  const float e = exp_band_estimate(delta);
+  if (u < __fmul_rd(e, 1.0f - kExpBand)) return true;
+  if (u >= __fmul_ru(e, 1.0f + kExpBand)) return false;
+  return u < exp_pinned(delta);
+}
+
 // u < w^j / w^k from log-weights: a ratio >= 1 or a zero-weight current state accepts.
 template <typename T>
 __device__ __forceinline__ bool metropolis_accept(T lwk, T lwj, T u) {
@@ -18,6 +46,12 @@ __device__ __forceinline__ bool metropolis_accept(T lwk, T lwj, T u) {
   const T delta = lwj - lwk;
   if (delta >= T(0)) return true;
   return u < exp_pinned(delta);
+}
+__device__ __forceinline__ bool metropolis_accept(float lwk, float lwj, float u) {
+  if (lwk == neg_inf<float>()) return true;
+  const float delta = lwj - lwk;
+  if (delta >= 0.0f) return true;
+  return u_below_exp(u, delta);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -70,13 +104,14 @@ __device__ __forceinline__ bool f64_accept_lt(double lwj, float lwj_f, bool okj,
   // u lies in [x0 2^-32, (x0 + 1) 2^-32)
   const float u_lo = __fmul_rn(__uint2float_rd(x.x), 0x1p-32f);
   const float u_hi = __fmul_rn(__fadd_ru(__uint2float_ru(x.x), 1.0f), 0x1p-32f);
-  const float ef = exp_pinned(df);
-  if (ef == 0.0f) {  // exp(df) < 2^-124: the binary64 ratio is below e^-86 < 2^-32 <= u
+  if (!(df >= -86.5f)) {  // exp(df) < 2^-124: the binary64 ratio is below e^-86 < 2^-32 <= u
     if (x.x != 0u) return false;
     return exact_f64_less_exp(lwj, lwk, x);
   }
-  // exp(lwj - lwk) within ef * exp(+-E) * (1 +- 2^-23) (1 +- 2^-52); m bounds all of it
-  const float m = __fmaf_ru(E, 1.02f, 0x1p-21f);
+  // ef = exp(df) within a relative 1e-5 (exp_band_estimate); exp(lwj - lwk) within
+  // ef * exp(+-E) * (1 +- 1e-5) (1 +- 2^-52): m bounds all of it
+  const float ef = exp_band_estimate(df);
+  const float m = __fmaf_ru(E, 1.02f, kExpBand);
   const float lo = __fmul_rd(ef, __fsub_rd(1.0f, m));
   const float hi = __fmul_ru(ef, __fadd_ru(1.0f, m));
   if (u_hi < lo) return true;
@@ -288,7 +323,7 @@ __device__ __forceinline__ bool rejection_accept(const RejBound& rb, uint4 x, fl
     if (!rb.clamp) flag_error(err, RS_ERR_BOUND_VIOLATED);
     return true;
   }
-  return delta == 0.0f || u < exp_pinned(delta);
+  return delta == 0.0f || u_below_exp(u, delta);
 }
 
 __device__ __forceinline__ bool rejection_accept(const RejBound& rb, uint4 x, double lwj,
