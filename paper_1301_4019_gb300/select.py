@@ -9,6 +9,9 @@ fastest scheme; with ``unbiased=True`` (the default) the Metropolis resampler, w
 for finite B (Section 2.1), is not considered. The skew can be given as y (the workload's
 observation, log w = -(y - x)^2 / 2 with x ~ N(0, 1)) or as beta = E(w)/w_max (Eq. beta2),
 which for that workload is exp(-y^2/4)/sqrt(2). Host-only, no GPU needed.
+
+The table is regenerated from a sweep's JSON line with
+``python -m paper_1301_4019_gb300.select --from-sweep sweep.json`` (``table_from_sweep``).
 """
 from __future__ import annotations
 
@@ -94,3 +97,34 @@ def choose_scheme(N: int, y: float | None = None, beta: float | None = None,
         if best is None or t < best[1]:
             best = (s, t)
     return best
+
+
+def table_from_sweep(sweep: dict) -> dict:
+    """The decision table from the JSON line of ``bench.py --sweep``: the median microseconds
+    per call of every (dtype, y, log2 N, scheme) row, with the sweep's conditions."""
+    tab = {}
+    for r in sweep["rows"]:
+        tab.setdefault(r["dtype"], {}).setdefault(str(float(r["y"])), {}).setdefault(
+            str(int(r["log2n"])), {})[r["scheme"]] = r["us"]
+    clocks = sweep.get("clocks", {})
+    return {"source": "python bench.py --sweep (one GB300, SM %g MHz, with Permute, L2 flushed; "
+                      "median microseconds per call)" % clocks.get("sm_mhz", float("nan")),
+            "metropolis_B": "Eq. B with eps = 0.01 and beta(y) = exp(-y^2/4)/sqrt(2)",
+            "rejection_log_wmax": 0.0, "us": tab}
+
+
+def _main(argv=None):
+    import argparse
+    p = argparse.ArgumentParser(description="Rebuild decision_gb300.json from a sweep.")
+    p.add_argument("--from-sweep", required=True, help="file holding bench.py --sweep output")
+    p.add_argument("--out", default=os.path.join(os.path.dirname(os.path.abspath(__file__)),
+                                                 "decision_gb300.json"))
+    a = p.parse_args(argv)
+    with open(a.from_sweep) as f:
+        sweep = json.loads(f.read().strip().splitlines()[-1])
+    with open(a.out, "w") as f:
+        json.dump(table_from_sweep(sweep), f, indent=0, sort_keys=True)
+
+
+if __name__ == "__main__":
+    _main()

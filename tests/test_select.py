@@ -41,3 +41,20 @@ def test_beta_and_y_agree():
     with pytest.raises(ValueError):
         select.choose_scheme(100, y=1.0, dtype="f16")
     assert math.isfinite(select.estimated_us("rejection", 1, 1.3))
+
+
+def test_table_from_sweep_and_cli(tmp_path):
+    """The committed generator of the decision table: rows of a sweep line become
+    us[dtype][y][log2 N][scheme]; the CLI writes the same table to the given file."""
+    import json
+    rows = [{"dtype": dt, "y": y, "log2n": n, "scheme": s, "us": 1.0 + n + k}
+            for dt in ("f32", "f64") for y in (0.0, 4.0) for n in (10, 11)
+            for k, s in enumerate(select.SCHEME_ORDER)]
+    sweep = {"rows": rows, "clocks": {"sm_mhz": 2070.0}}
+    t = select.table_from_sweep(sweep)
+    assert t["us"]["f64"]["4.0"]["11"]["rejection"] == 16.0
+    assert set(t["us"]["f32"]) == {"0.0", "4.0"} and "2070" in t["source"]
+    src, out = tmp_path / "sweep.json", tmp_path / "table.json"
+    src.write_text("log line\n" + json.dumps(sweep) + "\n")
+    select._main(["--from-sweep", str(src), "--out", str(out)])
+    assert json.load(open(out)) == json.loads(json.dumps(t))
