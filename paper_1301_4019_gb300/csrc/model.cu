@@ -126,6 +126,10 @@ __device__ __forceinline__ void lse_acc(double& acc, double& acc2, double x, dou
   acc += e;
   acc2 += e * e;
 }
+__device__ __forceinline__ void lse_acc(float2& acc, float x, float m) {
+  acc = add21(acc, expf(x - m));
+}
+__device__ __forceinline__ void lse_acc(double& acc, double x, double m) { acc += exp(x - m); }
 __device__ __forceinline__ double lse_to_double(float2 a) { return vto_double(a); }
 __device__ __forceinline__ double lse_to_double(double a) { return a; }
 
@@ -145,8 +149,9 @@ __device__ __forceinline__ int32_t metropolis_B_of(double beta, double log_eps) 
 // (Eq. beta2 evaluated on the filter's own weights) and B[f] = Eq. B for it; null outputs
 // are skipped. The exponentials in the log-weights' type, the per-thread sums in two-float
 // (binary32) or binary64, the CTA's sums in binary64. A filter that is empty or whose weights
-// are all zero gets -inf, 0, 0 and B = 1; NaN / +inf log-weights are flagged.
-template <typename T>
+// are all zero gets -inf, 0, 0 and B = 1; NaN / +inf log-weights are flagged. SQ: the sum of
+// squares is formed (only the ESS needs it; the sum of w is the same either way).
+template <typename T, bool SQ>
 __global__ void __launch_bounds__(kBlock)
 log_sum_batched_kernel(const T* __restrict__ lw, const int64_t* __restrict__ off, int F,
                        int64_t cap, WeightStatsOut o, int* err) {
@@ -186,13 +191,17 @@ log_sum_batched_kernel(const T* __restrict__ lw, const int64_t* __restrict__ off
   const T mt = static_cast<T>(md);
   using Acc = typename std::conditional<sizeof(T) == 4, float2, double>::type;
   Acc acc{}, acc2{};
-  for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x)
-    lse_acc(acc, acc2, __ldg(lw + i), mt);
+  for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+    if constexpr (SQ)
+      lse_acc(acc, acc2, __ldg(lw + i), mt);
+    else
+      lse_acc(acc, __ldg(lw + i), mt);
+  }
   double sum = lse_to_double(acc), sum2 = lse_to_double(acc2);
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
     sum += __shfl_xor_sync(0xffffffffu, sum, o);
-    sum2 += __shfl_xor_sync(0xffffffffu, sum2, o);
+    if constexpr (SQ) sum2 += __shfl_xor_sync(0xffffffffu, sum2, o);
   }
   if ((threadIdx.x & 31) == 0) {
     sh[threadIdx.x >> 5] = sum;
@@ -328,12 +337,20 @@ cudaError_t launch_weight_stats_batched(const Scratch& s, bool f64, const void* 
                                         cudaStream_t st) {
   trace_mark(s.trace, o.B ? "metropolis_B_batched" : o.ess ? "ess_batched" : "log_sum_batched",
              st);
-  if (f64)
-    launch_pdl(log_sum_batched_kernel<double>, F, kBlock, st, static_cast<const double*>(logw),
-               offsets, F, s.max_n, o, s.err);
+  const auto* l32 = static_cast<const float*>(logw);
+  const auto* l64 = static_cast<const double*>(logw);
+  if (f64 && o.ess)
+    launch_pdl(log_sum_batched_kernel<double, true>, F, kBlock, st, l64, offsets, F, s.max_n, o,
+               s.err);
+  else if (f64)
+    launch_pdl(log_sum_batched_kernel<double, false>, F, kBlock, st, l64, offsets, F, s.max_n, o,
+               s.err);
+  else if (o.ess)
+    launch_pdl(log_sum_batched_kernel<float, true>, F, kBlock, st, l32, offsets, F, s.max_n, o,
+               s.err);
   else
-    launch_pdl(log_sum_batched_kernel<float>, F, kBlock, st, static_cast<const float*>(logw),
-               offsets, F, s.max_n, o, s.err);
+    launch_pdl(log_sum_batched_kernel<float, false>, F, kBlock, st, l32, offsets, F, s.max_n, o,
+               s.err);
   return cudaGetLastError();
 }
 
