@@ -85,6 +85,8 @@ def parse_args():
                    "and MSE / N of the five resamplers over N and y, binary32 and binary64")
     p.add_argument("--accuracy-sizes", default="4,8,12,16,18,20,22",
                    help="log2 N of the accuracy experiment")
+    p.add_argument("--philox-peak", action="store_true",
+                   help="measure the Philox4x32-10 throughput (rs_philox_throughput)")
     p.add_argument("--single", default=None,
                    help="profile one call: scheme:dtype[:prec], e.g. metropolis:f32 "
                         "(runs warmup + steps calls with Permute, prints one JSON line)")
@@ -325,6 +327,32 @@ def kernel_roofline_units(label: str, N: int, B: int):
 # ---------------------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------------------
+def measure_philox_peak(rs, h, draws_per_thread: int = 1024, reps: int = 5) -> dict:
+    """The Philox4x32-10 throughput of this GPU (rs_philox_throughput: 2048 threads per SM,
+    each drawing `draws_per_thread` blocks; median of `reps` launches timed with CUDA events),
+    the peak of the Philox-bound kernels (Metropolis, rejection), beside the figure derived
+    from unit counts (152 SMs x 2070 MHz x 32 IMAD.WIDE per clock / 20 per draw)."""
+    import torch
+    sms = torch.cuda.get_device_properties(h.device).multi_processor_count
+    threads = sms * 2048
+    out = torch.empty(1, dtype=torch.int32, device=torch.device("cuda", h.device))
+    for _ in range(2):
+        rs.rs_philox_throughput(h, threads, draws_per_thread, seed=1, out=out)
+    times = []
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        rs.rs_philox_throughput(h, threads, draws_per_thread, seed=1, out=out)
+        e1.record()
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+    ms = statistics.median(times)
+    return {"measured_G_per_s": round(threads * draws_per_thread / (ms * 1e-3) / 1e9, 1),
+            "derived_G_per_s": round(152 * 2.070 * 32 / 20, 1),
+            "threads": threads, "draws_per_thread": draws_per_thread,
+            "ms_per_launch": round(ms, 4)}
+
+
 def run_ours(args):
     import torch
     import paper_1301_4019_gb300 as rs
@@ -352,6 +380,7 @@ def run_ours(args):
     conv = {name: [torch.empty(N, dtype=torch.int32, device=dev) for _ in range(4)]
             for name, _, _ in dtypes}
     h = rs.Handle(N)
+    philox = measure_philox_peak(rs, h)
     rs.rs_set_launch_mode(h, LAUNCH_MODES[args.launch_mode])
 
     def step(k):
@@ -477,12 +506,11 @@ def run_ours(args):
                 "traffic_note": "ncu dram bytes per launch, cold-cache replay (profiles/)",
                 "algorithmic_bytes_per_launch": amount}
     else:
-        # G Philox4x32-10 draws/s: 152 SMs x 2070 MHz x 32 IMAD.WIDE/clk/SM / 20 per draw
-        philox_peak = 152 * 2.070 * 32 / 20
         achieved = (amount or 0) / (dom_ms * 1e-3) / 1e9
         roof = {"bound": "alu", "kernel": dom_label, "achieved": round(achieved, 1),
-                "peak": philox_peak, "unit": "G Philox/s",
-                "frac": round(achieved / philox_peak, 4), "peak_source": "derived",
+                "peak": philox["measured_G_per_s"], "unit": "G Philox/s",
+                "frac": round(achieved / philox["measured_G_per_s"], 4),
+                "peak_source": "measured (rs_philox_throughput)",
                 "traffic": ncu_traffic(dom_label, N),
                 "traffic_note": "ncu dram bytes per launch, cold-cache replay (profiles/)"}
     roof["share_of_step"] = round(sum(by_label[dom_label]) / total_kernel_ms, 4)
@@ -492,6 +520,11 @@ def run_ours(args):
                         "launches_per_step": round(len(ds) / args.steps, 2),
                         "share": round(sum(ds) / total_kernel_ms, 4)}
                   for lab, ds in sorted(by_label.items(), key=lambda kv: -sum(kv[1]))}
+    for lab, v in per_kernel.items():  # the Philox-bound kernels against the measured peak
+        b, amt, _ = kernel_roofline_units(lab, N, B)
+        if b == "alu" and amt:
+            v["philox_frac"] = round(amt / (v["mean_us"] * 1e-6) / 1e9
+                                     / philox["measured_G_per_s"], 4)
 
     # per resampler breakdown: sum of the kernels of each resample call
     per_call = {}
@@ -607,6 +640,7 @@ def run_ours(args):
             "per_scheme_note": "one call with Permute, traced (kernel-to-kernel events); "
                                "hbm_frac = algorithmic bytes (sweep_hbm_bytes) / time / peak",
             "per_kernel": per_kernel,
+            "philox_peak": philox,
             "gpu_launches": gpu_launches_per_step * args.steps,
             "gpu_launches_per_step": gpu_launches_per_step,
             "traced_ms_per_step": round(ms_traced_total / args.steps, 5),
@@ -1432,6 +1466,10 @@ def main():
         run_metropolis_b(args)
     elif args.accuracy:
         run_accuracy(args)
+    elif args.philox_peak:
+        import paper_1301_4019_gb300 as rs
+        with rs.Handle(1024) as h:
+            print(json.dumps({"philox_peak": measure_philox_peak(rs, h, reps=21)}))
     elif args.impl == "reference":
         run_reference(args)
     else:

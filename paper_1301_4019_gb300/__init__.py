@@ -43,7 +43,7 @@ EXPORTED = [
     "rs_resample_batched", "rs_set_launch_mode", "rs_copy_ancestors", "rs_lgssm_step",
     "rs_ess", "rs_resample_prc", "rs_copy_ancestors_batched", "rs_lgssm_step_batched",
     "rs_log_sum_weights_batched", "rs_ess_batched", "rs_metropolis_B_batched",
-    "rs_set_batched_launch", "rs_get_batched_launch", "rs_tune_batched",
+    "rs_set_batched_launch", "rs_get_batched_launch", "rs_tune_batched", "rs_philox_throughput",
     "rs_cumulative_weights_f64",
     "rs_capture_if_below",
     "rs_capture_end_if", "rs_smc_mark_resampled", "rs_smc_loglik_step",
@@ -119,6 +119,7 @@ def _declare(lib):
         "rs_set_batched_launch": (I, [P, I, I, I]),
         "rs_get_batched_launch": (I, [P, I, C.POINTER(I), C.POINTER(I)]),
         "rs_tune_batched": (I, [P, I, P, P, I32, P, I32, I, P]),
+        "rs_philox_throughput": (I, [P, I64, C.c_uint32, U64, P, P]),
         "rs_capture_if_below": (I, [P, P, C.c_double, P, C.POINTER(P)]),
         "rs_capture_end_if": (I, [P, P]),
         "rs_smc_mark_resampled": (I, [P, P, I64, P, C.c_double, P, P]),
@@ -535,6 +536,20 @@ def rs_tune_batched(h: Handle, logw: torch.Tensor, offsets: torch.Tensor, B: int
     k = BATCHED_METROPOLIS_F64 if logw.dtype == torch.float64 else BATCHED_METROPOLIS_F32
     return {"metropolis": rs_get_batched_launch(h, k),
             "permute": rs_get_batched_launch(h, BATCHED_PERMUTE)}
+
+
+def rs_philox_throughput(h: Handle, threads: int, draws_per_thread: int, seed: int = 0,
+                         out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """Measurement aid (include/resample_measure.h): threads x draws_per_thread Philox blocks,
+    the XOR of all their words left in `out` (one int32 holding the uint32 bits)."""
+    dev = torch.device("cuda", h.device)
+    if out is None:
+        out = torch.empty(1, dtype=torch.int32, device=dev)
+    _check(load().rs_philox_throughput(h.ptr, int(threads), int(draws_per_thread),
+                                       int(seed) & 0xFFFFFFFFFFFFFFFF,
+                                       _dev(out, torch.int32, "out", 1, h), _stream(stream)),
+           "rs_philox_throughput")
+    return out
 
 
 def rs_capture_if_below(h: Handle, value: torch.Tensor, threshold: float, stream=None):

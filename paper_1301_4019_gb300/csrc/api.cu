@@ -7,8 +7,10 @@
 #include <cstring>
 #include <new>
 
+#include "../../include/resample_measure.h"
 #include "common.cuh"
 #include "internal.h"
+#include "measure.h"
 
 struct rs_handle {
   int device;
@@ -548,6 +550,19 @@ int rs_metropolis_B_batched(rs_handle* h, int dtype, const void* logw_dev,
   return cuda_status(e);
 }
 
+
+int rs_philox_throughput(rs_handle* h, int64_t threads, uint32_t draws_per_thread,
+                         uint64_t seed, uint32_t* xor_dev, void* stream) {
+  if (!h || !xor_dev || threads < 1 || threads > (int64_t{1} << 32) || draws_per_thread < 1)
+    return RS_ERR_ARG;
+  int st = set_device(h);
+  if (st != RS_OK) return st;
+  const cudaStream_t s = as_stream(stream);
+  rsk::trace_mark(h->s.trace, "philox_throughput", s);
+  const cudaError_t e = rsk::launch_philox_throughput(threads, draws_per_thread, seed, xor_dev, s);
+  end_mark(h, s);
+  return cuda_status(e);
+}
 
 int rs_set_batched_launch(rs_handle* h, int kernel, int block, int items_per_thread) {
   if (!h || kernel < 0 || kernel >= rsk::kCfgCount) return RS_ERR_ARG;

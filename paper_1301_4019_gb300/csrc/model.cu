@@ -7,6 +7,7 @@
 
 #include "common.cuh"
 #include "internal.h"
+#include "measure.h"
 #include "values.cuh"
 
 namespace rsk {
@@ -222,6 +223,24 @@ log_sum_batched_kernel(const T* __restrict__ lw, const int64_t* __restrict__ off
   }
 }
 
+// Philox throughput: thread i draws the blocks (i, n), n < J, under the given keys and XORs
+// all their words; the warps' XORs are folded into *out (zeroed before the launch).
+__global__ void __launch_bounds__(kBlock)
+philox_xor_kernel(Keys keys, int64_t T, uint32_t J, uint32_t* out) {
+  pdl_wait();
+  const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  uint32_t acc = 0;
+  if (i < T) {
+    for (uint32_t n = 0; n < J; ++n) {
+      const uint4 x = draw(keys, static_cast<uint32_t>(i), n);
+      acc ^= x.x ^ x.y ^ x.z ^ x.w;
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc ^= __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0 && acc != 0u) atomicXor(out, acc);
+}
+
 // ---------------------------------------------------------------------------------------
 // Resampling on demand inside a CUDA graph: the decision, and the bookkeeping of the
 // adaptive filter's likelihood, on the device.
@@ -351,6 +370,16 @@ cudaError_t launch_weight_stats_batched(const Scratch& s, bool f64, const void* 
   else
     launch_pdl(log_sum_batched_kernel<float, false>, F, kBlock, st, l32, offsets, F, s.max_n, o,
                s.err);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_philox_throughput(int64_t threads, uint32_t draws_per_thread, uint64_t seed,
+                                     uint32_t* xor_out, cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(xor_out, 0, sizeof(uint32_t), st);
+  if (e != cudaSuccess) return e;
+  const Keys keys = make_keys(seed, 0, 0u, 6u);
+  launch_pdl(philox_xor_kernel, static_cast<int>((threads + kBlock - 1) / kBlock), kBlock, st,
+             keys, threads, draws_per_thread, xor_out);
   return cudaGetLastError();
 }
 

@@ -1,5 +1,5 @@
 """CPU checks of the C ABI: the library builds for sm_103a, loads, exports every symbol that
-include/resample.h declares, and its host-only calls behave (no GPU needed)."""
+the headers under include/ declare, and its host-only calls behave (no GPU needed)."""
 import ctypes as C
 import math
 import os
@@ -14,7 +14,9 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
 def _declared_symbols():
-    text = open(os.path.join(ROOT, "include", "resample.h")).read()
+    inc = os.path.join(ROOT, "include")
+    text = "".join(open(os.path.join(inc, f)).read() for f in sorted(os.listdir(inc))
+                   if f.endswith(".h"))
     return sorted(set(re.findall(r"^\s*(?:int|const char\*|void)\s+(rs_\w+)\s*\(", text, re.M)))
 
 

@@ -471,3 +471,20 @@ def test_convenience_resample_matches_the_handle_call(rs, h):
     bad = torch.tensor([0.0, float("nan")], dtype=torch.float64, device=DEV)
     with pytest.raises(rs.RsError):
         rs.resample(bad, "metropolis", B=4)
+
+
+def test_philox_throughput_kernel_draws_the_oracle_blocks(rs, h):
+    """The measurement kernel behind the Philox roofline runs the resamplers' Philox: the XOR
+    of the words of blocks (i, n, 0, 6), i < T, n < J, equals the oracle's."""
+    T, J, seed = 1000, 7, 99
+    got = rs.rs_philox_throughput(h, T, J, seed=seed).item() & 0xFFFFFFFF
+    want = 0
+    for i in range(T):
+        for n in range(J):
+            x = oracle.draw(seed, i, n, 0, 0, 6)
+            want ^= int(x[0]) ^ int(x[1]) ^ int(x[2]) ^ int(x[3])
+    assert got == want
+    with pytest.raises(rs.RsError):
+        rs.rs_philox_throughput(h, 0, 1)
+    with pytest.raises(rs.RsError):
+        rs.rs_philox_throughput(h, 10, 0)
