@@ -492,10 +492,12 @@ def run_ours(args):
     dom_ms = statistics.mean(by_label[dom_label])
     launches_per_step_dom = len(by_label[dom_label]) / args.steps
     bound, amount, unit = kernel_roofline_units(dom_label, N, B)
+    # rejection: expected attempts per call N + sum_i (1 - w_i/w_max) / p, p = mean(w)/w_max
+    # (w_max = 1: log w_max = 0), one Philox draw each
+    w = np.exp(pools["f64"][0].double().cpu().numpy())
+    rej_attempts = int(N + np.sum(1.0 - w) / w.mean())
     if dom_label.startswith("rejection_"):
-        # expected attempts per call: N + sum_i (1 - w_i/w_max) / p, p = mean(w)/w_max
-        w = np.exp(pools["f64"][0].double().cpu().numpy())
-        amount = int(N + np.sum(1.0 - w) / w.mean())
+        amount = rej_attempts
     if bound == "hbm":
         achieved = amount / (dom_ms * 1e-3) / 1e9 if amount is not None else None
         roof = {"bound": "hbm", "kernel": dom_label,
@@ -522,6 +524,9 @@ def run_ours(args):
                   for lab, ds in sorted(by_label.items(), key=lambda kv: -sum(kv[1]))}
     for lab, v in per_kernel.items():  # the Philox-bound kernels against the measured peak
         b, amt, _ = kernel_roofline_units(lab, N, B)
+        if lab.startswith("rejection_"):
+            amt = rej_attempts
+            v["expected_trials_per_particle"] = round(rej_attempts / N, 3)
         if b == "alu" and amt:
             v["philox_frac"] = round(amt / (v["mean_us"] * 1e-6) / 1e9
                                      / philox["measured_G_per_s"], 4)
