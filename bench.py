@@ -1189,6 +1189,39 @@ def run_smc(args):
                          "G_particle_steps_per_s": round(total * T / (ms * 1e-3) / 1e9, 3),
                          "loglik_mean": round(float(np.mean(lls)), 4),
                          "loglik_sd": round(float(np.std(lls, ddof=1)), 4)})
+        # resampling on demand for every filter of the batch, decided on the device
+        for scheme in (rs.SYSTEMATIC,):
+            bufs = smc.BatchedLgssmBuffers(sizes, np.repeat(np.asarray(y)[:, None], 256, axis=1))
+            cs = torch.cuda.Stream()
+            cs.wait_stream(torch.cuda.current_stream())
+            with torch.cuda.stream(cs):
+                flags = smc.lgssm_batched_adaptive_launch(hb, bufs, scheme, phi, sx, sy, 0.5,
+                                                          seed=3, B=64, stream=cs)
+                torch.cuda.synchronize()
+                lls = smc.lgssm_batched_adaptive_loglik_from(bufs, flags, sy)
+                n_res = flags[1:].sum(dim=0).cpu().numpy()
+                g = torch.cuda.CUDAGraph()
+                with torch.cuda.graph(g, stream=cs):
+                    smc.lgssm_batched_adaptive_launch(hb, bufs, scheme, phi, sx, sy, 0.5,
+                                                      seed=3, B=64, stream=cs)
+            torch.cuda.current_stream().wait_stream(cs)
+            g.replay()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(reps):
+                g.replay()
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / reps
+            rows.append({"scheme": SCHEME_NAMES[scheme] + " (256 filters, batched, ESS < N/2 "
+                                                            "per filter)",
+                         "filters": 256, "particles": total,
+                         "ms_per_filter": round(ms, 3), "us_per_step": round(1e3 * ms / T, 2),
+                         "G_particle_steps_per_s": round(total * T / (ms * 1e-3) / 1e9, 3),
+                         "resamplings_mean": round(float(n_res.mean()), 2),
+                         "loglik_mean": round(float(np.mean(lls)), 4),
+                         "loglik_sd": round(float(np.std(lls, ddof=1)), 4)})
         st2 = rs.rs_last_error(hb)
     st = st if st != rs.RS_OK else st2
     clk = clocks.stop()

@@ -310,14 +310,36 @@ int rs_log_sum_weights_batched(rs_handle* h, int dtype, const void* logw_dev,
 /* The effective sample size of every filter of a batch (offsets_dev: F+1 int64 CSR bounds,
  * as for rs_resample_batched): ess_dev[f] = (sum_g w_g)^2 / sum_g w_g^2 over the filter's
  * particles g with w_g = exp(logw_g - max logw), the statistic that decides per filter
- * whether an adaptive filter resamples at a step (Section 4.3), and log_total_dev[f] = the
- * value rs_log_sum_weights_batched writes (same sums, bit for bit). F float64 each on the
- * device; either pointer may be NULL, not both. One CTA per filter, the same arithmetic as
+ * whether an adaptive filter resamples at a step (Section 4.3); log_total_dev[f] = the
+ * value rs_log_sum_weights_batched writes (same sums, bit for bit); below_dev[f] (uint8) =
+ * 1 where ess < threshold_frac * n_f, the filter's resampling decision, ready for
+ * rs_resample_batched_masked and rs_reset_weights_batched. F entries each on the device;
+ * any of the three pointers may be NULL, not all. One CTA per filter, the arithmetic of
  * rs_log_sum_weights_batched with the sum of squares beside the sum. An empty or all-zero
- * filter gets ess 0 and log total -inf (no error); NaN/+inf flag RS_ERR_NONFINITE; offsets
- * outside [0, the handle's max_n] flag RS_ERR_ARG. */
+ * filter gets ess 0, log total -inf and below 0 (no error); NaN/+inf flag RS_ERR_NONFINITE;
+ * offsets outside [0, the handle's max_n] flag RS_ERR_ARG; RS_ERR_ARG on the host for
+ * threshold_frac outside [0, 1] when below_dev is given. */
 int rs_ess_batched(rs_handle* h, int dtype, const void* logw_dev, const int64_t* offsets_dev,
-                   int32_t F, double* ess_dev, double* log_total_dev, void* stream);
+                   int32_t F, double* ess_dev, double* log_total_dev, double threshold_frac,
+                   uint8_t* below_dev, void* stream);
+
+/* rs_resample_batched for the filters f with resample_dev[f] != 0 (F uint8 on the device);
+ * every other filter keeps its particles: its ancestors are the identity a_i = i (with
+ * permute, c_i = i). The flagged filters' ancestors are those of rs_resample_batched, bit
+ * for bit. The resampling on demand of a batch of adaptive filters (Section 4.3), decided on
+ * the device (rs_ess_batched's below flags) without a host round trip. Same arguments and
+ * errors as rs_resample_batched otherwise (NaN checks cover every filter). */
+int rs_resample_batched_masked(rs_handle* h, int scheme, int dtype, const void* logw_dev,
+                               const int64_t* offsets_dev, int32_t F, const int32_t* B_dev,
+                               int32_t B, uint64_t seed, uint64_t step,
+                               const uint8_t* resample_dev, int32_t* ancestors_dev,
+                               int permute, const rs_opts* opts, void* stream);
+
+/* After a masked resampling: the binary32 log-weights of every flagged filter (flags_dev[f]
+ * != 0) set to 0 -- equal weights, the next step's log-likelihood terms are then added to
+ * them -- the other filters' left as they are. */
+int rs_reset_weights_batched(rs_handle* h, float* logw_dev, const int64_t* offsets_dev,
+                             int32_t F, const uint8_t* flags_dev, void* stream);
 
 /* Metropolis B picked per filter from its own weights: beta_dev[f] (may be NULL) = mean w /
  * max w over the filter's particles (the ratio of Eq. beta2, evaluated on the weights rather

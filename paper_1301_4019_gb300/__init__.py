@@ -43,6 +43,7 @@ EXPORTED = [
     "rs_resample_batched", "rs_set_launch_mode", "rs_copy_ancestors", "rs_lgssm_step",
     "rs_ess", "rs_resample_prc", "rs_copy_ancestors_batched", "rs_lgssm_step_batched",
     "rs_log_sum_weights_batched", "rs_ess_batched", "rs_metropolis_B_batched",
+    "rs_resample_batched_masked", "rs_reset_weights_batched",
     "rs_set_batched_launch", "rs_get_batched_launch", "rs_tune_batched", "rs_philox_throughput",
     "rs_cumulative_weights_f64",
     "rs_capture_if_below",
@@ -114,7 +115,10 @@ def _declare(lib):
         "rs_lgssm_step_batched": (I, [P, P, P, I32, I, I, C.c_float, C.c_float, P, C.c_float,
                                       U64, U64, P, P]),
         "rs_log_sum_weights_batched": (I, [P, I, P, P, I32, P, P]),
-        "rs_ess_batched": (I, [P, I, P, P, I32, P, P, P]),
+        "rs_ess_batched": (I, [P, I, P, P, I32, P, P, C.c_double, P, P]),
+        "rs_resample_batched_masked": (I, [P, I, I, P, P, I32, P, I32, U64, U64, P, P, I,
+                                           C.POINTER(_Opts), P]),
+        "rs_reset_weights_batched": (I, [P, P, P, I32, P, P]),
         "rs_metropolis_B_batched": (I, [P, I, P, P, I32, C.c_double, P, P, P]),
         "rs_set_batched_launch": (I, [P, I, I, I]),
         "rs_get_batched_launch": (I, [P, I, C.POINTER(I), C.POINTER(I)]),
@@ -251,25 +255,42 @@ def rs_resample_batched(h: Handle, scheme: int, logw: torch.Tensor, offsets: tor
                         B: int = 0, B_per_filter: torch.Tensor | None = None, seed: int = 0,
                         step: int = 0, out: torch.Tensor | None = None, permute: bool = False,
                         prec: int = PREC_PLAIN, log_wmax: float = 0.0,
-                        max_trials: int = 1 << 20, stream=None) -> torch.Tensor:
+                        max_trials: int = 1 << 20, resample: torch.Tensor | None = None,
+                        stream=None) -> torch.Tensor:
     """Resample F filters in CSR layout (offsets: F+1 int64) in one launch; returns the local
-    ancestors of every filter, concatenated."""
+    ancestors of every filter, concatenated. With ``resample`` (F uint8 flags on the device,
+    e.g. rs_ess_batched's ``below``), only the flagged filters are resampled and the others
+    get the identity (rs_resample_batched_masked)."""
     F = offsets.numel() - 1
     if out is None:
         out = torch.empty(logw.numel(), dtype=torch.int32, device=logw.device)
     opts = _Opts(prec, float(log_wmax), int(max_trials), 0)
     bptr = (_dev(B_per_filter, torch.int32, "B_per_filter", F, h)
             if B_per_filter is not None else None)
-    _check(load().rs_resample_batched(h.ptr, int(scheme), _dtype_code(logw),
-                                      _dev(logw, (torch.float32, torch.float64), "logw", h=h),
-                                      _dev(offsets, torch.int64, "offsets", F + 1, h), F, bptr,
-                                      int(B),
-                                      int(seed) & 0xFFFFFFFFFFFFFFFF,
-                                      int(step) & 0xFFFFFFFFFFFFFFFF,
-                                      _dev(out, torch.int32, "out", logw.numel(), h),
-                                      1 if permute else 0, C.byref(opts), _stream(stream)),
-           "rs_resample_batched")
+    head = (h.ptr, int(scheme), _dtype_code(logw),
+            _dev(logw, (torch.float32, torch.float64), "logw", h=h),
+            _dev(offsets, torch.int64, "offsets", F + 1, h), F, bptr, int(B),
+            int(seed) & 0xFFFFFFFFFFFFFFFF, int(step) & 0xFFFFFFFFFFFFFFFF)
+    tail = (_dev(out, torch.int32, "out", logw.numel(), h), 1 if permute else 0,
+            C.byref(opts), _stream(stream))
+    if resample is None:
+        _check(load().rs_resample_batched(*head, *tail), "rs_resample_batched")
+    else:
+        _check(load().rs_resample_batched_masked(
+            *head, _dev(resample, torch.uint8, "resample", F, h), *tail),
+            "rs_resample_batched_masked")
     return out
+
+
+def rs_reset_weights_batched(h: Handle, logw: torch.Tensor, offsets: torch.Tensor,
+                             flags: torch.Tensor, stream=None) -> torch.Tensor:
+    """Set the log-weights of the flagged filters (F uint8) to 0, in place."""
+    F = offsets.numel() - 1
+    _check(load().rs_reset_weights_batched(h.ptr, _dev(logw, torch.float32, "logw", h=h),
+                                           _dev(offsets, torch.int64, "offsets", F + 1, h), F,
+                                           _dev(flags, torch.uint8, "flags", F, h),
+                                           _stream(stream)), "rs_reset_weights_batched")
+    return logw
 
 
 def rs_cumulative_weights(h: Handle, logw: torch.Tensor, prec: int = PREC_PLAIN,
@@ -478,17 +499,20 @@ def rs_log_sum_weights_batched(h: Handle, logw: torch.Tensor, offsets: torch.Ten
 
 def rs_ess_batched(h: Handle, logw: torch.Tensor, offsets: torch.Tensor,
                    out: torch.Tensor | None = None, log_total: torch.Tensor | None = None,
+                   threshold: float = 0.5, below: torch.Tensor | None = None,
                    stream=None) -> torch.Tensor:
     """Effective sample size of every filter (float64, one per filter); with ``log_total``
-    (F float64), also each filter's log weight total (as rs_log_sum_weights_batched)."""
+    (F float64), also each filter's log weight total (as rs_log_sum_weights_batched); with
+    ``below`` (F uint8), the flags ESS_f < threshold * N_f."""
     F = offsets.numel() - 1
     if out is None:
         out = torch.empty(F, dtype=torch.float64, device=logw.device)
     lt = _dev(log_total, torch.float64, "log_total", F, h) if log_total is not None else None
+    bl = _dev(below, torch.uint8, "below", F, h) if below is not None else None
     _check(load().rs_ess_batched(h.ptr, _dtype_code(logw), _dev(logw, None, "logw", h=h),
                                  _dev(offsets, torch.int64, "offsets", F + 1, h), F,
-                                 _dev(out, torch.float64, "ess", F, h), lt, _stream(stream)),
-           "rs_ess_batched")
+                                 _dev(out, torch.float64, "ess", F, h), lt, float(threshold),
+                                 bl, _stream(stream)), "rs_ess_batched")
     return out
 
 

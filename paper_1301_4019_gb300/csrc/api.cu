@@ -286,10 +286,11 @@ int rs_resample_prc(rs_handle* h, int dtype, const void* logw_dev, int64_t N, do
   return cuda_status(e);
 }
 
-int rs_resample_batched(rs_handle* h, int scheme, int dtype, const void* logw_dev,
-                        const int64_t* offsets_dev, int32_t F, const int32_t* B_dev, int32_t B,
-                        uint64_t seed, uint64_t step, int32_t* ancestors_dev, int permute,
-                        const rs_opts* opts, void* stream) {
+int rs_resample_batched_masked(rs_handle* h, int scheme, int dtype, const void* logw_dev,
+                               const int64_t* offsets_dev, int32_t F, const int32_t* B_dev,
+                               int32_t B, uint64_t seed, uint64_t step,
+                               const uint8_t* resample_dev, int32_t* ancestors_dev, int permute,
+                               const rs_opts* opts, void* stream) {
   if (!h || !logw_dev || !offsets_dev || !ancestors_dev) return RS_ERR_ARG;
   if (F < 1) return RS_ERR_ARG;
   if (F > h->s.max_filters) return RS_ERR_CAPACITY;
@@ -313,8 +314,28 @@ int rs_resample_batched(rs_handle* h, int scheme, int dtype, const void* logw_de
   const cudaStream_t s = as_stream(stream);
   const cudaError_t e = rsk::launch_batched(h->s, scheme, accumulation(dtype, o.prec), logw_dev,
                                             offsets_dev, F, B_dev, B, seed, step, o.log_wmax,
-                                            o.max_trials, ancestors_dev, permute, s);
+                                            o.max_trials, resample_dev, ancestors_dev, permute, s);
   end_mark(h, s);
+  return cuda_status(e);
+}
+
+int rs_resample_batched(rs_handle* h, int scheme, int dtype, const void* logw_dev,
+                        const int64_t* offsets_dev, int32_t F, const int32_t* B_dev, int32_t B,
+                        uint64_t seed, uint64_t step, int32_t* ancestors_dev, int permute,
+                        const rs_opts* opts, void* stream) {
+  return rs_resample_batched_masked(h, scheme, dtype, logw_dev, offsets_dev, F, B_dev, B, seed,
+                                    step, nullptr, ancestors_dev, permute, opts, stream);
+}
+
+int rs_reset_weights_batched(rs_handle* h, float* logw_dev, const int64_t* offsets_dev,
+                             int32_t F, const uint8_t* flags_dev, void* stream) {
+  if (!h || !logw_dev || !offsets_dev || !flags_dev || F < 1) return RS_ERR_ARG;
+  if (F > INT_MAX / 2) return RS_ERR_ARG;
+  int st = set_device(h);
+  if (st != RS_OK) return st;
+  const cudaError_t e = rsk::launch_reset_logw_batched(h->s, logw_dev, offsets_dev, F, flags_dev,
+                                                       as_stream(stream));
+  end_mark(h, as_stream(stream));
   return cuda_status(e);
 }
 
@@ -515,9 +536,11 @@ int rs_log_sum_weights_batched(rs_handle* h, int dtype, const void* logw_dev,
 }
 
 int rs_ess_batched(rs_handle* h, int dtype, const void* logw_dev, const int64_t* offsets_dev,
-                   int32_t F, double* ess_dev, double* log_total_dev, void* stream) {
-  if (!h || !logw_dev || !offsets_dev || (!ess_dev && !log_total_dev) || F < 1)
+                   int32_t F, double* ess_dev, double* log_total_dev, double threshold_frac,
+                   uint8_t* below_dev, void* stream) {
+  if (!h || !logw_dev || !offsets_dev || (!ess_dev && !log_total_dev && !below_dev) || F < 1)
     return RS_ERR_ARG;
+  if (below_dev && !(threshold_frac >= 0.0 && threshold_frac <= 1.0)) return RS_ERR_ARG;
   if (dtype != RS_F32 && dtype != RS_F64) return RS_ERR_ARG;
   if (F > INT_MAX / 2) return RS_ERR_ARG;
   int st = set_device(h);
@@ -525,6 +548,8 @@ int rs_ess_batched(rs_handle* h, int dtype, const void* logw_dev, const int64_t*
   rsk::WeightStatsOut o{};
   o.log_total = log_total_dev;
   o.ess = ess_dev;
+  o.below = below_dev;
+  o.below_frac = threshold_frac;
   const cudaError_t e = rsk::launch_weight_stats_batched(h->s, dtype == RS_F64, logw_dev,
                                                          offsets_dev, F, o, as_stream(stream));
   end_mark(h, as_stream(stream));

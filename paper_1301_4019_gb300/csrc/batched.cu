@@ -95,8 +95,14 @@ struct Batch {
   double* fSd;           // F: total in binary64
   double2* s_rec;        // tile totals, indexed by batch tile
   double2* P_rec;        // tile prefixes, filter f at tile_start[f] + f
+  const uint8_t* resample;  // F flags (0: the filter keeps its particles), or null = all
   int* err;
 };
+
+// Filter f is resampled unless a flag array says otherwise (rs_resample_batched_masked).
+__device__ __forceinline__ bool resampled(const uint8_t* flags, int f) {
+  return flags == nullptr || __ldg(flags + f) != 0;
+}
 
 // Plan: tiles per filter and their exclusive prefix; per-filter maxima reset; offsets checked.
 __global__ void __launch_bounds__(1024) batch_plan_kernel(Batch b) {
@@ -242,7 +248,8 @@ batch_emit_kernel(const T* __restrict__ lw, Batch b, Keys base_keys,
   const int64_t n = L.hi - L.lo;
   const double M = filter_M(b, L.f);
   const double Sd = __ldcg(b.fSd + L.f);
-  if (!(M > -DBL_MAX) || !(Sd > 0.0)) {  // all weights zero: flagged; identity
+  // all weights zero (flagged), or a filter that is not resampled: the identity
+  if (!resampled(b.resample, L.f) || !(M > -DBL_MAX) || !(Sd > 0.0)) {
     for (int64_t e = L.base + threadIdx.x; e < L.hi && e < L.base + kTile; e += kBlock) {
       a[e] = static_cast<int32_t>(e - L.lo);
       if (d) d[e] = static_cast<int32_t>(e - L.lo);
@@ -277,7 +284,9 @@ batch_search_kernel(const V* __restrict__ W, Batch b, int64_t total, Keys base_k
   const int64_t g = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
   PartLoc P;
   if (g >= total || !locate_particle(b.off, b.F, b.max_n, g, P)) return;
-  if (!(__ldcg(b.fSd + P.f) > 0.0) || !(filter_M(b, P.f) > -DBL_MAX)) return;  // identity
+  if (!resampled(b.resample, P.f) || !(__ldcg(b.fSd + P.f) > 0.0) ||
+      !(filter_M(b, P.f) > -DBL_MAX))
+    return;  // the identity, written by the emission kernel
   const Keys keys = with_tag(base_keys, static_cast<uint32_t>(P.f), RS_MULTINOMIAL);
   const int32_t k = search_one<T, V>(W + P.lo, P.n, keys, P.i);
   a[g] = k;
@@ -309,7 +318,8 @@ __global__ void __launch_bounds__(kMaxTunedBlock)
 batch_mcmc_kernel(const T* __restrict__ lw, const int64_t* __restrict__ off, int F,
                   int64_t total, int scheme, const int32_t* __restrict__ Bf, int32_t B,
                   Keys base_keys, double log_wmax, int64_t max_trials,
-                  int32_t* __restrict__ a, int32_t* __restrict__ d, int ipt, int* err) {
+                  const uint8_t* __restrict__ flags, int32_t* __restrict__ a,
+                  int32_t* __restrict__ d, int ipt, int* err) {
   pdl_wait();
   for (int q = 0; q < ipt; ++q) {
     const int64_t g = item_index(ipt, q);
@@ -320,7 +330,9 @@ batch_mcmc_kernel(const T* __restrict__ lw, const int64_t* __restrict__ off, int
       continue;
     }
     int32_t k;
-    if (scheme == RS_METROPOLIS) {
+    if (!resampled(flags, P.f)) {
+      k = static_cast<int32_t>(P.i);  // the filter keeps its particles
+    } else if (scheme == RS_METROPOLIS) {
       int32_t Bv = Bf ? __ldg(Bf + P.f) : B;
       if (Bv < 0) {
         flag_error(err, RS_ERR_ARG);
@@ -343,7 +355,8 @@ template <typename T>
 __global__ void __launch_bounds__(kBlock)
 batch_rejection_kernel(const T* __restrict__ lw, const int64_t* __restrict__ off, int F,
                        int64_t total, Keys base_keys, double log_wmax, int64_t max_trials,
-                       int32_t* __restrict__ a, int32_t* __restrict__ d, int* err) {
+                       const uint8_t* __restrict__ flags, int32_t* __restrict__ a,
+                       int32_t* __restrict__ d, int* err) {
   pdl_wait();
   const int lane = threadIdx.x & 31;
   const int64_t run = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
@@ -357,6 +370,7 @@ batch_rejection_kernel(const T* __restrict__ lw, const int64_t* __restrict__ off
   PartLoc P;
   Keys keys = base_keys;
   T lwi = T(0);
+  bool keep = false;  // the particle's filter is not resampled: it settles on itself
   auto take = [&](int64_t gg) {
     g = gg;
     active = false;
@@ -366,6 +380,7 @@ batch_rejection_kernel(const T* __restrict__ lw, const int64_t* __restrict__ off
       return;
     }
     active = true;
+    keep = !resampled(flags, P.f);
     keys = with_tag(base_keys, static_cast<uint32_t>(P.f), RS_REJECTION);
     lwi = __ldg(lw + gg);
     if (nonfinite_logw(lwi)) flag_error(err, RS_ERR_NONFINITE);
@@ -376,9 +391,10 @@ batch_rejection_kernel(const T* __restrict__ lw, const int64_t* __restrict__ off
   for (;;) {
     bool settled = false;
     if (active) {
-      int64_t j;
-      settled = rejection_attempts<kRejBatch>(lw + P.lo, P.n, rb, keys, P.i,
-                                              static_cast<uint32_t>(s), lwi, max_trials, j, err);
+      int64_t j = P.i;
+      settled = keep || rejection_attempts<kRejBatch>(lw + P.lo, P.n, rb, keys, P.i,
+                                                      static_cast<uint32_t>(s), lwi, max_trials,
+                                                      j, err);
       s += kRejBatch;
       if (!settled && s >= static_cast<uint64_t>(max_trials)) {
         flag_error(err, RS_ERR_REJECTION_CAP);
@@ -465,7 +481,7 @@ cudaError_t run_batched_scan(const Scratch& s, int scheme, const T* lw, const Ba
 cudaError_t launch_batched(const Scratch& s, int scheme, Acc acc, const void* logw,
                            const int64_t* offsets, int F, const int32_t* Bf, int32_t B,
                            uint64_t seed, uint64_t step, double log_wmax, int64_t max_trials,
-                           int32_t* out, int permute, cudaStream_t st) {
+                           const uint8_t* flags, int32_t* out, int permute, cudaStream_t st) {
   int32_t* a = permute ? s.a_tmp : out;
   int32_t* d = permute ? s.d : nullptr;
   const bool f64 = acc == Acc::F64 || acc == Acc::F64N;
@@ -486,22 +502,22 @@ cudaError_t launch_batched(const Scratch& s, int scheme, Acc acc, const void* lo
     if (scheme == RS_REJECTION) {
       if (f64)
         launch_pdl(batch_rejection_kernel<double>, grid_runs, kBlock, st,
-            static_cast<const double*>(logw), offsets, F, total, keys, log_wmax, max_trials, a,
-            d, s.err);
+            static_cast<const double*>(logw), offsets, F, total, keys, log_wmax, max_trials,
+            flags, a, d, s.err);
       else
         launch_pdl(batch_rejection_kernel<float>, grid_runs, kBlock, st,
-            static_cast<const float*>(logw), offsets, F, total, keys, log_wmax, max_trials, a,
-            d, s.err);
+            static_cast<const float*>(logw), offsets, F, total, keys, log_wmax, max_trials,
+            flags, a, d, s.err);
     } else if (f64) {
       const LaunchCfg& c = s.batch_cfg[kCfgMetropolisF64];
       launch_pdl(batch_mcmc_kernel<double>, grid_shaped(total, c), c.block, st,
           static_cast<const double*>(logw), offsets, F, total, scheme, Bf, B, keys, log_wmax,
-          max_trials, a, d, c.ipt, s.err);
+          max_trials, flags, a, d, c.ipt, s.err);
     } else {
       const LaunchCfg& c = s.batch_cfg[kCfgMetropolisF32];
       launch_pdl(batch_mcmc_kernel<float>, grid_shaped(total, c), c.block, st,
           static_cast<const float*>(logw), offsets, F, total, scheme, Bf, B, keys, log_wmax,
-          max_trials, a, d, c.ipt, s.err);
+          max_trials, flags, a, d, c.ipt, s.err);
     }
   } else {
     Batch b;
@@ -515,6 +531,7 @@ cudaError_t launch_batched(const Scratch& s, int scheme, Acc acc, const void* lo
     b.fSd = s.batch_fSd;
     b.s_rec = s.batch_s_rec;
     b.P_rec = s.batch_P_rec;
+    b.resample = flags;
     b.err = s.err;
     trace_mark(s.trace, "batch_plan", st);
     launch_pdl(batch_plan_kernel, 1, 1024, st, b);

@@ -108,7 +108,8 @@ cudaError_t launch_fused_passes(const Scratch& s, int scheme, Acc acc, const voi
 cudaError_t launch_batched(const Scratch& s, int scheme, Acc acc, const void* logw,
                            const int64_t* offsets, int F, const int32_t* Bf, int32_t B,
                            uint64_t seed, uint64_t step, double log_wmax, int64_t max_trials,
-                           int32_t* out, int permute, cudaStream_t st);
+                           const uint8_t* resample_flags, int32_t* out, int permute,
+                           cudaStream_t st);
 
 // mcmc.cu (d, when given, is set to the sentinel N by the launch itself)
 cudaError_t launch_metropolis(const Scratch& s, bool f64, const void* logw, int64_t N,
@@ -164,7 +165,11 @@ struct WeightStatsOut {
   double* beta;       // mean w / max w
   int32_t* B;         // Eq. B for beta and log_eps
   double log_eps;
+  uint8_t* below;     // 1 where ess < below_frac * n (0 for empty or all-zero filters)
+  double below_frac;
 };
+cudaError_t launch_reset_logw_batched(const Scratch& s, float* logw, const int64_t* offsets,
+                                      int F, const uint8_t* flags, cudaStream_t st);
 cudaError_t launch_weight_stats_batched(const Scratch& s, bool f64, const void* logw,
                                         const int64_t* offsets, int F, const WeightStatsOut& o,
                                         cudaStream_t st);

@@ -186,6 +186,7 @@ log_sum_batched_kernel(const T* __restrict__ lw, const int64_t* __restrict__ off
       if (o.ess) o.ess[f] = 0.0;
       if (o.beta) o.beta[f] = 0.0;
       if (o.B) o.B[f] = 1;
+      if (o.below) o.below[f] = 0;
     }
     return;
   }
@@ -216,11 +217,26 @@ log_sum_batched_kernel(const T* __restrict__ lw, const int64_t* __restrict__ off
       t2 += sh2[k];
     }
     if (o.log_total) o.log_total[f] = md + log(t);
-    if (o.ess) o.ess[f] = t2 > 0.0 ? (t * t) / t2 : 0.0;
+    const double ess = t2 > 0.0 ? (t * t) / t2 : 0.0;
+    if (o.ess) o.ess[f] = ess;
+    if (o.below) o.below[f] = ess < o.below_frac * static_cast<double>(hi - lo) ? 1 : 0;
     const double beta = t / static_cast<double>(hi - lo);
     if (o.beta) o.beta[f] = beta;
     if (o.B) o.B[f] = metropolis_B_of(beta, o.log_eps);
   }
+}
+
+// The log-weights of the flagged filters of a batch set to 0 (equal weights after their
+// resampling); the other filters keep theirs.
+__global__ void __launch_bounds__(kBlock)
+reset_logw_batched_kernel(float* __restrict__ logw, const int64_t* __restrict__ off, int F,
+                          int64_t cap, const uint8_t* __restrict__ flags) {
+  pdl_wait();
+  const int64_t g = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  int64_t lo, n;
+  const int f = g < cap ? locate(off, F, cap, g, lo, n) : -1;
+  if (f < 0) return;
+  if (__ldg(flags + f) != 0) logw[g] = 0.0f;
 }
 
 // Philox throughput: thread i draws the blocks (i, n), n < J, under the given keys and XORs
@@ -354,22 +370,31 @@ cudaError_t launch_lgssm_step_batched(const Scratch& s, float* x, const int64_t*
 cudaError_t launch_weight_stats_batched(const Scratch& s, bool f64, const void* logw,
                                         const int64_t* offsets, int F, const WeightStatsOut& o,
                                         cudaStream_t st) {
-  trace_mark(s.trace, o.B ? "metropolis_B_batched" : o.ess ? "ess_batched" : "log_sum_batched",
-             st);
+  trace_mark(s.trace, o.B ? "metropolis_B_batched"
+                          : (o.ess || o.below) ? "ess_batched" : "log_sum_batched", st);
   const auto* l32 = static_cast<const float*>(logw);
   const auto* l64 = static_cast<const double*>(logw);
-  if (f64 && o.ess)
+  const bool sq = o.ess != nullptr || o.below != nullptr;
+  if (f64 && sq)
     launch_pdl(log_sum_batched_kernel<double, true>, F, kBlock, st, l64, offsets, F, s.max_n, o,
                s.err);
   else if (f64)
     launch_pdl(log_sum_batched_kernel<double, false>, F, kBlock, st, l64, offsets, F, s.max_n, o,
                s.err);
-  else if (o.ess)
+  else if (sq)
     launch_pdl(log_sum_batched_kernel<float, true>, F, kBlock, st, l32, offsets, F, s.max_n, o,
                s.err);
   else
     launch_pdl(log_sum_batched_kernel<float, false>, F, kBlock, st, l32, offsets, F, s.max_n, o,
                s.err);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_reset_logw_batched(const Scratch& s, float* logw, const int64_t* offsets,
+                                      int F, const uint8_t* flags, cudaStream_t st) {
+  trace_mark(s.trace, "reset_logw_batched", st);
+  launch_pdl(reset_logw_batched_kernel, grid_for(s.max_n), kBlock, st, logw, offsets, F,
+             s.max_n, flags);
   return cudaGetLastError();
 }
 

@@ -17,7 +17,8 @@ import torch
 from . import (PREC_COMPENSATED, Handle, rs_capture_end_if, rs_capture_if_below,
                rs_copy_ancestors, rs_copy_ancestors_batched, rs_ess,
                rs_lgssm_step, rs_lgssm_step_batched, rs_log_sum_weights_batched, rs_resample,
-               rs_resample_batched, rs_smc_loglik_step, rs_smc_mark_resampled)
+               rs_resample_batched, rs_smc_loglik_step, rs_smc_mark_resampled, rs_ess_batched,
+               rs_reset_weights_batched)
 
 
 class LgssmBuffers:
@@ -183,6 +184,50 @@ def lgssm_batched_launch(h: Handle, bufs: BatchedLgssmBuffers, scheme: int, phi:
                               seed=seed, step=t, logw=b.logw, stream=stream)
         rs_log_sum_weights_batched(h, b.logw, b.offsets, out=b.log_total[t], stream=stream)
     return b
+
+
+def lgssm_batched_adaptive_launch(h: Handle, bufs: BatchedLgssmBuffers, scheme: int,
+                                  phi: float, sigma_x: float, sigma_y: float,
+                                  threshold: float = 0.5, seed: int = 0, B: int = 64,
+                                  prec: int = PREC_COMPENSATED, stream=None) -> torch.Tensor:
+    """Enqueue F adaptive bootstrap filters (resampling on demand, Section 4.3), every
+    decision taken per filter on the device: before step t >= 1, rs_ess_batched flags the
+    filters whose ESS is below threshold * N_f; only those are resampled
+    (rs_resample_batched_masked), copied and given equal weights (rs_reset_weights_batched);
+    the others carry their weights, to which the step's log-likelihood terms are added.
+    Returns the T x F uint8 flags (row 0: the initial draw); log_total[t, f] as in
+    lgssm_batched_launch. No host synchronisation."""
+    b = bufs
+    T, F = b.y.shape[0], b.offsets.numel() - 1
+    flags = torch.zeros((T, F), dtype=torch.uint8, device=b.x.device)
+    flags[0].fill_(1)
+    ess = torch.empty(F, dtype=torch.float64, device=b.x.device)
+    for t in range(T):
+        if t > 0:
+            rs_ess_batched(h, b.logw, b.offsets, out=ess, threshold=threshold, below=flags[t],
+                           stream=stream)
+            rs_resample_batched(h, scheme, b.logw, b.offsets, B=B, seed=seed, step=t, out=b.c,
+                                permute=True, prec=prec, log_wmax=0.0, resample=flags[t],
+                                stream=stream)
+            rs_copy_ancestors_batched(h, b.x, b.c, b.offsets, stream=stream)
+            rs_reset_weights_batched(h, b.logw, b.offsets, flags[t], stream=stream)
+        rs_lgssm_step_batched(h, b.x, b.offsets, t == 0, phi, sigma_x, b.y[t], sigma_y,
+                              seed=seed, step=t, logw=b.logw, accumulate=t > 0, stream=stream)
+        rs_log_sum_weights_batched(h, b.logw, b.offsets, out=b.log_total[t], stream=stream)
+    return flags
+
+
+def lgssm_batched_adaptive_loglik_from(bufs: BatchedLgssmBuffers, flags: torch.Tensor,
+                                       sigma_y: float) -> np.ndarray:
+    """Per-filter log p-hat(y_1:T) of the adaptive filters: increment t is log sum w_t minus
+    log N_f after a resampling (and at t = 0), minus log sum w_{t-1} otherwise (the carried
+    weights), less the Gaussian constant."""
+    lt = bufs.log_total.cpu().numpy()
+    fl = flags.cpu().numpy().astype(bool)
+    logn = np.log(bufs.sizes.astype(np.float64))
+    base = np.where(fl[1:], logn[None, :], lt[:-1])
+    inc = np.concatenate([(lt[0] - logn)[None, :], lt[1:] - base], axis=0)
+    return inc.sum(axis=0) - lt.shape[0] * 0.5 * math.log(2 * math.pi * sigma_y ** 2)
 
 
 def lgssm_batched_loglik_from(bufs: BatchedLgssmBuffers, sigma_y: float) -> np.ndarray:

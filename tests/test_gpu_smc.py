@@ -262,7 +262,7 @@ def test_ess_batched_matches_host(rs, h):
     # neither output: refused on the host before any launch
     st = rs.load().rs_ess_batched(h.ptr, rs._dtype_code(t), rs._dev(t, None, "logw"),
                                   rs._dev(offs, torch.int64, "offsets"), len(sizes), None,
-                                  None, None)
+                                  None, 0.5, None, None)
     assert st == rs.RS_ERR_ARG
     bad = torch.tensor([0.0, float("nan")], dtype=torch.float32, device=DEV)
     rs.rs_ess_batched(h, bad, torch.tensor([0, 2], dtype=torch.int64, device=DEV))
@@ -283,3 +283,86 @@ def test_batched_loglik_matches_kalman(rs, h):
     sd = lls.std(ddof=1)
     assert sd < 1.0
     assert abs(lls.mean() - want) < 4 * sd / math.sqrt(F), (lls.mean(), want, sd)
+
+
+@pytest.mark.parametrize("scheme", [0, 2, 3, 4])
+@pytest.mark.parametrize("permute", [False, True])
+def test_masked_batched_resample(rs, h, scheme, permute):
+    """rs_resample_batched_masked: flagged filters get exactly the ancestors of the unmasked
+    call, the others the identity; all flags set gives the unmasked call bit for bit."""
+    sizes = np.array([1, 300, 4097, 0, 9000, 2, 1024, 70001], np.int64)
+    off, lw, _ = workload.ragged_logw(sizes, seed=31, dtype=np.float32)
+    t = torch.from_numpy(lw).to(DEV)
+    offs = torch.from_numpy(off).to(DEV)
+    kw = dict(B=9, seed=5, step=3, permute=permute, log_wmax=0.0)
+    full = rs.rs_resample_batched(h, scheme, t, offs, **kw).cpu().numpy()
+    flags = np.array([1, 0, 1, 1, 0, 1, 0, 1], np.uint8)
+    got = rs.rs_resample_batched(h, scheme, t, offs, resample=torch.from_numpy(flags).to(DEV),
+                                 **kw).cpu().numpy()
+    ones = rs.rs_resample_batched(h, scheme, t, offs, resample=torch.ones(len(sizes),
+                                  dtype=torch.uint8, device=DEV), **kw).cpu().numpy()
+    assert rs.rs_last_error(h) == rs.RS_OK
+    assert np.array_equal(ones, full)
+    for f in range(len(sizes)):
+        lo, hi = off[f], off[f + 1]
+        want = full[lo:hi] if flags[f] else np.arange(hi - lo, dtype=np.int32)
+        assert np.array_equal(got[lo:hi], want), (f, flags[f])
+
+
+def test_ess_flags_and_weight_reset(rs, h):
+    """rs_ess_batched's below flags are ESS_f < threshold * N_f (0 for empty and all-zero
+    filters); rs_reset_weights_batched zeroes exactly the flagged filters' log-weights."""
+    sizes = np.array([5, 0, 3000, 1, 70001, 300], np.int64)
+    off, lw, _ = workload.ragged_logw(sizes, seed=8, dtype=np.float32)
+    lw[off[3]:off[4]] = -np.inf
+    t = torch.from_numpy(lw).to(DEV)
+    offs = torch.from_numpy(off).to(DEV)
+    below = torch.empty(len(sizes), dtype=torch.uint8, device=DEV)
+    ess = rs.rs_ess_batched(h, t, offs, threshold=0.5, below=below).cpu().numpy()
+    assert rs.rs_last_error(h) == rs.RS_OK
+    fl = below.cpu().numpy()
+    want = (ess < 0.5 * sizes) & (ess > 0)
+    assert np.array_equal(fl.astype(bool), want), (fl, ess)
+    assert fl.any() and not fl.all()
+    rs.rs_reset_weights_batched(h, t, offs, below)
+    assert rs.rs_last_error(h) == rs.RS_OK
+    after = t.cpu().numpy()
+    for f in range(len(sizes)):
+        lo, hi = off[f], off[f + 1]
+        if fl[f]:
+            assert np.all(after[lo:hi] == 0.0)
+        else:
+            assert np.array_equal(after[lo:hi], lw[lo:hi])
+    with pytest.raises(rs.RsError):
+        rs.rs_ess_batched(h, t, offs, threshold=1.5, below=below)
+
+
+@pytest.mark.parametrize("scheme", [2, 4])
+def test_batched_adaptive_loglik_matches_kalman(rs, h, scheme):
+    """32 adaptive filters of N = 2^14 (each resampling when its own ESS < N/2, decided on the
+    device): log-likelihoods centred on Kalman within 4 standard errors, fewer resamplings
+    than steps, and with threshold 1 (always below) the filters equal the resample-every-step
+    batched loop bit for bit."""
+    from paper_1301_4019_gb300 import smc
+    T, F, N = 100, 32, 1 << 14
+    _, y = workload.lgssm_simulate(T, PHI, SX, SY, seed=21)
+    want = kalman.lgssm_loglik(y, PHI, SX, SY)
+    Y = np.repeat(y[:, None], F, axis=1)
+    b = smc.BatchedLgssmBuffers([N] * F, Y)
+    flags = smc.lgssm_batched_adaptive_launch(h, b, scheme, PHI, SX, SY, threshold=0.5,
+                                              seed=12)
+    lls = smc.lgssm_batched_adaptive_loglik_from(b, flags, SY)
+    assert rs.rs_last_error(h) == rs.RS_OK
+    n_res = flags[1:].sum(dim=0).cpu().numpy()
+    assert np.all(n_res < T - 1) and np.all(n_res > 0)
+    sd = lls.std(ddof=1)
+    assert sd < 1.0
+    assert abs(lls.mean() - want) < 4 * sd / math.sqrt(F), (lls.mean(), want, sd)
+    # threshold 1: every filter resamples at every step (ESS < N unless all weights equal)
+    a = smc.BatchedLgssmBuffers([N] * 4, Y[:, :4])
+    fa = smc.lgssm_batched_adaptive_launch(h, a, scheme, PHI, SX, SY, threshold=1.0, seed=3)
+    e = smc.BatchedLgssmBuffers([N] * 4, Y[:, :4])
+    smc.lgssm_batched_launch(h, e, scheme, PHI, SX, SY, seed=3)
+    assert rs.rs_last_error(h) == rs.RS_OK
+    assert bool(fa.all())
+    assert torch.equal(a.x, e.x) and torch.equal(a.log_total, e.log_total)
