@@ -225,25 +225,25 @@ class ClockSampler:
 # headers it includes, hashed; `traffic` is null once any of them has changed.
 # ---------------------------------------------------------------------------------------
 NCU_TRAFFIC = {  # label: (bytes per launch, source hash)
-               "permute": (8393383, "d1bec482251ad289"),
-               "metropolis_f64": (12606354, "ef0872bb78ac17a1"),
-               "metropolis_f32": (8403840, "ef0872bb78ac17a1"),
-               "permute_sorted": (8397120, "d1bec482251ad289"),
-               "rejection_f64": (8409271, "ef0872bb78ac17a1"),
-               "fused_stratified_f64": (8489376, "2d7ce1f5369a295d"),
-               "rejection_f32": (4213376, "ef0872bb78ac17a1"),
-               "fused_multinomial_f64": (8491808, "2d7ce1f5369a295d"),
-               "fused_systematic_f64": (8482656, "2d7ce1f5369a295d"),
-               "fused_multinomial_f32": (4278304, "2d7ce1f5369a295d"),
-               "fused_stratified_f32": (4261376, "2d7ce1f5369a295d"),
-               "fused_systematic_f32": (4259360, "2d7ce1f5369a295d"),
-               "iscan": (4213010, "d1bec482251ad289"),
-               "search_f64": (16785312, "ca9fe6017c87627e"),
-               "search_f32": (12591680, "ca9fe6017c87627e"),
-               "fill": (8764, "d1bec482251ad289"),
-               "cumoff_to_ancestors": (4199834, "d1bec482251ad289"),
-               "offspring": (8391259, "d1bec482251ad289"),
-               "adjacent_difference": (4197308, "d1bec482251ad289")}
+               "permute": (8392909, "4f161753fd8a152b"),
+               "metropolis_f64": (12598967, "7e0b5c67a9eb8e79"),
+               "metropolis_f32": (8403200, "7e0b5c67a9eb8e79"),
+               "rejection_f64": (8408832, "7e0b5c67a9eb8e79"),
+               "permute_sorted": (8397150, "4f161753fd8a152b"),
+               "rejection_f32": (4209088, "7e0b5c67a9eb8e79"),
+               "fused_multinomial_f64": (8493920, "1df9b149b8f7e471"),
+               "fused_stratified_f64": (8487205, "1df9b149b8f7e471"),
+               "fused_systematic_f64": (8481829, "1df9b149b8f7e471"),
+               "fused_multinomial_f32": (4276416, "1df9b149b8f7e471"),
+               "fused_stratified_f32": (4262016, "1df9b149b8f7e471"),
+               "iscan": (4215040, "4f161753fd8a152b"),
+               "fused_systematic_f32": (4257664, "1df9b149b8f7e471"),
+               "search_f32": (12590496, "d91e3b51ce47b299"),
+               "fill": (8431, "4f161753fd8a152b"),
+               "search_f64": (16783433, "d91e3b51ce47b299"),
+               "cumoff_to_ancestors": (4199408, "4f161753fd8a152b"),
+               "offspring": (8391328, "4f161753fd8a152b"),
+               "adjacent_difference": (4197392, "4f161753fd8a152b")}
 
 _LABEL_FILES = (("fused_", "fused.cu"), ("permute", "aux.cu"), ("iscan", "aux.cu"),
                 ("fill", "aux.cu"), ("offspring", "aux.cu"), ("adjacent", "aux.cu"),

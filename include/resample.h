@@ -327,8 +327,9 @@ int rs_ess_batched(rs_handle* h, int dtype, const void* logw_dev, const int64_t*
  * every other filter keeps its particles: its ancestors are the identity a_i = i (with
  * permute, c_i = i). The flagged filters' ancestors are those of rs_resample_batched, bit
  * for bit. The resampling on demand of a batch of adaptive filters (Section 4.3), decided on
- * the device (rs_ess_batched's below flags) without a host round trip. Same arguments and
- * errors as rs_resample_batched otherwise (NaN checks cover every filter). */
+ * the device (rs_ess_batched's below flags) without a host round trip; the unflagged filters
+ * skip every pass of the resampler (their NaN/+inf log-weights may go unchecked). Same
+ * arguments and errors as rs_resample_batched otherwise. */
 int rs_resample_batched_masked(rs_handle* h, int scheme, int dtype, const void* logw_dev,
                                const int64_t* offsets_dev, int32_t F, const int32_t* B_dev,
                                int32_t B, uint64_t seed, uint64_t step,

@@ -164,6 +164,7 @@ __global__ void __launch_bounds__(kBlock) batch_max_kernel(const T* __restrict__
   __shared__ long long sh[kWarps];
   TileLoc L;
   if (!locate_tile(b, blockIdx.x, L)) return;
+  if (!resampled(b.resample, L.f)) return;  // a filter that keeps its particles: no passes
   const bool vec = (reinterpret_cast<uintptr_t>(lw) & 15u) == 0;
   const int64_t end = min(L.hi, L.base + kTile);
   long long m = key_of(neg_inf<T>());
@@ -207,6 +208,7 @@ __global__ void __launch_bounds__(kBlock) batch_sum_kernel(const T* __restrict__
   __shared__ float2 sh_tab[64];
   TileLoc L;
   if (!locate_tile(b, blockIdx.x, L)) return;
+  if (!resampled(b.resample, L.f)) return;
   const double M = filter_M(b, L.f);
   if (M > -DBL_MAX) {
     const WeightCtx wc = make_ctx<T, V>(M, sh_tab);
@@ -223,7 +225,7 @@ __global__ void __launch_bounds__(kBlock) batch_prefix_kernel(Batch b) {
   const int f = blockIdx.x;
   const int64_t lo = b.off[f], hi = b.off[f + 1], n = hi - lo;
   const int t0 = b.tile_start[f], nt = b.tile_start[f + 1] - t0;
-  if (nt <= 0 || n <= 0) return;
+  if (nt <= 0 || n <= 0 || !resampled(b.resample, f)) return;
   if (!(filter_M(b, f) > -DBL_MAX)) {
     if (threadIdx.x == 0) {
       b.fSd[f] = 0.0;

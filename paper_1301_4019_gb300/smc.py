@@ -194,7 +194,8 @@ def lgssm_batched_adaptive_launch(h: Handle, bufs: BatchedLgssmBuffers, scheme: 
     decision taken per filter on the device: before step t >= 1, rs_ess_batched flags the
     filters whose ESS is below threshold * N_f; only those are resampled
     (rs_resample_batched_masked), copied and given equal weights (rs_reset_weights_batched);
-    the others carry their weights, to which the step's log-likelihood terms are added.
+    the others carry their weights, to which the step's log-likelihood terms are added. The
+    filters that keep their particles skip every pass of the batched resampler.
     Returns the T x F uint8 flags (row 0: the initial draw); log_total[t, f] as in
     lgssm_batched_launch. No host synchronisation."""
     b = bufs
@@ -204,8 +205,6 @@ def lgssm_batched_adaptive_launch(h: Handle, bufs: BatchedLgssmBuffers, scheme: 
     ess = torch.empty(F, dtype=torch.float64, device=b.x.device)
     for t in range(T):
         if t > 0:
-            rs_ess_batched(h, b.logw, b.offsets, out=ess, threshold=threshold, below=flags[t],
-                           stream=stream)
             rs_resample_batched(h, scheme, b.logw, b.offsets, B=B, seed=seed, step=t, out=b.c,
                                 permute=True, prec=prec, log_wmax=0.0, resample=flags[t],
                                 stream=stream)
@@ -213,7 +212,11 @@ def lgssm_batched_adaptive_launch(h: Handle, bufs: BatchedLgssmBuffers, scheme: 
             rs_reset_weights_batched(h, b.logw, b.offsets, flags[t], stream=stream)
         rs_lgssm_step_batched(h, b.x, b.offsets, t == 0, phi, sigma_x, b.y[t], sigma_y,
                               seed=seed, step=t, logw=b.logw, accumulate=t > 0, stream=stream)
-        rs_log_sum_weights_batched(h, b.logw, b.offsets, out=b.log_total[t], stream=stream)
+        if t + 1 < T:  # this step's log totals and the next step's decisions, one kernel
+            rs_ess_batched(h, b.logw, b.offsets, out=ess, log_total=b.log_total[t],
+                           threshold=threshold, below=flags[t + 1], stream=stream)
+        else:
+            rs_log_sum_weights_batched(h, b.logw, b.offsets, out=b.log_total[t], stream=stream)
     return flags
 
 
