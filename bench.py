@@ -225,25 +225,25 @@ class ClockSampler:
 # headers it includes, hashed; `traffic` is null once any of them has changed.
 # ---------------------------------------------------------------------------------------
 NCU_TRAFFIC = {  # label: (bytes per launch, source hash)
-               "permute": (8392909, "4f161753fd8a152b"),
-               "metropolis_f64": (12598967, "7e0b5c67a9eb8e79"),
-               "metropolis_f32": (8403200, "7e0b5c67a9eb8e79"),
-               "rejection_f64": (8408832, "7e0b5c67a9eb8e79"),
-               "permute_sorted": (8397150, "4f161753fd8a152b"),
-               "rejection_f32": (4209088, "7e0b5c67a9eb8e79"),
-               "fused_multinomial_f64": (8493920, "1df9b149b8f7e471"),
-               "fused_stratified_f64": (8487205, "1df9b149b8f7e471"),
-               "fused_systematic_f64": (8481829, "1df9b149b8f7e471"),
-               "fused_multinomial_f32": (4276416, "1df9b149b8f7e471"),
-               "fused_stratified_f32": (4262016, "1df9b149b8f7e471"),
-               "iscan": (4215040, "4f161753fd8a152b"),
-               "fused_systematic_f32": (4257664, "1df9b149b8f7e471"),
-               "search_f32": (12590496, "d91e3b51ce47b299"),
-               "fill": (8431, "4f161753fd8a152b"),
-               "search_f64": (16783433, "d91e3b51ce47b299"),
-               "cumoff_to_ancestors": (4199408, "4f161753fd8a152b"),
-               "offspring": (8391328, "4f161753fd8a152b"),
-               "adjacent_difference": (4197392, "4f161753fd8a152b")}
+               "permute": (8393626, "e894311ca809ba84"),
+               "metropolis_f64": (12597723, "2cceea6306c765cb"),
+               "metropolis_f32": (8403328, "2cceea6306c765cb"),
+               "rejection_f64": (8410149, "2cceea6306c765cb"),
+               "permute_sorted": (8396971, "e894311ca809ba84"),
+               "rejection_f32": (4209120, "2cceea6306c765cb"),
+               "fused_multinomial_f64": (8492416, "3efab4a1e18dda20"),
+               "fused_stratified_f64": (8487899, "3efab4a1e18dda20"),
+               "fused_systematic_f64": (8480110, "3efab4a1e18dda20"),
+               "fused_multinomial_f32": (4280320, "3efab4a1e18dda20"),
+               "fused_stratified_f32": (4261664, "3efab4a1e18dda20"),
+               "iscan": (4213872, "e894311ca809ba84"),
+               "fused_systematic_f32": (4257696, "3efab4a1e18dda20"),
+               "search_f32": (12592416, "8e04b4b14d8721c6"),
+               "fill": (8806, "e894311ca809ba84"),
+               "search_f64": (16784786, "8e04b4b14d8721c6"),
+               "cumoff_to_ancestors": (4199568, "e894311ca809ba84"),
+               "offspring": (8391456, "e894311ca809ba84"),
+               "adjacent_difference": (4197856, "e894311ca809ba84")}
 
 _LABEL_FILES = (("fused_", "fused.cu"), ("permute", "aux.cu"), ("iscan", "aux.cu"),
                 ("fill", "aux.cu"), ("offspring", "aux.cu"), ("adjacent", "aux.cu"),
