@@ -27,7 +27,8 @@ def _nvcc() -> str:
 
 def _deps_mtime() -> float:
     paths = [os.path.join(CSRC, f) for f in os.listdir(CSRC)]
-    paths.append(os.path.join(HERE, "..", "include", "resample.h"))
+    inc = os.path.join(HERE, "..", "include")
+    paths += [os.path.join(inc, f) for f in os.listdir(inc) if f.endswith(".h")]
     paths.append(os.path.abspath(__file__))
     return max(os.path.getmtime(p) for p in paths)
 
