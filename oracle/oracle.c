@@ -531,24 +531,38 @@ void orc_dd_prefix_f64(const double* w, int64_t N, double* hi, double* lo) {
 /* Cumulative offspring of the stratified and systematic resamplers (Appendix B.2, B.3)  */
 /* ------------------------------------------------------------------------------------ */
 
-/* r^i = N (W^i / W^N), the quotient formed first so that r^{N-1} = N exactly and trailing
- * zero weights receive no offspring. Systematic (Code 8): O^i = min(N, floor(r^i + u)).
- * Stratified (Code 7), 0-based: stratum k^i = min(N-1, floor(r^i)),
+/* r^i = N W^i / W^N (Codes 7 and 8) in one pinned evaluation order: the factor
+ * c = N / W^N is formed once, as the correctly rounded binary64 quotient rounded once more
+ * to the prefix-sum type, and r^i = W^i * c is one rounded product; where W^i equals the
+ * total (the last particle and every trailing zero weight) r^i = N exactly, so trailing zero
+ * weights receive no offspring. r is non-decreasing in W^i because every rounding is
+ * monotone. Systematic (Code 8): O^i = min(N, floor(r^i + u)), the sum rounded in the
+ * prefix-sum type. Stratified (Code 7), 0-based: stratum k^i = min(N-1, floor(r^i)),
  * O^i = min(N, k^i + 1, floor(r^i + u^{k^i})); the extra bound k^i + 1 holds in exact
- * arithmetic and keeps O non-decreasing when r^i + u rounds up to the next integer. */
+ * arithmetic and keeps O non-decreasing when r^i + u rounds up to the next integer.
+ * The double-double forms compute r^i = N (W^i / W^N) to about 2^-100 (the exact value,
+ * the reference for the compensated prefix sums). */
 static int64_t clamp_n(int64_t v, int64_t N) { return v < N ? v : N; }
+
+/* c = N / W^N: the binary64 quotient, then (binary32) rounded to the prefix-sum type. */
+static float scale_f32(int64_t N, float S) { return (float)((double)N / (double)S); }
+static double scale_f64(int64_t N, double S) { return (double)N / S; }
 
 void orc_systematic_O_given_u_f32(const float* W, int64_t N, float u, int32_t* O) {
     float S = W[N - 1];
+    float c = scale_f32(N, S);
     for (int64_t i = 0; i < N; ++i) {
-        float r = (float)N * (W[i] / S);
+        if (W[i] == S) { O[i] = (int32_t)N; continue; }
+        float r = W[i] * c;
         O[i] = (int32_t)clamp_n((int64_t)floorf(r + u), N);
     }
 }
 void orc_systematic_O_given_u_f64(const double* W, int64_t N, double u, int32_t* O) {
     double S = W[N - 1];
+    double c = scale_f64(N, S);
     for (int64_t i = 0; i < N; ++i) {
-        double r = (double)N * (W[i] / S);
+        if (W[i] == S) { O[i] = (int32_t)N; continue; }
+        double r = W[i] * c;
         O[i] = (int32_t)clamp_n((int64_t)floor(r + u), N);
     }
 }
@@ -568,8 +582,10 @@ void orc_systematic_O_given_u_dd(const double* Wh, const double* Wl, int64_t N, 
 /* Stratified with the per-stratum uniforms given explicitly (u has N entries). */
 void orc_stratified_O_given_u_f32(const float* W, int64_t N, const float* u, int32_t* O) {
     float S = W[N - 1];
+    float c = scale_f32(N, S);
     for (int64_t i = 0; i < N; ++i) {
-        float r = (float)N * (W[i] / S);
+        if (W[i] == S) { O[i] = (int32_t)N; continue; }
+        float r = W[i] * c;
         int64_t k = (int64_t)floorf(r);
         if (k > N - 1) k = N - 1;
         int64_t o = (int64_t)floorf(r + u[k]);
@@ -579,8 +595,10 @@ void orc_stratified_O_given_u_f32(const float* W, int64_t N, const float* u, int
 }
 void orc_stratified_O_given_u_f64(const double* W, int64_t N, const double* u, int32_t* O) {
     double S = W[N - 1];
+    double c = scale_f64(N, S);
     for (int64_t i = 0; i < N; ++i) {
-        double r = (double)N * (W[i] / S);
+        if (W[i] == S) { O[i] = (int32_t)N; continue; }
+        double r = W[i] * c;
         int64_t k = (int64_t)floor(r);
         if (k > N - 1) k = N - 1;
         int64_t o = (int64_t)floor(r + u[k]);
