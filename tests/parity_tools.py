@@ -14,6 +14,12 @@ within the rounding bound of a cumulative-weight boundary. The bound used here:
 
 and r = N W / W^N inherits N times these relative bounds (plus a few roundings of the
 product). Mismatching positions are counted and returned so the tests can report them.
+
+For plain binary32 the bound in units of r, N (KERNEL_C + 4) 2^-24, exceeds 1/2 from about
+N = 2^18, where every position would count as near a boundary. There the kernel's cumulative
+offspring are also held to the double-double oracle's: |O_k - O*| <= ceil(N (KERNEL_C + 4)
+eps_acc) + 1 at every position (truth_offset). Exact 0/1 weights give the bit-exact check at
+those sizes (test_gpu_exact_weights.py).
 """
 from __future__ import annotations
 
@@ -75,6 +81,21 @@ def cumulative_mismatches(kind: str, scheme: int, lw: np.ndarray, O_kernel: np.n
     # the particle's own count changes with its own O and the previous one's
     bad = [i for i in diff if not (near[i] or (i > 0 and near[i - 1]))]
     return len(diff), len(bad)
+
+
+def truth_offset(kind: str, scheme: int, lw: np.ndarray, O_kernel: np.ndarray, seed: int,
+                 step: int = 0, filter_: int = 0):
+    """(largest |O_kernel - O*| over the positions, the bound it must stay within), O* = the
+    cumulative offspring of the double-double oracle (the exact prefix sum). The kernel's r
+    is within N (KERNEL_C + 4) eps_acc of the exact r, which moves floor(r + u) (and the
+    stratum index with its uniform) by at most the ceiling of that plus one."""
+    N = len(lw)
+    f = oracle.systematic if scheme == oracle.SYSTEMATIC else oracle.stratified
+    st, O_t, _ = f(lw, seed, step=step, filter_=filter_, prec=1)
+    assert st == oracle.OK
+    dev = int(np.max(np.abs(np.asarray(O_kernel, np.int64) - O_t.astype(np.int64))))
+    bound = int(np.ceil(N * (KERNEL_C + 4) * EPS[kind] + N * 8 * 2.0 ** -53)) + 1
+    return dev, bound
 
 
 def multinomial_mismatches(kind: str, lw: np.ndarray, a_kernel: np.ndarray,

@@ -10,7 +10,7 @@ import torch
 
 import oracle
 import workload
-from parity_tools import cumulative_mismatches
+from parity_tools import cumulative_mismatches, truth_offset
 
 pytestmark = pytest.mark.gpu
 DEV = "cuda:0"
@@ -72,6 +72,8 @@ def test_fused_equals_separate_large_and_misaligned(rs, h):
         n, bad = cumulative_mismatches("f32", rs.SYSTEMATIC, lw[1:], O_k, O_t, seed=2,
                                        oracle_is_sequential=False)
         assert bad == 0, (N, n, bad)
+        dev, bound = truth_offset("f32", rs.SYSTEMATIC, lw[1:], O_k, seed=2)
+        assert dev <= bound, (N, dev, bound)
 
 
 def test_fused_statuses_match_separate(rs, h):

@@ -8,7 +8,8 @@ import torch
 
 import oracle
 import workload
-from parity_tools import cumulative_mismatches, multinomial_mismatches, truth_prefix
+from parity_tools import (cumulative_mismatches, multinomial_mismatches, truth_offset,
+                          truth_prefix)
 
 pytestmark = pytest.mark.gpu
 
@@ -135,6 +136,8 @@ def test_systematic_stratified_parity(rs, h, kind, dtype, prec, scheme, N):
         assert st == rs.RS_OK
         _check_valid_ancestry(a, lw, sorted_expected=True)
         O_k = np.cumsum(np.bincount(a, minlength=N))
+        dev, bound = truth_offset(kind, sch, lw, O_k, seed=21, step=2)
+        assert dev <= bound, (y, dev, bound)
         for oprec in sorted({0, prec}):
             ost, O_o, _ = f(lw, 21, step=2, prec=oprec)
             assert ost == oracle.OK
@@ -351,6 +354,8 @@ def test_full_size_scan_schemes(rs, kind, dtype, prec):
             n, bad = cumulative_mismatches(kind, sch, lw, O_k, O_t, seed=5,
                                            oracle_is_sequential=False)
             assert bad == 0, (sch, n, bad)
+            dev, bound = truth_offset(kind, sch, lw, O_k, seed=5)
+            assert dev <= bound, (sch, dev, bound)
             st, c = _run(rs, hh, sch, lw, seed=5, prec=prec, permute=True)
             o = np.bincount(a, minlength=N)
             assert np.all(c[o > 0] == np.nonzero(o > 0)[0])
