@@ -5,7 +5,7 @@
 // time is launch-bound, and giving each filter to one CTA serialises its passes and leaves the
 // largest (or, for Metropolis, the highest-B) filters as a long tail. Here the work units are
 // the tiles and the particles of all filters together:
-//   plan    : tiles per filter (1024 particles, starting at the filter's first particle) and
+//   plan    : tiles per filter (kTile particles, starting at the filter's first particle) and
 //             their prefix over filters; per-filter maxima reset            (1 CTA)
 //   max     : per tile, maximum log-weight, combined per filter by an atomic max of keys
 //   sums    : per tile, the tile scan total                               (tile-parallel)
@@ -273,7 +273,7 @@ batch_emit_kernel(const T* __restrict__ lw, Batch b, Keys base_keys,
     const typename Path<T, V>::U u_sys =
         SCHEME == RS_STRATIFIED ? typename Path<T, V>::U() : cta_uniform0<T, V>(keys);
     emit_tile_cumoff<T, V, SCHEME == RS_STRATIFIED>(
-        lw, L.lo, L.hi, L.base, wc, vec, Pt, Pn, L.t > 0, load_v_cg<V>(b.fS + L.f),
+        lw, L.lo, L.hi, L.base, wc, vec, Pt, Pn, load_v_cg<V>(b.fS + L.f),
         load_v_cg<V>(b.fscale + L.f), u_sys, keys, a, d, sh);
   }
 }

@@ -11,9 +11,9 @@
 namespace rsk {
 
 constexpr int kBlock = 256;          // threads per CTA of the streaming kernels
-constexpr int kTile = 1024;          // particles per CTA tile of the scan kernels
+constexpr int kPer = 8;              // consecutive particles per thread in a scan tile
+constexpr int kTile = kBlock * kPer; // particles per CTA tile of the scan kernels (2048)
 constexpr int kWarps = kBlock / 32;  // 8 warps
-constexpr int kRows = kTile / (kWarps * 128);  // rows of 128 particles per warp (1)
 
 // ---------------------------------------------------------------------------------------
 // Device status word: holds -status of the highest-priority error seen (lowest value),

@@ -71,23 +71,65 @@ struct FusedArgs {
   int* err;
 };
 
+// Maximum log-weight and NaN / +inf detection of x[0..3] (exact comparisons: binary32
+// values directly, binary64 values through their order-preserving keys on the integer pipe).
+__device__ __forceinline__ void max_step(const float (&x)[4], long long& m, float& mf, bool& bad) {
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    bad |= !(x[q] <= FLT_MAX);  // NaN or +inf (-inf and finite values pass)
+    mf = fmaxf(mf, x[q]);       // fmaxf skips NaN
+  }
+}
+__device__ __forceinline__ void max_step(const double (&x)[4], long long& m, float&, bool& bad) {
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const bool nan = is_nan(x[q]);
+    bad |= nan || is_pos_inf(x[q]);
+    const long long k = fkey(x[q]);
+    if (!nan && k > m) m = k;
+  }
+}
+
+// Block-wide sums of two u128 values (every thread gets both).
+__device__ __forceinline__ void block_sum2_u128(u128& a, u128& b, u128* sh) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    a += shfl_xor_u128(a, o);
+    b += shfl_xor_u128(b, o);
+  }
+  __syncthreads();
+  if (lane == 0) {
+    sh[warp] = a;
+    sh[kWarps + warp] = b;
+  }
+  __syncthreads();
+  a = 0;
+  b = 0;
+#pragma unroll
+  for (int k = 0; k < kWarps; ++k) {
+    a += sh[k];
+    b += sh[kWarps + k];
+  }
+}
+
 // CTA c owns the contiguous tiles [c T / G, (c+1) T / G) of the T tiles (G = gridDim.x <= T):
 //   phase 1  maximum over its particles -> barrier -> M = maximum over the CTAs;
 //   phase 2  tile totals s_t of its tiles, in order, and their exact running sum in fixed
 //            point (the in-range prefix of each tile, and the CTA total) -> barrier;
-//   phase 3  exclusive sum of the totals of the CTAs before it, then P_t = RN(that + in-range
-//            prefix) for its tiles (the last CTA also P_T and W^N, N / W^N) -> barrier;
+//   phase 3  every CTA sums the exact CTA totals: those before it (CP) and all (the total);
+//            P_t = RN(CP + in-range prefix of t) for its tiles and P_{t1} = RN(CP + its own
+//            total), which is the P_{t1} the next CTA computes; W^N = RN(total), N / W^N;
 //   phase 4  emission of its tiles.
 // P_t is the exact sum of the tile totals before t rounded once, as in tile_prefix_compute, so
-// the results equal those of the separate kernels.
+// the results equal those of the separate kernels. Two grid barriers per call.
 template <typename T, typename V, int SCHEME>
 __device__ __forceinline__ void fused_body(const T* __restrict__ lw, const FusedArgs& A,
                                            unsigned int& target) {
   __shared__ TileSh<V> sh;
   __shared__ float2 sh_tab[64];
   __shared__ long long sh_key[kWarps];
-  __shared__ u128 sh_sum[kWarps];
-  __shared__ Guide sh_gd;
+  __shared__ u128 sh_sum[2 * kWarps];
   const int64_t N = A.N;
   const int T_tiles = static_cast<int>((N + kTile - 1) / kTile);
   const int G = static_cast<int>(gridDim.x), c = static_cast<int>(blockIdx.x);
@@ -100,21 +142,26 @@ __device__ __forceinline__ void fused_body(const T* __restrict__ lw, const Fused
   // ---- phase 1: maximum log-weight (and the Prepermute sentinel of the multinomial claims) --
   {
     long long m = fkey(neg_inf<T>());
+    float mf = -INFINITY;
     bool bad = false;
     for (int64_t i0 = e0 + 4 * static_cast<int64_t>(threadIdx.x); i0 < e1; i0 += 4 * kBlock) {
       T x[4];
       load4(lw, i0, 0, e1, vec, x);
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const bool nan = is_nan(x[q]);
-        bad |= nan || is_pos_inf(x[q]);
-        const long long k = fkey(x[q]);
-        if (!nan && k > m) m = k;
-        if constexpr (SCHEME == RS_MULTINOMIAL) {
-          if (A.d && i0 + q < e1) A.d[i0 + q] = static_cast<int32_t>(N);
+      max_step(x, m, mf, bad);
+      if constexpr (SCHEME == RS_MULTINOMIAL) {
+        if (A.d) {
+          int32_t* p = A.d + i0;
+          if (i0 + 4 <= e1 && (reinterpret_cast<uintptr_t>(p) & 15u) == 0) {
+            const int32_t s = static_cast<int32_t>(N);
+            *reinterpret_cast<int4*>(p) = make_int4(s, s, s, s);
+          } else {
+            for (int q = 0; q < 4; ++q)
+              if (i0 + q < e1) p[q] = static_cast<int32_t>(N);
+          }
         }
       }
     }
+    if constexpr (sizeof(T) == 4) m = fkey(mf);
     if (bad) flag_error(A.err, RS_ERR_NONFINITE);
     const long long bm = block_max_key(m, sh_key);
     if (threadIdx.x == 0) A.blockmax[c] = fvalue(bm, T());
@@ -130,7 +177,7 @@ __device__ __forceinline__ void fused_body(const T* __restrict__ lw, const Fused
     M = fvalue(block_max_key(m, sh_key), 0.0);
   }
   const bool zero = !(M > -DBL_MAX);
-  u128* LP = reinterpret_cast<u128*>(A.P_rec);
+  u128* LP = reinterpret_cast<u128*>(A.P_rec);  // in-range exact prefixes, then rounded P_t
 
   // ---- phase 2: tile totals and their exact running sum ---------------------------------
   const WeightCtx wc = make_ctx<T, V>(zero ? 0.0 : M, sh_tab);
@@ -148,48 +195,14 @@ __device__ __forceinline__ void fused_body(const T* __restrict__ lw, const Fused
   }
   grid_barrier(&A.g->bar_count, target, A.err);
 
-  // ---- phase 3: tile prefixes P_t of this CTA's tiles (the last CTA: P_T, W^N, N / W^N) ----
-  if (zero) {
+  // ---- phase 3: the total and this CTA's tile prefixes --------------------------------------
+  if (zero) {  // all weights zero (flagged): every particle keeps itself
     if (c == 0 && threadIdx.x == 0) {
       A.g->S_d = 0.0;
       A.g->M = M;
       A.g->all_zero = 1;
       flag_error(A.err, RS_ERR_ZERO_WEIGHT);
     }
-  } else {
-    u128 part = 0;
-    for (int k = threadIdx.x; k < c; k += kBlock) part += ld_u128_cg(A.agg + k);
-    const u128 CP = block_sum_u128(part, sh_sum);
-    for (int t = t0 + threadIdx.x; t < t1; t += kBlock) {
-      const u128 lp = ld_u128_cg(LP + t);
-      store_v<V>(A.P_rec + t, fixed_to(CP + lp, V(), kFixFrac));
-    }
-    if (c == G - 1) {
-      if (threadIdx.x == 0)
-        store_v<V>(A.P_rec + T_tiles, fixed_to(CP + ld_u128_cg(A.agg + c), V(), kFixFrac));
-      __syncthreads();
-      if (threadIdx.x == 0) {
-        const V S = load_v_cg<V>(A.P_rec + T_tiles);  // as in tile_prefix_compute
-        const double Sd = vto_double(S);
-        store_v<V>(&A.g->S_raw, S);
-        store_v<V>(&A.g->scale_raw, vfrom_double(__ddiv_rn(static_cast<double>(N), Sd), V()));
-        A.g->S_d = Sd;
-        A.g->M = M;  // read by the search kernel
-        A.g->all_zero = !(Sd > 0.0);
-        const Guide gd = make_guide(Sd, N);
-        A.g->guide_step = gd.step;
-        A.g->guide_inv_step = gd.inv_step;
-        if (!(Sd > 0.0)) flag_error(A.err, RS_ERR_ZERO_WEIGHT);
-      }
-    }
-  }
-  grid_barrier(&A.g->bar_count, target, A.err);
-  const bool all_zero = __ldcg(&A.g->all_zero) != 0;
-  // the kernels that follow (search, Permute) may launch now; they wait for this grid's end
-  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-
-  // ---- phase 4: emission of this CTA's tiles -----------------------------------------------
-  if (all_zero) {  // all weights zero (flagged): every particle keeps itself
     if constexpr (SCHEME != RS_MULTINOMIAL) {  // (the search kernel writes the identity)
       for (int64_t i = e0 + threadIdx.x; i < e1; i += kBlock) {
         A.a[i] = static_cast<int32_t>(i);
@@ -198,23 +211,69 @@ __device__ __forceinline__ void fused_body(const T* __restrict__ lw, const Fused
     }
     return;  // uniform over the grid
   }
-  const V S = load_v_cg<V>(&A.g->S_raw), scale = load_v_cg<V>(&A.g->scale_raw);
+  u128 CP = 0, TOT = 0;
+  for (int k = threadIdx.x; k < G; k += kBlock) {
+    const u128 v = ld_u128_cg(A.agg + k);
+    TOT += v;
+    if (k < c) CP += v;
+  }
+  block_sum2_u128(CP, TOT, sh_sum);
+  const V S = fixed_to(TOT, V(), kFixFrac);
+  const double Sd = vto_double(S);
+  const bool all_zero = !(Sd > 0.0);
+  const V scale = vfrom_double(__ddiv_rn(static_cast<double>(N), Sd), V());
+  if (c == 0 && threadIdx.x == 0) {  // read by the search kernel and the host-side callers
+    store_v<V>(&A.g->S_raw, S);
+    store_v<V>(&A.g->scale_raw, scale);
+    A.g->S_d = Sd;
+    A.g->M = M;
+    A.g->all_zero = all_zero;
+    const Guide gd = make_guide(Sd, N);
+    A.g->guide_step = gd.step;
+    A.g->guide_inv_step = gd.inv_step;
+    if (all_zero) flag_error(A.err, RS_ERR_ZERO_WEIGHT);
+  }
+  // the kernels that follow (search, Permute) may launch now; they wait for this grid's end
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+  if (all_zero) {  // the total rounds to zero: every particle keeps itself
+    if constexpr (SCHEME != RS_MULTINOMIAL) {
+      for (int64_t i = e0 + threadIdx.x; i < e1; i += kBlock) {
+        A.a[i] = static_cast<int32_t>(i);
+        if (A.d) A.d[i] = static_cast<int32_t>(i);
+      }
+    }
+    return;
+  }
+  // rounded prefixes of this CTA's tiles, in place of their exact in-range prefixes (each
+  // slot is read and then overwritten by the same thread), and of the next CTA's first tile,
+  // which that CTA owns: kept in shared memory (the last CTA also writes the total's slot)
+  __shared__ double2 sh_pend;
+  for (int t = t0 + threadIdx.x; t <= t1; t += kBlock) {
+    const u128 lp = (t < t1) ? ld_u128_cg(LP + t) : ld_u128_cg(A.agg + c);
+    const V P = fixed_to(CP + lp, V(), kFixFrac);
+    if (t < t1 || c == G - 1) store_v<V>(A.P_rec + t, P);
+    if (t == t1) store_v<V>(&sh_pend, P);
+  }
+  __syncthreads();
+
+  // ---- phase 4: emission of this CTA's tiles -----------------------------------------------
   typename Path<T, V>::U u_sys = typename Path<T, V>::U();
+  Guide gd;
   if constexpr (SCHEME == RS_MULTINOMIAL) {
-    if (threadIdx.x == 0) sh_gd = Guide{__ldcg(&A.g->guide_step), __ldcg(&A.g->guide_inv_step)};
-    __syncthreads();
+    gd = make_guide(Sd, N);
   } else if constexpr (SCHEME == RS_SYSTEMATIC) {
     u_sys = cta_uniform0<T, V>(A.keys);
   }
   for (int t = t0; t < t1; ++t) {
     const int64_t base = static_cast<int64_t>(t) * kTile;
-    const V Pt = load_v_cg<V>(A.P_rec + t), Pn = load_v_cg<V>(A.P_rec + t + 1);
+    const V Pt = load_v_cg<V>(A.P_rec + t);
+    const V Pn = (t + 1 < t1) ? load_v_cg<V>(A.P_rec + t + 1) : load_v<V>(&sh_pend);
     if constexpr (SCHEME == RS_MULTINOMIAL) {
-      emit_tile_W_guide<T, V>(lw, 0, N, base, wc, vec, Pt, Pn, t > 0, sh_gd,
-                              static_cast<V*>(A.W), A.guide, sh);
+      emit_tile_W_guide<T, V>(lw, 0, N, base, wc, vec, Pt, Pn, gd, static_cast<V*>(A.W),
+                              A.guide, sh);
     } else {
-      emit_tile_cumoff<T, V, SCHEME == RS_STRATIFIED>(lw, 0, N, base, wc, vec, Pt, Pn, t > 0, S,
-                                                       scale, u_sys, A.keys, A.a, A.d, sh);
+      emit_tile_cumoff<T, V, SCHEME == RS_STRATIFIED>(lw, 0, N, base, wc, vec, Pt, Pn, S, scale,
+                                                       u_sys, A.keys, A.a, A.d, sh);
     }
   }
 }

@@ -4,7 +4,7 @@
 // Each call makes three passes over the log-weights (Appendix E renormalisation, Code 4
 // primitives):
 //   1. max pass      : M = max_i lw_i (last-CTA reduction), NaN/+inf detection.
-//   2. tile-sum pass : per tile of 1024 particles, the weights w_i = exp(lw_i - M) are
+//   2. tile-sum pass : per tile of kTile particles, the weights w_i = exp(lw_i - M) are
 //                      prefix-summed in the accumulator type; the tile total is written and
 //                      the last CTA to finish sums the tile totals exactly (128-bit fixed
 //                      point) into tile prefixes P_t, each rounded once, and the total W^N.
@@ -16,11 +16,11 @@
 // Reading the weights twice is inherent: the normaliser W^N is needed before any O_i. The
 // reduce-then-scan order needs no inter-CTA waiting at all.
 //
-// Monotonicity: floating-point tree sums are not monotone in general, so every tile value
-// is passed through an exact running maximum, and every global cumulative weight is
-// clamped into [P_t, P_{t+1}] with P monotone. Cumulative weights are therefore
-// non-decreasing, the cumulative offspring too, and Code 11 writes every position of the
-// ancestry vector exactly once.
+// Monotonicity: floating-point tree sums are not monotone in general, so the tile values are
+// raised to a running maximum and clamped into bounds that are non-decreasing across warps
+// and tiles (tile_cum_weights); every global cumulative weight lies in [P_t, P_{t+1}] with P
+// monotone. Cumulative weights are therefore non-decreasing, the cumulative offspring too,
+// and Code 11 writes every position of the ancestry vector exactly once.
 //
 // Accumulators (input type T, accumulator V): binary32 (float, float), two-float
 // (float, float2), double-float for binary64 inputs on the binary32 pipes (double, float2:
@@ -201,7 +201,7 @@ emit_cumoff_kernel(const T* __restrict__ lw, int64_t N, const ScanGlob* g, const
   const bool vec = (reinterpret_cast<uintptr_t>(lw) & 15u) == 0;
   const int t = blockIdx.x;
   const V Pt = load_v<V>(P_rec + t), Pn = load_v<V>(P_rec + t + 1);
-  emit_tile_cumoff<T, V, STRAT>(lw, 0, N, base, wc, vec, Pt, Pn, t > 0, load_v<V>(&g->S_raw),
+  emit_tile_cumoff<T, V, STRAT>(lw, 0, N, base, wc, vec, Pt, Pn, load_v<V>(&g->S_raw),
                                 load_v<V>(&g->scale_raw), u_sys, keys, a, d, sh);
 }
 
@@ -243,7 +243,7 @@ emit_W_guide_kernel(const T* __restrict__ lw, int64_t N, const ScanGlob* g, cons
   const bool vec = (reinterpret_cast<uintptr_t>(lw) & 15u) == 0;
   const int t = blockIdx.x;
   emit_tile_W_guide<T, V>(lw, 0, N, base, wc, vec, load_v<V>(P_rec + t), load_v<V>(P_rec + t + 1),
-                          t > 0, Guide{g->guide_step, g->guide_inv_step}, Wout, G, sh);
+                          Guide{g->guide_step, g->guide_inv_step}, Wout, G, sh);
 }
 
 // ---------------------------------------------------------------------------------------

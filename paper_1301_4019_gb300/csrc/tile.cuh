@@ -1,6 +1,7 @@
 // tile.cuh -- the tile scan shared by the single-filter and batched scan-based resamplers:
-// weights per (input type, accumulator type), the 1024-particle tile prefix sum with its
-// exact running maximum, and the cumulative offspring of Codes 7 and 8.
+// weights per (input type, accumulator type), the kTile-particle tile prefix sum made
+// monotone (tile_cum_weights), the exact tile prefixes, and the cumulative offspring of Codes
+// 7 and 8 with the Code-11 scatter.
 #pragma once
 
 #include <cfloat>
@@ -28,8 +29,9 @@ template <> struct Path<float, float> {
   using U = float;
   static constexpr int id = 0;
   static constexpr bool kTable = false;
+  // exp_pinned(-inf) = 0, so a zero weight needs no test (M is finite here)
   __device__ static float weight(float x, const WeightCtx& c) {
-    return (x == neg_inf<float>()) ? 0.0f : exp_pinned(__fsub_rn(x, c.Mf));
+    return exp_pinned(__fsub_rn(x, c.Mf));
   }
   __device__ static U draw_u(uint4 x) { return u01_f32(x); }
 };
@@ -38,7 +40,7 @@ template <> struct Path<float, float2> {
   static constexpr int id = 1;
   static constexpr bool kTable = false;
   __device__ static float2 weight(float x, const WeightCtx& c) {
-    return make_float2((x == neg_inf<float>()) ? 0.0f : exp_pinned(__fsub_rn(x, c.Mf)), 0.0f);
+    return make_float2(exp_pinned(__fsub_rn(x, c.Mf)), 0.0f);
   }
   __device__ static U draw_u(uint4 x) { return u01_f32(x); }
 };
@@ -100,6 +102,20 @@ __device__ __forceinline__ void load4(const T* __restrict__ lw, int64_t idx, int
   }
 }
 
+// The kPer consecutive log-weights idx .. idx + kPer - 1 (two load4 halves).
+template <typename T>
+__device__ __forceinline__ void load_per(const T* __restrict__ lw, int64_t idx, int64_t lo,
+                                         int64_t N, bool vec, T (&x)[kPer]) {
+  static_assert(kPer == 8, "two halves of four");
+  T h[4];
+  load4(lw, idx, lo, N, vec, h);
+#pragma unroll
+  for (int q = 0; q < 4; ++q) x[q] = h[q];
+  load4(lw, idx + 4, lo, N, vec, h);
+#pragma unroll
+  for (int q = 0; q < 4; ++q) x[4 + q] = h[q];
+}
+
 template <typename V> __device__ __forceinline__ V load_v(const double2* p) {
   return *reinterpret_cast<const V*>(p);
 }
@@ -117,10 +133,8 @@ template <> __device__ __forceinline__ float2 load_v_cg<float2>(const double2* p
   return __ldcg(reinterpret_cast<const float2*>(p));
 }
 
-// Element e of the tile owned by (warp, row, lane, q): warp*kRows*128 + row*128 + lane*4 + q.
-__device__ __forceinline__ int tile_offset(int warp, int r, int lane, int q) {
-  return warp * (kRows * 128) + r * 128 + lane * 4 + q;
-}
+// Particles of a tile: thread t holds the kPer consecutive offsets kPer t .. kPer t + kPer - 1,
+// so warp w holds 32 kPer consecutive particles and the tile kTile = kBlock kPer.
 // Valid elements of the tile starting at `base` of a sequence ending at N (tiles start at or
 // after the sequence start): offsets 0 .. count-1.
 __device__ __forceinline__ int tile_count(int64_t base, int64_t N) {
@@ -128,120 +142,47 @@ __device__ __forceinline__ int tile_count(int64_t base, int64_t N) {
   return c < kTile ? static_cast<int>(c) : kTile;
 }
 
-// The tile scan shared by the tile-sum and emit passes: val[r][q] = sum of the weights of
-// the tile up to and including the element (r, q) of this thread, as computed by a fixed
-// tree: sequential inside a lane, Hillis-Steele across the 32 lanes of a row, a running
-// carry across the 4 rows of a warp, and a sequential prefix over the 8 warps. Elements
-// outside [lo, N) have weight 0. All four rows are loaded before any arithmetic.
-template <typename T, typename V>
-__device__ __forceinline__ void tile_raw_values(const T* __restrict__ lw, int64_t lo, int64_t N,
-                                                int64_t base, const WeightCtx& wc, bool vec,
-                                                V (&val)[kRows][4], V* sh_tot) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  T x[kRows][4];
-#pragma unroll
-  for (int r = 0; r < kRows; ++r)
-    load4(lw, base + tile_offset(warp, r, lane, 0), lo, N, vec, x[r]);
-  V carry = vzero(V());
-#pragma unroll
-  for (int r = 0; r < kRows; ++r) {
-    V loc[4];
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const V wv = vfrom_w(Path<T, V>::weight(x[r][q], wc), V());
-      loc[q] = (q == 0) ? wv : vadd(loc[q - 1], wv);
-    }
-    V incl = loc[3];
-#pragma unroll
-    for (int dd = 1; dd < 32; dd <<= 1) {
-      const V y = vshfl_up(incl, dd);
-      if (lane >= dd) incl = vadd(y, incl);
-    }
-    V excl = vshfl_up(incl, 1);
-    if (lane == 0) excl = vzero(V());
-    const V rowtot = vshfl(incl, 31);
-#pragma unroll
-    for (int q = 0; q < 4; ++q) val[r][q] = vadd(carry, vadd(excl, loc[q]));
-    carry = vadd(carry, rowtot);
-  }
-  if (lane == 0) sh_tot[warp] = carry;
-  __syncthreads();
-  V pw = vzero(V());
-  for (int k = 0; k < warp; ++k) pw = vadd(pw, sh_tot[k]);
-#pragma unroll
-  for (int r = 0; r < kRows; ++r)
-#pragma unroll
-    for (int q = 0; q < 4; ++q) val[r][q] = vadd(pw, val[r][q]);
+// Maximum and minimum of non-negative accumulator values (exact; one instruction for the
+// IEEE types, whose values here are never NaN).
+__device__ __forceinline__ float tmax(float a, float b) { return fmaxf(a, b); }
+__device__ __forceinline__ float tmin(float a, float b) { return fminf(a, b); }
+__device__ __forceinline__ double tmax(double a, double b) { return fmax(a, b); }
+__device__ __forceinline__ double tmin(double a, double b) { return fmin(a, b); }
+__device__ __forceinline__ float2 tmax(float2 a, float2 b) { return vmax(a, b); }
+__device__ __forceinline__ float2 tmin(float2 a, float2 b) { return vmin(a, b); }
+
+// floor(x) as a 32-bit integer (x >= 0; values of 2^31 and above saturate, and every caller
+// clamps to n < 2^31 afterwards). floor of a two-float is floor(hi) unless hi is an integer.
+__device__ __forceinline__ int32_t floor_i32(float x) { return __float2int_rd(x); }
+__device__ __forceinline__ int32_t floor_i32(double x) { return __double2int_rd(x); }
+__device__ __forceinline__ int32_t floor_i32(float2 z) {
+  const float f = floorf(z.x);
+  if (!(f < 0x1p31f)) return INT32_MAX;
+  const int32_t i = __float2int_rz(f);
+  return f != z.x ? i : i + __float2int_rd(z.y);  // hi an integer below 2^31: |lo| < 64
 }
 
-// Running maximum of the tile values in element order (exact), restricted to the tile's valid
-// positions (tile_count; other positions keep their raw value and are never used). Returns, through sh_max, the
-// maximum of each warp's valid values; prevmax = maximum over the previous warps.
-template <typename V>
-__device__ __forceinline__ void tile_running_max(V (&val)[kRows][4], int64_t base, int64_t lo,
-                                                 int64_t N, V* sh_max, V& prevmax) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int cnt = tile_count(base, N);
-  V cm = vzero(V());
-#pragma unroll
-  for (int r = 0; r < kRows; ++r) {
-    V x[4];
-    V m = vzero(V());
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const bool valid = tile_offset(warp, r, lane, q) < cnt;
-      if (valid) m = vmax(m, val[r][q]);
-      x[q] = m;
-    }
-    V im = m;
-#pragma unroll
-    for (int dd = 1; dd < 32; dd <<= 1) {
-      const V y = vshfl_up(im, dd);
-      if (lane >= dd) im = vmax(y, im);
-    }
-    V em = vshfl_up(im, 1);
-    if (lane == 0) em = vzero(V());
-    const V before = vmax(em, cm);
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const bool valid = tile_offset(warp, r, lane, q) < cnt;
-      if (valid) val[r][q] = vmax(x[q], before);
-    }
-    cm = vmax(cm, vshfl(im, 31));
-  }
-  if (lane == 0) sh_max[warp] = cm;
-  __syncthreads();
-  prevmax = vzero(V());
-  for (int k = 0; k < warp; ++k) prevmax = vmax(prevmax, sh_max[k]);
-#pragma unroll
-  for (int r = 0; r < kRows; ++r)
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const bool valid = tile_offset(warp, r, lane, q) < cnt;
-      if (valid) val[r][q] = vmax(val[r][q], prevmax);
-    }
-}
-
-// Cumulative offspring of a cumulative weight W (Codes 7 and 8 with r = W * N / W^N).
+// Cumulative offspring of a cumulative weight W (Codes 7 and 8): r = W * c with c = N / W^N
+// rounded once (the order the oracle pins), O = floor(r + u) (systematic) or, for the stratum
+// k = min(n - 1, floor(r)) with its own uniform, min(k + 1, floor(r + u_k)) (stratified);
+// W equal to the total gives O = n (all later weights are zero). r and u are non-negative.
 template <typename T, typename V, bool STRAT>
 __device__ __forceinline__ int32_t cum_offspring(V W, V S, V scale,
                                                  typename Path<T, V>::U u_sys,
-                                                 const Keys& keys, int64_t N) {
-  if (veq(W, S)) return static_cast<int32_t>(N);
+                                                 const Keys& keys, int32_t n) {
+  if (veq(W, S)) return n;
   const V r = vscale(W, scale);
-  int64_t o;
+  int32_t o;
   if constexpr (STRAT) {
-    int64_t k = floor_to_i64(r);
-    k = k < N - 1 ? k : N - 1;
+    int32_t k = floor_i32(r);
+    k = k < n - 1 ? k : n - 1;
     const auto uk = Path<T, V>::draw_u(draw(keys, static_cast<uint32_t>(k), 0u));
-    o = floor_to_i64(vplus_u(r, uk));
+    o = floor_i32(vplus_u(r, uk));
     o = o < k + 1 ? o : k + 1;
   } else {
-    o = floor_to_i64(vplus_u(r, u_sys));
+    o = floor_i32(vplus_u(r, u_sys));
   }
-  o = o < N ? o : N;
-  o = o > 0 ? o : 0;
-  return static_cast<int32_t>(o);
+  return o < n ? o : n;
 }
 
 // ---------------------------------------------------------------------------------------
@@ -431,60 +372,103 @@ __device__ void tile_prefix_compute(const double2* s_rec, double2* P_rec, int nt
 // Shared scratch of the block-level tile functions.
 template <typename V> struct TileSh {
   V tot[kWarps];
-  V max[kWarps];
 };
 
-// The tile's total (its record), stored by thread 0 at rec; returned as fixed point in every
-// thread. A plain block reduction (sequential over a thread's elements, butterfly over the
-// warp, sequential over the warps): the tile prefixes only need an accurate total, because
-// the emission pins every tile's last particle to the next prefix (tile_cum_weights).
+// The tile's total (its record), stored by thread 0 at rec and returned in thread 0 as fixed
+// point (0 in the other threads). A plain block reduction: sequential over a thread's kPer
+// weights, butterfly over the warp, sequential over the warps. The tile prefixes only need an
+// accurate total, because the emission pins every tile's last particle to the next prefix
+// (tile_cum_weights).
 template <typename T, typename V>
 __device__ __forceinline__ u128 tile_record(const T* __restrict__ lw, int64_t lo, int64_t N,
                                             int64_t base, const WeightCtx& wc, bool vec,
                                             double2* rec, TileSh<V>& sh) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  T x[kRows][4];
+  T x[kPer];
+  load_per(lw, base + kPer * static_cast<int64_t>(threadIdx.x), lo, N, vec, x);
+  V t = vfrom_w(Path<T, V>::weight(x[0], wc), V());
 #pragma unroll
-  for (int r = 0; r < kRows; ++r)
-    load4(lw, base + tile_offset(warp, r, lane, 0), lo, N, vec, x[r]);
-  V t = vzero(V());
-#pragma unroll
-  for (int r = 0; r < kRows; ++r)
-#pragma unroll
-    for (int q = 0; q < 4; ++q) t = vadd(t, vfrom_w(Path<T, V>::weight(x[r][q], wc), V()));
+  for (int q = 1; q < kPer; ++q) t = vadd(t, vfrom_w(Path<T, V>::weight(x[q], wc), V()));
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) t = vadd(t, vshfl_xor(t, o));  // same value in every lane
   __syncthreads();  // sh.tot may still be read from the previous tile
   if (lane == 0) sh.tot[warp] = t;
   __syncthreads();
+  if (threadIdx.x != 0) return 0;
   V tm = sh.tot[0];
+#pragma unroll
   for (int k = 1; k < kWarps; ++k) tm = vadd(tm, sh.tot[k]);
-  if (threadIdx.x == 0) store_v<V>(rec, tm);
+  store_v<V>(rec, tm);
   return to_fixed(tm);
 }
 
-// Cumulative weights W[r][q] of this thread's elements of the tile (clamped into [Pt, Pn])
-// and Wwarp, the cumulative weight just before this warp's first element.
-// The tile's last valid particle gets exactly Pn, the next tile's prefix, so the cumulative
-// weight just before any tile is its own prefix Pt and tiles need nothing from each other's
-// scans (the total W^N is then the last prefix).
+// Cumulative weights W[q] of this thread's kPer particles of the tile starting at `base` of
+// the sequence [lo, N), for the tile prefixes Pt (this tile) and Pn (the next), and Wb, the
+// cumulative weight of the particle just before this thread's first one.
+//
+// Scan (the accumulator type's rounded additions, in a fixed order): l_q = sequential prefix
+// of the thread's weights; e = exclusive Hillis-Steele scan of the thread totals over the
+// warp; p_w = sequential sum of the totals of the warps before; W_q = RN(RN(Pt + RN(p_w + e))
+// + l_q) -- at most 7 + 5 + 7 + 3 roundings on any path. Tree sums are not monotone, so:
+//   * inside a thread W_q is non-decreasing by construction;
+//   * across the lanes of a warp, W_q is raised to the running maximum of the earlier lanes'
+//     last values (a max-scan over the lanes);
+//   * across warps, warp w's values are clamped into [B_w, B_{w+1}], B_w = min(RN(Pt + p_w),
+//     Pn), which is non-decreasing in w, and its last particle is pinned to B_{w+1};
+//   * the tile's last valid particle is pinned to Pn, so the particle before any tile has
+//     exactly that tile's prefix Pt, and tiles need nothing from each other's scans.
+// Every cumulative weight thus lies in [Pt, Pn] and the whole sequence is non-decreasing, so
+// Code 11 writes every ancestor position exactly once. Positions past the sequence end have
+// weight 0 and repeat the last valid value; callers do not emit them.
 template <typename T, typename V>
 __device__ __forceinline__ void tile_cum_weights(const T* __restrict__ lw, int64_t lo, int64_t N,
                                                  int64_t base, const WeightCtx& wc, bool vec,
-                                                 V Pt, V Pn, V (&W)[kRows][4], V& Wwarp,
+                                                 V Pt, V Pn, V (&W)[kPer], V& Wb,
                                                  TileSh<V>& sh) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  T x[kPer];
+  load_per(lw, base + kPer * static_cast<int64_t>(tid), lo, N, vec, x);
+#pragma unroll
+  for (int q = 0; q < kPer; ++q) {
+    const V wv = vfrom_w(Path<T, V>::weight(x[q], wc), V());
+    W[q] = (q == 0) ? wv : vadd(W[q - 1], wv);
+  }
+  V incl = W[kPer - 1];
+#pragma unroll
+  for (int dd = 1; dd < 32; dd <<= 1) {
+    const V y = vshfl_up(incl, dd);
+    if (lane >= dd) incl = vadd(y, incl);
+  }
+  V excl = vshfl_up(incl, 1);
+  if (lane == 0) excl = vzero(V());
+  const V wtot = vshfl(incl, 31);
+  __syncthreads();  // sh.tot may still be read from the previous tile
+  if (lane == 0) sh.tot[warp] = wtot;
+  __syncthreads();
+  V pw = vzero(V());
+  for (int k = 0; k < warp; ++k) pw = vadd(pw, sh.tot[k]);
+  const V Bw = tmin(vadd(Pt, pw), Pn);
+  const V Bn = tmin(vadd(Pt, vadd(pw, wtot)), Pn);
+  const V b = vadd(Pt, vadd(pw, excl));
+#pragma unroll
+  for (int q = 0; q < kPer; ++q) W[q] = vadd(b, W[q]);
+  V m = W[kPer - 1];
+#pragma unroll
+  for (int dd = 1; dd < 32; dd <<= 1) {
+    const V y = vshfl_up(m, dd);
+    if (lane >= dd) m = tmax(y, m);
+  }
+  V pm = vshfl_up(m, 1);
+  if (lane == 0) pm = Bw;
+#pragma unroll
+  for (int q = 0; q < kPer; ++q) W[q] = tmin(tmax(W[q], pm), Bn);
+  if (lane == 31) W[kPer - 1] = Bn;
   const int last = tile_count(base, N) - 1;
-  V val[kRows][4];
-  tile_raw_values<T, V>(lw, lo, N, base, wc, vec, val, sh.tot);
-  V prevmax;
-  tile_running_max<V>(val, base, lo, N, sh.max, prevmax);
 #pragma unroll
-  for (int r = 0; r < kRows; ++r)
-#pragma unroll
-    for (int q = 0; q < 4; ++q)
-      W[r][q] = tile_offset(warp, r, lane, q) == last ? Pn : vclamp(vadd(Pt, val[r][q]), Pt, Pn);
-  Wwarp = vclamp(vadd(Pt, prevmax), Pt, Pn);
+  for (int q = 0; q < kPer; ++q)
+    if (kPer * tid + q == last) W[q] = Pn;
+  Wb = vshfl_up(W[kPer - 1], 1);
+  if (lane == 0) Wb = Bw;
 }
 
 // The systematic uniform u (counter (0, 0)), drawn once per CTA.
@@ -497,61 +481,56 @@ __device__ __forceinline__ typename Path<T, V>::U cta_uniform0(const Keys& keys)
   return sh_u;
 }
 
+// kPer int32 values to p[0 .. cnt) (128-bit stores when all are inside and p is aligned).
+__device__ __forceinline__ void store_per(int32_t* __restrict__ p, const int32_t (&v)[kPer],
+                                          int cnt) {
+  if (cnt >= kPer && (reinterpret_cast<uintptr_t>(p) & 15u) == 0) {
+    reinterpret_cast<int4*>(p)[0] = make_int4(v[0], v[1], v[2], v[3]);
+    reinterpret_cast<int4*>(p)[1] = make_int4(v[4], v[5], v[6], v[7]);
+  } else {
+#pragma unroll
+    for (int q = 0; q < kPer; ++q)
+      if (q < cnt) p[q] = v[q];
+  }
+}
+
 // Systematic / stratified emission of one tile starting at `base` of the sequence [lo, N)
 // (block-level): cumulative offspring O of every particle, the Code-11 scatter of local
 // ancestor indices into a[lo + j] and, when d is given, the Prepermute claims
-// d[lo + i] = O_{i-1} if particle i has offspring, else n (for a non-decreasing ancestry
-// the lowest claimant of slot i is the first position of its run). Pt, Pn: prefixes of this
-// tile; has_prev: a tile precedes this one in the sequence (its last particle's cumulative
-// weight is Pt). u_sys: the systematic uniform (cta_uniform0; unused when STRAT).
+// d[lo + i] = O_{i-1} if particle i has offspring, else n (for a non-decreasing ancestry the
+// lowest claimant of slot i is the first position of its run). Pt, Pn: prefixes of this tile;
+// u_sys: the systematic uniform (cta_uniform0; unused when STRAT). Local indices are 32-bit
+// (n < 2^31).
 template <typename T, typename V, bool STRAT>
 __device__ __forceinline__ void emit_tile_cumoff(const T* __restrict__ lw, int64_t lo, int64_t N,
                                                  int64_t base, const WeightCtx& wc, bool vec,
-                                                 V Pt, V Pn, bool has_prev, V S,
-                                                 V scale, typename Path<T, V>::U u_sys,
+                                                 V Pt, V Pn, V S, V scale,
+                                                 typename Path<T, V>::U u_sys,
                                                  const Keys& keys, int32_t* __restrict__ a,
                                                  int32_t* __restrict__ d, TileSh<V>& sh) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int64_t n = N - lo;
-  const int cnt = tile_count(base, N);
-  V W[kRows][4], Wwarp;
-  tile_cum_weights<T, V>(lw, lo, N, base, wc, vec, Pt, Pn, W, Wwarp, sh);
-  int32_t O[kRows][4];
+  const int lane = threadIdx.x & 31;
+  const int32_t n = static_cast<int32_t>(N - lo);
+  const int cnt = tile_count(base, N) - kPer * static_cast<int>(threadIdx.x);  // valid here
+  const int32_t i0 = static_cast<int32_t>(base - lo) + kPer * static_cast<int32_t>(threadIdx.x);
+  V W[kPer], Wb;
+  tile_cum_weights<T, V>(lw, lo, N, base, wc, vec, Pt, Pn, W, Wb, sh);
+  int32_t O[kPer];
 #pragma unroll
-  for (int r = 0; r < kRows; ++r)
+  for (int q = 0; q < kPer; ++q) O[q] = cum_offspring<T, V, STRAT>(W[q], S, scale, u_sys, keys, n);
+  int32_t prev = __shfl_up_sync(0xffffffffu, O[kPer - 1], 1);
+  if (lane == 0) prev = cum_offspring<T, V, STRAT>(Wb, S, scale, u_sys, keys, n);
+  int32_t* const al = a + lo;
+  int32_t dv[kPer];
 #pragma unroll
-    for (int q = 0; q < 4; ++q)
-      O[r][q] = cum_offspring<T, V, STRAT>(W[r][q], S, scale, u_sys, keys, n);
-  // cumulative offspring just before this warp's first element
-  int32_t Obefore = 0;
-  if (lane == 0) {
-    if (warp > 0)
-      Obefore = cum_offspring<T, V, STRAT>(Wwarp, S, scale, u_sys, keys, n);
-    else if (has_prev)
-      Obefore = cum_offspring<T, V, STRAT>(Pt, S, scale, u_sys, keys, n);
+  for (int q = 0; q < kPer; ++q) {
+    const int32_t i = i0 + q;
+    const int32_t Oc = (i == n - 1) ? n : O[q];
+    if (q < cnt)
+      for (int32_t j = prev; j < Oc; ++j) al[j] = i;
+    dv[q] = (Oc > prev) ? prev : n;
+    prev = Oc;
   }
-#pragma unroll
-  for (int r = 0; r < kRows; ++r) {
-    int32_t prev = __shfl_up_sync(0xffffffffu, O[r][3], 1);
-    if (r > 0) {
-      const int32_t rowprev = __shfl_sync(0xffffffffu, O[r - 1][3], 31);
-      if (lane == 0) prev = rowprev;
-    } else if (lane == 0) {
-      prev = Obefore;
-    }
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int off = tile_offset(warp, r, lane, q);
-      const int64_t i = base + off - lo;
-      int32_t Oc = O[r][q];
-      if (i == n - 1) Oc = static_cast<int32_t>(n);
-      if (off < cnt) {
-        for (int32_t j = prev; j < Oc; ++j) a[lo + j] = static_cast<int32_t>(i);
-        if (d) d[lo + i] = (Oc > prev) ? prev : static_cast<int32_t>(n);
-      }
-      prev = Oc;
-    }
-  }
+  if (d && cnt > 0) store_per(d + lo + i0, dv, cnt);
 }
 
 // Stored cumulative weights of one tile (block-level): W[e] for e in [lo, N).
@@ -569,17 +548,13 @@ template <typename T, typename V, typename OUT>
 __device__ __forceinline__ void emit_tile_W(const T* __restrict__ lw, int64_t lo, int64_t N,
                                             int64_t base, const WeightCtx& wc, bool vec, V Pt,
                                             V Pn, OUT* __restrict__ Wout, TileSh<V>& sh) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int cnt = tile_count(base, N);
-  V W[kRows][4], Wwarp;
-  tile_cum_weights<T, V>(lw, lo, N, base, wc, vec, Pt, Pn, W, Wwarp, sh);
+  const int cnt = tile_count(base, N) - kPer * static_cast<int>(threadIdx.x);
+  V W[kPer], Wb;
+  tile_cum_weights<T, V>(lw, lo, N, base, wc, vec, Pt, Pn, W, Wb, sh);
+  OUT* const p = Wout + base + kPer * static_cast<int64_t>(threadIdx.x);
 #pragma unroll
-  for (int r = 0; r < kRows; ++r)
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int off = tile_offset(warp, r, lane, q);
-      if (off < cnt) Wout[base + off] = convert_out<V, OUT>(W[r][q]);
-    }
+  for (int q = 0; q < kPer; ++q)
+    if (q < cnt) p[q] = convert_out<V, OUT>(W[q]);
 }
 
 // Multinomial search (Code 5) for output i of a sequence of n cumulative weights W: u =
@@ -654,51 +629,34 @@ __device__ __forceinline__ int64_t guide_count(V W, const Guide& g, int64_t n) {
 template <typename T, typename V>
 __device__ __forceinline__ void emit_tile_W_guide(const T* __restrict__ lw, int64_t lo, int64_t N,
                                                   int64_t base, const WeightCtx& wc, bool vec,
-                                                  V Pt, V Pn, bool has_prev,
-                                                  const Guide& gd, V* __restrict__ Wout,
+                                                  V Pt, V Pn, const Guide& gd,
+                                                  V* __restrict__ Wout,
                                                   int32_t* __restrict__ G, TileSh<V>& sh) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int64_t n = N - lo;
-  const int cnt = tile_count(base, N);
-  V W[kRows][4], Wwarp;
-  tile_cum_weights<T, V>(lw, lo, N, base, wc, vec, Pt, Pn, W, Wwarp, sh);
-  int64_t C[kRows][4];
+  const int lane = threadIdx.x & 31;
+  const int32_t n = static_cast<int32_t>(N - lo);
+  const int cnt = tile_count(base, N) - kPer * static_cast<int>(threadIdx.x);
+  const int32_t j0 = static_cast<int32_t>(base - lo) + kPer * static_cast<int32_t>(threadIdx.x);
+  V W[kPer], Wb;
+  tile_cum_weights<T, V>(lw, lo, N, base, wc, vec, Pt, Pn, W, Wb, sh);
+  V* const p = Wout + base + kPer * static_cast<int64_t>(threadIdx.x);
+  int32_t C[kPer];
 #pragma unroll
-  for (int r = 0; r < kRows; ++r)
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int off = tile_offset(warp, r, lane, q);
-      if (off < cnt) Wout[base + off] = W[r][q];
-      C[r][q] = guide_count<V>(W[r][q], gd, n);
-    }
-  int64_t Cbefore = 0;
-  if (lane == 0) {
-    if (warp > 0)
-      Cbefore = guide_count<V>(Wwarp, gd, n);
-    else if (has_prev)
-      Cbefore = guide_count<V>(Pt, gd, n);
+  for (int q = 0; q < kPer; ++q) {
+    if (q < cnt) p[q] = W[q];
+    C[q] = static_cast<int32_t>(guide_count<V>(W[q], gd, n));
   }
+  int32_t prev = __shfl_up_sync(0xffffffffu, C[kPer - 1], 1);
+  if (lane == 0) prev = static_cast<int32_t>(guide_count<V>(Wb, gd, n));
+  int32_t* const Gl = G + lo;
 #pragma unroll
-  for (int r = 0; r < kRows; ++r) {
-    int64_t prev = __shfl_up_sync(0xffffffffu, C[r][3], 1);
-    if (r > 0) {
-      const int64_t rowprev = __shfl_sync(0xffffffffu, C[r - 1][3], 31);
-      if (lane == 0) prev = rowprev;
-    } else if (lane == 0) {
-      prev = Cbefore;
+  for (int q = 0; q < kPer; ++q) {
+    const int32_t j = j0 + q;
+    const int32_t Cc = (j == n - 1) ? n : C[q];
+    if (q < cnt) {
+      for (int32_t b = prev; b < Cc; ++b) Gl[b] = j;
+      if (j == n - 1) Gl[n] = n - 1;
     }
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int off = tile_offset(warp, r, lane, q);
-      const int64_t j = base + off - lo;
-      int64_t Cc = C[r][q];
-      if (j == n - 1) Cc = n;
-      if (off < cnt) {
-        for (int64_t b = prev; b < Cc; ++b) G[lo + b] = static_cast<int32_t>(j);
-        if (j == n - 1) G[lo + n] = static_cast<int32_t>(n - 1);
-      }
-      prev = Cc;
-    }
+    prev = Cc;
   }
 }
 
