@@ -207,6 +207,14 @@ int rs_permute(rs_handle* h, const int32_t* a_dev, int64_t N, int32_t* c_dev, vo
 #define RS_LAUNCH_SEPARATE 2
 int rs_set_launch_mode(rs_handle* h, int mode);
 
+/* The longest a grid-wide barrier of the handle's cooperative kernels waits, in nanoseconds
+ * (default 10 s). A wait that runs out records RS_ERR_TIMEOUT and the kernel goes on, so it
+ * ends and the context stays usable; rs_last_error reports the status and resets the
+ * handle's barrier state, after which the handle works again. Tests set a short limit.
+ * Synchronises the handle's device; RS_ERR_ARG for timeout_ns = 0. The paper has no
+ * counterpart (its kernels never wait on each other). */
+int rs_set_barrier_timeout(rs_handle* h, uint64_t timeout_ns);
+
 /* Effective sample size of N log-weights: *ess_dev (one binary64 on the device) =
  * (sum_i w_i)^2 / sum_i w_i^2 with w_i = exp(logw_i - max logw) (Appendix E), between 1 and N
  * -- the statistic an adaptive particle filter compares with a threshold to decide whether to
@@ -415,11 +423,15 @@ const char* rs_trace_label(const rs_handle* h, int i);
  *   status_dev         : NULL, or one device int32 that receives RS_OK or the device-side
  *                        status (the codes of rs_last_error) when the stream reaches the end
  *                        of the call.
- * The first call on each device looks up the device address of the static array
- * (cudaGetSymbolAddress) with that device current: make that first call before any stream
- * capture. All calls on a device share the one array and overwrite it: calls that overlap
- * on the GPU (several streams or host threads at once) race and must be serialised by the
- * caller. The call allocates and frees nothing. */
+ * logw_dev, ancestors_dev and status_dev must be memory of the current device (or managed
+ * memory): a pointer of another device or of host memory returns RS_ERR_ARG before anything
+ * is launched. The first call on each device looks up the device address of the static
+ * array (cudaGetSymbolAddress) with that device current and keeps it for the life of the
+ * process: make that first call before any stream capture, and make no call on a device
+ * after cudaDeviceReset on it (the kept address would be stale). All calls on a device share
+ * the one array and overwrite it: calls that overlap on the GPU (several streams or host
+ * threads at once) race and must be serialised by the caller. The call allocates and frees
+ * nothing. */
 #define RS_NOALLOC_MAX_N (1 << 22)
 int rs_systematic_noalloc(int dtype, const void* logw_dev, int64_t N, uint64_t seed,
                           uint64_t step, int32_t* ancestors_dev, int32_t* status_dev,

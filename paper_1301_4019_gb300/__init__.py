@@ -45,7 +45,8 @@ EXPORTED = [
     "rs_log_sum_weights_batched", "rs_ess_batched", "rs_metropolis_B_batched",
     "rs_resample_batched_masked", "rs_reset_weights_batched",
     "rs_set_batched_launch", "rs_get_batched_launch", "rs_tune_batched", "rs_philox_throughput",
-    "rs_cumulative_weights_f64",
+    "rs_cumulative_weights_f64", "rs_check_acceptance", "rs_set_barrier_timeout",
+    "rs_check_barrier_timeout",
     "rs_capture_if_below",
     "rs_capture_end_if", "rs_smc_mark_resampled", "rs_smc_loglik_step",
 ]
@@ -124,6 +125,9 @@ def _declare(lib):
         "rs_get_batched_launch": (I, [P, I, C.POINTER(I), C.POINTER(I)]),
         "rs_tune_batched": (I, [P, I, P, P, I32, P, I32, I, P]),
         "rs_philox_throughput": (I, [P, I64, C.c_uint32, U64, P, P]),
+        "rs_check_acceptance": (I, [I, I64, P, P]),
+        "rs_set_barrier_timeout": (I, [P, U64]),
+        "rs_check_barrier_timeout": (I, [P, P]),
         "rs_capture_if_below": (I, [P, P, C.c_double, P, C.POINTER(P)]),
         "rs_capture_end_if": (I, [P, P]),
         "rs_smc_mark_resampled": (I, [P, P, I64, P, C.c_double, P, P]),
@@ -576,6 +580,30 @@ def rs_philox_throughput(h: Handle, threads: int, draws_per_thread: int, seed: i
     return out
 
 
+def rs_set_barrier_timeout(h: Handle, timeout_ns: int) -> None:
+    """Longest wait of a grid barrier of the handle's cooperative kernels (default 10 s)."""
+    _check(load().rs_set_barrier_timeout(h.ptr, int(timeout_ns)), "rs_set_barrier_timeout")
+
+
+def rs_check_barrier_timeout(h: Handle, stream=None) -> None:
+    """Self-check (include/resample_measure.h): a cooperative launch whose barrier wait runs
+    out; rs_last_error then reports RS_ERR_TIMEOUT and resets the barrier state."""
+    _check(load().rs_check_barrier_timeout(h.ptr, _stream(stream)), "rs_check_barrier_timeout")
+
+
+def rs_check_acceptance(mode: int, n: int = 0, device: int | None = None) -> int:
+    """Self-check of the acceptance tests (include/resample_measure.h): the number of wrong
+    decisions found (mode 0: every binary32 delta in [-86.5, 0); mode 1: the binary64
+    decisions on n log-weight pairs). Synchronises the device's current stream."""
+    dev = torch.device("cuda", torch.cuda.current_device() if device is None else device)
+    with torch.cuda.device(dev):
+        out = torch.zeros(1, dtype=torch.int64, device=dev)
+        _check(load().rs_check_acceptance(int(mode), int(n), out.data_ptr(),
+                                          _stream(torch.cuda.current_stream(dev))),
+               "rs_check_acceptance")
+        return int(out.item())
+
+
 def rs_capture_if_below(h: Handle, value: torch.Tensor, threshold: float, stream=None):
     """Inside a CUDA graph capture on `stream`: open a conditional body that runs when
     value[0] < threshold on the device; returns the stream to capture the body on."""
@@ -644,17 +672,27 @@ def rs_systematic_noalloc(logw: torch.Tensor, seed: int = 0, step: int = 0,
                           stream=None) -> torch.Tensor:
     """Systematic resampling for callers that cannot allocate device memory: no handle, the
     scratch is a static device array of the library (N <= NOALLOC_MAX_N). Calls that overlap
-    on the GPU race on that array. ``out`` and ``status`` (one int32) are caller buffers."""
+    on the GPU race on that array. ``out`` and ``status`` (one int32) are caller buffers on
+    logw's device; the call runs with that device current, on ``stream`` or that device's
+    current stream."""
+    if not isinstance(logw, torch.Tensor) or not logw.is_cuda:
+        raise TypeError("logw must be a CUDA tensor")
+    dev = logw.device
+    for name, t in (("out", out), ("status", status)):
+        if t is not None and (not isinstance(t, torch.Tensor) or t.device != dev):
+            raise ValueError(f"{name} must be a CUDA tensor on {dev}")
     N = logw.numel()
-    if out is None:
-        out = torch.empty(N, dtype=torch.int32, device=logw.device)
-    st_ptr = _dev(status, torch.int32, "status", 1) if status is not None else None
-    _check(load().rs_systematic_noalloc(_dtype_code(logw), _dev(logw, None, "logw"), N,
-                                        int(seed) & 0xFFFFFFFFFFFFFFFF,
-                                        int(step) & 0xFFFFFFFFFFFFFFFF,
-                                        _dev(out, torch.int32, "out", N), st_ptr,
-                                        _stream(stream)),
-           "rs_systematic_noalloc")
+    with torch.cuda.device(dev):
+        if out is None:
+            out = torch.empty(N, dtype=torch.int32, device=dev)
+        st_ptr = _dev(status, torch.int32, "status", 1) if status is not None else None
+        _check(load().rs_systematic_noalloc(_dtype_code(logw), _dev(logw, None, "logw"), N,
+                                            int(seed) & 0xFFFFFFFFFFFFFFFF,
+                                            int(step) & 0xFFFFFFFFFFFFFFFF,
+                                            _dev(out, torch.int32, "out", N), st_ptr,
+                                            _stream(stream if stream is not None
+                                                    else torch.cuda.current_stream(dev))),
+               "rs_systematic_noalloc")
     return out
 
 

@@ -149,6 +149,9 @@ int rs_create(rs_handle** out, int64_t max_n, int device) {
   ok &= cudaMalloc(&s.err, sizeof(int)) == cudaSuccess;
   if (ok) {
     ok &= cudaMemset(s.glob, 0, sizeof(rsk::ScanGlob)) == cudaSuccess;
+    const unsigned long long limit = rsk::kDefaultBarrierTimeoutNs;
+    ok &= cudaMemcpy(&s.glob->bar.timeout_ns, &limit, sizeof(limit), cudaMemcpyHostToDevice) ==
+          cudaSuccess;
     const int none = rsk::kNoError;
     ok &= cudaMemcpy(s.err, &none, sizeof(int), cudaMemcpyHostToDevice) == cudaSuccess;
     ok &= cudaDeviceSynchronize() == cudaSuccess;
@@ -589,6 +592,31 @@ int rs_philox_throughput(rs_handle* h, int64_t threads, uint32_t draws_per_threa
   return cuda_status(e);
 }
 
+int rs_set_barrier_timeout(rs_handle* h, uint64_t timeout_ns) {
+  if (!h || timeout_ns == 0) return RS_ERR_ARG;
+  int st = set_device(h);
+  if (st != RS_OK) return st;
+  const unsigned long long v = timeout_ns;
+  if (cudaDeviceSynchronize() != cudaSuccess ||
+      cudaMemcpy(&h->s.glob->bar.timeout_ns, &v, sizeof(v), cudaMemcpyHostToDevice) !=
+          cudaSuccess)
+    return RS_ERR_CUDA;
+  return RS_OK;
+}
+
+int rs_check_barrier_timeout(rs_handle* h, void* stream) {
+  if (!h) return RS_ERR_ARG;
+  int st = set_device(h);
+  if (st != RS_OK) return st;
+  if (!h->s.coop) return RS_ERR_CUDA;
+  return cuda_status(rsk::launch_barrier_timeout_probe(h->s, as_stream(stream)));
+}
+
+int rs_check_acceptance(int mode, int64_t n, unsigned long long* count_dev, void* stream) {
+  if (!count_dev || mode < 0 || mode > 1 || (mode == 1 && n < 1)) return RS_ERR_ARG;
+  return cuda_status(rsk::launch_check_acceptance(mode, n, count_dev, as_stream(stream)));
+}
+
 int rs_set_batched_launch(rs_handle* h, int kernel, int block, int items_per_thread) {
   if (!h || kernel < 0 || kernel >= rsk::kCfgCount) return RS_ERR_ARG;
   if (!valid_launch(block, items_per_thread)) return RS_ERR_ARG;
@@ -753,7 +781,7 @@ int rs_last_error(rs_handle* h, void* stream) {
   if (cudaMemcpy(h->s.err, &none, sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess)
     return RS_ERR_CUDA;
   if (v == -RS_ERR_TIMEOUT) {  // a grid barrier gave up: its arrival counter may be stale
-    if (cudaMemset(&h->s.glob->bar_count, 0, sizeof(unsigned int)) != cudaSuccess ||
+    if (cudaMemset(&h->s.glob->bar.count, 0, sizeof(unsigned int)) != cudaSuccess ||
         cudaDeviceSynchronize() != cudaSuccess)
       return RS_ERR_CUDA;
   }

@@ -59,11 +59,9 @@ permute_sorted_kernel(const int32_t* __restrict__ a, const int32_t* __restrict__
 }
 
 // Permute of a non-decreasing ancestry (permute_sorted_one) with four consecutive slots per
-// thread: the slot loads of a and d are 128-bit and every thread has four slots' loads in
-// flight; the walks of failed claims follow one after the other. The reads and writes of each
-// slot are those of permute_sorted_one, so c is the same. (For an unsorted ancestry the same
-// layout measured 1-3 % slower than one slot per thread: there the random claim checks and
-// walks dominate.)
+// thread: the slot loads of a and d are 128-bit, and the walks of failed claims run together
+// (walk4), up to four dependent chains in flight per thread. The reads and writes of each
+// slot are those of permute_sorted_one, so c is the same.
 __global__ void __launch_bounds__(kBlock)
 permute_sorted4_kernel(const int32_t* __restrict__ a, const int32_t* __restrict__ d, int64_t N,
                        int32_t* __restrict__ c, int* err) {
@@ -101,24 +99,60 @@ permute_sorted4_kernel(const int32_t* __restrict__ a, const int32_t* __restrict_
 #pragma unroll
   for (int q = 0; q < 4; ++q)
     if (ok[q] && D[q] != sentinel) c[i0 + q] = static_cast<int32_t>(i0 + q);
+  int32_t x[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) x[q] = static_cast<int32_t>(i0 + q);
+  walk4(d, sentinel, c, x, D, A, fail, N, err);
+}
+
+// Permute of any ancestry (permute_one) with four consecutive slots per thread: 128-bit slot
+// loads, the four claim checks d[a_i] issued together, and the walks of failed claims run
+// together (walk4). Same reads and writes per slot as permute_one, so c is the same.
+__global__ void __launch_bounds__(kBlock)
+permute4_kernel(const int32_t* __restrict__ a, const int32_t* __restrict__ d, int64_t N,
+                int32_t* __restrict__ c, int* err) {
+  pdl_wait();
+  const int64_t i0 = 4 * (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x);
+  if (i0 >= N) return;
+  const int32_t sentinel = static_cast<int32_t>(N);
+  int32_t A[4], D[4];
+  const bool vec = i0 + 3 < N &&
+                   ((reinterpret_cast<uintptr_t>(a) | reinterpret_cast<uintptr_t>(d)) & 15u) == 0;
+  if (vec) {
+    const int4 va = *reinterpret_cast<const int4*>(a + i0);
+    const int4 vd = *reinterpret_cast<const int4*>(d + i0);
+    A[0] = va.x; A[1] = va.y; A[2] = va.z; A[3] = va.w;
+    D[0] = vd.x; D[1] = vd.y; D[2] = vd.z; D[3] = vd.w;
+  } else {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      A[q] = i0 + q < N ? a[i0 + q] : 0;
+      D[q] = i0 + q < N ? d[i0 + q] : sentinel;
+    }
+  }
+  bool ok[4];
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
-    if (!fail[q]) continue;
-    int64_t x = i0 + q;
-    int32_t dx = D[q];
-    int64_t steps = 0;
-    bool good = true;
-    while (dx != sentinel) {
-      if (dx < 0 || dx > sentinel || ++steps > N) {  // only a corrupted d can get here
-        flag_error(err, RS_ERR_ARG);
-        good = false;
-        break;
-      }
-      x = dx;
-      dx = d[x];
+    ok[q] = i0 + q < N;
+    if (ok[q] && (A[q] < 0 || A[q] >= N)) {
+      flag_error(err, RS_ERR_ARG);
+      ok[q] = false;
     }
-    if (good) c[x] = A[q];
   }
+  int32_t claim[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) claim[q] = ok[q] ? d[A[q]] : static_cast<int32_t>(i0 + q);
+#pragma unroll
+  for (int q = 0; q < 4; ++q)
+    if (ok[q] && D[q] != sentinel) c[i0 + q] = static_cast<int32_t>(i0 + q);
+  bool fail[4];
+  int32_t x[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    fail[q] = ok[q] && claim[q] != static_cast<int32_t>(i0 + q);
+    x[q] = static_cast<int32_t>(i0 + q);
+  }
+  walk4(d, sentinel, c, x, D, A, fail, N, err);
 }
 
 // Ancestors-to-Offspring (Code 12).
@@ -271,7 +305,7 @@ __device__ __forceinline__ long long block_sum_ll(long long v, long long* sh) {
 
 __global__ void __launch_bounds__(kBlock)
 iscan_coop_kernel(const int32_t* __restrict__ in, int64_t N, int T, long long* tot,
-                  long long* pre, int32_t* __restrict__ out, unsigned int* bar, int* err) {
+                  long long* pre, int32_t* __restrict__ out, GridBar* bar, int* err) {
   __shared__ long long sh[kWarps];
   unsigned int target = 0;
   const int G = static_cast<int>(gridDim.x), c = static_cast<int>(blockIdx.x);
@@ -303,6 +337,15 @@ iscan_coop_kernel(const int32_t* __restrict__ in, int64_t N, int T, long long* t
   grid_exit(bar, target);
 }
 
+// Self-check of the bounded grid barrier: the barrier's target is one arrival more than the
+// grid makes, so every CTA waits until the handle's timeout, records RS_ERR_TIMEOUT and goes
+// on; the exit arrivals then cannot return the counter to 0 (rs_last_error resets it).
+__global__ void __launch_bounds__(kBlock) barrier_timeout_probe_kernel(GridBar* bar, int* err) {
+  unsigned int target = 1;
+  grid_barrier(bar, target, err);
+  grid_exit(bar, target);
+}
+
 inline int grid_for(int64_t N) { return static_cast<int>((N + kBlock - 1) / kBlock); }
 
 }  // namespace
@@ -327,10 +370,18 @@ cudaError_t launch_prepermute(const Scratch& s, const int32_t* a, int64_t N, int
   return cudaGetLastError();
 }
 
+// Four slots per thread (permute4_kernel) from kPermute4MinN slots; below, one slot per
+// thread keeps more threads in flight.
+constexpr int64_t kPermute4MinN = int64_t{1} << 18;
+
 cudaError_t launch_permute(const Scratch& s, const int32_t* a, const int32_t* d, int64_t N,
                            int32_t* c, cudaStream_t st) {
   trace_mark(s.trace, "permute", st);
-  launch_pdl(permute_kernel, grid_for(N), kBlock, st, a, d, N, c, s.err);
+  if (N >= kPermute4MinN)
+    launch_pdl(permute4_kernel, static_cast<int>((N + 4 * kBlock - 1) / (4 * kBlock)), kBlock,
+               st, a, d, N, c, s.err);
+  else
+    launch_pdl(permute_kernel, grid_for(N), kBlock, st, a, d, N, c, s.err);
   return cudaGetLastError();
 }
 
@@ -370,7 +421,7 @@ cudaError_t launch_inclusive_scan_i32(const Scratch& s, const int32_t* o, int64_
       const int grid = tiles < cap ? tiles : cap;
       trace_mark(s.trace, "iscan", st);
       return coop_launch(iscan_coop_kernel, grid, st, o, N, tiles, tot, pre, O,
-                         &s.glob->bar_count, s.err);
+                         &s.glob->bar, s.err);
     }
   }
   trace_mark(s.trace, "iscan_sum", st);
@@ -378,6 +429,17 @@ cudaError_t launch_inclusive_scan_i32(const Scratch& s, const int32_t* o, int64_
   trace_mark(s.trace, "iscan_emit", st);
   launch_pdl(iscan_emit_kernel, tiles, kBlock, st, o, N, pre, O);
   return cudaGetLastError();
+}
+
+cudaError_t launch_barrier_timeout_probe(const Scratch& s, cudaStream_t st) {
+  const int cap = coop_capacity(reinterpret_cast<const void*>(barrier_timeout_probe_kernel));
+  if (cap < 1) return cudaErrorCooperativeLaunchTooLarge;
+  int dev = 0, sms = 1;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int grid = sms < cap ? sms : cap;
+  trace_mark(s.trace, "barrier_timeout_probe", st);
+  return coop_launch(barrier_timeout_probe_kernel, grid, st, &s.glob->bar, s.err);
 }
 
 cudaError_t launch_adjacent_difference(const int32_t* O, int64_t N, int32_t* o,

@@ -42,7 +42,7 @@ __device__ __forceinline__ float ess_weight(double x, float, float2 M2) {
 
 template <typename T>
 __global__ void __launch_bounds__(kBlock)
-ess_kernel(const T* __restrict__ lw, int64_t N, double* blockmax, u128* agg, unsigned int* bar,
+ess_kernel(const T* __restrict__ lw, int64_t N, double* blockmax, u128* agg, GridBar* bar,
            double* ess_out, double* log_total_out, int* err) {
   __shared__ long long sh_key[kWarps];
   __shared__ float2 sh_s[kWarps][2];
@@ -164,9 +164,9 @@ cudaError_t launch_ess(const Scratch& s, bool f64, const void* logw, int64_t N, 
   trace_mark(s.trace, f64 ? "ess_f64" : "ess_f32", st);
   if (f64)
     return coop_launch(ess_kernel<double>, grid, st, static_cast<const double*>(logw), N,
-                       s.blockmax, agg, &s.glob->bar_count, ess, log_total, s.err);
+                       s.blockmax, agg, &s.glob->bar, ess, log_total, s.err);
   return coop_launch(ess_kernel<float>, grid, st, static_cast<const float*>(logw), N,
-                     s.blockmax, agg, &s.glob->bar_count, ess, log_total, s.err);
+                     s.blockmax, agg, &s.glob->bar, ess, log_total, s.err);
 }
 
 }  // namespace rsk

@@ -8,7 +8,7 @@
 // separate kernels on the same tiles: the results are identical. The latency-bound
 // particle-parallel steps that follow (the multinomial search, Permute) stay separate
 // full-occupancy kernels.
-// A barrier waits at most kBarrierTimeoutNs (then it records RS_ERR_TIMEOUT and proceeds;
+// A barrier waits at most the handle's barrier timeout (then it records RS_ERR_TIMEOUT and proceeds;
 // every phase stays bounds-checked, so the kernel still ends); the barrier counter returns
 // to 0 at the end of every launch.
 #include <cfloat>
@@ -166,7 +166,7 @@ __device__ __forceinline__ void fused_body(const T* __restrict__ lw, const Fused
     const long long bm = block_max_key(m, sh_key);
     if (threadIdx.x == 0) A.blockmax[c] = fvalue(bm, T());
   }
-  grid_barrier(&A.g->bar_count, target, A.err);
+  grid_barrier(&A.g->bar, target, A.err);
   double M;
   {
     long long m = fkey(-static_cast<double>(INFINITY));
@@ -193,7 +193,7 @@ __device__ __forceinline__ void fused_body(const T* __restrict__ lw, const Fused
     }
     if (threadIdx.x == 0) st_u128(A.agg + c, run);
   }
-  grid_barrier(&A.g->bar_count, target, A.err);
+  grid_barrier(&A.g->bar, target, A.err);
 
   // ---- phase 3: the total and this CTA's tile prefixes --------------------------------------
   if (zero) {  // all weights zero (flagged): every particle keeps itself
@@ -218,10 +218,23 @@ __device__ __forceinline__ void fused_body(const T* __restrict__ lw, const Fused
     if (k < c) CP += v;
   }
   block_sum2_u128(CP, TOT, sh_sum);
-  const V S = fixed_to(TOT, V(), kFixFrac);
-  const double Sd = vto_double(S);
+  // the total, N / total and the guide step: once per CTA (a binary64 division runs on the
+  // 1/57-rate pipe), then shared
+  __shared__ double2 sh_S, sh_scale;
+  __shared__ double sh_Sd;
+  __shared__ Guide sh_gd;
+  if (threadIdx.x == 0) {
+    const V S0 = fixed_to(TOT, V(), kFixFrac);
+    const double Sd0 = vto_double(S0);
+    store_v<V>(&sh_S, S0);
+    store_v<V>(&sh_scale, vfrom_double(__ddiv_rn(static_cast<double>(N), Sd0), V()));
+    sh_Sd = Sd0;
+    if constexpr (SCHEME == RS_MULTINOMIAL) sh_gd = make_guide(Sd0, N);
+  }
+  __syncthreads();
+  const V S = load_v<V>(&sh_S), scale = load_v<V>(&sh_scale);
+  const double Sd = sh_Sd;
   const bool all_zero = !(Sd > 0.0);
-  const V scale = vfrom_double(__ddiv_rn(static_cast<double>(N), Sd), V());
   if (c == 0 && threadIdx.x == 0) {  // read by the search kernel and the host-side callers
     store_v<V>(&A.g->S_raw, S);
     store_v<V>(&A.g->scale_raw, scale);
@@ -260,7 +273,7 @@ __device__ __forceinline__ void fused_body(const T* __restrict__ lw, const Fused
   typename Path<T, V>::U u_sys = typename Path<T, V>::U();
   Guide gd;
   if constexpr (SCHEME == RS_MULTINOMIAL) {
-    gd = make_guide(Sd, N);
+    gd = sh_gd;
   } else if constexpr (SCHEME == RS_SYSTEMATIC) {
     u_sys = cta_uniform0<T, V>(A.keys);
   }
@@ -282,7 +295,7 @@ template <typename T, typename V, int SCHEME>
 __global__ void __launch_bounds__(kBlock) fused_scan_kernel(const T* __restrict__ lw, FusedArgs A) {
   unsigned int target = 0;
   fused_body<T, V, SCHEME>(lw, A, target);
-  grid_exit(&A.g->bar_count, target);
+  grid_exit(&A.g->bar, target);
 }
 
 template <typename T, typename V, int SCHEME>

@@ -9,11 +9,10 @@
 #include <cuda_runtime.h>
 
 #include "common.cuh"
+#include "internal.h"
 
 namespace rsk {
 namespace {
-
-constexpr unsigned long long kBarrierTimeoutNs = 10ull * 1000 * 1000 * 1000;  // 10 s
 
 __device__ __forceinline__ unsigned long long global_ns() {
   unsigned long long t;
@@ -26,8 +25,11 @@ __device__ __forceinline__ unsigned long long global_ns() {
 // passed when the counter reaches k * gridDim.x. Thread 0 of each CTA arrives with a release
 // reduction and polls with acquire loads (the CTA's writes are ordered before the arrival by
 // the preceding __syncthreads, and every later read after the poll by the following one).
-// The wait is bounded: after kBarrierTimeoutNs it records RS_ERR_TIMEOUT and goes on.
-__device__ __forceinline__ void grid_barrier(unsigned int* count, unsigned int& target, int* err) {
+// The wait is bounded: after the handle's timeout (bar->timeout_ns, 10 s unless set by
+// rs_set_barrier_timeout) it records RS_ERR_TIMEOUT and goes on; rs_last_error, which reports
+// the status, then resets the counter.
+__device__ __forceinline__ void grid_barrier(GridBar* bar, unsigned int& target, int* err) {
+  unsigned int* count = &bar->count;
   target += gridDim.x;
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -36,11 +38,12 @@ __device__ __forceinline__ void grid_barrier(unsigned int* count, unsigned int& 
     asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(cur) : "l"(count) : "memory");
     if (static_cast<int>(cur - target) < 0) {
       const unsigned long long t0 = global_ns();
+      const unsigned long long limit = __ldcg(&bar->timeout_ns);
       for (;;) {
         __nanosleep(20);
         asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(cur) : "l"(count) : "memory");
         if (static_cast<int>(cur - target) >= 0) break;
-        if (global_ns() - t0 > kBarrierTimeoutNs) {
+        if (global_ns() - t0 > limit) {
           flag_error(err, RS_ERR_TIMEOUT);
           break;
         }
@@ -52,8 +55,9 @@ __device__ __forceinline__ void grid_barrier(unsigned int* count, unsigned int& 
 
 // Last act of every CTA: one more arrival; the CTA that completes it returns the counter to
 // 0 for the next launch (stream order makes the reset visible to it).
-__device__ __forceinline__ void grid_exit(unsigned int* count, unsigned int target) {
-  if (threadIdx.x == 0 && atomicAdd(count, 1u) == target + gridDim.x - 1) atomicExch(count, 0u);
+__device__ __forceinline__ void grid_exit(GridBar* bar, unsigned int target) {
+  if (threadIdx.x == 0 && atomicAdd(&bar->count, 1u) == target + gridDim.x - 1)
+    atomicExch(&bar->count, 0u);
 }
 
 // Largest co-resident grid of a kernel with kBlock threads (cached per kernel; identical

@@ -6,6 +6,15 @@
 
 namespace rsk {
 
+// Grid-barrier state of a handle's cooperative kernels: the arrival counter (0 between
+// launches) and the longest a barrier waits before it gives up with RS_ERR_TIMEOUT.
+struct GridBar {
+  unsigned int count;
+  unsigned int pad;
+  unsigned long long timeout_ns;
+};
+constexpr unsigned long long kDefaultBarrierTimeoutNs = 10ull * 1000 * 1000 * 1000;  // 10 s
+
 // Device-side state of the scan-based schemes (one per handle).
 struct ScanGlob {
   double M;                  // max log-weight of the current call
@@ -15,7 +24,7 @@ struct ScanGlob {
   unsigned int ticket_iscan;
   unsigned int batch_next;   // work counter of the batched kernel (self-resetting)
   unsigned int batch_ticket;
-  unsigned int bar_count;    // grid-barrier arrivals of the fused kernel (0 between launches)
+  GridBar bar;               // grid barrier of the cooperative kernels
   int all_zero;              // every weight of the call is zero (set with the total)
   float guide_step;          // W^N / N and N / W^N in binary32 (multinomial guide table),
   float guide_inv_step;      //   set with the total so that no later kernel divides
@@ -119,6 +128,13 @@ cudaError_t launch_rejection(const Scratch& s, bool f64, const void* logw, int64
                              double log_wmax, bool clamp, int64_t max_trials, uint64_t seed,
                              uint64_t step, uint32_t filter, int32_t* a_out,
                              int32_t* d_or_null, cudaStream_t st);
+// aux.cu: a cooperative launch whose grid barrier expects one arrival more than the grid
+// makes, so that every CTA's bounded wait runs out (RS_ERR_TIMEOUT) and the kernel ends.
+cudaError_t launch_barrier_timeout_probe(const Scratch& s, cudaStream_t st);
+// Self-checks of the acceptance tests (mode 0: binary32 band, every delta; mode 1: binary64
+// decisions on n log-weight pairs): the number of wrong decisions goes to *count.
+cudaError_t launch_check_acceptance(int mode, int64_t n, unsigned long long* count,
+                                    cudaStream_t st);
 cudaError_t launch_prc_weights(const Scratch& s, bool f64, const void* logw, const int32_t* c,
                                int64_t N, double log_vmax, void* out, cudaStream_t st);
 

@@ -26,7 +26,7 @@ template <typename T> constexpr int metropolis_min_ctas() { return sizeof(T) == 
 template <typename T, bool COOP>
 __global__ void __launch_bounds__(kBlock, metropolis_min_ctas<T>())
 metropolis_kernel(const T* __restrict__ lw, int64_t N, int32_t B, Keys keys,
-                  int32_t* __restrict__ a, int32_t* __restrict__ d, unsigned int* bar, int* err) {
+                  int32_t* __restrict__ a, int32_t* __restrict__ d, GridBar* bar, int* err) {
   pdl_wait();
   const int64_t t0 = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
   const int64_t stride = COOP ? static_cast<int64_t>(gridDim.x) * blockDim.x : N;
@@ -97,7 +97,7 @@ template <typename T, bool COOP>
 __global__ void __launch_bounds__(kBlock)
 rejection_kernel(const T* __restrict__ lw, int64_t N, double log_wmax, bool clamp,
                  int64_t max_trials, Keys keys, int32_t* __restrict__ a,
-                 int32_t* __restrict__ d, int64_t run_len, unsigned int* bar, int* err) {
+                 int32_t* __restrict__ d, int64_t run_len, GridBar* bar, int* err) {
   pdl_wait();
   unsigned int target = 0;
   if constexpr (COOP) {
@@ -139,6 +139,88 @@ prc_weights_kernel(const T* __restrict__ lw, const int32_t* __restrict__ c, int6
   out[i] = w > lvmax ? w - lvmax : T(0);
 }
 
+// ---------------------------------------------------------------------------------------
+// Self-checks of the acceptance tests (rs_check_acceptance): they run the device functions
+// the resamplers run and count the cases where a shortcut would decide differently from the
+// definition u < exp_pinned(delta).
+// ---------------------------------------------------------------------------------------
+__device__ __forceinline__ void count_add(unsigned long long* out, unsigned long long v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0 && v) atomicAdd(out, v);
+}
+
+// Every binary32 delta with bit pattern first + k (k < count): the binary32 test decides
+// from the band [RD(e (1 - 2^-15)), RU(e (1 + 2^-15))] around e = exp_band_estimate(delta),
+// which is right exactly when exp_pinned(delta) lies inside it.
+__global__ void __launch_bounds__(kBlock)
+check_band_f32_kernel(uint32_t first, uint32_t count, unsigned long long* out) {
+  unsigned long long bad = 0;
+  const uint32_t stride = gridDim.x * blockDim.x;
+  for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < count; k += stride) {
+    const float delta = __uint_as_float(first + k);
+    const float e = exp_band_estimate(delta);
+    const float lo = __fmul_rd(e, 1.0f - kExpBand), hi = __fmul_ru(e, 1.0f + kExpBand);
+    const float p = exp_pinned(delta);
+    if (!(lo <= p && p <= hi)) ++bad;
+  }
+  count_add(out, bad);
+}
+
+// The 53-bit uniform u = m 2^-53 as the Philox words it is drawn from (u01_f64).
+__device__ __forceinline__ uint4 words_of_u(uint64_t m) {
+  return make_uint4(static_cast<uint32_t>(m >> 21), static_cast<uint32_t>((m & 0x1fffffu) << 11),
+                    0u, 0u);
+}
+
+// Binary64 decisions on the binary32 pipes (f64_accept_lt) against the binary64 definition
+// u < exp_pinned(lwj - lwk), on n log-weight pairs: lwk from four magnitudes (0, -2.75,
+// -1234.5678, 30000.5: the last two push the filter to its exact fallback), lwj = lwk + d with
+// d spread over [-90, 0) (plus hashed low bits, so that many bit patterns occur), and per pair
+// uniforms on the 53-bit grid at and next to p = exp_pinned(lwj - lwk), next to p (1 +- 2^-20),
+// p (1 +- 2^-15) and p (1 +- 2^-10), and two hashed ones.
+__global__ void __launch_bounds__(kBlock)
+check_f64_decisions_kernel(int64_t n, unsigned long long* out) {
+  unsigned long long bad = 0;
+  const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+  const double base[4] = {0.0, -2.75, -1234.5678, 30000.5};
+  for (int64_t k = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; k < n;
+       k += stride) {
+    const uint64_t h = (static_cast<uint64_t>(k) + 1) * 0x9E3779B97F4A7C15ull;
+    const double lwk = base[k & 3];
+    const double frac = (static_cast<double>(k >> 2) + 0.5) / static_cast<double>(n / 4 + 1);
+    const double d = -90.0 * frac * (1.0 + static_cast<double>(h >> 40) * 0x1p-50);
+    const double lwj = __dadd_rn(lwk, d);
+    if (!(lwj < lwk)) continue;
+    const double p = exp_pinned(__dsub_rn(lwj, lwk));
+    float lwj_f, lwk_f;
+    const bool okj = f64_to_f32_trunc(lwj, lwj_f), okk = f64_to_f32_trunc(lwk, lwk_f);
+    const double mid = p * 0x1p53;
+    const double targets[9] = {mid, mid * (1.0 - 0x1p-20), mid * (1.0 + 0x1p-20),
+                               mid * (1.0 - 0x1p-15), mid * (1.0 + 0x1p-15),
+                               mid * (1.0 - 0x1p-10), mid * (1.0 + 0x1p-10),
+                               static_cast<double>(h >> 11),
+                               static_cast<double>((h * 0xBF58476D1CE4E5B9ull) >> 11)};
+#pragma unroll 1
+    for (int t = 0; t < 9; ++t) {
+      const double tm = targets[t];
+      if (!(tm < 0x1p53)) continue;
+      const uint64_t m0 = static_cast<uint64_t>(tm);
+#pragma unroll 1
+      for (int dm = -1; dm <= 1; ++dm) {
+        if (dm < 0 && m0 == 0) continue;
+        const uint64_t m = m0 + dm;
+        if (m >= (1ull << 53)) continue;
+        const uint4 x = words_of_u(m);
+        const bool got = f64_accept_lt(lwj, lwj_f, okj, lwk, lwk_f, okk, x);
+        const bool want = u01_f64(x) < p;
+        if (got != want) ++bad;
+      }
+    }
+  }
+  count_add(out, bad);
+}
+
 }  // namespace
 
 // d, when given, is first set to the sentinel N (the Prepermute initialisation): inside the
@@ -149,7 +231,7 @@ cudaError_t launch_metropolis_t(const Scratch& s, const T* lw, int64_t N, int32_
                                 cudaStream_t st) {
   // (The cooperative form, fill and chains in one launch, measured slower than a fill launch
   // followed by one thread per particle: the chains hide their gathers better in waves.)
-  unsigned int* bar = &s.glob->bar_count;
+  GridBar* bar = &s.glob->bar;
   if (d) {
     trace_mark(s.trace, "fill", st);
     const cudaError_t e = launch_fill(d, N, static_cast<int32_t>(N), st);
@@ -165,7 +247,7 @@ template <typename T>
 cudaError_t launch_rejection_t(const Scratch& s, const T* lw, int64_t N, double log_wmax,
                                bool clamp, int64_t max_trials, const Keys& keys, int32_t* a_out,
                                int32_t* d, bool f64, cudaStream_t st) {
-  unsigned int* bar = &s.glob->bar_count;
+  GridBar* bar = &s.glob->bar;
   const int64_t runs = (N + kRejRun - 1) / kRejRun;
   const int64_t want = (runs * 32 + kBlock - 1) / kBlock;
   if (s.coop && s.launch_mode != RS_LAUNCH_SEPARATE) {
@@ -227,6 +309,24 @@ cudaError_t launch_prc_weights(const Scratch& s, bool f64, const void* logw, con
   else  // the bound in binary32 as the binary32 attempts use it: RN(log v_max)
     launch_pdl(prc_weights_kernel<float>, grid, kBlock, st, static_cast<const float*>(logw), c,
                N, static_cast<float>(log_vmax), static_cast<float*>(out), s.err);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_check_acceptance(int mode, int64_t n, unsigned long long* count,
+                                    cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(count, 0, sizeof(unsigned long long), st);
+  if (e != cudaSuccess) return e;
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1)
+    sms = 1;
+  const int grid = sms * 8;
+  if (mode == 0) {  // every binary32 delta in [-86.5, 0): patterns 0x80000001 .. 0xc2ad0000
+    const uint32_t first = 0x80000001u, last = 0xc2ad0000u;
+    check_band_f32_kernel<<<grid, kBlock, 0, st>>>(first, last - first + 1, count);
+  } else {
+    check_f64_decisions_kernel<<<grid, kBlock, 0, st>>>(n, count);
+  }
   return cudaGetLastError();
 }
 

@@ -40,6 +40,8 @@ __global__ void noalloc_begin_kernel() {
   g->ticket_max = 0u;
   g->ticket_tile = 0u;
   g->ticket_iscan = 0u;
+  g->bar.count = 0u;
+  g->bar.timeout_ns = kDefaultBarrierTimeoutNs;
   *reinterpret_cast<int*>(g_noalloc_scratch + kOffErr) = kNoError;
 }
 
@@ -69,6 +71,19 @@ int scratch_for_current_device(unsigned char** out) {
   return RS_OK;
 }
 
+// A caller buffer must be device memory of the current device (or managed memory, which
+// every device reaches): a pointer into another GPU's memory or into pageable host memory
+// would make the kernels fault.
+bool usable_here(const void* p, int dev) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();  // the failed query leaves a (non-sticky) error: clear it
+    return false;
+  }
+  if (at.type == cudaMemoryTypeManaged) return true;
+  return at.type == cudaMemoryTypeDevice && at.device == dev;
+}
+
 }  // namespace
 }  // namespace rsk
 
@@ -80,6 +95,11 @@ extern "C" int rs_systematic_noalloc(int dtype, const void* logw_dev, int64_t N,
   if (dtype != RS_F32 && dtype != RS_F64) return RS_ERR_ARG;
   if (N < 1) return RS_ERR_ARG;
   if (N > kNoAllocMaxN) return RS_ERR_CAPACITY;
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess) return RS_ERR_CUDA;
+  if (!usable_here(logw_dev, dev) || !usable_here(ancestors_dev, dev) ||
+      (status_dev && !usable_here(status_dev, dev)))
+    return RS_ERR_ARG;
   unsigned char* base = nullptr;
   const int st = scratch_for_current_device(&base);
   if (st != RS_OK) return st;

@@ -82,5 +82,39 @@ __device__ __forceinline__ void permute_sorted_one(const int32_t* __restrict__ a
   }
 }
 
+// Up to four walks of Code 10 at once: walker q stands at slot x[q] with dx[q] = d[x[q]]
+// already loaded, and ends at the first unclaimed slot, where c receives val[q]. Each round
+// moves every live walker one step and then issues the loads of all live walkers together,
+// so up to four dependent chains are in flight per thread; the walks are disjoint (see
+// permute_one), so the writes are those of four separate walks.
+__device__ __forceinline__ void walk4(const int32_t* __restrict__ d, int32_t sentinel,
+                                      int32_t* __restrict__ c, int32_t (&x)[4],
+                                      int32_t (&dx)[4], const int32_t (&val)[4],
+                                      bool (&act)[4], int64_t n, int* err) {
+  const uint32_t us = static_cast<uint32_t>(sentinel);
+  bool bad = false;
+  for (uint32_t steps = 0; act[0] | act[1] | act[2] | act[3]; ++steps) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      if (!act[q]) continue;
+      const uint32_t v = static_cast<uint32_t>(dx[q]);
+      if (v >= us) {  // the sentinel (the walk ends here), or a corrupted d
+        if (v == us) c[x[q]] = val[q]; else bad = true;
+        act[q] = false;
+      } else {
+        x[q] = dx[q];
+      }
+    }
+    if (steps >= static_cast<uint32_t>(n)) {  // only a corrupted d can get here
+      bad = true;
+      break;
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+      if (act[q]) dx[q] = d[x[q]];
+  }
+  if (bad) flag_error(err, RS_ERR_ARG);
+}
+
 }  // namespace
 }  // namespace rsk

@@ -102,18 +102,32 @@ __device__ __forceinline__ void load4(const T* __restrict__ lw, int64_t idx, int
   }
 }
 
-// The kPer consecutive log-weights idx .. idx + kPer - 1 (two load4 halves).
+// The kPer consecutive log-weights idx .. idx + kPer - 1: 128-bit loads when all are inside
+// [lo, N) and the first is 16-byte aligned (one test for the eight), else guarded loads.
 template <typename T>
 __device__ __forceinline__ void load_per(const T* __restrict__ lw, int64_t idx, int64_t lo,
                                          int64_t N, bool vec, T (&x)[kPer]) {
-  static_assert(kPer == 8, "two halves of four");
-  T h[4];
-  load4(lw, idx, lo, N, vec, h);
+  static_assert(kPer == 8, "eight consecutive values");
+  constexpr int64_t kAlign = sizeof(T) == 4 ? 3 : 1;
+  if (vec && idx >= lo && idx + kPer <= N && (idx & kAlign) == 0) {
+    if constexpr (sizeof(T) == 4) {
+      const float4 v0 = __ldg(reinterpret_cast<const float4*>(lw + idx));
+      const float4 v1 = __ldg(reinterpret_cast<const float4*>(lw + idx + 4));
+      x[0] = v0.x; x[1] = v0.y; x[2] = v0.z; x[3] = v0.w;
+      x[4] = v1.x; x[5] = v1.y; x[6] = v1.z; x[7] = v1.w;
+    } else {
 #pragma unroll
-  for (int q = 0; q < 4; ++q) x[q] = h[q];
-  load4(lw, idx + 4, lo, N, vec, h);
+      for (int h = 0; h < 4; ++h) {
+        const double2 v = __ldg(reinterpret_cast<const double2*>(lw + idx + 2 * h));
+        x[2 * h] = v.x;
+        x[2 * h + 1] = v.y;
+      }
+    }
+  } else {
 #pragma unroll
-  for (int q = 0; q < 4; ++q) x[4 + q] = h[q];
+    for (int q = 0; q < kPer; ++q)
+      x[q] = (idx + q >= lo && idx + q < N) ? lw[idx + q] : neg_inf<T>();
+  }
 }
 
 template <typename V> __device__ __forceinline__ V load_v(const double2* p) {
@@ -151,6 +165,11 @@ __device__ __forceinline__ double tmin(double a, double b) { return fmin(a, b); 
 __device__ __forceinline__ float2 tmax(float2 a, float2 b) { return vmax(a, b); }
 __device__ __forceinline__ float2 tmin(float2 a, float2 b) { return vmin(a, b); }
 
+// Equality of two accumulator values (non-negative, never NaN here).
+__device__ __forceinline__ bool vsame(float a, float b) { return a == b; }
+__device__ __forceinline__ bool vsame(double a, double b) { return a == b; }
+__device__ __forceinline__ bool vsame(float2 a, float2 b) { return a.x == b.x && a.y == b.y; }
+
 // floor(x) as a 32-bit integer (x >= 0; values of 2^31 and above saturate, and every caller
 // clamps to n < 2^31 afterwards). floor of a two-float is floor(hi) unless hi is an integer.
 __device__ __forceinline__ int32_t floor_i32(float x) { return __float2int_rd(x); }
@@ -170,7 +189,7 @@ template <typename T, typename V, bool STRAT>
 __device__ __forceinline__ int32_t cum_offspring(V W, V S, V scale,
                                                  typename Path<T, V>::U u_sys,
                                                  const Keys& keys, int32_t n) {
-  if (veq(W, S)) return n;
+  if (vsame(W, S)) return n;
   const V r = vscale(W, scale);
   int32_t o;
   if constexpr (STRAT) {
@@ -463,10 +482,12 @@ __device__ __forceinline__ void tile_cum_weights(const T* __restrict__ lw, int64
 #pragma unroll
   for (int q = 0; q < kPer; ++q) W[q] = tmin(tmax(W[q], pm), Bn);
   if (lane == 31) W[kPer - 1] = Bn;
-  const int last = tile_count(base, N) - 1;
+  const int lq = tile_count(base, N) - 1 - kPer * tid;  // the tile's last valid particle here?
+  if (lq >= 0 && lq < kPer) {
 #pragma unroll
-  for (int q = 0; q < kPer; ++q)
-    if (kPer * tid + q == last) W[q] = Pn;
+    for (int q = 0; q < kPer; ++q)
+      if (q == lq) W[q] = Pn;
+  }
   Wb = vshfl_up(W[kPer - 1], 1);
   if (lane == 0) Wb = Bw;
 }

@@ -61,3 +61,25 @@ def test_noalloc_limits_and_status(rs):
     assert _noalloc(lib, good, 1, 0, out3, status) == rs.RS_OK
     torch.cuda.synchronize()
     assert status.item() == rs.RS_OK
+
+
+def test_noalloc_refuses_buffers_of_another_kind(rs):
+    """Pointers the kernels could not use -- pageable host memory, or (on a machine with more
+    than one GPU) memory of another device -- are refused with RS_ERR_ARG before any launch,
+    and the binding refuses tensors on the CPU or on another device than logw's."""
+    lib = rs.load()
+    t = torch.zeros(64, dtype=torch.float32, device="cuda")
+    out = torch.empty(64, dtype=torch.int32, device="cuda")
+    status = torch.zeros(1, dtype=torch.int32, device="cuda")
+    host = np.zeros(64, np.int32)
+    stream = C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    assert lib.rs_systematic_noalloc(0, C.c_void_p(t.data_ptr()), 64, 1, 0,
+                                     C.c_void_p(host.ctypes.data), C.c_void_p(status.data_ptr()),
+                                     stream) == rs.RS_ERR_ARG
+    with pytest.raises((TypeError, ValueError)):
+        rs.rs_systematic_noalloc(t, out=torch.empty(64, dtype=torch.int32))
+    with pytest.raises(TypeError):
+        rs.rs_systematic_noalloc(t.cpu())
+    a = rs.rs_systematic_noalloc(t, seed=1, out=out, status=status)
+    torch.cuda.synchronize()
+    assert status.item() == rs.RS_OK and a.cpu().tolist() == list(range(64))
