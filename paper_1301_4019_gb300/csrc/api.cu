@@ -120,7 +120,11 @@ int rs_create(rs_handle** out, int64_t max_n, int device) {
   std::memset(&s, 0, sizeof(s));
   s.max_n = max_n;
   s.max_tiles = (max_n + rsk::kTile - 1) / rsk::kTile;
-  s.max_blocks = 152 * 8;
+  int sms = 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess ||
+      sms < 1)
+    sms = 1;
+  s.max_blocks = sms * 8;  // grid of the max pass: 8 CTAs per SM of this device
   s.launch_mode = RS_LAUNCH_AUTO;
   for (int k = 0; k < rsk::kCfgCount; ++k) s.batch_cfg[k] = rsk::LaunchCfg{rsk::kBlock, 1};
   int coop = 0;

@@ -353,7 +353,8 @@ inline int grid_for(int64_t N) { return static_cast<int>((N + kBlock - 1) / kBlo
 cudaError_t launch_fill(int32_t* p, int64_t N, int32_t v, cudaStream_t st) {
   int64_t g = (N / 4 + kBlock - 1) / kBlock;
   if (g < 1) g = 1;
-  if (g > 152 * 16) g = 152 * 16;
+  const int64_t cap = static_cast<int64_t>(device_sm_count()) * 16;  // 16 CTAs per SM
+  if (g > cap) g = cap;
   launch_pdl(fill_kernel, static_cast<int>(g), kBlock, st, p, N, v);
   return cudaGetLastError();
 }
@@ -371,7 +372,9 @@ cudaError_t launch_prepermute(const Scratch& s, const int32_t* a, int64_t N, int
 }
 
 // Four slots per thread (permute4_kernel) from kPermute4MinN slots; below, one slot per
-// thread keeps more threads in flight.
+// thread keeps more threads in flight. (Handing the walks that outlast a few rounds to a tail
+// kernel through a queue measured 3x slower at 2^24: every queued walk takes an atomic on one
+// counter.)
 constexpr int64_t kPermute4MinN = int64_t{1} << 18;
 
 cudaError_t launch_permute(const Scratch& s, const int32_t* a, const int32_t* d, int64_t N,

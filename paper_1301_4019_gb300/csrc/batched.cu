@@ -13,6 +13,9 @@
 //   emit    : per tile, cumulative offspring + Code-11 scatter + claims, or stored W
 //   search / Metropolis / rejection / Permute: one thread per particle, its filter found by a
 //             binary search of the offsets.
+// With cooperative launches (the default), max, sums, prefixes and emission run as one
+// persistent launch over the tiles of all filters (batch_coop_kernel) after the plan, so a
+// scan-based scheme is plan + one launch (+ the search for the multinomial) + Permute.
 // Every unit runs the same device functions as the single-filter kernels on the same tile
 // structure (relative to the filter's first particle), with the filter index in the
 // random-number counter: filter f of a batched call equals rs_resample on that filter's slice
@@ -20,6 +23,7 @@
 #include <climits>
 
 #include "common.cuh"
+#include "grid.cuh"
 #include "internal.h"
 #include "mcmc.cuh"
 #include "permute.cuh"
@@ -278,6 +282,155 @@ batch_emit_kernel(const T* __restrict__ lw, Batch b, Keys base_keys,
   }
 }
 
+// ---------------------------------------------------------------------------------------
+// The max, sum, prefix and emission passes of all filters in one cooperative launch (after the
+// plan kernel): CTA c owns the contiguous batch tiles [c T / G, (c+1) T / G) of the T tiles of
+// all filters together, and the CTAs meet at two grid barriers:
+//   phase 1  per tile, the maximum log-weight, combined per filter by an atomic max of keys;
+//   phase 2  per tile, its record (tile_record) relative to its filter's maximum;
+//   phase 3  per tile, the exact sums of its filter's records (those before it, and all),
+//            rounded once to P_t, P_{t+1} and W^N as tile_prefix_compute rounds them, then the
+//            emission.
+// Every tile goes through the same device functions and rounded prefixes as in the separate
+// batched kernels and the single-filter kernels, so filter f still equals rs_resample on its
+// slice with filter = f, bit for bit.
+// ---------------------------------------------------------------------------------------
+template <typename T, typename V, int SCHEME>
+__global__ void __launch_bounds__(kBlock)
+batch_coop_kernel(const T* __restrict__ lw, Batch b, Keys base_keys, int32_t* __restrict__ a,
+                  int32_t* __restrict__ d, V* __restrict__ W, GridBar* bar) {
+  __shared__ TileSh<V> sh;
+  __shared__ float2 sh_tab[64];
+  __shared__ long long sh_key[kWarps];
+  __shared__ u128 sh_sum[2 * kWarps];
+  __shared__ double2 sh_Pt, sh_Pn, sh_S, sh_scale;
+  __shared__ double sh_Sd;
+  unsigned int target = 0;
+  const int T_tiles = __ldcg(b.tile_start + b.F);
+  const int G = static_cast<int>(gridDim.x), c = static_cast<int>(blockIdx.x);
+  const int t0 = static_cast<int>(static_cast<int64_t>(c) * T_tiles / G);
+  const int t1 = static_cast<int>(static_cast<int64_t>(c + 1) * T_tiles / G);
+  const bool vec = (reinterpret_cast<uintptr_t>(lw) & 15u) == 0;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+
+  // ---- phase 1: tile maxima -> filter maxima ------------------------------------------------
+  for (int t = t0; t < t1; ++t) {
+    TileLoc L;
+    if (!locate_tile(b, t, L) || !resampled(b.resample, L.f)) continue;  // uniform per CTA
+    const int64_t end = min(L.hi, L.base + kTile);
+    long long m = key_of(neg_inf<T>());
+    bool bad = false;
+    T x[kPer];
+    load_per(lw, L.base + kPer * static_cast<int64_t>(threadIdx.x), L.lo, end, vec, x);
+#pragma unroll
+    for (int q = 0; q < kPer; ++q) {
+      const bool nan = is_nan(x[q]);
+      bad |= nan || is_pos_inf(x[q]);
+      const long long k = key_of(x[q]);
+      if (!nan && k > m) m = k;
+    }
+    if (bad) flag_error(b.err, RS_ERR_NONFINITE);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const long long y = __shfl_xor_sync(0xffffffffu, m, o);
+      m = y > m ? y : m;
+    }
+    __syncthreads();
+    if (lane == 0) sh_key[warp] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      long long bm = sh_key[0];
+      for (int k = 1; k < kWarps; ++k) bm = sh_key[k] > bm ? sh_key[k] : bm;
+      atomicMax(b.fmax + L.f, key_of(value_of(bm, T())));
+    }
+  }
+  grid_barrier(bar, target, b.err);
+
+  // ---- phase 2: tile records ------------------------------------------------------------------
+  for (int t = t0; t < t1; ++t) {
+    TileLoc L;
+    if (!locate_tile(b, t, L) || !resampled(b.resample, L.f)) continue;
+    const double M = filter_M(b, L.f);
+    if (M > -DBL_MAX) {
+      const WeightCtx wc = make_ctx<T, V>(M, sh_tab);
+      tile_record<T, V>(lw, L.lo, L.hi, L.base, wc, vec, b.s_rec + t, sh);
+    } else if (threadIdx.x == 0) {
+      store_v<V>(b.s_rec + t, vzero(V()));
+    }
+  }
+  grid_barrier(bar, target, b.err);
+
+  // ---- phase 3: prefixes of each tile from its filter's exact record sums, emission ---------
+  for (int t = t0; t < t1; ++t) {
+    TileLoc L;
+    if (!locate_tile(b, t, L)) continue;
+    const int64_t n = L.hi - L.lo;
+    const double M = filter_M(b, L.f);
+    const bool active = resampled(b.resample, L.f) && M > -DBL_MAX;
+    if (resampled(b.resample, L.f) && !(M > -DBL_MAX) && L.t == 0 && threadIdx.x == 0) {
+      b.fSd[L.f] = 0.0;
+      flag_error(b.err, RS_ERR_ZERO_WEIGHT);
+    }
+    double Sd = 0.0;
+    V Pt = vzero(V()), Pn = vzero(V()), S = vzero(V()), scale = vzero(V());
+    if (active) {
+      const int first = __ldg(b.tile_start + L.f);
+      const int nt = __ldg(b.tile_start + L.f + 1) - first;
+      u128 part = 0, tot = 0;
+      for (int k = threadIdx.x; k < nt; k += kBlock) {
+        const u128 v = rec_fixed<V>(b.s_rec + first + k);
+        tot += v;
+        if (k < L.t) part += v;
+      }
+      block_sum2_u128(part, tot, sh_sum);
+      if (threadIdx.x == 0) {
+        const V S0 = fixed_to(tot, V(), kFixFrac);
+        const double Sd0 = vto_double(S0);
+        const V sc0 = vfrom_double(__ddiv_rn(static_cast<double>(n), Sd0), V());
+        store_v<V>(&sh_Pt, fixed_to(part, V(), kFixFrac));
+        store_v<V>(&sh_Pn, fixed_to(part + rec_fixed<V>(b.s_rec + t), V(), kFixFrac));
+        store_v<V>(&sh_S, S0);
+        store_v<V>(&sh_scale, sc0);
+        sh_Sd = Sd0;
+        if (L.t == 0) {  // the filter's totals, for the search kernel
+          store_v<V>(b.fS + L.f, S0);
+          store_v<V>(b.fscale + L.f, sc0);
+          b.fSd[L.f] = Sd0;
+        }
+      }
+      __syncthreads();
+      Pt = load_v<V>(&sh_Pt);
+      Pn = load_v<V>(&sh_Pn);
+      S = load_v<V>(&sh_S);
+      scale = load_v<V>(&sh_scale);
+      Sd = sh_Sd;
+      __syncthreads();  // the shared values are rewritten by the next tile
+    }
+    if (!active || !(Sd > 0.0)) {  // all weights zero (flagged) or not resampled: identity
+      for (int64_t e = L.base + threadIdx.x; e < L.hi && e < L.base + kTile; e += kBlock) {
+        a[e] = static_cast<int32_t>(e - L.lo);
+        if (d) d[e] = static_cast<int32_t>(e - L.lo);
+        if (W) W[e] = vzero(V());
+      }
+      continue;
+    }
+    const WeightCtx wc = make_ctx<T, V>(M, sh_tab);
+    if constexpr (SCHEME == RS_MULTINOMIAL) {
+      if (d)  // claims of the search kernel start from the sentinel n
+        for (int64_t e = L.base + threadIdx.x; e < L.hi && e < L.base + kTile; e += kBlock)
+          d[e] = static_cast<int32_t>(n);
+      emit_tile_W<T, V, V>(lw, L.lo, L.hi, L.base, wc, vec, Pt, Pn, W, sh);
+    } else {
+      const Keys keys = with_tag(base_keys, static_cast<uint32_t>(L.f), SCHEME);
+      const typename Path<T, V>::U u_sys =
+          SCHEME == RS_STRATIFIED ? typename Path<T, V>::U() : cta_uniform0<T, V>(keys);
+      emit_tile_cumoff<T, V, SCHEME == RS_STRATIFIED>(lw, L.lo, L.hi, L.base, wc, vec, Pt, Pn,
+                                                       S, scale, u_sys, keys, a, d, sh);
+    }
+  }
+  grid_exit(bar, target);
+}
+
 template <typename T, typename V>
 __global__ void __launch_bounds__(kBlock)
 batch_search_kernel(const V* __restrict__ W, Batch b, int64_t total, Keys base_keys,
@@ -447,12 +600,54 @@ const char* const kLblEmit[4] = {"batch_emit_f32", "batch_emit_f32c", "batch_emi
 const char* const kLblSearch[4] = {"batch_search_f32", "batch_search_f32c", "batch_search_f64",
                                    "batch_search_f64n"};
 
+const char* const kLblCoop[4] = {"batch_coop_f32", "batch_coop_f32c", "batch_coop_f64",
+                                 "batch_coop_f64n"};
+
+// The cooperative form of the batched scan passes (batch_coop_kernel), sized to the resident
+// grid; false when the device cannot run it (then the separate kernels run).
+template <typename T, typename V, int SCHEME>
+bool launch_batched_coop(const Scratch& s, const T* lw, const Batch& b, int64_t cap_tiles,
+                         const Keys& keys, int32_t* a, int32_t* d, V* W, cudaStream_t st,
+                         cudaError_t& e) {
+  const int cap = coop_capacity(reinterpret_cast<const void*>(batch_coop_kernel<T, V, SCHEME>));
+  if (cap < 1) return false;
+  const int grid = static_cast<int64_t>(cap) < cap_tiles ? cap : static_cast<int>(cap_tiles);
+  trace_mark(s.trace, kLblCoop[Path<T, V>::id], st);
+  e = coop_launch(batch_coop_kernel<T, V, SCHEME>, grid, st, lw, b, keys, a, d, W, &s.glob->bar);
+  return true;
+}
+
 template <typename T, typename V>
 cudaError_t run_batched_scan(const Scratch& s, int scheme, const T* lw, const Batch& b,
                              int64_t cap_tiles, const Keys& keys, int32_t* a, int32_t* d,
                              cudaStream_t st) {
   constexpr int ai = Path<T, V>::id;
   const int tiles = static_cast<int>(cap_tiles);
+  if (s.coop && s.launch_mode != RS_LAUNCH_SEPARATE) {
+    cudaError_t e = cudaSuccess;
+    V* Wc = static_cast<V*>(s.W);
+    bool done;
+    switch (scheme) {
+      case RS_MULTINOMIAL:
+        done = launch_batched_coop<T, V, RS_MULTINOMIAL>(s, lw, b, cap_tiles, keys, a, d, Wc, st, e);
+        if (done && e == cudaSuccess) {
+          trace_mark(s.trace, kLblSearch[ai], st);
+          launch_pdl(batch_search_kernel<T, V>, grid_particles(s.max_n), kBlock, st, Wc, b,
+                     s.max_n, keys, a, d);
+          e = cudaGetLastError();
+        }
+        break;
+      case RS_STRATIFIED:
+        done = launch_batched_coop<T, V, RS_STRATIFIED>(s, lw, b, cap_tiles, keys, a, d, nullptr,
+                                                        st, e);
+        break;
+      default:
+        done = launch_batched_coop<T, V, RS_SYSTEMATIC>(s, lw, b, cap_tiles, keys, a, d, nullptr,
+                                                        st, e);
+        break;
+    }
+    if (done) return e;
+  }
   trace_mark(s.trace, "batch_max", st);
   launch_pdl(batch_max_kernel<T>, tiles, kBlock, st, lw, b);
   trace_mark(s.trace, kLblSum[ai], st);

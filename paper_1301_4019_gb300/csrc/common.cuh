@@ -158,6 +158,21 @@ inline bool& pdl_disabled() {
   return off;
 }
 
+// Streaming multiprocessors of the current device (queried once per device).
+inline int device_sm_count() {
+  static int cache[64] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 1;
+  if (cache[dev] < 1) {
+    int sms = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        sms < 1)
+      return 1;
+    cache[dev] = sms;
+  }
+  return cache[dev];
+}
+
 template <typename... KArgs, typename... Args>
 inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, cudaStream_t st,
                               Args&&... args) {

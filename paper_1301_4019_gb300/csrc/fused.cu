@@ -73,16 +73,18 @@ struct FusedArgs {
 
 // Maximum log-weight and NaN / +inf detection of x[0..3] (exact comparisons: binary32
 // values directly, binary64 values through their order-preserving keys on the integer pipe).
-__device__ __forceinline__ void max_step(const float (&x)[4], long long& m, float& mf, bool& bad) {
+template <int K>
+__device__ __forceinline__ void max_step(const float (&x)[K], long long& m, float& mf, bool& bad) {
 #pragma unroll
-  for (int q = 0; q < 4; ++q) {
+  for (int q = 0; q < K; ++q) {
     bad |= !(x[q] <= FLT_MAX);  // NaN or +inf (-inf and finite values pass)
     mf = fmaxf(mf, x[q]);       // fmaxf skips NaN
   }
 }
-__device__ __forceinline__ void max_step(const double (&x)[4], long long& m, float&, bool& bad) {
+template <int K>
+__device__ __forceinline__ void max_step(const double (&x)[K], long long& m, float&, bool& bad) {
 #pragma unroll
-  for (int q = 0; q < 4; ++q) {
+  for (int q = 0; q < K; ++q) {
     const bool nan = is_nan(x[q]);
     bad |= nan || is_pos_inf(x[q]);
     const long long k = fkey(x[q]);
@@ -90,39 +92,21 @@ __device__ __forceinline__ void max_step(const double (&x)[4], long long& m, flo
   }
 }
 
-// Block-wide sums of two u128 values (every thread gets both).
-__device__ __forceinline__ void block_sum2_u128(u128& a, u128& b, u128* sh) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    a += shfl_xor_u128(a, o);
-    b += shfl_xor_u128(b, o);
-  }
-  __syncthreads();
-  if (lane == 0) {
-    sh[warp] = a;
-    sh[kWarps + warp] = b;
-  }
-  __syncthreads();
-  a = 0;
-  b = 0;
-#pragma unroll
-  for (int k = 0; k < kWarps; ++k) {
-    a += sh[k];
-    b += sh[kWarps + k];
-  }
-}
+// Tiles per CTA up to which the record pass runs in reverse order (its records in shared
+// memory: 16 bytes each).
+constexpr int kZigTiles = 512;
 
 // CTA c owns the contiguous tiles [c T / G, (c+1) T / G) of the T tiles (G = gridDim.x <= T):
 //   phase 1  maximum over its particles -> barrier -> M = maximum over the CTAs;
-//   phase 2  tile totals s_t of its tiles, in order, and their exact running sum in fixed
-//            point (the in-range prefix of each tile, and the CTA total) -> barrier;
+//   phase 2  tile totals s_t of its tiles (last to first, see below) and their exact running
+//            sum in fixed point (the in-range prefix of each tile, and the CTA total) -> barrier;
 //   phase 3  every CTA sums the exact CTA totals: those before it (CP) and all (the total);
 //            P_t = RN(CP + in-range prefix of t) for its tiles and P_{t1} = RN(CP + its own
 //            total), which is the P_{t1} the next CTA computes; W^N = RN(total), N / W^N;
 //   phase 4  emission of its tiles.
 // P_t is the exact sum of the tile totals before t rounded once, as in tile_prefix_compute, so
 // the results equal those of the separate kernels. Two grid barriers per call.
+
 template <typename T, typename V, int SCHEME>
 __device__ __forceinline__ void fused_body(const T* __restrict__ lw, const FusedArgs& A,
                                            unsigned int& target) {
@@ -144,20 +128,22 @@ __device__ __forceinline__ void fused_body(const T* __restrict__ lw, const Fused
     long long m = fkey(neg_inf<T>());
     float mf = -INFINITY;
     bool bad = false;
-    for (int64_t i0 = e0 + 4 * static_cast<int64_t>(threadIdx.x); i0 < e1; i0 += 4 * kBlock) {
-      T x[4];
-      load4(lw, i0, 0, e1, vec, x);
+    // two groups of kPer in flight per thread and iteration
+    for (int64_t i0 = e0 + kPer * static_cast<int64_t>(threadIdx.x); i0 < e1;
+         i0 += 2 * kPer * kBlock) {
+      const int64_t i1 = i0 + kPer * kBlock;
+      T x[kPer], y[kPer];
+      load_per(lw, i0, 0, e1, vec, x);
+      load_per(lw, i1, 0, e1, vec, y);  // (past e1: -inf)
       max_step(x, m, mf, bad);
+      max_step(y, m, mf, bad);
       if constexpr (SCHEME == RS_MULTINOMIAL) {
         if (A.d) {
-          int32_t* p = A.d + i0;
-          if (i0 + 4 <= e1 && (reinterpret_cast<uintptr_t>(p) & 15u) == 0) {
-            const int32_t s = static_cast<int32_t>(N);
-            *reinterpret_cast<int4*>(p) = make_int4(s, s, s, s);
-          } else {
-            for (int q = 0; q < 4; ++q)
-              if (i0 + q < e1) p[q] = static_cast<int32_t>(N);
-          }
+          int32_t sv[kPer];
+#pragma unroll
+          for (int q = 0; q < kPer; ++q) sv[q] = static_cast<int32_t>(N);
+          store_per(A.d + i0, sv, e1 - i0 < kPer ? static_cast<int>(e1 - i0) : kPer);
+          if (i1 < e1) store_per(A.d + i1, sv, e1 - i1 < kPer ? static_cast<int>(e1 - i1) : kPer);
         }
       }
     }
@@ -180,18 +166,38 @@ __device__ __forceinline__ void fused_body(const T* __restrict__ lw, const Fused
   u128* LP = reinterpret_cast<u128*>(A.P_rec);  // in-range exact prefixes, then rounded P_t
 
   // ---- phase 2: tile totals and their exact running sum ---------------------------------
+  // The tiles are visited last to first here and first to last in the other passes, so that
+  // each pass starts on the tiles the previous one touched last (still in L2 when the log-
+  // weights exceed half of it); the records wait in shared memory for the in-order sums.
   const WeightCtx wc = make_ctx<T, V>(zero ? 0.0 : M, sh_tab);
   if (!zero) {
-    u128 run = 0;  // meaningful in thread 0
-    for (int t = t0; t < t1; ++t) {
-      const int64_t base = static_cast<int64_t>(t) * kTile;
-      const u128 f = tile_record<T, V>(lw, 0, N, base, wc, vec, A.s_rec + t, sh);
-      if (threadIdx.x == 0) {
-        st_u128(LP + t, run);
-        run += f;
+    if (t1 - t0 <= kZigTiles) {
+      __shared__ u128 sh_f[kZigTiles];
+      for (int t = t1 - 1; t >= t0; --t) {
+        const int64_t base = static_cast<int64_t>(t) * kTile;
+        const u128 f = tile_record<T, V>(lw, 0, N, base, wc, vec, A.s_rec + t, sh);
+        if (threadIdx.x == 0) sh_f[t - t0] = f;
       }
+      if (threadIdx.x == 0) {
+        u128 run = 0;
+        for (int t = t0; t < t1; ++t) {
+          st_u128(LP + t, run);
+          run += sh_f[t - t0];
+        }
+        st_u128(A.agg + c, run);
+      }
+    } else {
+      u128 run = 0;  // meaningful in thread 0
+      for (int t = t0; t < t1; ++t) {
+        const int64_t base = static_cast<int64_t>(t) * kTile;
+        const u128 f = tile_record<T, V>(lw, 0, N, base, wc, vec, A.s_rec + t, sh);
+        if (threadIdx.x == 0) {
+          st_u128(LP + t, run);
+          run += f;
+        }
+      }
+      if (threadIdx.x == 0) st_u128(A.agg + c, run);
     }
-    if (threadIdx.x == 0) st_u128(A.agg + c, run);
   }
   grid_barrier(&A.g->bar, target, A.err);
 

@@ -23,10 +23,13 @@ template <typename T> constexpr int metropolis_min_ctas() { return sizeof(T) == 
 // One thread per particle. COOP: a persistent cooperative grid that first sets the claims to
 // the sentinel N (the Prepermute initialisation), meets at a grid barrier, then runs the
 // chains over a grid-stride loop -- one launch instead of a fill and the chains.
+// Binary64 log-weights come with their sidecars lwf (f64_sidecar; sidecar_kernel), which the
+// chains gather instead of the binary64 values.
 template <typename T, bool COOP>
 __global__ void __launch_bounds__(kBlock, metropolis_min_ctas<T>())
-metropolis_kernel(const T* __restrict__ lw, int64_t N, int32_t B, Keys keys,
-                  int32_t* __restrict__ a, int32_t* __restrict__ d, GridBar* bar, int* err) {
+metropolis_kernel(const T* __restrict__ lw, const float* __restrict__ lwf, int64_t N, int32_t B,
+                  Keys keys, int32_t* __restrict__ a, int32_t* __restrict__ d, GridBar* bar,
+                  int* err) {
   pdl_wait();
   const int64_t t0 = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
   const int64_t stride = COOP ? static_cast<int64_t>(gridDim.x) * blockDim.x : N;
@@ -37,7 +40,9 @@ metropolis_kernel(const T* __restrict__ lw, int64_t N, int32_t B, Keys keys,
     grid_barrier(bar, target, err);
   }
   for (int64_t i = t0; i < N; i += stride) {
-    const int32_t k = metropolis_one(lw, N, B, keys, i, err);
+    int32_t k;
+    if constexpr (sizeof(T) == 8) k = metropolis_one_sc(lw, lwf, N, B, keys, i, err);
+    else k = metropolis_one(lw, N, B, keys, i, err);
     a[i] = k;
     if (d) atomicMin(d + k, static_cast<int32_t>(i));
   }
@@ -46,8 +51,9 @@ metropolis_kernel(const T* __restrict__ lw, int64_t N, int32_t B, Keys keys,
 
 // Rejection with warp refill (mcmc.cuh) over the particles [start, end) of one warp run.
 template <typename T>
-__device__ __forceinline__ void rejection_run(const T* __restrict__ lw, int64_t N, int64_t start,
-                                              int64_t end, const RejBound& rb,
+__device__ __forceinline__ void rejection_run(const T* __restrict__ lw,
+                                              const float* __restrict__ lwf, int64_t N,
+                                              int64_t start, int64_t end, const RejBound& rb,
                                               int64_t max_trials, const Keys& keys,
                                               int32_t* __restrict__ a, int32_t* __restrict__ d,
                                               int* err) {
@@ -62,8 +68,13 @@ __device__ __forceinline__ void rejection_run(const T* __restrict__ lw, int64_t 
     bool settled = false;
     if (active) {
       int64_t j;
-      settled = rejection_attempts<kRejBatch>(lw, N, rb, keys, i, static_cast<uint32_t>(s),
-                                              lwi, max_trials, j, err);
+      if constexpr (sizeof(T) == 8)
+        settled = rejection_attempts_sc<kRejBatch>(lw, lwf, N, rb, keys, i,
+                                                   static_cast<uint32_t>(s), f64_sidecar(lwi),
+                                                   max_trials, j, err);
+      else
+        settled = rejection_attempts<kRejBatch>(lw, N, rb, keys, i, static_cast<uint32_t>(s),
+                                                lwi, max_trials, j, err);
       s += kRejBatch;
       if (!settled && s >= static_cast<uint64_t>(max_trials)) {
         flag_error(err, RS_ERR_REJECTION_CAP);
@@ -93,19 +104,23 @@ __device__ __forceinline__ void rejection_run(const T* __restrict__ lw, int64_t 
 // Warp w takes the runs w, w + W, ... of run_len particles (W = warps of the grid). The host
 // sizes run_len so that every warp gets exactly one run (a warp that took an extra run
 // would set the kernel's length).
+// Binary64 log-weights come with their sidecars lwf, written by the cooperative grid before
+// its barrier, else beforehand by sidecar_kernel.
 template <typename T, bool COOP>
 __global__ void __launch_bounds__(kBlock)
-rejection_kernel(const T* __restrict__ lw, int64_t N, double log_wmax, bool clamp,
-                 int64_t max_trials, Keys keys, int32_t* __restrict__ a,
+rejection_kernel(const T* __restrict__ lw, float* __restrict__ lwf, int64_t N, double log_wmax,
+                 bool clamp, int64_t max_trials, Keys keys, int32_t* __restrict__ a,
                  int32_t* __restrict__ d, int64_t run_len, GridBar* bar, int* err) {
   pdl_wait();
   unsigned int target = 0;
   if constexpr (COOP) {
-    if (d) {
+    if (d || sizeof(T) == 8) {
       const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
       for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < N;
-           i += stride)
-        d[i] = static_cast<int32_t>(N);
+           i += stride) {
+        if (d) d[i] = static_cast<int32_t>(N);
+        if constexpr (sizeof(T) == 8) lwf[i] = f64_sidecar(__ldg(lw + i));
+      }
     }
     grid_barrier(bar, target, err);
   }
@@ -115,7 +130,7 @@ rejection_kernel(const T* __restrict__ lw, int64_t N, double log_wmax, bool clam
        run * run_len < N; run += warps) {  // uniform across the warp
     const int64_t start = run * run_len;
     const int64_t end = start + run_len < N ? start + run_len : N;
-    rejection_run(lw, N, start, end, rb, max_trials, keys, a, d, err);
+    rejection_run(lw, lwf, N, start, end, rb, max_trials, keys, a, d, err);
   }
   if constexpr (COOP) grid_exit(bar, target);
 }
@@ -137,6 +152,35 @@ prc_weights_kernel(const T* __restrict__ lw, const int32_t* __restrict__ c, int6
   }
   const T w = __ldg(lw + ci);
   out[i] = w > lvmax ? w - lvmax : T(0);
+}
+
+// Sidecars of binary64 log-weights (f64_sidecar) and, when d is given, the claims d = N (the
+// Prepermute initialisation): one pass that replaces the fill of the claims.
+__global__ void __launch_bounds__(kBlock)
+sidecar_kernel(const double* __restrict__ lw, int64_t N, float* __restrict__ lwf,
+               int32_t* __restrict__ d) {
+  pdl_wait();
+  const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x * 4;
+  const bool vec = ((reinterpret_cast<uintptr_t>(lw) | reinterpret_cast<uintptr_t>(lwf) |
+                     reinterpret_cast<uintptr_t>(d)) & 15u) == 0;
+  for (int64_t i = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) * 4; i < N;
+       i += stride) {
+    if (vec && i + 4 <= N) {  // 128-bit loads and stores
+      const double2 u = __ldg(reinterpret_cast<const double2*>(lw + i));
+      const double2 v = __ldg(reinterpret_cast<const double2*>(lw + i + 2));
+      *reinterpret_cast<float4*>(lwf + i) =
+          make_float4(f64_sidecar(u.x), f64_sidecar(u.y), f64_sidecar(v.x), f64_sidecar(v.y));
+      if (d) {
+        const int32_t n = static_cast<int32_t>(N);
+        *reinterpret_cast<int4*>(d + i) = make_int4(n, n, n, n);
+      }
+    } else {
+      for (int64_t k = i; k < i + 4 && k < N; ++k) {
+        lwf[k] = f64_sidecar(__ldg(lw + k));
+        if (d) d[k] = static_cast<int32_t>(N);
+      }
+    }
+  }
 }
 
 // ---------------------------------------------------------------------------------------
@@ -223,6 +267,14 @@ check_f64_decisions_kernel(int64_t n, unsigned long long* out) {
 
 }  // namespace
 
+// Grid of the sidecar pass: up to 16 CTAs per SM over a grid-stride loop, four particles per
+// thread.
+inline int side_grid(int64_t N) {
+  const int64_t want = (N + 4 * kBlock - 1) / (4 * kBlock);
+  const int64_t cap = static_cast<int64_t>(device_sm_count()) * 16;
+  return static_cast<int>(want < cap ? want : cap);
+}
+
 // d, when given, is first set to the sentinel N (the Prepermute initialisation): inside the
 // cooperative rejection kernel when the device allows it, else by a fill launch.
 template <typename T>
@@ -232,14 +284,21 @@ cudaError_t launch_metropolis_t(const Scratch& s, const T* lw, int64_t N, int32_
   // (The cooperative form, fill and chains in one launch, measured slower than a fill launch
   // followed by one thread per particle: the chains hide their gathers better in waves.)
   GridBar* bar = &s.glob->bar;
-  if (d) {
+  float* lwf = static_cast<float*>(s.W);  // the sidecars of binary64 log-weights (4 B each)
+  if (sizeof(T) == 8) {
+    trace_mark(s.trace, "sidecar", st);
+    launch_pdl(sidecar_kernel, side_grid(N), kBlock, st, reinterpret_cast<const double*>(lw), N,
+               lwf, d);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  } else if (d) {
     trace_mark(s.trace, "fill", st);
     const cudaError_t e = launch_fill(d, N, static_cast<int32_t>(N), st);
     if (e != cudaSuccess) return e;
   }
   trace_mark(s.trace, f64 ? "metropolis_f64" : "metropolis_f32", st);
   launch_pdl(metropolis_kernel<T, false>, static_cast<int>((N + kBlock - 1) / kBlock), kBlock,
-             st, lw, N, B, keys, a_out, d, bar, s.err);
+             st, lw, lwf, N, B, keys, a_out, d, bar, s.err);
   return cudaGetLastError();
 }
 
@@ -248,6 +307,7 @@ cudaError_t launch_rejection_t(const Scratch& s, const T* lw, int64_t N, double 
                                bool clamp, int64_t max_trials, const Keys& keys, int32_t* a_out,
                                int32_t* d, bool f64, cudaStream_t st) {
   GridBar* bar = &s.glob->bar;
+  float* lwf = static_cast<float*>(s.W);  // the sidecars of binary64 log-weights (4 B each)
   const int64_t runs = (N + kRejRun - 1) / kRejRun;
   const int64_t want = (runs * 32 + kBlock - 1) / kBlock;
   if (s.coop && s.launch_mode != RS_LAUNCH_SEPARATE) {
@@ -261,18 +321,25 @@ cudaError_t launch_rejection_t(const Scratch& s, const T* lw, int64_t N, double 
       int64_t run_len = (N + warps - 1) / warps;
       run_len = run_len > kRejRun ? run_len : kRejRun;
       trace_mark(s.trace, f64 ? "rejection_f64" : "rejection_f32", st);
-      return coop_launch(rejection_kernel<T, true>, grid, st, lw, N, log_wmax, clamp,
+      return coop_launch(rejection_kernel<T, true>, grid, st, lw, lwf, N, log_wmax, clamp,
                          max_trials, keys, a_out, d, run_len, bar, s.err);
     }
   }
-  if (d) {
+  if (sizeof(T) == 8) {
+    trace_mark(s.trace, "sidecar", st);
+    launch_pdl(sidecar_kernel, side_grid(N), kBlock, st, reinterpret_cast<const double*>(lw), N,
+               lwf, d);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  } else if (d) {
     trace_mark(s.trace, "fill", st);
     const cudaError_t e = launch_fill(d, N, static_cast<int32_t>(N), st);
     if (e != cudaSuccess) return e;
   }
   trace_mark(s.trace, f64 ? "rejection_f64" : "rejection_f32", st);
-  launch_pdl(rejection_kernel<T, false>, static_cast<int>(want), kBlock, st, lw, N, log_wmax,
-             clamp, max_trials, keys, a_out, d, static_cast<int64_t>(kRejRun), bar, s.err);
+  launch_pdl(rejection_kernel<T, false>, static_cast<int>(want), kBlock, st, lw, lwf, N,
+             log_wmax, clamp, max_trials, keys, a_out, d, static_cast<int64_t>(kRejRun), bar,
+             s.err);
   return cudaGetLastError();
 }
 

@@ -93,20 +93,22 @@ __device__ __noinline__ bool exact_f64_less_exp(double lwj, double lwk, uint4 x)
   return u01_f64(x) < exp_pinned(__dsub_rn(lwj, lwk));
 }
 
-__device__ __forceinline__ bool f64_accept_lt(double lwj, float lwj_f, bool okj, double lwk,
-                                              float lwk_f, bool okk, uint4 x) {
-  if (!(okj && okk)) return exact_f64_less_exp(lwj, lwk, x);
+// The filter of f64_accept_lt on usable truncations lwj_f, lwk_f: true / false where they
+// decide, else exact() -- the binary64 test, which the caller evaluates only then (so its
+// binary64 log-weights are read only then).
+template <typename Exact>
+__device__ __forceinline__ bool f64_filter_lt(float lwj_f, float lwk_f, uint4 x, const Exact& exact) {
   const float df = __fsub_rn(lwj_f, lwk_f);  // <= 0 up to rounding
   // bound on |df - (lwj - lwk)|: both truncations, the subtraction's rounding, margin
   const float E = __fmaf_ru(fabsf(lwj_f) + fabsf(lwk_f), 0x1p-23f,
                             __fmaf_ru(fabsf(df), 0x1p-24f, 0x1p-124f));
-  if (!(E < 0.01f)) return exact_f64_less_exp(lwj, lwk, x);
+  if (!(E < 0.01f)) return exact();
   // u lies in [x0 2^-32, (x0 + 1) 2^-32)
   const float u_lo = __fmul_rn(__uint2float_rd(x.x), 0x1p-32f);
   const float u_hi = __fmul_rn(__fadd_ru(__uint2float_ru(x.x), 1.0f), 0x1p-32f);
   if (!(df >= -86.5f)) {  // exp(df) < 2^-124: the binary64 ratio is below e^-86 < 2^-32 <= u
     if (x.x != 0u) return false;
-    return exact_f64_less_exp(lwj, lwk, x);
+    return exact();
   }
   // ef = exp(df) within a relative 1e-5 (exp_band_estimate); exp(lwj - lwk) within
   // ef * exp(+-E) * (1 +- 1e-5) (1 +- 2^-52): m bounds all of it
@@ -116,7 +118,27 @@ __device__ __forceinline__ bool f64_accept_lt(double lwj, float lwj_f, bool okj,
   const float hi = __fmul_ru(ef, __fadd_ru(1.0f, m));
   if (u_hi < lo) return true;
   if (u_lo >= hi) return false;
-  return exact_f64_less_exp(lwj, lwk, x);
+  return exact();
+}
+
+__device__ __forceinline__ bool f64_accept_lt(double lwj, float lwj_f, bool okj, double lwk,
+                                              float lwk_f, bool okk, uint4 x) {
+  if (!(okj && okk)) return exact_f64_less_exp(lwj, lwk, x);
+  return f64_filter_lt(lwj_f, lwk_f, x, [&] { return exact_f64_less_exp(lwj, lwk, x); });
+}
+
+// ---------------------------------------------------------------------------------------
+// Binary32 sidecar of binary64 log-weights. The binary64 chains gather a 4-byte sidecar per
+// proposal instead of the 8-byte log-weight: the truncation of lw_j to binary32 when usable,
+// -inf for lw_j = -inf, a NaN otherwise (NaN, +inf, or beyond the binary32 range). Truncation
+// is monotone, so t_j > t_k implies lw_j > lw_k and t_j < t_k implies lw_j < lw_k; the
+// binary64 values are read only when the sidecars are equal or NaN, and for the exact
+// fallback of the filter. Every decision equals the one taken from the binary64 values.
+// ---------------------------------------------------------------------------------------
+__device__ __forceinline__ float f64_sidecar(double x) {
+  float f;
+  if (f64_to_f32_trunc(x, f)) return f;
+  return is_neg_inf(x) ? -INFINITY : __int_as_float(0x7fffffff);
 }
 
 constexpr int kUnroll = 4;    // binary32 chains: proposals issued together
@@ -219,6 +241,66 @@ __device__ __forceinline__ int32_t metropolis_one(const double* __restrict__ lw,
       lwk_f = lwj_f;
       okk = okj;
       kk = kj;
+    }
+  }
+  return static_cast<int32_t>(k);
+}
+
+// A Metropolis step of a binary64 chain decided from sidecars (f64_sidecar): state k with
+// sidecar tk, proposal j with tj; the binary64 log-weights lw[k], lw[j] are read only when the
+// sidecars cannot decide. Same decision as f64_step_accept on the binary64 values.
+__device__ __forceinline__ bool sc_step_accept(const double* __restrict__ lw, int64_t k, float tk,
+                                               int64_t j, float tj, uint4 x) {
+  if (tk == -INFINITY) return true;              // zero-weight state (tk = -inf iff lw_k = -inf)
+  if (!(tj == tj) || !(tk == tk) || tj == tk) {  // undecided by the truncations
+    const double lwk = __ldg(lw + k), lwj = __ldg(lw + j);
+    float fk, fj;
+    const bool okk = f64_to_f32_trunc(lwk, fk), okj = f64_to_f32_trunc(lwj, fj);
+    return f64_step_accept(lwk, fk, okk, f64_key(lwk), lwj, fj, okj, f64_key(lwj), x);
+  }
+  if (tj > tk) return true;                      // lw_j > lw_k: ratio above 1
+  if (tj == -INFINITY) return false;             // zero-weight proposal
+  return f64_filter_lt(tj, tk, x,
+                       [&] { return exact_f64_less_exp(__ldg(lw + j), __ldg(lw + k), x); });
+}
+
+// metropolis_one for binary64 log-weights with their sidecars lwf: the proposals gather
+// 4 bytes (lwf[j]) instead of 8; same ancestor as metropolis_one.
+__device__ __forceinline__ int32_t metropolis_one_sc(const double* __restrict__ lw,
+                                                     const float* __restrict__ lwf, int64_t n,
+                                                     int32_t B, const Keys& keys, int64_t i,
+                                                     int* err) {
+  const double lwi = __ldg(lw + i);
+  if (nonfinite_logw(lwi)) flag_error(err, RS_ERR_NONFINITE);
+  int64_t k = i;
+  float tk = f64_sidecar(lwi);
+  const uint32_t ii = static_cast<uint32_t>(i);
+  int32_t s = 0;
+  for (; s + kUnroll64 <= B; s += kUnroll64) {
+    uint4 x[kUnroll64];
+    int64_t j[kUnroll64];
+    float tj[kUnroll64];
+#pragma unroll
+    for (int q = 0; q < kUnroll64; ++q) {
+      x[q] = draw(keys, ii, static_cast<uint32_t>(s + q));
+      j[q] = uniform_index(x[q], n);
+      tj[q] = __ldg(lwf + j[q]);
+    }
+#pragma unroll
+    for (int q = 0; q < kUnroll64; ++q) {
+      if (sc_step_accept(lw, k, tk, j[q], tj[q], x[q])) {
+        k = j[q];
+        tk = tj[q];
+      }
+    }
+  }
+  for (; s < B; ++s) {
+    const uint4 x = draw(keys, ii, static_cast<uint32_t>(s));
+    const int64_t j = uniform_index(x, n);
+    const float tj = __ldg(lwf + j);
+    if (sc_step_accept(lw, k, tk, j, tj, x)) {
+      k = j;
+      tk = tj;
     }
   }
   return static_cast<int32_t>(k);
@@ -340,6 +422,21 @@ __device__ __forceinline__ bool rejection_accept(const RejBound& rb, uint4 x, do
   return f64_accept_lt(lwj, lwj_f, okj, rb.lwmax, rb.lwmax_f, rb.okm, x);
 }
 
+// rejection_accept for a binary64 proposal decided from its sidecar tj (f64_sidecar); the
+// binary64 log-weight lw[j] is read only when the sidecar cannot decide. Same decision.
+__device__ __forceinline__ bool rejection_accept_sc(const RejBound& rb, uint4 x,
+                                                    const double* __restrict__ lw, int64_t j,
+                                                    float tj, int* err) {
+  if (!(tj == tj) || !rb.okm || tj == rb.lwmax_f) return rejection_accept(rb, x, __ldg(lw + j), err);
+  if (tj > rb.lwmax_f) {  // lw_j above the bound
+    if (!rb.clamp) flag_error(err, RS_ERR_BOUND_VIOLATED);
+    return true;
+  }
+  if (tj == -INFINITY) return false;
+  return f64_filter_lt(tj, rb.lwmax_f, x,
+                       [&] { return exact_f64_less_exp(__ldg(lw + j), rb.lwmax, x); });
+}
+
 // Attempts a lane issues together (rejection_attempts): 2 measured 7-16 % faster than 1 at
 // N = 2^20 (y = 2 and 4); 4 is faster still at y = 4 but slower at y = 2, where most particles
 // settle within two attempts.
@@ -368,6 +465,35 @@ __device__ __forceinline__ bool rejection_attempts(const T* __restrict__ lw, int
   for (int q = 0; q < K; ++q) {
     if (static_cast<int64_t>(s) + q >= max_trials) return false;
     if (rejection_accept(rb, x[q], lwj[q], err)) {
+      j = jq[q];
+      return true;
+    }
+  }
+  return false;
+}
+
+// rejection_attempts for binary64 log-weights with their sidecars lwf (ti: the sidecar of
+// particle i's own log-weight): the proposals gather 4 bytes instead of 8; same outcome.
+template <int K>
+__device__ __forceinline__ bool rejection_attempts_sc(const double* __restrict__ lw,
+                                                      const float* __restrict__ lwf, int64_t n,
+                                                      const RejBound& rb, const Keys& keys,
+                                                      int64_t i, uint32_t s, float ti,
+                                                      int64_t max_trials, int64_t& j, int* err) {
+  uint4 x[K];
+  int64_t jq[K];
+  float tj[K];
+#pragma unroll
+  for (int q = 0; q < K; ++q) {
+    const uint32_t sq = s + static_cast<uint32_t>(q);
+    x[q] = draw(keys, static_cast<uint32_t>(i), sq);
+    jq[q] = (sq > 0) ? uniform_index(x[q], n) : i;
+    tj[q] = (sq > 0) ? __ldg(lwf + jq[q]) : ti;
+  }
+#pragma unroll
+  for (int q = 0; q < K; ++q) {
+    if (static_cast<int64_t>(s) + q >= max_trials) return false;
+    if (rejection_accept_sc(rb, x[q], lw, jq[q], tj[q], err)) {
       j = jq[q];
       return true;
     }

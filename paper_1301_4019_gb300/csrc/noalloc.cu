@@ -19,7 +19,9 @@ namespace {
 
 constexpr int64_t kNoAllocMaxN = RS_NOALLOC_MAX_N;
 constexpr int64_t kNoAllocMaxTiles = (kNoAllocMaxN + kTile - 1) / kTile;
-constexpr int kNoAllocMaxBlocks = 152 * 8;
+// Entries for the per-CTA maxima: the max pass runs 8 CTAs per SM, capped here (devices of
+// up to 256 SMs get the full grid).
+constexpr int kNoAllocMaxBlocks = 256 * 8;
 
 // Layout of the static scratch (offsets in bytes, each 256-byte aligned).
 constexpr size_t align256(size_t x) { return (x + 255) & ~static_cast<size_t>(255); }
@@ -111,7 +113,8 @@ extern "C" int rs_systematic_noalloc(int dtype, const void* logw_dev, int64_t N,
   s.rec = reinterpret_cast<double2*>(base + kOffRec);
   s.max_n = kNoAllocMaxN;
   s.max_tiles = kNoAllocMaxTiles;
-  s.max_blocks = kNoAllocMaxBlocks;
+  s.max_blocks = device_sm_count() * 8 < kNoAllocMaxBlocks ? device_sm_count() * 8
+                                                            : kNoAllocMaxBlocks;
   const cudaStream_t cs = static_cast<cudaStream_t>(stream);
   launch_pdl(noalloc_begin_kernel, 1, 1, cs);
   cudaError_t e = cudaGetLastError();

@@ -321,6 +321,29 @@ __device__ __forceinline__ u128 block_sum_u128(u128 v, u128* sh) {
   return t;
 }
 
+// Block-wide sums of two u128 values (every thread gets both).
+__device__ __forceinline__ void block_sum2_u128(u128& a, u128& b, u128* sh) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    a += shfl_xor_u128(a, o);
+    b += shfl_xor_u128(b, o);
+  }
+  __syncthreads();
+  if (lane == 0) {
+    sh[warp] = a;
+    sh[kWarps + warp] = b;
+  }
+  __syncthreads();
+  a = 0;
+  b = 0;
+#pragma unroll
+  for (int k = 0; k < kWarps; ++k) {
+    a += sh[k];
+    b += sh[kWarps + k];
+  }
+}
+
 // A tile's record: its total in the accumulator type; rec_fixed returns it in fixed point.
 template <typename V> __device__ __forceinline__ u128 rec_fixed(const double2* p) {
   return to_fixed(load_v_cg<V>(p));
@@ -389,9 +412,70 @@ __device__ void tile_prefix_compute(const double2* s_rec, double2* P_rec, int nt
 }
 
 // Shared scratch of the block-level tile functions.
+constexpr int kRunWin = 32 * kPer;  // output positions a warp writes per round of warp_runs
+
 template <typename V> struct TileSh {
   V tot[kWarps];
+  alignas(16) int32_t win[kWarps][kRunWin];  // warp_runs windows
 };
+
+// Code 11 for the particles of one warp: out[j] = the index of the particle whose run
+// [O_{i-1}, O_i) holds j, for every j of the warp's range [P0, P1) (P0 = the count before the
+// warp's first particle, P1 = after its last). Lane l holds the non-decreasing counts Oe[q] of
+// its kPer particles i0 + q and `prev`, the count before them. The range is written in
+// rounds of kRunWin positions through the warp's shared window: -1 everywhere, the first
+// position of each run receives its particle's index, a running maximum (in-lane, then a
+// max-scan over the lanes, then the last value of the previous round, which every lane takes
+// into account: a run can cover a whole round) fills the runs, and the window is stored with
+// consecutive lanes on consecutive positions. The first position P0 always starts a run, so
+// the carry of the first round can be -1. Same result as writing out[j] = i for j in
+// [O_{i-1}, O_i) particle by particle, without its divergent loops.
+__device__ __forceinline__ void warp_runs(const int32_t (&Oe)[kPer], int32_t prev, int32_t i0,
+                                          int32_t* __restrict__ out, int32_t* win) {
+  const int lane = threadIdx.x & 31;
+  const int32_t P0 = __shfl_sync(0xffffffffu, prev, 0);
+  const int32_t P1 = __shfl_sync(0xffffffffu, Oe[kPer - 1], 31);
+  int4* const w4 = reinterpret_cast<int4*>(win);
+  int32_t carry = -1;
+  for (int32_t base = P0; base < P1; base += kRunWin) {  // warp-uniform
+    __syncwarp();
+    w4[2 * lane] = make_int4(-1, -1, -1, -1);
+    w4[2 * lane + 1] = make_int4(-1, -1, -1, -1);
+    __syncwarp();
+    int32_t p = prev;
+#pragma unroll
+    for (int q = 0; q < kPer; ++q) {
+      const int32_t pos = p - base;
+      if (Oe[q] > p && pos >= 0 && pos < kRunWin) win[pos] = i0 + q;
+      p = Oe[q];
+    }
+    __syncwarp();
+    const int4 u0 = w4[2 * lane], u1 = w4[2 * lane + 1];
+    int32_t v[kPer] = {u0.x, u0.y, u0.z, u0.w, u1.x, u1.y, u1.z, u1.w};
+#pragma unroll
+    for (int k = 1; k < kPer; ++k) v[k] = max(v[k], v[k - 1]);
+    int32_t m = v[kPer - 1];
+#pragma unroll
+    for (int dd = 1; dd < 32; dd <<= 1) {
+      const int32_t y = __shfl_up_sync(0xffffffffu, m, dd);
+      if (lane >= dd) m = max(m, y);
+    }
+    int32_t em = __shfl_up_sync(0xffffffffu, m, 1);  // the earlier lanes of this round
+    em = lane == 0 ? carry : max(em, carry);          // and the run carried into the round
+#pragma unroll
+    for (int k = 0; k < kPer; ++k) v[k] = max(v[k], em);
+    carry = __shfl_sync(0xffffffffu, v[kPer - 1], 31);
+    __syncwarp();
+    w4[2 * lane] = make_int4(v[0], v[1], v[2], v[3]);
+    w4[2 * lane + 1] = make_int4(v[4], v[5], v[6], v[7]);
+    __syncwarp();
+#pragma unroll
+    for (int k = 0; k < kPer; ++k) {
+      const int32_t j = base + 32 * k + lane;
+      if (j < P1) out[j] = win[32 * k + lane];
+    }
+  }
+}
 
 // The tile's total (its record), stored by thread 0 at rec and returned in thread 0 as fixed
 // point (0 in the other threads). A plain block reduction: sequential over a thread's kPer
@@ -535,22 +619,26 @@ __device__ __forceinline__ void emit_tile_cumoff(const T* __restrict__ lw, int64
   const int32_t i0 = static_cast<int32_t>(base - lo) + kPer * static_cast<int32_t>(threadIdx.x);
   V W[kPer], Wb;
   tile_cum_weights<T, V>(lw, lo, N, base, wc, vec, Pt, Pn, W, Wb, sh);
+  // O of this thread's particles; the last particle of the sequence gets n, and positions
+  // past the end repeat the count before them (no offspring). A thread with a position past
+  // the end holds the sequence's last particle or none, so its last count is n either way.
   int32_t O[kPer];
 #pragma unroll
   for (int q = 0; q < kPer; ++q) O[q] = cum_offspring<T, V, STRAT>(W[q], S, scale, u_sys, keys, n);
-  int32_t prev = __shfl_up_sync(0xffffffffu, O[kPer - 1], 1);
-  if (lane == 0) prev = cum_offspring<T, V, STRAT>(Wb, S, scale, u_sys, keys, n);
-  int32_t* const al = a + lo;
+  const int32_t last = (cnt >= kPer && i0 + kPer - 1 != n - 1) ? O[kPer - 1] : n;
+  int32_t prev = __shfl_up_sync(0xffffffffu, last, 1);
+  if (lane == 0)  // (a warp wholly past the end follows the sequence's last particle: n)
+    prev = cnt > 0 ? cum_offspring<T, V, STRAT>(Wb, S, scale, u_sys, keys, n) : n;
   int32_t dv[kPer];
+  int32_t p = prev;
 #pragma unroll
   for (int q = 0; q < kPer; ++q) {
-    const int32_t i = i0 + q;
-    const int32_t Oc = (i == n - 1) ? n : O[q];
-    if (q < cnt)
-      for (int32_t j = prev; j < Oc; ++j) al[j] = i;
-    dv[q] = (Oc > prev) ? prev : n;
-    prev = Oc;
+    const int32_t Oc = (q >= cnt) ? p : ((i0 + q == n - 1) ? n : O[q]);
+    dv[q] = (Oc > p) ? p : n;
+    O[q] = Oc;
+    p = Oc;
   }
+  warp_runs(O, prev, i0, a + lo, sh.win[threadIdx.x >> 5]);
   if (d && cnt > 0) store_per(d + lo + i0, dv, cnt);
 }
 
@@ -666,19 +754,21 @@ __device__ __forceinline__ void emit_tile_W_guide(const T* __restrict__ lw, int6
     if (q < cnt) p[q] = W[q];
     C[q] = static_cast<int32_t>(guide_count<V>(W[q], gd, n));
   }
-  int32_t prev = __shfl_up_sync(0xffffffffu, C[kPer - 1], 1);
-  if (lane == 0) prev = static_cast<int32_t>(guide_count<V>(Wb, gd, n));
-  int32_t* const Gl = G + lo;
+  // the guide entries of a particle's buckets form runs like the ancestors of Code 11 (the
+  // last particle's run ends at n, positions past the end add none)
+  const int32_t last = (cnt >= kPer && j0 + kPer - 1 != n - 1) ? C[kPer - 1] : n;
+  int32_t prev = __shfl_up_sync(0xffffffffu, last, 1);
+  if (lane == 0) prev = cnt > 0 ? static_cast<int32_t>(guide_count<V>(Wb, gd, n)) : n;
+  int32_t pc = prev;
 #pragma unroll
   for (int q = 0; q < kPer; ++q) {
-    const int32_t j = j0 + q;
-    const int32_t Cc = (j == n - 1) ? n : C[q];
-    if (q < cnt) {
-      for (int32_t b = prev; b < Cc; ++b) Gl[b] = j;
-      if (j == n - 1) Gl[n] = n - 1;
-    }
-    prev = Cc;
+    const int32_t Cc = (q >= cnt) ? pc : ((j0 + q == n - 1) ? n : C[q]);
+    C[q] = Cc;
+    pc = Cc;
   }
+  int32_t* const Gl = G + lo;
+  warp_runs(C, prev, j0, Gl, sh.win[threadIdx.x >> 5]);
+  if (j0 <= n - 1 && n - 1 < j0 + kPer) Gl[n] = n - 1;
 }
 
 // Loads of W and G; kCoherent: written earlier in the same kernel launch, read through L2.

@@ -224,3 +224,34 @@ def test_metropolis_B_per_filter_from_the_weights(rs, h, dtype):
     assert st == oracle.OK and np.array_equal(a[offsets[2]:offsets[3]], want)
     with pytest.raises(rs.RsError):
         rs.rs_metropolis_B_batched(h, t, off, eps=1.0)
+
+
+@pytest.mark.parametrize("dtype,prec", MODES)
+def test_batched_cooperative_equals_separate_kernels(rs, h, dtype, prec):
+    """The one-launch cooperative form of the batched scan passes and the one-kernel-per-pass
+    form give the same ancestors and statuses, including an all-zero filter (flagged, identity)
+    and filters that the mask leaves untouched."""
+    sizes = [4097, 1, 2048, 2049, 0, 9000, 777, 30000, 5]
+    offsets, lw = _batch(sizes, dtype, seed=11)
+    lw[offsets[6]:offsets[7]] = -np.inf  # filter 6: every weight zero
+    t = torch.from_numpy(lw).to(DEV)
+    off = torch.from_numpy(offsets).to(DEV)
+    flags = torch.tensor([1, 1, 0, 1, 1, 1, 1, 0, 1], dtype=torch.uint8, device=DEV)
+    for scheme in (rs.MULTINOMIAL, rs.STRATIFIED, rs.SYSTEMATIC):
+        for permute in (False, True):
+            got = []
+            for mode in (rs.LAUNCH_AUTO, rs.LAUNCH_SEPARATE):
+                rs.rs_set_launch_mode(h, mode)
+                a = rs.rs_resample_batched(h, scheme, t, off, seed=3, step=2, permute=permute,
+                                           prec=prec).cpu().numpy()
+                st = rs.rs_last_error(h)
+                a2 = rs.rs_resample_batched(h, scheme, t, off, seed=3, step=2, resample=flags,
+                                            permute=permute, prec=prec).cpu().numpy()
+                st2 = rs.rs_last_error(h)
+                got.append((a, st, a2, st2))
+            rs.rs_set_launch_mode(h, rs.LAUNCH_AUTO)
+            (a, st, a2, st2), (b, sb, b2, sb2) = got
+            assert st == sb == rs.RS_ERR_ZERO_WEIGHT and st2 == sb2 == rs.RS_ERR_ZERO_WEIGHT
+            assert np.array_equal(a, b) and np.array_equal(a2, b2), (scheme, permute)
+            lo, hi = offsets[6], offsets[7]
+            assert np.array_equal(np.sort(a[lo:hi]), np.arange(hi - lo))
