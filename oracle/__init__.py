@@ -34,6 +34,7 @@ ERR_BOUND_VIOLATED = -4
 ERR_REJECTION_CAP = -5
 
 MULTINOMIAL, STRATIFIED, SYSTEMATIC, METROPOLIS, REJECTION = range(5)
+BOUND_ESTIMATE = 5  # draw purpose of the estimated rejection bound
 
 
 def build(force: bool = False) -> str:
@@ -85,6 +86,8 @@ def _declare(lib):
         "orc_prc_f32": (C.c_int, [_P, _I64, C.c_double, _I64, _U64, _U64, _U32, _P, _P]),
         "orc_prc_f64": (C.c_int, [_P, _I64, C.c_double, _I64, _U64, _U64, _U32, _P, _P]),
         "orc_prc_weights_f32": (C.c_int, [_P, _P, _I64, C.c_double, _P]),
+        "orc_estimate_log_wmax_f32": (C.c_double, [_P, _I64, _I64, _U64, _U64, _U32]),
+        "orc_estimate_log_wmax_f64": (C.c_double, [_P, _I64, _I64, _U64, _U64, _U32]),
         "orc_prc_weights_f64": (C.c_int, [_P, _P, _I64, C.c_double, _P]),
         "orc_weights_f32": (C.c_int, [_P, _I64, _P, _P]),
         "orc_weights_f64": (C.c_int, [_P, _I64, _P, _P]),
@@ -204,6 +207,33 @@ def rejection(lw: np.ndarray, log_wmax: float, seed: int, step: int = 0, filter_
                                                      max_trials, seed, step, filter_,
                                                      _ptr(a), _ptr(t))
     return (st, a, t) if with_trials else (st, a)
+
+
+def estimate_log_wmax(lw: np.ndarray, sample: int, seed: int, step: int = 0,
+                      filter_: int = 0) -> float:
+    """Substitute bound of the rejection resampler (Section 2.2): the largest of `sample`
+    log-weights at uniformly drawn indices (NaN passed over; -inf if none is finite)."""
+    lw = np.ascontiguousarray(lw)
+    return getattr(_load(), "orc_estimate_log_wmax_" + _sfx(lw))(_ptr(lw), len(lw), sample,
+                                                                  seed, step, filter_)
+
+
+def rejection_estimated(lw: np.ndarray, sample: int, seed: int, step: int = 0,
+                        filter_: int = 0, max_trials: int = 1 << 20, permuted: bool = False):
+    """Rejection resampling with the estimated bound (Section 2.2): v_max = estimate_log_wmax,
+    partial rejection control with that bound, and the count of log-weights above it (its
+    violations). Returns (status, a, lw_out, log_wmax, violations); with no finite drawn
+    log-weight the status is ERR_ZERO_WEIGHT and a is the identity."""
+    lw = np.ascontiguousarray(lw)
+    est = estimate_log_wmax(lw, sample, seed, step, filter_)
+    N = len(lw)
+    if not np.isfinite(est):
+        return ERR_ZERO_WEIGHT, np.arange(N, dtype=np.int32), np.zeros_like(lw), est, 0
+    st, a, out = partial_rejection_control(lw, est, seed, step, filter_, max_trials,
+                                           permuted=permuted)
+    lwc = lw.astype(np.float32) if lw.dtype == np.float32 else lw
+    viol = int(np.sum(lwc > (np.float32(est) if lw.dtype == np.float32 else est)))
+    return st, a, out, est, viol
 
 
 def partial_rejection_control(lw: np.ndarray, log_vmax: float, seed: int, step: int = 0,

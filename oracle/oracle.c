@@ -35,6 +35,7 @@
 #define ORC_SYSTEMATIC 2u
 #define ORC_METROPOLIS 3u
 #define ORC_REJECTION 4u
+#define ORC_BOUND_ESTIMATE 5u
 
 /* ------------------------------------------------------------------------------------ */
 /* Counter-based random numbers                                                           */
@@ -386,6 +387,36 @@ int orc_prc_f64(const double* lw, int64_t N, double log_vmax, int64_t max_trials
         if (trials) trials[i] = n;
     }
     return status;
+}
+
+/* A substitute bound for the rejection resampler when no hard bound on the weights is known
+ * (Section 2.2: "some reasonable substitute can be made"; the empirical maximum would be a
+ * collective over all weights): the largest of `sample` log-weights at indices drawn
+ * uniformly, the k-th index from counter (k, 0) with purpose ORC_BOUND_ESTIMATE. NaN
+ * log-weights are passed over; the result is -inf when every drawn log-weight is -inf or NaN.
+ * Partial rejection control with v_max = this bound then gives a weighted outcome
+ * (orc_prc_*, orc_prc_weights_*); the weights above it are its violations. */
+double orc_estimate_log_wmax_f32(const float* lw, int64_t N, int64_t sample, uint64_t seed,
+                                 uint64_t step, uint32_t filter) {
+    double m = -INFINITY;
+    for (int64_t k = 0; k < sample; ++k) {
+        uint32_t x[4];
+        orc_draw(seed, (uint32_t)k, 0u, step, filter, ORC_BOUND_ESTIMATE, x);
+        float v = lw[orc_uniform_index(x, N)];
+        if (v == v && (double)v > m) m = (double)v;
+    }
+    return m;
+}
+double orc_estimate_log_wmax_f64(const double* lw, int64_t N, int64_t sample, uint64_t seed,
+                                 uint64_t step, uint32_t filter) {
+    double m = -INFINITY;
+    for (int64_t k = 0; k < sample; ++k) {
+        uint32_t x[4];
+        orc_draw(seed, (uint32_t)k, 0u, step, filter, ORC_BOUND_ESTIMATE, x);
+        double v = lw[orc_uniform_index(x, N)];
+        if (v == v && v > m) m = v;
+    }
+    return m;
 }
 
 /* The log-weights of the outcome of partial rejection control for a delivered ancestry c
