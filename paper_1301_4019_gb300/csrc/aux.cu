@@ -60,14 +60,15 @@ permute_sorted_kernel(const int32_t* __restrict__ a, const int32_t* __restrict__
 
 // Permute of a non-decreasing ancestry (permute_sorted_one) with four consecutive slots per
 // thread: the slot loads of a and d are 128-bit, and the walks of failed claims run together
-// (walk4), up to four dependent chains in flight per thread. The reads and writes of each
-// slot are those of permute_sorted_one, so c is the same.
+// (walk4_warp: up to four dependent chains in flight per thread, then the rare long walks
+// compacted across the warp). The reads and writes of each slot are those of
+// permute_sorted_one, so c is the same.
 __global__ void __launch_bounds__(kBlock)
 permute_sorted4_kernel(const int32_t* __restrict__ a, const int32_t* __restrict__ d, int64_t N,
                        int32_t* __restrict__ c, int* err) {
   pdl_wait();
   const int64_t i0 = 4 * (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x);
-  if (i0 >= N) return;
+  // (no early exit: the walks are finished warp-wide; threads past N have no slots)
   const int32_t sentinel = static_cast<int32_t>(N);
   int32_t A[4], D[4];
   const bool vec = i0 + 3 < N &&
@@ -84,7 +85,7 @@ permute_sorted4_kernel(const int32_t* __restrict__ a, const int32_t* __restrict_
       D[q] = i0 + q < N ? d[i0 + q] : sentinel;
     }
   }
-  int32_t prev = i0 > 0 ? a[i0 - 1] : -1;
+  int32_t prev = (i0 > 0 && i0 - 1 < N) ? a[i0 - 1] : -1;
   bool ok[4], fail[4];
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
@@ -102,18 +103,19 @@ permute_sorted4_kernel(const int32_t* __restrict__ a, const int32_t* __restrict_
   int32_t x[4];
 #pragma unroll
   for (int q = 0; q < 4; ++q) x[q] = static_cast<int32_t>(i0 + q);
-  walk4(d, sentinel, c, x, D, A, fail, N, err);
+  __shared__ int2 pend[kBlock / 32][128];
+  walk4_warp(d, sentinel, c, x, D, A, fail, N, pend[threadIdx.x >> 5], err);
 }
 
 // Permute of any ancestry (permute_one) with four consecutive slots per thread: 128-bit slot
 // loads, the four claim checks d[a_i] issued together, and the walks of failed claims run
-// together (walk4). Same reads and writes per slot as permute_one, so c is the same.
+// together (walk4_warp). Same reads and writes per slot as permute_one, so c is the same.
 __global__ void __launch_bounds__(kBlock)
 permute4_kernel(const int32_t* __restrict__ a, const int32_t* __restrict__ d, int64_t N,
                 int32_t* __restrict__ c, int* err) {
   pdl_wait();
   const int64_t i0 = 4 * (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x);
-  if (i0 >= N) return;
+  // (no early exit: the walks are finished warp-wide; threads past N have no slots)
   const int32_t sentinel = static_cast<int32_t>(N);
   int32_t A[4], D[4];
   const bool vec = i0 + 3 < N &&
@@ -152,7 +154,8 @@ permute4_kernel(const int32_t* __restrict__ a, const int32_t* __restrict__ d, in
     fail[q] = ok[q] && claim[q] != static_cast<int32_t>(i0 + q);
     x[q] = static_cast<int32_t>(i0 + q);
   }
-  walk4(d, sentinel, c, x, D, A, fail, N, err);
+  __shared__ int2 pend[kBlock / 32][128];
+  walk4_warp(d, sentinel, c, x, D, A, fail, N, pend[threadIdx.x >> 5], err);
 }
 
 // Ancestors-to-Offspring (Code 12).

@@ -116,5 +116,75 @@ __device__ __forceinline__ void walk4(const int32_t* __restrict__ d, int32_t sen
   if (bad) flag_error(err, RS_ERR_ARG);
 }
 
+// Walks of the four-slot kernels in two stages, for a whole warp: first every lane moves its
+// (up to) four walkers for at most kWalkRounds rounds (walk4's loop), which ends most walks;
+// then the walks still going are compacted into the warp's shared list `pend` (128 entries:
+// slot reached and value) and finished one walk per lane, 32 at a time. A warp otherwise
+// runs as many four-walker rounds as its longest walk takes, with most lanes predicated off.
+// Every walk still moves through the same slots and ends at the same unclaimed slot, so c is
+// the same as with walk4.
+constexpr uint32_t kWalkRounds = 2;
+
+__device__ __forceinline__ void walk4_warp(const int32_t* __restrict__ d, int32_t sentinel,
+                                           int32_t* __restrict__ c, int32_t (&x)[4],
+                                           int32_t (&dx)[4], const int32_t (&val)[4],
+                                           bool (&act)[4], int64_t n, int2* pend, int* err) {
+  const uint32_t us = static_cast<uint32_t>(sentinel);
+  const int lane = threadIdx.x & 31;
+  bool bad = false;
+  for (uint32_t r = 0; r < kWalkRounds && (act[0] | act[1] | act[2] | act[3]); ++r) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      if (!act[q]) continue;
+      const uint32_t v = static_cast<uint32_t>(dx[q]);
+      if (v >= us) {  // the sentinel (the walk ends here), or a corrupted d
+        if (v == us) c[x[q]] = val[q]; else bad = true;
+        act[q] = false;
+      } else {
+        x[q] = dx[q];
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+      if (act[q]) dx[q] = d[x[q]];
+  }
+  // compaction of the walks still going (each at slot x with d[x] loaded as dx)
+  const int mine = static_cast<int>(act[0]) + act[1] + act[2] + act[3];
+  int incl = mine;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += y;
+  }
+  const int total = __shfl_sync(0xffffffffu, incl, 31);
+  if (total > 0) {
+    int pos = incl - mine;
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+      if (act[q]) pend[pos++] = make_int2(x[q], val[q]);
+    __syncwarp();
+    for (int b = 0; b < total; b += 32) {
+      if (b + lane < total) {
+        const int2 e = pend[b + lane];
+        int32_t xs = e.x;
+        for (int64_t steps = 0;; ++steps) {
+          const uint32_t v = static_cast<uint32_t>(d[xs]);
+          if (v == us) {
+            c[xs] = e.y;
+            break;
+          }
+          if (v > us || steps > n) {  // only a corrupted d can get here
+            bad = true;
+            break;
+          }
+          xs = static_cast<int32_t>(v);
+        }
+      }
+    }
+    __syncwarp();
+  }
+  if (bad) flag_error(err, RS_ERR_ARG);
+}
+
 }  // namespace
 }  // namespace rsk
