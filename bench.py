@@ -154,6 +154,8 @@ def workload_config(args, N, B):
                         "5 resamplers x {f32, f64} + Permute + offspring conversions",
             "N": N, "y": args.y, "metropolis_B": B, "log_wmax": 0.0,
             "f32_prefix_sum": "plain binary32",
+            "f64_prefix_sum": "double-float (two binary32, about 2^-43 per rounding) over "
+                              "binary64 inputs; IEEE binary64 sums are the f64n rows",
             "parallelism": f"replicas x{max(1, args.gpus)}",
             "l2": (f"inputs rotate through a pool of {args.pool} weight vectors per dtype "
                    f"({args.pool * N * 12 / 2**20:.0f} MiB, "
@@ -325,15 +327,99 @@ def kernel_roofline_units(label: str, N: int, B: int):
 
 
 # ---------------------------------------------------------------------------------------
+# boundary mismatches of the scan-based resamplers against the oracle (after the timed
+# regions, on rank 0; the oracle is the checker, never on the measured path)
+# ---------------------------------------------------------------------------------------
+SCAN_MODES = (("f32", "f32", 0, (0, 1)), ("f32c", "f32", 1, (1,)), ("f64", "f64", 0, (0, 1)),
+              ("f64n", "f64", 2, (0, 1)))
+
+
+def scan_mismatches(rs, h, lw_by_name, N, seed=SEED):
+    """For every scan-based scheme and accumulation mode, one call's ancestors at the bench's
+    N against the oracle: positions that differ, how many of them lie within the rounding
+    bound of a cumulative-weight boundary (counted) and how many do not (must be 0), against
+    the sequential oracle in the call's own precision and the double-double one; for plain
+    binary32 also the largest offset of the cumulative offspring from the double-double
+    oracle's and the bound it must stay within (the boundary rule alone accepts every position
+    from about N = 2^18 in binary32)."""
+    import oracle
+    sys.path.insert(0, os.path.join(ROOT, "tests"))
+    from parity_tools import cumulative_mismatches, multinomial_mismatches, truth_offset
+    oracle.build()
+    out = {}
+    for kind, pname, prec, oprecs in SCAN_MODES:
+        lw_t = lw_by_name[pname]
+        lw = lw_t.cpu().numpy()
+        for s in (0, 1, 2):  # multinomial, stratified, systematic
+            a = rs.rs_resample(h, s, lw_t, seed=seed, prec=prec).cpu().numpy()
+            entry = {}
+            O_k = None if s == 0 else np.cumsum(np.bincount(a, minlength=N))
+            for op in oprecs:
+                if s == 0:
+                    _, a_o = oracle.multinomial(lw, seed, prec=op)
+                    n, bad = multinomial_mismatches(kind, lw, a, a_o, seed,
+                                                    oracle_is_sequential=(op == 0))
+                else:
+                    f = oracle.stratified if s == 1 else oracle.systematic
+                    _, O_o, _ = f(lw, seed, prec=op)
+                    n, bad = cumulative_mismatches(kind, s, lw, O_k, O_o, seed,
+                                                   oracle_is_sequential=(op == 0))
+                entry["vs_sequential" if op == 0 else "vs_exact"] = {
+                    "differ": int(n), "near_boundary": int(n - bad), "unexplained": int(bad)}
+            if s != 0 and kind == "f32":
+                dev, bound = truth_offset(kind, s, lw, O_k, seed)
+                entry["max_offset_vs_exact"] = dev
+                entry["offset_bound"] = bound
+            out[f"{SCHEME_NAMES[s]}_{kind}"] = entry
+    st = rs.rs_last_error(h)
+    if st != rs.RS_OK:
+        raise SystemExit(f"device status after the mismatch calls: {rs.rs_strerror(st)}")
+    return out
+
+
+def precision_mode_rows(rs, h, pools, N, hbm_peak, reps=21):
+    """Per-call time (with Permute) of the scan-based schemes in the compensated binary32 and
+    IEEE binary64 modes, which the timed step does not contain; inputs rotate through the
+    pools as in the step; median of `reps` calls, each between CUDA events on the stream."""
+    import torch
+    rows = {}
+    out = torch.empty(N, dtype=torch.int32, device=pools["f32"][0].device)
+    for kind, pname, prec in (("f32c", "f32", 1), ("f64n", "f64", 2)):
+        S = 4 if pname == "f32" else 8
+        for s in (0, 1, 2):
+            ts = []
+            for k in range(reps + 3):
+                lw = pools[pname][k % len(pools[pname])]
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record()
+                rs.rs_resample(h, s, lw, seed=SEED, step=k, out=out, permute=True, prec=prec)
+                e1.record()
+                torch.cuda.synchronize()
+                if k >= 3:
+                    ts.append(e0.elapsed_time(e1))
+            ms = statistics.median(ts)
+            rows[f"{SCHEME_NAMES[s]}_{kind}"] = {
+                "ms": round(ms, 5), "G_ancestors_per_s": round(N / (ms * 1e-3) / 1e9, 3),
+                "hbm_frac": round(sweep_hbm_bytes(s, S, N) / (ms * 1e-3) / 1e9 / hbm_peak, 4),
+                "timing": "single call between events (not in the timed step)"}
+    return rows
+
+
+# ---------------------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------------------
 def measure_philox_peak(rs, h, draws_per_thread: int = 1024, reps: int = 5) -> dict:
     """The Philox4x32-10 throughput of this GPU (rs_philox_throughput: 2048 threads per SM,
     each drawing `draws_per_thread` blocks; median of `reps` launches timed with CUDA events),
     the peak of the Philox-bound kernels (Metropolis, rejection), beside the figure derived
-    from unit counts (152 SMs x 2070 MHz x 32 IMAD.WIDE per clock / 20 per draw)."""
+    from unit counts (SMs x maximum SM clock x 32 IMAD.WIDE per clock / 20 per draw; the
+    clock from MEASURED_PEAKS.json, else 2070 MHz)."""
     import torch
     sms = torch.cuda.get_device_properties(h.device).multi_processor_count
+    peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    ghz = (float(json.load(open(peaks_path)).get("sm_max_mhz", 2070.0))
+           if os.path.exists(peaks_path) else 2070.0) / 1000.0
     threads = sms * 2048
     out = torch.empty(1, dtype=torch.int32, device=torch.device("cuda", h.device))
     for _ in range(2):
@@ -348,7 +434,7 @@ def measure_philox_peak(rs, h, draws_per_thread: int = 1024, reps: int = 5) -> d
         times.append(e0.elapsed_time(e1))
     ms = statistics.median(times)
     return {"measured_G_per_s": round(threads * draws_per_thread / (ms * 1e-3) / 1e9, 1),
-            "derived_G_per_s": round(152 * 2.070 * 32 / 20, 1),
+            "derived_G_per_s": round(sms * ghz * 32 / 20, 1), "sms": sms,
             "threads": threads, "draws_per_thread": draws_per_thread,
             "ms_per_launch": round(ms, 4)}
 
@@ -442,6 +528,15 @@ def run_ours(args):
     st = rs.rs_last_error(h)
     if st != rs.RS_OK:
         raise SystemExit(f"device status after timed region: {rs.rs_strerror(st)}")
+    # a timed region shorter than a second gives the 100 ms clock sampler few samples: the
+    # same graphs keep replaying (untimed) until the sampled window covers a second of work
+    extra = 0
+    while time.perf_counter() - wall0 < 1.0 and extra < 100000:
+        for k in range(args.steps):
+            graphs[k % period].replay()
+        torch.cuda.synchronize()
+        extra += args.steps
+    clock_window_s = time.perf_counter() - wall0
 
     # --- traced steps: per-kernel durations on the launching stream ---------------------
     n_ev = 256
@@ -621,11 +716,14 @@ def run_ours(args):
     d2h = sum(t.numel() * t.element_size() for p in host_out.values() for t in p)
 
     batched = None if args.no_batched else run_batched(args, dev, world)
+    per_scheme.update(precision_mode_rows(rs, h, pools, N, hbm_peak))
 
     cpu = None
+    mism = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(N, B, args.y, budget_s=20.0)
         cpu["all_cores"] = cpu_all_cores(N, B, args.y)
+        mism = scan_mismatches(rs, h, {"f32": pools["f32"][0], "f64": pools["f64"][0]}, N)
 
     if rank == 0:
         line = {
@@ -643,7 +741,10 @@ def run_ours(args):
             "roofline": roof,
             "per_scheme": per_scheme,
             "per_scheme_note": "one call with Permute, traced (kernel-to-kernel events); "
-                               "hbm_frac = algorithmic bytes (sweep_hbm_bytes) / time / peak",
+                               "hbm_frac = algorithmic bytes (sweep_hbm_bytes) / time / peak; "
+                               "f32 = plain binary32 sums, f64 = double-float sums over "
+                               "binary64 inputs, f32c = compensated two-float sums, f64n = "
+                               "IEEE binary64 sums",
             "per_kernel": per_kernel,
             "philox_peak": philox,
             "gpu_launches": gpu_launches_per_step * args.steps,
@@ -651,8 +752,16 @@ def run_ours(args):
             "traced_ms_per_step": round(ms_traced_total / args.steps, 5),
             "wall_s_timed_region": round(wall, 4),
             "clocks": {"sm_mhz": clk["sm_mhz"], "sm_max_mhz": clk["sm_max_mhz"],
-                       "reasons": clk["reasons"], "samples": clk["samples"]},
+                       "reasons": clk["reasons"], "samples": clk["samples"],
+                       "window_s": round(clock_window_s, 3),
+                       "window": "nvidia-smi every 100 ms over the timed replays, untimed "
+                                 "replays of the same graphs that extend them to 1 s, and "
+                                 "the traced steps"},
             "cpu_baseline": cpu,
+            "mismatches": mism,
+            "mismatches_note": ("one call per scan-based scheme and mode on the first pool "
+                                "vector, against the oracle (tests/parity_tools.py rules); "
+                                "unexplained must be 0"),
             "batched": batched,
         }
         print(json.dumps(line))
@@ -858,10 +967,19 @@ def run_reference(args):
     import oracle
     oracle.build()
     N, B = workload_params(args, oracle.metropolis_B)
-    n_sample = min(N, 1 << 18)
-    lws = [workload.synthetic_logw(n_sample, args.y, seed=SEED + 5, dtype=np.float32),
-           workload.synthetic_logw(n_sample, args.y, seed=SEED + 5, dtype=np.float64)]
-    for k in range(args.warmup):
+    # the config's N when the whole run fits about three minutes (timed from one step),
+    # else a 2^18-particle sample; the N used is stated in the config either way
+    n_sample = N
+    lws = [workload.synthetic_logw(N, args.y, seed=SEED + 5, dtype=np.float32),
+           workload.synthetic_logw(N, args.y, seed=SEED + 5, dtype=np.float64)]
+    t_one = time.perf_counter()
+    oracle_step(lws, B, SEED, 0)
+    t_one = time.perf_counter() - t_one
+    if t_one * (args.steps + args.warmup) > 180.0 and N > (1 << 18):
+        n_sample = 1 << 18
+        lws = [workload.synthetic_logw(n_sample, args.y, seed=SEED + 5, dtype=np.float32),
+               workload.synthetic_logw(n_sample, args.y, seed=SEED + 5, dtype=np.float64)]
+    for k in range(1, args.warmup):
         oracle_step(lws, B, SEED, k)
     t0 = time.perf_counter()
     done = 0
@@ -876,7 +994,7 @@ def run_reference(args):
         "n_gpus": 0, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": round(el / args.steps * 1e3, 3), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
-        "config": workload_config(args, N, B),
+        "config": dict(workload_config(args, N, B), reference_N=n_sample),
         "cpu_baseline": {"value": round(value, 6), "unit": UNIT, "cores": 1, "kind": "oracle",
                          "sample": sample, "host": host_info()},
         "e2e": {"value": round(value, 6), "unit": UNIT, "h2d_bytes_per_step": 0,
@@ -944,14 +1062,16 @@ def run_sweep(args):
             N = 1 << log2n
             B = workload_params(argparse.Namespace(log2n=log2n, y=y))[1]
             out = torch.empty(N, dtype=torch.int32, device="cuda")
-            for name, npdt in (("f32", np.float32), ("f64", np.float64)):
+            for name, npdt, prec in (("f32", np.float32, 0), ("f32c", np.float32, 1),
+                                     ("f64", np.float64, 0), ("f64n", np.float64, 2)):
                 lw = torch.from_numpy(workload.synthetic_logw(N, y, seed=SEED + log2n,
                                                               dtype=npdt)).cuda()
-                S = 4 if name == "f32" else 8
-                for scheme in range(5):
+                S = 4 if npdt == np.float32 else 8
+                # the compensated and IEEE binary64 modes change only the scan-based schemes
+                for scheme in (range(5) if prec == 0 else range(3)):
                     for k in range(3):
                         rs.rs_resample(h, scheme, lw, B=B, seed=SEED, step=k, out=out,
-                                       permute=True, log_wmax=0.0)
+                                       permute=True, log_wmax=0.0, prec=prec)
                     ts = []
                     for k in range(args.sweep_reps):
                         flush.fill_(float(k))
@@ -959,7 +1079,7 @@ def run_sweep(args):
                         e1 = torch.cuda.Event(enable_timing=True)
                         e0.record()
                         rs.rs_resample(h, scheme, lw, B=B, seed=SEED, step=k, out=out,
-                                       permute=True, log_wmax=0.0)
+                                       permute=True, log_wmax=0.0, prec=prec)
                         e1.record()
                         torch.cuda.synchronize()
                         ts.append(e0.elapsed_time(e1))
@@ -973,7 +1093,7 @@ def run_sweep(args):
                         row["us_graph"] = round(_graph_call_us(
                             lambda k, st: rs.rs_resample(h, scheme, lw, B=B, seed=SEED, step=k,
                                                          out=out, permute=True, log_wmax=0.0,
-                                                         stream=st)), 2)
+                                                         prec=prec, stream=st)), 2)
                     rows.append(row)
                 del lw
         st = rs.rs_last_error(h)
@@ -981,7 +1101,10 @@ def run_sweep(args):
     if st != rs.RS_OK:
         raise SystemExit(f"device status after sweep: {rs.rs_strerror(st)}")
     print(json.dumps({"sweep": "N = 2^10 .. 2^24, y in {%s}, B from Eq. B, log_wmax = 0, with "
-                      "Permute; median of %d calls, each after writing %d MiB (L2 flush); "
+                      "Permute; dtype f32 = plain binary32 sums, f32c = compensated, f64 = "
+                      "double-float over binary64 inputs, f64n = IEEE binary64 (the last "
+                      "three for the scan-based schemes); median of %d calls, each after "
+                      "writing %d MiB (L2 flush); "
                       "hbm_frac = algorithmic bytes (sweep_hbm_bytes) / time / %.1f GB/s "
                       "(measured); us_graph (N <= 2^16): %d calls captured in one CUDA graph, "
                       "replayed, time / calls (no flush: the inputs stay in L2)"

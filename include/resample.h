@@ -139,6 +139,27 @@ int rs_resample_prc(rs_handle* h, int dtype, const void* logw_dev, int64_t N, do
                     int64_t max_trials, uint64_t seed, uint64_t step, uint32_t filter,
                     int32_t* ancestors_dev, void* logw_out_dev, int permute, void* stream);
 
+/* Rejection resampling with an estimated bound (Section 2.2: when no hard bound on the
+ * weights is known, "some reasonable substitute" v_max; the empirical maximum would be a
+ * collective over all weights). log v_max is estimated on the device as the largest of
+ * `sample` log-weights at indices drawn uniformly (Philox, counter (k, 0, step, filter * 8 +
+ * 5) for the k-th; NaN passed over), then partial rejection control runs with it exactly as
+ * rs_resample_prc does, so the outcome is weighted: logw_out_dev[i] = lw[c_i] - min(lw[c_i],
+ * log v_max), nonzero only for ancestors whose weight exceeds the estimate.
+ *   log_wmax_dev   : one binary64 on the device, receives the estimate;
+ *   violations_dev : one uint64 on the device, receives the number of particles whose
+ *                    log-weight exceeds the estimate (the bound's violations);
+ *   sample         : 1 <= sample <= 2^31 - 1 (one CTA draws them: cost ~ sample / 1024);
+ *   the rest as rs_resample_prc. When no drawn log-weight is finite the estimate is -inf,
+ * every particle keeps itself (logw_out 0) and rs_last_error reports RS_ERR_ZERO_WEIGHT;
+ * otherwise the statuses of rs_resample_prc. Asynchronous on `stream`, no host sync. */
+int rs_resample_rejection_estimated(rs_handle* h, int dtype, const void* logw_dev, int64_t N,
+                                    int64_t sample, int64_t max_trials, uint64_t seed,
+                                    uint64_t step, uint32_t filter, int32_t* ancestors_dev,
+                                    void* logw_out_dev, double* log_wmax_dev,
+                                    unsigned long long* violations_dev, int permute,
+                                    void* stream);
+
 /* Many independent filters in one launch. F filters in CSR layout: offsets_dev holds F + 1
  * int64 offsets (device), filter f owning the particles offsets[f] .. offsets[f+1]-1 of
  * logw_dev and ancestors_dev; every filter has at most 2^20 particles (empty filters are

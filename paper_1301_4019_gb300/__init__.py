@@ -46,7 +46,7 @@ EXPORTED = [
     "rs_resample_batched_masked", "rs_reset_weights_batched",
     "rs_set_batched_launch", "rs_get_batched_launch", "rs_tune_batched", "rs_philox_throughput",
     "rs_cumulative_weights_f64", "rs_check_acceptance", "rs_set_barrier_timeout",
-    "rs_check_barrier_timeout",
+    "rs_check_barrier_timeout", "rs_resample_rejection_estimated",
     "rs_capture_if_below",
     "rs_capture_end_if", "rs_smc_mark_resampled", "rs_smc_loglik_step",
 ]
@@ -134,6 +134,8 @@ def _declare(lib):
         "rs_smc_loglik_step": (I, [P, P, P, P, P, C.c_double, C.c_double, I, P]),
         "rs_resample_prc": (I, [P, I, P, I64, C.c_double, I64, U64, U64, C.c_uint32, P, P, I,
                                 P]),
+        "rs_resample_rejection_estimated": (I, [P, I, P, I64, I64, I64, U64, U64, C.c_uint32, P,
+                                                P, P, P, I, P]),
         "rs_lgssm_step": (I, [P, P, I64, I, I, C.c_float, C.c_float, C.c_float, C.c_float,
                               U64, U64, C.c_uint32, P, P]),
     }
@@ -253,6 +255,28 @@ def rs_resample_prc(h: Handle, logw: torch.Tensor, log_vmax: float, seed: int = 
                                   1 if permute else 0,
                                   _stream(stream)), "rs_resample_prc")
     return out, logw_out
+
+
+def rs_resample_rejection_estimated(h: Handle, logw: torch.Tensor, sample: int, seed: int = 0,
+                                    step: int = 0, max_trials: int = 1 << 20, filter: int = 0,
+                                    permute: bool = False, stream=None):
+    """Rejection resampling with an estimated bound (Section 2.2): the bound is the largest of
+    `sample` log-weights at uniformly drawn indices, then partial rejection control with it.
+    Returns (ancestors, outcome log-weights, bound (one float64), violations (one int64))."""
+    N = logw.numel()
+    dev = logw.device
+    a = torch.empty(N, dtype=torch.int32, device=dev)
+    out = torch.empty_like(logw)
+    bound = torch.empty(1, dtype=torch.float64, device=dev)
+    viol = torch.empty(1, dtype=torch.int64, device=dev)
+    _check(load().rs_resample_rejection_estimated(
+        h.ptr, _dtype_code(logw), _dev(logw, (torch.float32, torch.float64), "logw", h=h), N,
+        int(sample), int(max_trials), int(seed) & 0xFFFFFFFFFFFFFFFF,
+        int(step) & 0xFFFFFFFFFFFFFFFF, int(filter), _dev(a, torch.int32, "a", N, h),
+        _dev(out, None, "out", N, h), _dev(bound, torch.float64, "bound", 1, h),
+        _dev(viol, torch.int64, "violations", 1, h), 1 if permute else 0, _stream(stream)),
+        "rs_resample_rejection_estimated")
+    return a, out, bound, viol
 
 
 def rs_resample_batched(h: Handle, scheme: int, logw: torch.Tensor, offsets: torch.Tensor,

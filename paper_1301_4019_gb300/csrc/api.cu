@@ -293,6 +293,40 @@ int rs_resample_prc(rs_handle* h, int dtype, const void* logw_dev, int64_t N, do
   return cuda_status(e);
 }
 
+int rs_resample_rejection_estimated(rs_handle* h, int dtype, const void* logw_dev, int64_t N,
+                                    int64_t sample, int64_t max_trials, uint64_t seed,
+                                    uint64_t step, uint32_t filter, int32_t* ancestors_dev,
+                                    void* logw_out_dev, double* log_wmax_dev,
+                                    unsigned long long* violations_dev, int permute,
+                                    void* stream) {
+  if (!h || !logw_dev || !ancestors_dev || !logw_out_dev || !log_wmax_dev || !violations_dev)
+    return RS_ERR_ARG;
+  int st = check_n(h, N);
+  if (st != RS_OK) return st;
+  if (dtype != RS_F32 && dtype != RS_F64) return RS_ERR_ARG;
+  if (permute != 0 && permute != 1) return RS_ERR_ARG;
+  if (sample < 1 || sample > kMaxN) return RS_ERR_ARG;
+  if (max_trials < 1 || max_trials > 0xFFFFFFFFLL) return RS_ERR_ARG;
+  if (filter >= (1u << 29)) return RS_ERR_ARG;
+  if (logw_out_dev == logw_dev) return RS_ERR_ARG;
+  if ((st = set_device(h)) != RS_OK) return st;
+  const cudaStream_t s = as_stream(stream);
+  const bool f64 = dtype == RS_F64;
+  int32_t* a_out = permute ? h->s.a_tmp : ancestors_dev;
+  int32_t* d = permute ? h->s.d : nullptr;
+  cudaError_t e = rsk::launch_estimate_bound(h->s, f64, logw_dev, N, sample, seed, step, filter,
+                                             log_wmax_dev, violations_dev, s);
+  if (e == cudaSuccess)
+    e = rsk::launch_rejection(h->s, f64, logw_dev, N, 0.0, true, max_trials, seed, step, filter,
+                              a_out, d, s, log_wmax_dev);
+  if (e == cudaSuccess && permute) e = rsk::launch_permute(h->s, a_out, d, N, ancestors_dev, s);
+  if (e == cudaSuccess)
+    e = rsk::launch_prc_weights(h->s, f64, logw_dev, ancestors_dev, N, 0.0, logw_out_dev, s,
+                                log_wmax_dev, violations_dev);
+  end_mark(h, s);
+  return cuda_status(e);
+}
+
 int rs_resample_batched_masked(rs_handle* h, int scheme, int dtype, const void* logw_dev,
                                const int64_t* offsets_dev, int32_t F, const int32_t* B_dev,
                                int32_t B, uint64_t seed, uint64_t step,

@@ -30,7 +30,10 @@ __device__ __forceinline__ void flag_error(int* err, int status) { atomicMin(err
 // depend on the seed only, so they are computed once per call (on the host) and read from
 // the kernel parameters.
 // ---------------------------------------------------------------------------------------
-// The draw keying of the library: key = seed; counter = (index, n, step, filter*8+scheme).
+// The draw keying of the library: key = seed; counter = (index, n, step, filter*8+purpose),
+// purpose = the scheme (0..4), kPurposeBoundEstimate for the estimated rejection bound, 6 for
+// the Philox throughput measurement.
+constexpr uint32_t kPurposeBoundEstimate = 5;
 struct Keys {
   uint32_t rk0[10], rk1[10];  // round keys: seed words plus r times the Weyl constants
   uint32_t step;              // SMC step mod 2^32

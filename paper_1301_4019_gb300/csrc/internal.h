@@ -124,10 +124,17 @@ cudaError_t launch_batched(const Scratch& s, int scheme, Acc acc, const void* lo
 cudaError_t launch_metropolis(const Scratch& s, bool f64, const void* logw, int64_t N,
                               int32_t B, uint64_t seed, uint64_t step, uint32_t filter,
                               int32_t* a_out, int32_t* d_or_null, cudaStream_t st);
+// (lwmax_dev: the bound read on the device instead of log_wmax, an estimated bound of -inf
+// giving the identity, flagged RS_ERR_ZERO_WEIGHT)
 cudaError_t launch_rejection(const Scratch& s, bool f64, const void* logw, int64_t N,
                              double log_wmax, bool clamp, int64_t max_trials, uint64_t seed,
                              uint64_t step, uint32_t filter, int32_t* a_out,
-                             int32_t* d_or_null, cudaStream_t st);
+                             int32_t* d_or_null, cudaStream_t st,
+                             const double* lwmax_dev = nullptr);
+// The estimated rejection bound (largest of `sample` drawn log-weights) to *est; *viol = 0.
+cudaError_t launch_estimate_bound(const Scratch& s, bool f64, const void* logw, int64_t N,
+                                  int64_t sample, uint64_t seed, uint64_t step, uint32_t filter,
+                                  double* est, unsigned long long* viol, cudaStream_t st);
 // aux.cu: a cooperative launch whose grid barrier expects one arrival more than the grid
 // makes, so that every CTA's bounded wait runs out (RS_ERR_TIMEOUT) and the kernel ends.
 cudaError_t launch_barrier_timeout_probe(const Scratch& s, cudaStream_t st);
@@ -135,8 +142,11 @@ cudaError_t launch_barrier_timeout_probe(const Scratch& s, cudaStream_t st);
 // decisions on n log-weight pairs): the number of wrong decisions goes to *count.
 cudaError_t launch_check_acceptance(int mode, int64_t n, unsigned long long* count,
                                     cudaStream_t st);
+// (lvmax_dev: the bound read on the device; viol: count of log-weights above it)
 cudaError_t launch_prc_weights(const Scratch& s, bool f64, const void* logw, const int32_t* c,
-                               int64_t N, double log_vmax, void* out, cudaStream_t st);
+                               int64_t N, double log_vmax, void* out, cudaStream_t st,
+                               const double* lvmax_dev = nullptr,
+                               unsigned long long* viol = nullptr);
 
 // aux.cu
 cudaError_t launch_fill(int32_t* p, int64_t N, int32_t v, cudaStream_t st);

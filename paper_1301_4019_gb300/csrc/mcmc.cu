@@ -7,6 +7,8 @@
 // numbers of step s do not depend on the chain state: the proposals and their log-weight
 // gathers of several steps are issued together and only the accept decisions run in
 // sequence (mcmc.cuh).
+#include <cfloat>
+
 #include "common.cuh"
 #include "grid.cuh"
 #include "internal.h"
@@ -109,8 +111,9 @@ __device__ __forceinline__ void rejection_run(const T* __restrict__ lw,
 template <typename T, bool COOP>
 __global__ void __launch_bounds__(kBlock)
 rejection_kernel(const T* __restrict__ lw, float* __restrict__ lwf, int64_t N, double log_wmax,
-                 bool clamp, int64_t max_trials, Keys keys, int32_t* __restrict__ a,
-                 int32_t* __restrict__ d, int64_t run_len, GridBar* bar, int* err) {
+                 const double* lwmax_dev, bool clamp, int64_t max_trials, Keys keys,
+                 int32_t* __restrict__ a, int32_t* __restrict__ d, int64_t run_len,
+                 GridBar* bar, int* err) {
   pdl_wait();
   unsigned int target = 0;
   if constexpr (COOP) {
@@ -124,7 +127,21 @@ rejection_kernel(const T* __restrict__ lw, float* __restrict__ lwf, int64_t N, d
     }
     grid_barrier(bar, target, err);
   }
-  const RejBound rb = make_bound(log_wmax, clamp);
+  // the bound: the argument, or (lwmax_dev) one estimated on the device; an estimate of -inf
+  // (no finite log-weight drawn) leaves every particle its own ancestor, flagged
+  const double lwm = lwmax_dev ? __ldcg(lwmax_dev) : log_wmax;
+  if (!(lwm > -DBL_MAX)) {
+    const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+    for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < N;
+         i += stride) {
+      a[i] = static_cast<int32_t>(i);
+      if (d) atomicMin(d + i, static_cast<int32_t>(i));
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) flag_error(err, RS_ERR_ZERO_WEIGHT);
+    if constexpr (COOP) grid_exit(bar, target);
+    return;
+  }
+  const RejBound rb = make_bound(lwm, clamp);
   const int64_t warps = (static_cast<int64_t>(gridDim.x) * blockDim.x) >> 5;
   for (int64_t run = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
        run * run_len < N; run += warps) {  // uniform across the warp
@@ -138,20 +155,64 @@ rejection_kernel(const T* __restrict__ lw, float* __restrict__ lwf, int64_t N, d
 // Log-weights of the outcome of partial rejection control for the delivered ancestry c:
 // out_i = lw[c_i] - min(lw[c_i], log v_max), in the log-weights' type (0 unless the ancestor's
 // weight exceeds v_max; 0 for a zero weight, which only the trial cap can deliver).
+// With lvmax_dev the bound is read on the device (rounded to T as the attempts round it), a
+// bound of -inf gives 0 everywhere (the identity ancestry), and *viol (set to 0 before) counts
+// the particles whose own log-weight exceeds the bound.
 template <typename T>
 __global__ void __launch_bounds__(kBlock)
 prc_weights_kernel(const T* __restrict__ lw, const int32_t* __restrict__ c, int64_t N, T lvmax,
-                   T* __restrict__ out, int* err) {
+                   const double* lvmax_dev, T* __restrict__ out,
+                   unsigned long long* viol, int* err) {
   pdl_wait();
   const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (i >= N) return;
-  const int32_t ci = c[i];
-  if (ci < 0 || ci >= N) {
-    flag_error(err, RS_ERR_ARG);
-    return;
+  const T bound = lvmax_dev ? static_cast<T>(__ldcg(lvmax_dev)) : lvmax;
+  bool above = false;
+  if (i < N) {
+    const int32_t ci = c[i];
+    if (ci < 0 || ci >= N) {
+      flag_error(err, RS_ERR_ARG);
+    } else {
+      const T w = __ldg(lw + ci);
+      out[i] = (w > bound && bound > neg_inf<T>()) ? w - bound : T(0);
+    }
+    above = viol && __ldg(lw + i) > bound;
   }
-  const T w = __ldg(lw + ci);
-  out[i] = w > lvmax ? w - lvmax : T(0);
+  if (viol) {
+    const unsigned mask = __ballot_sync(0xffffffffu, above);
+    if ((threadIdx.x & 31) == 0 && mask) atomicAdd(viol, static_cast<unsigned long long>(__popc(mask)));
+  }
+}
+
+// The estimated bound of the rejection resampler (Section 2.2, a substitute for w_max): the
+// largest of `sample` log-weights at indices drawn uniformly, the k-th from counter (k, 0)
+// under the keys' purpose; NaN is passed over, -inf when nothing finite was drawn. One CTA of
+// kEstBlock threads; also sets *viol to 0 for the weights kernel.
+constexpr int kEstBlock = 1024;
+template <typename T>
+__global__ void __launch_bounds__(kEstBlock)
+estimate_bound_kernel(const T* __restrict__ lw, int64_t N, int64_t sample, Keys keys,
+                      double* est, unsigned long long* viol) {
+  pdl_wait();
+  __shared__ double sh[kEstBlock / 32];
+  double m = -INFINITY;
+  for (int64_t k = threadIdx.x; k < sample; k += kEstBlock) {
+    const uint4 x = draw(keys, static_cast<uint32_t>(k), 0u);
+    const double v = static_cast<double>(__ldg(lw + uniform_index(x, N)));
+    if (v > m) m = v;  // (NaN never compares)
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const double y = __shfl_xor_sync(0xffffffffu, m, o);
+    m = y > m ? y : m;
+  }
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double b = sh[0];
+    for (int w = 1; w < kEstBlock / 32; ++w) b = sh[w] > b ? sh[w] : b;
+    *est = b;
+    if (viol) *viol = 0ull;
+  }
 }
 
 // Sidecars of binary64 log-weights (f64_sidecar) and, when d is given, the claims d = N (the
@@ -304,8 +365,9 @@ cudaError_t launch_metropolis_t(const Scratch& s, const T* lw, int64_t N, int32_
 
 template <typename T>
 cudaError_t launch_rejection_t(const Scratch& s, const T* lw, int64_t N, double log_wmax,
-                               bool clamp, int64_t max_trials, const Keys& keys, int32_t* a_out,
-                               int32_t* d, bool f64, cudaStream_t st) {
+                               const double* lwmax_dev, bool clamp, int64_t max_trials,
+                               const Keys& keys, int32_t* a_out, int32_t* d, bool f64,
+                               cudaStream_t st) {
   GridBar* bar = &s.glob->bar;
   float* lwf = static_cast<float*>(s.W);  // the sidecars of binary64 log-weights (4 B each)
   const int64_t runs = (N + kRejRun - 1) / kRejRun;
@@ -321,8 +383,8 @@ cudaError_t launch_rejection_t(const Scratch& s, const T* lw, int64_t N, double 
       int64_t run_len = (N + warps - 1) / warps;
       run_len = run_len > kRejRun ? run_len : kRejRun;
       trace_mark(s.trace, f64 ? "rejection_f64" : "rejection_f32", st);
-      return coop_launch(rejection_kernel<T, true>, grid, st, lw, lwf, N, log_wmax, clamp,
-                         max_trials, keys, a_out, d, run_len, bar, s.err);
+      return coop_launch(rejection_kernel<T, true>, grid, st, lw, lwf, N, log_wmax, lwmax_dev,
+                         clamp, max_trials, keys, a_out, d, run_len, bar, s.err);
     }
   }
   if (sizeof(T) == 8) {
@@ -338,8 +400,8 @@ cudaError_t launch_rejection_t(const Scratch& s, const T* lw, int64_t N, double 
   }
   trace_mark(s.trace, f64 ? "rejection_f64" : "rejection_f32", st);
   launch_pdl(rejection_kernel<T, false>, static_cast<int>(want), kBlock, st, lw, lwf, N,
-             log_wmax, clamp, max_trials, keys, a_out, d, static_cast<int64_t>(kRejRun), bar,
-             s.err);
+             log_wmax, lwmax_dev, clamp, max_trials, keys, a_out, d,
+             static_cast<int64_t>(kRejRun), bar, s.err);
   return cudaGetLastError();
 }
 
@@ -357,25 +419,41 @@ cudaError_t launch_metropolis(const Scratch& s, bool f64, const void* logw, int6
 cudaError_t launch_rejection(const Scratch& s, bool f64, const void* logw, int64_t N,
                              double log_wmax, bool clamp, int64_t max_trials, uint64_t seed,
                              uint64_t step, uint32_t filter, int32_t* a_out, int32_t* d,
-                             cudaStream_t st) {
+                             cudaStream_t st, const double* lwmax_dev) {
   const Keys keys = make_keys(seed, step, filter, RS_REJECTION);
   if (f64)
-    return launch_rejection_t(s, static_cast<const double*>(logw), N, log_wmax, clamp,
+    return launch_rejection_t(s, static_cast<const double*>(logw), N, log_wmax, lwmax_dev, clamp,
                               max_trials, keys, a_out, d, true, st);
-  return launch_rejection_t(s, static_cast<const float*>(logw), N, log_wmax, clamp, max_trials,
-                            keys, a_out, d, false, st);
+  return launch_rejection_t(s, static_cast<const float*>(logw), N, log_wmax, lwmax_dev, clamp,
+                            max_trials, keys, a_out, d, false, st);
+}
+
+cudaError_t launch_estimate_bound(const Scratch& s, bool f64, const void* logw, int64_t N,
+                                  int64_t sample, uint64_t seed, uint64_t step, uint32_t filter,
+                                  double* est, unsigned long long* viol, cudaStream_t st) {
+  const Keys keys = make_keys(seed, step, filter, kPurposeBoundEstimate);
+  trace_mark(s.trace, "estimate_bound", st);
+  if (f64)
+    launch_pdl(estimate_bound_kernel<double>, 1, kEstBlock, st, static_cast<const double*>(logw),
+               N, sample, keys, est, viol);
+  else
+    launch_pdl(estimate_bound_kernel<float>, 1, kEstBlock, st, static_cast<const float*>(logw),
+               N, sample, keys, est, viol);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_prc_weights(const Scratch& s, bool f64, const void* logw, const int32_t* c,
-                               int64_t N, double log_vmax, void* out, cudaStream_t st) {
+                               int64_t N, double log_vmax, void* out, cudaStream_t st,
+                               const double* lvmax_dev, unsigned long long* viol) {
   trace_mark(s.trace, "prc_weights", st);
   const int grid = static_cast<int>((N + kBlock - 1) / kBlock);
   if (f64)
     launch_pdl(prc_weights_kernel<double>, grid, kBlock, st, static_cast<const double*>(logw),
-               c, N, log_vmax, static_cast<double*>(out), s.err);
+               c, N, log_vmax, lvmax_dev, static_cast<double*>(out), viol, s.err);
   else  // the bound in binary32 as the binary32 attempts use it: RN(log v_max)
     launch_pdl(prc_weights_kernel<float>, grid, kBlock, st, static_cast<const float*>(logw), c,
-               N, static_cast<float>(log_vmax), static_cast<float*>(out), s.err);
+               N, static_cast<float>(log_vmax), lvmax_dev, static_cast<float*>(out), viol,
+               s.err);
   return cudaGetLastError();
 }
 
