@@ -227,30 +227,31 @@ class ClockSampler:
 # headers it includes, hashed; `traffic` is null once any of them has changed.
 # ---------------------------------------------------------------------------------------
 NCU_TRAFFIC = {  # label: (bytes per launch, source hash)
-               "permute": (8393626, "e894311ca809ba84"),
-               "metropolis_f64": (12597723, "2cceea6306c765cb"),
-               "metropolis_f32": (8403328, "2cceea6306c765cb"),
-               "rejection_f64": (8410149, "2cceea6306c765cb"),
-               "permute_sorted": (8396971, "e894311ca809ba84"),
-               "rejection_f32": (4209120, "2cceea6306c765cb"),
-               "fused_multinomial_f64": (8492416, "3efab4a1e18dda20"),
-               "fused_stratified_f64": (8487899, "3efab4a1e18dda20"),
-               "fused_systematic_f64": (8480110, "3efab4a1e18dda20"),
-               "fused_multinomial_f32": (4280320, "3efab4a1e18dda20"),
-               "fused_stratified_f32": (4261664, "3efab4a1e18dda20"),
-               "iscan": (4213872, "e894311ca809ba84"),
-               "fused_systematic_f32": (4257696, "3efab4a1e18dda20"),
-               "search_f32": (12592416, "8e04b4b14d8721c6"),
-               "fill": (8806, "e894311ca809ba84"),
-               "search_f64": (16784786, "8e04b4b14d8721c6"),
-               "cumoff_to_ancestors": (4199568, "e894311ca809ba84"),
-               "offspring": (8391456, "e894311ca809ba84"),
-               "adjacent_difference": (4197856, "e894311ca809ba84")}
+               "offspring": (8391280, "0248ac8c98f19735"),
+               "iscan": (4213152, "0248ac8c98f19735"),
+               "adjacent_difference": (4197824, "0248ac8c98f19735"),
+               "cumoff_to_ancestors": (4200592, "0248ac8c98f19735"),
+               "fill": (8392, "0248ac8c98f19735"),
+               "fused_multinomial_f32": (4288256, "facf564dfdd5c288"),
+               "search_f32": (12591712, "2ceb13f0e29c28de"),
+               "permute": (8399969, "0248ac8c98f19735"),
+               "fused_stratified_f32": (4266368, "facf564dfdd5c288"),
+               "permute_sorted": (8400213, "0248ac8c98f19735"),
+               "fused_systematic_f32": (4262528, "facf564dfdd5c288"),
+               "metropolis_f32": (8412384, "32cec44800ec390c"),
+               "rejection_f32": (4214336, "32cec44800ec390c"),
+               "fused_multinomial_f64": (8549184, "facf564dfdd5c288"),
+               "search_f64": (16784165, "2ceb13f0e29c28de"),
+               "fused_stratified_f64": (8536027, "facf564dfdd5c288"),
+               "fused_systematic_f64": (8527543, "facf564dfdd5c288"),
+               "sidecar": (8394057, "32cec44800ec390c"),
+               "metropolis_f64": (16804425, "32cec44800ec390c"),
+               "rejection_f64": (8418597, "32cec44800ec390c")}
 
 _LABEL_FILES = (("fused_", "fused.cu"), ("permute", "aux.cu"), ("iscan", "aux.cu"),
                 ("fill", "aux.cu"), ("offspring", "aux.cu"), ("adjacent", "aux.cu"),
                 ("cumoff", "aux.cu"), ("metropolis", "mcmc.cu"), ("rejection", "mcmc.cu"),
-                ("prc_", "mcmc.cu"), ("max_", "scan.cu"), ("tile_sum", "scan.cu"),
+                ("prc_", "mcmc.cu"), ("sidecar", "mcmc.cu"), ("max_", "scan.cu"), ("tile_sum", "scan.cu"),
                 ("emit_", "scan.cu"), ("search_", "scan.cu"))
 
 
