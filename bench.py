@@ -295,11 +295,9 @@ def kernel_roofline_units(label: str, N: int, B: int):
     S = 8 if ("_f64" in label) else 4
     V = 8 if ("_f64" in label or label.endswith("_f32c")) else 4
     if label.startswith("fused_systematic_") or label.startswith("fused_stratified_"):
-        # two reads of logw (the normaliser precedes every O_i), write a, then Permute:
-        # write and read the claims d, read a, write c
-        return "hbm", (2 * S + 4 + 16) * N, "B"
+        return "hbm", (2 * S + 8) * N, "B"        # two reads of logw, write a and the claims d
     if label.startswith("fused_multinomial_"):
-        return "hbm", (2 * S + V + 4 + 16) * N, "B"  # as above plus the stored W
+        return "hbm", (2 * S + V + 4) * N, "B"    # two reads of logw, W, the claims' sentinel
     if label.startswith("max_") or label.startswith("tile_sum_"):
         return "hbm", S * N, "B"
     if label.startswith("emit_systematic_") or label.startswith("emit_stratified_"):
@@ -313,7 +311,7 @@ def kernel_roofline_units(label: str, N: int, B: int):
     if label.startswith("rejection_"):
         return "alu", None, "Philox"
     if label in ("permute", "permute_sorted"):
-        return "hbm", 16 * N, "B"                  # read a, d (claims); write c; claims written
+        return "hbm", 12 * N, "B"                  # read a and the claims d, write c
     if label == "fill":
         return "hbm", 4 * N, "B"
     if label == "offspring":

@@ -33,22 +33,6 @@
 namespace rsk {
 namespace {
 
-__device__ __forceinline__ long long key_of(float v) {
-  const int b = __float_as_int(v);
-  return static_cast<long long>(b >= 0 ? b : (b ^ 0x7fffffff));
-}
-__device__ __forceinline__ long long key_of(double v) {
-  const long long b = __double_as_longlong(v);
-  return b >= 0 ? b : (b ^ 0x7fffffffffffffffLL);
-}
-__device__ __forceinline__ double value_of(long long k, float) {
-  const int b = static_cast<int>(k);
-  return static_cast<double>(__int_as_float(b >= 0 ? b : (b ^ 0x7fffffff)));
-}
-__device__ __forceinline__ double value_of(long long k, double) {
-  return __longlong_as_double(k >= 0 ? k : (k ^ 0x7fffffffffffffffLL));
-}
-
 // Particle g of the batch -> (filter f, its first particle lo, its size n, local index i).
 // Returns false for positions past offsets[F] and for filters the plan rejected.
 struct PartLoc {
@@ -171,7 +155,7 @@ __global__ void __launch_bounds__(kBlock) batch_max_kernel(const T* __restrict__
   if (!resampled(b.resample, L.f)) return;  // a filter that keeps its particles: no passes
   const bool vec = (reinterpret_cast<uintptr_t>(lw) & 15u) == 0;
   const int64_t end = min(L.hi, L.base + kTile);
-  long long m = key_of(neg_inf<T>());
+  long long m = max_key(neg_inf<T>());
   bool bad = false;
   for (int64_t i0 = L.base + 4 * static_cast<int64_t>(threadIdx.x); i0 < end; i0 += 4 * kBlock) {
     T x[4];
@@ -180,7 +164,7 @@ __global__ void __launch_bounds__(kBlock) batch_max_kernel(const T* __restrict__
     for (int q = 0; q < 4; ++q) {
       const bool nan = is_nan(x[q]);
       bad |= nan || is_pos_inf(x[q]);
-      const long long k = key_of(x[q]);
+      const long long k = max_key(x[q]);
       if (!nan && k > m) m = k;
     }
   }
@@ -197,12 +181,12 @@ __global__ void __launch_bounds__(kBlock) batch_max_kernel(const T* __restrict__
     long long bm = sh[0];
     for (int k = 1; k < kWarps; ++k) bm = sh[k] > bm ? sh[k] : bm;
     // stored as the key of the binary64 value, comparable across both input types
-    atomicMax(b.fmax + L.f, key_of(value_of(bm, T())));
+    atomicMax(b.fmax + L.f, max_key(key_to_double(bm, T())));
   }
 }
 
 __device__ __forceinline__ double filter_M(const Batch& b, int f) {
-  return value_of(__ldcg(b.fmax + f), 0.0);
+  return key_to_double(__ldcg(b.fmax + f), 0.0);
 }
 
 template <typename T, typename V>
@@ -213,14 +197,15 @@ __global__ void __launch_bounds__(kBlock) batch_sum_kernel(const T* __restrict__
   TileLoc L;
   if (!locate_tile(b, blockIdx.x, L)) return;
   if (!resampled(b.resample, L.f)) return;
-  const double M = filter_M(b, L.f);
-  if (M > -DBL_MAX) {
-    const WeightCtx wc = make_ctx<T, V>(M, sh_tab);
-    const bool vec = (reinterpret_cast<uintptr_t>(lw) & 15u) == 0;
-    tile_record<T, V>(lw, L.lo, L.hi, L.base, wc, vec, b.s_rec + blockIdx.x, sh);
-  } else if (threadIdx.x == 0) {
-    store_v<V>(b.s_rec + blockIdx.x, vzero(V()));
+  if (threadIdx.x < 64) sh_tab[threadIdx.x] = kExp2Frac64[threadIdx.x];  // (read after a sync)
+  const bool vec = (reinterpret_cast<uintptr_t>(lw) & 15u) == 0;
+  bool bad = false;  // (the max pass flags non-finite input)
+  long long ref = kTileMaxRef;
+  if constexpr (!Path<T, V>::kTileRef) {
+    const double M = filter_M(b, L.f);
+    if (M > -DBL_MAX) ref = max_key(static_cast<T>(M));  // (records relative to M)
   }
+  tile_record<T, V>(lw, L.lo, L.hi, L.base, sh_tab, vec, b.s_rec + blockIdx.x, sh, bad, ref);
 }
 
 template <typename T, typename V>
@@ -237,9 +222,9 @@ __global__ void __launch_bounds__(kBlock) batch_prefix_kernel(Batch b) {
     }
     return;
   }
-  tile_prefix_compute<V>(b.s_rec + t0, b.P_rec + t0 + f, nt, n,
-                            reinterpret_cast<V*>(b.fS + f), reinterpret_cast<V*>(b.fscale + f),
-                            b.fSd + f);
+  tile_prefix_compute<T, V>(b.s_rec + t0, b.P_rec + t0 + f, nt, n,
+                            static_cast<T>(filter_M(b, f)), reinterpret_cast<V*>(b.fS + f),
+                            reinterpret_cast<V*>(b.fscale + f), b.fSd + f);
 }
 
 template <typename T, typename V, int SCHEME>
@@ -285,12 +270,13 @@ batch_emit_kernel(const T* __restrict__ lw, Batch b, Keys base_keys,
 // ---------------------------------------------------------------------------------------
 // The max, sum, prefix and emission passes of all filters in one cooperative launch (after the
 // plan kernel): CTA c owns the contiguous batch tiles [c T / G, (c+1) T / G) of the T tiles of
-// all filters together, and the CTAs meet at two grid barriers:
-//   phase 1  per tile, the maximum log-weight, combined per filter by an atomic max of keys;
-//   phase 2  per tile, its record (tile_record) relative to its filter's maximum;
-//   phase 3  per tile, the exact sums of its filter's records (those before it, and all),
-//            rounded once to P_t, P_{t+1} and W^N as tile_prefix_compute rounds them, then the
-//            emission.
+// all filters together, and the CTAs meet at one grid barrier (two for compensated binary32,
+// whose records follow the filter maxima):
+//   phase 1  per tile, its record (tile_record: the tile's maximum log-weight and its weights'
+//            sum relative to it), the maxima combined per filter by an atomic max of keys;
+//   phase 2  per tile, the exact sums of its filter's records scaled to the filter's maximum
+//            (those before it, and all), rounded once to P_t, P_{t+1} and W^N as
+//            tile_prefix_compute rounds them, then the emission.
 // Every tile goes through the same device functions and rounded prefixes as in the separate
 // batched kernels and the single-filter kernels, so filter f still equals rs_resample on its
 // slice with filter = f, bit for bit.
@@ -313,54 +299,59 @@ batch_coop_kernel(const T* __restrict__ lw, Batch b, Keys base_keys, int32_t* __
   const bool vec = (reinterpret_cast<uintptr_t>(lw) & 15u) == 0;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 
-  // ---- phase 1: tile maxima -> filter maxima ------------------------------------------------
-  for (int t = t0; t < t1; ++t) {
-    TileLoc L;
-    if (!locate_tile(b, t, L) || !resampled(b.resample, L.f)) continue;  // uniform per CTA
-    const int64_t end = min(L.hi, L.base + kTile);
-    long long m = key_of(neg_inf<T>());
+  // ---- phase 1: tile records -> filter maxima ------------------------------------------------
+  // (compensated binary32: the maxima first, then the records relative to them)
+  if (threadIdx.x < 64) sh_tab[threadIdx.x] = kExp2Frac64[threadIdx.x];  // (read after a sync)
+  {
     bool bad = false;
-    T x[kPer];
-    load_per(lw, L.base + kPer * static_cast<int64_t>(threadIdx.x), L.lo, end, vec, x);
+    for (int t = t0; t < t1; ++t) {
+      TileLoc L;
+      if (!locate_tile(b, t, L) || !resampled(b.resample, L.f)) continue;  // uniform per CTA
+      long long k;
+      if constexpr (Path<T, V>::kTileRef) {
+        k = tile_record<T, V>(lw, L.lo, L.hi, L.base, sh_tab, vec, b.s_rec + t, sh, bad);
+      } else {
+        const int64_t end = min(L.hi, L.base + kTile);
+        T x[kPer];
+        load_per(lw, L.base + kPer * static_cast<int64_t>(threadIdx.x), L.lo, end, vec, x);
+        long long m = max_key(neg_inf<T>());
 #pragma unroll
-    for (int q = 0; q < kPer; ++q) {
-      const bool nan = is_nan(x[q]);
-      bad |= nan || is_pos_inf(x[q]);
-      const long long k = key_of(x[q]);
-      if (!nan && k > m) m = k;
+        for (int q = 0; q < kPer; ++q) {
+          const bool nan = is_nan(x[q]);
+          bad |= nan || is_pos_inf(x[q]);
+          const long long kq = max_key(x[q]);
+          if (!nan && kq > m) m = kq;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          const long long y = __shfl_xor_sync(0xffffffffu, m, o);
+          m = y > m ? y : m;
+        }
+        __syncthreads();
+        if (lane == 0) sh_key[warp] = m;
+        __syncthreads();
+        k = sh_key[0];
+        for (int w = 1; w < kWarps; ++w) k = sh_key[w] > k ? sh_key[w] : k;
+      }
+      // stored as the key of the binary64 value, comparable across both input types
+      if (threadIdx.x == 0) atomicMax(b.fmax + L.f, max_key(key_to_double(k, T())));
     }
     if (bad) flag_error(b.err, RS_ERR_NONFINITE);
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      const long long y = __shfl_xor_sync(0xffffffffu, m, o);
-      m = y > m ? y : m;
-    }
-    __syncthreads();
-    if (lane == 0) sh_key[warp] = m;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      long long bm = sh_key[0];
-      for (int k = 1; k < kWarps; ++k) bm = sh_key[k] > bm ? sh_key[k] : bm;
-      atomicMax(b.fmax + L.f, key_of(value_of(bm, T())));
-    }
   }
   grid_barrier(bar, target, b.err);
-
-  // ---- phase 2: tile records ------------------------------------------------------------------
-  for (int t = t0; t < t1; ++t) {
-    TileLoc L;
-    if (!locate_tile(b, t, L) || !resampled(b.resample, L.f)) continue;
-    const double M = filter_M(b, L.f);
-    if (M > -DBL_MAX) {
-      const WeightCtx wc = make_ctx<T, V>(M, sh_tab);
-      tile_record<T, V>(lw, L.lo, L.hi, L.base, wc, vec, b.s_rec + t, sh);
-    } else if (threadIdx.x == 0) {
-      store_v<V>(b.s_rec + t, vzero(V()));
+  if constexpr (!Path<T, V>::kTileRef) {
+    bool bad = false;
+    for (int t = t0; t < t1; ++t) {
+      TileLoc L;
+      if (!locate_tile(b, t, L) || !resampled(b.resample, L.f)) continue;
+      const double M = filter_M(b, L.f);
+      tile_record<T, V>(lw, L.lo, L.hi, L.base, sh_tab, vec, b.s_rec + t, sh, bad,
+                        M > -DBL_MAX ? max_key(static_cast<T>(M)) : kTileMaxRef);
     }
+    grid_barrier(bar, target, b.err);
   }
-  grid_barrier(bar, target, b.err);
 
-  // ---- phase 3: prefixes of each tile from its filter's exact record sums, emission ---------
+  // ---- phase 2: prefixes of each tile from its filter's exact record sums, emission ---------
   for (int t = t0; t < t1; ++t) {
     TileLoc L;
     if (!locate_tile(b, t, L)) continue;
@@ -376,9 +367,10 @@ batch_coop_kernel(const T* __restrict__ lw, Batch b, Keys base_keys, int32_t* __
     if (active) {
       const int first = __ldg(b.tile_start + L.f);
       const int nt = __ldg(b.tile_start + L.f + 1) - first;
+      const T Mt = static_cast<T>(M);  // (exact: M is one of the filter's log-weights)
       u128 part = 0, tot = 0;
       for (int k = threadIdx.x; k < nt; k += kBlock) {
-        const u128 v = rec_fixed<V>(b.s_rec + first + k);
+        const u128 v = rec_fixed<T, V>(b.s_rec + first + k, Mt);
         tot += v;
         if (k < L.t) part += v;
       }
@@ -388,7 +380,7 @@ batch_coop_kernel(const T* __restrict__ lw, Batch b, Keys base_keys, int32_t* __
         const double Sd0 = vto_double(S0);
         const V sc0 = vfrom_double(__ddiv_rn(static_cast<double>(n), Sd0), V());
         store_v<V>(&sh_Pt, fixed_to(part, V(), kFixFrac));
-        store_v<V>(&sh_Pn, fixed_to(part + rec_fixed<V>(b.s_rec + t), V(), kFixFrac));
+        store_v<V>(&sh_Pn, fixed_to(part + rec_fixed<T, V>(b.s_rec + t, Mt), V(), kFixFrac));
         store_v<V>(&sh_S, S0);
         store_v<V>(&sh_scale, sc0);
         sh_Sd = Sd0;

@@ -13,6 +13,7 @@ namespace rsk {
 constexpr int kBlock = 256;          // threads per CTA of the streaming kernels
 constexpr int kPer = 8;              // consecutive particles per thread in a scan tile
 constexpr int kTile = kBlock * kPer; // particles per CTA tile of the scan kernels (2048)
+constexpr int kRunWin = 32 * kPer;  // positions a warp covers per round of Code 11 (warp_runs)
 constexpr int kWarps = kBlock / 32;  // 8 warps
 
 // ---------------------------------------------------------------------------------------

@@ -23,23 +23,6 @@
 namespace rsk {
 namespace {
 
-// Order-preserving integer keys of the log-weights (exact comparisons, no binary64 ALU).
-__device__ __forceinline__ long long fkey(float v) {
-  const int b = __float_as_int(v);
-  return static_cast<long long>(b >= 0 ? b : (b ^ 0x7fffffff));
-}
-__device__ __forceinline__ long long fkey(double v) {
-  const long long b = __double_as_longlong(v);
-  return b >= 0 ? b : (b ^ 0x7fffffffffffffffLL);
-}
-__device__ __forceinline__ double fvalue(long long k, float) {
-  const int b = static_cast<int>(k);
-  return static_cast<double>(__int_as_float(b >= 0 ? b : (b ^ 0x7fffffff)));
-}
-__device__ __forceinline__ double fvalue(long long k, double) {
-  return __longlong_as_double(k >= 0 ? k : (k ^ 0x7fffffffffffffffLL));
-}
-
 // Block-wide maximum of a key (every thread gets the result).
 __device__ __forceinline__ long long block_max_key(long long m, long long* sh) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -71,41 +54,23 @@ struct FusedArgs {
   int* err;
 };
 
-// Maximum log-weight and NaN / +inf detection of x[0..3] (exact comparisons: binary32
-// values directly, binary64 values through their order-preserving keys on the integer pipe).
-template <int K>
-__device__ __forceinline__ void max_step(const float (&x)[K], long long& m, float& mf, bool& bad) {
-#pragma unroll
-  for (int q = 0; q < K; ++q) {
-    bad |= !(x[q] <= FLT_MAX);  // NaN or +inf (-inf and finite values pass)
-    mf = fmaxf(mf, x[q]);       // fmaxf skips NaN
-  }
-}
-template <int K>
-__device__ __forceinline__ void max_step(const double (&x)[K], long long& m, float&, bool& bad) {
-#pragma unroll
-  for (int q = 0; q < K; ++q) {
-    const bool nan = is_nan(x[q]);
-    bad |= nan || is_pos_inf(x[q]);
-    const long long k = fkey(x[q]);
-    if (!nan && k > m) m = k;
-  }
-}
-
-// Tiles per CTA up to which the record pass runs in reverse order (its records in shared
-// memory: 16 bytes each).
-constexpr int kZigTiles = 512;
-
 // CTA c owns the contiguous tiles [c T / G, (c+1) T / G) of the T tiles (G = gridDim.x <= T):
-//   phase 1  maximum over its particles -> barrier -> M = maximum over the CTAs;
-//   phase 2  tile totals s_t of its tiles (last to first, see below) and their exact running
-//            sum in fixed point (the in-range prefix of each tile, and the CTA total) -> barrier;
+//   phase 1  the records (m_t, s_t) of its tiles (tile_record: the tile's maximum and its
+//            weights' sum relative to it), last tile to first, and its largest m_t -> barrier;
+//   phase 2  M = maximum over the CTAs; T_t = s_t exp(m_t - M) (rec_scaled) of its tiles and
+//            their exact running sum in fixed point (the in-range prefix of each tile, and the
+//            CTA total) -> barrier;
+//            (compensated binary32, whose records must sum the weights exp(lw - M) themselves:
+//            phase 1 forms the maximum only and phase 2 the records relative to M, which then
+//            scale by exactly 1);
 //   phase 3  every CTA sums the exact CTA totals: those before it (CP) and all (the total);
 //            P_t = RN(CP + in-range prefix of t) for its tiles and P_{t1} = RN(CP + its own
 //            total), which is the P_{t1} the next CTA computes; W^N = RN(total), N / W^N;
-//   phase 4  emission of its tiles.
-// P_t is the exact sum of the tile totals before t rounded once, as in tile_prefix_compute, so
-// the results equal those of the separate kernels. Two grid barriers per call.
+//   phase 4  emission of its tiles, first to last: it starts on the tiles phase 1 read last (still in L2 when the log-weights exceed half of it).
+// The log-weights are read twice (phases 1 and 4; three times for compensated binary32), the
+// least the normaliser allows. P_t is the
+// exact sum of the T_t before t rounded once, as in tile_prefix_compute, so the results equal
+// those of the separate kernels. Two grid barriers per call.
 
 template <typename T, typename V, int SCHEME>
 __device__ __forceinline__ void fused_body(const T* __restrict__ lw, const FusedArgs& A,
@@ -114,6 +79,7 @@ __device__ __forceinline__ void fused_body(const T* __restrict__ lw, const Fused
   __shared__ float2 sh_tab[64];
   __shared__ long long sh_key[kWarps];
   __shared__ u128 sh_sum[2 * kWarps];
+  __shared__ u128 sh_f[kBlock];
   const int64_t N = A.N;
   const int T_tiles = static_cast<int>((N + kTile - 1) / kTile);
   const int G = static_cast<int>(gridDim.x), c = static_cast<int>(blockIdx.x);
@@ -122,82 +88,90 @@ __device__ __forceinline__ void fused_body(const T* __restrict__ lw, const Fused
   const int64_t e0 = static_cast<int64_t>(t0) * kTile;
   const int64_t e1 = min(static_cast<int64_t>(t1) * kTile, N);
   const bool vec = (reinterpret_cast<uintptr_t>(lw) & 15u) == 0;
+  if (threadIdx.x < 64) sh_tab[threadIdx.x] = kExp2Frac64[threadIdx.x];  // (read after a sync)
 
-  // ---- phase 1: maximum log-weight (and the Prepermute sentinel of the multinomial claims) --
+  // ---- phase 1: tile records, last to first (and the Prepermute sentinel of the multinomial
+  // claims); the next tile's log-weights are loaded while this one is reduced. Without
+  // kTileRef, the maximum only (the records follow once M is known) -----------------------
   {
-    long long m = fkey(neg_inf<T>());
-    float mf = -INFINITY;
+    long long cm = max_key(neg_inf<T>());
     bool bad = false;
-    // two groups of kPer in flight per thread and iteration
-    for (int64_t i0 = e0 + kPer * static_cast<int64_t>(threadIdx.x); i0 < e1;
-         i0 += 2 * kPer * kBlock) {
-      const int64_t i1 = i0 + kPer * kBlock;
-      T x[kPer], y[kPer];
-      load_per(lw, i0, 0, e1, vec, x);
-      load_per(lw, i1, 0, e1, vec, y);  // (past e1: -inf)
-      max_step(x, m, mf, bad);
-      max_step(y, m, mf, bad);
-      if constexpr (SCHEME == RS_MULTINOMIAL) {
-        if (A.d) {
-          int32_t sv[kPer];
+    const int64_t off = kPer * static_cast<int64_t>(threadIdx.x);
+    if constexpr (Path<T, V>::kTileRef) {
+      T xn[kPer];
+      if (t1 > t0) load_per(lw, static_cast<int64_t>(t1 - 1) * kTile + off, 0, N, vec, xn);
+      for (int t = t1 - 1; t >= t0; --t) {
+        T x[kPer];
 #pragma unroll
-          for (int q = 0; q < kPer; ++q) sv[q] = static_cast<int32_t>(N);
-          store_per(A.d + i0, sv, e1 - i0 < kPer ? static_cast<int>(e1 - i0) : kPer);
-          if (i1 < e1) store_per(A.d + i1, sv, e1 - i1 < kPer ? static_cast<int>(e1 - i1) : kPer);
+        for (int q = 0; q < kPer; ++q) x[q] = xn[q];
+        if (t > t0) load_per(lw, static_cast<int64_t>(t - 1) * kTile + off, 0, N, vec, xn);
+        const long long k = tile_record<T, V>(x, sh_tab, A.s_rec + t, sh, bad);
+        cm = k > cm ? k : cm;
+      }
+    } else {
+      float mf = -INFINITY;  // (binary32 inputs)
+      for (int t = t0; t < t1; ++t) {
+        T x[kPer];
+        load_per(lw, static_cast<int64_t>(t) * kTile + off, 0, N, vec, x);
+#pragma unroll
+        for (int q = 0; q < kPer; ++q) {
+          bad |= !(x[q] <= FLT_MAX);  // NaN or +inf
+          mf = fmaxf(mf, static_cast<float>(x[q]));
         }
       }
+      cm = block_max_key(max_key(mf), sh_key);
     }
-    if constexpr (sizeof(T) == 4) m = fkey(mf);
+    if constexpr (SCHEME == RS_MULTINOMIAL) {
+      if (A.d) {
+        int32_t sv[kPer];
+#pragma unroll
+        for (int q = 0; q < kPer; ++q) sv[q] = static_cast<int32_t>(N);
+        for (int64_t i0 = e0 + off; i0 < e1; i0 += kTile)
+          store_per(A.d + i0, sv, e1 - i0 < kPer ? static_cast<int>(e1 - i0) : kPer);
+      }
+    }
     if (bad) flag_error(A.err, RS_ERR_NONFINITE);
-    const long long bm = block_max_key(m, sh_key);
-    if (threadIdx.x == 0) A.blockmax[c] = fvalue(bm, T());
+    if (threadIdx.x == 0) A.blockmax[c] = key_to_double(cm, T());
   }
   grid_barrier(&A.g->bar, target, A.err);
   double M;
   {
-    long long m = fkey(-static_cast<double>(INFINITY));
+    long long m = max_key(-static_cast<double>(INFINITY));
     for (int b = threadIdx.x; b < G; b += kBlock) {
-      const long long y = fkey(__ldcg(A.blockmax + b));
+      const long long y = max_key(__ldcg(A.blockmax + b));
       m = y > m ? y : m;
     }
-    M = fvalue(block_max_key(m, sh_key), 0.0);
+    M = key_to_double(block_max_key(m, sh_key), 0.0);
   }
   const bool zero = !(M > -DBL_MAX);
   u128* LP = reinterpret_cast<u128*>(A.P_rec);  // in-range exact prefixes, then rounded P_t
 
-  // ---- phase 2: tile totals and their exact running sum ---------------------------------
-  // The tiles are visited last to first here and first to last in the other passes, so that
-  // each pass starts on the tiles the previous one touched last (still in L2 when the log-
-  // weights exceed half of it); the records wait in shared memory for the in-order sums.
+  // ---- phase 2: tile totals relative to M and their exact running sum ----------------------
   const WeightCtx wc = make_ctx<T, V>(zero ? 0.0 : M, sh_tab);
   if (!zero) {
-    if (t1 - t0 <= kZigTiles) {
-      __shared__ u128 sh_f[kZigTiles];
-      for (int t = t1 - 1; t >= t0; --t) {
-        const int64_t base = static_cast<int64_t>(t) * kTile;
-        const u128 f = tile_record<T, V>(lw, 0, N, base, wc, vec, A.s_rec + t, sh);
-        if (threadIdx.x == 0) sh_f[t - t0] = f;
-      }
-      if (threadIdx.x == 0) {
-        u128 run = 0;
-        for (int t = t0; t < t1; ++t) {
-          st_u128(LP + t, run);
-          run += sh_f[t - t0];
-        }
-        st_u128(A.agg + c, run);
-      }
-    } else {
-      u128 run = 0;  // meaningful in thread 0
-      for (int t = t0; t < t1; ++t) {
-        const int64_t base = static_cast<int64_t>(t) * kTile;
-        const u128 f = tile_record<T, V>(lw, 0, N, base, wc, vec, A.s_rec + t, sh);
-        if (threadIdx.x == 0) {
-          st_u128(LP + t, run);
-          run += f;
-        }
-      }
-      if (threadIdx.x == 0) st_u128(A.agg + c, run);
+    const T Mt = static_cast<T>(M);  // (exact: M is one of the log-weights)
+    if constexpr (!Path<T, V>::kTileRef) {  // the records, relative to M, last to first
+      bool bad = false;
+      for (int t = t1 - 1; t >= t0; --t)
+        tile_record<T, V>(lw, 0, N, static_cast<int64_t>(t) * kTile, sh_tab, vec, A.s_rec + t,
+                          sh, bad, max_key(Mt));
+      __syncthreads();  // (thread 0 stored them; all threads read them below)
     }
+    u128 run = 0;  // meaningful in thread 0
+    for (int tb = t0; tb < t1; tb += kBlock) {
+      const int t = tb + static_cast<int>(threadIdx.x);
+      if (t < t1) sh_f[threadIdx.x] = rec_fixed<T, V>(A.s_rec + t, Mt);
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        const int cnt = t1 - tb < kBlock ? t1 - tb : kBlock;
+        for (int k = 0; k < cnt; ++k) {
+          st_u128(LP + tb + k, run);
+          run += sh_f[k];
+        }
+      }
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) st_u128(A.agg + c, run);
   }
   grid_barrier(&A.g->bar, target, A.err);
 
@@ -363,7 +337,6 @@ const char* const kLblFused[4][3] = {
     {"fused_multinomial_f32c", "fused_stratified_f32c", "fused_systematic_f32c"},
     {"fused_multinomial_f64", "fused_stratified_f64", "fused_systematic_f64"},
     {"fused_multinomial_f64n", "fused_stratified_f64n", "fused_systematic_f64n"}};
-
 }  // namespace
 
 bool fused_available(const Scratch& s, int scheme, Acc acc) {

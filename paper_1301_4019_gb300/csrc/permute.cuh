@@ -82,74 +82,57 @@ __device__ __forceinline__ void permute_sorted_one(const int32_t* __restrict__ a
   }
 }
 
-// Up to four walks of Code 10 at once: walker q stands at slot x[q] with dx[q] = d[x[q]]
-// already loaded, and ends at the first unclaimed slot, where c receives val[q]. Each round
-// moves every live walker one step and then issues the loads of all live walkers together,
-// so up to four dependent chains are in flight per thread; the walks are disjoint (see
-// permute_one), so the writes are those of four separate walks.
-__device__ __forceinline__ void walk4(const int32_t* __restrict__ d, int32_t sentinel,
-                                      int32_t* __restrict__ c, int32_t (&x)[4],
-                                      int32_t (&dx)[4], const int32_t (&val)[4],
-                                      bool (&act)[4], int64_t n, int* err) {
-  const uint32_t us = static_cast<uint32_t>(sentinel);
-  bool bad = false;
-  for (uint32_t steps = 0; act[0] | act[1] | act[2] | act[3]; ++steps) {
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      if (!act[q]) continue;
-      const uint32_t v = static_cast<uint32_t>(dx[q]);
-      if (v >= us) {  // the sentinel (the walk ends here), or a corrupted d
-        if (v == us) c[x[q]] = val[q]; else bad = true;
-        act[q] = false;
-      } else {
-        x[q] = dx[q];
-      }
-    }
-    if (steps >= static_cast<uint32_t>(n)) {  // only a corrupted d can get here
-      bad = true;
-      break;
-    }
-#pragma unroll
-    for (int q = 0; q < 4; ++q)
-      if (act[q]) dx[q] = d[x[q]];
-  }
-  if (bad) flag_error(err, RS_ERR_ARG);
-}
+// Claims of Code 10 read from the Prepermute vector d (d[x] = the lowest position whose
+// ancestor is x, or the sentinel n).
+struct ClaimsOf {
+  const int32_t* __restrict__ d;
+  __device__ __forceinline__ int32_t operator()(int32_t x) const { return d[x]; }
+};
 
-// Walks of the four-slot kernels in two stages, for a whole warp: first every lane moves its
-// (up to) four walkers for at most kWalkRounds rounds (walk4's loop), which ends most walks;
-// then the walks still going are compacted into the warp's shared list `pend` (128 entries:
-// slot reached and value) and finished one walk per lane, 32 at a time. A warp otherwise
-// runs as many four-walker rounds as its longest walk takes, with most lanes predicated off.
-// Every walk still moves through the same slots and ends at the same unclaimed slot, so c is
-// the same as with walk4.
+// Walks of Code 10 for a whole warp, K walkers per lane: walker q stands at slot x[q] with
+// dx[q] = claim(x[q]) already loaded (claim: the Prepermute claim of a slot, the sentinel n
+// for an unclaimed one) and ends at the first unclaimed slot, where c receives val[q]. First
+// every lane moves its live walkers for at most kWalkRounds rounds, each round moving every
+// live walker one step and then issuing the claim loads of all of them together (up to K
+// dependent chains in flight per thread); then the walks still going are compacted into the
+// warp's shared list `pend` (32 K entries: slot reached and value) and finished one walk per
+// lane, 32 at a time. A warp otherwise runs as many rounds as its longest walk takes, with
+// most lanes predicated off. The walks start at distinct failed claims and are disjoint (see
+// permute_one), so every walk ends at its own unclaimed slot: c is the same as walking each
+// one alone. Called by all 32 lanes (lanes without walkers pass act = false).
 constexpr uint32_t kWalkRounds = 2;
 
-__device__ __forceinline__ void walk4_warp(const int32_t* __restrict__ d, int32_t sentinel,
-                                           int32_t* __restrict__ c, int32_t (&x)[4],
-                                           int32_t (&dx)[4], const int32_t (&val)[4],
-                                           bool (&act)[4], int64_t n, int2* pend, int* err) {
+template <int K, typename Claim>
+__device__ __forceinline__ void walk_warp(const Claim& claim, int32_t sentinel,
+                                          int32_t* __restrict__ c, int32_t (&x)[K],
+                                          int32_t (&dx)[K], const int32_t (&val)[K],
+                                          bool (&act)[K], int64_t n, int2* pend, int* err) {
   const uint32_t us = static_cast<uint32_t>(sentinel);
   const int lane = threadIdx.x & 31;
   bool bad = false;
-  for (uint32_t r = 0; r < kWalkRounds && (act[0] | act[1] | act[2] | act[3]); ++r) {
+  for (uint32_t r = 0; r < kWalkRounds; ++r) {
+    bool any = false;
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
+    for (int q = 0; q < K; ++q) {
       if (!act[q]) continue;
       const uint32_t v = static_cast<uint32_t>(dx[q]);
-      if (v >= us) {  // the sentinel (the walk ends here), or a corrupted d
+      if (v >= us) {  // the sentinel (the walk ends here), or a corrupted claim
         if (v == us) c[x[q]] = val[q]; else bad = true;
         act[q] = false;
       } else {
         x[q] = dx[q];
+        any = true;
       }
     }
+    if (!any) break;  // (per lane)
 #pragma unroll
-    for (int q = 0; q < 4; ++q)
-      if (act[q]) dx[q] = d[x[q]];
+    for (int q = 0; q < K; ++q)
+      if (act[q]) dx[q] = claim(x[q]);
   }
-  // compaction of the walks still going (each at slot x with d[x] loaded as dx)
-  const int mine = static_cast<int>(act[0]) + act[1] + act[2] + act[3];
+  // compaction of the walks still going (each at slot x with its claim loaded as dx)
+  int mine = 0;
+#pragma unroll
+  for (int q = 0; q < K; ++q) mine += static_cast<int>(act[q]);
   int incl = mine;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
@@ -160,7 +143,7 @@ __device__ __forceinline__ void walk4_warp(const int32_t* __restrict__ d, int32_
   if (total > 0) {
     int pos = incl - mine;
 #pragma unroll
-    for (int q = 0; q < 4; ++q)
+    for (int q = 0; q < K; ++q)
       if (act[q]) pend[pos++] = make_int2(x[q], val[q]);
     __syncwarp();
     for (int b = 0; b < total; b += 32) {
@@ -168,12 +151,12 @@ __device__ __forceinline__ void walk4_warp(const int32_t* __restrict__ d, int32_
         const int2 e = pend[b + lane];
         int32_t xs = e.x;
         for (int64_t steps = 0;; ++steps) {
-          const uint32_t v = static_cast<uint32_t>(d[xs]);
+          const uint32_t v = static_cast<uint32_t>(claim(xs));
           if (v == us) {
             c[xs] = e.y;
             break;
           }
-          if (v > us || steps > n) {  // only a corrupted d can get here
+          if (v > us || steps > n) {  // only a corrupted claim vector can get here
             bad = true;
             break;
           }

@@ -4,10 +4,12 @@
 // Each call makes three passes over the log-weights (Appendix E renormalisation, Code 4
 // primitives):
 //   1. max pass      : M = max_i lw_i (last-CTA reduction), NaN/+inf detection.
-//   2. tile-sum pass : per tile of kTile particles, the weights w_i = exp(lw_i - M) are
-//                      prefix-summed in the accumulator type; the tile total is written and
-//                      the last CTA to finish sums the tile totals exactly (128-bit fixed
-//                      point) into tile prefixes P_t, each rounded once, and the total W^N.
+//   2. tile-sum pass : per tile of kTile particles, its record: the tile's largest log-weight
+//                      m_t and the sum of exp(lw_i - m_t) in the accumulator type; the last
+//                      CTA to finish scales each record to M (T_t = s_t exp(m_t - M)) and sums
+//                      them exactly (128-bit fixed point) into tile prefixes P_t, each rounded
+//                      once, and the total W^N. (The records need no M, so the fused kernel
+//                      forms them in its first pass together with M.)
 //   3. emit pass     : the same tile scan is recomputed bit for bit, offset by P_t, and
 //                      turned into cumulative offspring O_i (systematic / stratified) with a
 //                      direct Code-11 scatter of the ancestors and the Prepermute claims; or
@@ -41,22 +43,6 @@ namespace {
 // Pass 1: maximum log-weight, compared through order-preserving integer keys (exact, and
 // no binary64 arithmetic). NaN is skipped (and flagged, as is +inf).
 // ---------------------------------------------------------------------------------------
-__device__ __forceinline__ long long max_key(float v) {
-  const int b = __float_as_int(v);
-  return static_cast<long long>(b >= 0 ? b : (b ^ 0x7fffffff));
-}
-__device__ __forceinline__ long long max_key(double v) {
-  const long long b = __double_as_longlong(v);
-  return b >= 0 ? b : (b ^ 0x7fffffffffffffffLL);
-}
-__device__ __forceinline__ double key_to_double(long long k, float) {
-  const int b = static_cast<int>(k);
-  return static_cast<double>(__int_as_float(b >= 0 ? b : (b ^ 0x7fffffff)));
-}
-__device__ __forceinline__ double key_to_double(long long k, double) {
-  return __longlong_as_double(k >= 0 ? k : (k ^ 0x7fffffffffffffffLL));
-}
-
 template <typename T>
 __global__ void __launch_bounds__(kBlock)
 max_kernel(const T* __restrict__ lw, int64_t N, ScanGlob* g, double* blockmax, int* err,
@@ -134,8 +120,9 @@ template <typename T, typename V>
 __device__ __noinline__ void tile_prefix_last_cta(const double2* s_rec, double2* P_rec, int nt,
                                                   int64_t N, ScanGlob* g, int* err,
                                                   double* log_total_out) {
-  tile_prefix_compute<V>(s_rec, P_rec, nt, N, reinterpret_cast<V*>(&g->S_raw),
-                            reinterpret_cast<V*>(&g->scale_raw), &g->S_d);
+  tile_prefix_compute<T, V>(s_rec, P_rec, nt, N, static_cast<T>(g->M),
+                            reinterpret_cast<V*>(&g->S_raw), reinterpret_cast<V*>(&g->scale_raw),
+                            &g->S_d);
   if (threadIdx.x == 0) {
     const double Sd = g->S_d;
     if (!(Sd > 0.0)) flag_error(err, RS_ERR_ZERO_WEIGHT);
@@ -156,16 +143,16 @@ tile_sum_kernel(const T* __restrict__ lw, int64_t N, ScanGlob* g, double2* s_rec
   __shared__ TileSh<V> sh;
   __shared__ float2 sh_tab[64];
   __shared__ bool am_last;
-  const double Md = g->M;
-  const bool zero = !(Md > -DBL_MAX);
   const int64_t base = static_cast<int64_t>(blockIdx.x) * kTile;
-  if (!zero) {
-    const WeightCtx wc = make_ctx<T, V>(Md, sh_tab);
-    const bool vec = (reinterpret_cast<uintptr_t>(lw) & 15u) == 0;
-    tile_record<T, V>(lw, 0, N, base, wc, vec, s_rec + blockIdx.x, sh);
-  } else if (threadIdx.x == 0) {
-    store_v<V>(s_rec + blockIdx.x, vzero(V()));
+  if (threadIdx.x < 64) sh_tab[threadIdx.x] = kExp2Frac64[threadIdx.x];  // (read after a sync)
+  const bool vec = (reinterpret_cast<uintptr_t>(lw) & 15u) == 0;
+  bool bad = false;  // (the max pass flags non-finite input)
+  long long ref = kTileMaxRef;
+  if constexpr (!Path<T, V>::kTileRef) {
+    const double Md = g->M;
+    if (Md > -DBL_MAX) ref = max_key(static_cast<T>(Md));  // (records relative to M)
   }
+  tile_record<T, V>(lw, 0, N, base, sh_tab, vec, s_rec + blockIdx.x, sh, bad, ref);
   if (threadIdx.x == 0) {
     __threadfence();
     const unsigned t = atomicAdd(&g->ticket_tile, 1u);

@@ -5,7 +5,9 @@
 #pragma once
 
 #include <cfloat>
+#include <climits>
 #include <cstdint>
+#include <type_traits>
 
 #include "common.cuh"
 #include "dfexp.cuh"
@@ -24,11 +26,17 @@ struct WeightCtx {
   const float2* tab;  // 2^(j/64) table in shared memory (double-float path)
 };
 
+// kTileRef: the tile records are formed relative to the tile's own maximum (tile_record), in
+// the same pass as the maximum of the whole sequence. Not for the compensated binary32 sums:
+// they must add exactly the binary32 weights exp(lw - M) that the emission scans, and weights
+// rounded to binary32 relative to another reference are other numbers; their records are
+// formed relative to M, after the maximum pass.
 template <typename T, typename V> struct Path;
 template <> struct Path<float, float> {
   using U = float;
   static constexpr int id = 0;
   static constexpr bool kTable = false;
+  static constexpr bool kTileRef = true;
   // exp_pinned(-inf) = 0, so a zero weight needs no test (M is finite here)
   __device__ static float weight(float x, const WeightCtx& c) {
     return exp_pinned(__fsub_rn(x, c.Mf));
@@ -39,6 +47,7 @@ template <> struct Path<float, float2> {
   using U = float;
   static constexpr int id = 1;
   static constexpr bool kTable = false;
+  static constexpr bool kTileRef = false;
   __device__ static float2 weight(float x, const WeightCtx& c) {
     return make_float2(exp_pinned(__fsub_rn(x, c.Mf)), 0.0f);
   }
@@ -48,6 +57,7 @@ template <> struct Path<double, float2> {
   using U = float2;
   static constexpr int id = 2;
   static constexpr bool kTable = true;
+  static constexpr bool kTileRef = true;
   __device__ static float2 weight(double x, const WeightCtx& c) {
     if (is_neg_inf(x)) return make_float2(0.0f, 0.0f);
     return exp_df(add22_accurate(split_f64(x), neg2(c.M2)), c.tab);
@@ -58,11 +68,56 @@ template <> struct Path<double, double> {
   using U = double;
   static constexpr int id = 3;
   static constexpr bool kTable = false;
+  static constexpr bool kTileRef = true;
   __device__ static double weight(double x, const WeightCtx& c) {
     return (x == neg_inf<double>()) ? 0.0 : exp_pinned(__dsub_rn(x, c.Md));
   }
   __device__ static U draw_u(uint4 x) { return u01_f64(x); }
 };
+
+// Order-preserving integer keys of the log-weights (exact comparisons on the integer pipe, no
+// binary64 arithmetic); binary32 keys are 32-bit patterns widened, binary64 keys 64-bit.
+__device__ __forceinline__ long long max_key(float v) {
+  const int b = __float_as_int(v);
+  return static_cast<long long>(b >= 0 ? b : (b ^ 0x7fffffff));
+}
+__device__ __forceinline__ long long max_key(double v) {
+  const long long b = __double_as_longlong(v);
+  return b >= 0 ? b : (b ^ 0x7fffffffffffffffLL);
+}
+__device__ __forceinline__ float key_to_float(long long k) {
+  const int b = static_cast<int>(k);
+  return __int_as_float(b >= 0 ? b : (b ^ 0x7fffffff));
+}
+__device__ __forceinline__ double key_to_double(long long k, float) {
+  return static_cast<double>(key_to_float(k));
+}
+__device__ __forceinline__ double key_to_double(long long k, double) {
+  return __longlong_as_double(k >= 0 ? k : (k ^ 0x7fffffffffffffffLL));
+}
+template <typename T> __device__ __forceinline__ T key_to(long long k);
+template <> __device__ __forceinline__ float key_to<float>(long long k) { return key_to_float(k); }
+template <> __device__ __forceinline__ double key_to<double>(long long k) {
+  return key_to_double(k, 0.0);
+}
+
+// The weight context of a reference log-weight given by its key (the fields its path reads,
+// from the bit pattern: no binary64 arithmetic).
+template <typename T, typename V>
+__device__ __forceinline__ WeightCtx ctx_of_key(long long k, const float2* tab) {
+  WeightCtx c;
+  c.tab = tab;
+  if constexpr (sizeof(T) == 4) {
+    c.Mf = key_to_float(k);
+    c.Md = 0.0;  // (unused by the binary32 paths)
+    c.M2 = make_float2(c.Mf, 0.0f);
+  } else {
+    c.Md = key_to_double(k, 0.0);
+    c.M2 = split_f64(c.Md);
+    c.Mf = c.M2.x;
+  }
+  return c;
+}
 
 // Builds the weight context (and stages the exp table in shared memory when needed).
 template <typename T, typename V>
@@ -344,21 +399,85 @@ __device__ __forceinline__ void block_sum2_u128(u128& a, u128& b, u128* sh) {
   }
 }
 
-// A tile's record: its total in the accumulator type; rec_fixed returns it in fixed point.
-template <typename V> __device__ __forceinline__ u128 rec_fixed(const double2* p) {
-  return to_fixed(load_v_cg<V>(p));
+// A tile's record (tile_record): its largest log-weight m_t, in the input type, in the first
+// 4 or 8 bytes of a double2, and s_t = the sum of its weights relative to m_t,
+// exp(lw_i - m_t), in the accumulator type, in the last 8 bytes.
+template <typename T, typename V>
+__device__ __forceinline__ void store_rec(double2* p, T m, V s) {
+  *reinterpret_cast<T*>(p) = m;
+  *reinterpret_cast<V*>(reinterpret_cast<char*>(p) + 8) = s;
+}
+__device__ __forceinline__ void from_bits(unsigned long long b, float& v) {
+  v = __uint_as_float(static_cast<unsigned int>(b));
+}
+__device__ __forceinline__ void from_bits(unsigned long long b, double& v) {
+  v = __longlong_as_double(static_cast<long long>(b));
+}
+__device__ __forceinline__ void from_bits(unsigned long long b, float2& v) {
+  v = make_float2(__uint_as_float(static_cast<unsigned int>(b)),
+                  __uint_as_float(static_cast<unsigned int>(b >> 32)));
+}
+template <typename T, typename V>
+__device__ __forceinline__ void load_rec(const double2* p, T& m, V& s) {
+  const double2 r = __ldcg(p);  // (written by another CTA, or earlier, in this launch)
+  from_bits(static_cast<unsigned long long>(__double_as_longlong(r.x)), m);
+  from_bits(static_cast<unsigned long long>(__double_as_longlong(r.y)), s);
 }
 
-// Prefixes of one sequence of nt tile totals s_t (block-level, every thread of the CTA calls
-// it): P_t = RN(s_0 + ... + s_{t-1}) for t = 0..nt, the exact sums taken in fixed point (each
+// The tile's total relative to the maximum M of the whole sequence: s_t exp(m_t - M), rounded
+// in the accumulator type, 0 for a tile of zero weights. The difference m_t - M is taken
+// exactly (a two-term sum: with it rounded, the relative error of the factor would grow with
+// |m_t - M|); binary32 and binary64 scale by exp_pinned(d_hi) (1 + d_lo), the two-float
+// accumulators by the two-float exp of the two-term difference, as their weights are formed.
+// M = +inf (flagged non-finite input) gives 0 for finite m_t and NaN for m_t = +inf, as the
+// weights exp(lw_i - M) themselves do.
+template <typename T, typename V>
+__device__ __forceinline__ V rec_scaled(const double2* p, T M) {
+  T m;
+  V sv;
+  load_rec<T, V>(p, m, sv);
+  if (!(m > neg_inf<T>())) return vzero(V());
+  if constexpr (std::is_same_v<V, float>) {
+    const float dh = __fsub_rn(m, M);
+    float dl = 0.0f;
+    if (dh > -INFINITY && dh < INFINITY) {  // TwoSum error of m - M
+      const float bb = __fsub_rn(dh, m);
+      dl = __fadd_rn(__fsub_rn(m, __fsub_rn(dh, bb)), __fsub_rn(-M, bb));
+    }
+    const float e = exp_pinned(dh);
+    return __fmul_rn(sv, __fmaf_rn(e, dl, e));
+  } else if constexpr (std::is_same_v<V, double>) {
+    const double dh = __dsub_rn(m, M);
+    double dl = 0.0;
+    if (dh > -DBL_MAX && dh < DBL_MAX) {
+      const double bb = __dsub_rn(dh, m);
+      dl = __dadd_rn(__dsub_rn(m, __dsub_rn(dh, bb)), __dsub_rn(-M, bb));
+    }
+    const double e = exp_pinned(dh);
+    return __dmul_rn(sv, __fma_rn(e, dl, e));
+  } else {  // two-float accumulators
+    float2 d;
+    if constexpr (sizeof(T) == 4) d = two_sum(m, -M);
+    else d = add22_accurate(split_f64(m), neg2(split_f64(M)));
+    return mul22(sv, exp_df(d, kExp2Frac64));
+  }
+}
+template <typename T, typename V>
+__device__ __forceinline__ u128 rec_fixed(const double2* p, T M) {
+  return to_fixed(rec_scaled<T, V>(p, M));
+}
+
+// Prefixes of one sequence of nt tile records, M the sequence's maximum log-weight (block-level,
+// every thread of the CTA calls it): with T_t = rec_scaled(record t), P_t = RN(T_0 + ... +
+// T_{t-1}) for t = 0..nt, the exact sums taken in fixed point (each
 // thread a contiguous chunk of tiles, then a warp scan and a scan over the warps: integer
 // adds, so the order does not matter). P is non-decreasing because the exact prefixes are and
 // rounding is monotone. The total S is P_nt, the cumulative weight the emission gives the
 // last particle (tile_cum_weights), so that particle receives O = N.
 // Thread 0 writes S, N / S and S (binary64) to the given pointers, then the CTA synchronises.
-template <typename V>
+template <typename T, typename V>
 __device__ void tile_prefix_compute(const double2* s_rec, double2* P_rec, int nt, int64_t N,
-                                    V* S_out, V* scale_out, double* Sd_out) {
+                                    T M, V* S_out, V* scale_out, double* Sd_out) {
   __shared__ u128 sh_sum[kWarps];
   constexpr int kGroup = 4;  // tile totals loaded together
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -369,7 +488,7 @@ __device__ void tile_prefix_compute(const double2* s_rec, double2* P_rec, int nt
   for (int g = t0; g < t1; g += kGroup) {
     u128 f[kGroup];
 #pragma unroll
-    for (int k = 0; k < kGroup; ++k) f[k] = (g + k < t1) ? rec_fixed<V>(s_rec + g + k) : 0;
+    for (int k = 0; k < kGroup; ++k) f[k] = (g + k < t1) ? rec_fixed<T, V>(s_rec + g + k, M) : 0;
 #pragma unroll
     for (int k = 0; k < kGroup; ++k) {
       local += f[k];
@@ -390,7 +509,7 @@ __device__ void tile_prefix_compute(const double2* s_rec, double2* P_rec, int nt
     u128 f[kGroup];
 #pragma unroll
     for (int k = 0; k < kGroup; ++k)
-      f[k] = (g == t0) ? cache[k] : ((g + k < t1) ? rec_fixed<V>(s_rec + g + k) : 0);
+      f[k] = (g == t0) ? cache[k] : ((g + k < t1) ? rec_fixed<T, V>(s_rec + g + k, M) : 0);
 #pragma unroll
     for (int k = 0; k < kGroup; ++k) {
       if (g + k < t1) {
@@ -412,10 +531,10 @@ __device__ void tile_prefix_compute(const double2* s_rec, double2* P_rec, int nt
 }
 
 // Shared scratch of the block-level tile functions.
-constexpr int kRunWin = 32 * kPer;  // output positions a warp writes per round of warp_runs
 
 template <typename V> struct TileSh {
   V tot[kWarps];
+  long long key[kWarps];
   alignas(16) int32_t win[kWarps][kRunWin];  // warp_runs windows
 };
 
@@ -477,32 +596,88 @@ __device__ __forceinline__ void warp_runs(const int32_t (&Oe)[kPer], int32_t pre
   }
 }
 
-// The tile's total (its record), stored by thread 0 at rec and returned in thread 0 as fixed
-// point (0 in the other threads). A plain block reduction: sequential over a thread's kPer
-// weights, butterfly over the warp, sequential over the warps. The tile prefixes only need an
-// accurate total, because the emission pins every tile's last particle to the next prefix
-// (tile_cum_weights).
+// The record of a tile (block-level) from this thread's kPer log-weights x of it (-inf outside
+// the sequence): m_t = the tile's largest log-weight (NaN skipped; NaN and +inf set `bad`) and
+// s_t = the sum of the weights relative to it, exp(x_i - m_t), in the accumulator type
+// (sequential over a thread's kPer, butterfly over the warp, sequential over the warps; 0 when
+// m_t = -inf). Thread 0 stores the record at rec; every thread gets the key of m_t. A record
+// does not depend on the sequence's maximum M, so the records are formed in the same pass as
+// M; T_t = s_t exp(m_t - M) (rec_scaled) is the tile's total relative to M. With a reference
+// key `ref` (the paths without kTileRef pass M's) m_t is that reference instead, and nothing
+// is flagged here (their maximum pass flags it): the record of M then scales by exactly 1.
+// The tile prefixes only need an accurate total, because the emission pins every tile's last
+// particle to the next prefix (tile_cum_weights).
+constexpr long long kTileMaxRef = LLONG_MIN;  // (no valid reference key: never that of a number)
+
 template <typename T, typename V>
-__device__ __forceinline__ u128 tile_record(const T* __restrict__ lw, int64_t lo, int64_t N,
-                                            int64_t base, const WeightCtx& wc, bool vec,
-                                            double2* rec, TileSh<V>& sh) {
+__device__ __forceinline__ long long tile_record(const T (&x)[kPer], const float2* tab,
+                                                 double2* rec, TileSh<V>& sh, bool& bad,
+                                                 long long ref = kTileMaxRef) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  T x[kPer];
-  load_per(lw, base + kPer * static_cast<int64_t>(threadIdx.x), lo, N, vec, x);
-  V t = vfrom_w(Path<T, V>::weight(x[0], wc), V());
+  long long m;
+  if (ref != kTileMaxRef) {  // (uniform) a given reference replaces the tile's maximum
+    m = ref;
+  } else if constexpr (sizeof(T) == 4) {
+    float mf = -INFINITY;
 #pragma unroll
-  for (int q = 1; q < kPer; ++q) t = vadd(t, vfrom_w(Path<T, V>::weight(x[q], wc), V()));
+    for (int q = 0; q < kPer; ++q) {
+      bad |= !(x[q] <= FLT_MAX);  // NaN or +inf (-inf and finite values pass)
+      mf = fmaxf(mf, x[q]);       // fmaxf skips NaN
+    }
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) t = vadd(t, vshfl_xor(t, o));  // same value in every lane
-  __syncthreads();  // sh.tot may still be read from the previous tile
+    for (int o = 16; o > 0; o >>= 1) mf = fmaxf(mf, __shfl_xor_sync(0xffffffffu, mf, o));
+    m = max_key(mf);
+  } else {
+    m = max_key(neg_inf<double>());
+#pragma unroll
+    for (int q = 0; q < kPer; ++q) {
+      const bool nan = is_nan(x[q]);
+      bad |= nan || is_pos_inf(x[q]);
+      const long long k = max_key(x[q]);
+      if (!nan && k > m) m = k;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const long long y = __shfl_xor_sync(0xffffffffu, m, o);
+      m = y > m ? y : m;
+    }
+  }
+  __syncthreads();  // sh may still be read from the previous tile
+  if (lane == 0) sh.key[warp] = m;
+  __syncthreads();
+  long long bm = sh.key[0];
+#pragma unroll
+  for (int k = 1; k < kWarps; ++k) bm = sh.key[k] > bm ? sh.key[k] : bm;
+  if (ref != kTileMaxRef) bm = ref;
+  V t = vzero(V());
+  if (bm > max_key(neg_inf<T>())) {  // (uniform over the block)
+    const WeightCtx wc = ctx_of_key<T, V>(bm, tab);
+    t = vfrom_w(Path<T, V>::weight(x[0], wc), V());
+#pragma unroll
+    for (int q = 1; q < kPer; ++q) t = vadd(t, vfrom_w(Path<T, V>::weight(x[q], wc), V()));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t = vadd(t, vshfl_xor(t, o));  // same value in every lane
+  }
   if (lane == 0) sh.tot[warp] = t;
   __syncthreads();
-  if (threadIdx.x != 0) return 0;
-  V tm = sh.tot[0];
+  if (threadIdx.x == 0) {
+    V tm = sh.tot[0];
 #pragma unroll
-  for (int k = 1; k < kWarps; ++k) tm = vadd(tm, sh.tot[k]);
-  store_v<V>(rec, tm);
-  return to_fixed(tm);
+    for (int k = 1; k < kWarps; ++k) tm = vadd(tm, sh.tot[k]);
+    store_rec<T, V>(rec, key_to<T>(bm), tm);
+  }
+  return bm;
+}
+
+// The same, loading the log-weights of the tile starting at `base` of the sequence [lo, N).
+template <typename T, typename V>
+__device__ __forceinline__ long long tile_record(const T* __restrict__ lw, int64_t lo, int64_t N,
+                                                 int64_t base, const float2* tab, bool vec,
+                                                 double2* rec, TileSh<V>& sh, bool& bad,
+                                                 long long ref = kTileMaxRef) {
+  T x[kPer];
+  load_per(lw, base + kPer * static_cast<int64_t>(threadIdx.x), lo, N, vec, x);
+  return tile_record<T, V>(x, tab, rec, sh, bad, ref);
 }
 
 // Cumulative weights W[q] of this thread's kPer particles of the tile starting at `base` of

@@ -6,8 +6,12 @@ order than the oracle's sequential sum, so an output may differ only where the d
 within the rounding bound of a cumulative-weight boundary. The bound used here:
 
   kernel:  |W_i - W*_i| <= KERNEL_C * eps_acc * W^N     (W* = exact prefix of the oracle's
-           weights; KERNEL_C covers the <= 30 roundings on any path of the tile scan, the
-           tile-prefix rounding and the final add; eps_acc = 2^-24 binary32, 2^-44 two-float,
+           weights; KERNEL_C covers the <= 45 roundings on any path of the tile scan, the
+           tile records (a tree sum of exp(lw - m_t), m_t the tile's maximum, scaled by
+           exp(m_t - M)), the tile-prefix rounding and the final add, and the records' weights
+           formed from lw - m_t where the oracle's use lw - M (two roundings of the argument, a
+           relative difference below |lw - M| eps per weight: about 20 eps at most for the
+           weights that carry the sums); eps_acc = 2^-24 binary32, 2^-44 two-float,
            2^-43 double-float over binary64 inputs (which also covers the 2^-40-relative
            weights of its exp), 2^-53 native binary64)
   oracle:  |W^o_i - W*_i| <= i * eps_dtype * W*_i        (sequential sum, Higham's bound)
@@ -16,7 +20,7 @@ and r = N W / W^N inherits N times these relative bounds (plus a few roundings o
 product). Mismatching positions are counted and returned so the tests can report them.
 
 For plain binary32 the bound in units of r, N (KERNEL_C + 4) 2^-24, exceeds 1/2 from about
-N = 2^18, where every position would count as near a boundary. There the kernel's cumulative
+N = 2^17, where every position would count as near a boundary. There the kernel's cumulative
 offspring are also held to the double-double oracle's: |O_k - O*| <= ceil(N (KERNEL_C + 4)
 eps_acc) + 1 at every position (truth_offset). Exact 0/1 weights give the bit-exact check at
 those sizes (test_gpu_exact_weights.py).
@@ -27,7 +31,7 @@ import numpy as np
 
 import oracle
 
-KERNEL_C = 40.0
+KERNEL_C = 64.0
 EPS = {"f32": 2.0 ** -24, "f32c": 2.0 ** -44, "f64": 2.0 ** -43, "f64n": 2.0 ** -53}
 EPS_DTYPE = {"f32": 2.0 ** -24, "f32c": 2.0 ** -24, "f64": 2.0 ** -53, "f64n": 2.0 ** -53}
 
