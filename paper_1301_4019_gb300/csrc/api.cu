@@ -135,7 +135,7 @@ int rs_create(rs_handle** out, int64_t max_n, int device) {
   ok &= cudaMalloc(&s.a_tmp, sizeof(int32_t) * max_n) == cudaSuccess;
   ok &= cudaMalloc(&s.W, 8 * static_cast<size_t>(max_n)) == cudaSuccess;
   ok &= cudaMalloc(&s.guide, sizeof(int32_t) * (max_n + 1)) == cudaSuccess;
-  ok &= cudaMalloc(&s.rec, sizeof(double2) * 2 * (s.max_tiles + 2)) == cudaSuccess;
+  ok &= cudaMalloc(&s.rec, sizeof(double2) * 2 * rsk::seg_cap(s.max_tiles)) == cudaSuccess;
   ok &= cudaMalloc(&s.blockmax, sizeof(double) * s.max_blocks) == cudaSuccess;
   ok &= cudaMalloc(&s.irec, sizeof(long long) * 2 * (s.max_tiles + 2)) == cudaSuccess;
   ok &= cudaMalloc(&s.glob, sizeof(rsk::ScanGlob)) == cudaSuccess;
@@ -148,8 +148,8 @@ int rs_create(rs_handle** out, int64_t max_n, int device) {
   ok &= cudaMalloc(&s.batch_fS, sizeof(double2) * mf) == cudaSuccess;
   ok &= cudaMalloc(&s.batch_fscale, sizeof(double2) * mf) == cudaSuccess;
   ok &= cudaMalloc(&s.batch_fSd, sizeof(double) * mf) == cudaSuccess;
-  ok &= cudaMalloc(&s.batch_s_rec, sizeof(double2) * tc) == cudaSuccess;
-  ok &= cudaMalloc(&s.batch_P_rec, sizeof(double2) * (tc + mf)) == cudaSuccess;
+  ok &= cudaMalloc(&s.batch_s_rec, sizeof(double2) * rsk::kWarps * tc) == cudaSuccess;
+  ok &= cudaMalloc(&s.batch_P_rec, sizeof(double2) * (rsk::kWarps * tc + mf)) == cudaSuccess;
   ok &= cudaMalloc(&s.err, sizeof(int)) == cudaSuccess;
   if (ok) {
     ok &= cudaMemset(s.glob, 0, sizeof(rsk::ScanGlob)) == cudaSuccess;

@@ -192,20 +192,22 @@ __device__ __forceinline__ double filter_M(const Batch& b, int f) {
 template <typename T, typename V>
 __global__ void __launch_bounds__(kBlock) batch_sum_kernel(const T* __restrict__ lw, Batch b) {
   pdl_wait();
-  __shared__ TileSh<V> sh;
   __shared__ float2 sh_tab[64];
   TileLoc L;
   if (!locate_tile(b, blockIdx.x, L)) return;
   if (!resampled(b.resample, L.f)) return;
-  if (threadIdx.x < 64) sh_tab[threadIdx.x] = kExp2Frac64[threadIdx.x];  // (read after a sync)
+  if (threadIdx.x < 64) sh_tab[threadIdx.x] = kExp2Frac64[threadIdx.x];
+  __syncthreads();
   const bool vec = (reinterpret_cast<uintptr_t>(lw) & 15u) == 0;
+  const int warp = threadIdx.x >> 5;
   bool bad = false;  // (the max pass flags non-finite input)
   long long ref = kTileMaxRef;
   if constexpr (!Path<T, V>::kTileRef) {
     const double M = filter_M(b, L.f);
     if (M > -DBL_MAX) ref = max_key(static_cast<T>(M));  // (records relative to M)
   }
-  tile_record<T, V>(lw, L.lo, L.hi, L.base, sh_tab, vec, b.s_rec + blockIdx.x, sh, bad, ref);
+  seg_record<T, V>(lw, L.lo, L.hi, L.base + kSeg * warp, sh_tab, vec,
+                   b.s_rec + kWarps * blockIdx.x + warp, bad, ref);
 }
 
 template <typename T, typename V>
@@ -222,9 +224,9 @@ __global__ void __launch_bounds__(kBlock) batch_prefix_kernel(Batch b) {
     }
     return;
   }
-  tile_prefix_compute<T, V>(b.s_rec + t0, b.P_rec + t0 + f, nt, n,
-                            static_cast<T>(filter_M(b, f)), reinterpret_cast<V*>(b.fS + f),
-                            reinterpret_cast<V*>(b.fscale + f), b.fSd + f);
+  seg_prefix_compute<T, V>(b.s_rec + kWarps * t0, b.P_rec + kWarps * t0 + f, kWarps * nt, n,
+                           static_cast<T>(filter_M(b, f)), reinterpret_cast<V*>(b.fS + f),
+                           reinterpret_cast<V*>(b.fscale + f), b.fSd + f);
 }
 
 template <typename T, typename V, int SCHEME>
@@ -232,7 +234,7 @@ __global__ void __launch_bounds__(kBlock)
 batch_emit_kernel(const T* __restrict__ lw, Batch b, Keys base_keys,
                   int32_t* __restrict__ a, int32_t* __restrict__ d, V* __restrict__ W) {
   pdl_wait();
-  __shared__ TileSh<V> sh;
+  __shared__ SegSh sh;
   __shared__ float2 sh_tab[64];
   TileLoc L;
   if (!locate_tile(b, blockIdx.x, L)) return;
@@ -250,20 +252,23 @@ batch_emit_kernel(const T* __restrict__ lw, Batch b, Keys base_keys,
   }
   const WeightCtx wc = make_ctx<T, V>(M, sh_tab);
   const bool vec = (reinterpret_cast<uintptr_t>(lw) & 15u) == 0;
-  const double2* P = b.P_rec + __ldg(b.tile_start + L.f) + L.f;
-  const V Pt = load_v_cg<V>(P + L.t), Pn = load_v_cg<V>(P + L.t + 1);
+  const int warp = threadIdx.x >> 5;
+  const double2* P = b.P_rec + kWarps * __ldg(b.tile_start + L.f) + L.f;
+  const int gl = kWarps * L.t + warp;  // this warp's segment within the filter
+  const V Ps = load_v_cg<V>(P + gl), Pn = load_v_cg<V>(P + gl + 1);
+  const int64_t base = L.base + kSeg * warp;
   if constexpr (SCHEME == RS_MULTINOMIAL) {
     if (d)  // claims of the search kernel start from the sentinel n
       for (int64_t e = L.base + threadIdx.x; e < L.hi && e < L.base + kTile; e += kBlock)
         d[e] = static_cast<int32_t>(n);
-    emit_tile_W<T, V, V>(lw, L.lo, L.hi, L.base, wc, vec, Pt, Pn, W, sh);
+    emit_seg_W<T, V, V>(lw, L.lo, L.hi, base, wc, vec, Ps, Pn, W);
   } else {
     const Keys keys = with_tag(base_keys, static_cast<uint32_t>(L.f), SCHEME);
     const typename Path<T, V>::U u_sys =
         SCHEME == RS_STRATIFIED ? typename Path<T, V>::U() : cta_uniform0<T, V>(keys);
-    emit_tile_cumoff<T, V, SCHEME == RS_STRATIFIED>(
-        lw, L.lo, L.hi, L.base, wc, vec, Pt, Pn, load_v_cg<V>(b.fS + L.f),
-        load_v_cg<V>(b.fscale + L.f), u_sys, keys, a, d, sh);
+    emit_seg_cumoff<T, V, SCHEME == RS_STRATIFIED>(
+        lw, L.lo, L.hi, base, wc, vec, Ps, Pn, load_v_cg<V>(b.fS + L.f),
+        load_v_cg<V>(b.fscale + L.f), u_sys, keys, a, d, sh.win[warp]);
   }
 }
 
@@ -272,12 +277,13 @@ batch_emit_kernel(const T* __restrict__ lw, Batch b, Keys base_keys,
 // plan kernel): CTA c owns the contiguous batch tiles [c T / G, (c+1) T / G) of the T tiles of
 // all filters together, and the CTAs meet at one grid barrier (two for compensated binary32,
 // whose records follow the filter maxima):
-//   phase 1  per tile, its record (tile_record: the tile's maximum log-weight and its weights'
-//            sum relative to it), the maxima combined per filter by an atomic max of keys;
+//   phase 1  per tile, the records of its segments (seg_record, each warp its own: the
+//            segment's maximum log-weight and its weights' sum relative to it), the maxima
+//            combined per filter by an atomic max of keys;
 //   phase 2  per tile, the exact sums of its filter's records scaled to the filter's maximum
-//            (those before it, and all), rounded once to P_t, P_{t+1} and W^N as
-//            tile_prefix_compute rounds them, then the emission.
-// Every tile goes through the same device functions and rounded prefixes as in the separate
+//            (those before each of its segments, and all), rounded once to the segment
+//            prefixes and W^N as seg_prefix_compute rounds them, then the emission.
+// Every segment goes through the same device functions and rounded prefixes as in the separate
 // batched kernels and the single-filter kernels, so filter f still equals rs_resample on its
 // slice with filter = f, bit for bit.
 // ---------------------------------------------------------------------------------------
@@ -285,11 +291,11 @@ template <typename T, typename V, int SCHEME>
 __global__ void __launch_bounds__(kBlock)
 batch_coop_kernel(const T* __restrict__ lw, Batch b, Keys base_keys, int32_t* __restrict__ a,
                   int32_t* __restrict__ d, V* __restrict__ W, GridBar* bar) {
-  __shared__ TileSh<V> sh;
+  __shared__ SegSh sh;
   __shared__ float2 sh_tab[64];
-  __shared__ long long sh_key[kWarps];
   __shared__ u128 sh_sum[2 * kWarps];
-  __shared__ double2 sh_Pt, sh_Pn, sh_S, sh_scale;
+  __shared__ u128 sh_f[kWarps];
+  __shared__ double2 sh_P[kWarps + 1], sh_S, sh_scale;
   __shared__ double sh_Sd;
   unsigned int target = 0;
   const int T_tiles = __ldcg(b.tile_start + b.F);
@@ -298,43 +304,39 @@ batch_coop_kernel(const T* __restrict__ lw, Batch b, Keys base_keys, int32_t* __
   const int t1 = static_cast<int>(static_cast<int64_t>(c + 1) * T_tiles / G);
   const bool vec = (reinterpret_cast<uintptr_t>(lw) & 15u) == 0;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (threadIdx.x < 64) sh_tab[threadIdx.x] = kExp2Frac64[threadIdx.x];
+  __syncthreads();
 
-  // ---- phase 1: tile records -> filter maxima ------------------------------------------------
-  // (compensated binary32: the maxima first, then the records relative to them)
-  if (threadIdx.x < 64) sh_tab[threadIdx.x] = kExp2Frac64[threadIdx.x];  // (read after a sync)
+  // ---- phase 1: segment records -> filter maxima (compensated binary32: the maxima only) ----
   {
     bool bad = false;
     for (int t = t0; t < t1; ++t) {
       TileLoc L;
       if (!locate_tile(b, t, L) || !resampled(b.resample, L.f)) continue;  // uniform per CTA
+      const int64_t base = L.base + kSeg * warp;
       long long k;
       if constexpr (Path<T, V>::kTileRef) {
-        k = tile_record<T, V>(lw, L.lo, L.hi, L.base, sh_tab, vec, b.s_rec + t, sh, bad);
+        k = seg_record<T, V>(lw, L.lo, L.hi, base, sh_tab, vec,
+                             b.s_rec + kWarps * t + warp, bad);
       } else {
-        const int64_t end = min(L.hi, L.base + kTile);
         T x[kPer];
-        load_per(lw, L.base + kPer * static_cast<int64_t>(threadIdx.x), L.lo, end, vec, x);
-        long long m = max_key(neg_inf<T>());
+        load_per(lw, base + kPer * static_cast<int64_t>(lane), L.lo, L.hi, vec, x);
+        k = max_key(neg_inf<T>());
 #pragma unroll
         for (int q = 0; q < kPer; ++q) {
           const bool nan = is_nan(x[q]);
           bad |= nan || is_pos_inf(x[q]);
           const long long kq = max_key(x[q]);
-          if (!nan && kq > m) m = kq;
+          if (!nan && kq > k) k = kq;
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
-          const long long y = __shfl_xor_sync(0xffffffffu, m, o);
-          m = y > m ? y : m;
+          const long long y = __shfl_xor_sync(0xffffffffu, k, o);
+          k = y > k ? y : k;
         }
-        __syncthreads();
-        if (lane == 0) sh_key[warp] = m;
-        __syncthreads();
-        k = sh_key[0];
-        for (int w = 1; w < kWarps; ++w) k = sh_key[w] > k ? sh_key[w] : k;
       }
       // stored as the key of the binary64 value, comparable across both input types
-      if (threadIdx.x == 0) atomicMax(b.fmax + L.f, max_key(key_to_double(k, T())));
+      if (lane == 0) atomicMax(b.fmax + L.f, max_key(key_to_double(k, T())));
     }
     if (bad) flag_error(b.err, RS_ERR_NONFINITE);
   }
@@ -345,13 +347,14 @@ batch_coop_kernel(const T* __restrict__ lw, Batch b, Keys base_keys, int32_t* __
       TileLoc L;
       if (!locate_tile(b, t, L) || !resampled(b.resample, L.f)) continue;
       const double M = filter_M(b, L.f);
-      tile_record<T, V>(lw, L.lo, L.hi, L.base, sh_tab, vec, b.s_rec + t, sh, bad,
-                        M > -DBL_MAX ? max_key(static_cast<T>(M)) : kTileMaxRef);
+      seg_record<T, V>(lw, L.lo, L.hi, L.base + kSeg * warp, sh_tab, vec,
+                       b.s_rec + kWarps * t + warp, bad,
+                       M > -DBL_MAX ? max_key(static_cast<T>(M)) : kTileMaxRef);
     }
     grid_barrier(bar, target, b.err);
   }
 
-  // ---- phase 2: prefixes of each tile from its filter's exact record sums, emission ---------
+  // ---- phase 2: prefixes of each segment from its filter's exact record sums, emission -------
   for (int t = t0; t < t1; ++t) {
     TileLoc L;
     if (!locate_tile(b, t, L)) continue;
@@ -363,24 +366,29 @@ batch_coop_kernel(const T* __restrict__ lw, Batch b, Keys base_keys, int32_t* __
       flag_error(b.err, RS_ERR_ZERO_WEIGHT);
     }
     double Sd = 0.0;
-    V Pt = vzero(V()), Pn = vzero(V()), S = vzero(V()), scale = vzero(V());
+    V Ps = vzero(V()), Pn = vzero(V()), S = vzero(V()), scale = vzero(V());
     if (active) {
-      const int first = __ldg(b.tile_start + L.f);
-      const int nt = __ldg(b.tile_start + L.f + 1) - first;
+      const int first = kWarps * __ldg(b.tile_start + L.f);  // the filter's first segment
+      const int nseg = kWarps * __ldg(b.tile_start + L.f + 1) - first;
+      const int own = kWarps * L.t;                          // this tile's first, in the filter
       const T Mt = static_cast<T>(M);  // (exact: M is one of the filter's log-weights)
       u128 part = 0, tot = 0;
-      for (int k = threadIdx.x; k < nt; k += kBlock) {
+      for (int k = threadIdx.x; k < nseg; k += kBlock) {
         const u128 v = rec_fixed<T, V>(b.s_rec + first + k, Mt);
         tot += v;
-        if (k < L.t) part += v;
+        if (k < own) part += v;
+        if (k >= own && k < own + kWarps) sh_f[k - own] = v;
       }
-      block_sum2_u128(part, tot, sh_sum);
+      block_sum2_u128(part, tot, sh_sum);  // (its barriers also publish sh_f)
       if (threadIdx.x == 0) {
         const V S0 = fixed_to(tot, V(), kFixFrac);
         const double Sd0 = vto_double(S0);
         const V sc0 = vfrom_double(__ddiv_rn(static_cast<double>(n), Sd0), V());
-        store_v<V>(&sh_Pt, fixed_to(part, V(), kFixFrac));
-        store_v<V>(&sh_Pn, fixed_to(part + rec_fixed<T, V>(b.s_rec + t, Mt), V(), kFixFrac));
+        u128 p = part;
+        for (int w = 0; w <= kWarps; ++w) {
+          store_v<V>(&sh_P[w], fixed_to(p, V(), kFixFrac));
+          if (w < kWarps) p += sh_f[w];
+        }
         store_v<V>(&sh_S, S0);
         store_v<V>(&sh_scale, sc0);
         sh_Sd = Sd0;
@@ -391,8 +399,8 @@ batch_coop_kernel(const T* __restrict__ lw, Batch b, Keys base_keys, int32_t* __
         }
       }
       __syncthreads();
-      Pt = load_v<V>(&sh_Pt);
-      Pn = load_v<V>(&sh_Pn);
+      Ps = load_v<V>(&sh_P[warp]);
+      Pn = load_v<V>(&sh_P[warp + 1]);
       S = load_v<V>(&sh_S);
       scale = load_v<V>(&sh_scale);
       Sd = sh_Sd;
@@ -407,17 +415,18 @@ batch_coop_kernel(const T* __restrict__ lw, Batch b, Keys base_keys, int32_t* __
       continue;
     }
     const WeightCtx wc = make_ctx<T, V>(M, sh_tab);
+    const int64_t base = L.base + kSeg * warp;
     if constexpr (SCHEME == RS_MULTINOMIAL) {
       if (d)  // claims of the search kernel start from the sentinel n
         for (int64_t e = L.base + threadIdx.x; e < L.hi && e < L.base + kTile; e += kBlock)
           d[e] = static_cast<int32_t>(n);
-      emit_tile_W<T, V, V>(lw, L.lo, L.hi, L.base, wc, vec, Pt, Pn, W, sh);
+      emit_seg_W<T, V, V>(lw, L.lo, L.hi, base, wc, vec, Ps, Pn, W);
     } else {
       const Keys keys = with_tag(base_keys, static_cast<uint32_t>(L.f), SCHEME);
       const typename Path<T, V>::U u_sys =
           SCHEME == RS_STRATIFIED ? typename Path<T, V>::U() : cta_uniform0<T, V>(keys);
-      emit_tile_cumoff<T, V, SCHEME == RS_STRATIFIED>(lw, L.lo, L.hi, L.base, wc, vec, Pt, Pn,
-                                                       S, scale, u_sys, keys, a, d, sh);
+      emit_seg_cumoff<T, V, SCHEME == RS_STRATIFIED>(lw, L.lo, L.hi, base, wc, vec, Ps, Pn, S,
+                                                      scale, u_sys, keys, a, d, sh.win[warp]);
     }
   }
   grid_exit(bar, target);

@@ -15,6 +15,9 @@ constexpr int kPer = 8;              // consecutive particles per thread in a sc
 constexpr int kTile = kBlock * kPer; // particles per CTA tile of the scan kernels (2048)
 constexpr int kRunWin = 32 * kPer;  // positions a warp covers per round of Code 11 (warp_runs)
 constexpr int kWarps = kBlock / 32;  // 8 warps
+// Entries of each of the two record blocks of the scan scratch (records, then prefixes): one
+// per warp segment of kRunWin particles (kWarps per tile), plus the total's prefix and a spare.
+constexpr int64_t seg_cap(int64_t max_tiles) { return int64_t{kWarps} * max_tiles + 2; }
 
 // ---------------------------------------------------------------------------------------
 // Device status word: holds -status of the highest-priority error seen (lowest value),

@@ -1,8 +1,9 @@
 // fused.cu -- the passes of the multinomial, stratified and systematic resamplers of one filter
-// (max, tile totals, tile prefixes, emission) as one persistent cooperative kernel.
+// (maximum and segment records, segment prefixes, emission) as one persistent cooperative
+// kernel.
 //
 // Each CTA owns a contiguous range of tiles; the CTAs are all resident at once (cooperative
-// launch) and meet at grid-wide barriers between the phases (see fused_body). The tile
+// launch) and meet at grid-wide barriers between the phases (see fused_body). The segment
 // prefixes are exact fixed-point sums, so they can be assembled in parallel from per-CTA
 // totals instead of by one CTA, and each phase calls the same device functions as the
 // separate kernels on the same tiles: the results are identical. The latency-bound
@@ -46,8 +47,8 @@ struct FusedArgs {
   int32_t* d;      // Prepermute claims, or nullptr
   void* W;         // multinomial cumulative weights
   int32_t* guide;  // multinomial guide table
-  double2* s_rec;  // tile totals (accumulator type)
-  double2* P_rec;  // tile prefixes: exact in-range prefixes (u128), then rounded P_t
+  double2* s_rec;  // segment records
+  double2* P_rec;  // segment prefixes: exact in-range prefixes (u128), then rounded P_g
   u128* agg;       // per-CTA exact totals (gridDim.x entries)
   ScanGlob* g;
   double* blockmax;  // per-CTA maxima (gridDim.x entries)
@@ -55,48 +56,53 @@ struct FusedArgs {
 };
 
 // CTA c owns the contiguous tiles [c T / G, (c+1) T / G) of the T tiles (G = gridDim.x <= T):
-//   phase 1  the records (m_t, s_t) of its tiles (tile_record: the tile's maximum and its
-//            weights' sum relative to it), last tile to first, and its largest m_t -> barrier;
-//   phase 2  M = maximum over the CTAs; T_t = s_t exp(m_t - M) (rec_scaled) of its tiles and
-//            their exact running sum in fixed point (the in-range prefix of each tile, and the
-//            CTA total) -> barrier;
+//   phase 1  the records (m_g, s_g) of its tiles' segments (seg_record, each warp its own:
+//            the segment's maximum and its weights' sum relative to it), last tile to first,
+//            and its largest m_g -> barrier;
+//   phase 2  M = maximum over the CTAs; T_g = s_g exp(m_g - M) (rec_scaled) of its segments
+//            and their exact running sum in fixed point (the in-range prefix of each segment,
+//            and the CTA total) -> barrier;
 //            (compensated binary32, whose records must sum the weights exp(lw - M) themselves:
 //            phase 1 forms the maximum only and phase 2 the records relative to M, which then
 //            scale by exactly 1);
 //   phase 3  every CTA sums the exact CTA totals: those before it (CP) and all (the total);
-//            P_t = RN(CP + in-range prefix of t) for its tiles and P_{t1} = RN(CP + its own
-//            total), which is the P_{t1} the next CTA computes; W^N = RN(total), N / W^N;
-//   phase 4  emission of its tiles, first to last: it starts on the tiles phase 1 read last (still in L2 when the log-weights exceed half of it).
-// The log-weights are read twice (phases 1 and 4; three times for compensated binary32), the
-// least the normaliser allows. P_t is the
-// exact sum of the T_t before t rounded once, as in tile_prefix_compute, so the results equal
+//            P_g = RN(CP + in-range prefix of g) for its segments and P_{g1} = RN(CP + its
+//            own total), which is the P_{g1} the next CTA computes; W^N = RN(total), N / W^N;
+//   phase 4  emission of its tiles, first to last (it starts on the tiles phase 1 read last,
+//            still in L2 when the log-weights exceed half of it), each warp its segments.
+// Phases 1 and 4 are warp-level work only: no block barrier per tile. The log-weights are read
+// twice (phases 1 and 4; three times for compensated binary32), the least the normaliser
+// allows. P_g is the exact sum of the T before g rounded once, as in seg_prefix_compute, so the
+// results equal
 // those of the separate kernels. Two grid barriers per call.
 
 template <typename T, typename V, int SCHEME>
 __device__ __forceinline__ void fused_body(const T* __restrict__ lw, const FusedArgs& A,
                                            unsigned int& target) {
-  __shared__ TileSh<V> sh;
+  __shared__ SegSh sh;
   __shared__ float2 sh_tab[64];
   __shared__ long long sh_key[kWarps];
   __shared__ u128 sh_sum[2 * kWarps];
-  __shared__ u128 sh_f[kBlock];
   const int64_t N = A.N;
   const int T_tiles = static_cast<int>((N + kTile - 1) / kTile);
   const int G = static_cast<int>(gridDim.x), c = static_cast<int>(blockIdx.x);
   const int t0 = static_cast<int>(static_cast<int64_t>(c) * T_tiles / G);
   const int t1 = static_cast<int>(static_cast<int64_t>(c + 1) * T_tiles / G);
+  const int g0 = kWarps * t0, g1 = kWarps * t1;  // this CTA's segments
+  const int warp = threadIdx.x >> 5;
   const int64_t e0 = static_cast<int64_t>(t0) * kTile;
   const int64_t e1 = min(static_cast<int64_t>(t1) * kTile, N);
+  const int64_t off = kPer * static_cast<int64_t>(threadIdx.x);  // (= kSeg warp + kPer lane)
   const bool vec = (reinterpret_cast<uintptr_t>(lw) & 15u) == 0;
-  if (threadIdx.x < 64) sh_tab[threadIdx.x] = kExp2Frac64[threadIdx.x];  // (read after a sync)
+  if (threadIdx.x < 64) sh_tab[threadIdx.x] = kExp2Frac64[threadIdx.x];
+  __syncthreads();
 
-  // ---- phase 1: tile records, last to first (and the Prepermute sentinel of the multinomial
-  // claims); the next tile's log-weights are loaded while this one is reduced. Without
-  // kTileRef, the maximum only (the records follow once M is known) -----------------------
+  // ---- phase 1: segment records, last tile to first (and the Prepermute sentinel of the
+  // multinomial claims); the next tile's log-weights are loaded while this one is reduced.
+  // Without kTileRef, the maximum only (the records follow once M is known) ----------------
   {
     long long cm = max_key(neg_inf<T>());
     bool bad = false;
-    const int64_t off = kPer * static_cast<int64_t>(threadIdx.x);
     if constexpr (Path<T, V>::kTileRef) {
       T xn[kPer];
       if (t1 > t0) load_per(lw, static_cast<int64_t>(t1 - 1) * kTile + off, 0, N, vec, xn);
@@ -105,7 +111,7 @@ __device__ __forceinline__ void fused_body(const T* __restrict__ lw, const Fused
 #pragma unroll
         for (int q = 0; q < kPer; ++q) x[q] = xn[q];
         if (t > t0) load_per(lw, static_cast<int64_t>(t - 1) * kTile + off, 0, N, vec, xn);
-        const long long k = tile_record<T, V>(x, sh_tab, A.s_rec + t, sh, bad);
+        const long long k = seg_record<T, V>(x, sh_tab, A.s_rec + kWarps * t + warp, bad);
         cm = k > cm ? k : cm;
       }
     } else {
@@ -119,7 +125,7 @@ __device__ __forceinline__ void fused_body(const T* __restrict__ lw, const Fused
           mf = fmaxf(mf, static_cast<float>(x[q]));
         }
       }
-      cm = block_max_key(max_key(mf), sh_key);
+      cm = max_key(mf);
     }
     if constexpr (SCHEME == RS_MULTINOMIAL) {
       if (A.d) {
@@ -131,6 +137,7 @@ __device__ __forceinline__ void fused_body(const T* __restrict__ lw, const Fused
       }
     }
     if (bad) flag_error(A.err, RS_ERR_NONFINITE);
+    cm = block_max_key(cm, sh_key);
     if (threadIdx.x == 0) A.blockmax[c] = key_to_double(cm, T());
   }
   grid_barrier(&A.g->bar, target, A.err);
@@ -144,38 +151,33 @@ __device__ __forceinline__ void fused_body(const T* __restrict__ lw, const Fused
     M = key_to_double(block_max_key(m, sh_key), 0.0);
   }
   const bool zero = !(M > -DBL_MAX);
-  u128* LP = reinterpret_cast<u128*>(A.P_rec);  // in-range exact prefixes, then rounded P_t
+  u128* LP = reinterpret_cast<u128*>(A.P_rec);  // in-range exact prefixes, then rounded P_g
 
-  // ---- phase 2: tile totals relative to M and their exact running sum ----------------------
+  // ---- phase 2: segment totals relative to M and their exact running sum -------------------
   const WeightCtx wc = make_ctx<T, V>(zero ? 0.0 : M, sh_tab);
   if (!zero) {
     const T Mt = static_cast<T>(M);  // (exact: M is one of the log-weights)
-    if constexpr (!Path<T, V>::kTileRef) {  // the records, relative to M, last to first
+    if constexpr (!Path<T, V>::kTileRef) {  // the records, relative to M, last tile to first
       bool bad = false;
       for (int t = t1 - 1; t >= t0; --t)
-        tile_record<T, V>(lw, 0, N, static_cast<int64_t>(t) * kTile, sh_tab, vec, A.s_rec + t,
-                          sh, bad, max_key(Mt));
-      __syncthreads();  // (thread 0 stored them; all threads read them below)
+        seg_record<T, V>(lw, 0, N, static_cast<int64_t>(t) * kTile + kSeg * warp, sh_tab, vec,
+                         A.s_rec + kWarps * t + warp, bad, max_key(Mt));
+      __syncthreads();  // (lane 0 of each warp stored them; all threads read them below)
     }
-    u128 run = 0;  // meaningful in thread 0
-    for (int tb = t0; tb < t1; tb += kBlock) {
-      const int t = tb + static_cast<int>(threadIdx.x);
-      if (t < t1) sh_f[threadIdx.x] = rec_fixed<T, V>(A.s_rec + t, Mt);
-      __syncthreads();
-      if (threadIdx.x == 0) {
-        const int cnt = t1 - tb < kBlock ? t1 - tb : kBlock;
-        for (int k = 0; k < cnt; ++k) {
-          st_u128(LP + tb + k, run);
-          run += sh_f[k];
-        }
-      }
-      __syncthreads();
+    u128 run = 0;  // (the same in every thread)
+    for (int gb = g0; gb < g1; gb += kBlock) {
+      const int g = gb + static_cast<int>(threadIdx.x);
+      const u128 f = g < g1 ? rec_fixed<T, V>(A.s_rec + g, Mt) : static_cast<u128>(0);
+      u128 tot;
+      const u128 ex = block_excl_scan_u128(f, sh_sum, tot);
+      if (g < g1) st_u128(LP + g, run + ex);
+      run += tot;
     }
     if (threadIdx.x == 0) st_u128(A.agg + c, run);
   }
   grid_barrier(&A.g->bar, target, A.err);
 
-  // ---- phase 3: the total and this CTA's tile prefixes --------------------------------------
+  // ---- phase 3: the total and this CTA's segment prefixes ----------------------------------
   if (zero) {  // all weights zero (flagged): every particle keeps itself
     if (c == 0 && threadIdx.x == 0) {
       A.g->S_d = 0.0;
@@ -237,19 +239,21 @@ __device__ __forceinline__ void fused_body(const T* __restrict__ lw, const Fused
     }
     return;
   }
-  // rounded prefixes of this CTA's tiles, in place of their exact in-range prefixes (each
-  // slot is read and then overwritten by the same thread), and of the next CTA's first tile,
-  // which that CTA owns: kept in shared memory (the last CTA also writes the total's slot)
+  // rounded prefixes of this CTA's segments, in place of their exact in-range prefixes (each
+  // slot is read and then overwritten by the same thread), and of the next CTA's first
+  // segment, which that CTA owns: kept in shared memory (the last CTA also writes the total's
+  // slot)
   __shared__ double2 sh_pend;
-  for (int t = t0 + threadIdx.x; t <= t1; t += kBlock) {
-    const u128 lp = (t < t1) ? ld_u128_cg(LP + t) : ld_u128_cg(A.agg + c);
+  for (int g = g0 + threadIdx.x; g <= g1; g += kBlock) {
+    const u128 lp = (g < g1) ? ld_u128_cg(LP + g) : ld_u128_cg(A.agg + c);
     const V P = fixed_to(CP + lp, V(), kFixFrac);
-    if (t < t1 || c == G - 1) store_v<V>(A.P_rec + t, P);
-    if (t == t1) store_v<V>(&sh_pend, P);
+    if (g < g1 || c == G - 1) store_v<V>(A.P_rec + g, P);
+    if (g == g1) store_v<V>(&sh_pend, P);
   }
   __syncthreads();
 
-  // ---- phase 4: emission of this CTA's tiles -----------------------------------------------
+  // ---- phase 4: emission of this CTA's tiles, each warp its own segments (no block-level
+  // synchronisation) -------------------------------------------------------------------------
   typename Path<T, V>::U u_sys = typename Path<T, V>::U();
   Guide gd;
   if constexpr (SCHEME == RS_MULTINOMIAL) {
@@ -258,15 +262,16 @@ __device__ __forceinline__ void fused_body(const T* __restrict__ lw, const Fused
     u_sys = cta_uniform0<T, V>(A.keys);
   }
   for (int t = t0; t < t1; ++t) {
-    const int64_t base = static_cast<int64_t>(t) * kTile;
-    const V Pt = load_v_cg<V>(A.P_rec + t);
-    const V Pn = (t + 1 < t1) ? load_v_cg<V>(A.P_rec + t + 1) : load_v<V>(&sh_pend);
+    const int g = kWarps * t + warp;
+    const int64_t base = static_cast<int64_t>(t) * kTile + kSeg * warp;
+    const V Ps = load_v_cg<V>(A.P_rec + g);
+    const V Pn = (g + 1 < g1) ? load_v_cg<V>(A.P_rec + g + 1) : load_v<V>(&sh_pend);
     if constexpr (SCHEME == RS_MULTINOMIAL) {
-      emit_tile_W_guide<T, V>(lw, 0, N, base, wc, vec, Pt, Pn, gd, static_cast<V*>(A.W),
-                              A.guide, sh);
+      emit_seg_W_guide<T, V>(lw, 0, N, base, wc, vec, Ps, Pn, gd, static_cast<V*>(A.W), A.guide,
+                             sh.win[warp]);
     } else {
-      emit_tile_cumoff<T, V, SCHEME == RS_STRATIFIED>(lw, 0, N, base, wc, vec, Pt, Pn, S, scale,
-                                                       u_sys, A.keys, A.a, A.d, sh);
+      emit_seg_cumoff<T, V, SCHEME == RS_STRATIFIED>(lw, 0, N, base, wc, vec, Ps, Pn, S, scale,
+                                                      u_sys, A.keys, A.a, A.d, sh.win[warp]);
     }
   }
 }
@@ -361,7 +366,7 @@ cudaError_t launch_fused_passes(const Scratch& s, int scheme, Acc acc, const voi
   A.W = s.W;
   A.guide = s.guide;
   A.s_rec = s.rec;
-  A.P_rec = s.rec + (s.max_tiles + 2);
+  A.P_rec = s.rec + seg_cap(s.max_tiles);
   A.agg = reinterpret_cast<u128*>(s.irec);  // (max_tiles + 2) entries >= gridDim.x
   A.g = s.glob;
   A.blockmax = s.blockmax;

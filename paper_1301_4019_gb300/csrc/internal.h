@@ -67,7 +67,7 @@ struct Scratch {
   int32_t* a_tmp;    // unpermuted ancestors, max_n
   void* W;           // cumulative weights of the multinomial scheme, 8 * max_n bytes
   int32_t* guide;    // guide table of the multinomial search, max_n + 1
-  double2* rec;      // per-tile records: sums then prefixes (two blocks of max_tiles + 2)
+  double2* rec;      // per-segment records, then prefixes (two blocks of seg_cap(max_tiles))
   double* blockmax;  // per-CTA maxima of the max pass
   long long* irec;   // per-tile records of the integer scan (2 * (max_tiles + 2))
   ScanGlob* glob;
@@ -78,8 +78,8 @@ struct Scratch {
   double2* batch_fS;          // max_filters
   double2* batch_fscale;      // max_filters
   double* batch_fSd;          // max_filters
-  double2* batch_s_rec;       // batch_tile_cap
-  double2* batch_P_rec;       // batch_tile_cap + max_filters
+  double2* batch_s_rec;       // kWarps * batch_tile_cap (one per segment)
+  double2* batch_P_rec;       // kWarps * batch_tile_cap + max_filters
   int64_t max_filters;        // max(1024, max_n / 16)
   int64_t batch_tile_cap;     // max_n / kTile + max_filters + 1
   int64_t max_n;

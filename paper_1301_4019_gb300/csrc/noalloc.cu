@@ -29,8 +29,8 @@ constexpr size_t kOffGlob = 0;
 constexpr size_t kOffErr = align256(kOffGlob + sizeof(ScanGlob));
 constexpr size_t kOffBlockmax = align256(kOffErr + sizeof(int));
 constexpr size_t kOffRec = align256(kOffBlockmax + sizeof(double) * kNoAllocMaxBlocks);
-constexpr size_t kNoAllocBytes = align256(kOffRec + sizeof(double2) * 2 * (kNoAllocMaxTiles + 2));
-static_assert(kNoAllocBytes <= 160 * 1024, "the static scratch must stay modest");
+constexpr size_t kNoAllocBytes = align256(kOffRec + sizeof(double2) * 2 * seg_cap(kNoAllocMaxTiles));
+static_assert(kNoAllocBytes <= 640 * 1024, "the static scratch must stay modest");
 
 // Shared by every call on a device; zero at module load.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];

@@ -112,17 +112,17 @@ max_kernel(const T* __restrict__ lw, int64_t N, ScanGlob* g, double* blockmax, i
 }
 
 // ---------------------------------------------------------------------------------------
-// Pass 2: tile sums and, in the last CTA, tile prefixes.
+// Pass 2: segment records (each warp its own) and, in the last CTA, the segment prefixes.
 // ---------------------------------------------------------------------------------------
 // The last CTA's work, kept out of line so that its registers do not limit the occupancy of
 // the tile work.
 template <typename T, typename V>
-__device__ __noinline__ void tile_prefix_last_cta(const double2* s_rec, double2* P_rec, int nt,
-                                                  int64_t N, ScanGlob* g, int* err,
-                                                  double* log_total_out) {
-  tile_prefix_compute<T, V>(s_rec, P_rec, nt, N, static_cast<T>(g->M),
-                            reinterpret_cast<V*>(&g->S_raw), reinterpret_cast<V*>(&g->scale_raw),
-                            &g->S_d);
+__device__ __noinline__ void seg_prefix_last_cta(const double2* s_rec, double2* P_rec, int nseg,
+                                                 int64_t N, ScanGlob* g, int* err,
+                                                 double* log_total_out) {
+  seg_prefix_compute<T, V>(s_rec, P_rec, nseg, N, static_cast<T>(g->M),
+                           reinterpret_cast<V*>(&g->S_raw), reinterpret_cast<V*>(&g->scale_raw),
+                           &g->S_d);
   if (threadIdx.x == 0) {
     const double Sd = g->S_d;
     if (!(Sd > 0.0)) flag_error(err, RS_ERR_ZERO_WEIGHT);
@@ -140,11 +140,12 @@ __global__ void __launch_bounds__(kBlock, 4)
 tile_sum_kernel(const T* __restrict__ lw, int64_t N, ScanGlob* g, double2* s_rec,
                 double2* P_rec, int* err, double* log_total_out) {
   pdl_wait();
-  __shared__ TileSh<V> sh;
   __shared__ float2 sh_tab[64];
   __shared__ bool am_last;
-  const int64_t base = static_cast<int64_t>(blockIdx.x) * kTile;
-  if (threadIdx.x < 64) sh_tab[threadIdx.x] = kExp2Frac64[threadIdx.x];  // (read after a sync)
+  const int warp = threadIdx.x >> 5;
+  const int64_t base = static_cast<int64_t>(blockIdx.x) * kTile + kSeg * warp;
+  if (threadIdx.x < 64) sh_tab[threadIdx.x] = kExp2Frac64[threadIdx.x];
+  __syncthreads();
   const bool vec = (reinterpret_cast<uintptr_t>(lw) & 15u) == 0;
   bool bad = false;  // (the max pass flags non-finite input)
   long long ref = kTileMaxRef;
@@ -152,7 +153,8 @@ tile_sum_kernel(const T* __restrict__ lw, int64_t N, ScanGlob* g, double2* s_rec
     const double Md = g->M;
     if (Md > -DBL_MAX) ref = max_key(static_cast<T>(Md));  // (records relative to M)
   }
-  tile_record<T, V>(lw, 0, N, base, sh_tab, vec, s_rec + blockIdx.x, sh, bad, ref);
+  seg_record<T, V>(lw, 0, N, base, sh_tab, vec, s_rec + kWarps * blockIdx.x + warp, bad, ref);
+  __syncthreads();
   if (threadIdx.x == 0) {
     __threadfence();
     const unsigned t = atomicAdd(&g->ticket_tile, 1u);
@@ -161,11 +163,12 @@ tile_sum_kernel(const T* __restrict__ lw, int64_t N, ScanGlob* g, double2* s_rec
   __syncthreads();
   if (!am_last) return;
   __threadfence();
-  tile_prefix_last_cta<T, V>(s_rec, P_rec, static_cast<int>(gridDim.x), N, g, err, log_total_out);
+  seg_prefix_last_cta<T, V>(s_rec, P_rec, kWarps * static_cast<int>(gridDim.x), N, g, err,
+                            log_total_out);
 }
 
 // ---------------------------------------------------------------------------------------
-// Pass 3a: systematic / stratified emission, one tile per CTA.
+// Pass 3a: systematic / stratified emission, one tile per CTA, one segment per warp.
 // ---------------------------------------------------------------------------------------
 template <typename T, typename V, bool STRAT>
 __global__ void __launch_bounds__(kBlock)
@@ -173,7 +176,7 @@ emit_cumoff_kernel(const T* __restrict__ lw, int64_t N, const ScanGlob* g, const
                    const double2* P_rec, Keys keys, int32_t* __restrict__ a,
                    int32_t* __restrict__ d) {
   pdl_wait();
-  __shared__ TileSh<V> sh;
+  __shared__ SegSh sh;
   __shared__ float2 sh_tab[64];
   const int64_t base = static_cast<int64_t>(blockIdx.x) * kTile;
   if (g->all_zero) {  // all weights zero: flagged; emit identity
@@ -186,22 +189,22 @@ emit_cumoff_kernel(const T* __restrict__ lw, int64_t N, const ScanGlob* g, const
   const WeightCtx wc = make_ctx<T, V>(g->M, sh_tab);
   const typename Path<T, V>::U u_sys = STRAT ? typename Path<T, V>::U() : cta_uniform0<T, V>(keys);
   const bool vec = (reinterpret_cast<uintptr_t>(lw) & 15u) == 0;
-  const int t = blockIdx.x;
-  const V Pt = load_v<V>(P_rec + t), Pn = load_v<V>(P_rec + t + 1);
-  emit_tile_cumoff<T, V, STRAT>(lw, 0, N, base, wc, vec, Pt, Pn, load_v<V>(&g->S_raw),
-                                load_v<V>(&g->scale_raw), u_sys, keys, a, d, sh);
+  const int warp = threadIdx.x >> 5;
+  const int64_t sg = static_cast<int64_t>(kWarps) * blockIdx.x + warp;
+  emit_seg_cumoff<T, V, STRAT>(lw, 0, N, base + kSeg * warp, wc, vec, load_v<V>(P_rec + sg),
+                               load_v<V>(P_rec + sg + 1), load_v<V>(&g->S_raw),
+                               load_v<V>(&g->scale_raw), u_sys, keys, a, d, sh.win[warp]);
 }
 
 // ---------------------------------------------------------------------------------------
 // Pass 3b: stored cumulative weights (multinomial search input, or rs_cumulative_weights
-// output converted to the element type), one tile per CTA.
+// output converted to the element type), one tile per CTA, one segment per warp.
 // ---------------------------------------------------------------------------------------
 template <typename T, typename V, typename OUT>
 __global__ void __launch_bounds__(kBlock)
 emit_W_kernel(const T* __restrict__ lw, int64_t N, const ScanGlob* g, const double2* P_rec,
               OUT* __restrict__ Wout) {
   pdl_wait();
-  __shared__ TileSh<V> sh;
   __shared__ float2 sh_tab[64];
   const int64_t base = static_cast<int64_t>(blockIdx.x) * kTile;
   if (g->all_zero) {
@@ -211,9 +214,10 @@ emit_W_kernel(const T* __restrict__ lw, int64_t N, const ScanGlob* g, const doub
   }
   const WeightCtx wc = make_ctx<T, V>(g->M, sh_tab);
   const bool vec = (reinterpret_cast<uintptr_t>(lw) & 15u) == 0;
-  const int t = blockIdx.x;
-  emit_tile_W<T, V, OUT>(lw, 0, N, base, wc, vec, load_v<V>(P_rec + t), load_v<V>(P_rec + t + 1),
-                         Wout, sh);
+  const int warp = threadIdx.x >> 5;
+  const int64_t sg = static_cast<int64_t>(kWarps) * blockIdx.x + warp;
+  emit_seg_W<T, V, OUT>(lw, 0, N, base + kSeg * warp, wc, vec, load_v<V>(P_rec + sg),
+                        load_v<V>(P_rec + sg + 1), Wout);
 }
 
 // Pass 3b for the multinomial scheme: stored cumulative weights plus the guide table.
@@ -222,15 +226,17 @@ __global__ void __launch_bounds__(kBlock)
 emit_W_guide_kernel(const T* __restrict__ lw, int64_t N, const ScanGlob* g, const double2* s_rec,
                     const double2* P_rec, V* __restrict__ Wout, int32_t* __restrict__ G) {
   pdl_wait();
-  __shared__ TileSh<V> sh;
+  __shared__ SegSh sh;
   __shared__ float2 sh_tab[64];
   const int64_t base = static_cast<int64_t>(blockIdx.x) * kTile;
   if (g->all_zero) return;  // the search writes the identity
   const WeightCtx wc = make_ctx<T, V>(g->M, sh_tab);
   const bool vec = (reinterpret_cast<uintptr_t>(lw) & 15u) == 0;
-  const int t = blockIdx.x;
-  emit_tile_W_guide<T, V>(lw, 0, N, base, wc, vec, load_v<V>(P_rec + t), load_v<V>(P_rec + t + 1),
-                          Guide{g->guide_step, g->guide_inv_step}, Wout, G, sh);
+  const int warp = threadIdx.x >> 5;
+  const int64_t sg = static_cast<int64_t>(kWarps) * blockIdx.x + warp;
+  emit_seg_W_guide<T, V>(lw, 0, N, base + kSeg * warp, wc, vec, load_v<V>(P_rec + sg),
+                         load_v<V>(P_rec + sg + 1), Guide{g->guide_step, g->guide_inv_step},
+                         Wout, G, sh.win[warp]);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -275,7 +281,7 @@ cudaError_t run_scan(const Scratch& s, int scheme, Acc acc, const T* lw, int64_t
                      bool fused, cudaStream_t st) {
   const int tiles = static_cast<int>((N + kTile - 1) / kTile);
   double2* s_rec = s.rec;
-  double2* P_rec = s.rec + (s.max_tiles + 2);
+  double2* P_rec = s.rec + seg_cap(s.max_tiles);
   const Keys keys = make_keys(seed, step, filter, static_cast<uint32_t>(scheme));
   constexpr int ai = Path<T, V>::id;
   if (fused) {
@@ -315,7 +321,7 @@ cudaError_t run_cumw(const Scratch& s, const T* lw, int64_t N, OUT* W_out, doubl
                      cudaStream_t st) {
   const int tiles = static_cast<int>((N + kTile - 1) / kTile);
   double2* s_rec = s.rec;
-  double2* P_rec = s.rec + (s.max_tiles + 2);
+  double2* P_rec = s.rec + seg_cap(s.max_tiles);
   constexpr int ai = Path<T, V>::id;
   trace_mark(s.trace, kLblMax[ai], st);
   launch_pdl(max_kernel<T>, max_grid(N, s.max_blocks), kBlock, st, lw, N, s.glob, s.blockmax, s.err,

@@ -210,6 +210,13 @@ __device__ __forceinline__ int tile_count(int64_t base, int64_t N) {
   const int64_t c = N - base;
   return c < kTile ? static_cast<int>(c) : kTile;
 }
+// The same for a segment: the kSeg = 32 kPer particles of one warp (lane l holds kPer l ..
+// kPer l + kPer - 1); zero or negative past the end.
+constexpr int kSeg = 32 * kPer;
+__device__ __forceinline__ int seg_count(int64_t base, int64_t N) {
+  const int64_t c = N - base;
+  return c < kSeg ? static_cast<int>(c) : kSeg;
+}
 
 // Maximum and minimum of non-negative accumulator values (exact; one instruction for the
 // IEEE types, whose values here are never NaN).
@@ -376,6 +383,29 @@ __device__ __forceinline__ u128 block_sum_u128(u128 v, u128* sh) {
   return t;
 }
 
+// Block-wide exclusive scan of u128 values in thread order; `total` gets the block's sum
+// (every thread). sh: kWarps entries.
+__device__ __forceinline__ u128 block_excl_scan_u128(u128 v, u128* sh, u128& total) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  u128 incl = v;
+#pragma unroll
+  for (int dd = 1; dd < 32; dd <<= 1) {
+    const u128 y = shfl_up_u128(incl, dd);
+    if (lane >= dd) incl += y;
+  }
+  __syncthreads();  // sh may still be read from a previous call
+  if (lane == 31) sh[warp] = incl;
+  __syncthreads();
+  u128 before = 0, tot = 0;
+#pragma unroll
+  for (int k = 0; k < kWarps; ++k) {
+    if (k < warp) before += sh[k];
+    tot += sh[k];
+  }
+  total = tot;
+  return before + incl - v;
+}
+
 // Block-wide sums of two u128 values (every thread gets both).
 __device__ __forceinline__ void block_sum2_u128(u128& a, u128& b, u128* sh) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -399,7 +429,7 @@ __device__ __forceinline__ void block_sum2_u128(u128& a, u128& b, u128* sh) {
   }
 }
 
-// A tile's record (tile_record): its largest log-weight m_t, in the input type, in the first
+// A segment's record (seg_record): its largest log-weight m_t, in the input type, in the first
 // 4 or 8 bytes of a double2, and s_t = the sum of its weights relative to m_t,
 // exp(lw_i - m_t), in the accumulator type, in the last 8 bytes.
 template <typename T, typename V>
@@ -424,8 +454,8 @@ __device__ __forceinline__ void load_rec(const double2* p, T& m, V& s) {
   from_bits(static_cast<unsigned long long>(__double_as_longlong(r.y)), s);
 }
 
-// The tile's total relative to the maximum M of the whole sequence: s_t exp(m_t - M), rounded
-// in the accumulator type, 0 for a tile of zero weights. The difference m_t - M is taken
+// The segment's total relative to the maximum M of the whole sequence: s_t exp(m_t - M),
+// rounded in the accumulator type, 0 for a segment of zero weights. The difference m_t - M is taken
 // exactly (a two-term sum: with it rounded, the relative error of the factor would grow with
 // |m_t - M|); binary32 and binary64 scale by exp_pinned(d_hi) (1 + d_lo), the two-float
 // accumulators by the two-float exp of the two-term difference, as their weights are formed.
@@ -467,17 +497,17 @@ __device__ __forceinline__ u128 rec_fixed(const double2* p, T M) {
   return to_fixed(rec_scaled<T, V>(p, M));
 }
 
-// Prefixes of one sequence of nt tile records, M the sequence's maximum log-weight (block-level,
-// every thread of the CTA calls it): with T_t = rec_scaled(record t), P_t = RN(T_0 + ... +
-// T_{t-1}) for t = 0..nt, the exact sums taken in fixed point (each
-// thread a contiguous chunk of tiles, then a warp scan and a scan over the warps: integer
-// adds, so the order does not matter). P is non-decreasing because the exact prefixes are and
-// rounding is monotone. The total S is P_nt, the cumulative weight the emission gives the
-// last particle (tile_cum_weights), so that particle receives O = N.
+// Prefixes of one sequence of nt segment records, M the sequence's maximum log-weight
+// (block-level, every thread of the CTA calls it): with T_g = rec_scaled(record g), P_g =
+// RN(T_0 + ... + T_{g-1}) for g = 0..nt, the exact sums taken in fixed point (each thread a
+// contiguous chunk of records, then a warp scan and a scan over the warps: integer adds, so the
+// order does not matter). P is non-decreasing because the exact prefixes are and rounding is
+// monotone. The total S is P_nt, the cumulative weight the emission gives the last particle
+// (seg_cum_weights), so that particle receives O = N.
 // Thread 0 writes S, N / S and S (binary64) to the given pointers, then the CTA synchronises.
 template <typename T, typename V>
-__device__ void tile_prefix_compute(const double2* s_rec, double2* P_rec, int nt, int64_t N,
-                                    T M, V* S_out, V* scale_out, double* Sd_out) {
+__device__ void seg_prefix_compute(const double2* s_rec, double2* P_rec, int nt, int64_t N,
+                                   T M, V* S_out, V* scale_out, double* Sd_out) {
   __shared__ u128 sh_sum[kWarps];
   constexpr int kGroup = 4;  // tile totals loaded together
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -530,12 +560,9 @@ __device__ void tile_prefix_compute(const double2* s_rec, double2* P_rec, int nt
   __syncthreads();
 }
 
-// Shared scratch of the block-level tile functions.
-
-template <typename V> struct TileSh {
-  V tot[kWarps];
-  long long key[kWarps];
-  alignas(16) int32_t win[kWarps][kRunWin];  // warp_runs windows
+// Shared scratch of the segment emissions: one warp_runs window per warp.
+struct SegSh {
+  alignas(16) int32_t win[kWarps][kRunWin];
 };
 
 // Code 11 for the particles of one warp: out[j] = the index of the particle whose run
@@ -596,26 +623,26 @@ __device__ __forceinline__ void warp_runs(const int32_t (&Oe)[kPer], int32_t pre
   }
 }
 
-// The record of a tile (block-level) from this thread's kPer log-weights x of it (-inf outside
-// the sequence): m_t = the tile's largest log-weight (NaN skipped; NaN and +inf set `bad`) and
-// s_t = the sum of the weights relative to it, exp(x_i - m_t), in the accumulator type
-// (sequential over a thread's kPer, butterfly over the warp, sequential over the warps; 0 when
-// m_t = -inf). Thread 0 stores the record at rec; every thread gets the key of m_t. A record
-// does not depend on the sequence's maximum M, so the records are formed in the same pass as
-// M; T_t = s_t exp(m_t - M) (rec_scaled) is the tile's total relative to M. With a reference
-// key `ref` (the paths without kTileRef pass M's) m_t is that reference instead, and nothing
-// is flagged here (their maximum pass flags it): the record of M then scales by exactly 1.
-// The tile prefixes only need an accurate total, because the emission pins every tile's last
-// particle to the next prefix (tile_cum_weights).
+// The record of a segment (warp-level) from this lane's kPer log-weights x of it (-inf outside
+// the sequence): m_t = the segment's largest log-weight (NaN skipped; NaN and +inf set `bad`)
+// and s_t = the sum of the weights relative to it, exp(x_i - m_t), in the accumulator type
+// (sequential over a lane's kPer, then a butterfly over the warp; 0 when m_t = -inf). Lane 0
+// stores the record at rec; every lane gets the key of m_t. A record does not depend on the
+// sequence's maximum M, so the records are formed in the same pass as M; T_t = s_t
+// exp(m_t - M) (rec_scaled) is the segment's total relative to M. With a reference key `ref`
+// (the paths without kTileRef pass M's) m_t is that reference instead, and nothing is flagged
+// here (their maximum pass flags it): the record of M then scales by exactly 1. The prefixes
+// only need an accurate total, because the emission pins every segment's last particle to the
+// next prefix (seg_cum_weights). No block-level synchronisation.
 constexpr long long kTileMaxRef = LLONG_MIN;  // (no valid reference key: never that of a number)
 
 template <typename T, typename V>
-__device__ __forceinline__ long long tile_record(const T (&x)[kPer], const float2* tab,
-                                                 double2* rec, TileSh<V>& sh, bool& bad,
-                                                 long long ref = kTileMaxRef) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+__device__ __forceinline__ long long seg_record(const T (&x)[kPer], const float2* tab,
+                                                double2* rec, bool& bad,
+                                                long long ref = kTileMaxRef) {
+  const int lane = threadIdx.x & 31;
   long long m;
-  if (ref != kTileMaxRef) {  // (uniform) a given reference replaces the tile's maximum
+  if (ref != kTileMaxRef) {  // (uniform) a given reference replaces the segment's maximum
     m = ref;
   } else if constexpr (sizeof(T) == 4) {
     float mf = -INFINITY;
@@ -642,70 +669,54 @@ __device__ __forceinline__ long long tile_record(const T (&x)[kPer], const float
       m = y > m ? y : m;
     }
   }
-  __syncthreads();  // sh may still be read from the previous tile
-  if (lane == 0) sh.key[warp] = m;
-  __syncthreads();
-  long long bm = sh.key[0];
-#pragma unroll
-  for (int k = 1; k < kWarps; ++k) bm = sh.key[k] > bm ? sh.key[k] : bm;
-  if (ref != kTileMaxRef) bm = ref;
   V t = vzero(V());
-  if (bm > max_key(neg_inf<T>())) {  // (uniform over the block)
-    const WeightCtx wc = ctx_of_key<T, V>(bm, tab);
+  if (m > max_key(neg_inf<T>())) {  // (uniform over the warp)
+    const WeightCtx wc = ctx_of_key<T, V>(m, tab);
     t = vfrom_w(Path<T, V>::weight(x[0], wc), V());
 #pragma unroll
     for (int q = 1; q < kPer; ++q) t = vadd(t, vfrom_w(Path<T, V>::weight(x[q], wc), V()));
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) t = vadd(t, vshfl_xor(t, o));  // same value in every lane
   }
-  if (lane == 0) sh.tot[warp] = t;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    V tm = sh.tot[0];
-#pragma unroll
-    for (int k = 1; k < kWarps; ++k) tm = vadd(tm, sh.tot[k]);
-    store_rec<T, V>(rec, key_to<T>(bm), tm);
-  }
-  return bm;
+  if (lane == 0) store_rec<T, V>(rec, key_to<T>(m), t);
+  return m;
 }
 
-// The same, loading the log-weights of the tile starting at `base` of the sequence [lo, N).
+// The same, loading the log-weights of the segment starting at `base` of the sequence [lo, N).
 template <typename T, typename V>
-__device__ __forceinline__ long long tile_record(const T* __restrict__ lw, int64_t lo, int64_t N,
-                                                 int64_t base, const float2* tab, bool vec,
-                                                 double2* rec, TileSh<V>& sh, bool& bad,
-                                                 long long ref = kTileMaxRef) {
+__device__ __forceinline__ long long seg_record(const T* __restrict__ lw, int64_t lo, int64_t N,
+                                                int64_t base, const float2* tab, bool vec,
+                                                double2* rec, bool& bad,
+                                                long long ref = kTileMaxRef) {
   T x[kPer];
-  load_per(lw, base + kPer * static_cast<int64_t>(threadIdx.x), lo, N, vec, x);
-  return tile_record<T, V>(x, tab, rec, sh, bad, ref);
+  load_per(lw, base + kPer * static_cast<int64_t>(threadIdx.x & 31), lo, N, vec, x);
+  return seg_record<T, V>(x, tab, rec, bad, ref);
 }
 
-// Cumulative weights W[q] of this thread's kPer particles of the tile starting at `base` of
-// the sequence [lo, N), for the tile prefixes Pt (this tile) and Pn (the next), and Wb, the
-// cumulative weight of the particle just before this thread's first one.
+// Cumulative weights W[q] of this lane's kPer particles of the segment starting at `base` of
+// the sequence [lo, N) (warp-level), for the segment prefixes Ps (this segment) and Pn (the
+// next), and Wb, the cumulative weight of the particle just before this lane's first one.
 //
 // Scan (the accumulator type's rounded additions, in a fixed order): l_q = sequential prefix
-// of the thread's weights; e = exclusive Hillis-Steele scan of the thread totals over the
-// warp; p_w = sequential sum of the totals of the warps before; W_q = RN(RN(Pt + RN(p_w + e))
-// + l_q) -- at most 7 + 5 + 7 + 3 roundings on any path. Tree sums are not monotone, so:
-//   * inside a thread W_q is non-decreasing by construction;
-//   * across the lanes of a warp, W_q is raised to the running maximum of the earlier lanes'
-//     last values (a max-scan over the lanes);
-//   * across warps, warp w's values are clamped into [B_w, B_{w+1}], B_w = min(RN(Pt + p_w),
-//     Pn), which is non-decreasing in w, and its last particle is pinned to B_{w+1};
-//   * the tile's last valid particle is pinned to Pn, so the particle before any tile has
-//     exactly that tile's prefix Pt, and tiles need nothing from each other's scans.
-// Every cumulative weight thus lies in [Pt, Pn] and the whole sequence is non-decreasing, so
+// of the lane's weights; e = exclusive Hillis-Steele scan of the lane totals over the warp;
+// W_q = RN(RN(Ps + e) + l_q) -- at most 7 + 5 + 2 roundings on any path. Tree sums are not
+// monotone, so:
+//   * inside a lane W_q is non-decreasing by construction;
+//   * across the lanes, W_q is raised to the running maximum of the earlier lanes' last values
+//     (a max-scan over the lanes, from Ps) and clamped to at most Pn;
+//   * the segment's last position, and its last valid particle, are pinned to Pn, so the
+//     particle before any segment has exactly that segment's prefix Ps, and segments need
+//     nothing from each other's scans.
+// Every cumulative weight thus lies in [Ps, Pn] and the whole sequence is non-decreasing, so
 // Code 11 writes every ancestor position exactly once. Positions past the sequence end have
 // weight 0 and repeat the last valid value; callers do not emit them.
 template <typename T, typename V>
-__device__ __forceinline__ void tile_cum_weights(const T* __restrict__ lw, int64_t lo, int64_t N,
-                                                 int64_t base, const WeightCtx& wc, bool vec,
-                                                 V Pt, V Pn, V (&W)[kPer], V& Wb,
-                                                 TileSh<V>& sh) {
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+__device__ __forceinline__ void seg_cum_weights(const T* __restrict__ lw, int64_t lo, int64_t N,
+                                                int64_t base, const WeightCtx& wc, bool vec,
+                                                V Ps, V Pn, V (&W)[kPer], V& Wb) {
+  const int lane = threadIdx.x & 31;
   T x[kPer];
-  load_per(lw, base + kPer * static_cast<int64_t>(tid), lo, N, vec, x);
+  load_per(lw, base + kPer * static_cast<int64_t>(lane), lo, N, vec, x);
 #pragma unroll
   for (int q = 0; q < kPer; ++q) {
     const V wv = vfrom_w(Path<T, V>::weight(x[q], wc), V());
@@ -719,15 +730,7 @@ __device__ __forceinline__ void tile_cum_weights(const T* __restrict__ lw, int64
   }
   V excl = vshfl_up(incl, 1);
   if (lane == 0) excl = vzero(V());
-  const V wtot = vshfl(incl, 31);
-  __syncthreads();  // sh.tot may still be read from the previous tile
-  if (lane == 0) sh.tot[warp] = wtot;
-  __syncthreads();
-  V pw = vzero(V());
-  for (int k = 0; k < warp; ++k) pw = vadd(pw, sh.tot[k]);
-  const V Bw = tmin(vadd(Pt, pw), Pn);
-  const V Bn = tmin(vadd(Pt, vadd(pw, wtot)), Pn);
-  const V b = vadd(Pt, vadd(pw, excl));
+  const V b = vadd(Ps, excl);
 #pragma unroll
   for (int q = 0; q < kPer; ++q) W[q] = vadd(b, W[q]);
   V m = W[kPer - 1];
@@ -737,18 +740,18 @@ __device__ __forceinline__ void tile_cum_weights(const T* __restrict__ lw, int64
     if (lane >= dd) m = tmax(y, m);
   }
   V pm = vshfl_up(m, 1);
-  if (lane == 0) pm = Bw;
+  if (lane == 0) pm = Ps;
 #pragma unroll
-  for (int q = 0; q < kPer; ++q) W[q] = tmin(tmax(W[q], pm), Bn);
-  if (lane == 31) W[kPer - 1] = Bn;
-  const int lq = tile_count(base, N) - 1 - kPer * tid;  // the tile's last valid particle here?
+  for (int q = 0; q < kPer; ++q) W[q] = tmin(tmax(W[q], pm), Pn);
+  if (lane == 31) W[kPer - 1] = Pn;
+  const int lq = seg_count(base, N) - 1 - kPer * lane;  // the segment's last valid particle here?
   if (lq >= 0 && lq < kPer) {
 #pragma unroll
     for (int q = 0; q < kPer; ++q)
       if (q == lq) W[q] = Pn;
   }
   Wb = vshfl_up(W[kPer - 1], 1);
-  if (lane == 0) Wb = Bw;
+  if (lane == 0) Wb = Ps;
 }
 
 // The systematic uniform u (counter (0, 0)), drawn once per CTA.
@@ -774,35 +777,35 @@ __device__ __forceinline__ void store_per(int32_t* __restrict__ p, const int32_t
   }
 }
 
-// Systematic / stratified emission of one tile starting at `base` of the sequence [lo, N)
-// (block-level): cumulative offspring O of every particle, the Code-11 scatter of local
-// ancestor indices into a[lo + j] and, when d is given, the Prepermute claims
-// d[lo + i] = O_{i-1} if particle i has offspring, else n (for a non-decreasing ancestry the
-// lowest claimant of slot i is the first position of its run). Pt, Pn: prefixes of this tile;
-// u_sys: the systematic uniform (cta_uniform0; unused when STRAT). Local indices are 32-bit
-// (n < 2^31).
+// Systematic / stratified emission of one segment starting at `base` of the sequence [lo, N)
+// (warp-level): cumulative offspring O of every particle, the Code-11 scatter of local
+// ancestor indices into a[lo + j] through the warp's window `win` and, when d is given, the
+// Prepermute claims d[lo + i] = O_{i-1} if particle i has offspring, else n (for a
+// non-decreasing ancestry the lowest claimant of slot i is the first position of its run).
+// Ps, Pn: prefixes of this segment and the next; u_sys: the systematic uniform (cta_uniform0;
+// unused when STRAT). Local indices are 32-bit (n < 2^31).
 template <typename T, typename V, bool STRAT>
-__device__ __forceinline__ void emit_tile_cumoff(const T* __restrict__ lw, int64_t lo, int64_t N,
-                                                 int64_t base, const WeightCtx& wc, bool vec,
-                                                 V Pt, V Pn, V S, V scale,
-                                                 typename Path<T, V>::U u_sys,
-                                                 const Keys& keys, int32_t* __restrict__ a,
-                                                 int32_t* __restrict__ d, TileSh<V>& sh) {
+__device__ __forceinline__ void emit_seg_cumoff(const T* __restrict__ lw, int64_t lo, int64_t N,
+                                                int64_t base, const WeightCtx& wc, bool vec,
+                                                V Ps, V Pn, V S, V scale,
+                                                typename Path<T, V>::U u_sys,
+                                                const Keys& keys, int32_t* __restrict__ a,
+                                                int32_t* __restrict__ d, int32_t* win) {
   const int lane = threadIdx.x & 31;
   const int32_t n = static_cast<int32_t>(N - lo);
-  const int cnt = tile_count(base, N) - kPer * static_cast<int>(threadIdx.x);  // valid here
-  const int32_t i0 = static_cast<int32_t>(base - lo) + kPer * static_cast<int32_t>(threadIdx.x);
+  const int cnt = seg_count(base, N) - kPer * lane;  // valid here
+  const int32_t i0 = static_cast<int32_t>(base - lo) + kPer * lane;
   V W[kPer], Wb;
-  tile_cum_weights<T, V>(lw, lo, N, base, wc, vec, Pt, Pn, W, Wb, sh);
-  // O of this thread's particles; the last particle of the sequence gets n, and positions
-  // past the end repeat the count before them (no offspring). A thread with a position past
+  seg_cum_weights<T, V>(lw, lo, N, base, wc, vec, Ps, Pn, W, Wb);
+  // O of this lane's particles; the last particle of the sequence gets n, and positions
+  // past the end repeat the count before them (no offspring). A lane with a position past
   // the end holds the sequence's last particle or none, so its last count is n either way.
   int32_t O[kPer];
 #pragma unroll
   for (int q = 0; q < kPer; ++q) O[q] = cum_offspring<T, V, STRAT>(W[q], S, scale, u_sys, keys, n);
   const int32_t last = (cnt >= kPer && i0 + kPer - 1 != n - 1) ? O[kPer - 1] : n;
   int32_t prev = __shfl_up_sync(0xffffffffu, last, 1);
-  if (lane == 0)  // (a warp wholly past the end follows the sequence's last particle: n)
+  if (lane == 0)  // (a segment wholly past the end follows the sequence's last particle: n)
     prev = cnt > 0 ? cum_offspring<T, V, STRAT>(Wb, S, scale, u_sys, keys, n) : n;
   int32_t dv[kPer];
   int32_t p = prev;
@@ -813,11 +816,11 @@ __device__ __forceinline__ void emit_tile_cumoff(const T* __restrict__ lw, int64
     O[q] = Oc;
     p = Oc;
   }
-  warp_runs(O, prev, i0, a + lo, sh.win[threadIdx.x >> 5]);
+  warp_runs(O, prev, i0, a + lo, win);
   if (d && cnt > 0) store_per(d + lo + i0, dv, cnt);
 }
 
-// Stored cumulative weights of one tile (block-level): W[e] for e in [lo, N).
+// Stored cumulative weights of one segment (warp-level): W[e] for e in [lo, N).
 template <typename V, typename OUT> __device__ __forceinline__ OUT convert_out(V v);
 template <> __device__ __forceinline__ float convert_out<float, float>(float v) { return v; }
 template <> __device__ __forceinline__ double convert_out<float, double>(float v) { return v; }
@@ -829,13 +832,14 @@ template <> __device__ __forceinline__ double convert_out<float2, double>(float2
 }
 
 template <typename T, typename V, typename OUT>
-__device__ __forceinline__ void emit_tile_W(const T* __restrict__ lw, int64_t lo, int64_t N,
-                                            int64_t base, const WeightCtx& wc, bool vec, V Pt,
-                                            V Pn, OUT* __restrict__ Wout, TileSh<V>& sh) {
-  const int cnt = tile_count(base, N) - kPer * static_cast<int>(threadIdx.x);
+__device__ __forceinline__ void emit_seg_W(const T* __restrict__ lw, int64_t lo, int64_t N,
+                                           int64_t base, const WeightCtx& wc, bool vec, V Ps,
+                                           V Pn, OUT* __restrict__ Wout) {
+  const int lane = threadIdx.x & 31;
+  const int cnt = seg_count(base, N) - kPer * lane;
   V W[kPer], Wb;
-  tile_cum_weights<T, V>(lw, lo, N, base, wc, vec, Pt, Pn, W, Wb, sh);
-  OUT* const p = Wout + base + kPer * static_cast<int64_t>(threadIdx.x);
+  seg_cum_weights<T, V>(lw, lo, N, base, wc, vec, Ps, Pn, W, Wb);
+  OUT* const p = Wout + base + kPer * static_cast<int64_t>(lane);
 #pragma unroll
   for (int q = 0; q < kPer; ++q)
     if (q < cnt) p[q] = convert_out<V, OUT>(W[q]);
@@ -908,21 +912,21 @@ __device__ __forceinline__ int64_t guide_count(V W, const Guide& g, int64_t n) {
   return b;
 }
 
-// Stored cumulative weights of one tile plus the guide-table scatter of its particles
-// (block-level; same cumulative-count pattern as emit_tile_cumoff).
+// Stored cumulative weights of one segment plus the guide-table scatter of its particles
+// (warp-level; same cumulative-count pattern as emit_seg_cumoff).
 template <typename T, typename V>
-__device__ __forceinline__ void emit_tile_W_guide(const T* __restrict__ lw, int64_t lo, int64_t N,
-                                                  int64_t base, const WeightCtx& wc, bool vec,
-                                                  V Pt, V Pn, const Guide& gd,
-                                                  V* __restrict__ Wout,
-                                                  int32_t* __restrict__ G, TileSh<V>& sh) {
+__device__ __forceinline__ void emit_seg_W_guide(const T* __restrict__ lw, int64_t lo, int64_t N,
+                                                 int64_t base, const WeightCtx& wc, bool vec,
+                                                 V Ps, V Pn, const Guide& gd,
+                                                 V* __restrict__ Wout,
+                                                 int32_t* __restrict__ G, int32_t* win) {
   const int lane = threadIdx.x & 31;
   const int32_t n = static_cast<int32_t>(N - lo);
-  const int cnt = tile_count(base, N) - kPer * static_cast<int>(threadIdx.x);
-  const int32_t j0 = static_cast<int32_t>(base - lo) + kPer * static_cast<int32_t>(threadIdx.x);
+  const int cnt = seg_count(base, N) - kPer * lane;
+  const int32_t j0 = static_cast<int32_t>(base - lo) + kPer * lane;
   V W[kPer], Wb;
-  tile_cum_weights<T, V>(lw, lo, N, base, wc, vec, Pt, Pn, W, Wb, sh);
-  V* const p = Wout + base + kPer * static_cast<int64_t>(threadIdx.x);
+  seg_cum_weights<T, V>(lw, lo, N, base, wc, vec, Ps, Pn, W, Wb);
+  V* const p = Wout + base + kPer * static_cast<int64_t>(lane);
   int32_t C[kPer];
 #pragma unroll
   for (int q = 0; q < kPer; ++q) {
@@ -942,7 +946,7 @@ __device__ __forceinline__ void emit_tile_W_guide(const T* __restrict__ lw, int6
     pc = Cc;
   }
   int32_t* const Gl = G + lo;
-  warp_runs(C, prev, j0, Gl, sh.win[threadIdx.x >> 5]);
+  warp_runs(C, prev, j0, Gl, win);
   if (j0 <= n - 1 && n - 1 < j0 + kPer) Gl[n] = n - 1;
 }
 

@@ -6,9 +6,10 @@ order than the oracle's sequential sum, so an output may differ only where the d
 within the rounding bound of a cumulative-weight boundary. The bound used here:
 
   kernel:  |W_i - W*_i| <= KERNEL_C * eps_acc * W^N     (W* = exact prefix of the oracle's
-           weights; KERNEL_C covers the <= 45 roundings on any path of the tile scan, the
-           tile records (a tree sum of exp(lw - m_t), m_t the tile's maximum, scaled by
-           exp(m_t - M)), the tile-prefix rounding and the final add, and the records' weights
+           weights; KERNEL_C covers the <= 30 roundings on any path of the segment scan (a
+           warp's 256 particles), the segment records (a tree sum of exp(lw - m_t), m_t the
+           segment's maximum, scaled by exp(m_t - M)), the prefix rounding and the final add,
+           and the records' weights
            formed from lw - m_t where the oracle's use lw - M (two roundings of the argument, a
            relative difference below |lw - M| eps per weight: about 20 eps at most for the
            weights that carry the sums); eps_acc = 2^-24 binary32, 2^-44 two-float,
