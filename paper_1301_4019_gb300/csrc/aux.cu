@@ -60,8 +60,8 @@ permute_sorted_kernel(const int32_t* __restrict__ a, const int32_t* __restrict__
 
 // Permute of a non-decreasing ancestry (permute_sorted_one) with four consecutive slots per
 // thread: the slot loads of a and d are 128-bit, and the walks of failed claims run together
-// (walk_warp: up to four dependent chains in flight per thread, then the rare long walks
-// compacted across the warp). The reads and writes of each slot are those of
+// (walk_queue: walks that end at their own slot at once, the others queued across the
+// warp and run one per lane). The reads and writes of each slot are those of
 // permute_sorted_one, so c is the same.
 __global__ void __launch_bounds__(kBlock)
 permute_sorted4_kernel(const int32_t* __restrict__ a, const int32_t* __restrict__ d, int64_t N,
@@ -104,12 +104,12 @@ permute_sorted4_kernel(const int32_t* __restrict__ a, const int32_t* __restrict_
 #pragma unroll
   for (int q = 0; q < 4; ++q) x[q] = static_cast<int32_t>(i0 + q);
   __shared__ int2 pend[kBlock / 32][128];
-  walk_warp<4>(ClaimsOf{d}, sentinel, c, x, D, A, fail, N, pend[threadIdx.x >> 5], err);
+  walk_queue<4>(ClaimsOf{d}, sentinel, c, x, D, A, fail, N, pend[threadIdx.x >> 5], err);
 }
 
 // Permute of any ancestry (permute_one) with four consecutive slots per thread: 128-bit slot
 // loads, the four claim checks d[a_i] issued together, and the walks of failed claims run
-// together (walk_warp). Same reads and writes per slot as permute_one, so c is the same.
+// together (walk_queue). Same reads and writes per slot as permute_one, so c is the same.
 __global__ void __launch_bounds__(kBlock)
 permute4_kernel(const int32_t* __restrict__ a, const int32_t* __restrict__ d, int64_t N,
                 int32_t* __restrict__ c, int* err) {
@@ -155,7 +155,7 @@ permute4_kernel(const int32_t* __restrict__ a, const int32_t* __restrict__ d, in
     x[q] = static_cast<int32_t>(i0 + q);
   }
   __shared__ int2 pend[kBlock / 32][128];
-  walk_warp<4>(ClaimsOf{d}, sentinel, c, x, D, A, fail, N, pend[threadIdx.x >> 5], err);
+  walk_queue<4>(ClaimsOf{d}, sentinel, c, x, D, A, fail, N, pend[threadIdx.x >> 5], err);
 }
 
 // Ancestors-to-Offspring (Code 12).

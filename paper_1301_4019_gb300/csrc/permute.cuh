@@ -169,5 +169,56 @@ __device__ __forceinline__ void walk_warp(const Claim& claim, int32_t sentinel,
   if (bad) flag_error(err, RS_ERR_ARG);
 }
 
+// The same walks, queued: a walker whose claim ends at its own slot (dx = the sentinel) is
+// done at once; the others take their first step and are collected, by ballot, into the warp's
+// shared list `pend` (32 K entries), which the lanes then work off one walk each to its end
+// (lane l takes entries l, l + 32, ...). Every lane runs only the walks that go on, instead of
+// K predicated walkers per round. c is the same as walking each one alone. Called by all 32
+// lanes.
+template <int K, typename Claim>
+__device__ __forceinline__ void walk_queue(const Claim& claim, int32_t sentinel,
+                                           int32_t* __restrict__ c, const int32_t (&x)[K],
+                                           const int32_t (&dx)[K], const int32_t (&val)[K],
+                                           const bool (&act)[K], int64_t n, int2* pend,
+                                           int* err) {
+  const uint32_t us = static_cast<uint32_t>(sentinel);
+  const int lane = threadIdx.x & 31;
+  const unsigned below = (1u << lane) - 1u;
+  bool bad = false;
+  int total = 0;
+#pragma unroll
+  for (int q = 0; q < K; ++q) {
+    bool go = false;
+    if (act[q]) {
+      const uint32_t v = static_cast<uint32_t>(dx[q]);
+      if (v == us) c[x[q]] = val[q];  // its own slot is unclaimed: the walk ends there
+      else if (v > us) bad = true;    // (only a corrupted claim vector)
+      else go = true;
+    }
+    const unsigned m = __ballot_sync(0xffffffffu, go);
+    if (go) pend[total + __popc(m & below)] = make_int2(dx[q], val[q]);  // one step taken
+    total += __popc(m);
+  }
+  __syncwarp();
+  for (int e = lane; e < total; e += 32) {
+    const int2 w = pend[e];
+    int32_t xs = w.x;
+    for (int64_t steps = 0;; ++steps) {
+      const uint32_t v = static_cast<uint32_t>(claim(xs));
+      if (v == us) {
+        c[xs] = w.y;
+        break;
+      }
+      if (v > us || steps > n) {  // only a corrupted claim vector can get here
+        bad = true;
+        break;
+      }
+      xs = static_cast<int32_t>(v);
+    }
+  }
+  __syncwarp();
+  if (bad) flag_error(err, RS_ERR_ARG);
+}
+
 }  // namespace
 }  // namespace rsk
