@@ -294,10 +294,11 @@ def kernel_roofline_units(label: str, N: int, B: int):
     """(bound, algorithmic amount per launch, unit) for a traced kernel label."""
     S = 8 if ("_f64" in label) else 4
     V = 8 if ("_f64" in label or label.endswith("_f32c")) else 4
+    # the per-particle figures of the path (2S + 4, + 16 for Permute) split over its kernels
     if label.startswith("fused_systematic_") or label.startswith("fused_stratified_"):
-        return "hbm", (2 * S + 8) * N, "B"        # two reads of logw, write a and the claims d
+        return "hbm", (2 * S + 4) * N, "B"        # two reads of logw, write a
     if label.startswith("fused_multinomial_"):
-        return "hbm", (2 * S + V + 4) * N, "B"    # two reads of logw, W, the claims' sentinel
+        return "hbm", (2 * S + V) * N, "B"        # two reads of logw, write W
     if label.startswith("max_") or label.startswith("tile_sum_"):
         return "hbm", S * N, "B"
     if label.startswith("emit_systematic_") or label.startswith("emit_stratified_"):
@@ -305,13 +306,13 @@ def kernel_roofline_units(label: str, N: int, B: int):
     if label.startswith("emit_W_"):
         return "hbm", S * N + V * N, "B"           # read logw, write W
     if label.startswith("search_"):
-        return "hbm", V * N + 8 * N, "B"           # read W once, write a, claim d
+        return "hbm", V * N + 4 * N, "B"           # read W once, write a
     if label.startswith("metropolis_"):
         return "alu", B * N, "Philox"              # one Philox4x32-10 draw per step
     if label.startswith("rejection_"):
         return "alu", None, "Philox"
     if label in ("permute", "permute_sorted"):
-        return "hbm", 12 * N, "B"                  # read a and the claims d, write c
+        return "hbm", 16 * N, "B"                  # the claims d written and read, read a, write c
     if label == "fill":
         return "hbm", 4 * N, "B"
     if label == "offspring":

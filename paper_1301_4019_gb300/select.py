@@ -101,9 +101,12 @@ def choose_scheme(N: int, y: float | None = None, beta: float | None = None,
 
 def table_from_sweep(sweep: dict) -> dict:
     """The decision table from the JSON line of ``bench.py --sweep``: the median microseconds
-    per call of every (dtype, y, log2 N, scheme) row, with the sweep's conditions."""
+    per call of every (dtype, y, log2 N, scheme) row of the binary32 and binary64 defaults,
+    with the sweep's conditions."""
     tab = {}
     for r in sweep["rows"]:
+        if r["dtype"] not in ("f32", "f64"):  # (the other accumulation modes: scan schemes only)
+            continue
         tab.setdefault(r["dtype"], {}).setdefault(str(float(r["y"])), {}).setdefault(
             str(int(r["log2n"])), {})[r["scheme"]] = r["us"]
     clocks = sweep.get("clocks", {})
@@ -113,15 +116,77 @@ def table_from_sweep(sweep: dict) -> dict:
             "rejection_log_wmax": 0.0, "us": tab}
 
 
+_ABBREV = {"multinomial": "Mu", "stratified": "St", "systematic": "Sy", "metropolis": "Me",
+           "rejection": "Re"}
+
+
+def sweep_markdown(sweep: dict, ys=(0.0, 2.0, 4.0)) -> str:
+    """Markdown tables of a ``bench.py --sweep`` line: microseconds per call and HBM fraction
+    per (dtype, scheme) over N at the given y, and the decision matrices (the fastest scheme
+    and its time per (y, N), binary32 and binary64)."""
+    rows = sweep["rows"]
+    sizes = sorted({int(r["log2n"]) for r in rows})
+    dtypes = [d for d in ("f32", "f32c", "f64", "f64n") if any(r["dtype"] == d for r in rows)]
+    head = "| dtype | scheme | " + " | ".join(f"2^{n}" for n in sizes) + " |"
+    rule = "|---|---|" + "---|" * len(sizes)
+    by = {(r["dtype"], float(r["y"]), int(r["log2n"]), r["scheme"]): r for r in rows}
+    out = []
+    for key, title in (("us", "Time per call, microseconds"), ("hbm_frac", "HBM fraction")):
+        for y in (ys if key == "us" else (2.0,)):
+            out += [f"## {title} at y = {y:g}", "", head, rule]
+            for d in dtypes:
+                for sch in SCHEME_ORDER:
+                    cells = [by.get((d, y, n, sch)) for n in sizes]
+                    if all(c is None for c in cells):
+                        continue
+                    fmt = "{:.1f}" if key == "us" else "{:.3f}"
+                    out.append(f"| {d} | {sch} | " + " | ".join(
+                        fmt.format(c[key]) if c else "" for c in cells) + " |")
+            out.append("")
+    small = [n for n in sizes if any("us_graph" in r and int(r["log2n"]) == n for r in rows)]
+    if small:
+        out += ["## Time per call inside a CUDA graph at y = 2, microseconds", "",
+                "| dtype | scheme | " + " | ".join(f"2^{n}" for n in small) + " |",
+                "|---|---|" + "---|" * len(small)]
+        for d in dtypes:
+            for sch in SCHEME_ORDER:
+                cells = [by.get((d, 2.0, n, sch)) for n in small]
+                if all(c is None or "us_graph" not in c for c in cells):
+                    continue
+                out.append(f"| {d} | {sch} | " + " | ".join(
+                    f"{c['us_graph']:.1f}" if c and "us_graph" in c else "" for c in cells)
+                    + " |")
+        out.append("")
+    ygrid = sorted({float(r["y"]) for r in rows})
+    for d in ("f32", "f64"):
+        out += [f"## Decision matrix, {d}: fastest scheme and its microseconds", "",
+                "| y \\ N | " + " | ".join(f"2^{n}" for n in sizes) + " |",
+                "|---|" + "---|" * len(sizes)]
+        for y in ygrid:
+            cells = []
+            for n in sizes:
+                best = min(((by[(d, y, n, s)]["us"], s) for s in SCHEME_ORDER
+                            if (d, y, n, s) in by), default=None)
+                cells.append(f"{_ABBREV[best[1]]} {best[0]:.0f}" if best else "")
+            out.append(f"| {y:g} | " + " | ".join(cells) + " |")
+        out.append("")
+    return "\n".join(out)
+
+
 def _main(argv=None):
     import argparse
     p = argparse.ArgumentParser(description="Rebuild decision_gb300.json from a sweep.")
     p.add_argument("--from-sweep", required=True, help="file holding bench.py --sweep output")
     p.add_argument("--out", default=os.path.join(os.path.dirname(os.path.abspath(__file__)),
                                                  "decision_gb300.json"))
+    p.add_argument("--markdown", action="store_true",
+                   help="print the sweep's tables and decision matrices instead")
     a = p.parse_args(argv)
     with open(a.from_sweep) as f:
         sweep = json.loads(f.read().strip().splitlines()[-1])
+    if a.markdown:
+        print(sweep_markdown(sweep))
+        return
     with open(a.out, "w") as f:
         json.dump(table_from_sweep(sweep), f, indent=0, sort_keys=True)
 
