@@ -227,26 +227,26 @@ class ClockSampler:
 # headers it includes, hashed; `traffic` is null once any of them has changed.
 # ---------------------------------------------------------------------------------------
 NCU_TRAFFIC = {  # label: (bytes per launch, source hash)
-               "offspring": (8391280, "0248ac8c98f19735"),
-               "iscan": (4213152, "0248ac8c98f19735"),
-               "adjacent_difference": (4197824, "0248ac8c98f19735"),
-               "cumoff_to_ancestors": (4200592, "0248ac8c98f19735"),
-               "fill": (8392, "0248ac8c98f19735"),
-               "fused_multinomial_f32": (4288256, "facf564dfdd5c288"),
-               "search_f32": (12591712, "2ceb13f0e29c28de"),
-               "permute": (8399969, "0248ac8c98f19735"),
-               "fused_stratified_f32": (4266368, "facf564dfdd5c288"),
-               "permute_sorted": (8400213, "0248ac8c98f19735"),
-               "fused_systematic_f32": (4262528, "facf564dfdd5c288"),
-               "metropolis_f32": (8412384, "32cec44800ec390c"),
-               "rejection_f32": (4214336, "32cec44800ec390c"),
-               "fused_multinomial_f64": (8549184, "facf564dfdd5c288"),
-               "search_f64": (16784165, "2ceb13f0e29c28de"),
-               "fused_stratified_f64": (8536027, "facf564dfdd5c288"),
-               "fused_systematic_f64": (8527543, "facf564dfdd5c288"),
-               "sidecar": (8394057, "32cec44800ec390c"),
-               "metropolis_f64": (16804425, "32cec44800ec390c"),
-               "rejection_f64": (8418597, "32cec44800ec390c")}
+"offspring": (8391600, "a3649656c285867b"),
+               "iscan": (4213136, "a3649656c285867b"),
+               "adjacent_difference": (4197472, "a3649656c285867b"),
+               "cumoff_to_ancestors": (4199232, "a3649656c285867b"),
+               "fill": (8593, "a3649656c285867b"),
+               "fused_multinomial_f32": (4351552, "973d12f0f91ad813"),
+               "search_f32": (12591008, "9ea69d45c82269bc"),
+               "permute": (8397443, "a3649656c285867b"),
+               "fused_stratified_f32": (4327072, "973d12f0f91ad813"),
+               "permute_sorted": (8397568, "a3649656c285867b"),
+               "fused_systematic_f32": (4326208, "973d12f0f91ad813"),
+               "metropolis_f32": (8405376, "f689bcb83a88e718"),
+               "rejection_f32": (4213856, "f689bcb83a88e718"),
+               "fused_multinomial_f64": (8522048, "973d12f0f91ad813"),
+               "search_f64": (16786066, "9ea69d45c82269bc"),
+               "fused_stratified_f64": (8509403, "973d12f0f91ad813"),
+               "fused_systematic_f64": (8500517, "973d12f0f91ad813"),
+               "sidecar": (8394679, "f689bcb83a88e718"),
+               "metropolis_f64": (16802926, "f689bcb83a88e718"),
+               "rejection_f64": (8418414, "f689bcb83a88e718")}
 
 _LABEL_FILES = (("fused_", "fused.cu"), ("permute", "aux.cu"), ("iscan", "aux.cu"),
                 ("fill", "aux.cu"), ("offspring", "aux.cu"), ("adjacent", "aux.cu"),

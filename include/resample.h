@@ -434,7 +434,7 @@ const char* rs_trace_label(const rs_handle* h, int i);
  * device memory -- code running under another framework's memory pool or allocator hooks,
  * plugins whose host forbids cudaMalloc after start-up, real-time loops that must never wait
  * on the allocator. It computes exactly what rs_resample(RS_SYSTEMATIC, permute = 0) computes
- * (same kernels, same results) without a handle: its scratch (about 82 KB) is a static
+ * (same kernels, same results) without a handle: its scratch (about 530 KB) is a static
  * device array of the library, which every GPU that loads the library keeps until the
  * process exits. The caller passes only inputs and outputs:
  *   dtype, logw_dev, N : as for rs_resample; 1 <= N <= RS_NOALLOC_MAX_N, larger N returns
