@@ -446,9 +446,11 @@ const char* rs_trace_label(const rs_handle* h, int i);
  *                        of the call.
  * logw_dev, ancestors_dev and status_dev must be memory of the current device (or managed
  * memory): a pointer of another device or of host memory returns RS_ERR_ARG before anything
- * is launched. The first call on each device looks up the device address of the static
- * array (cudaGetSymbolAddress) with that device current and keeps it for the life of the
- * process: make that first call before any stream capture, and make no call on a device
+ * is launched. The device address of the static array is looked up once per device
+ * (cudaGetSymbolAddress, with that device current) by the first call or by rs_create on
+ * that device, and kept for the life of the process. The lookup is not made while `stream`
+ * is being captured: a first call inside a capture, with neither an earlier call nor a
+ * handle on that device, returns RS_ERR_ARG and launches nothing. Make no call on a device
  * after cudaDeviceReset on it (the kept address would be stale). All calls on a device share
  * the one array and overwrite it: calls that overlap on the GPU (several streams or host
  * threads at once) race and must be serialised by the caller. The call allocates and frees

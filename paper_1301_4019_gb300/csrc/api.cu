@@ -130,7 +130,9 @@ int rs_create(rs_handle** out, int64_t max_n, int device) {
   int coop = 0;
   if (cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, device) != cudaSuccess) coop = 0;
   s.coop = coop;
-  bool ok = true;
+  // the allocation-free call's static scratch on this device: looked up now, so that calls
+  // made later while a stream is captured find it ready
+  bool ok = rsk::noalloc_prepare_current_device() == RS_OK;
   ok &= cudaMalloc(&s.d, sizeof(int32_t) * max_n) == cudaSuccess;
   ok &= cudaMalloc(&s.a_tmp, sizeof(int32_t) * max_n) == cudaSuccess;
   ok &= cudaMalloc(&s.W, 8 * static_cast<size_t>(max_n)) == cudaSuccess;

@@ -148,6 +148,9 @@ cudaError_t launch_prc_weights(const Scratch& s, bool f64, const void* logw, con
                                const double* lvmax_dev = nullptr,
                                unsigned long long* viol = nullptr);
 
+// noalloc.cu: the static scratch's address for the current device, looked up once
+int noalloc_prepare_current_device();
+
 // aux.cu
 cudaError_t launch_fill(int32_t* p, int64_t N, int32_t v, cudaStream_t st);
 cudaError_t launch_prepermute(const Scratch& s, const int32_t* a, int64_t N, int32_t* d,

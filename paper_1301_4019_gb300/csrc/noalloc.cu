@@ -60,11 +60,17 @@ std::mutex g_setup_mutex;
 constexpr int kMaxDevices = 64;
 unsigned char* g_scratch_ptr[kMaxDevices] = {};
 
-int scratch_for_current_device(unsigned char** out) {
+int scratch_for_current_device(unsigned char** out, cudaStream_t capture_check = nullptr,
+                               bool check = false) {
   int dev = -1;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return RS_ERR_CUDA;
   std::lock_guard<std::mutex> lock(g_setup_mutex);
   if (!g_scratch_ptr[dev]) {
+    // the lookup may load the module: not while the caller's stream is being captured
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (check && cudaStreamIsCapturing(capture_check, &cap) == cudaSuccess &&
+        cap != cudaStreamCaptureStatusNone)
+      return RS_ERR_ARG;
     void* p = nullptr;
     if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return RS_ERR_CUDA;
     g_scratch_ptr[dev] = static_cast<unsigned char*>(p);
@@ -87,6 +93,14 @@ bool usable_here(const void* p, int dev) {
 }
 
 }  // namespace
+
+// Resolves the static array's address for the current device (rs_create calls it, so that a
+// handle's device is ready for calls made during a stream capture).
+int noalloc_prepare_current_device() {
+  unsigned char* base = nullptr;
+  return scratch_for_current_device(&base);
+}
+
 }  // namespace rsk
 
 extern "C" int rs_systematic_noalloc(int dtype, const void* logw_dev, int64_t N, uint64_t seed,
@@ -103,7 +117,8 @@ extern "C" int rs_systematic_noalloc(int dtype, const void* logw_dev, int64_t N,
       (status_dev && !usable_here(status_dev, dev)))
     return RS_ERR_ARG;
   unsigned char* base = nullptr;
-  const int st = scratch_for_current_device(&base);
+  const cudaStream_t cs = static_cast<cudaStream_t>(stream);
+  const int st = scratch_for_current_device(&base, cs, true);
   if (st != RS_OK) return st;
   Scratch s;
   std::memset(&s, 0, sizeof(s));
@@ -115,7 +130,6 @@ extern "C" int rs_systematic_noalloc(int dtype, const void* logw_dev, int64_t N,
   s.max_tiles = kNoAllocMaxTiles;
   s.max_blocks = device_sm_count() * 8 < kNoAllocMaxBlocks ? device_sm_count() * 8
                                                             : kNoAllocMaxBlocks;
-  const cudaStream_t cs = static_cast<cudaStream_t>(stream);
   launch_pdl(noalloc_begin_kernel, 1, 1, cs);
   cudaError_t e = cudaGetLastError();
   if (e == cudaSuccess)

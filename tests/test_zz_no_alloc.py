@@ -83,3 +83,49 @@ def test_noalloc_refuses_buffers_of_another_kind(rs):
     a = rs.rs_systematic_noalloc(t, seed=1, out=out, status=status)
     torch.cuda.synchronize()
     assert status.item() == rs.RS_OK and a.cpu().tolist() == list(range(64))
+
+
+_CAPTURE_FIRST = r"""
+import sys, torch
+sys.path.insert(0, {root!r})
+import paper_1301_4019_gb300 as rs
+lw = torch.randn(5000, device="cuda")
+out = torch.empty(5000, dtype=torch.int32, device="cuda")
+if {with_handle}:
+    rs.Handle(16).close()  # a handle on the device prepares the static scratch
+g = torch.cuda.CUDAGraph()
+try:
+    with torch.cuda.graph(g):
+        rs.rs_systematic_noalloc(lw, seed=3, step=1, out=out)
+except Exception as e:  # (ending the capture may raise in turn, with ours as its context)
+    err = e if isinstance(e, rs.RsError) else e.__context__
+    if isinstance(err, rs.RsError):
+        print("refused", err.status)
+        sys.exit(0)
+    raise
+g.replay()
+torch.cuda.synchronize()
+ref = rs.rs_systematic_noalloc(lw, seed=3, step=1)
+torch.cuda.synchronize()
+print("captured", bool(torch.equal(out, ref)))
+"""
+
+
+@pytest.mark.parametrize("with_handle", [False, True])
+def test_noalloc_first_call_inside_a_capture(rs, with_handle):
+    """In a fresh process: a first call made while a stream is captured is refused
+    (RS_ERR_ARG, nothing launched) unless a handle on the device prepared the static scratch;
+    with one, the captured call replays to the direct call's ancestors."""
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    code = _CAPTURE_FIRST.format(root=root, with_handle=with_handle)
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True,
+                       timeout=300)
+    assert r.returncode == 0, r.stderr[-2000:]
+    line = r.stdout.strip().splitlines()[-1]
+    if with_handle:
+        assert line == "captured True", r.stdout
+    else:
+        assert line == f"refused {rs.RS_ERR_ARG}", r.stdout
