@@ -261,6 +261,52 @@ search_kernel(const V* __restrict__ W, const int32_t* __restrict__ G, int64_t N,
   if (d) atomicMin(d + k, static_cast<int32_t>(i));
 }
 
+// The same search, four consecutive outputs per thread (their loads in flight together) and
+// one 128-bit store of the four ancestors; used from kSearch4MinN particles, where W and the
+// guide table leave L2 (measured at 2^24: 577 vs 656 us binary32, 668 vs 754 us double-float;
+// at 2^20-2^22, with the tables in L2, one output per thread keeps more loads in flight:
+// 21 vs 27 us at 2^20).
+template <typename T, typename V>
+__global__ void __launch_bounds__(kBlock)
+search4_kernel(const V* __restrict__ W, const int32_t* __restrict__ G, int64_t N,
+               const ScanGlob* g, Keys keys, int32_t* __restrict__ a, int32_t* __restrict__ d) {
+  pdl_wait();
+  const int64_t i0 = 4 * (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x);
+  if (i0 >= N) return;
+  int32_t k[4];
+  if (g->all_zero) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) k[q] = static_cast<int32_t>(i0 + q);
+  } else {
+    const Guide gd{g->guide_step, g->guide_inv_step};
+    search_group_guided<T, V, 4>(W, G, N, gd, keys, i0, k);
+  }
+  if (i0 + 3 < N && (reinterpret_cast<uintptr_t>(a + i0) & 15u) == 0) {
+    *reinterpret_cast<int4*>(a + i0) = make_int4(k[0], k[1], k[2], k[3]);
+  } else {
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+      if (i0 + q < N) a[i0 + q] = k[q];
+  }
+  if (d) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+      if (i0 + q < N) atomicMin(d + k[q], static_cast<int32_t>(i0 + q));
+  }
+}
+constexpr int64_t kSearch4MinN = int64_t{1} << 23;
+
+template <typename T, typename V>
+void launch_search(const Scratch& s, const V* W, int64_t N, const Keys& keys, int32_t* a,
+                   int32_t* d, cudaStream_t st) {
+  if (N >= kSearch4MinN)
+    launch_pdl(search4_kernel<T, V>, static_cast<int>((N + 4 * kBlock - 1) / (4 * kBlock)),
+               kBlock, st, W, s.guide, N, s.glob, keys, a, d);
+  else
+    launch_pdl(search_kernel<T, V>, static_cast<int>((N + kBlock - 1) / kBlock), kBlock, st, W,
+               s.guide, N, s.glob, keys, a, d);
+}
+
 int max_grid(int64_t N, int max_blocks) {
   const int64_t want = (N + 4 * kBlock - 1) / (4 * kBlock);  // one 1024-element slice per CTA
   return static_cast<int>(want < max_blocks ? want : max_blocks);
@@ -288,8 +334,7 @@ cudaError_t run_scan(const Scratch& s, int scheme, Acc acc, const T* lw, int64_t
     cudaError_t e = launch_fused_passes(s, scheme, acc, lw, N, keys, a_out, d, st);
     if (e != cudaSuccess || scheme != RS_MULTINOMIAL) return e;
     trace_mark(s.trace, kLblSearch[ai], st);
-    launch_pdl(search_kernel<T, V>, static_cast<int>((N + kBlock - 1) / kBlock), kBlock, st,
-               static_cast<const V*>(s.W), s.guide, N, s.glob, keys, a_out, d);
+    launch_search<T, V>(s, static_cast<const V*>(s.W), N, keys, a_out, d, st);
     return cudaGetLastError();
   }
   trace_mark(s.trace, kLblMax[ai], st);
@@ -309,9 +354,8 @@ cudaError_t run_scan(const Scratch& s, int scheme, Acc acc, const T* lw, int64_t
     V* W = static_cast<V*>(s.W);
     trace_mark(s.trace, kLblW[ai], st);
     launch_pdl(emit_W_guide_kernel<T, V>, tiles, kBlock, st, lw, N, s.glob, s_rec, P_rec, W, s.guide);
-    const int grid = static_cast<int>((N + kBlock - 1) / kBlock);
     trace_mark(s.trace, kLblSearch[ai], st);
-    launch_pdl(search_kernel<T, V>, grid, kBlock, st, W, s.guide, N, s.glob, keys, a_out, d);
+    launch_search<T, V>(s, W, N, keys, a_out, d, st);
   }
   return cudaGetLastError();
 }

@@ -993,5 +993,69 @@ __device__ __forceinline__ int32_t search_one_guided(const V* __restrict__ W,
   return static_cast<int32_t>(lo < n ? lo : n - 1);
 }
 
+// The same search for K outputs i0 .. i0 + K - 1 at once (the valid ones: i0 + q < n): the
+// bucket of every draw first, then the guide entries of all K issued together, then their
+// short W ranges (up to 8 entries each) together, so that K dependent chains of loads are in
+// flight per thread. Each result equals search_one_guided's for its output.
+template <typename T, typename V, int K>
+__device__ __forceinline__ void search_group_guided(const V* __restrict__ W,
+                                                    const int32_t* __restrict__ G, int64_t n,
+                                                    const Guide& gd, const Keys& keys,
+                                                    int64_t i0, int32_t (&res)[K]) {
+  const V S = __ldg(W + (n - 1));
+  V u[K];
+  int64_t lo[K], hi[K];
+  bool ok[K];
+#pragma unroll
+  for (int q = 0; q < K; ++q) {
+    ok[q] = i0 + q < n;
+    const auto U = Path<T, V>::draw_u(draw(keys, static_cast<uint32_t>(i0 + q), 0u));
+    u[q] = vtimes_u(S, U);
+    const float est = floorf(__fmul_rn(vhi(u[q]), gd.inv_step));
+    int64_t b = est > 0.0f
+                    ? (est < __int2float_rn(static_cast<int>(n - 1)) ? __float2int_rz(est) : n - 1)
+                    : 0;
+    int steps = 0;
+    while (b > 0 && !vle(edge_as<V>(guide_edge(b, gd, n)), u[q]) && ++steps < 64) --b;
+    while (b < n - 1 && vle(edge_as<V>(guide_edge(b + 1, gd, n)), u[q]) && ++steps < 64) ++b;
+    lo[q] = steps < 64 ? b : -1;  // (-1: search the whole range)
+  }
+#pragma unroll
+  for (int q = 0; q < K; ++q) {
+    const int64_t b = lo[q];
+    if (ok[q] && b >= 0) {
+      lo[q] = __ldg(G + b);
+      hi[q] = static_cast<int64_t>(__ldg(G + b + 1)) + 1;
+    } else {
+      lo[q] = 0;
+      hi[q] = ok[q] ? n : 0;  // (no output: an empty range)
+    }
+  }
+  int cnt[K];
+#pragma unroll
+  for (int q = 0; q < K; ++q) {
+    cnt[q] = 0;
+    const int64_t len = hi[q] - lo[q];
+    if (ok[q] && len <= 8) {
+#pragma unroll
+      for (int k = 0; k < 8; ++k)
+        if (k < len && vle(__ldg(W + lo[q] + k), u[q])) ++cnt[q];
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < K; ++q) {
+    int64_t l = lo[q], h = hi[q];
+    if (h - l <= 8) {
+      l += cnt[q];
+    } else {
+      while (l < h) {
+        const int64_t mid = l + ((h - l) >> 1);
+        if (vle(__ldg(W + mid), u[q])) l = mid + 1; else h = mid;
+      }
+    }
+    res[q] = static_cast<int32_t>(l < n ? l : n - 1);
+  }
+}
+
 }  // namespace
 }  // namespace rsk
