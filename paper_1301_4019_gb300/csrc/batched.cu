@@ -380,15 +380,15 @@ batch_coop_kernel(const T* __restrict__ lw, Batch b, Keys base_keys, int32_t* __
         if (k >= own && k < own + kWarps) sh_f[k - own] = v;
       }
       block_sum2_u128(part, tot, sh_sum);  // (its barriers also publish sh_f)
+      if (threadIdx.x <= kWarps) {  // the tile's segment prefixes, one per thread
+        u128 p = part;
+        for (int w = 0; w < static_cast<int>(threadIdx.x); ++w) p += sh_f[w];
+        store_v<V>(&sh_P[threadIdx.x], fixed_to(p, V(), kFixFrac));
+      }
       if (threadIdx.x == 0) {
         const V S0 = fixed_to(tot, V(), kFixFrac);
         const double Sd0 = vto_double(S0);
         const V sc0 = vfrom_double(__ddiv_rn(static_cast<double>(n), Sd0), V());
-        u128 p = part;
-        for (int w = 0; w <= kWarps; ++w) {
-          store_v<V>(&sh_P[w], fixed_to(p, V(), kFixFrac));
-          if (w < kWarps) p += sh_f[w];
-        }
         store_v<V>(&sh_S, S0);
         store_v<V>(&sh_scale, sc0);
         sh_Sd = Sd0;
@@ -414,7 +414,7 @@ batch_coop_kernel(const T* __restrict__ lw, Batch b, Keys base_keys, int32_t* __
       }
       continue;
     }
-    const WeightCtx wc = make_ctx<T, V>(M, sh_tab);
+    const WeightCtx wc = ctx_staged<T, V>(M, sh_tab);  // (the table was staged at the start)
     const int64_t base = L.base + kSeg * warp;
     if constexpr (SCHEME == RS_MULTINOMIAL) {
       if (d)  // claims of the search kernel start from the sentinel n
@@ -423,8 +423,10 @@ batch_coop_kernel(const T* __restrict__ lw, Batch b, Keys base_keys, int32_t* __
       emit_seg_W<T, V, V>(lw, L.lo, L.hi, base, wc, vec, Ps, Pn, W);
     } else {
       const Keys keys = with_tag(base_keys, static_cast<uint32_t>(L.f), SCHEME);
+      // the filter's systematic uniform, drawn by every thread (no block synchronisation)
       const typename Path<T, V>::U u_sys =
-          SCHEME == RS_STRATIFIED ? typename Path<T, V>::U() : cta_uniform0<T, V>(keys);
+          SCHEME == RS_STRATIFIED ? typename Path<T, V>::U()
+                                  : Path<T, V>::draw_u(draw(keys, 0u, 0u));
       emit_seg_cumoff<T, V, SCHEME == RS_STRATIFIED>(lw, L.lo, L.hi, base, wc, vec, Ps, Pn, S,
                                                       scale, u_sys, keys, a, d, sh.win[warp]);
     }

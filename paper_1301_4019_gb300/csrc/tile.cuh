@@ -119,6 +119,17 @@ __device__ __forceinline__ WeightCtx ctx_of_key(long long k, const float2* tab) 
   return c;
 }
 
+// The weight context for the maximum Md with the exp table already staged at tab.
+template <typename T, typename V>
+__device__ __forceinline__ WeightCtx ctx_staged(double Md, const float2* tab) {
+  WeightCtx c;
+  c.Md = Md;
+  c.Mf = static_cast<float>(Md);
+  c.M2 = split_f64(Md);
+  c.tab = tab;
+  return c;
+}
+
 // Builds the weight context (and stages the exp table in shared memory when needed).
 template <typename T, typename V>
 __device__ __forceinline__ WeightCtx make_ctx(double Md, float2* sh_tab) {

@@ -12,7 +12,7 @@ in the same order on both sides (W^i times N / W^N rounded once) the ancestors m
 
 Sizes 2^20, 2^22 + 4097 and 2^24 run through the cooperative kernel with several tiles per CTA
 and a ragged last tile; the patterns include a power-of-two and an arbitrary count of ones,
-long runs of zeros, trailing zeros and all ones. Permute is checked on the same calls."""
+long runs of zeros, trailing zeros, all ones and a single one (one run covering every slot). Permute is checked on the same calls."""
 import numpy as np
 import pytest
 import torch
@@ -52,6 +52,8 @@ def _pattern(name, N, rng):
         ones[: N - 10007] = rng.random(N - 10007) < 0.5
     elif name == "all":
         ones[:] = True
+    elif name == "one":  # a single particle carries all the weight: one run covers every slot
+        ones[int(rng.integers(N))] = True
     return ones
 
 
@@ -72,9 +74,9 @@ def _pow2(x):
     return x > 0 and (x & (x - 1)) == 0
 
 
-PATTERNS = {1 << 20: ["quarter", "arbitrary", "runs", "trailing", "all"],
+PATTERNS = {1 << 20: ["quarter", "arbitrary", "runs", "trailing", "all", "one"],
             (1 << 22) + 4097: ["arbitrary", "runs", "trailing"],
-            1 << 24: ["quarter", "arbitrary", "trailing"]}
+            1 << 24: ["quarter", "arbitrary", "trailing", "one"]}
 
 
 @pytest.mark.parametrize("N", SIZES)
