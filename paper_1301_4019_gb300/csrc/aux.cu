@@ -172,13 +172,33 @@ offspring_kernel(const int32_t* __restrict__ a, int64_t N, int32_t* __restrict__
   atomicAdd(o + ai, 1);
 }
 
-// Adjacent-Difference: o_i = O_i - O_{i-1} (o_0 = O_0).
+// Adjacent-Difference: o_i = O_i - O_{i-1} (o_0 = O_0), four consecutive positions per thread
+// (128-bit loads and stores when inside and aligned; O_{i0-1} from the previous lane).
 __global__ void __launch_bounds__(kBlock)
 adjacent_difference_kernel(const int32_t* __restrict__ O, int64_t N, int32_t* __restrict__ o) {
   pdl_wait();
-  const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (i >= N) return;
-  o[i] = i == 0 ? O[0] : O[i] - O[i - 1];
+  const int64_t i0 = 4 * (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x);
+  const bool vec = i0 + 4 <= N &&
+                   ((reinterpret_cast<uintptr_t>(O) | reinterpret_cast<uintptr_t>(o)) & 15u) == 0;
+  int32_t x[4];
+  if (vec) {
+    const int4 u = __ldg(reinterpret_cast<const int4*>(O + i0));
+    x[0] = u.x; x[1] = u.y; x[2] = u.z; x[3] = u.w;
+  } else {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) x[q] = i0 + q < N ? O[i0 + q] : 0;
+  }
+  int32_t prev = __shfl_up_sync(0xffffffffu, x[3], 1);
+  if ((threadIdx.x & 31) == 0) prev = (i0 > 0 && i0 - 1 < N) ? O[i0 - 1] : 0;
+  if (i0 >= N) return;  // (after the shuffle: the whole warp takes part in it)
+  const int32_t y[4] = {x[0] - prev, x[1] - x[0], x[2] - x[1], x[3] - x[2]};
+  if (vec) {
+    *reinterpret_cast<int4*>(o + i0) = make_int4(y[0], y[1], y[2], y[3]);
+  } else {
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+      if (i0 + q < N) o[i0 + q] = y[q];
+  }
 }
 
 // Cumulative-Offspring-to-Ancestors (Code 11): particle i fills a[O_{i-1} .. O_i - 1].
@@ -209,10 +229,20 @@ __device__ __forceinline__ long long block_tile_scan(const int32_t* __restrict__
   // thread t owns the 16 consecutive elements base + 16 t .. base + 16 t + 15
   long long run = 0;
   const int64_t idx = base + 16 * threadIdx.x;
+  int32_t x[16];
+  if (idx + 16 <= N && (reinterpret_cast<uintptr_t>(in) & 15u) == 0) {  // four 128-bit loads
+#pragma unroll
+    for (int h = 0; h < 4; ++h) {
+      const int4 u = __ldg(reinterpret_cast<const int4*>(in + idx) + h);
+      x[4 * h] = u.x; x[4 * h + 1] = u.y; x[4 * h + 2] = u.z; x[4 * h + 3] = u.w;
+    }
+  } else {
+#pragma unroll
+    for (int q = 0; q < 16; ++q) x[q] = (idx + q < N) ? in[idx + q] : 0;
+  }
 #pragma unroll
   for (int q = 0; q < 16; ++q) {
-    const long long x = (idx + q < N) ? in[idx + q] : 0;
-    run += x;
+    run += x[q];
     v[q] = run;
   }
   long long incl = run;
@@ -231,6 +261,23 @@ __device__ __forceinline__ long long block_tile_scan(const int32_t* __restrict__
   long long total = 0;
   for (int k = 0; k < kWarps; ++k) total += sh[k];
   return total;
+}
+
+// out[idx + q] = v[q] + p for the 16 consecutive positions idx .. idx + 15 inside [0, N)
+// (four 128-bit stores when all are inside and aligned).
+__device__ __forceinline__ void store16(int32_t* __restrict__ out, int64_t idx, int64_t N,
+                                        const long long (&v)[16], long long p) {
+  if (idx + 16 <= N && (reinterpret_cast<uintptr_t>(out) & 15u) == 0) {
+#pragma unroll
+    for (int h = 0; h < 4; ++h)
+      reinterpret_cast<int4*>(out + idx)[h] = make_int4(
+          static_cast<int32_t>(v[4 * h] + p), static_cast<int32_t>(v[4 * h + 1] + p),
+          static_cast<int32_t>(v[4 * h + 2] + p), static_cast<int32_t>(v[4 * h + 3] + p));
+  } else {
+#pragma unroll
+    for (int q = 0; q < 16; ++q)
+      if (idx + q < N) out[idx + q] = static_cast<int32_t>(v[q] + p);
+  }
 }
 
 __global__ void __launch_bounds__(kBlock)
@@ -284,10 +331,7 @@ iscan_emit_kernel(const int32_t* __restrict__ in, int64_t N, const long long* pr
   const int64_t base = static_cast<int64_t>(blockIdx.x) * kIscanTile;
   block_tile_scan(in, N, base, v, sh);
   const long long p = pre[blockIdx.x];
-  const int64_t idx = base + 16 * threadIdx.x;
-#pragma unroll
-  for (int q = 0; q < 16; ++q)
-    if (idx + q < N) out[idx + q] = static_cast<int32_t>(v[q] + p);
+  store16(out, base + 16 * threadIdx.x, N, v, p);
 }
 
 // The same scan as one cooperative launch: CTA c owns the contiguous tiles
@@ -332,10 +376,7 @@ iscan_coop_kernel(const int32_t* __restrict__ in, int64_t N, int T, long long* t
     const int64_t base = static_cast<int64_t>(t) * kIscanTile;
     block_tile_scan(in, N, base, v, sh);
     const long long p = CP + __ldcg(pre + t);
-    const int64_t idx = base + 16 * threadIdx.x;
-#pragma unroll
-    for (int q = 0; q < 16; ++q)
-      if (idx + q < N) out[idx + q] = static_cast<int32_t>(v[q] + p);
+    store16(out, base + 16 * threadIdx.x, N, v, p);
   }
   grid_exit(bar, target);
 }
@@ -450,7 +491,8 @@ cudaError_t launch_barrier_timeout_probe(const Scratch& s, cudaStream_t st) {
 
 cudaError_t launch_adjacent_difference(const int32_t* O, int64_t N, int32_t* o,
                                        cudaStream_t st) {
-  launch_pdl(adjacent_difference_kernel, grid_for(N), kBlock, st, O, N, o);
+  launch_pdl(adjacent_difference_kernel, static_cast<int>((N + 4 * kBlock - 1) / (4 * kBlock)),
+             kBlock, st, O, N, o);
   return cudaGetLastError();
 }
 
