@@ -5,6 +5,7 @@
 #include "grid.cuh"
 #include "internal.h"
 #include "permute.cuh"
+#include "tile.cuh"
 
 namespace rsk {
 namespace {
@@ -201,20 +202,67 @@ adjacent_difference_kernel(const int32_t* __restrict__ O, int64_t N, int32_t* __
   }
 }
 
-// Cumulative-Offspring-to-Ancestors (Code 11): particle i fills a[O_{i-1} .. O_i - 1].
+// Cumulative-Offspring-to-Ancestors (Code 11): particle i fills a[O_{i-1} .. O_i - 1]. One
+// warp per kSeg particles (kPer consecutive per lane): the counts are checked as Code 11
+// needs them (RS_ERR_ARG for a count below the one before it or outside [0, n], or a last
+// count other than n; such counts are clamped, so that every write stays inside a), then
+// warp_runs writes the warp's positions [O_{j0-1}, O_{j0+kSeg-1}) through its shared window
+// with coalesced stores. For valid counts the writes are exactly Code 11's.
 __global__ void __launch_bounds__(kBlock)
 cumoff_to_ancestors_kernel(const int32_t* __restrict__ O, int64_t N, int32_t* __restrict__ a,
                            int* err) {
   pdl_wait();
-  const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (i >= N) return;
-  const int64_t start = i == 0 ? 0 : O[i - 1];
-  const int64_t end = O[i];
-  if (start < 0 || end < start || end > N || (i == N - 1 && end != N)) {
-    flag_error(err, RS_ERR_ARG);
-    return;
+  __shared__ alignas(16) int32_t win[kWarps][kRunWin];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t j0l = (static_cast<int64_t>(blockIdx.x) * kWarps + warp) * kSeg;
+  if (j0l >= N) return;  // (warp-uniform: only warp-level synchronisation below)
+  const int32_t n = static_cast<int32_t>(N);
+  const int32_t j0 = static_cast<int32_t>(j0l);
+  const int32_t i0 = j0 + kPer * lane;
+  int32_t Oe[kPer];
+  if (i0 + kPer <= n && (reinterpret_cast<uintptr_t>(O) & 15u) == 0) {
+    const int4 u0 = __ldg(reinterpret_cast<const int4*>(O + i0));
+    const int4 u1 = __ldg(reinterpret_cast<const int4*>(O + i0 + 4));
+    Oe[0] = u0.x; Oe[1] = u0.y; Oe[2] = u0.z; Oe[3] = u0.w;
+    Oe[4] = u1.x; Oe[5] = u1.y; Oe[6] = u1.z; Oe[7] = u1.w;
+  } else {
+#pragma unroll
+    for (int q = 0; q < kPer; ++q) Oe[q] = i0 + q < n ? __ldg(O + i0 + q) : n;
   }
-  for (int64_t j = start; j < end; ++j) a[j] = static_cast<int32_t>(i);
+  int32_t prev = __shfl_up_sync(0xffffffffu, Oe[kPer - 1], 1);
+  if (lane == 0) prev = j0 > 0 ? __ldg(O + j0 - 1) : 0;
+  bool bad = false;
+  {
+    int32_t p = prev;
+#pragma unroll
+    for (int q = 0; q < kPer; ++q) {
+      if (i0 + q < n)
+        bad |= p < 0 || Oe[q] < p || Oe[q] > n || (i0 + q == n - 1 && Oe[q] != n);
+      p = Oe[q];
+    }
+    // clamped into [0, n] and made non-decreasing within the lane, then across the warp
+    prev = min(max(prev, 0), n);
+    p = prev;
+#pragma unroll
+    for (int q = 0; q < kPer; ++q) {
+      Oe[q] = min(max(Oe[q], p), n);
+      p = Oe[q];
+    }
+    int32_t m = Oe[kPer - 1];
+#pragma unroll
+    for (int dd = 1; dd < 32; dd <<= 1) {
+      const int32_t y = __shfl_up_sync(0xffffffffu, m, dd);
+      if (lane >= dd) m = max(m, y);
+    }
+    const int32_t before = __shfl_up_sync(0xffffffffu, m, 1);
+    if (lane > 0 && before > prev) {
+      prev = before;
+#pragma unroll
+      for (int q = 0; q < kPer; ++q) Oe[q] = max(Oe[q], before);
+    }
+  }
+  if (__any_sync(0xffffffffu, bad) && lane == 0) flag_error(err, RS_ERR_ARG);
+  warp_runs(Oe, prev, i0, a, win[warp]);
 }
 
 // Integer inclusive prefix sum, reduce-then-scan over tiles of 4096 (exact in int64):
@@ -499,7 +547,8 @@ cudaError_t launch_adjacent_difference(const int32_t* O, int64_t N, int32_t* o,
 cudaError_t launch_cumoff_to_ancestors(const Scratch& s, const int32_t* O, int64_t N,
                                        int32_t* a, cudaStream_t st) {
   trace_mark(s.trace, "cumoff_to_ancestors", st);
-  launch_pdl(cumoff_to_ancestors_kernel, grid_for(N), kBlock, st, O, N, a, s.err);
+  launch_pdl(cumoff_to_ancestors_kernel, static_cast<int>((N + kTile - 1) / kTile), kBlock, st,
+             O, N, a, s.err);
   return cudaGetLastError();
 }
 
