@@ -227,26 +227,26 @@ class ClockSampler:
 # headers it includes, hashed; `traffic` is null once any of them has changed.
 # ---------------------------------------------------------------------------------------
 NCU_TRAFFIC = {  # label: (bytes per launch, source hash)
-"offspring": (8391600, "a3649656c285867b"),
-               "iscan": (4213136, "a3649656c285867b"),
-               "adjacent_difference": (4197472, "a3649656c285867b"),
-               "cumoff_to_ancestors": (4199232, "a3649656c285867b"),
-               "fill": (8593, "a3649656c285867b"),
-               "fused_multinomial_f32": (4351552, "973d12f0f91ad813"),
-               "search_f32": (12591008, "9ea69d45c82269bc"),
-               "permute": (8397443, "a3649656c285867b"),
-               "fused_stratified_f32": (4327072, "973d12f0f91ad813"),
-               "permute_sorted": (8397568, "a3649656c285867b"),
-               "fused_systematic_f32": (4326208, "973d12f0f91ad813"),
-               "metropolis_f32": (8405376, "f689bcb83a88e718"),
-               "rejection_f32": (4213856, "f689bcb83a88e718"),
-               "fused_multinomial_f64": (8522048, "973d12f0f91ad813"),
-               "search_f64": (16786066, "9ea69d45c82269bc"),
-               "fused_stratified_f64": (8509403, "973d12f0f91ad813"),
-               "fused_systematic_f64": (8500517, "973d12f0f91ad813"),
-               "sidecar": (8394679, "f689bcb83a88e718"),
-               "metropolis_f64": (16802926, "f689bcb83a88e718"),
-               "rejection_f64": (8418414, "f689bcb83a88e718")}
+    "offspring": (8391424, "75d1007247b47cad"),
+    "iscan": (4214048, "75d1007247b47cad"),
+    "adjacent_difference": (4198608, "75d1007247b47cad"),
+    "cumoff_to_ancestors": (4204608, "75d1007247b47cad"),
+    "fill": (8392, "75d1007247b47cad"),
+    "fused_multinomial_f32": (4350592, "843d08cc262f3307"),
+    "search_f32": (12592128, "da21887443d9d760"),
+    "permute": (8397363, "75d1007247b47cad"),
+    "fused_stratified_f32": (4327232, "843d08cc262f3307"),
+    "permute_sorted": (8397756, "75d1007247b47cad"),
+    "fused_systematic_f32": (4326944, "843d08cc262f3307"),
+    "metropolis_f32": (8405120, "366ada29b2119d6b"),
+    "rejection_f32": (4213760, "366ada29b2119d6b"),
+    "fused_multinomial_f64": (8524640, "843d08cc262f3307"),
+    "search_f64": (16784165, "da21887443d9d760"),
+    "fused_stratified_f64": (8511269, "843d08cc262f3307"),
+    "fused_systematic_f64": (8500882, "843d08cc262f3307"),
+    "sidecar": (8394203, "366ada29b2119d6b"),
+    "metropolis_f64": (16801536, "366ada29b2119d6b"),
+    "rejection_f64": (8424448, "366ada29b2119d6b")}
 
 _LABEL_FILES = (("fused_", "fused.cu"), ("permute", "aux.cu"), ("iscan", "aux.cu"),
                 ("fill", "aux.cu"), ("offspring", "aux.cu"), ("adjacent", "aux.cu"),
