@@ -56,6 +56,19 @@ int rs_check_barrier_timeout(rs_handle* h, void* stream);
  * unknown mode, n < 1 (mode 1) or a null count_dev; RS_ERR_CUDA if a launch fails. */
 int rs_check_acceptance(int mode, int64_t n, unsigned long long* count_dev, void* stream);
 
+/* Self-check of the exponential of the plain binary32 scans (the weights exp(lw - M) that the
+ * multinomial, stratified and systematic resamplers of Codes 5, 7 and 8 sum in plain binary32;
+ * every other path uses the pinned exponential). Over every binary32 t <= 0 (-0 through -inf,
+ * 2,139,095,041 values), with the device function the scans run, against the binary64 pinned
+ * exponential: *count_dev (one uint64 on the current device) receives the number of t in
+ * [-87, 0] whose relative error exceeds `bound`, plus the number of t < -87 whose result lies
+ * outside [0, 2^-125]; *max_rel_dev (one binary64 on the same device) the largest relative
+ * error over [-87, 0]. The parity tolerance of the plain binary32 scans assumes the bound
+ * 2^-21. Asynchronous on `stream` (the results are valid after the stream reaches them).
+ * RS_ERR_ARG for a null pointer or bound <= 0; RS_ERR_CUDA if a launch fails. */
+int rs_check_weight_exp(double bound, unsigned long long* count_dev, double* max_rel_dev,
+                        void* stream);
+
 #ifdef __cplusplus
 }
 #endif

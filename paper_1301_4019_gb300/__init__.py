@@ -45,7 +45,8 @@ EXPORTED = [
     "rs_log_sum_weights_batched", "rs_ess_batched", "rs_metropolis_B_batched",
     "rs_resample_batched_masked", "rs_reset_weights_batched",
     "rs_set_batched_launch", "rs_get_batched_launch", "rs_tune_batched", "rs_philox_throughput",
-    "rs_cumulative_weights_f64", "rs_check_acceptance", "rs_set_barrier_timeout",
+    "rs_cumulative_weights_f64", "rs_check_acceptance", "rs_check_weight_exp",
+    "rs_set_barrier_timeout",
     "rs_check_barrier_timeout", "rs_resample_rejection_estimated",
     "rs_capture_if_below",
     "rs_capture_end_if", "rs_smc_mark_resampled", "rs_smc_loglik_step",
@@ -126,6 +127,7 @@ def _declare(lib):
         "rs_tune_batched": (I, [P, I, P, P, I32, P, I32, I, P]),
         "rs_philox_throughput": (I, [P, I64, C.c_uint32, U64, P, P]),
         "rs_check_acceptance": (I, [I, I64, P, P]),
+        "rs_check_weight_exp": (I, [C.c_double, P, P, P]),
         "rs_set_barrier_timeout": (I, [P, U64]),
         "rs_check_barrier_timeout": (I, [P, P]),
         "rs_capture_if_below": (I, [P, P, C.c_double, P, C.POINTER(P)]),
@@ -626,6 +628,23 @@ def rs_check_acceptance(mode: int, n: int = 0, device: int | None = None) -> int
                                           _stream(torch.cuda.current_stream(dev))),
                "rs_check_acceptance")
         return int(out.item())
+
+
+SCAN_EXP_REL_ERR = 2.0 ** -21  # the bound the plain binary32 scans' parity tolerance assumes
+
+
+def rs_check_weight_exp(bound: float = SCAN_EXP_REL_ERR, device: int | None = None):
+    """Self-check of the plain binary32 scans' exponential over every binary32 t <= 0
+    (include/resample_measure.h): (number of results outside `bound`, largest relative error
+    over [-87, 0]). Synchronises the device's current stream."""
+    dev = torch.device("cuda", torch.cuda.current_device() if device is None else device)
+    with torch.cuda.device(dev):
+        cnt = torch.zeros(1, dtype=torch.int64, device=dev)
+        mx = torch.zeros(1, dtype=torch.float64, device=dev)
+        _check(load().rs_check_weight_exp(float(bound), cnt.data_ptr(), mx.data_ptr(),
+                                          _stream(torch.cuda.current_stream(dev))),
+               "rs_check_weight_exp")
+        return int(cnt.item()), float(mx.item())
 
 
 def rs_capture_if_below(h: Handle, value: torch.Tensor, threshold: float, stream=None):

@@ -657,6 +657,12 @@ int rs_check_acceptance(int mode, int64_t n, unsigned long long* count_dev, void
   return cuda_status(rsk::launch_check_acceptance(mode, n, count_dev, as_stream(stream)));
 }
 
+int rs_check_weight_exp(double bound, unsigned long long* count_dev, double* max_rel_dev,
+                        void* stream) {
+  if (!count_dev || !max_rel_dev || !(bound > 0.0)) return RS_ERR_ARG;
+  return cuda_status(rsk::launch_check_weight_exp(bound, count_dev, max_rel_dev, as_stream(stream)));
+}
+
 int rs_set_batched_launch(rs_handle* h, int kernel, int block, int items_per_thread) {
   if (!h || kernel < 0 || kernel >= rsk::kCfgCount) return RS_ERR_ARG;
   if (!valid_launch(block, items_per_thread)) return RS_ERR_ARG;

@@ -150,6 +150,31 @@ __device__ __forceinline__ double exp_pinned(double x) {
 }
 
 // ---------------------------------------------------------------------------------------
+// Binary32 exponential of the plain binary32 scans (the weights exp(lw - M) that the
+// multinomial, stratified and systematic resamplers sum in plain binary32), for t <= 0: the
+// hardware base-2 exponential (PTX ex2.approx.ftz.f32) of t log2(e) with the rounding error
+// of that product restored. With L1 = RN(log2 e) and L2 = RN(log2 e - L1):
+//   a = RN(t L1),  e = fma(t, L1, -a) + t L2
+// (fma(t, L1, -a) is the exact error of the product: the error-free product of Dekker in the
+// FMA form of Ogita, Rump and Oishi, 2005), so t log2(e) = a + e up to a few 2^-48 relative,
+// and exp(t) = 2^a 2^e ~ y (1 + e ln 2) with y = ex2(a), the last step one FMA (|e| < 2^-17:
+// the dropped (e ln 2)^2 / 2 is below 2^-35). Its relative error is that of ex2 plus about
+// two roundings, whatever |t|; kScanExpRelErr bounds it, and rs_check_weight_exp checks that
+// bound for every binary32 t in [-87, 0]. Below -150 the argument is clamped (so -inf gives
+// 0, not NaN); every t < -87 gives 0 or a value below 2^-125. NaN stays NaN.
+// ---------------------------------------------------------------------------------------
+constexpr double kScanExpRelErr = 0x1p-21;
+__device__ __forceinline__ float exp_scan_f32(float t) {
+  t = (t < -150.0f) ? -150.0f : t;
+  const float a = __fmul_rn(t, 0x1.715476p+0f);
+  float e = __fmaf_rn(t, 0x1.715476p+0f, -a);
+  e = __fmaf_rn(t, 0x1.4ae0c0p-26f, e);
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(a));
+  return __fmaf_rn(y, __fmul_rn(e, 0x1.62e430p-1f), y);
+}
+
+// ---------------------------------------------------------------------------------------
 // Programmatic dependent launch. Kernels of a call are launched with programmatic stream
 // serialization, so a kernel is set up while its predecessor drains; it waits here, before
 // touching memory, until the predecessor has completed and its writes are visible. (No

@@ -142,6 +142,10 @@ cudaError_t launch_barrier_timeout_probe(const Scratch& s, cudaStream_t st);
 // decisions on n log-weight pairs): the number of wrong decisions goes to *count.
 cudaError_t launch_check_acceptance(int mode, int64_t n, unsigned long long* count,
                                     cudaStream_t st);
+// scan.cu: self-check of the plain binary32 scans' exponential over every binary32 t <= 0
+// (count of results outside the bound; the largest relative error for t >= -87).
+cudaError_t launch_check_weight_exp(double bound, unsigned long long* count, double* max_rel,
+                                    cudaStream_t st);
 // (lvmax_dev: the bound read on the device; viol: count of log-weights above it)
 cudaError_t launch_prc_weights(const Scratch& s, bool f64, const void* logw, const int32_t* c,
                                int64_t N, double log_vmax, void* out, cudaStream_t st,

@@ -378,7 +378,60 @@ cudaError_t run_cumw(const Scratch& s, const T* lw, int64_t N, OUT* W_out, doubl
   return cudaGetLastError();
 }
 
+// Self-check of exp_scan_f32 (rs_check_weight_exp): the binary32 values t with bit patterns
+// first + k (k < count, all t <= 0), against the binary64 pinned exponential of t (within
+// about 2^-52 of exp): for t >= -87 a relative error above `bound` counts, and the largest
+// relative error is kept (non-negative binary64 values order like their bit patterns, so an
+// integer maximum of the patterns is the maximum); below -87 a result outside [0, 2^-125]
+// counts.
+__global__ void __launch_bounds__(kBlock)
+check_scan_exp_kernel(uint32_t first, uint32_t count, double bound, unsigned long long* bad_out,
+                      unsigned long long* maxrel_bits) {
+  unsigned long long bad = 0;
+  double mx = 0.0;
+  const uint32_t stride = gridDim.x * blockDim.x;
+  for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < count; k += stride) {
+    const float t = __uint_as_float(first + k);
+    const float y = exp_scan_f32(t);
+    if (t >= -87.0f) {
+      const double e = exp_pinned(static_cast<double>(t));
+      const double rel = __ddiv_rn(fabs(__dsub_rn(static_cast<double>(y), e)), e);
+      if (!(rel <= bound)) ++bad;
+      if (rel > mx) mx = rel;
+    } else if (!(y >= 0.0f && y <= 0x1p-125f)) {
+      ++bad;
+    }
+  }
+  unsigned long long mb = static_cast<unsigned long long>(__double_as_longlong(mx));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    bad += __shfl_xor_sync(0xffffffffu, bad, o);
+    const unsigned long long y = __shfl_xor_sync(0xffffffffu, mb, o);
+    mb = y > mb ? y : mb;
+  }
+  if ((threadIdx.x & 31) == 0) {
+    if (bad) atomicAdd(bad_out, bad);
+    atomicMax(maxrel_bits, mb);
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_check_weight_exp(double bound, unsigned long long* count, double* max_rel,
+                                    cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(count, 0, sizeof(unsigned long long), st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(max_rel, 0, sizeof(double), st);
+  if (e != cudaSuccess) return e;
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1)
+    sms = 1;
+  // every binary32 t <= 0: -0 (0x80000000) through -inf (0xff800000)
+  const uint32_t first = 0x80000000u, last = 0xff800000u;
+  check_scan_exp_kernel<<<sms * 8, kBlock, 0, st>>>(
+      first, last - first + 1, bound, count, reinterpret_cast<unsigned long long*>(max_rel));
+  return cudaGetLastError();
+}
 
 cudaError_t launch_scan_resample(const Scratch& s, int scheme, Acc acc, const void* logw,
                                  int64_t N, uint64_t seed, uint64_t step, uint32_t filter,

@@ -26,20 +26,24 @@ struct WeightCtx {
   const float2* tab;  // 2^(j/64) table in shared memory (double-float path)
 };
 
-// kTileRef: the tile records are formed relative to the tile's own maximum (tile_record), in
-// the same pass as the maximum of the whole sequence. Not for the compensated binary32 sums:
-// they must add exactly the binary32 weights exp(lw - M) that the emission scans, and weights
-// rounded to binary32 relative to another reference are other numbers; their records are
-// formed relative to M, after the maximum pass.
+// kTileRef: the segment records are formed relative to the segment's own maximum
+// (seg_record), in the same pass as the maximum of the whole sequence. Not for the compensated
+// binary32 sums: they must add exactly the binary32 weights exp(lw - M) that the emission
+// scans, and weights rounded to binary32 relative to another reference are other numbers;
+// their records are formed relative to M, after the maximum pass.
+//
+// Weights: the plain binary32 sums use exp_scan_f32 (relative error below kScanExpRelErr,
+// a bound the parity tolerance of these sums includes); every other path uses the pinned
+// exponential, so its weights are the oracle's bit for bit.
 template <typename T, typename V> struct Path;
 template <> struct Path<float, float> {
   using U = float;
   static constexpr int id = 0;
   static constexpr bool kTable = false;
   static constexpr bool kTileRef = true;
-  // exp_pinned(-inf) = 0, so a zero weight needs no test (M is finite here)
+  // exp_scan_f32(-inf) = 0, so a zero weight needs no test (M is finite here)
   __device__ static float weight(float x, const WeightCtx& c) {
-    return exp_pinned(__fsub_rn(x, c.Mf));
+    return exp_scan_f32(__fsub_rn(x, c.Mf));
   }
   __device__ static U draw_u(uint4 x) { return u01_f32(x); }
 };
