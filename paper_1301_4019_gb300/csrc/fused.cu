@@ -14,6 +14,7 @@
 // to 0 at the end of every launch.
 #include <cfloat>
 #include <climits>
+#include <type_traits>
 
 #include "common.cuh"
 #include "grid.cuh"
@@ -76,6 +77,13 @@ struct FusedArgs {
 // results equal
 // those of the separate kernels. Two grid barriers per call.
 
+// kKept: phase 2 takes this thread's first record from a load issued before the first grid
+// barrier, and phase 3 its first exact in-range prefix and the CTA total from registers (not
+// for the compensated binary32 path, whose records follow the maximum pass, nor for native
+// binary64, whose emission runs short of registers with them: both read them back from L2).
+template <typename T, typename V>
+constexpr bool kKept = Path<T, V>::kTileRef && !std::is_same_v<V, double>;
+
 template <typename T, typename V, int SCHEME>
 __device__ __forceinline__ void fused_body(const T* __restrict__ lw, const FusedArgs& A,
                                            unsigned int& target) {
@@ -100,6 +108,7 @@ __device__ __forceinline__ void fused_body(const T* __restrict__ lw, const Fused
   // ---- phase 1: segment records, last tile to first (and the Prepermute sentinel of the
   // multinomial claims); the next tile's log-weights are loaded while this one is reduced.
   // Without kTileRef, the maximum only (the records follow once M is known) ----------------
+  double2 rec0 = make_double2(0.0, 0.0);  // (kKept) the record of segment g0 + threadIdx.x
   {
     long long cm = max_key(neg_inf<T>());
     bool bad = false;
@@ -139,6 +148,13 @@ __device__ __forceinline__ void fused_body(const T* __restrict__ lw, const Fused
     if (bad) flag_error(A.err, RS_ERR_NONFINITE);
     cm = block_max_key(cm, sh_key);
     if (threadIdx.x == 0) A.blockmax[c] = key_to_double(cm, T());
+    // this thread's record for phase 2, loaded before the grid barrier so that the load
+    // overlaps the wait (lane 0 of each warp stored the records before block_max_key's
+    // block barrier)
+    if constexpr (kKept<T, V>) {
+      const int g = g0 + static_cast<int>(threadIdx.x);
+      if (g < g1) rec0 = __ldcg(A.s_rec + g);
+    }
   }
   grid_barrier(&A.g->bar, target, A.err);
   double M;
@@ -155,6 +171,8 @@ __device__ __forceinline__ void fused_body(const T* __restrict__ lw, const Fused
 
   // ---- phase 2: segment totals relative to M and their exact running sum -------------------
   const WeightCtx wc = make_ctx<T, V>(zero ? 0.0 : M, sh_tab);
+  u128 run = 0;  // the running exact total of this CTA's segments (the same in every thread)
+  u128 lp0 = 0;  // the exact in-range prefix of segment g0 + threadIdx.x (kept for phase 3)
   if (!zero) {
     const T Mt = static_cast<T>(M);  // (exact: M is one of the log-weights)
     if constexpr (!Path<T, V>::kTileRef) {  // the records, relative to M, last tile to first
@@ -164,13 +182,17 @@ __device__ __forceinline__ void fused_body(const T* __restrict__ lw, const Fused
                          A.s_rec + kWarps * t + warp, bad, max_key(Mt));
       __syncthreads();  // (lane 0 of each warp stored them; all threads read them below)
     }
-    u128 run = 0;  // (the same in every thread)
     for (int gb = g0; gb < g1; gb += kBlock) {
       const int g = gb + static_cast<int>(threadIdx.x);
-      const u128 f = g < g1 ? rec_fixed<T, V>(A.s_rec + g, Mt) : static_cast<u128>(0);
+      u128 f = 0;
+      if (g < g1) {
+        if (kKept<T, V> && gb == g0) f = rec_fixed_of<T, V>(rec0, Mt);
+        else f = rec_fixed<T, V>(A.s_rec + g, Mt);
+      }
       u128 tot;
       const u128 ex = block_excl_scan_u128(f, sh_sum, tot);
       if (g < g1) st_u128(LP + g, run + ex);
+      if (gb == g0) lp0 = ex;
       run += tot;
     }
     if (threadIdx.x == 0) st_u128(A.agg + c, run);
@@ -244,8 +266,12 @@ __device__ __forceinline__ void fused_body(const T* __restrict__ lw, const Fused
   // segment, which that CTA owns: kept in shared memory (the last CTA also writes the total's
   // slot)
   __shared__ double2 sh_pend;
-  for (int g = g0 + threadIdx.x; g <= g1; g += kBlock) {
-    const u128 lp = (g < g1) ? ld_u128_cg(LP + g) : ld_u128_cg(A.agg + c);
+  // (kKept: the exact in-range prefixes of the first kBlock segments and the CTA total are
+  // still in registers from phase 2)
+  const int gfirst = g0 + static_cast<int>(threadIdx.x);
+  for (int g = gfirst; g <= g1; g += kBlock) {
+    const u128 lp = (g == g1) ? (kKept<T, V> ? run : ld_u128_cg(A.agg + c))
+                              : (kKept<T, V> && g == gfirst) ? lp0 : ld_u128_cg(LP + g);
     const V P = fixed_to(CP + lp, V(), kFixFrac);
     if (g < g1 || c == G - 1) store_v<V>(A.P_rec + g, P);
     if (g == g1) store_v<V>(&sh_pend, P);
@@ -276,8 +302,10 @@ __device__ __forceinline__ void fused_body(const T* __restrict__ lw, const Fused
   }
 }
 
+// (at most 64 registers a thread, so that four CTAs of kBlock threads share an SM: the
+// cooperative grid is four CTAs per SM)
 template <typename T, typename V, int SCHEME>
-__global__ void __launch_bounds__(kBlock) fused_scan_kernel(const T* __restrict__ lw, FusedArgs A) {
+__global__ void __launch_bounds__(kBlock, 4) fused_scan_kernel(const T* __restrict__ lw, FusedArgs A) {
   unsigned int target = 0;
   fused_body<T, V, SCHEME>(lw, A, target);
   grid_exit(&A.g->bar, target);

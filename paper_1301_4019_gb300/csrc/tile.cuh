@@ -477,10 +477,11 @@ __device__ __forceinline__ void load_rec(const double2* p, T& m, V& s) {
 // M = +inf (flagged non-finite input) gives 0 for finite m_t and NaN for m_t = +inf, as the
 // weights exp(lw_i - M) themselves do.
 template <typename T, typename V>
-__device__ __forceinline__ V rec_scaled(const double2* p, T M) {
+__device__ __forceinline__ V rec_scaled_of(const double2 r, T M) {
   T m;
   V sv;
-  load_rec<T, V>(p, m, sv);
+  from_bits(static_cast<unsigned long long>(__double_as_longlong(r.x)), m);
+  from_bits(static_cast<unsigned long long>(__double_as_longlong(r.y)), sv);
   if (!(m > neg_inf<T>())) return vzero(V());
   if constexpr (std::is_same_v<V, float>) {
     const float dh = __fsub_rn(m, M);
@@ -508,8 +509,16 @@ __device__ __forceinline__ V rec_scaled(const double2* p, T M) {
   }
 }
 template <typename T, typename V>
+__device__ __forceinline__ V rec_scaled(const double2* p, T M) {
+  return rec_scaled_of<T, V>(__ldcg(p), M);  // (written by another CTA, or earlier, in this launch)
+}
+template <typename T, typename V>
 __device__ __forceinline__ u128 rec_fixed(const double2* p, T M) {
   return to_fixed(rec_scaled<T, V>(p, M));
+}
+template <typename T, typename V>
+__device__ __forceinline__ u128 rec_fixed_of(const double2 r, T M) {
+  return to_fixed(rec_scaled_of<T, V>(r, M));
 }
 
 // Prefixes of one sequence of nt segment records, M the sequence's maximum log-weight
@@ -824,12 +833,20 @@ __device__ __forceinline__ void emit_seg_cumoff(const T* __restrict__ lw, int64_
     prev = cnt > 0 ? cum_offspring<T, V, STRAT>(Wb, S, scale, u_sys, keys, n) : n;
   int32_t dv[kPer];
   int32_t p = prev;
+  if (base + kSeg < N) {  // (warp-uniform) all kSeg particles valid, none the sequence's last
 #pragma unroll
-  for (int q = 0; q < kPer; ++q) {
-    const int32_t Oc = (q >= cnt) ? p : ((i0 + q == n - 1) ? n : O[q]);
-    dv[q] = (Oc > p) ? p : n;
-    O[q] = Oc;
-    p = Oc;
+    for (int q = 0; q < kPer; ++q) {
+      dv[q] = (O[q] > p) ? p : n;
+      p = O[q];
+    }
+  } else {
+#pragma unroll
+    for (int q = 0; q < kPer; ++q) {
+      const int32_t Oc = (q >= cnt) ? p : ((i0 + q == n - 1) ? n : O[q]);
+      dv[q] = (Oc > p) ? p : n;
+      O[q] = Oc;
+      p = Oc;
+    }
   }
   warp_runs(O, prev, i0, a + lo, win);
   if (d && cnt > 0) store_per(d + lo + i0, dv, cnt);
