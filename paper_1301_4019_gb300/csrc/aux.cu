@@ -108,6 +108,102 @@ permute_sorted4_kernel(const int32_t* __restrict__ a, const int32_t* __restrict_
   walk_queue<4>(ClaimsOf{d}, sentinel, c, x, D, A, fail, N, pend[threadIdx.x >> 5], err);
 }
 
+// Permute of a non-decreasing ancestry from a and the claimed bits of its emission (cl: bit
+// i % 8 of cl[i / 8] set when particle i has offspring), K consecutive slots per thread. For
+// such an ancestry the claims of Prepermute are d_j = the first position of the run of j for
+// every claimed j, so Code 10's walks can be followed from their ends instead of their starts:
+//  - a claimed slot x keeps its particle: c_x = x;
+//  - an unclaimed slot x that is not the first of its run (a_{x-1} = a_x) is a failed claim
+//    whose walk ends at once, at x: c_x = a_x;
+//  - an unclaimed slot x that is the first of its run was reached from z = a_x (d_z = x);
+//    while z is itself the first of its run (z = 0 or a_{z-1} != a_z) it was reached from
+//    a_z in turn, and the first z that is not is the walk's start: c_x = a_z.
+// d is injective on the claimed slots and the walks end (Appendix C), so each backward chain
+// is one walk reversed and c is Code 10's exactly; the claims are never stored. The chains
+// that go on past their first step are queued per warp and run one per lane (as walk_queue).
+template <int K>
+__global__ void __launch_bounds__(kBlock)
+permute_sorted_bits_kernel(const int32_t* __restrict__ a, const uint8_t* __restrict__ cl,
+                           int64_t N, int32_t* __restrict__ c, int* err) {
+  static_assert(K == 1 || K == 4, "one or four slots per thread");
+  pdl_wait();
+  const int64_t i0 = K * (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x);
+  // (no early exit: the chains are finished warp-wide; threads past N have no slots)
+  const int lane = threadIdx.x & 31;
+  const bool full = i0 + K <= N;
+  int32_t A[K];
+  if (K == 4 && full && (reinterpret_cast<uintptr_t>(a) & 15u) == 0) {
+    const int4 va = *reinterpret_cast<const int4*>(a + i0);
+    A[0] = va.x; A[1] = va.y; A[2] = va.z; A[3] = va.w;
+  } else {
+#pragma unroll
+    for (int q = 0; q < K; ++q) A[q] = i0 + q < N ? a[i0 + q] : 0;
+  }
+  // a_{i0-1}: the previous lane's last slot, loaded by lane 0 only
+  int32_t prev = __shfl_up_sync(0xffffffffu, A[K - 1], 1);
+  if (lane == 0) prev = (i0 > 0 && i0 - 1 < N) ? a[i0 - 1] : -1;
+  const uint32_t bits = i0 < N ? static_cast<uint32_t>(cl[i0 >> 3]) >> (i0 & 7) : 0u;
+  // the warp's K * 32 consecutive results are gathered here and stored 128 bits at a time
+  __shared__ alignas(16) int32_t cbuf[kBlock / 32][32 * K];
+  __shared__ int2 pend[kBlock / 32][32 * K];
+  int32_t* const cw = cbuf[threadIdx.x >> 5];
+  int2* const pq = pend[threadIdx.x >> 5];
+  const unsigned below = (1u << lane) - 1u;
+  int total = 0;
+  bool bad = false;
+  int32_t R[K];
+#pragma unroll
+  for (int q = 0; q < K; ++q) {
+    const int64_t x = i0 + q;
+    bool go = false;
+    R[q] = 0;
+    const int32_t ax = A[q];
+    if (x < N) {
+      if (ax < 0 || ax >= N) bad = true;
+      else if ((bits >> q) & 1u) R[q] = static_cast<int32_t>(x);
+      else if (prev == ax) R[q] = ax;  // not the first of its run
+      else go = true;
+      prev = ax;
+    }
+    const unsigned m = __ballot_sync(0xffffffffu, go);
+    if (go) pq[total + __popc(m & below)] = make_int2(K * lane + q, ax);
+    total += __popc(m);
+  }
+  if (K == 4) {
+    reinterpret_cast<int4*>(cw)[lane] = make_int4(R[0], R[1], R[2], R[3]);
+  } else {
+    cw[lane] = R[0];
+  }
+  __syncwarp();
+  const uint32_t un = static_cast<uint32_t>(N);
+  for (int e = lane; e < total; e += 32) {
+    const int2 w = pq[e];
+    int32_t z = w.y;
+    for (int64_t steps = 0;; ++steps) {
+      const int32_t y = a[z];
+      const bool zhead = z == 0 || a[z - 1] != y;
+      if (static_cast<uint32_t>(y) >= un || steps > N) {  // only a corrupted a can get here
+        bad = true;
+        break;
+      }
+      if (!zhead) {
+        cw[w.x] = y;
+        break;
+      }
+      z = y;
+    }
+  }
+  __syncwarp();
+  if (K == 4 && full && (reinterpret_cast<uintptr_t>(c) & 15u) == 0) {
+    *reinterpret_cast<int4*>(c + i0) = reinterpret_cast<const int4*>(cw)[lane];
+  } else {
+#pragma unroll
+    for (int q = 0; q < K; ++q)
+      if (i0 + q < N) c[i0 + q] = cw[K * lane + q];
+  }
+  if (bad) flag_error(err, RS_ERR_ARG);
+}
+
 // Permute of any ancestry (permute_one) with four consecutive slots per thread: 128-bit slot
 // loads, the four claim checks d[a_i] issued together, and the walks of failed claims run
 // together (walk_queue). Same reads and writes per slot as permute_one, so c is the same.
@@ -492,6 +588,17 @@ cudaError_t launch_permute_sorted(const Scratch& s, const int32_t* a, const int3
                kBlock, st, a, d, N, c, s.err);
   else
     launch_pdl(permute_sorted_kernel, grid_for(N), kBlock, st, a, d, N, c, s.err);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_permute_sorted_bits(const Scratch& s, const int32_t* a, const uint8_t* cl,
+                                       int64_t N, int32_t* c, cudaStream_t st) {
+  trace_mark(s.trace, "permute_sorted", st);
+  if (N >= kSorted4MinN)
+    launch_pdl(permute_sorted_bits_kernel<4>, static_cast<int>((N + 4 * kBlock - 1) / (4 * kBlock)),
+               kBlock, st, a, cl, N, c, s.err);
+  else
+    launch_pdl(permute_sorted_bits_kernel<1>, grid_for(N), kBlock, st, a, cl, N, c, s.err);
   return cudaGetLastError();
 }
 

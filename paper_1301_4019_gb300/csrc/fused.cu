@@ -46,6 +46,7 @@ struct FusedArgs {
   Keys keys;
   int32_t* a;      // ancestors (systematic / stratified)
   int32_t* d;      // Prepermute claims, or nullptr
+  uint8_t* cl;     // claimed bits of the particles (in place of d for the sorted Permute), or nullptr
   void* W;         // multinomial cumulative weights
   int32_t* guide;  // multinomial guide table
   double2* s_rec;  // segment records
@@ -212,6 +213,8 @@ __device__ __forceinline__ void fused_body(const T* __restrict__ lw, const Fused
         A.a[i] = static_cast<int32_t>(i);
         if (A.d) A.d[i] = static_cast<int32_t>(i);
       }
+      if (A.cl)  // every slot claimed (e0 is a multiple of 8)
+        for (int64_t b = (e0 >> 3) + threadIdx.x; b < ((e1 + 7) >> 3); b += kBlock) A.cl[b] = 0xFFu;
     }
     return;  // uniform over the grid
   }
@@ -258,6 +261,8 @@ __device__ __forceinline__ void fused_body(const T* __restrict__ lw, const Fused
         A.a[i] = static_cast<int32_t>(i);
         if (A.d) A.d[i] = static_cast<int32_t>(i);
       }
+      if (A.cl)
+        for (int64_t b = (e0 >> 3) + threadIdx.x; b < ((e1 + 7) >> 3); b += kBlock) A.cl[b] = 0xFFu;
     }
     return;
   }
@@ -297,7 +302,7 @@ __device__ __forceinline__ void fused_body(const T* __restrict__ lw, const Fused
                              sh.win[warp]);
     } else {
       emit_seg_cumoff<T, V, SCHEME == RS_STRATIFIED>(lw, 0, N, base, wc, vec, Ps, Pn, S, scale,
-                                                      u_sys, A.keys, A.a, A.d, sh.win[warp]);
+                                                      u_sys, A.keys, A.a, A.d, sh.win[warp], A.cl);
     }
   }
 }
@@ -385,12 +390,13 @@ bool fused_available(const Scratch& s, int scheme, Acc acc) {
 
 cudaError_t launch_fused_passes(const Scratch& s, int scheme, Acc acc, const void* logw,
                                 int64_t N, const Keys& keys, int32_t* a_out, int32_t* d,
-                                cudaStream_t st) {
+                                uint8_t* cl, cudaStream_t st) {
   FusedArgs A;
   A.N = N;
   A.keys = keys;
   A.a = a_out;
   A.d = d;
+  A.cl = scheme == RS_MULTINOMIAL ? nullptr : cl;
   A.W = s.W;
   A.guide = s.guide;
   A.s_rec = s.rec;

@@ -100,7 +100,7 @@ struct Keys;
 cudaError_t launch_scan_resample(const Scratch& s, int scheme, Acc acc, const void* logw,
                                  int64_t N, uint64_t seed, uint64_t step, uint32_t filter,
                                  int32_t* a_out, int32_t* d_or_null, bool fused,
-                                 cudaStream_t st);
+                                 cudaStream_t st, uint8_t* cl_or_null = nullptr);
 cudaError_t launch_cumulative_weights(const Scratch& s, Acc acc, const void* logw, int64_t N,
                                       void* W_out, double* log_total, cudaStream_t st);
 cudaError_t launch_cumulative_weights_f64(const Scratch& s, Acc acc, const void* logw, int64_t N,
@@ -111,7 +111,7 @@ cudaError_t launch_cumulative_weights_f64(const Scratch& s, Acc acc, const void*
 bool fused_available(const Scratch& s, int scheme, Acc acc);
 cudaError_t launch_fused_passes(const Scratch& s, int scheme, Acc acc, const void* logw,
                                 int64_t N, const Keys& keys, int32_t* a_out, int32_t* d,
-                                cudaStream_t st);
+                                uint8_t* cl, cudaStream_t st);
 
 // batched.cu
 cudaError_t launch_batched(const Scratch& s, int scheme, Acc acc, const void* logw,
@@ -163,6 +163,9 @@ cudaError_t launch_permute(const Scratch& s, const int32_t* a, const int32_t* d,
                            int32_t* c, cudaStream_t st);
 cudaError_t launch_permute_sorted(const Scratch& s, const int32_t* a, const int32_t* d, int64_t N,
                                   int32_t* c, cudaStream_t st);
+// the same from the claimed bits cl of the fused emission instead of the claims d
+cudaError_t launch_permute_sorted_bits(const Scratch& s, const int32_t* a, const uint8_t* cl,
+                                       int64_t N, int32_t* c, cudaStream_t st);
 cudaError_t launch_offspring(const Scratch& s, const int32_t* a, int64_t N, int32_t* o,
                              cudaStream_t st);
 cudaError_t launch_inclusive_scan_i32(const Scratch& s, const int32_t* o, int64_t N,

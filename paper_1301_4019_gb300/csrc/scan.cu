@@ -324,14 +324,14 @@ const char* const kLblSearch[4] = {"search_f32", "search_f32c", "search_f64", "s
 template <typename T, typename V>
 cudaError_t run_scan(const Scratch& s, int scheme, Acc acc, const T* lw, int64_t N,
                      uint64_t seed, uint64_t step, uint32_t filter, int32_t* a_out, int32_t* d,
-                     bool fused, cudaStream_t st) {
+                     bool fused, cudaStream_t st, uint8_t* cl) {
   const int tiles = static_cast<int>((N + kTile - 1) / kTile);
   double2* s_rec = s.rec;
   double2* P_rec = s.rec + seg_cap(s.max_tiles);
   const Keys keys = make_keys(seed, step, filter, static_cast<uint32_t>(scheme));
   constexpr int ai = Path<T, V>::id;
   if (fused) {
-    cudaError_t e = launch_fused_passes(s, scheme, acc, lw, N, keys, a_out, d, st);
+    cudaError_t e = launch_fused_passes(s, scheme, acc, lw, N, keys, a_out, d, cl, st);
     if (e != cudaSuccess || scheme != RS_MULTINOMIAL) return e;
     trace_mark(s.trace, kLblSearch[ai], st);
     launch_search<T, V>(s, static_cast<const V*>(s.W), N, keys, a_out, d, st);
@@ -435,20 +435,21 @@ cudaError_t launch_check_weight_exp(double bound, unsigned long long* count, dou
 
 cudaError_t launch_scan_resample(const Scratch& s, int scheme, Acc acc, const void* logw,
                                  int64_t N, uint64_t seed, uint64_t step, uint32_t filter,
-                                 int32_t* a_out, int32_t* d, bool fused, cudaStream_t st) {
+                                 int32_t* a_out, int32_t* d, bool fused, cudaStream_t st,
+                                 uint8_t* cl) {
   switch (acc) {
     case Acc::F32:
       return run_scan<float, float>(s, scheme, acc, static_cast<const float*>(logw), N, seed,
-                                    step, filter, a_out, d, fused, st);
+                                    step, filter, a_out, d, fused, st, cl);
     case Acc::F32C:
       return run_scan<float, float2>(s, scheme, acc, static_cast<const float*>(logw), N, seed,
-                                     step, filter, a_out, d, fused, st);
+                                     step, filter, a_out, d, fused, st, cl);
     case Acc::F64:
       return run_scan<double, float2>(s, scheme, acc, static_cast<const double*>(logw), N, seed,
-                                      step, filter, a_out, d, fused, st);
+                                      step, filter, a_out, d, fused, st, cl);
     case Acc::F64N:
       return run_scan<double, double>(s, scheme, acc, static_cast<const double*>(logw), N, seed,
-                                      step, filter, a_out, d, fused, st);
+                                      step, filter, a_out, d, fused, st, cl);
   }
   return cudaErrorInvalidValue;
 }

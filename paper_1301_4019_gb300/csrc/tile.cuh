@@ -806,6 +806,10 @@ __device__ __forceinline__ void store_per(int32_t* __restrict__ p, const int32_t
 // ancestor indices into a[lo + j] through the warp's window `win` and, when d is given, the
 // Prepermute claims d[lo + i] = O_{i-1} if particle i has offspring, else n (for a
 // non-decreasing ancestry the lowest claimant of slot i is the first position of its run).
+// When cl is given (single sequence, lo = 0), one bit per particle instead: bit i % 8 of
+// cl[i / 8] is set when particle i has offspring (its slot is claimed), the only part of the
+// claims that the Permute of a non-decreasing ancestry cannot read off a itself
+// (permute_sorted_bits_kernel).
 // Ps, Pn: prefixes of this segment and the next; u_sys: the systematic uniform (cta_uniform0;
 // unused when STRAT). Local indices are 32-bit (n < 2^31).
 template <typename T, typename V, bool STRAT>
@@ -814,7 +818,8 @@ __device__ __forceinline__ void emit_seg_cumoff(const T* __restrict__ lw, int64_
                                                 V Ps, V Pn, V S, V scale,
                                                 typename Path<T, V>::U u_sys,
                                                 const Keys& keys, int32_t* __restrict__ a,
-                                                int32_t* __restrict__ d, int32_t* win) {
+                                                int32_t* __restrict__ d, int32_t* win,
+                                                uint8_t* __restrict__ cl = nullptr) {
   const int lane = threadIdx.x & 31;
   const int32_t n = static_cast<int32_t>(N - lo);
   const int cnt = seg_count(base, N) - kPer * lane;  // valid here
@@ -850,6 +855,12 @@ __device__ __forceinline__ void emit_seg_cumoff(const T* __restrict__ lw, int64_
   }
   warp_runs(O, prev, i0, a + lo, win);
   if (d && cnt > 0) store_per(d + lo + i0, dv, cnt);
+  if (cl && cnt > 0) {  // (i0 is a multiple of kPer = 8: one byte per lane)
+    uint32_t bits = 0;
+#pragma unroll
+    for (int q = 0; q < kPer; ++q) bits |= static_cast<uint32_t>(dv[q] != n) << q;
+    cl[i0 >> 3] = static_cast<uint8_t>(bits);
+  }
 }
 
 // Stored cumulative weights of one segment (warp-level): W[e] for e in [lo, N).
