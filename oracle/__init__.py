@@ -75,6 +75,8 @@ def _declare(lib):
         "orc_draw": (None, [_U64, _U32, _U32, _U64, _U32, _U32, _P]),
         "orc_u01_f32": (C.c_float, [_P]),
         "orc_u01_f64": (C.c_double, [_P]),
+        "orc_stratum_u_f32": (C.c_float, [_U64, _I64, _U64, _U32]),
+        "orc_stratum_u_f64": (C.c_double, [_U64, _I64, _U64, _U32]),
         "orc_uniform_index": (_I64, [_P, _I64]),
         "orc_exp_f32": (C.c_float, [C.c_float]),
         "orc_exp_f64": (C.c_double, [C.c_double]),
@@ -164,6 +166,16 @@ def u01_f32(x) -> float:
 def u01_f64(x) -> float:
     x = _c(x, np.uint32)
     return _load().orc_u01_f64(_ptr(x))
+
+
+def stratum_u_f32(seed, k, step=0, filter_=0) -> float:
+    """The binary32 uniform of stratum k of the stratified resampler (Code 7)."""
+    return _load().orc_stratum_u_f32(seed, k, step, filter_)
+
+
+def stratum_u_f64(seed, k, step=0, filter_=0) -> float:
+    """The 53-bit uniform of stratum k of the stratified resampler (Code 7)."""
+    return _load().orc_stratum_u_f64(seed, k, step, filter_)
 
 
 def uniform_index(x, N: int) -> int:

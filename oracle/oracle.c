@@ -83,6 +83,23 @@ double orc_u01_f64(const uint32_t x[4]) {
     return (double)m * 0x1p-53;
 }
 
+/* The uniform u_k of stratum k (Code 7). One Philox block serves consecutive strata: in
+ * binary32 stratum k takes the top 24 bits of word k mod 4 of counter (floor(k/4), 0), times
+ * 2^-24; in binary64 words 2 (k mod 2) and 2 (k mod 2) + 1 of counter (floor(k/2), 0), as
+ * orc_u01_f64 takes words 0 and 1. */
+float orc_stratum_u_f32(uint64_t seed, int64_t k, uint64_t step, uint32_t filter) {
+    uint32_t x[4];
+    orc_draw(seed, (uint32_t)(k / 4), 0u, step, filter, ORC_STRATIFIED, x);
+    return (float)(x[k % 4] >> 8) * 0x1p-24f;
+}
+
+double orc_stratum_u_f64(uint64_t seed, int64_t k, uint64_t step, uint32_t filter) {
+    uint32_t x[4];
+    orc_draw(seed, (uint32_t)(k / 2), 0u, step, filter, ORC_STRATIFIED, x);
+    uint32_t pair[4] = {x[2 * (k % 2)], x[2 * (k % 2) + 1], 0u, 0u};
+    return orc_u01_f64(pair);
+}
+
 /* Uniform index on {0..N-1}: floor(V * N / 2^64) with V = words 2,3 as a 64-bit integer. */
 int64_t orc_uniform_index(const uint32_t x[4], int64_t N) {
     uint64_t v = ((uint64_t)x[2] << 32) | (uint64_t)x[3];
@@ -844,18 +861,14 @@ int orc_systematic_f64(const double* lw, int64_t N, int prec, uint64_t seed, uin
     return orc_cumulative_offspring_to_ancestors(O, N, a);
 }
 
-/* Code 7 then Code 11: the uniform of stratum k comes from counter (k, 0). */
+/* Code 7 then Code 11: the uniform of stratum k is orc_stratum_u_f32 / orc_stratum_u_f64. */
 int orc_stratified_f32(const float* lw, int64_t N, int prec, uint64_t seed, uint64_t step,
                        uint32_t filter, int32_t* O, int32_t* a) {
     float* w = (float*)malloc((size_t)N * sizeof(float));
     int st = orc_weights_f32(lw, N, w, NULL);
     if (st != ORC_OK) { free(w); return st; }
     float* u = (float*)malloc((size_t)N * sizeof(float));
-    for (int64_t k = 0; k < N; ++k) {
-        uint32_t x[4];
-        orc_draw(seed, (uint32_t)k, 0u, step, filter, ORC_STRATIFIED, x);
-        u[k] = orc_u01_f32(x);
-    }
+    for (int64_t k = 0; k < N; ++k) u[k] = orc_stratum_u_f32(seed, k, step, filter);
     if (prec == 0) {
         float* W = (float*)malloc((size_t)N * sizeof(float));
         orc_inclusive_prefix_sum_f32(w, N, W);
@@ -882,11 +895,7 @@ int orc_stratified_f64(const double* lw, int64_t N, int prec, uint64_t seed, uin
     int st = orc_weights_f64(lw, N, w, NULL);
     if (st != ORC_OK) { free(w); return st; }
     double* u = (double*)malloc((size_t)N * sizeof(double));
-    for (int64_t k = 0; k < N; ++k) {
-        uint32_t x[4];
-        orc_draw(seed, (uint32_t)k, 0u, step, filter, ORC_STRATIFIED, x);
-        u[k] = orc_u01_f64(x);
-    }
+    for (int64_t k = 0; k < N; ++k) u[k] = orc_stratum_u_f64(seed, k, step, filter);
     if (prec == 0) {
         double* W = (double*)malloc((size_t)N * sizeof(double));
         orc_inclusive_prefix_sum_f64(w, N, W);

@@ -258,27 +258,149 @@ __device__ __forceinline__ int32_t floor_i32(float2 z) {
   return f != z.x ? i : i + __float2int_rd(z.y);  // hi an integer below 2^31: |lo| < 64
 }
 
+// Uniforms of the strata (Code 7: one uniform u_k per stratum k). One Philox4x32-10 block
+// serves consecutive strata: four at 24 bits (stratum k takes the top 24 bits of word k mod 4
+// of counter floor(k / 4)) and two at 53 bits (words 2 (k mod 2) and 2 (k mod 2) + 1 of
+// counter floor(k / 2), as u01_f64 takes words 0 and 1).
+template <typename U> struct StratumU;
+template <> struct StratumU<float> {
+  static constexpr int kShift = 2;  // log2 of the strata per block
+  __device__ static float from(uint2 w) { return u01_f32(make_uint4(w.x, 0u, 0u, 0u)); }
+};
+template <> struct StratumU<float2> {
+  static constexpr int kShift = 1;
+  __device__ static float2 from(uint2 w) { return u01_f2(make_uint4(w.x, w.y, 0u, 0u)); }
+};
+template <> struct StratumU<double> {
+  static constexpr int kShift = 1;
+  __device__ static double from(uint2 w) { return u01_f64(make_uint4(w.x, w.y, 0u, 0u)); }
+};
+// the word(s) of stratum k in its block x
+template <typename U>
+__device__ __forceinline__ uint2 stratum_words(uint4 x, int32_t k) {
+  if constexpr (StratumU<U>::kShift == 2) {
+    const int j = k & 3;
+    return make_uint2(j == 0 ? x.x : j == 1 ? x.y : j == 2 ? x.z : x.w, 0u);
+  } else {
+    return (k & 1) ? make_uint2(x.z, x.w) : make_uint2(x.x, x.y);
+  }
+}
+template <typename U>
+__device__ __forceinline__ U stratum_u(const Keys& keys, int32_t k) {
+  const uint4 x = draw(keys, static_cast<uint32_t>(k) >> StratumU<U>::kShift, 0u);
+  return StratumU<U>::from(stratum_words<U>(x, k));
+}
+
 // Cumulative offspring of a cumulative weight W (Codes 7 and 8): r = W * c with c = N / W^N
 // rounded once (the order the oracle pins), O = floor(r + u) (systematic) or, for the stratum
 // k = min(n - 1, floor(r)) with its own uniform, min(k + 1, floor(r + u_k)) (stratified);
 // W equal to the total gives O = n (all later weights are zero). r and u are non-negative.
+template <typename T, typename V>
+__device__ __forceinline__ int32_t stratum_of(V r, int32_t n) {
+  const int32_t k = floor_i32(r);
+  return k < n - 1 ? k : n - 1;
+}
+template <typename T, typename V>
+__device__ __forceinline__ int32_t strat_count(V r, int32_t k, typename Path<T, V>::U uk,
+                                               int32_t n) {
+  int32_t o = floor_i32(vplus_u(r, uk));
+  o = o < k + 1 ? o : k + 1;
+  return o < n ? o : n;
+}
 template <typename T, typename V, bool STRAT>
 __device__ __forceinline__ int32_t cum_offspring(V W, V S, V scale,
                                                  typename Path<T, V>::U u_sys,
                                                  const Keys& keys, int32_t n) {
   if (vsame(W, S)) return n;
   const V r = vscale(W, scale);
-  int32_t o;
   if constexpr (STRAT) {
-    int32_t k = floor_i32(r);
-    k = k < n - 1 ? k : n - 1;
-    const auto uk = Path<T, V>::draw_u(draw(keys, static_cast<uint32_t>(k), 0u));
-    o = floor_i32(vplus_u(r, uk));
-    o = o < k + 1 ? o : k + 1;
+    const int32_t k = stratum_of<T, V>(r, n);
+    return strat_count<T, V>(r, k, stratum_u<typename Path<T, V>::U>(keys, k), n);
   } else {
-    o = floor_i32(vplus_u(r, u_sys));
+    const int32_t o = floor_i32(vplus_u(r, u_sys));
+    return o < n ? o : n;
   }
-  return o < n ? o : n;
+}
+
+// Stratified cumulative offspring of a warp's kPer particles per lane (W) and, in lane 0 when
+// `has_b`, of the particle before them (Wb -> Ob), with the Philox blocks shared: the strata
+// of the warp are non-decreasing in particle order, so each block the warp needs is listed
+// once (where it differs from the previous particle's), drawn by one lane (the list dealt
+// over the lanes) into the warp's shared table, and read back by every particle of it:
+// about span / 4 + 1 blocks for a warp whose strata span `span` (binary32), instead of one
+// per particle. A warp needing more than kStratCap blocks draws per particle. The uniforms,
+// and so the counts, are those of cum_offspring.
+constexpr int kStratCap = 160;
+
+template <typename T, typename V>
+__device__ __forceinline__ void strat_offspring_warp(const V (&W)[kPer], V Wb, V S, V scale,
+                                                     const Keys& keys, int32_t n, bool has_b,
+                                                     int32_t (&O)[kPer], int32_t& Ob) {
+  using U = typename Path<T, V>::U;
+  constexpr int sh = StratumU<U>::kShift;
+  __shared__ uint4 tab[kWarps][kStratCap];
+  const int lane = threadIdx.x & 31;
+  uint4* const tw = tab[threadIdx.x >> 5];
+  V r[kPer];
+  int32_t k[kPer];
+  uint32_t all = 0;  // W = W^N: O = n, no uniform
+#pragma unroll
+  for (int q = 0; q < kPer; ++q) {
+    all |= static_cast<uint32_t>(vsame(W[q], S)) << q;
+    r[q] = vscale(W[q], scale);
+    k[q] = stratum_of<T, V>(r[q], n);
+  }
+  const V rb = vscale(Wb, scale);
+  const int32_t kb = stratum_of<T, V>(rb, n);
+  const bool first_b = lane == 0 && has_b;
+  int32_t cprev = __shfl_up_sync(0xffffffffu, k[kPer - 1] >> sh, 1);
+  if (lane == 0) cprev = has_b ? (kb >> sh) : -1;
+  uint32_t nm = 0;  // particles whose block differs from the one before
+#pragma unroll
+  for (int q = 0; q < kPer; ++q) {
+    const int32_t c = k[q] >> sh;
+    nm |= static_cast<uint32_t>(c != cprev) << q;
+    cprev = c;
+  }
+  const int mine = __popc(nm) + (first_b ? 1 : 0);
+  int incl = mine;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += y;
+  }
+  const int total = __shfl_sync(0xffffffffu, incl, 31);
+  const int ex = incl - mine;  // this lane's first entry
+  if (total <= kStratCap) {  // (warp-uniform)
+    int pos = ex;
+    if (first_b) tw[pos++].x = static_cast<uint32_t>(kb >> sh);
+#pragma unroll
+    for (int q = 0; q < kPer; ++q)
+      if ((nm >> q) & 1u) tw[pos++].x = static_cast<uint32_t>(k[q] >> sh);
+    __syncwarp();
+    for (int j = lane; j < total; j += 32) tw[j] = draw(keys, tw[j].x, 0u);
+    __syncwarp();
+    auto u_at = [&](int t, int32_t kk) -> U {
+      if constexpr (sh == 2) {
+        return StratumU<U>::from(make_uint2(reinterpret_cast<const uint32_t*>(tw + t)[kk & 3], 0u));
+      } else {
+        return StratumU<U>::from(reinterpret_cast<const uint2*>(tw + t)[kk & 1]);
+      }
+    };
+    if (first_b) Ob = vsame(Wb, S) ? n : strat_count<T, V>(rb, kb, u_at(0, kb), n);
+    int t = ex + (first_b ? 1 : 0) - 1;  // the entry before this lane's first particle
+#pragma unroll
+    for (int q = 0; q < kPer; ++q) {
+      t += static_cast<int>((nm >> q) & 1u);
+      O[q] = ((all >> q) & 1u) ? n : strat_count<T, V>(r[q], k[q], u_at(t, k[q]), n);
+    }
+    __syncwarp();  // (the table is rewritten by the warp's next segment)
+  } else {
+    if (first_b) Ob = vsame(Wb, S) ? n : strat_count<T, V>(rb, kb, stratum_u<U>(keys, kb), n);
+#pragma unroll
+    for (int q = 0; q < kPer; ++q)
+      O[q] = ((all >> q) & 1u) ? n : strat_count<T, V>(r[q], k[q], stratum_u<U>(keys, k[q]), n);
+  }
 }
 
 // ---------------------------------------------------------------------------------------
@@ -830,12 +952,18 @@ __device__ __forceinline__ void emit_seg_cumoff(const T* __restrict__ lw, int64_
   // past the end repeat the count before them (no offspring). A lane with a position past
   // the end holds the sequence's last particle or none, so its last count is n either way.
   int32_t O[kPer];
+  int32_t Ob = n;  // (lane 0: the count before the segment)
+  if constexpr (STRAT) {
+    strat_offspring_warp<T, V>(W, Wb, S, scale, keys, n, cnt > 0, O, Ob);
+  } else {
 #pragma unroll
-  for (int q = 0; q < kPer; ++q) O[q] = cum_offspring<T, V, STRAT>(W[q], S, scale, u_sys, keys, n);
+    for (int q = 0; q < kPer; ++q) O[q] = cum_offspring<T, V, STRAT>(W[q], S, scale, u_sys, keys, n);
+    if (lane == 0 && cnt > 0) Ob = cum_offspring<T, V, STRAT>(Wb, S, scale, u_sys, keys, n);
+  }
   const int32_t last = (cnt >= kPer && i0 + kPer - 1 != n - 1) ? O[kPer - 1] : n;
   int32_t prev = __shfl_up_sync(0xffffffffu, last, 1);
   if (lane == 0)  // (a segment wholly past the end follows the sequence's last particle: n)
-    prev = cnt > 0 ? cum_offspring<T, V, STRAT>(Wb, S, scale, u_sys, keys, n) : n;
+    prev = Ob;
   int32_t dv[kPer];
   int32_t p = prev;
   if (base + kSeg < N) {  // (warp-uniform) all kSeg particles valid, none the sequence's last

@@ -38,6 +38,19 @@ import numpy as np
 
 import oracle
 
+
+def stratum_u(seed: int, k: int, step: int, filter_: int, f32: bool) -> float:
+    """u_k of the stratified resampler, restated from its definition: one Philox4x32-10 block
+    serves four strata at 24 bits (stratum k: the top 24 bits of word k mod 4 of counter
+    k div 4, times 2^-24) or two at 53 bits (words 2 (k mod 2) and 2 (k mod 2) + 1 of counter
+    k div 2, read as u01_f64 reads words 0 and 1)."""
+    if f32:
+        x = oracle.draw(seed, k // 4, 0, step, filter_, oracle.STRATIFIED)
+        return (int(x[k % 4]) >> 8) * 2.0 ** -24
+    x = oracle.draw(seed, k // 2, 0, step, filter_, oracle.STRATIFIED)
+    m = (int(x[2 * (k % 2)]) << 21) | (int(x[2 * (k % 2) + 1]) >> 11)
+    return m * 2.0 ** -53
+
 KERNEL_C = {"f32": 80.0, "f32c": 64.0, "f64": 64.0, "f64n": 64.0}
 EPS = {"f32": 2.0 ** -24, "f32c": 2.0 ** -44, "f64": 2.0 ** -43, "f64n": 2.0 ** -53}
 EPS_DTYPE = {"f32": 2.0 ** -24, "f32c": 2.0 ** -24, "f64": 2.0 ** -53, "f64n": 2.0 ** -53}
@@ -84,8 +97,7 @@ def cumulative_mismatches(kind: str, scheme: int, lw: np.ndarray, O_kernel: np.n
         k = np.clip(np.floor(r).astype(np.int64), 0, N - 1)
         for dk in (-1, 0, 1):
             kk = np.clip(k + dk, 0, N - 1)
-            uk = np.array([u01(oracle.draw(seed, int(x), 0, step, filter_, oracle.STRATIFIED))
-                           for x in kk[diff]])
+            uk = np.array([stratum_u(seed, int(x), step, filter_, f32) for x in kk[diff]])
             near_d = np.zeros(N, bool)
             near_d[diff] = _dist_to_int(r[diff] + uk) <= (tol[diff] if np.ndim(tol) else tol)
             near |= near_d

@@ -12,6 +12,7 @@ from scipy import stats
 
 import oracle
 import workload
+from parity_tools import stratum_u
 
 
 def _pi(w):
@@ -245,7 +246,7 @@ def test_one_ancestor_per_stratum_exact(scheme, prec):
         us = [u0] * N
     else:
         st, O, a = oracle.stratified(lw, seed, prec=prec)
-        us = [oracle.u01_f64(oracle.draw(seed, k, 0, 0, 0, oracle.STRATIFIED)) for k in range(N)]
+        us = [stratum_u(seed, k, 0, 0, False) for k in range(N)]
     assert st == oracle.OK
     _, w, _ = oracle.weights(lw)
     Wf = _exact_prefix(w)
@@ -363,3 +364,22 @@ def test_scale_invariance_exact():
         _, r0 = oracle.rejection(lw, 0.0, seed=3)
         _, r1 = oracle.rejection(lw + c, c, seed=3)
         assert np.array_equal(r0, r1)
+
+
+@pytest.mark.parametrize("f32", [True, False])
+def test_stratum_uniforms_share_blocks(f32):
+    """The oracle's stratum uniforms follow the block mapping (four strata per Philox block at
+    24 bits, two at 53), are exact multiples of 2^-24 / 2^-53 in [0, 1), and strata that share
+    a block take distinct words of it (so they are independent draws)."""
+    seed, step, filt = 987654321, 7, 3
+    f = oracle.stratum_u_f32 if f32 else oracle.stratum_u_f64
+    per = 4 if f32 else 2
+    us = [f(seed, k, step, filt) for k in range(64)]
+    for k, u in enumerate(us):
+        assert u == stratum_u(seed, k, step, filt, f32)
+        assert 0.0 <= u < 1.0
+        assert (u * 2.0 ** (24 if f32 else 53)).is_integer()
+    # within a block the uniforms are distinct words; blocks do not repeat
+    for b in range(0, 64, per):
+        assert len(set(us[b:b + per])) == per
+    assert len(set(us)) == 64

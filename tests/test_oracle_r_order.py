@@ -11,6 +11,7 @@ import numpy as np
 import pytest
 
 import oracle
+from parity_tools import stratum_u
 
 
 def _zero_one_logw(N, K, rng, dtype):
@@ -38,7 +39,7 @@ def test_exact_zero_one_weights_match_rationals(dtype):
         for i in range(N):
             r = Fraction(N * int(W[i]), K)
             k = min(N - 1, int(r // 1))
-            uk = Fraction(u01(oracle.draw(seed, k, 0, 0, 0, oracle.STRATIFIED)))
+            uk = Fraction(stratum_u(seed, k, 0, 0, dtype == np.float32))
             o = min(N, k + 1, int((r + uk) // 1))
             assert O[i] == (N if W[i] == K else o), i
 
