@@ -307,8 +307,10 @@ def kernel_roofline_units(label: str, N: int, B: int):
         return "hbm", S * N + V * N, "B"           # read logw, write W
     if label.startswith("search_"):
         return "hbm", V * N + 4 * N, "B"           # read W once, write a
+    if label.startswith("metropolis_f32"):
+        return "alu", (B + 1) // 2 * N, "Philox"   # one Philox4x32-10 block per two steps
     if label.startswith("metropolis_"):
-        return "alu", B * N, "Philox"              # one Philox4x32-10 draw per step
+        return "alu", B * N, "Philox"              # one Philox4x32-10 block per step
     if label.startswith("rejection_"):
         return "alu", None, "Philox"
     if label in ("permute", "permute_sorted"):

@@ -78,6 +78,8 @@ def _declare(lib):
         "orc_stratum_u_f32": (C.c_float, [_U64, _I64, _U64, _U32]),
         "orc_stratum_u_f64": (C.c_double, [_U64, _I64, _U64, _U32]),
         "orc_uniform_index": (_I64, [_P, _I64]),
+        "orc_half_u01_f32": (C.c_float, [_P, C.c_int]),
+        "orc_half_index": (_I64, [_P, C.c_int, _I64]),
         "orc_exp_f32": (C.c_float, [C.c_float]),
         "orc_exp_f64": (C.c_double, [C.c_double]),
         "orc_metropolis_f32": (C.c_int, [_P, _I64, _I32, _U64, _U64, _U32, _P]),
@@ -181,6 +183,18 @@ def stratum_u_f64(seed, k, step=0, filter_=0) -> float:
 def uniform_index(x, N: int) -> int:
     x = _c(x, np.uint32)
     return _load().orc_uniform_index(_ptr(x), N)
+
+
+def half_u01_f32(x, h: int) -> float:
+    """Uniform of step half h (0, 1) of a binary32 Metropolis block."""
+    x = _c(x, np.uint32)
+    return _load().orc_half_u01_f32(_ptr(x), h)
+
+
+def half_index(x, h: int, N: int) -> int:
+    """Proposal of step half h (0, 1) of a binary32 Metropolis block (40-bit index)."""
+    x = _c(x, np.uint32)
+    return _load().orc_half_index(_ptr(x), h, N)
 
 
 def exp_f32(x: float) -> np.float32:

@@ -107,6 +107,18 @@ int64_t orc_uniform_index(const uint32_t x[4], int64_t N) {
     return (int64_t)(uint64_t)(p >> 64);
 }
 
+/* The binary32 Metropolis chain takes two steps from one block: step half h (0 or 1) uses
+ * words 2h and 2h + 1. Its uniform is the top 24 bits of word 2h times 2^-24; its proposal is
+ * floor(V * N / 2^40) with V = (the low 8 bits of word 2h) * 2^32 + word 2h + 1, a 40-bit
+ * integer (each index has probability within a factor 1 +- N / 2^40 of 1/N). */
+float orc_half_u01_f32(const uint32_t x[4], int h) { return (float)(x[2 * h] >> 8) * 0x1p-24f; }
+
+int64_t orc_half_index(const uint32_t x[4], int h, int64_t N) {
+    uint64_t v = ((uint64_t)(x[2 * h] & 0xffu) << 32) | (uint64_t)x[2 * h + 1];
+    unsigned __int128 p = (unsigned __int128)v * (unsigned __int128)(uint64_t)N;
+    return (int64_t)(uint64_t)(p >> 40);
+}
+
 /* ------------------------------------------------------------------------------------ */
 /* Pinned exponential (both precisions), defined for x <= 0                               */
 /* ------------------------------------------------------------------------------------ */
@@ -193,8 +205,10 @@ static int metropolis_accept_f64(double lwk, double lwj, double u) {
     return u < orc_exp_f64(delta);
 }
 
-/* For each particle i: start the chain at k = i; for n = 0..B-1 draw (u, j) from counter
- * (i, n) and move to j on acceptance; the ancestor is the final state. */
+/* For each particle i: start the chain at k = i; for n = 0..B-1 draw (u, j) and move to j on
+ * acceptance; the ancestor is the final state. Binary32: step n takes half n mod 2 of the
+ * block of counter (i, floor(n/2)) (orc_half_u01_f32, orc_half_index); binary64: the block of
+ * counter (i, n), its 53-bit uniform and 64-bit index. */
 int orc_metropolis_f32(const float* lw, int64_t N, int32_t B, uint64_t seed, uint64_t step,
                        uint32_t filter, int32_t* a) {
     if (check_n(N) != ORC_OK || B < 0) return ORC_ERR_ARG;
@@ -204,9 +218,9 @@ int orc_metropolis_f32(const float* lw, int64_t N, int32_t B, uint64_t seed, uin
         float lwk = lw[i];
         for (int32_t n = 0; n < B; ++n) {
             uint32_t x[4];
-            orc_draw(seed, (uint32_t)i, (uint32_t)n, step, filter, ORC_METROPOLIS, x);
-            int64_t j = orc_uniform_index(x, N);
-            float u = orc_u01_f32(x);
+            orc_draw(seed, (uint32_t)i, (uint32_t)(n / 2), step, filter, ORC_METROPOLIS, x);
+            int64_t j = orc_half_index(x, n % 2, N);
+            float u = orc_half_u01_f32(x, n % 2);
             float lwj = lw[j];
             if (metropolis_accept_f32(lwk, lwj, u)) {
                 k = j;

@@ -97,6 +97,21 @@ __device__ __forceinline__ int64_t uniform_index(uint4 x, int64_t N) {
   return static_cast<int64_t>(hi >> 32);
 }
 
+// The two step halves of a binary32 Metropolis block (h = 0: words 0, 1; h = 1: words 2, 3):
+// the uniform is the top 24 bits of the first word times 2^-24, the proposal floor(V N / 2^40)
+// with V = (the first word's low byte) 2^32 + the second word. With Q = (V >> 32) N and
+// P = (V mod 2^32) N, V N = (Q + floor(P / 2^32)) 2^32 + (P mod 2^32) and the last term
+// cannot carry past bit 40, so the index is (Q + floor(P / 2^32)) / 2^8 rounded down.
+__device__ __forceinline__ float half_u01_f32(uint32_t w0) {
+  return __fmul_rn(__uint2float_rn(w0 >> 8), 0x1p-24f);
+}
+__device__ __forceinline__ int64_t half_index(uint32_t w0, uint32_t w1, int64_t N) {
+  const uint64_t n = static_cast<uint64_t>(N);
+  const uint64_t P = static_cast<uint64_t>(w1) * n;
+  const uint64_t Q = static_cast<uint64_t>(w0 & 0xffu) * n;
+  return static_cast<int64_t>((Q + (P >> 32)) >> 8);
+}
+
 // ---------------------------------------------------------------------------------------
 // Pinned exponential for x <= 0, identical bit for bit on host and device: Cody & Waite
 // argument reduction (x = k ln2 + r with ln2 split in head and tail), Taylor polynomial of

@@ -144,25 +144,30 @@ __device__ __forceinline__ float f64_sidecar(double x) {
 constexpr int kUnroll = 4;    // binary32 chains: proposals issued together
 constexpr int kUnroll64 = 4;  // binary64 chains (2 measured slower)
 
-// Metropolis chain of particle i over n log-weights lw (Code 2): B steps, step s proposes j
-// and draws u from counter (i, s). Returns the ancestor.
+// Metropolis chain of particle i over n binary32 log-weights lw (Code 2): B steps; steps 2m
+// and 2m + 1 take the two halves of the block of counter (i, m) (half_u01_f32, half_index),
+// so a chain draws ceil(B / 2) blocks. Returns the ancestor.
 __device__ __forceinline__ int32_t metropolis_one(const float* __restrict__ lw, int64_t n,
                                                   int32_t B, const Keys& keys, int64_t i,
                                                   int* err) {
+  static_assert(kUnroll % 2 == 0, "whole blocks per round");
   float lwk = __ldg(lw + i);
   if (nonfinite_logw(lwk)) flag_error(err, RS_ERR_NONFINITE);
   int64_t k = i;
   const uint32_t ii = static_cast<uint32_t>(i);
   int32_t s = 0;
-  for (; s + kUnroll <= B; s += kUnroll) {
+  for (; s + kUnroll <= B; s += kUnroll) {  // (s even)
     float u[kUnroll], lwj[kUnroll];
     int64_t j[kUnroll];
 #pragma unroll
-    for (int q = 0; q < kUnroll; ++q) {
-      const uint4 x = draw(keys, ii, static_cast<uint32_t>(s + q));
-      j[q] = uniform_index(x, n);
-      u[q] = u01_f32(x);
-      lwj[q] = __ldg(lw + j[q]);
+    for (int p = 0; p < kUnroll / 2; ++p) {
+      const uint4 x = draw(keys, ii, static_cast<uint32_t>(s / 2 + p));
+      j[2 * p] = half_index(x.x, x.y, n);
+      u[2 * p] = half_u01_f32(x.x);
+      j[2 * p + 1] = half_index(x.z, x.w, n);
+      u[2 * p + 1] = half_u01_f32(x.z);
+      lwj[2 * p] = __ldg(lw + j[2 * p]);
+      lwj[2 * p + 1] = __ldg(lw + j[2 * p + 1]);
     }
 #pragma unroll
     for (int q = 0; q < kUnroll; ++q) {
@@ -172,13 +177,21 @@ __device__ __forceinline__ int32_t metropolis_one(const float* __restrict__ lw, 
       }
     }
   }
-  for (; s < B; ++s) {
-    const uint4 x = draw(keys, ii, static_cast<uint32_t>(s));
-    const int64_t j = uniform_index(x, n);
-    const float lwj = __ldg(lw + j);
-    if (metropolis_accept(lwk, lwj, u01_f32(x))) {
-      k = j;
-      lwk = lwj;
+  for (; s < B; s += 2) {  // the last B mod kUnroll steps, a block per two
+    const uint4 x = draw(keys, ii, static_cast<uint32_t>(s / 2));
+    const int64_t j0 = half_index(x.x, x.y, n);
+    const float lwj0 = __ldg(lw + j0);
+    if (metropolis_accept(lwk, lwj0, half_u01_f32(x.x))) {
+      k = j0;
+      lwk = lwj0;
+    }
+    if (s + 1 < B) {
+      const int64_t j1 = half_index(x.z, x.w, n);
+      const float lwj1 = __ldg(lw + j1);
+      if (metropolis_accept(lwk, lwj1, half_u01_f32(x.z))) {
+        k = j1;
+        lwk = lwj1;
+      }
     }
   }
   return static_cast<int32_t>(k);

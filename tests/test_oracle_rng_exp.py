@@ -101,6 +101,33 @@ def test_uniforms_and_index_exact():
             j = oracle.uniform_index(x, N)
             assert j == (((x2 << 32) | x3) * N) >> 64
             assert 0 <= j < N
+        # the two step halves of a binary32 Metropolis block: words (0, 1) and (2, 3)
+        for h, (wa, wb) in enumerate(((x0, x1), (x2, x3))):
+            uh = oracle.half_u01_f32(x, h)
+            assert Fraction(uh) == Fraction(wa >> 8, 2**24)
+            for N in [1, 2, 3, 1000, 2**20, 2**31 - 1]:
+                j = oracle.half_index(x, h, N)
+                assert j == ((((wa & 0xFF) << 32) | wb) * N) >> 40
+                assert 0 <= j < N
+
+
+def test_half_index_near_uniform():
+    """The 40-bit proposal index: over all 2^40 values of V each index j is hit by
+    floor or ceil of 2^40 / N values (counted exactly from the inverse map), so its
+    probability is within a factor 1 +- N / 2^40 of 1 / N."""
+    for N in [3, 1000, 2**20 + 7, 2**31 - 1]:
+        # V maps to j iff j N' <= V N < (j + 1) N' with N' = 2^40: V in [ceil(j 2^40 / N),
+        # ceil((j + 1) 2^40 / N)); count for a spread of j
+        T = 2**40
+        for j in [0, 1, N // 3, N // 2, N - 2, N - 1]:
+            if j < 0:
+                continue
+            cnt = -(-(j + 1) * T // N) - (-(-j * T // N))
+            assert T // N <= cnt <= T // N + 1
+            # and the oracle's map sends the first and last such V to j
+            for V in (-(-j * T // N), -(-(j + 1) * T // N) - 1):
+                x = np.array([(V >> 32) & 0xFF, V & 0xFFFFFFFF, 0, 0], np.uint32)
+                assert oracle.half_index(x, 0, N) == j
 
 
 def _ulp32(v):
