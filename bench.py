@@ -593,8 +593,12 @@ def run_ours(args):
     # (w_max = 1: log w_max = 0), one Philox draw each
     w = np.exp(pools["f64"][0].double().cpu().numpy())
     rej_attempts = int(N + np.sum(1.0 - w) / w.mean())
+    # binary32 attempts 2m, 2m + 1 share one block: E ceil(T / 2) per particle, T = 1 with
+    # probability w_i, else 1 + a geometric count of attempts accepting with p = mean(w)
+    q_rej = 1.0 - w.mean()
+    rej_blocks_f32 = int(np.sum(w + (1.0 - w) * (1.0 + q_rej / (1.0 - q_rej ** 2))))
     if dom_label.startswith("rejection_"):
-        amount = rej_attempts
+        amount = rej_blocks_f32 if dom_label.startswith("rejection_f32") else rej_attempts
     if bound == "hbm":
         achieved = amount / (dom_ms * 1e-3) / 1e9 if amount is not None else None
         roof = {"bound": "hbm", "kernel": dom_label,
@@ -622,7 +626,7 @@ def run_ours(args):
     for lab, v in per_kernel.items():  # the Philox-bound kernels against the measured peak
         b, amt, _ = kernel_roofline_units(lab, N, B)
         if lab.startswith("rejection_"):
-            amt = rej_attempts
+            amt = rej_blocks_f32 if lab.startswith("rejection_f32") else rej_attempts
             v["expected_trials_per_particle"] = round(rej_attempts / N, 3)
         if b == "alu" and amt:
             v["philox_frac"] = round(amt / (v["mean_us"] * 1e-6) / 1e9

@@ -270,7 +270,9 @@ int32_t orc_metropolis_B(double eps, double beta) {
 /* ------------------------------------------------------------------------------------ */
 
 /* For each particle i: attempt 0 proposes j = i; attempt n >= 1 proposes j uniformly; both
- * take u from counter (i, n). Accept when u < w^j / w_max, formed as exp(lw^j - log w_max).
+ * draw from counter (i, n) in binary64, and in binary32 from half n mod 2 of the block of
+ * counter (i, floor(n/2)) (orc_half_u01_f32, orc_half_index: two attempts per block, as the
+ * binary32 Metropolis steps). Accept when u < w^j / w_max, formed as exp(lw^j - log w_max).
  * A log-weight above the bound is a violated bound: it is flagged and accepted. After
  * max_trials attempts without acceptance the particle keeps a^i = i and the cap is flagged. */
 int orc_rejection_f32(const float* lw, int64_t N, double log_wmax, int64_t max_trials,
@@ -286,9 +288,9 @@ int orc_rejection_f32(const float* lw, int64_t N, double log_wmax, int64_t max_t
         int accepted = 0;
         while (n < max_trials) {
             uint32_t x[4];
-            orc_draw(seed, (uint32_t)i, (uint32_t)n, step, filter, ORC_REJECTION, x);
-            if (n > 0) j = orc_uniform_index(x, N);
-            float u = orc_u01_f32(x);
+            orc_draw(seed, (uint32_t)i, (uint32_t)(n / 2), step, filter, ORC_REJECTION, x);
+            if (n > 0) j = orc_half_index(x, (int)(n % 2), N);
+            float u = orc_half_u01_f32(x, (int)(n % 2));
             float delta = lw[j] - lwmax;
             n += 1;
             if (delta > 0.0f) {
@@ -367,9 +369,9 @@ int orc_prc_f32(const float* lw, int64_t N, double log_vmax, int64_t max_trials,
         int accepted = 0;
         while (n < max_trials) {
             uint32_t x[4];
-            orc_draw(seed, (uint32_t)i, (uint32_t)n, step, filter, ORC_REJECTION, x);
-            if (n > 0) j = orc_uniform_index(x, N);
-            float u = orc_u01_f32(x);
+            orc_draw(seed, (uint32_t)i, (uint32_t)(n / 2), step, filter, ORC_REJECTION, x);
+            if (n > 0) j = orc_half_index(x, (int)(n % 2), N);
+            float u = orc_half_u01_f32(x, (int)(n % 2));
             float lv = lw[j] < lvmax ? lw[j] : lvmax;
             float delta = lv - lvmax;
             n += 1;

@@ -62,6 +62,29 @@ __device__ __forceinline__ int filter_of(const int64_t* __restrict__ off, int F,
   return lo;
 }
 
+// The filter of position g >= off[f] from the filter f of an earlier position: a few steps
+// past the offsets g has crossed, else filter_of. Same filter as filter_of(off, F, g).
+__device__ __forceinline__ int advance_filter(const int64_t* __restrict__ off, int F, int64_t g,
+                                              int f) {
+  for (int st = 0; st < 8; ++st) {
+    if (f + 1 >= F || __ldg(off + f + 1) > g) return f;
+    ++f;
+  }
+  return (f + 1 < F && __ldg(off + f + 1) <= g) ? filter_of(off, F, g) : f;
+}
+
+// locate_particle for position g < off[F] once its filter f is known.
+__device__ __forceinline__ bool locate_in(const int64_t* __restrict__ off, int f, int64_t max_n,
+                                          int64_t g, PartLoc& P) {
+  P.f = f;
+  P.lo = __ldg(off + f);
+  const int64_t hi = __ldg(off + f + 1);
+  P.n = hi - P.lo;
+  P.i = g - P.lo;
+  return P.lo >= 0 && hi <= max_n && P.n > 0 &&
+         P.n <= kBatchMaxN && P.i >= 0 && P.i < P.n;
+}
+
 // Tile t of the batch -> its filter (the last f with tile_start[f] <= t).
 __device__ __forceinline__ int filter_of_tile(const int32_t* __restrict__ ts, int F, int t) {
   int lo = 0, hi = F;
@@ -451,15 +474,43 @@ batch_search_kernel(const V* __restrict__ W, Batch b, int64_t total, Keys base_k
   if (d) atomicMin(d + P.lo + k, static_cast<int32_t>(P.i));
 }
 
-// Claims start from the sentinel n of each particle's filter.
+// Claims start from the sentinel n of each particle's filter. Eight consecutive particles per
+// thread: the filter of the first is found by binary search (filter_of) and the others by
+// stepping past the offsets they cross; each particle gets what locate_particle gives it
+// (nothing when it fails), stored 128 bits at a time where all eight are set.
+constexpr int kFillPer = 8;
 __global__ void __launch_bounds__(kBlock)
 batch_fill_sentinel_kernel(const int64_t* __restrict__ off, int F, int64_t total,
                            int32_t* __restrict__ d) {
   pdl_wait();
-  const int64_t g = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
-  PartLoc P;
-  if (g >= total || !locate_particle(off, F, total, g, P)) return;
-  d[g] = static_cast<int32_t>(P.n);
+  const int64_t g0 = kFillPer * (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x);
+  const int64_t offF = __ldg(off + F);
+  const int64_t end = offF < total ? offF : total;
+  if (g0 >= end) return;
+  int f = filter_of(off, F, g0);
+  int32_t v[kFillPer];
+  unsigned set = 0;
+#pragma unroll
+  for (int q = 0; q < kFillPer; ++q) {
+    const int64_t g = g0 + q;
+    v[q] = 0;
+    if (g >= end) continue;
+    f = advance_filter(off, F, g, f);
+    PartLoc P;
+    if (locate_in(off, f, total, g, P)) {
+      v[q] = static_cast<int32_t>(P.n);
+      set |= 1u << q;
+    }
+  }
+  if (set == (1u << kFillPer) - 1u && (reinterpret_cast<uintptr_t>(d + g0) & 15u) == 0) {
+    int4* const p4 = reinterpret_cast<int4*>(d + g0);
+    p4[0] = make_int4(v[0], v[1], v[2], v[3]);
+    p4[1] = make_int4(v[4], v[5], v[6], v[7]);
+  } else {
+#pragma unroll
+    for (int q = 0; q < kFillPer; ++q)
+      if ((set >> q) & 1u) d[g0 + q] = v[q];
+  }
 }
 
 // First particle of item q of this thread when each CTA covers blockDim.x * ipt consecutive
@@ -580,11 +631,14 @@ batch_permute_kernel(const int64_t* __restrict__ off, int F, int64_t total,
                      const int32_t* __restrict__ a, const int32_t* __restrict__ d,
                      int32_t* __restrict__ c, int ipt, int* err) {
   pdl_wait();
+  const int64_t offF = __ldg(off + F);
+  int f = -1;  // the filter of this thread's previous item (items ascend by blockDim.x)
   for (int q = 0; q < ipt; ++q) {
     const int64_t g = item_index(ipt, q);
-    if (g >= total) return;
+    if (g >= total || g >= offF) return;
+    f = f < 0 ? filter_of(off, F, g) : advance_filter(off, F, g, f);
     PartLoc P;
-    if (!locate_particle(off, F, total, g, P)) continue;
+    if (!locate_in(off, f, total, g, P)) continue;
     permute_one(a + P.lo, d + P.lo, P.n, c + P.lo, P.i, err);
   }
 }
@@ -692,7 +746,9 @@ cudaError_t launch_batched(const Scratch& s, int scheme, Acc acc, const void* lo
   if (scheme == RS_METROPOLIS || scheme == RS_REJECTION) {
     if (d) {
       trace_mark(s.trace, "batch_fill", st);
-      launch_pdl(batch_fill_sentinel_kernel, grid_particles(total), kBlock, st, offsets, F, total, d);
+      launch_pdl(batch_fill_sentinel_kernel,
+                 static_cast<int>((total + kFillPer * kBlock - 1) / (kFillPer * kBlock)), kBlock, st,
+                 offsets, F, total, d);
     }
     trace_mark(s.trace, scheme == RS_METROPOLIS ? (f64 ? "batch_metropolis_f64" : "batch_metropolis_f32")
                                                 : (f64 ? "batch_rejection_f64" : "batch_rejection_f32"),

@@ -320,9 +320,10 @@ __device__ __forceinline__ int32_t metropolis_one_sc(const double* __restrict__ 
 }
 
 // Rejection loop of particle i (Code 3): attempt 0 proposes j = i, attempt s >= 1 a uniform
-// j; both draw u from counter (i, s); accept when u < exp(lw^j - log w_max). A log-weight
-// above the bound is flagged and accepted; max_trials attempts without acceptance keep i and
-// flag the cap. *trials receives the attempts made.
+// j; binary64 attempts draw from counter (i, s), binary32 ones from half s mod 2 of the block
+// of counter (i, floor(s/2)) (half_u01_f32, half_index); accept when u < exp(lw^j - log w_max).
+// A log-weight above the bound is flagged and accepted; max_trials attempts without
+// acceptance keep i and flag the cap.
 __device__ __forceinline__ int32_t rejection_one(const float* __restrict__ lw, int64_t n,
                                                  double log_wmax, int64_t max_trials,
                                                  const Keys& keys, int64_t i, int* err) {
@@ -331,10 +332,12 @@ __device__ __forceinline__ int32_t rejection_one(const float* __restrict__ lw, i
   if (nonfinite_logw(lwi)) flag_error(err, RS_ERR_NONFINITE);
   const uint32_t ii = static_cast<uint32_t>(i);
   int64_t j = i;
+  uint4 x = make_uint4(0u, 0u, 0u, 0u);
   for (int64_t s = 0; s < max_trials; ++s) {
-    const uint4 x = draw(keys, ii, static_cast<uint32_t>(s));
-    if (s > 0) j = uniform_index(x, n);
-    const float u = u01_f32(x);
+    if ((s & 1) == 0) x = draw(keys, ii, static_cast<uint32_t>(s >> 1));
+    const uint32_t w0 = (s & 1) ? x.z : x.x, w1 = (s & 1) ? x.w : x.y;
+    if (s > 0) j = half_index(w0, w1, n);
+    const float u = half_u01_f32(w0);
     const float lwj = (s == 0) ? lwi : __ldg(lw + j);
     const float delta = lwj - lwmax;
     if (delta > 0.0f) {
@@ -407,12 +410,11 @@ __device__ __forceinline__ RejBound make_bound(double log_wmax, bool clamp = fal
   return r;
 }
 
-// Decision of one rejection attempt with draw x and proposal log-weight lwj: accept when
-// u < exp(lw^j - log w_max); a log-weight above the bound is flagged (unless clamped) and
-// accepted.
-__device__ __forceinline__ bool rejection_accept(const RejBound& rb, uint4 x, float lwj,
+// Decision of one rejection attempt with uniform u (binary32) or draw x (binary64) and
+// proposal log-weight lwj: accept when u < exp(lw^j - log w_max); a log-weight above the bound
+// is flagged (unless clamped) and accepted.
+__device__ __forceinline__ bool rejection_accept(const RejBound& rb, float u, float lwj,
                                                  int* err) {
-  const float u = u01_f32(x);
   const float delta = lwj - rb.lwmax_rn;
   if (delta > 0.0f) {
     if (!rb.clamp) flag_error(err, RS_ERR_BOUND_VIOLATED);
@@ -478,6 +480,38 @@ __device__ __forceinline__ bool rejection_attempts(const T* __restrict__ lw, int
   for (int q = 0; q < K; ++q) {
     if (static_cast<int64_t>(s) + q >= max_trials) return false;
     if (rejection_accept(rb, x[q], lwj[q], err)) {
+      j = jq[q];
+      return true;
+    }
+  }
+  return false;
+}
+
+// The same for binary32 log-weights, whose attempts 2m and 2m + 1 share the block of counter
+// (i, m) (s even, K even): K / 2 blocks for K attempts.
+template <int K>
+__device__ __forceinline__ bool rejection_attempts(const float* __restrict__ lw, int64_t n,
+                                                   const RejBound& rb, const Keys& keys,
+                                                   int64_t i, uint32_t s, float lwi,
+                                                   int64_t max_trials, int64_t& j, int* err) {
+  static_assert(K % 2 == 0, "whole blocks");
+  float u[K], lwj[K];
+  int64_t jq[K];
+#pragma unroll
+  for (int p = 0; p < K / 2; ++p) {
+    const uint4 x = draw(keys, static_cast<uint32_t>(i), s / 2 + static_cast<uint32_t>(p));
+    const uint32_t s0 = s + 2 * static_cast<uint32_t>(p);
+    jq[2 * p] = (s0 > 0) ? half_index(x.x, x.y, n) : i;
+    u[2 * p] = half_u01_f32(x.x);
+    jq[2 * p + 1] = half_index(x.z, x.w, n);
+    u[2 * p + 1] = half_u01_f32(x.z);
+    lwj[2 * p] = (s0 > 0) ? __ldg(lw + jq[2 * p]) : lwi;
+    lwj[2 * p + 1] = __ldg(lw + jq[2 * p + 1]);
+  }
+#pragma unroll
+  for (int q = 0; q < K; ++q) {
+    if (static_cast<int64_t>(s) + q >= max_trials) return false;
+    if (rejection_accept(rb, u[q], lwj[q], err)) {
       j = jq[q];
       return true;
     }
