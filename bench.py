@@ -227,26 +227,26 @@ class ClockSampler:
 # headers it includes, hashed; `traffic` is null once any of them has changed.
 # ---------------------------------------------------------------------------------------
 NCU_TRAFFIC = {  # label: (bytes per launch, source hash)
-    "offspring": (8391424, "75d1007247b47cad"),
-    "iscan": (4214048, "75d1007247b47cad"),
-    "adjacent_difference": (4198608, "75d1007247b47cad"),
-    "cumoff_to_ancestors": (4204608, "75d1007247b47cad"),
-    "fill": (8392, "75d1007247b47cad"),
-    "fused_multinomial_f32": (4350592, "843d08cc262f3307"),
-    "search_f32": (12592128, "da21887443d9d760"),
-    "permute": (8397363, "75d1007247b47cad"),
-    "fused_stratified_f32": (4327232, "843d08cc262f3307"),
-    "permute_sorted": (8397756, "75d1007247b47cad"),
-    "fused_systematic_f32": (4326944, "843d08cc262f3307"),
-    "metropolis_f32": (8405120, "366ada29b2119d6b"),
-    "rejection_f32": (4213760, "366ada29b2119d6b"),
-    "fused_multinomial_f64": (8524640, "843d08cc262f3307"),
-    "search_f64": (16784165, "da21887443d9d760"),
-    "fused_stratified_f64": (8511269, "843d08cc262f3307"),
-    "fused_systematic_f64": (8500882, "843d08cc262f3307"),
-    "sidecar": (8394203, "366ada29b2119d6b"),
-    "metropolis_f64": (16801536, "366ada29b2119d6b"),
-    "rejection_f64": (8424448, "366ada29b2119d6b")}
+    "permute": (8397761, "d12f9b06a52d609d"),
+    "metropolis_f64": (16806290, "e0ca71fa2e23442f"),
+    "metropolis_f32": (8402752, "e0ca71fa2e23442f"),
+    "rejection_f64": (8420974, "e0ca71fa2e23442f"),
+    "fused_multinomial_f64": (8527008, "89e373c4e6b95bd3"),
+    "rejection_f32": (4212416, "e0ca71fa2e23442f"),
+    "fused_stratified_f64": (8513353, "89e373c4e6b95bd3"),
+    "permute_sorted": (4332962, "d12f9b06a52d609d"),
+    "fused_systematic_f64": (8506551, "89e373c4e6b95bd3"),
+    "fused_multinomial_f32": (4351360, "89e373c4e6b95bd3"),
+    "fused_stratified_f32": (4330816, "89e373c4e6b95bd3"),
+    "fused_systematic_f32": (4328736, "89e373c4e6b95bd3"),
+    "iscan": (4215152, "d12f9b06a52d609d"),
+    "search_f32": (12591104, "d3b9ad961ad2fadf"),
+    "search_f64": (16783104, "d3b9ad961ad2fadf"),
+    "cumoff_to_ancestors": (4204096, "d12f9b06a52d609d"),
+    "offspring": (8391344, "d12f9b06a52d609d"),
+    "fill": (8403, "d12f9b06a52d609d"),
+    "adjacent_difference": (4198720, "d12f9b06a52d609d"),
+    "sidecar": (8394240, "e0ca71fa2e23442f")}
 
 _LABEL_FILES = (("fused_", "fused.cu"), ("permute", "aux.cu"), ("iscan", "aux.cu"),
                 ("fill", "aux.cu"), ("offspring", "aux.cu"), ("adjacent", "aux.cu"),
