@@ -28,7 +28,11 @@
  *    valid indices but otherwise unspecified.
  *  - Random numbers: draw n of particle (or stratum) i is Philox4x32-10 (Salmon et al.,
  *    SC'11) with key = seed and counter = (i, n, step mod 2^32, filter * 8 + scheme), so any
- *    result is reproducible from (seed, step) on any machine.
+ *    result is reproducible from (seed, step) on any machine. Some uses take several values
+ *    from one 128-bit block: stratum k of the stratified scheme uses word k mod 4 of block
+ *    (k / 4, 0) at 24 bits, or words 2 (k mod 2), 2 (k mod 2) + 1 of block (k / 2, 0) at 53
+ *    bits; binary32 Metropolis step n and binary32 rejection attempt n use half n mod 2 of
+ *    block (i, n / 2) (a 24-bit uniform and a 40-bit proposal index).
  */
 #ifndef RS_RESAMPLE_H
 #define RS_RESAMPLE_H
