@@ -493,3 +493,39 @@ def test_philox_throughput_kernel_draws_the_oracle_blocks(rs, h):
         rs.rs_philox_throughput(h, 0, 1)
     with pytest.raises(rs.RsError):
         rs.rs_philox_throughput(h, 10, 0)
+
+
+@pytest.mark.parametrize("N", [1, 2, 7, 8, 9, 255, 257, 2**18 - 1, 2**18, 2**18 + 7])
+def test_sorted_permute_from_claimed_bits(rs, h, N):
+    """The fused stratified/systematic path permutes from one claimed bit per particle and
+    follows Code 10's walks from their ends; its output must be Code 10's (oracle.permute of
+    the same call's unpermuted ancestors) on degenerate weights too: one particle carrying all
+    the weight (first, middle, last), two particles, equal weights, zero weights everywhere
+    (every slot then keeps itself), and weights that leave most particles without offspring.
+    Sizes on both sides of the four-slots-per-thread threshold and ragged byte tails."""
+    rng = np.random.default_rng(1000 + N)
+    cases = {"equal": np.zeros(N)}
+    for name, k in (("first", 0), ("middle", N // 2), ("last", N - 1)):
+        lw = np.full(N, -np.inf)
+        lw[k] = -3.0
+        cases["one_" + name] = lw
+    if N >= 2:
+        lw = np.full(N, -np.inf)
+        lw[[0, N - 1]] = [-1.0, 0.0]
+        cases["two"] = lw
+    cases["skewed"] = np.where(rng.random(N) < 0.05, rng.normal(0.0, 1.0, N), -40.0)
+    cases["spread"] = rng.normal(0.0, 3.0, N)
+    for dtype in (np.float32, np.float64):
+        for sch in (rs.SYSTEMATIC, rs.STRATIFIED):
+            for name, lw in cases.items():
+                x = lw.astype(dtype)
+                st0, a = _run(rs, h, sch, x, seed=17, step=N % 5)
+                st1, c = _run(rs, h, sch, x, seed=17, step=N % 5, permute=True)
+                assert st0 == st1 == rs.RS_OK, (name, st0, st1)
+                assert np.all(np.diff(a) >= 0), name
+                assert np.array_equal(c, oracle.permute(a)), (name, dtype, sch)
+            zero = np.full(N, -np.inf, dtype)
+            st, c = _run(rs, h, sch, zero, seed=1, permute=True)
+            assert st == rs.RS_ERR_ZERO_WEIGHT
+            assert np.array_equal(c, np.arange(N))
+    assert rs.rs_last_error(h) == rs.RS_OK
