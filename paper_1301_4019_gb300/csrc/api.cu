@@ -237,8 +237,8 @@ int rs_resample(rs_handle* h, int scheme, int dtype, const void* logw_dev, int64
   const bool f64 = dtype == RS_F64;
   int32_t* a_out = permute ? h->s.a_tmp : ancestors_dev;
   int32_t* d = permute ? h->s.d : nullptr;
-  // the fused stratified / systematic emission gives the sorted Permute its claimed bits
-  // (in the claims' buffer) instead of the claims
+  // the stratified / systematic emission gives the sorted Permute its claimed bits (in the
+  // claims' buffer) instead of the claims
   uint8_t* cl = nullptr;
   cudaError_t e = cudaSuccess;
   switch (scheme) {
@@ -248,7 +248,7 @@ int rs_resample(rs_handle* h, int scheme, int dtype, const void* logw_dev, int64
       const rsk::Acc acc = accumulation(dtype, o.prec);
       const int mode = h->s.launch_mode;
       const bool fused = mode != RS_LAUNCH_SEPARATE && rsk::fused_available(h->s, scheme, acc);
-      if (permute && fused && scheme != RS_MULTINOMIAL) {
+      if (permute && scheme != RS_MULTINOMIAL) {
         cl = reinterpret_cast<uint8_t*>(h->s.d);
         d = nullptr;
       }
@@ -265,10 +265,8 @@ int rs_resample(rs_handle* h, int scheme, int dtype, const void* logw_dev, int64
       break;
   }
   if (e == cudaSuccess && permute) {
-    if (cl)
+    if (cl)  // stratified, systematic: a non-decreasing ancestry
       e = rsk::launch_permute_sorted_bits(h->s, a_out, cl, N, ancestors_dev, s);
-    else if (scheme == RS_STRATIFIED || scheme == RS_SYSTEMATIC)  // non-decreasing ancestry
-      e = rsk::launch_permute_sorted(h->s, a_out, d, N, ancestors_dev, s);
     else
       e = rsk::launch_permute(h->s, a_out, d, N, ancestors_dev, s);
   }

@@ -49,65 +49,6 @@ permute_kernel(const int32_t* __restrict__ a, const int32_t* __restrict__ d, int
   permute_one(a, d, N, c, i, err);
 }
 
-// The same for a non-decreasing ancestry with its claims (permute_sorted_one).
-__global__ void __launch_bounds__(kBlock)
-permute_sorted_kernel(const int32_t* __restrict__ a, const int32_t* __restrict__ d, int64_t N,
-                      int32_t* __restrict__ c, int* err) {
-  pdl_wait();
-  const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (i >= N) return;
-  permute_sorted_one(a, d, N, c, i, err);
-}
-
-// Permute of a non-decreasing ancestry (permute_sorted_one) with four consecutive slots per
-// thread: the slot loads of a and d are 128-bit, and the walks of failed claims run together
-// (walk_queue: walks that end at their own slot at once, the others queued across the
-// warp and run one per lane). The reads and writes of each slot are those of
-// permute_sorted_one, so c is the same.
-__global__ void __launch_bounds__(kBlock)
-permute_sorted4_kernel(const int32_t* __restrict__ a, const int32_t* __restrict__ d, int64_t N,
-                       int32_t* __restrict__ c, int* err) {
-  pdl_wait();
-  const int64_t i0 = 4 * (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x);
-  // (no early exit: the walks are finished warp-wide; threads past N have no slots)
-  const int32_t sentinel = static_cast<int32_t>(N);
-  int32_t A[4], D[4];
-  const bool vec = i0 + 3 < N &&
-                   ((reinterpret_cast<uintptr_t>(a) | reinterpret_cast<uintptr_t>(d)) & 15u) == 0;
-  if (vec) {
-    const int4 va = *reinterpret_cast<const int4*>(a + i0);
-    const int4 vd = *reinterpret_cast<const int4*>(d + i0);
-    A[0] = va.x; A[1] = va.y; A[2] = va.z; A[3] = va.w;
-    D[0] = vd.x; D[1] = vd.y; D[2] = vd.z; D[3] = vd.w;
-  } else {
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      A[q] = i0 + q < N ? a[i0 + q] : 0;
-      D[q] = i0 + q < N ? d[i0 + q] : sentinel;
-    }
-  }
-  int32_t prev = (i0 > 0 && i0 - 1 < N) ? a[i0 - 1] : -1;
-  bool ok[4], fail[4];
-#pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    ok[q] = i0 + q < N;
-    if (ok[q] && (A[q] < 0 || A[q] >= N)) {
-      flag_error(err, RS_ERR_ARG);
-      ok[q] = false;
-    }
-    fail[q] = ok[q] && prev == A[q];  // the claim of slot i failed: a_{i-1} = a_i
-    prev = A[q];
-  }
-#pragma unroll
-  for (int q = 0; q < 4; ++q)
-    if (ok[q] && D[q] != sentinel) c[i0 + q] = static_cast<int32_t>(i0 + q);
-  int32_t x[4];
-#pragma unroll
-  for (int q = 0; q < 4; ++q) x[q] = static_cast<int32_t>(i0 + q);
-  __shared__ int2 pend[kBlock / 32][128];
-  walk_queue<4>(ClaimsOf{d}, sentinel, c, x, D, A, fail, N, pend[threadIdx.x >> 5], err);
-}
-
 // Permute of a non-decreasing ancestry from a and the claimed bits of its emission (cl: bit
 // i % 8 of cl[i / 8] set when particle i has offspring), K consecutive slots per thread. For
 // such an ancestry the claims of Prepermute are d_j = the first position of the run of j for
@@ -579,17 +520,6 @@ cudaError_t launch_permute(const Scratch& s, const int32_t* a, const int32_t* d,
 // Four slots per thread from 2^18 slots (measured 2 % faster at 2^20, 9 % at 2^22, 18 % at
 // 2^24); below, one slot per thread keeps more threads in flight.
 constexpr int64_t kSorted4MinN = int64_t{1} << 18;
-
-cudaError_t launch_permute_sorted(const Scratch& s, const int32_t* a, const int32_t* d, int64_t N,
-                                  int32_t* c, cudaStream_t st) {
-  trace_mark(s.trace, "permute_sorted", st);
-  if (N >= kSorted4MinN)
-    launch_pdl(permute_sorted4_kernel, static_cast<int>((N + 4 * kBlock - 1) / (4 * kBlock)),
-               kBlock, st, a, d, N, c, s.err);
-  else
-    launch_pdl(permute_sorted_kernel, grid_for(N), kBlock, st, a, d, N, c, s.err);
-  return cudaGetLastError();
-}
 
 cudaError_t launch_permute_sorted_bits(const Scratch& s, const int32_t* a, const uint8_t* cl,
                                        int64_t N, int32_t* c, cudaStream_t st) {

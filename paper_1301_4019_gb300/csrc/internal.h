@@ -161,9 +161,8 @@ cudaError_t launch_prepermute(const Scratch& s, const int32_t* a, int64_t N, int
                               bool init, cudaStream_t st);
 cudaError_t launch_permute(const Scratch& s, const int32_t* a, const int32_t* d, int64_t N,
                            int32_t* c, cudaStream_t st);
-cudaError_t launch_permute_sorted(const Scratch& s, const int32_t* a, const int32_t* d, int64_t N,
-                                  int32_t* c, cudaStream_t st);
-// the same from the claimed bits cl of the fused emission instead of the claims d
+// Permute of a non-decreasing ancestry (stratified, systematic) from the claimed bits cl of
+// its emission instead of the claims d
 cudaError_t launch_permute_sorted_bits(const Scratch& s, const int32_t* a, const uint8_t* cl,
                                        int64_t N, int32_t* c, cudaStream_t st);
 cudaError_t launch_offspring(const Scratch& s, const int32_t* a, int64_t N, int32_t* o,

@@ -51,37 +51,6 @@ __device__ __forceinline__ void permute_one(const int32_t* __restrict__ a,
   }
 }
 
-// The same slot when a is non-decreasing and d holds its claims (the systematic and stratified
-// ancestries of Code 11): the lowest claimant of particle a_i is the first position of its
-// run, so the claim of position i failed exactly when i > 0 and a_{i-1} = a_i. That replaces
-// the dependent load of d[a_i] by a load next to a_i; the writes are those of permute_one.
-__device__ __forceinline__ void permute_sorted_one(const int32_t* __restrict__ a,
-                                                   const int32_t* __restrict__ d, int64_t n,
-                                                   int32_t* __restrict__ c, int64_t i, int* err) {
-  const int32_t sentinel = static_cast<int32_t>(n);
-  const int32_t ai = a[i];
-  if (ai < 0 || ai >= n) {
-    flag_error(err, RS_ERR_ARG);
-    return;
-  }
-  const int32_t di = d[i];
-  if (di != sentinel) c[i] = static_cast<int32_t>(i);
-  if (i > 0 && a[i - 1] == ai) {
-    int64_t x = i;
-    int32_t dx = di;
-    int64_t steps = 0;
-    while (dx != sentinel) {
-      if (dx < 0 || dx > sentinel || ++steps > n) {  // only a corrupted d can get here
-        flag_error(err, RS_ERR_ARG);
-        return;
-      }
-      x = dx;
-      dx = d[x];
-    }
-    c[x] = ai;
-  }
-}
-
 // Claims of Code 10 read from the Prepermute vector d (d[x] = the lowest position whose
 // ancestor is x, or the sentinel n).
 struct ClaimsOf {
@@ -89,92 +58,15 @@ struct ClaimsOf {
   __device__ __forceinline__ int32_t operator()(int32_t x) const { return d[x]; }
 };
 
-// Walks of Code 10 for a whole warp, K walkers per lane: walker q stands at slot x[q] with
-// dx[q] = claim(x[q]) already loaded (claim: the Prepermute claim of a slot, the sentinel n
-// for an unclaimed one) and ends at the first unclaimed slot, where c receives val[q]. First
-// every lane moves its live walkers for at most kWalkRounds rounds, each round moving every
-// live walker one step and then issuing the claim loads of all of them together (up to K
-// dependent chains in flight per thread); then the walks still going are compacted into the
-// warp's shared list `pend` (32 K entries: slot reached and value) and finished one walk per
-// lane, 32 at a time. A warp otherwise runs as many rounds as its longest walk takes, with
-// most lanes predicated off. The walks start at distinct failed claims and are disjoint (see
-// permute_one), so every walk ends at its own unclaimed slot: c is the same as walking each
+// Walks of Code 10 for a whole warp, K walkers per lane, queued: walker q stands at slot
+// x[q] with dx[q] = claim(x[q]) already loaded (claim: the Prepermute claim of a slot, the
+// sentinel n for an unclaimed one) and ends at the first unclaimed slot, where c receives
+// val[q]. A walker whose claim ends at its own slot (dx = the sentinel) is done at once; the
+// others take their first step and are collected, by ballot, into the warp's shared list
+// `pend` (32 K entries), which the lanes then work off one walk each to its end (lane l takes
+// entries l, l + 32, ...), so every lane runs only walks that go on. The walks start at
+// distinct failed claims and are disjoint (see permute_one): c is the same as walking each
 // one alone. Called by all 32 lanes (lanes without walkers pass act = false).
-constexpr uint32_t kWalkRounds = 2;
-
-template <int K, typename Claim>
-__device__ __forceinline__ void walk_warp(const Claim& claim, int32_t sentinel,
-                                          int32_t* __restrict__ c, int32_t (&x)[K],
-                                          int32_t (&dx)[K], const int32_t (&val)[K],
-                                          bool (&act)[K], int64_t n, int2* pend, int* err) {
-  const uint32_t us = static_cast<uint32_t>(sentinel);
-  const int lane = threadIdx.x & 31;
-  bool bad = false;
-  for (uint32_t r = 0; r < kWalkRounds; ++r) {
-    bool any = false;
-#pragma unroll
-    for (int q = 0; q < K; ++q) {
-      if (!act[q]) continue;
-      const uint32_t v = static_cast<uint32_t>(dx[q]);
-      if (v >= us) {  // the sentinel (the walk ends here), or a corrupted claim
-        if (v == us) c[x[q]] = val[q]; else bad = true;
-        act[q] = false;
-      } else {
-        x[q] = dx[q];
-        any = true;
-      }
-    }
-    if (!any) break;  // (per lane)
-#pragma unroll
-    for (int q = 0; q < K; ++q)
-      if (act[q]) dx[q] = claim(x[q]);
-  }
-  // compaction of the walks still going (each at slot x with its claim loaded as dx)
-  int mine = 0;
-#pragma unroll
-  for (int q = 0; q < K; ++q) mine += static_cast<int>(act[q]);
-  int incl = mine;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const int y = __shfl_up_sync(0xffffffffu, incl, o);
-    if (lane >= o) incl += y;
-  }
-  const int total = __shfl_sync(0xffffffffu, incl, 31);
-  if (total > 0) {
-    int pos = incl - mine;
-#pragma unroll
-    for (int q = 0; q < K; ++q)
-      if (act[q]) pend[pos++] = make_int2(x[q], val[q]);
-    __syncwarp();
-    for (int b = 0; b < total; b += 32) {
-      if (b + lane < total) {
-        const int2 e = pend[b + lane];
-        int32_t xs = e.x;
-        for (int64_t steps = 0;; ++steps) {
-          const uint32_t v = static_cast<uint32_t>(claim(xs));
-          if (v == us) {
-            c[xs] = e.y;
-            break;
-          }
-          if (v > us || steps > n) {  // only a corrupted claim vector can get here
-            bad = true;
-            break;
-          }
-          xs = static_cast<int32_t>(v);
-        }
-      }
-    }
-    __syncwarp();
-  }
-  if (bad) flag_error(err, RS_ERR_ARG);
-}
-
-// The same walks, queued: a walker whose claim ends at its own slot (dx = the sentinel) is
-// done at once; the others take their first step and are collected, by ballot, into the warp's
-// shared list `pend` (32 K entries), which the lanes then work off one walk each to its end
-// (lane l takes entries l, l + 32, ...). Every lane runs only the walks that go on, instead of
-// K predicated walkers per round. c is the same as walking each one alone. Called by all 32
-// lanes.
 template <int K, typename Claim>
 __device__ __forceinline__ void walk_queue(const Claim& claim, int32_t sentinel,
                                            int32_t* __restrict__ c, const int32_t (&x)[K],

@@ -174,16 +174,19 @@ template <typename T, typename V, bool STRAT>
 __global__ void __launch_bounds__(kBlock)
 emit_cumoff_kernel(const T* __restrict__ lw, int64_t N, const ScanGlob* g, const double2* s_rec,
                    const double2* P_rec, Keys keys, int32_t* __restrict__ a,
-                   int32_t* __restrict__ d) {
+                   int32_t* __restrict__ d, uint8_t* __restrict__ cl) {
   pdl_wait();
   __shared__ SegSh sh;
   __shared__ float2 sh_tab[64];
   const int64_t base = static_cast<int64_t>(blockIdx.x) * kTile;
-  if (g->all_zero) {  // all weights zero: flagged; emit identity
-    for (int64_t i = base + threadIdx.x; i < N && i < base + kTile; i += kBlock) {
+  if (g->all_zero) {  // all weights zero: flagged; emit identity (every slot claimed)
+    const int64_t end = N < base + kTile ? N : base + kTile;
+    for (int64_t i = base + threadIdx.x; i < end; i += kBlock) {
       a[i] = static_cast<int32_t>(i);
       if (d) d[i] = static_cast<int32_t>(i);
     }
+    if (cl)  // (base is a multiple of 8)
+      for (int64_t b = (base >> 3) + threadIdx.x; b < ((end + 7) >> 3); b += kBlock) cl[b] = 0xFFu;
     return;
   }
   const WeightCtx wc = make_ctx<T, V>(g->M, sh_tab);
@@ -193,7 +196,7 @@ emit_cumoff_kernel(const T* __restrict__ lw, int64_t N, const ScanGlob* g, const
   const int64_t sg = static_cast<int64_t>(kWarps) * blockIdx.x + warp;
   emit_seg_cumoff<T, V, STRAT>(lw, 0, N, base + kSeg * warp, wc, vec, load_v<V>(P_rec + sg),
                                load_v<V>(P_rec + sg + 1), load_v<V>(&g->S_raw),
-                               load_v<V>(&g->scale_raw), u_sys, keys, a, d, sh.win[warp]);
+                               load_v<V>(&g->scale_raw), u_sys, keys, a, d, sh.win[warp], cl);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -345,11 +348,11 @@ cudaError_t run_scan(const Scratch& s, int scheme, Acc acc, const T* lw, int64_t
   if (scheme == RS_SYSTEMATIC) {
     trace_mark(s.trace, kLblSys[ai], st);
     launch_pdl(emit_cumoff_kernel<T, V, false>, tiles, kBlock, st, lw, N, s.glob, s_rec, P_rec, keys,
-                                                             a_out, d);
+               a_out, d, cl);
   } else if (scheme == RS_STRATIFIED) {
     trace_mark(s.trace, kLblStr[ai], st);
     launch_pdl(emit_cumoff_kernel<T, V, true>, tiles, kBlock, st, lw, N, s.glob, s_rec, P_rec, keys,
-                                                            a_out, d);
+               a_out, d, cl);
   } else {
     V* W = static_cast<V*>(s.W);
     trace_mark(s.trace, kLblW[ai], st);
