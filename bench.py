@@ -227,26 +227,26 @@ class ClockSampler:
 # headers it includes, hashed; `traffic` is null once any of them has changed.
 # ---------------------------------------------------------------------------------------
 NCU_TRAFFIC = {  # label: (bytes per launch, source hash)
-    "permute": (8397761, "d12f9b06a52d609d"),
-    "metropolis_f64": (16806290, "e0ca71fa2e23442f"),
-    "metropolis_f32": (8402752, "e0ca71fa2e23442f"),
-    "rejection_f64": (8420974, "e0ca71fa2e23442f"),
-    "fused_multinomial_f64": (8527008, "89e373c4e6b95bd3"),
-    "rejection_f32": (4212416, "e0ca71fa2e23442f"),
-    "fused_stratified_f64": (8513353, "89e373c4e6b95bd3"),
-    "permute_sorted": (4332962, "d12f9b06a52d609d"),
-    "fused_systematic_f64": (8506551, "89e373c4e6b95bd3"),
-    "fused_multinomial_f32": (4351360, "89e373c4e6b95bd3"),
-    "fused_stratified_f32": (4330816, "89e373c4e6b95bd3"),
-    "fused_systematic_f32": (4328736, "89e373c4e6b95bd3"),
-    "iscan": (4215152, "d12f9b06a52d609d"),
-    "search_f32": (12591104, "d3b9ad961ad2fadf"),
-    "search_f64": (16783104, "d3b9ad961ad2fadf"),
-    "cumoff_to_ancestors": (4204096, "d12f9b06a52d609d"),
-    "offspring": (8391344, "d12f9b06a52d609d"),
-    "fill": (8403, "d12f9b06a52d609d"),
-    "adjacent_difference": (4198720, "d12f9b06a52d609d"),
-    "sidecar": (8394240, "e0ca71fa2e23442f")}
+    "permute": (8397335, "c58a05fdbe177342"),
+    "metropolis_f64": (16816274, "d615c761ac6d902f"),
+    "metropolis_f32": (8406848, "d615c761ac6d902f"),
+    "rejection_f64": (8425509, "d615c761ac6d902f"),
+    "fused_multinomial_f64": (8526432, "3c6d5b24560863c7"),
+    "rejection_f32": (4211584, "d615c761ac6d902f"),
+    "fused_stratified_f64": (8513134, "3c6d5b24560863c7"),
+    "permute_sorted": (4333935, "c58a05fdbe177342"),
+    "fused_systematic_f64": (8505051, "3c6d5b24560863c7"),
+    "fused_multinomial_f32": (4349728, "3c6d5b24560863c7"),
+    "fused_stratified_f32": (4331584, "3c6d5b24560863c7"),
+    "fused_systematic_f32": (4327104, "3c6d5b24560863c7"),
+    "iscan": (4214048, "c58a05fdbe177342"),
+    "search_f32": (12592928, "efe338a438ab9d19"),
+    "search_f64": (16783872, "efe338a438ab9d19"),
+    "cumoff_to_ancestors": (4203984, "c58a05fdbe177342"),
+    "offspring": (8391328, "c58a05fdbe177342"),
+    "fill": (8392, "c58a05fdbe177342"),
+    "adjacent_difference": (4198352, "c58a05fdbe177342"),
+    "sidecar": (8394094, "d615c761ac6d902f")}
 
 _LABEL_FILES = (("fused_", "fused.cu"), ("permute", "aux.cu"), ("iscan", "aux.cu"),
                 ("fill", "aux.cu"), ("offspring", "aux.cu"), ("adjacent", "aux.cu"),
