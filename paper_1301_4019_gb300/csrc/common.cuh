@@ -190,6 +190,36 @@ __device__ __forceinline__ float exp_scan_f32(float t) {
 }
 
 // ---------------------------------------------------------------------------------------
+// L2 eviction priority of the streaming loads of the log-weights (a cache hint: the values
+// loaded are the same). A pass whose data the same launch reads again marks its loads
+// evict_last; the last pass over them marks its loads evict_first, leaving room in L2 for
+// what the next kernel reads (the ancestors written by the emission).
+// ---------------------------------------------------------------------------------------
+enum class L2Hint { kNormal, kEvictLast, kEvictFirst };
+__device__ __forceinline__ uint64_t l2_policy(L2Hint h) {
+  uint64_t p = 0;
+  if (h == L2Hint::kEvictLast)
+    asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+  else if (h == L2Hint::kEvictFirst)
+    asm("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+__device__ __forceinline__ float4 ld_stream(const float4* p, L2Hint h, uint64_t pol) {
+  if (h == L2Hint::kNormal) return __ldg(p);
+  float4 v;
+  asm("ld.global.nc.L2::cache_hint.v4.f32 {%0, %1, %2, %3}, [%4], %5;"
+      : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "l"(p), "l"(pol));
+  return v;
+}
+__device__ __forceinline__ double2 ld_stream(const double2* p, L2Hint h, uint64_t pol) {
+  if (h == L2Hint::kNormal) return __ldg(p);
+  double2 v;
+  asm("ld.global.nc.L2::cache_hint.v2.f64 {%0, %1}, [%2], %3;"
+      : "=d"(v.x), "=d"(v.y) : "l"(p), "l"(pol));
+  return v;
+}
+
+// ---------------------------------------------------------------------------------------
 // Programmatic dependent launch. Kernels of a call are launched with programmatic stream
 // serialization, so a kernel is set up while its predecessor drains; it waits here, before
 // touching memory, until the predecessor has completed and its writes are visible. (No

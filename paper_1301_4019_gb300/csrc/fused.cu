@@ -115,12 +115,14 @@ __device__ __forceinline__ void fused_body(const T* __restrict__ lw, const Fused
     bool bad = false;
     if constexpr (Path<T, V>::kTileRef) {
       T xn[kPer];
-      if (t1 > t0) load_per(lw, static_cast<int64_t>(t1 - 1) * kTile + off, 0, N, vec, xn);
+      if (t1 > t0)
+        load_per(lw, static_cast<int64_t>(t1 - 1) * kTile + off, 0, N, vec, xn, L2Hint::kEvictLast);
       for (int t = t1 - 1; t >= t0; --t) {
         T x[kPer];
 #pragma unroll
         for (int q = 0; q < kPer; ++q) x[q] = xn[q];
-        if (t > t0) load_per(lw, static_cast<int64_t>(t - 1) * kTile + off, 0, N, vec, xn);
+        if (t > t0)
+          load_per(lw, static_cast<int64_t>(t - 1) * kTile + off, 0, N, vec, xn, L2Hint::kEvictLast);
         const long long k = seg_record<T, V>(x, sh_tab, A.s_rec + kWarps * t + warp, bad);
         cm = k > cm ? k : cm;
       }
@@ -128,7 +130,7 @@ __device__ __forceinline__ void fused_body(const T* __restrict__ lw, const Fused
       float mf = -INFINITY;  // (binary32 inputs)
       for (int t = t0; t < t1; ++t) {
         T x[kPer];
-        load_per(lw, static_cast<int64_t>(t) * kTile + off, 0, N, vec, x);
+        load_per(lw, static_cast<int64_t>(t) * kTile + off, 0, N, vec, x, L2Hint::kEvictLast);
 #pragma unroll
         for (int q = 0; q < kPer; ++q) {
           bad |= !(x[q] <= FLT_MAX);  // NaN or +inf
@@ -180,7 +182,7 @@ __device__ __forceinline__ void fused_body(const T* __restrict__ lw, const Fused
       bool bad = false;
       for (int t = t1 - 1; t >= t0; --t)
         seg_record<T, V>(lw, 0, N, static_cast<int64_t>(t) * kTile + kSeg * warp, sh_tab, vec,
-                         A.s_rec + kWarps * t + warp, bad, max_key(Mt));
+                         A.s_rec + kWarps * t + warp, bad, max_key(Mt), L2Hint::kEvictLast);
       __syncthreads();  // (lane 0 of each warp stored them; all threads read them below)
     }
     for (int gb = g0; gb < g1; gb += kBlock) {
@@ -299,10 +301,11 @@ __device__ __forceinline__ void fused_body(const T* __restrict__ lw, const Fused
     const V Pn = (g + 1 < g1) ? load_v_cg<V>(A.P_rec + g + 1) : load_v<V>(&sh_pend);
     if constexpr (SCHEME == RS_MULTINOMIAL) {
       emit_seg_W_guide<T, V>(lw, 0, N, base, wc, vec, Ps, Pn, gd, static_cast<V*>(A.W), A.guide,
-                             sh.win[warp]);
+                             sh.win[warp], L2Hint::kEvictFirst);
     } else {
       emit_seg_cumoff<T, V, SCHEME == RS_STRATIFIED>(lw, 0, N, base, wc, vec, Ps, Pn, S, scale,
-                                                      u_sys, A.keys, A.a, A.d, sh.win[warp], A.cl);
+                                                      u_sys, A.keys, A.a, A.d, sh.win[warp], A.cl,
+                                                      L2Hint::kEvictFirst);
     }
   }
 }

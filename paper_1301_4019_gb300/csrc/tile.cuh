@@ -176,19 +176,21 @@ __device__ __forceinline__ void load4(const T* __restrict__ lw, int64_t idx, int
 // [lo, N) and the first is 16-byte aligned (one test for the eight), else guarded loads.
 template <typename T>
 __device__ __forceinline__ void load_per(const T* __restrict__ lw, int64_t idx, int64_t lo,
-                                         int64_t N, bool vec, T (&x)[kPer]) {
+                                         int64_t N, bool vec, T (&x)[kPer],
+                                         L2Hint hint = L2Hint::kNormal) {
   static_assert(kPer == 8, "eight consecutive values");
   constexpr int64_t kAlign = sizeof(T) == 4 ? 3 : 1;
   if (vec && idx >= lo && idx + kPer <= N && (idx & kAlign) == 0) {
+    const uint64_t pol = l2_policy(hint);
     if constexpr (sizeof(T) == 4) {
-      const float4 v0 = __ldg(reinterpret_cast<const float4*>(lw + idx));
-      const float4 v1 = __ldg(reinterpret_cast<const float4*>(lw + idx + 4));
+      const float4 v0 = ld_stream(reinterpret_cast<const float4*>(lw + idx), hint, pol);
+      const float4 v1 = ld_stream(reinterpret_cast<const float4*>(lw + idx + 4), hint, pol);
       x[0] = v0.x; x[1] = v0.y; x[2] = v0.z; x[3] = v0.w;
       x[4] = v1.x; x[5] = v1.y; x[6] = v1.z; x[7] = v1.w;
     } else {
 #pragma unroll
       for (int h = 0; h < 4; ++h) {
-        const double2 v = __ldg(reinterpret_cast<const double2*>(lw + idx + 2 * h));
+        const double2 v = ld_stream(reinterpret_cast<const double2*>(lw + idx + 2 * h), hint, pol);
         x[2 * h] = v.x;
         x[2 * h + 1] = v.y;
       }
@@ -833,9 +835,10 @@ template <typename T, typename V>
 __device__ __forceinline__ long long seg_record(const T* __restrict__ lw, int64_t lo, int64_t N,
                                                 int64_t base, const float2* tab, bool vec,
                                                 double2* rec, bool& bad,
-                                                long long ref = kTileMaxRef) {
+                                                long long ref = kTileMaxRef,
+                                                L2Hint hint = L2Hint::kNormal) {
   T x[kPer];
-  load_per(lw, base + kPer * static_cast<int64_t>(threadIdx.x & 31), lo, N, vec, x);
+  load_per(lw, base + kPer * static_cast<int64_t>(threadIdx.x & 31), lo, N, vec, x, hint);
   return seg_record<T, V>(x, tab, rec, bad, ref);
 }
 
@@ -859,10 +862,11 @@ __device__ __forceinline__ long long seg_record(const T* __restrict__ lw, int64_
 template <typename T, typename V>
 __device__ __forceinline__ void seg_cum_weights(const T* __restrict__ lw, int64_t lo, int64_t N,
                                                 int64_t base, const WeightCtx& wc, bool vec,
-                                                V Ps, V Pn, V (&W)[kPer], V& Wb) {
+                                                V Ps, V Pn, V (&W)[kPer], V& Wb,
+                                                L2Hint hint = L2Hint::kNormal) {
   const int lane = threadIdx.x & 31;
   T x[kPer];
-  load_per(lw, base + kPer * static_cast<int64_t>(lane), lo, N, vec, x);
+  load_per(lw, base + kPer * static_cast<int64_t>(lane), lo, N, vec, x, hint);
 #pragma unroll
   for (int q = 0; q < kPer; ++q) {
     const V wv = vfrom_w(Path<T, V>::weight(x[q], wc), V());
@@ -941,13 +945,14 @@ __device__ __forceinline__ void emit_seg_cumoff(const T* __restrict__ lw, int64_
                                                 typename Path<T, V>::U u_sys,
                                                 const Keys& keys, int32_t* __restrict__ a,
                                                 int32_t* __restrict__ d, int32_t* win,
-                                                uint8_t* __restrict__ cl = nullptr) {
+                                                uint8_t* __restrict__ cl = nullptr,
+                                                L2Hint hint = L2Hint::kNormal) {
   const int lane = threadIdx.x & 31;
   const int32_t n = static_cast<int32_t>(N - lo);
   const int cnt = seg_count(base, N) - kPer * lane;  // valid here
   const int32_t i0 = static_cast<int32_t>(base - lo) + kPer * lane;
   V W[kPer], Wb;
-  seg_cum_weights<T, V>(lw, lo, N, base, wc, vec, Ps, Pn, W, Wb);
+  seg_cum_weights<T, V>(lw, lo, N, base, wc, vec, Ps, Pn, W, Wb, hint);
   // O of this lane's particles; the last particle of the sequence gets n, and positions
   // past the end repeat the count before them (no offspring). A lane with a position past
   // the end holds the sequence's last particle or none, so its last count is n either way.
@@ -1090,13 +1095,14 @@ __device__ __forceinline__ void emit_seg_W_guide(const T* __restrict__ lw, int64
                                                  int64_t base, const WeightCtx& wc, bool vec,
                                                  V Ps, V Pn, const Guide& gd,
                                                  V* __restrict__ Wout,
-                                                 int32_t* __restrict__ G, int32_t* win) {
+                                                 int32_t* __restrict__ G, int32_t* win,
+                                                 L2Hint hint = L2Hint::kNormal) {
   const int lane = threadIdx.x & 31;
   const int32_t n = static_cast<int32_t>(N - lo);
   const int cnt = seg_count(base, N) - kPer * lane;
   const int32_t j0 = static_cast<int32_t>(base - lo) + kPer * lane;
   V W[kPer], Wb;
-  seg_cum_weights<T, V>(lw, lo, N, base, wc, vec, Ps, Pn, W, Wb);
+  seg_cum_weights<T, V>(lw, lo, N, base, wc, vec, Ps, Pn, W, Wb, hint);
   V* const p = Wout + base + kPer * static_cast<int64_t>(lane);
   int32_t C[kPer];
 #pragma unroll
