@@ -227,26 +227,26 @@ class ClockSampler:
 # headers it includes, hashed; `traffic` is null once any of them has changed.
 # ---------------------------------------------------------------------------------------
 NCU_TRAFFIC = {  # label: (bytes per launch, source hash)
-    "permute": (8397335, "c58a05fdbe177342"),
-    "metropolis_f64": (16816274, "d615c761ac6d902f"),
-    "metropolis_f32": (8406848, "d615c761ac6d902f"),
-    "rejection_f64": (8425509, "d615c761ac6d902f"),
-    "fused_multinomial_f64": (8526432, "3c6d5b24560863c7"),
-    "rejection_f32": (4211584, "d615c761ac6d902f"),
-    "fused_stratified_f64": (8513134, "3c6d5b24560863c7"),
-    "permute_sorted": (4333935, "c58a05fdbe177342"),
-    "fused_systematic_f64": (8505051, "3c6d5b24560863c7"),
-    "fused_multinomial_f32": (4349728, "3c6d5b24560863c7"),
-    "fused_stratified_f32": (4331584, "3c6d5b24560863c7"),
-    "fused_systematic_f32": (4327104, "3c6d5b24560863c7"),
-    "iscan": (4214048, "c58a05fdbe177342"),
-    "search_f32": (12592928, "efe338a438ab9d19"),
-    "search_f64": (16783872, "efe338a438ab9d19"),
-    "cumoff_to_ancestors": (4203984, "c58a05fdbe177342"),
-    "offspring": (8391328, "c58a05fdbe177342"),
-    "fill": (8392, "c58a05fdbe177342"),
-    "adjacent_difference": (4198352, "c58a05fdbe177342"),
-    "sidecar": (8394094, "d615c761ac6d902f")}
+    "permute": (8397926, "e733186968d7e6df"),
+    "metropolis_f64": (16800695, "c46523a1c822c284"),
+    "metropolis_f32": (8404544, "c46523a1c822c284"),
+    "fused_multinomial_f64": (8527008, "97e0f268cecd64bc"),
+    "rejection_f64": (8419657, "c46523a1c822c284"),
+    "rejection_f32": (4212192, "c46523a1c822c284"),
+    "fused_stratified_f64": (8512987, "97e0f268cecd64bc"),
+    "permute_sorted": (4333500, "e733186968d7e6df"),
+    "fused_systematic_f64": (8506295, "97e0f268cecd64bc"),
+    "fused_multinomial_f32": (4351392, "97e0f268cecd64bc"),
+    "fused_stratified_f32": (4331552, "97e0f268cecd64bc"),
+    "iscan": (4214240, "e733186968d7e6df"),
+    "fused_systematic_f32": (4326752, "97e0f268cecd64bc"),
+    "search_f32": (12592032, "1abea534c25ecb07"),
+    "search_f64": (16783872, "1abea534c25ecb07"),
+    "cumoff_to_ancestors": (4204688, "e733186968d7e6df"),
+    "offspring": (8391520, "e733186968d7e6df"),
+    "fill": (8437, "e733186968d7e6df"),
+    "adjacent_difference": (4198432, "e733186968d7e6df"),
+    "sidecar": (8394167, "c46523a1c822c284")}
 
 _LABEL_FILES = (("fused_", "fused.cu"), ("permute", "aux.cu"), ("iscan", "aux.cu"),
                 ("fill", "aux.cu"), ("offspring", "aux.cu"), ("adjacent", "aux.cu"),
