@@ -12,9 +12,10 @@
 //                      forms them in its first pass together with M.)
 //   3. emit pass     : the same tile scan is recomputed bit for bit, offset by P_t, and
 //                      turned into cumulative offspring O_i (systematic / stratified) with a
-//                      direct Code-11 scatter of the ancestors and the Prepermute claims; or
-//                      into stored cumulative weights W_i (multinomial, followed by the
-//                      search kernel).
+//                      direct Code-11 scatter of the ancestors and, for Permute, the claimed
+//                      bit of every particle (its Prepermute claim is the first position of
+//                      its run); or into stored cumulative weights W_i (multinomial, followed
+//                      by the search kernel).
 // Reading the weights twice is inherent: the normaliser W^N is needed before any O_i. The
 // reduce-then-scan order needs no inter-CTA waiting at all.
 //
