@@ -240,8 +240,8 @@ NCU_TRAFFIC = {  # label: (bytes per launch, source hash)
     "fused_stratified_f32": (4331552, "97e0f268cecd64bc"),
     "iscan": (4214240, "e733186968d7e6df"),
     "fused_systematic_f32": (4326752, "97e0f268cecd64bc"),
-    "search_f32": (12592032, "1abea534c25ecb07"),
-    "search_f64": (16783872, "1abea534c25ecb07"),
+    "search_f32": (12592032, "88475038523181d3"),
+    "search_f64": (16783872, "88475038523181d3"),
     "cumoff_to_ancestors": (4204688, "e733186968d7e6df"),
     "offspring": (8391520, "e733186968d7e6df"),
     "fill": (8437, "e733186968d7e6df"),
