@@ -290,6 +290,20 @@ def ncu_traffic(label: str, N: int):
 # ---------------------------------------------------------------------------------------
 # algorithmic bytes / operations per kernel launch (roofline numerators)
 # ---------------------------------------------------------------------------------------
+def rejection_expected_draws(w):
+    """Expected attempts and binary32 Philox blocks of one rejection call with weights w
+    (w_max = 1): particle i's attempt count T is 1 with probability w_i (attempt 0 proposes
+    i itself), else 1 + a geometric count of attempts that accept with p = mean(w). Binary32
+    attempts 2m, 2m + 1 share one block, so a particle draws ceil(T / 2) blocks:
+    E ceil(T / 2) = w_i + (1 - w_i) (1 + q / (1 - q^2)), q = 1 - p."""
+    w = np.asarray(w, dtype=np.float64)
+    p = w.mean()
+    q = 1.0 - p
+    attempts = int(len(w) + np.sum(1.0 - w) / p)
+    blocks = int(np.sum(w + (1.0 - w) * (1.0 + q / (1.0 - q * q))))
+    return attempts, blocks
+
+
 def kernel_roofline_units(label: str, N: int, B: int):
     """(bound, algorithmic amount per launch, unit) for a traced kernel label."""
     S = 8 if ("_f64" in label) else 4
@@ -592,11 +606,7 @@ def run_ours(args):
     # rejection: expected attempts per call N + sum_i (1 - w_i/w_max) / p, p = mean(w)/w_max
     # (w_max = 1: log w_max = 0), one Philox draw each
     w = np.exp(pools["f64"][0].double().cpu().numpy())
-    rej_attempts = int(N + np.sum(1.0 - w) / w.mean())
-    # binary32 attempts 2m, 2m + 1 share one block: E ceil(T / 2) per particle, T = 1 with
-    # probability w_i, else 1 + a geometric count of attempts accepting with p = mean(w)
-    q_rej = 1.0 - w.mean()
-    rej_blocks_f32 = int(np.sum(w + (1.0 - w) * (1.0 + q_rej / (1.0 - q_rej ** 2))))
+    rej_attempts, rej_blocks_f32 = rejection_expected_draws(w)
     if dom_label.startswith("rejection_"):
         amount = rej_blocks_f32 if dom_label.startswith("rejection_f32") else rej_attempts
     if bound == "hbm":

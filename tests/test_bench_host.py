@@ -1,5 +1,6 @@
 """Host logic of bench.py that needs no GPU: the algorithmic amount behind every roofline, the
 DRAM-traffic table's source hashing, and the sweep's byte counts."""
+import numpy as np
 import pytest
 
 import bench
@@ -70,3 +71,25 @@ def test_cpu_baseline_on_all_cores_runs_the_oracle():
     r = bench.cpu_all_cores(1 << 10, 4, 2.0, steps=1)
     assert r["value"] > 0 and r["cores"] == (os.cpu_count() or 1)
     assert "10 independent oracle calls" in r["sample"]
+
+
+def test_rejection_expected_draws_against_simulation():
+    """The expected attempts and binary32 Philox blocks (two attempts per block) of a
+    rejection call, against a direct simulation of every particle's attempt count."""
+    rng = np.random.default_rng(5)
+    N = 2000
+    w = np.exp(-0.5 * (rng.standard_normal(N) - 2.0) ** 2)
+    attempts, blocks = bench.rejection_expected_draws(w)
+    p = w.mean()
+    R = 400
+    t_sum = 0
+    b_sum = 0
+    for _ in range(R):
+        first = rng.random(N) < w                       # attempt 0 proposes i itself
+        more = rng.geometric(p, N)                      # later attempts until one accepts
+        T = np.where(first, 1, 1 + more)
+        t_sum += T.sum()
+        b_sum += ((T + 1) // 2).sum()
+    assert abs(t_sum / R - attempts) < 0.01 * attempts
+    assert abs(b_sum / R - blocks) < 0.01 * blocks
+    assert blocks < attempts
